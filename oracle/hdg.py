@@ -1,0 +1,333 @@
+"""H(div)-HDG local systems, static condensation and the exact discrete solution.
+
+TEST INFRASTRUCTURE ONLY (see oracle/__init__.py).
+
+Scheme (Section 3.2, eq. stWeak): find (L_h, u_h, û_h, p_h) in
+W^k × RT_k × V̂^k × W^k with, on every cell,
+  (ν⁻¹L, G) + (∇u, G) − ⟨tng(u − û), G n⟩                      = 0,
+  −(L, ∇v) + ⟨L n, tng(v − v̂)⟩ + β(u, v) − (p, div v)           = (f, v),
+  (div u, q)                                                        = 0.
+The oracle writes this full local matrix over (L, u, û, p) by quadrature in
+physical coordinates, then eliminates the local unknowns (L, the interior RT
+moments, the mean-free part of p) by a plain dense Schur complement
+(Section 3.2, "we first eliminate the local variables").  What remains per
+cell is the condensed matrix A_K on the 3(2k+2) facet unknowns (RT normal
+moments and tangential Legendre coefficients), the condensed load F_K, and
+the flux row d_K (∫_{∂K} v·n of each unknown) that carries B (eq. stOptForm).
+The augmented-Lagrangian operator adds ε⁻¹|K|⁻¹ d_K d_Kᵀ with ε⁻¹ = γν
+(eq. stALform, written per cell because (div u, div v)_K = |K|⁻¹(d_K·u)(d_K·v)
+for the piecewise-constant divergence of the global space).
+
+Local unknown order on a cell (the layout the library uses as well): facet
+f = 0, 1, 2 (opposite local vertex f), and within a facet the normal moments
+m = 0..k followed by the tangential coefficients m = 0..k.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from workloads.manufactured import lattice_barycentric_2d
+
+from .quadrature import triangle_points
+from .spaces import Element, exponents
+from .topology import Topology
+
+
+def _signature(X, gv, k, nu, beta):
+    rel = np.ascontiguousarray(X - X[0])
+    ranks = tuple(np.argsort(np.argsort(np.asarray(gv))).tolist())
+    return (rel.tobytes(), ranks, k, float(nu), float(beta))
+
+
+@dataclass
+class CondensedCell:
+    A: np.ndarray        # (ng, ng) condensed matrix without the AL term
+    d: np.ndarray        # (ng,) flux row: d·x = ∫_{∂K} u·n_K
+    Fmap: np.ndarray     # (ng, n_lat*2) lattice forcing -> condensed load
+    area: float
+    # recovery: local unknowns y_l = Rf f - Rg x_g - Rp p_K
+    Rf: np.ndarray
+    Rg: np.ndarray
+    Rp: np.ndarray
+    el: Element
+    lat_inv: np.ndarray  # lattice Vandermonde inverse (monomials of degree k+1)
+
+
+def local_system(el: Element, nu: float, beta: float):
+    """Full local matrix over (L, u, û, p), forcing map and index sets."""
+    k = el.k
+    npk = len(exponents(k))
+    nL, nrt, nh, npp = 4 * npk, el.n_rt, 3 * (k + 1), npk
+    oL, ou, oh, op = 0, nL, nL + nrt, nL + nrt + nh
+    n = op + npp
+    M = np.zeros((n, n))
+    xq, wq = triangle_points(el.X, k + 3)
+    Pk = el.mono(xq, k)
+    mean = (wq @ Pk) / el.area
+    pv = Pk - mean[None, :]
+    pv[:, 0] = 1.0                      # exponents(k)[0] == (0, 0): global P0 part
+    U = el.rt_values(xq)
+    GU = el.rt_grads(xq)
+    DU = GU[:, :, 0, 0] + GU[:, :, 1, 1]
+    Mp = (Pk * wq[:, None]).T @ Pk
+    for ce in range(4):
+        M[oL + ce * npk:oL + (ce + 1) * npk, oL + ce * npk:oL + (ce + 1) * npk] = Mp / nu
+    # (∇u, G)
+    for c in range(2):
+        for e in range(2):
+            ce = 2 * c + e
+            M[oL + ce * npk:oL + (ce + 1) * npk, ou:ou + nrt] += (Pk * wq[:, None]).T @ GU[:, :, c, e]
+    for f in range(3):
+        fd = el.facets[f]
+        s, xf, wf = el.facet_points(f, k + 3)
+        Uf = el.rt_values(xf)
+        nK = fd["nK"]
+        tngU = Uf - np.einsum("qi,c->qic", Uf @ nK, nK)
+        Pf = el.mono(xf, k)
+        lm = el.facet_legendre(f, s)
+        for c in range(2):
+            for e in range(2):
+                ce = 2 * c + e
+                rows = slice(oL + ce * npk, oL + (ce + 1) * npk)
+                # − ⟨tng(u), G n⟩
+                M[rows, ou:ou + nrt] -= (Pf * (wf * nK[e])[:, None]).T @ tngU[:, :, c]
+                # + ⟨tng(û), G n⟩ with û = ℓ_m t_F on this facet
+                M[rows, oh + f * (k + 1):oh + (f + 1) * (k + 1)] += \
+                    (Pf * (wf * nK[e] * fd["t"][c])[:, None]).T @ lm
+    # −(L, ∇v) + ⟨L n, tng(v)⟩ and −⟨L n, tng(v̂)⟩ are the negative transposes
+    M[ou:ou + nrt, oL:oL + nL] = -M[oL:oL + nL, ou:ou + nrt].T
+    M[oh:oh + nh, oL:oL + nL] = -M[oL:oL + nL, oh:oh + nh].T
+    M[ou:ou + nrt, ou:ou + nrt] += beta * np.einsum("q,qic,qjc->ij", wq, U, U)
+    Bd = np.einsum("q,qi,qj->ij", wq, DU, pv)
+    M[ou:ou + nrt, op:op + npp] = -Bd
+    M[op:op + npp, ou:ou + nrt] = Bd.T
+    # forcing: f_h ∈ [P^{k+1}]² from its values at the degree-(k+1) lattice
+    lam = lattice_barycentric_2d(k + 1)
+    Xl = lam @ el.X
+    lat_inv = np.linalg.inv(el.mono(Xl, k + 1))
+    Lq = el.mono(xq, k + 1) @ lat_inv                     # (q, n_lat) lattice Lagrange values
+    Rf = np.einsum("q,qn,qic->inc", wq, Lq, U).reshape(nrt, -1)
+    rhs_map = np.zeros((n, Rf.shape[1]))
+    rhs_map[ou:ou + nrt] = Rf
+    g = []
+    for f in range(3):
+        g += [ou + f * (k + 1) + m for m in range(k + 1)]
+        g += [oh + f * (k + 1) + m for m in range(k + 1)]
+    loc = list(range(oL, oL + nL)) + list(range(ou + 3 * (k + 1), ou + nrt)) + \
+        list(range(op + 1, op + npp))
+    return M, rhs_map, np.asarray(g), np.asarray(loc), op, lat_inv, \
+        dict(oL=oL, ou=ou, oh=oh, op=op, npk=npk, nrt=nrt)
+
+
+def condense_cell(el: Element, nu: float, beta: float) -> CondensedCell:
+    """Static condensation of one cell by a dense Schur complement."""
+    M, rhs_map, g, loc, p0, lat_inv, _ = local_system(el, nu, beta)
+    Mll = M[np.ix_(loc, loc)]
+    Mlg = M[np.ix_(loc, g)]
+    Mgl = M[np.ix_(g, loc)]
+    X = np.linalg.solve(Mll, np.hstack([Mlg, M[loc, p0][:, None], rhs_map[loc]]))
+    ng = len(g)
+    Xg, Xp, Xf = X[:, :ng], X[:, ng], X[:, ng + 1:]
+    A = M[np.ix_(g, g)] - Mgl @ Xg
+    d = M[p0, g] - M[p0, loc] @ Xg
+    Fmap = rhs_map[g] - Mgl @ Xf
+    return CondensedCell(A=A, d=d, Fmap=Fmap, area=el.area, Rf=Xf, Rg=Xg, Rp=Xp,
+                         el=el, lat_inv=lat_inv)
+
+
+class HDG:
+    """Condensed H(div)-HDG operator of order k on one mesh level."""
+
+    def __init__(self, topo: Topology, k: int, nu: float = 1.0, beta: float = 0.0,
+                 gamma: float = 0.0, nu_elem: Optional[np.ndarray] = None,
+                 cache: bool = True):
+        self.topo, self.k = topo, k
+        self.dpf = 2 * (k + 1)
+        self.ng = 3 * self.dpf
+        self.nu = float(nu)
+        self.beta = float(beta)
+        self.gamma = float(gamma)
+        nc = topo.n_cells
+        self.nu_elem = np.full(nc, self.nu) if nu_elem is None else np.asarray(nu_elem, float)
+        self.n_dof = topo.n_interior * self.dpf
+        self.cells = []
+        memo = {}
+        for c in range(nc):
+            gv = topo.cells[c]
+            X = topo.coords[gv]
+            key = _signature(X, gv, k, self.nu_elem[c], beta) if cache else None
+            if key is not None and key in memo:
+                cc = memo[key]
+            else:
+                el = Element(X - X[0], gv, k)
+                cc = condense_cell(el, self.nu_elem[c], beta)
+                if key is not None:
+                    memo[key] = cc
+            self.cells.append(cc)
+        self.area = np.array([cc.area for cc in self.cells])
+        self.eps_inv = self.gamma * self.nu_elem
+        # local → global unknown map (−1 for boundary facets)
+        self.l2g = -np.ones((nc, self.ng), dtype=np.int64)
+        for c in range(nc):
+            for f in range(3):
+                i = topo.interior_index[topo.cell_facets[c, f]]
+                if i >= 0:
+                    self.l2g[c, f * self.dpf:(f + 1) * self.dpf] = i * self.dpf + np.arange(self.dpf)
+
+    # ------------------------------------------------------------ element data
+    def element_matrix(self, c: int, with_al: bool = True) -> np.ndarray:
+        cc = self.cells[c]
+        A = cc.A.copy()
+        if with_al:
+            A += (self.eps_inv[c] / cc.area) * np.outer(cc.d, cc.d)
+        return A
+
+    def element_load(self, c: int, fvals_c: np.ndarray) -> np.ndarray:
+        return self.cells[c].Fmap @ np.asarray(fvals_c).reshape(-1)
+
+    # ------------------------------------------------------------ global
+    def matrix(self, with_al: bool = True) -> sp.csr_matrix:
+        rows, cols, vals = [], [], []
+        for c in range(self.topo.n_cells):
+            idx = self.l2g[c]
+            m = idx >= 0
+            A = self.element_matrix(c, with_al)[np.ix_(m, m)]
+            I = idx[m]
+            rows.append(np.repeat(I, len(I)))
+            cols.append(np.tile(I, len(I)))
+            vals.append(A.ravel())
+        return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(self.n_dof, self.n_dof))
+
+    def flux_matrix(self) -> sp.csr_matrix:
+        """D (n_cells × n_dof): (D u)_K = ∫_{∂K} u·n_K = |K| (div u)_K."""
+        rows, cols, vals = [], [], []
+        for c in range(self.topo.n_cells):
+            idx = self.l2g[c]
+            m = idx >= 0
+            rows.append(np.full(int(m.sum()), c))
+            cols.append(idx[m])
+            vals.append(self.cells[c].d[m])
+        return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                             shape=(self.topo.n_cells, self.n_dof))
+
+    def load(self, fvals: np.ndarray) -> np.ndarray:
+        """Condensed load F (n_dof,) from lattice forcing (n_cells, n_lat, 2)."""
+        F = np.zeros(self.n_dof)
+        for c in range(self.topo.n_cells):
+            idx = self.l2g[c]
+            m = idx >= 0
+            F[idx[m]] += self.element_load(c, fvals[c])[m]
+        return F
+
+    def gather(self, x: np.ndarray, c: int) -> np.ndarray:
+        idx = self.l2g[c]
+        out = np.zeros(self.ng)
+        out[idx >= 0] = x[idx[idx >= 0]]
+        return out
+
+    # ------------------------------------------------------------ exact solve
+    def solve_direct(self, F: np.ndarray):
+        """Exact discrete solution of A u − Dᵀp = F, D u = 0, Σ|K|p_K = 0.
+
+        The condensed saddle point of eq. stOptForm (the B-rows are the cell
+        fluxes; the mean-zero pressure is imposed by one Lagrange multiplier).
+        Returns (u (n_dof,), p (n_cells,)).
+        """
+        A = self.matrix(with_al=False)
+        D = self.flux_matrix()
+        nc = self.topo.n_cells
+        w = sp.csr_matrix(self.area[:, None])
+        K = sp.bmat([[A, -D.T, None], [D, None, w], [None, w.T, None]], format="csc")
+        rhs = np.concatenate([F, np.zeros(nc + 1)])
+        sol = spla.splu(K).solve(rhs)
+        return sol[:self.n_dof], sol[self.n_dof:self.n_dof + nc]
+
+    # ------------------------------------------------------------ recovery
+    def recover_cell(self, c: int, u: np.ndarray, pK: float, fvals_c: np.ndarray):
+        """Local fields on cell c: (L coeffs (4, npk), RT coeffs (n_rt,), p coeffs (npk,))."""
+        cc = self.cells[c]
+        k = self.k
+        npk = len(exponents(k))
+        xg = self.gather(u, c)
+        y = cc.Rf @ np.asarray(fvals_c).reshape(-1) - cc.Rg @ xg - cc.Rp * pK
+        nL = 4 * npk
+        Lc = y[:nL].reshape(4, npk)
+        nrt = cc.el.n_rt
+        rt = np.zeros(nrt)
+        for f in range(3):
+            rt[f * (k + 1):(f + 1) * (k + 1)] = xg[f * self.dpf:f * self.dpf + k + 1]
+        n_int = nrt - 3 * (k + 1)
+        rt[3 * (k + 1):] = y[nL:nL + n_int]
+        pc = np.concatenate([[pK], y[nL + n_int:]])
+        return Lc, rt, pc
+
+    def fields_at(self, c, coeffs, xq):
+        """Evaluate (L (q,2,2), u (q,2), div u (q,), p (q,)) at points xq (translated)."""
+        Lc, rt, pc = coeffs
+        el = self.cells[c].el
+        Pk = el.mono(xq, self.k)
+        L = np.einsum("qr,cr->qc", Pk, Lc).reshape(-1, 2, 2)
+        U = el.rt_values(xq)
+        u = np.einsum("qic,i->qc", U, rt)
+        divu = el.rt_div(xq) @ rt
+        # pressure basis: 1 and mean-free monomials (same as in local_system)
+        xq2, wq2 = triangle_points(el.X, self.k + 3)
+        mean = (wq2 @ el.mono(xq2, self.k)) / el.area
+        pv = Pk - mean[None, :]
+        pv[:, 0] = 1.0
+        p = pv @ pc
+        return L, u, divu, p
+
+    def errors(self, u, p, fvals, sol, nq: Optional[int] = None):
+        """L2 errors of u_h, L_h (L = −ν∇u), p_h (both mean-free), ‖div u_h‖, and u*.
+
+        The post-processed u* ∈ [P^{k+1}]² solves, per cell,
+        (∇u*, ∇v)_K = (−ν⁻¹L_h, ∇v)_K and (u*, 1)_K = (u_h, 1)_K (eq. stPost,
+        read with L = −ν∇u so that ∇u* approximates ∇u).
+        """
+        k = self.k
+        nq = nq or (k + 5)
+        eu = eL = ediv = eus = 0.0
+        pint = pex_int = 0.0
+        ph_vals, pe_vals, wts = [], [], []
+        for c in range(self.topo.n_cells):
+            X0 = self.topo.coords[self.topo.cells[c][0]]
+            el = self.cells[c].el
+            xq, wq = triangle_points(el.X, nq)
+            coeffs = self.recover_cell(c, u, p[c], fvals[c])
+            L, uh, divu, ph = self.fields_at(c, coeffs, xq)
+            xa = xq + X0
+            ue = sol.u(xa)
+            Le = -self.nu_elem[c] * sol.grad_u(xa)
+            eu += wq @ np.sum((ue - uh) ** 2, axis=1)
+            eL += wq @ np.sum((Le - L) ** 2, axis=(1, 2))
+            ediv += wq @ divu ** 2
+            ph_vals.append(ph)
+            pe_vals.append(sol.p(xa))
+            wts.append(wq)
+            # post-processing u* in [P^{k+1}]^2
+            Gm = el.mono_grad(xq, k + 1)
+            Mo = el.mono(xq, k + 1)
+            S = np.einsum("q,qid,qjd->ij", wq, Gm, Gm)
+            S[0, :] = wq @ Mo
+            us = np.zeros((Mo.shape[1], 2))
+            for a in range(2):
+                r = np.einsum("q,qid,qd->i", wq, Gm, -L[:, a, :] / self.nu_elem[c])
+                r[0] = wq @ uh[:, a]
+                us[:, a] = np.linalg.solve(S, r)
+            ustar = Mo @ us
+            eus += wq @ np.sum((ue - ustar) ** 2, axis=1)
+        ph = np.concatenate(ph_vals)
+        pe = np.concatenate(pe_vals)
+        w = np.concatenate(wts)
+        ph = ph - (w @ ph) / w.sum()
+        pe = pe - (w @ pe) / w.sum()
+        ep = np.sqrt(w @ (ph - pe) ** 2)
+        return dict(u=np.sqrt(eu), L=np.sqrt(eL), p=ep, div=np.sqrt(ediv), ustar=np.sqrt(eus))

@@ -1,0 +1,143 @@
+"""Flexible GMRES and the augmented-Lagrangian Uzawa iteration (oracle).
+
+TEST INFRASTRUCTURE ONLY.
+
+* FGMRES (right preconditioning, preconditioner allowed to vary): Arnoldi
+  with classical Gram–Schmidt applied twice, Givens rotations on the
+  Hessenberg matrix, stop when the Euclidean norm of the residual vector
+  is <= an absolute target (the caller derives it from the relative 1e-8 /
+  absolute 1e-10 settings of Section 5), restart length 30.  The Krylov
+  method is GMRES throughout because the mixed-precision preconditioner is
+  not exactly linear; the paper uses PCG for Stokes (Section 3.3).
+* Uzawa (eq. stOpEq-ALU): p⁰ = 0;  A^ε u⁽ⁿ⁾ = F − B*p⁽ⁿ⁻¹⁾;
+  p⁽ⁿ⁾ = p⁽ⁿ⁻¹⁾ − ε⁻¹ div u⁽ⁿ⁾ on every cell.  With the flux matrix D
+  ((D u)_K = ∫_{∂K} u·n) this is  A^ε u = F + Dᵀp,  p_K ← p_K − ε⁻¹ (Du)_K/|K|.
+  The update is written with div u: with B as defined in eq. stOptForm
+  ([Bu, q] = −(div u, q)) the printed sign would make the iteration diverge;
+  the form above is the one whose error contracts by ε/(ε+μ0) per step
+  (Lemma 3.1).  The inner solves are warm-started from the previous u and,
+  as in Section 5, stop at relative 1e-8 / absolute 1e-10, but never below
+  floor_rel·‖F‖ (default 1e-9; Remark 3.1: much smaller residuals are
+  round-off at large ε⁻¹):
+  ‖g − A^ε u‖ <= max(rtol·‖g − A^ε u_start‖, floor_rel·‖F‖, atol).
+  The outer loop stops once the pressure error estimate of a linearly
+  converging iteration, ρ/(1−ρ)·‖p⁽ⁿ⁾ − p⁽ⁿ⁻¹⁾‖ with ρ the observed ratio of
+  successive updates (Lemma 3.1 gives ρ = ε/(ε+μ0)), is <= uzawa_tol·‖p⁽ⁿ⁾‖
+  in L2(Ω), or when an inner solve makes no progress.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Callable, List
+
+import numpy as np
+import scipy.linalg as sla
+
+
+def fgmres(A, b, x0, M: Callable, rtol: float = 1e-8, atol: float = 1e-10,
+           restart: int = 30, max_it: int = 1000):
+    """Solve A x = b to ‖r‖ <= max(rtol‖r0‖, atol).
+
+    Returns (x, iterations, final residual norm, history of residual norms).
+    """
+    x = np.array(x0, dtype=np.float64, copy=True)
+    total = 0
+    hist = []
+    tol = None
+    while True:
+        r = b - A @ x
+        beta = float(np.linalg.norm(r))
+        if tol is None:
+            tol = max(rtol * beta, atol)
+        hist.append(beta)
+        if beta <= tol or total >= max_it:
+            return x, total, beta, hist
+        n = b.shape[0]
+        V = np.zeros((restart + 1, n))
+        Z = np.zeros((restart, n))
+        H = np.zeros((restart + 1, restart))
+        cs = np.zeros(restart)
+        sn = np.zeros(restart)
+        g = np.zeros(restart + 1)
+        g[0] = beta
+        V[0] = r / beta
+        j_end = 0
+        for j in range(restart):
+            Z[j] = M(V[j])
+            w = A @ Z[j]
+            h1 = V[:j + 1] @ w
+            w = w - V[:j + 1].T @ h1
+            h2 = V[:j + 1] @ w
+            w = w - V[:j + 1].T @ h2
+            h = h1 + h2
+            hn = float(np.linalg.norm(w))
+            col = np.zeros(restart + 1)
+            col[:j + 1] = h
+            col[j + 1] = hn
+            for i in range(j):
+                a, bb = col[i], col[i + 1]
+                col[i] = cs[i] * a + sn[i] * bb
+                col[i + 1] = -sn[i] * a + cs[i] * bb
+            den = float(np.hypot(col[j], col[j + 1]))
+            cs[j] = col[j] / den
+            sn[j] = col[j + 1] / den
+            col[j] = den
+            col[j + 1] = 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+            H[:, j] = col
+            total += 1
+            j_end = j
+            hist.append(abs(g[j + 1]))
+            if abs(g[j + 1]) <= tol or total >= max_it or hn == 0.0:
+                break
+            V[j + 1] = w / hn
+        m = j_end + 1
+        y = sla.solve_triangular(H[:m, :m], g[:m])
+        x = x + Z[:m].T @ y
+
+
+@dataclass
+class UzawaResult:
+    u: np.ndarray
+    p: np.ndarray
+    krylov_its: List[int] = field(default_factory=list)
+    res_mom: float = 0.0
+    res_div: float = 0.0
+    dp_rel: float = 0.0
+    normF: float = 0.0
+
+
+def uzawa(Aeps, D, area, eps_inv, F, M: Callable, rtol: float = 1e-8, atol: float = 1e-10,
+          restart: int = 30, max_it: int = 1000, max_uzawa: int = 200,
+          uzawa_tol: float = 1e-8, floor_rel: float = 1e-9, u0=None) -> UzawaResult:
+    """Augmented-Lagrangian Uzawa with FGMRES inner solves (eq. stOpEq-ALU)."""
+    normF = float(np.linalg.norm(F))
+    u = np.zeros_like(F) if u0 is None else np.array(u0, copy=True)
+    p = np.zeros(D.shape[0])
+    res = UzawaResult(u=u, p=p, normF=normF)
+    floor = max(floor_rel * normF, atol)
+    ndp_prev = None
+    for n in range(max_uzawa):
+        g = F + D.T @ p
+        u, its, rn, _ = fgmres(Aeps, g, u, M, rtol=rtol, atol=floor, restart=restart,
+                               max_it=max_it)
+        du = D @ u
+        dp = eps_inv * du / area
+        p = p - dp
+        res.krylov_its.append(its)
+        res.res_mom = rn
+        res.res_div = float(np.linalg.norm(du))
+        ndp = float(np.sqrt(area @ dp ** 2))
+        npn = float(np.sqrt(area @ p ** 2))
+        res.dp_rel = ndp / npn if npn > 0 else 0.0
+        if ndp <= atol or (n > 0 and its == 0):
+            break
+        if ndp_prev is not None:
+            rho = min(ndp / ndp_prev, 0.99)
+            if rho / (1.0 - rho) * ndp <= uzawa_tol * npn:
+                break
+        ndp_prev = ndp
+    res.u, res.p = u, p
+    return res

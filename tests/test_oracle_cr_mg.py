@@ -1,0 +1,348 @@
+"""Pins of the oracle's lowest-order equivalence, transfers, smoothers, MG and Krylov.
+
+* Theorem 3.1: the condensed lowest-order H(div)-HDG operator (with the AL
+  term) equals T^T A_CR T for an independently assembled pressure-robust CR
+  scheme, T = Π^CR; loads match; solutions relate by eq. solRelation.
+* Lemma 3.2: Π^RT Π^CR v = v and div Π^CR v = div v.
+* Averaging transfer (eq. avgOpt) reproduces fields whose CR representation
+  is a global linear function.
+* Harmonic extension (eqs. div-transfer, harmonic-ex): (A^ε 𝓘v)_T = 0; the
+  energy of 𝓘v stays bounded uniformly in the AL parameter, while plain
+  averaging grows with it (the reason for the correction).
+* Block GS: after a patch update its residual vanishes; MG_hp is symmetric
+  (reverse sweeps + transposed restriction).
+* FGMRES: exact preconditioner ⇒ one iteration; Uzawa error contracts per
+  step by ε/(ε+μ0) with exact inner solves (Lemma 3.1).
+* Iteration counts: flat in the mesh size and the AL parameter, mildly
+  growing in k (Section 5.2.1 claims); paper's table as context.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse.linalg as spla
+
+from workloads import unit_square, unit_square_hierarchy, curl_bubble_2d, forcing_at_lattice
+from oracle.hdg import HDG
+from oracle.spaces import Element
+from oracle.cr import cr_system, pi_cr_matrix, _bary
+from oracle.mg import (averaging_prolongation, interior_fine_dofs, harmonic_prolongation,
+                       vertex_patches, BlockGS, build_hpmg)
+from oracle.krylov import fgmres, uzawa
+from oracle.quadrature import triangle_points
+from _util import topo_of, hierarchy, forcing, rel
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.mark.parametrize("beta", [0.0, 3.0])
+def test_theorem_3_1_operator_and_load(beta):
+    m = unit_square_hierarchy(2, 3, jitter=0.3, seed=7, shuffle_seed=2)[-1]
+    t = topo_of(m)
+    nu, gamma = 1.7, 50.0
+    h = HDG(t, 0, nu=nu, beta=beta, gamma=gamma)
+    fv = forcing(m, 0, curl_bubble_2d(), nu, beta)
+    Acr, Fcr = cr_system(t, nu, beta, gamma * nu, fv)
+    T = pi_cr_matrix(t)
+    assert rel((T.T @ Acr @ T).toarray(), h.matrix().toarray()) < 1e-13
+    assert rel(T.T @ Fcr, h.load(fv)) < 1e-13
+
+
+def test_theorem_3_1_solution_relation():
+    m = unit_square(6, shuffle_seed=4)
+    t = topo_of(m)
+    nu, beta = 1.0, 2.0
+    h = HDG(t, 0, nu=nu, beta=beta)
+    fv = forcing(m, 0, curl_bubble_2d(), nu, beta)
+    u, p = h.solve_direct(h.load(fv))
+    # independent CR saddle point: [A_CR, -D_CR^T; D_CR, 0] with mean-zero pressure
+    import scipy.sparse as sp
+    Acr, Fcr = cr_system(t, nu, beta, 0.0, fv)
+    T = pi_cr_matrix(t)
+    D = h.flux_matrix() @ spla.inv(T.tocsc())      # fluxes as functions of CR values
+    w = sp.csr_matrix(h.area[:, None])
+    K = sp.bmat([[Acr, -D.T, None], [D, None, w], [None, w.T, None]], format="csc")
+    sol = spla.splu(K).solve(np.concatenate([Fcr, np.zeros(t.n_cells + 1)]))
+    ucr = sol[:Acr.shape[0]]
+    pcr = sol[Acr.shape[0]:Acr.shape[0] + t.n_cells]
+    assert rel(T @ u, ucr) < 1e-11            # Π^CR u_h = u^CR
+    assert rel(p, pcr) < 1e-10                # p_h = p^CR
+    # L_h = -nu grad u^CR on every cell
+    for c in range(t.n_cells):
+        Lc, rt, pc = h.recover_cell(c, u, p[c], fv[c])
+        X = t.coords[t.cells[c]]
+        lam_grad = np.linalg.inv(np.stack([X[1] - X[0], X[2] - X[0]], 1))
+        G = np.stack([-lam_grad[0] - lam_grad[1], lam_grad[0], lam_grad[1]])
+        grad = np.zeros((2, 2))
+        for i in range(3):
+            ii = t.interior_index[t.cell_facets[c, i]]
+            if ii >= 0:
+                grad += np.outer(ucr[2 * ii:2 * ii + 2], -2.0 * G[i])
+        assert np.allclose(Lc.reshape(2, 2), -nu * grad, atol=1e-9)
+
+
+def test_lemma_3_2():
+    rng = np.random.default_rng(0)
+    X = np.array([[0.0, 0.1], [1.1, 0.0], [0.2, 0.9]])
+    el = Element(X, [4, 9, 1], 0)
+    xq, _ = triangle_points(X, 4)
+    lam = _bary(X, xq)
+    area = el.area
+    for _ in range(3):
+        c = rng.standard_normal((3, 2))     # (c_n, c_t) per local facet
+        # RT0 part of the HDG function
+        vh = np.einsum("qic,i->qc", el.rt_values(xq), c[:, 0])
+        # Π^CR: midpoint values, then Π^RT: RT0 with the CR fluxes
+        cr_mid = np.stack([(c[f, 0] * el.facets[f]["nF"] + c[f, 1] * el.facets[f]["t"])
+                           / np.sqrt(el.facets[f]["L"]) for f in range(3)])
+        prt = np.zeros_like(vh)
+        div_cr = 0.0
+        G = np.linalg.inv(np.stack([X[1] - X[0], X[2] - X[0]], 1))
+        Gb = np.stack([-G[0] - G[1], G[0], G[1]])
+        for i in range(3):
+            fd = el.facets[i]
+            flux = fd["L"] * cr_mid[i] @ fd["nK"]
+            prt += flux * (xq - X[i]) / (2 * area)
+            div_cr += cr_mid[i] @ (-2.0 * Gb[i])
+        assert np.abs(prt - vh).max() < 1e-13 * max(1, np.abs(vh).max())
+        assert abs(div_cr - el.rt_div(xq[:1])[0] @ c[:, 0]) < 1e-12
+
+
+def test_averaging_reproduces_constant_fields():
+    ms, ts, ps = hierarchy(2, 2, jitter=0.25, seed=3, shuffle_seed=5)
+    c, f = ts
+    I = averaging_prolongation(c, f, ps[1])
+    a = np.array([0.7, -1.3])
+
+    def dofs(t):
+        v = np.zeros(2 * t.n_interior)
+        for i, F in enumerate(t.interior_facets):
+            _, _, L, tt, nF = t.facet_geometry(F)
+            v[2 * i] = np.sqrt(L) * a @ nF
+            v[2 * i + 1] = np.sqrt(L) * a @ tt
+        return v
+    # constants vanish on the boundary only if the boundary facets are dropped:
+    # compare on fine facets away from the coarse boundary
+    vf = I @ dofs(c)
+    ef = dofs(f)
+    bnd = set()
+    for F in range(c.facets.shape[0]):
+        if c.facet_cells[F, 1] < 0:
+            bnd.update(c.facets[F].tolist())
+    ok = []
+    for i, F in enumerate(f.interior_facets):
+        c0, c1 = f.facet_cells[F]
+        cells = {ps[1][c0], ps[1][c1]}
+        touches = any(c.interior_index[c.cell_facets[K, j]] < 0 for K in cells for j in range(3))
+        if not touches:
+            ok += [2 * i, 2 * i + 1]
+    assert len(ok) > 0
+    assert np.abs(vf[ok] - ef[ok]).max() < 1e-13
+
+
+def _two_level(gamma, jitter=0.0):
+    ms, ts, ps = hierarchy(2, 3, jitter=jitter, seed=1)
+    hc = HDG(ts[1], 0, gamma=gamma)
+    hf = HDG(ts[2], 0, gamma=gamma)
+    Af, Ac = hf.matrix(), hc.matrix()
+    Ia = averaging_prolongation(ts[1], ts[2], ps[2])
+    T = interior_fine_dofs(ts[2], ps[2])
+    return Af, Ac, Ia, T
+
+
+def test_harmonic_extension_property():
+    Af, Ac, Ia, T = _two_level(1e3, jitter=0.2)
+    P = harmonic_prolongation(Af, Ia, T)
+    v = np.random.default_rng(2).standard_normal(Ac.shape[0])
+    r = Af @ (P @ v)
+    assert np.abs(r[T]).max() < 1e-10 * np.abs(r).max()
+    # outside T the harmonic transfer agrees with plain averaging
+    notT = np.setdiff1d(np.arange(Af.shape[0]), T)
+    assert np.abs((P @ v)[notT] - (Ia @ v)[notT]).max() < 1e-14
+
+
+def test_transfer_energy_robust_in_gamma():
+    ratios_h, ratios_a = [], []
+    for gamma in [1.0, 1e2, 1e4, 1e6]:
+        Af, Ac, Ia, T = _two_level(gamma)
+        P = harmonic_prolongation(Af, Ia, T)
+        Ac_d = Ac.toarray()
+        for Q, store in ((P, ratios_h), (Ia, ratios_a)):
+            E = (Q.T @ Af @ Q).toarray()
+            store.append(sla.eigh(E, Ac_d, eigvals_only=True).max())
+    assert max(ratios_h) < 5 * min(ratios_h) and max(ratios_h) < 20
+    assert ratios_a[-1] > 1e3 * ratios_a[0]
+
+
+def test_block_gs_patch_residual_vanishes():
+    t = topo_of(unit_square(3, shuffle_seed=2))
+    h = HDG(t, 2, gamma=100.0)
+    A = h.matrix()
+    pats = vertex_patches(t, h.dpf)
+    assert sum(len(d) for _, d in pats) == 2 * h.n_dof      # every facet sits in 2 patches
+    gs = BlockGS(A, pats)
+    g = np.random.default_rng(3).standard_normal(h.n_dof)
+    u = gs.forward(g, np.zeros(h.n_dof))
+    last = pats[-1][1]
+    assert np.abs((g - A @ u)[last]).max() < 1e-10 * np.abs(g).max()
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_mghp_symmetric(k):
+    ms, ts, ps = hierarchy(2, 3, shuffle_seed=9)
+    M = build_hpmg(ts, ps, k, 1.0, 1.0, 100.0)
+    rng = np.random.default_rng(4)
+    x, y = rng.standard_normal((2, M.A.shape[0]))
+    assert abs(x @ M(y) - y @ M(x)) < 1e-11 * abs(x @ M(y))
+
+
+def test_fgmres_exact_preconditioner_one_step():
+    t = topo_of(unit_square(3))
+    h = HDG(t, 1, gamma=10.0)
+    A = h.matrix().tocsc()
+    lu = spla.splu(A)
+    b = np.random.default_rng(5).standard_normal(h.n_dof)
+    x, its, rn, _ = fgmres(A, b, np.zeros_like(b), lu.solve, rtol=1e-12, atol=0.0)
+    assert its == 1 and rel(x, lu.solve(b)) < 1e-12
+    x2, its2, _, _ = fgmres(A, b, np.zeros_like(b), lambda v: v, rtol=1e-10, atol=0.0,
+                            restart=8, max_it=5000)
+    assert rel(x2, lu.solve(b)) < 1e-7 and its2 > 8          # restarts exercised
+
+
+@pytest.mark.parametrize("gamma", [1.0, 10.0])
+def test_uzawa_contraction_lemma_3_1(gamma):
+    m = unit_square(4)
+    t = topo_of(m)
+    nu = 1.0
+    h = HDG(t, 1, nu=nu, beta=1.0, gamma=gamma)
+    fv = forcing(m, 1, curl_bubble_2d(), nu, 1.0)
+    F = h.load(fv)
+    u_ex, p_ex = h.solve_direct(F)
+    A = h.matrix(with_al=False).toarray()
+    D = h.flux_matrix().toarray()
+    Mp = np.diag(h.area)
+    S = D @ np.linalg.solve(A, D.T)
+    mu = sla.eigh(S, Mp, eigvals_only=True)
+    mu0 = np.sort(mu)[1]                         # drop the constant-pressure null mode
+    eps = 1.0 / (gamma * nu)
+    rate = eps / (eps + mu0)
+    Ae = h.matrix(with_al=True).tocsc()
+    lu = spla.splu(Ae)
+    p = np.zeros(t.n_cells)
+    errs = []
+    for _ in range(6):
+        u = lu.solve(F + D.T @ p)
+        p = p - h.eps_inv * (D @ u) / h.area
+        e = p - p_ex
+        e -= (h.area @ e) / h.area.sum()
+        errs.append(np.sqrt(h.area @ e ** 2))
+    ratios = np.array(errs[1:]) / np.array(errs[:-1])
+    assert ratios.max() <= rate * (1 + 1e-6)
+    assert ratios[-1] > 0.5 * rate
+
+
+def _pcg_its(A, b, M, rtol=1e-8):
+    """Preconditioned CG (the paper's Krylov method for Stokes, Section 5) iteration count."""
+    x = np.zeros_like(b)
+    r = b.copy()
+    z = M(r)
+    p = z.copy()
+    rz = rz0 = r @ z
+    for it in range(1, 500):
+        Ap = A @ p
+        a = rz / (p @ Ap)
+        x += a * p
+        r -= a * Ap
+        z = M(r)
+        rzn = r @ z
+        if np.sqrt(rzn) <= rtol * np.sqrt(rz0):
+            return it
+        p = z + (rzn / rz) * p
+        rz = rzn
+    return 500
+
+
+class _ExactLowest:
+    def __init__(self, A):
+        self.lu = spla.splu(A.tocsc())
+
+    def __call__(self, g, m, q, u0=None):
+        return self.lu.solve(g)
+
+
+def test_hp_relaxation_reproduces_paper_counts_with_exact_lowest_order():
+    """Algorithm 2 with the lowest-order solve done exactly: PCG counts flat in h.
+
+    The paper's k = 2, m = 1, V-cycle counts (Table tab:stokesLid) are 17, 19, 20, 20;
+    this configuration (structured stand-in meshes, gamma = 1e4, beta = 0) gives
+    counts in the same narrow band.
+    """
+    from oracle.mg import MGhp
+    table = np.loadtxt(os.path.join(GOLDEN, "paper_table_stokes_lid_2d.txt"))
+    paper = table[table[:, 0] == 2][:, 2]
+    its = []
+    for nl in (3, 4, 5):
+        ms, ts, ps = hierarchy(2, nl)
+        h = HDG(ts[-1], 2, beta=0.0, gamma=1e4)
+        A0 = HDG(ts[-1], 0, beta=0.0, gamma=1e4).matrix()
+        M = MGhp(h, _ExactLowest(A0))
+        F = h.load(forcing(ms[-1], 2, curl_bubble_2d(), 1.0, 0.0))
+        its.append(_pcg_its(M.A, F, M))
+    assert max(its) - min(its) <= 3
+    assert abs(np.mean(its) - paper.mean()) <= 3
+
+
+def test_two_level_galerkin_robust():
+    """Smoother + harmonic transfer with a Galerkin coarse operator: contraction
+    bounded independently of h and of the AL parameter (Theorem 3.2 premise)."""
+    from oracle.mg import Level
+    facs = []
+    for Nc in (2, 4, 8):
+        for gamma in (1.0, 1e4):
+            ms, ts, ps = hierarchy(Nc, 2)
+            Lf = Level(HDG(ts[1], 0, gamma=gamma))
+            Ia = averaging_prolongation(ts[0], ts[1], ps[1])
+            P = harmonic_prolongation(Lf.A, Ia, interior_fine_dofs(ts[1], ps[1]))
+            lu = spla.splu((P.T @ Lf.A @ P).tocsc())
+            A = Lf.A
+            e = np.random.default_rng(0).standard_normal(A.shape[0])
+            z = np.zeros_like(e)
+            for _ in range(25):
+                u = e.copy()
+                Lf.gs.forward(z, u)
+                u += P @ lu.solve(P.T @ (-(A @ u)))
+                Lf.gs.backward(z, u)
+                nrm = np.sqrt(u @ (A @ u))
+                rho = nrm / np.sqrt(e @ (A @ e))
+                e = u / nrm
+            facs.append(rho)
+    assert max(facs) < 0.45
+
+
+def test_iteration_counts_mild_growth():
+    """Full Algorithm 2 (V-cycle MG_h on rediscretised CR levels): counts stay in the
+    paper's range and grow only mildly with refinement and k (Section 5.2.1)."""
+    def counts(nl, k, gamma):
+        ms, ts, ps = hierarchy(2, nl)
+        h = HDG(ts[-1], k, beta=1.0, gamma=gamma)
+        M = build_hpmg(ts, ps, k, 1.0, 1.0, gamma, hdg_k=h)
+        F = h.load(forcing(ms[-1], k, curl_bubble_2d(), 1.0, 1.0))
+        return fgmres(M.A, F, np.zeros_like(F), M, rtol=1e-8, atol=1e-10)[1]
+    c = [counts(nl, 2, g) for nl in (3, 4) for g in (1e2, 1e4)]
+    assert max(c) <= 30 and min(c) >= 12
+    assert abs(counts(3, 2, 1e2) - counts(3, 2, 1e4)) <= 2          # robust in gamma
+    assert counts(3, 3, 1e2) - counts(3, 1, 1e2) <= 4                 # mild growth in k
+
+
+def test_uzawa_solves_saddle_point():
+    ms, ts, ps = hierarchy(2, 3)
+    h = HDG(ts[-1], 2, beta=1.0, gamma=100.0)
+    M = build_hpmg(ts, ps, 2, 1.0, 1.0, 100.0, hdg_k=h)
+    fv = forcing(ms[-1], 2, curl_bubble_2d(), 1.0, 1.0)
+    F = h.load(fv)
+    r = uzawa(M.A, h.flux_matrix(), h.area, h.eps_inv, F, M)
+    u, p = h.solve_direct(F)
+    assert np.linalg.norm(r.u - u) < 1e-9 * np.linalg.norm(u)
+    e = r.p - p
+    assert np.linalg.norm(e) < 1e-7 * np.linalg.norm(p)

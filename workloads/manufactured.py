@@ -1,0 +1,189 @@
+"""Manufactured solutions of the generalized Stokes problem and forcing samples.
+
+The model problem is -div(nu grad u) + beta u + grad p = f, div u = 0 in
+Omega = (0,1)^2, u = 0 on the boundary (Section 3.1, eq. stModel).  Each
+solution below is given in closed form together with its gradient and its
+Laplacian, so that the forcing f = -nu Δu + beta u + grad p is exact.
+
+* ``curl_bubble_2d``: u = curl psi = (d psi/dy, -d psi/dx) with
+  psi = sin²(pi x) sin²(pi y) and p = sin(2 pi x) cos(2 pi y).
+* ``polynomial_2d``: the paper's 2D convergence-check solution
+  (Section 5.1), u = (-g(x) g'(y), g'(x) g(y)) with g(t) = t²(t-1)² and
+  p = x(1-x)(1-y) - 1/12.
+
+Forcing enters the library as values of a vector polynomial of degree k+1 on
+each cell, sampled at the cell's degree-(k+1) lattice points (see
+``lattice_points_2d``).  Sampling the exact f there defines the discrete
+forcing f_h ∈ [P^{k+1}(K)]^2 element by element.
+"""
+
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Callable, Optional
+
+import numpy as np
+
+PI = np.pi
+
+
+@dataclass
+class Solution2D:
+    """Exact velocity, velocity gradient, pressure and Laplacian at points."""
+    u: Callable[[np.ndarray], np.ndarray]        # (n,2) -> (n,2)
+    grad_u: Callable[[np.ndarray], np.ndarray]   # (n,2) -> (n,2,2), [i,j] = d u_i / d x_j
+    lap_u: Callable[[np.ndarray], np.ndarray]    # (n,2) -> (n,2)
+    p: Callable[[np.ndarray], np.ndarray]        # (n,2) -> (n,)
+    grad_p: Callable[[np.ndarray], np.ndarray]   # (n,2) -> (n,2)
+
+    def forcing(self, nu: float, beta: float,
+                conv: Optional[Callable[[np.ndarray], np.ndarray]] = None
+                ) -> Callable[[np.ndarray], np.ndarray]:
+        """f = -nu Δu + beta u + grad p (+ (b·grad) u when a convecting field b is given)."""
+        def f(x):
+            val = -nu * self.lap_u(x) + beta * self.u(x) + self.grad_p(x)
+            if conv is not None:
+                b = conv(x)
+                val = val + np.einsum("nij,nj->ni", self.grad_u(x), b)
+            return val
+        return f
+
+
+def curl_bubble_2d() -> Solution2D:
+    s = lambda t: np.sin(PI * t) ** 2
+    s1 = lambda t: PI * np.sin(2 * PI * t)
+    s2 = lambda t: 2 * PI ** 2 * np.cos(2 * PI * t)
+    s3 = lambda t: -4 * PI ** 3 * np.sin(2 * PI * t)
+
+    def u(x):
+        X, Y = x[:, 0], x[:, 1]
+        return np.stack([s(X) * s1(Y), -s1(X) * s(Y)], axis=1)
+
+    def grad_u(x):
+        X, Y = x[:, 0], x[:, 1]
+        g = np.empty((x.shape[0], 2, 2))
+        g[:, 0, 0] = s1(X) * s1(Y)
+        g[:, 0, 1] = s(X) * s2(Y)
+        g[:, 1, 0] = -s2(X) * s(Y)
+        g[:, 1, 1] = -s1(X) * s1(Y)
+        return g
+
+    def lap_u(x):
+        X, Y = x[:, 0], x[:, 1]
+        return np.stack([s2(X) * s1(Y) + s(X) * s3(Y),
+                         -s3(X) * s(Y) - s1(X) * s2(Y)], axis=1)
+
+    def p(x):
+        return np.sin(2 * PI * x[:, 0]) * np.cos(2 * PI * x[:, 1])
+
+    def grad_p(x):
+        X, Y = x[:, 0], x[:, 1]
+        return np.stack([2 * PI * np.cos(2 * PI * X) * np.cos(2 * PI * Y),
+                         -2 * PI * np.sin(2 * PI * X) * np.sin(2 * PI * Y)], axis=1)
+
+    return Solution2D(u, grad_u, lap_u, p, grad_p)
+
+
+def polynomial_2d() -> Solution2D:
+    g = lambda t: t ** 2 * (t - 1) ** 2
+    g1 = lambda t: 4 * t ** 3 - 6 * t ** 2 + 2 * t
+    g2 = lambda t: 12 * t ** 2 - 12 * t + 2
+    g3 = lambda t: 24 * t - 12
+
+    def u(x):
+        X, Y = x[:, 0], x[:, 1]
+        return np.stack([-g(X) * g1(Y), g1(X) * g(Y)], axis=1)
+
+    def grad_u(x):
+        X, Y = x[:, 0], x[:, 1]
+        G = np.empty((x.shape[0], 2, 2))
+        G[:, 0, 0] = -g1(X) * g1(Y)
+        G[:, 0, 1] = -g(X) * g2(Y)
+        G[:, 1, 0] = g2(X) * g(Y)
+        G[:, 1, 1] = g1(X) * g1(Y)
+        return G
+
+    def lap_u(x):
+        X, Y = x[:, 0], x[:, 1]
+        return np.stack([-g2(X) * g1(Y) - g(X) * g3(Y),
+                         g3(X) * g(Y) + g1(X) * g2(Y)], axis=1)
+
+    def p(x):
+        X, Y = x[:, 0], x[:, 1]
+        return X * (1 - X) * (1 - Y) - 1.0 / 12.0
+
+    def grad_p(x):
+        X, Y = x[:, 0], x[:, 1]
+        return np.stack([(1 - 2 * X) * (1 - Y), -X * (1 - X)], axis=1)
+
+    return Solution2D(u, grad_u, lap_u, p, grad_p)
+
+
+def n_lattice_2d(q: int) -> int:
+    return (q + 1) * (q + 2) // 2
+
+
+def lattice_barycentric_2d(q: int) -> np.ndarray:
+    """(n, 3) barycentric coordinates of the degree-q lattice of a triangle.
+
+    Order: for a2 = 0..q, for a1 = 0..q-a2: (lambda1, lambda2) = (a1/q, a2/q),
+    lambda0 = 1 - lambda1 - lambda2.  For q = 0 the single point is the centroid.
+    """
+    if q == 0:
+        return np.array([[1 / 3, 1 / 3, 1 / 3]])
+    pts = []
+    for a2 in range(q + 1):
+        for a1 in range(q + 1 - a2):
+            l1, l2 = a1 / q, a2 / q
+            pts.append((1 - l1 - l2, l1, l2))
+    return np.asarray(pts)
+
+
+def lattice_points_2d(coords: np.ndarray, cells: np.ndarray, q: int) -> np.ndarray:
+    """(n_cells, n_lattice, 2) physical lattice points of every cell."""
+    lam = lattice_barycentric_2d(q)
+    V = coords[cells]                      # (nc, 3, 2)
+    return np.einsum("pv,cvd->cpd", lam, V)
+
+
+def forcing_at_lattice(coords: np.ndarray, cells: np.ndarray, k: int,
+                       f: Callable[[np.ndarray], np.ndarray]) -> np.ndarray:
+    """Forcing samples (n_cells, n_lattice(k+1), 2) at the degree-(k+1) lattice."""
+    X = lattice_points_2d(coords, cells, k + 1)
+    nc, npt, _ = X.shape
+    return f(X.reshape(-1, 2)).reshape(nc, npt, 2)
+
+
+def gradient_field_2d(a: np.ndarray):
+    """grad phi for phi = sum_{i+j<=deg} a[i,j] x^i y^j (a: (deg+1, deg+1)).
+
+    Used to add an irrotational field to the forcing; returns (phi, grad phi).
+    """
+    deg = a.shape[0] - 1
+
+    def phi(x):
+        X, Y = x[:, 0], x[:, 1]
+        out = np.zeros(x.shape[0])
+        for i in range(deg + 1):
+            for j in range(deg + 1 - i):
+                out += a[i, j] * X ** i * Y ** j
+        return out
+
+    def grad(x):
+        X, Y = x[:, 0], x[:, 1]
+        gx = np.zeros(x.shape[0])
+        gy = np.zeros(x.shape[0])
+        for i in range(deg + 1):
+            for j in range(deg + 1 - i):
+                if i > 0:
+                    gx += a[i, j] * i * X ** (i - 1) * Y ** j
+                if j > 0:
+                    gy += a[i, j] * j * X ** i * Y ** (j - 1)
+        return np.stack([gx, gy], axis=1)
+
+    return phi, grad
+
+
+def seeded_vector(n: int, seed: int, dtype=np.float64) -> np.ndarray:
+    """Standard-normal test vector from numpy's PCG64 with the given seed."""
+    return np.random.default_rng(seed).standard_normal(n).astype(dtype)
