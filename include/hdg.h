@@ -1,0 +1,244 @@
+/*
+ * hdg.h — C ABI of the GB300 library for the hp-multigrid preconditioned
+ * flexible GMRES solver of the statically condensed H(div)-HDG discretisation
+ * of the generalized Stokes equation with an augmented-Lagrangian term
+ * (G. Fu & W. Kuang, "hp-multigrid preconditioner for a divergence-conforming
+ * HDG scheme for the incompressible flow problems").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Meshes: conforming triangulations (dim = 2) given level by level, level 0
+ * the coarsest, each finer level a uniform (red) refinement of the previous
+ * one (Section 3.4.2).  Local facet f of a cell is the facet opposite local
+ * vertex f.  Facets are numbered in lexicographic order of their sorted
+ * global vertex pair; a facet is oriented from its lower to its higher
+ * global vertex id (unit tangent t_F, unit normal n_F = (t_y, -t_x), facet
+ * parameter s in [0,1] from the lower vertex).  Boundary facets carry the
+ * homogeneous Dirichlet condition (Section 3.1) and own no unknowns.
+ *
+ * Skeleton vectors (order k): for every interior facet, in facet order,
+ * dpf = 2(k+1) doubles: the normal moments  int_F (u.n_F) l_m ds, m = 0..k,
+ * then the tangential coefficients of the facet unknown in the same basis,
+ * where l_m = sqrt(2m+1) P_m(2s-1) / sqrt|F| is L2-orthonormal on F.
+ * n_dof = n_interior_facets * dpf.  Vectors are dual (load/residual) or
+ * primal (solution) in this one layout; the condensed operator is the
+ * matrix of the bilinear form in this basis.
+ *
+ * Element matrices: per cell, n_loc x n_loc with n_loc = 3 dpf, row-major,
+ * local unknown order facet 0,1,2 and within a facet the dpf unknowns above
+ * (boundary facets included: the matrix is the cell's own Schur complement).
+ *
+ * Forcing: per cell, the values of f_h in [P^{k+1}(K)]^2 at the degree-(k+1)
+ * lattice, points x = v0 + (a1/q)(v1-v0) + (a2/q)(v2-v0) with q = k+1,
+ * ordered a2 = 0..q outer, a1 = 0..q-a2 inner, each point 2 doubles (x, y
+ * components).  Layout [n_cells][n_lat][2], n_lat = (q+1)(q+2)/2.
+ *
+ * Pressure: one double per cell (the cell-constant pressure p^∂ of the
+ * condensed saddle point, eq. stOptForm).
+ *
+ * Memory: pointers documented "device" must be device memory on the
+ * context's device; "host" pointers are host memory.  The caller owns every
+ * buffer it passes; the context owns the mesh data, element and patch
+ * matrices and all workspaces and frees them in hdg_destroy.
+ *
+ * Streams: every call that takes a stream enqueues its work on that stream
+ * (NULL = legacy default stream).  hdg_condense and hdg_solve synchronise
+ * the stream before returning so that their status is final.
+ *
+ * Errors: no exception crosses the ABI.  Each call returns an hdg_status;
+ * hdg_last_error(ctx) gives a message for the last failure on the context.
+ * After HDG_ERR_CUDA the context must be destroyed.  One context per host
+ * thread at a time.
+ */
+#ifndef HDG_H
+#define HDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hdg_ctx hdg_ctx;
+typedef struct CUstream_st *hdg_stream_t;   /* the cudaStream_t type */
+
+typedef enum {
+    HDG_OK = 0,
+    HDG_ERR_INVALID_ARG = 1,   /* a size, pointer or option is out of range          */
+    HDG_ERR_OOM = 2,           /* device or host allocation failed                  */
+    HDG_ERR_CUDA = 3,          /* a CUDA runtime call or kernel failed              */
+    HDG_ERR_SINGULAR = 4,      /* a local, patch or coarse matrix has a pivot <= 0  */
+    HDG_ERR_NOT_CONVERGED = 5, /* iteration limit reached before the tolerance      */
+    HDG_ERR_BREAKDOWN = 6,     /* Krylov breakdown with a nonzero residual          */
+    HDG_ERR_NONFINITE = 7,     /* NaN or Inf in a residual                          */
+    HDG_ERR_UNSUPPORTED = 8,   /* valid request this build does not implement       */
+    HDG_ERR_STATE = 9          /* call order violated (e.g. solve before condense)  */
+} hdg_status;
+
+typedef enum {
+    HDG_FP64 = 0,        /* preconditioner in FP64                                 */
+    HDG_MIXED_FP32 = 1   /* preconditioner (smoothers, transfers, V-cycle) in FP32; */
+                         /* outer operator, Krylov, coarse solve stay FP64          */
+} hdg_precision;
+
+typedef struct {
+    int dim;                              /* 2                                      */
+    int n_levels;                         /* >= 1, level 0 = coarsest               */
+    const int64_t *n_vertices;            /* host [n_levels]                        */
+    const int64_t *n_cells;               /* host [n_levels]                        */
+    const double *const *coords;          /* host [n_levels] -> [n_vertices*dim]    */
+    const int32_t *const *cells;          /* host [n_levels] -> [n_cells*(dim+1)]   */
+    const int32_t *const *parent;         /* host [n_levels] -> [n_cells]: cell of  */
+                                          /* level l-1 containing each cell of l;   */
+                                          /* entry 0 is ignored                      */
+    const int32_t *const *vertex_colour;  /* host [n_levels] -> [n_vertices] proper */
+                                          /* colouring, or NULL / NULL entries for  */
+                                          /* greedy colouring in vertex-id order    */
+} hdg_mesh_desc;
+
+typedef struct {
+    int k;                   /* polynomial order of the finest space, 0..4         */
+    double nu;               /* viscosity nu > 0                                   */
+    double beta;             /* lower-order coefficient beta >= 0                  */
+    double gamma;            /* augmented-Lagrangian weight: eps^{-1} = gamma*nu   */
+    int m_p;                 /* high-order relaxation steps (Algorithm 2), >= 1    */
+    int m_h;                 /* smoothing steps on the finest CR level, >= 1       */
+    int cycle;               /* q of Algorithm 1: 1 = variable V, 2 = W            */
+    int vcycle_growth;       /* m(l-1) = growth * m(l) for q = 1 (2 = doubling)    */
+    hdg_precision precision; /* precision of the preconditioner                    */
+} hdg_params;
+
+typedef struct {
+    double rtol;        /* inner relative tolerance (Section 5: 1e-8)               */
+    double atol;        /* inner absolute tolerance (Section 5: 1e-10)              */
+    double floor_rel;   /* inner solves stop at <= floor_rel*|F| at the latest      */
+    double uzawa_tol;   /* stop when the pressure error estimate <= uzawa_tol |p|   */
+    int restart;        /* FGMRES restart length, 1..32                             */
+    int max_it;         /* FGMRES iterations per inner solve                        */
+    int max_uzawa;      /* Uzawa steps, 1..64                                       */
+} hdg_solve_opts;
+
+typedef struct {
+    int uzawa_its;              /* Uzawa steps taken                                */
+    int krylov_its_total;       /* FGMRES iterations summed over the Uzawa steps   */
+    int krylov_its[64];         /* per Uzawa step                                   */
+    double res_mom;             /* final |g - A^eps u| of the last inner solve      */
+    double dp_rel;              /* last |p^n - p^{n-1}|_L2 / |p^n|_L2               */
+    double normF;               /* |F|_2                                            */
+} hdg_solve_info;
+
+typedef struct {
+    int k;
+    int n_levels;
+    int64_t n_cells;            /* finest level                                     */
+    int64_t n_interior_facets;  /* finest level                                     */
+    int64_t n_dof;              /* order-k skeleton unknowns, finest level          */
+    int64_t n_dof_level[16];    /* lowest-order unknowns per level (2 per facet)    */
+    int n_colours_level[16];    /* vertex colours per level                         */
+    int n_lat;                  /* forcing lattice points per cell                  */
+} hdg_sizes;
+
+/* Fill the defaults of Section 5: rtol 1e-8, atol 1e-10, floor_rel 1e-9,
+ * uzawa_tol 1e-8, restart 30, max_it 1000, max_uzawa 64. */
+void hdg_default_solve_opts(hdg_solve_opts *opts);
+
+/* Build the topology of every level: facets, orientations, interior-facet
+ * numbering, vertex patches and their colouring, parent/child maps and the
+ * coarse-facet/fine-facet relations needed by the averaging transfer of
+ * eq. avgOpt (Sections 2, 3.4.2).  Host arrays are copied; the caller may
+ * free them on return.  device: CUDA ordinal.  Returns HDG_ERR_INVALID_ARG
+ * for dim != 2, n_levels outside 1..16, inconsistent parents or a colouring
+ * that is not proper. */
+hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_ctx **out);
+
+/* Static condensation (Section 3.2, eq. stWeak; AL term eq. stALform) of the
+ * order-k operator on the finest level and of the lowest-order operator on
+ * every level, in FP64 on the device; then the patch inverses of the block
+ * smoothers (eq. bjac, Sections 3.4.2, 3.5), the harmonic-extension blocks of
+ * the transfer (eqs. div-transfer, harmonic-ex) and the dense inverse of the
+ * coarsest operator.  forcing: device [n_cells][n_lat][2] (layout above) or
+ * NULL; rhs_out: device [n_dof] condensed load F, or NULL.  May be called
+ * again with new parameters or forcing.  Returns HDG_ERR_SINGULAR if a
+ * factorisation meets a non-positive pivot. */
+hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *params, const double *forcing,
+                        double *rhs_out, hdg_stream_t stream);
+
+/* Condensed load only (forcing -> F, device in/out), reusing the condensed
+ * cells of the last hdg_condense.  Same layouts as hdg_condense. */
+hdg_status hdg_load(hdg_ctx *ctx, const double *forcing, double *rhs_out, hdg_stream_t stream);
+
+/* y = A^eps_{k,h} x (eqs. stOptForm, stALform): element-by-element Schur
+ * complements gathered and summed per facet.  x, y: device [n_dof] FP64,
+ * must not overlap. */
+hdg_status hdg_apply(hdg_ctx *ctx, const double *x, double *y, hdg_stream_t stream);
+
+/* z = MG_hp(r, 0, m_p, m_h, q) of Algorithm 2 (Algorithm 1 inside), in the
+ * precision chosen at hdg_condense.  r, z: device [n_dof] FP64, must not
+ * overlap. */
+hdg_status hdg_precond_apply(hdg_ctx *ctx, const double *r, double *z, hdg_stream_t stream);
+
+/* Augmented-Lagrangian Uzawa iteration (eq. stOpEq-ALU, with the convergent
+ * sign p <- p - eps^{-1} div u) with FGMRES inner solves right-preconditioned
+ * by MG_hp.  F: device [n_dof] condensed load; u: device [n_dof], in: initial
+ * guess, out: skeleton velocity; p: device [n_cells], in: initial pressure,
+ * out: cell pressures.  opts NULL = defaults.  info may be NULL.  Returns
+ * HDG_ERR_NOT_CONVERGED when max_uzawa or max_it is reached. */
+hdg_status hdg_solve(hdg_ctx *ctx, const double *F, double *u, double *p,
+                     const hdg_solve_opts *opts, hdg_solve_info *info, hdg_stream_t stream);
+
+/* Sizes after hdg_setup_mesh_hierarchy (k-dependent fields after hdg_condense). */
+hdg_status hdg_get_sizes(const hdg_ctx *ctx, hdg_sizes *out);
+
+/* Copy the condensed element matrices (with the AL term) to out (device):
+ * level = -1: order-k finest operator [n_cells][n_loc][n_loc];
+ * level = l >= 0: lowest-order operator of level l [n_cells_l][6][6]. */
+hdg_status hdg_get_element_matrices(hdg_ctx *ctx, int level, double *out, hdg_stream_t stream);
+
+/* Step-level entry points of the hot path (parity testing and composition).
+ * All vectors FP64 device; lowest-order vectors have 2 unknowns per interior
+ * facet of their level.  level = -1 selects the order-k operator on the
+ * finest mesh, level >= 0 the lowest-order operator of that level.        */
+
+/* y = A x on a level (level = -1: same as hdg_apply). */
+hdg_status hdg_level_apply(hdg_ctx *ctx, int level, const double *x, double *y, hdg_stream_t stream);
+
+/* n_sweeps block Gauss-Seidel sweeps on u for A u = g over the vertex
+ * patches, colours in increasing order (reverse = 0) or decreasing order
+ * (reverse = 1, the transpose R^T).  u updated in place. */
+hdg_status hdg_smooth(hdg_ctx *ctx, int level, const double *g, double *u, int n_sweeps,
+                      int reverse, hdg_stream_t stream);
+
+/* uf += I_{l-1}^l uc (harmonic-extension-corrected averaging, level l >= 1). */
+hdg_status hdg_prolong_add(hdg_ctx *ctx, int level, const double *uc, double *uf, hdg_stream_t stream);
+
+/* rc = (I_{l-1}^l)^T rf (level l >= 1). */
+hdg_status hdg_restrict(hdg_ctx *ctx, int level, const double *rf, double *rc, hdg_stream_t stream);
+
+/* u = (A^eps_{0,0})^{-1} g on the coarsest level. */
+hdg_status hdg_coarse_solve(hdg_ctx *ctx, const double *g, double *u, hdg_stream_t stream);
+
+/* u = MG_h(L, g, 0, m_h, q) of Algorithm 1 on the lowest-order operator of
+ * the finest level L. */
+hdg_status hdg_mg_h(hdg_ctx *ctx, const double *g, double *u, hdg_stream_t stream);
+
+/* Host-side reference-element integrals that hdg_condense contracts with each
+ * cell's Jacobian to form the local system of eq. stWeak (Section 3.2) for
+ * order k: the blocks R1..R6 packed in that order (layouts in the library
+ * source, csrc/reference.cpp).  Returns the number of doubles; writes them to
+ * out (host memory) when out is not NULL; returns -1 for k outside 0..4.
+ * Needs no GPU. */
+int64_t hdg_reference_tables(int k, double *out);
+
+/* Number of CUDA kernels this library has enqueued in the calling process
+ * (all contexts, all streams), for launch accounting in benchmarks. */
+uint64_t hdg_kernel_launches(void);
+
+void hdg_destroy(hdg_ctx *ctx);
+const char *hdg_status_string(hdg_status s);
+const char *hdg_last_error(const hdg_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HDG_H */

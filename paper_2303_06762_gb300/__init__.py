@@ -1,0 +1,375 @@
+"""GB300 hp-multigrid preconditioned FGMRES for the condensed H(div)-HDG scheme.
+
+Thin Python binding of the C ABI declared in ``include/hdg.h``: the functions
+below have the same names as the C entry points and only marshal arguments
+(torch tensors -> device pointers, the current CUDA stream, ctypes structs).
+Every step of the computation runs in the library's CUDA kernels.  There is
+no CPU fallback: if the shared library is missing or no GPU is present the
+calls raise.
+
+Typical use::
+
+    import paper_2303_06762_gb300 as hdg
+    ctx = hdg.hdg_setup_mesh_hierarchy(levels)          # list of meshes, coarsest first
+    F = hdg.hdg_condense(ctx, hdg.Params(k=3, gamma=1e2), forcing)   # forcing: cuda tensor
+    u, p, info = hdg.hdg_solve(ctx, F)
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional, Sequence
+
+import numpy as np
+
+from .build import LIB, build as _build
+
+HDG_FP64 = 0
+HDG_MIXED_FP32 = 1
+
+_STATUS = {0: "HDG_OK", 1: "HDG_ERR_INVALID_ARG", 2: "HDG_ERR_OOM", 3: "HDG_ERR_CUDA",
+           4: "HDG_ERR_SINGULAR", 5: "HDG_ERR_NOT_CONVERGED", 6: "HDG_ERR_BREAKDOWN",
+           7: "HDG_ERR_NONFINITE", 8: "HDG_ERR_UNSUPPORTED", 9: "HDG_ERR_STATE"}
+
+# every exported entry point of include/hdg.h
+EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense", "hdg_load",
+           "hdg_apply", "hdg_precond_apply", "hdg_solve", "hdg_get_sizes",
+           "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
+           "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
+           "hdg_reference_tables", "hdg_destroy",
+           "hdg_status_string", "hdg_last_error")
+
+
+class HdgError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _MeshDesc(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("n_levels", ctypes.c_int),
+                ("n_vertices", ctypes.POINTER(ctypes.c_int64)),
+                ("n_cells", ctypes.POINTER(ctypes.c_int64)),
+                ("coords", ctypes.POINTER(ctypes.POINTER(ctypes.c_double))),
+                ("cells", ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))),
+                ("parent", ctypes.POINTER(ctypes.POINTER(ctypes.c_int32))),
+                ("vertex_colour", ctypes.POINTER(ctypes.POINTER(ctypes.c_int32)))]
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("nu", ctypes.c_double), ("beta", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("m_p", ctypes.c_int), ("m_h", ctypes.c_int),
+                ("cycle", ctypes.c_int), ("vcycle_growth", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class SolveOpts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("floor_rel", ctypes.c_double),
+                ("uzawa_tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_it", ctypes.c_int),
+                ("max_uzawa", ctypes.c_int)]
+
+
+class SolveInfo(ctypes.Structure):
+    _fields_ = [("uzawa_its", ctypes.c_int), ("krylov_its_total", ctypes.c_int),
+                ("krylov_its", ctypes.c_int * 64), ("res_mom", ctypes.c_double),
+                ("dp_rel", ctypes.c_double), ("normF", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(uzawa_its=self.uzawa_its, krylov_its_total=self.krylov_its_total,
+                    krylov_its=list(self.krylov_its[:self.uzawa_its]), res_mom=self.res_mom,
+                    dp_rel=self.dp_rel, normF=self.normF)
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("n_levels", ctypes.c_int), ("n_cells", ctypes.c_int64),
+                ("n_interior_facets", ctypes.c_int64), ("n_dof", ctypes.c_int64),
+                ("n_dof_level", ctypes.c_int64 * 16), ("n_colours_level", ctypes.c_int * 16),
+                ("n_lat", ctypes.c_int)]
+
+
+@dataclass
+class Params:
+    """Solver parameters (hdg_params); defaults follow Section 5 (m_p = m_h = 1, V-cycle)."""
+    k: int = 2
+    nu: float = 1.0
+    beta: float = 0.0
+    gamma: float = 1e2
+    m_p: int = 1
+    m_h: int = 1
+    cycle: int = 1
+    vcycle_growth: int = 2
+    precision: int = HDG_FP64
+
+    def to_c(self) -> _Params:
+        return _Params(self.k, self.nu, self.beta, self.gamma, self.m_p, self.m_h, self.cycle,
+                       self.vcycle_growth, self.precision)
+
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None) -> ctypes.CDLL:
+    """Load (building first if needed) the shared library; raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB
+    if not os.path.exists(path):
+        _build()
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    I = ctypes.c_int
+    sigs = {
+        "hdg_default_solve_opts": (None, [ctypes.POINTER(SolveOpts)]),
+        "hdg_setup_mesh_hierarchy": (I, [ctypes.POINTER(_MeshDesc), I, ctypes.POINTER(P)]),
+        "hdg_condense": (I, [P, ctypes.POINTER(_Params), P, P, P]),
+        "hdg_load": (I, [P, P, P, P]),
+        "hdg_apply": (I, [P, P, P, P]),
+        "hdg_precond_apply": (I, [P, P, P, P]),
+        "hdg_solve": (I, [P, P, P, P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), P]),
+        "hdg_get_sizes": (I, [P, ctypes.POINTER(Sizes)]),
+        "hdg_get_element_matrices": (I, [P, I, P, P]),
+        "hdg_level_apply": (I, [P, I, P, P, P]),
+        "hdg_smooth": (I, [P, I, P, P, I, I, P]),
+        "hdg_prolong_add": (I, [P, I, P, P, P]),
+        "hdg_restrict": (I, [P, I, P, P, P]),
+        "hdg_coarse_solve": (I, [P, P, P, P]),
+        "hdg_mg_h": (I, [P, P, P, P]),
+        "hdg_kernel_launches": (ctypes.c_uint64, []),
+        "hdg_reference_tables": (ctypes.c_int64, [I, P]),
+        "hdg_destroy": (None, [P]),
+        "hdg_status_string": (ctypes.c_char_p, [I]),
+        "hdg_last_error": (ctypes.c_char_p, [P]),
+    }
+    for name, (res, args) in sigs.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    del D
+    _lib = lib
+    return lib
+
+
+# ------------------------------------------------------------------ helpers
+def _stream(stream=None):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _ptr(t):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """Owns an hdg_ctx handle; freed by close() or garbage collection."""
+
+    def __init__(self, handle: ctypes.c_void_p, device: int):
+        self.handle = handle
+        self.device = device
+
+    def check(self, st: int):
+        if st != 0:
+            msg = load_library().hdg_last_error(self.handle)
+            raise HdgError(st, msg.decode() if msg else "")
+
+    def sizes(self) -> Sizes:
+        s = Sizes()
+        self.check(load_library().hdg_get_sizes(self.handle, ctypes.byref(s)))
+        return s
+
+    def close(self):
+        if self.handle:
+            load_library().hdg_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------ C-ABI mirrors
+def hdg_setup_mesh_hierarchy(levels: Sequence, device: int = 0) -> Context:
+    """levels: objects with .coords (nv,2) float64, .cells (nc,3) int32, .parent (levels >= 1)
+    and optional .vertex_colour, coarsest first."""
+    lib = load_library()
+    n = len(levels)
+    keep = []
+    nv = (ctypes.c_int64 * n)(*[int(m.coords.shape[0]) for m in levels])
+    nc = (ctypes.c_int64 * n)(*[int(m.cells.shape[0]) for m in levels])
+    co = (ctypes.POINTER(ctypes.c_double) * n)()
+    ce = (ctypes.POINTER(ctypes.c_int32) * n)()
+    pa = (ctypes.POINTER(ctypes.c_int32) * n)()
+    vc = (ctypes.POINTER(ctypes.c_int32) * n)()
+    for l, m in enumerate(levels):
+        a = np.ascontiguousarray(m.coords, dtype=np.float64)
+        b = np.ascontiguousarray(m.cells, dtype=np.int32)
+        keep += [a, b]
+        co[l] = a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        ce[l] = b.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        if l > 0:
+            p = np.ascontiguousarray(m.parent, dtype=np.int32)
+            keep.append(p)
+            pa[l] = p.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        col = getattr(m, "vertex_colour", None)
+        if col is not None:
+            c = np.ascontiguousarray(col, dtype=np.int32)
+            keep.append(c)
+            vc[l] = c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+    desc = _MeshDesc(2, n, nv, nc, co, ce, pa, vc)
+    h = ctypes.c_void_p()
+    st = lib.hdg_setup_mesh_hierarchy(ctypes.byref(desc), device, ctypes.byref(h))
+    ctx = Context(h, device)
+    ctx.check(st)
+    ctx.level_cells = [int(m.cells.shape[0]) for m in levels]
+    return ctx
+
+
+def hdg_condense(ctx: Context, params: Params, forcing=None, stream=None):
+    """Condense; returns the condensed load F (cuda float64 tensor) when forcing is given."""
+    import torch
+    lib = load_library()
+    p = params.to_c()
+    F = None
+    if forcing is not None:
+        n = ctx.sizes().n_interior_facets * 2 * (params.k + 1)
+        F = torch.empty(n, dtype=torch.float64, device=forcing.device)
+        ctx.check(lib.hdg_condense(ctx.handle, ctypes.byref(p), _ptr(forcing), _ptr(F),
+                                   _stream(stream)))
+    else:
+        ctx.check(lib.hdg_condense(ctx.handle, ctypes.byref(p), None, None, _stream(stream)))
+    return F
+
+
+def hdg_apply(ctx: Context, x, y=None, stream=None):
+    import torch
+    y = torch.empty_like(x) if y is None else y
+    ctx.check(load_library().hdg_apply(ctx.handle, _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def hdg_precond_apply(ctx: Context, r, z=None, stream=None):
+    import torch
+    z = torch.empty_like(r) if z is None else z
+    ctx.check(load_library().hdg_precond_apply(ctx.handle, _ptr(r), _ptr(z), _stream(stream)))
+    return z
+
+
+def default_solve_opts() -> SolveOpts:
+    o = SolveOpts()
+    load_library().hdg_default_solve_opts(ctypes.byref(o))
+    return o
+
+
+def hdg_solve(ctx: Context, F, u=None, p=None, opts: Optional[SolveOpts] = None, stream=None,
+              raise_on_nonconvergence: bool = True):
+    """Uzawa + FGMRES; returns (u, p, info dict).  u, p are updated in place when given."""
+    import torch
+    s = ctx.sizes()
+    u = torch.zeros(s.n_dof, dtype=torch.float64, device=F.device) if u is None else u
+    p = torch.zeros(s.n_cells, dtype=torch.float64, device=F.device) if p is None else p
+    info = SolveInfo()
+    o = opts if opts is not None else default_solve_opts()
+    st = load_library().hdg_solve(ctx.handle, _ptr(F), _ptr(u), _ptr(p), ctypes.byref(o),
+                                  ctypes.byref(info), _stream(stream))
+    if st != 0 and (st != 5 or raise_on_nonconvergence):
+        ctx.check(st)
+    return u, p, info.as_dict()
+
+
+def hdg_get_element_matrices(ctx: Context, level: int = -1, stream=None):
+    import torch
+    s = ctx.sizes()
+    if level < 0:
+        nloc = 6 * (s.k + 1)
+        nc = s.n_cells
+    else:
+        nloc = 6
+        nc = _level_cells(ctx, level)
+    out = torch.empty((nc, nloc, nloc), dtype=torch.float64, device=f"cuda:{ctx.device}")
+    ctx.check(load_library().hdg_get_element_matrices(ctx.handle, level, _ptr(out), _stream(stream)))
+    return out
+
+
+def _level_cells(ctx: Context, level: int) -> int:
+    return ctx.level_cells[level]
+
+
+def hdg_level_apply(ctx: Context, level: int, x, y=None, stream=None):
+    import torch
+    y = torch.empty_like(x) if y is None else y
+    ctx.check(load_library().hdg_level_apply(ctx.handle, level, _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def hdg_smooth(ctx: Context, level: int, g, u, n_sweeps: int = 1, reverse: bool = False, stream=None):
+    ctx.check(load_library().hdg_smooth(ctx.handle, level, _ptr(g), _ptr(u), n_sweeps, int(reverse),
+                                        _stream(stream)))
+    return u
+
+
+def hdg_prolong_add(ctx: Context, level: int, uc, uf, stream=None):
+    ctx.check(load_library().hdg_prolong_add(ctx.handle, level, _ptr(uc), _ptr(uf), _stream(stream)))
+    return uf
+
+
+def hdg_restrict(ctx: Context, level: int, rf, rc=None, stream=None):
+    import torch
+    if rc is None:
+        rc = torch.empty(int(ctx.sizes().n_dof_level[level - 1]), dtype=torch.float64, device=rf.device)
+    ctx.check(load_library().hdg_restrict(ctx.handle, level, _ptr(rf), _ptr(rc), _stream(stream)))
+    return rc
+
+
+def hdg_coarse_solve(ctx: Context, g, u=None, stream=None):
+    import torch
+    u = torch.empty_like(g) if u is None else u
+    ctx.check(load_library().hdg_coarse_solve(ctx.handle, _ptr(g), _ptr(u), _stream(stream)))
+    return u
+
+
+def hdg_mg_h(ctx: Context, g, u=None, stream=None):
+    import torch
+    u = torch.empty_like(g) if u is None else u
+    ctx.check(load_library().hdg_mg_h(ctx.handle, _ptr(g), _ptr(u), _stream(stream)))
+    return u
+
+
+def hdg_reference_tables(k: int) -> dict:
+    """Reference-element integrals R1..R6 used by the device condensation (host call)."""
+    lib = load_library()
+    n = lib.hdg_reference_tables(k, None)
+    if n < 0:
+        raise HdgError(1, "k out of range")
+    buf = np.empty(n, dtype=np.float64)
+    lib.hdg_reference_tables(k, buf.ctypes.data_as(ctypes.c_void_p))
+    npk, nrt, nf, nlat = (k + 1) * (k + 2) // 2, (k + 1) * (k + 3), k + 1, (k + 2) * (k + 3) // 2
+    shapes = dict(R1=(nrt, 2, 2, npk), R2=(3, nrt, 2, npk), R3=(3, npk, nf), R4=(nrt, 2, nrt, 2),
+                  R5=(nrt, npk), R6=(nrt, 2, nlat))
+    out, o = {}, 0
+    for name, shp in shapes.items():
+        m = int(np.prod(shp))
+        out[name] = buf[o:o + m].reshape(shp)
+        o += m
+    assert o == n
+    return out
+
+
+def hdg_kernel_launches() -> int:
+    return int(load_library().hdg_kernel_launches())
+
+
+def hdg_destroy(ctx: Context):
+    ctx.close()

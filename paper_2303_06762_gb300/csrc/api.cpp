@@ -1,0 +1,782 @@
+// C ABI of the GB300 H(div)-HDG hp-multigrid library: context management,
+// setup (topology upload, condensation driver), and the host orchestration of
+// the hot path: Algorithm 1 (MG_h), Algorithm 2 (MG_hp), flexible GMRES and the
+// augmented-Lagrangian Uzawa iteration (eq. stOpEq-ALU).  Every numerical step
+// runs in the CUDA kernels of condense.cu / ops.cu; this file only sequences
+// launches on the caller's stream and reads back the few scalars that decide
+// convergence.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "hdg_internal.h"
+
+using namespace hdg;
+
+namespace {
+
+struct Fail {
+    hdg_status st;
+};
+
+#define CK(expr)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            ctx->err = std::string(#expr) + ": " + cudaGetErrorString(e_);                  \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? HDG_ERR_OOM : HDG_ERR_CUDA};        \
+        }                                                                                    \
+    } while (0)
+
+#define REQUIRE(cond, msg)                                                                   \
+    do {                                                                                     \
+        if (!(cond)) {                                                                       \
+            ctx->err = (msg);                                                                \
+            throw Fail{HDG_ERR_INVALID_ARG};                                                 \
+        }                                                                                    \
+    } while (0)
+
+template <class T>
+void dalloc(hdg_ctx *ctx, DBuf<T> &b, size_t n) {
+    if (b.p && b.n >= n) return;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+    if (n == 0) return;
+    CK(cudaMalloc((void **)&b.p, sizeof(T) * n));
+    b.n = n;
+}
+
+template <class T>
+void dfree(DBuf<T> &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.n = 0;
+}
+
+template <class T>
+void upload(hdg_ctx *ctx, DBuf<T> &b, const std::vector<T> &h) {
+    dalloc(ctx, b, h.size());
+    if (!h.empty()) CK(cudaMemcpy(b.p, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice));
+}
+
+void free_operator(DevOperator &op) {
+    dfree(op.A);
+    dfree(op.Af);
+    dfree(op.Fel);
+    dfree(op.Pinv);
+    dfree(op.Pinvf);
+}
+
+void free_level(DevLevel &L) {
+    dfree(L.coords); dfree(L.cells); dfree(L.cell_int); dfree(L.facet_adj); dfree(L.cell_d);
+    dfree(L.cell_area); dfree(L.patch_nf); dfree(L.patch_facets); dfree(L.patch_nc);
+    dfree(L.patch_cells); dfree(L.patch_slot_src);
+    free_operator(L.op0);
+    dfree(L.tr_slots); dfree(L.tr_nbr); dfree(L.tr_children); dfree(L.tr_child_slot);
+    dfree(L.tr_fineB); dfree(L.tr_fineB_src); dfree(L.tr_W); dfree(L.tr_H); dfree(L.tr_Wf);
+    dfree(L.tr_Hf);
+    dfree(L.g); dfree(L.u); dfree(L.r); dfree(L.t);
+    dfree(L.gf); dfree(L.uf); dfree(L.rf); dfree(L.tf);
+    dfree(L.ct1); dfree(L.ct2); dfree(L.ct1f); dfree(L.ct2f);
+}
+
+template <class Fn>
+hdg_status guard(hdg_ctx *ctx, Fn &&fn) {
+    try {
+        fn();
+        return HDG_OK;
+    } catch (const Fail &f) {
+        return f.st;
+    } catch (const std::exception &e) {
+        if (ctx) ctx->err = e.what();
+        return HDG_ERR_INVALID_ARG;
+    } catch (...) {
+        if (ctx) ctx->err = "unknown exception";
+        return HDG_ERR_CUDA;
+    }
+}
+
+void check_flag(hdg_ctx *ctx, cudaStream_t s) {
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, ctx->status_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (flag) {
+        ctx->err = "non-positive pivot in a factorisation (flag " + std::to_string(flag) + ")";
+        throw Fail{HDG_ERR_SINGULAR};
+    }
+}
+
+double read_scalar(hdg_ctx *ctx, const double *dev, cudaStream_t s) {
+    CK(cudaMemcpyAsync(ctx->h_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return ctx->h_pinned[0];
+}
+
+// ---------------------------------------------------------------- MG_h (Algorithm 1)
+template <class T>
+struct Prec;
+
+template <>
+struct Prec<double> {
+    static const double *A(const DevOperator &o) { return o.A.p; }
+    static const double *P(const DevOperator &o) { return o.Pinv.p; }
+    static double *g(DevLevel &L) { return L.g.p; }
+    static double *u(DevLevel &L) { return L.u.p; }
+    static double *r(DevLevel &L) { return L.r.p; }
+    static double *t(DevLevel &L) { return L.t.p; }
+    static double *c1(DevLevel &L) { return L.ct1.p; }
+    static double *c2(DevLevel &L) { return L.ct2.p; }
+    static const double *W(const DevLevel &L) { return L.tr_W.p; }
+    static const double *H(const DevLevel &L) { return L.tr_H.p; }
+};
+template <>
+struct Prec<float> {
+    static const float *A(const DevOperator &o) { return o.Af.p; }
+    static const float *P(const DevOperator &o) { return o.Pinvf.p; }
+    static float *g(DevLevel &L) { return L.gf.p; }
+    static float *u(DevLevel &L) { return L.uf.p; }
+    static float *r(DevLevel &L) { return L.rf.p; }
+    static float *t(DevLevel &L) { return L.tf.p; }
+    static float *c1(DevLevel &L) { return L.ct1f.p; }
+    static float *c2(DevLevel &L) { return L.ct2f.p; }
+    static const float *W(const DevLevel &L) { return L.tr_Wf.p; }
+    static const float *H(const DevLevel &L) { return L.tr_Hf.p; }
+};
+
+template <class T>
+void sweep(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, const T *g, T *u, bool reverse,
+           cudaStream_t s) {
+    for (int i = 0; i < L.n_colours; ++i) {
+        int c = reverse ? L.n_colours - 1 - i : i;
+        CK(launch_gs_colour<T>(L, op, Prec<T>::A(op), Prec<T>::P(op), c, g, u, s));
+    }
+}
+
+template <class T>
+void coarse_solve(hdg_ctx *ctx, cudaStream_t s) {
+    DevLevel &L0 = ctx->L[0];
+    int64_t n = 2 * L0.n_int;
+    if constexpr (std::is_same<T, double>::value) {
+        CK(launch_coarse_apply(ctx->coarse_inv.p, n, L0.g.p, L0.u.p, s));
+    } else {
+        CK(launch_f2d(L0.gf.p, L0.g.p, n, s));
+        CK(launch_coarse_apply(ctx->coarse_inv.p, n, L0.g.p, L0.u.p, s));
+        CK(launch_d2f(L0.u.p, L0.uf.p, n, s));
+    }
+}
+
+// u_l = MG_h(l, g_l, u_l (zero_init ? 0 : as is), m, q)
+template <class T>
+void mg_h(hdg_ctx *ctx, int l, int m, bool zero_init, cudaStream_t s) {
+    if (l == 0) {
+        coarse_solve<T>(ctx, s);
+        return;
+    }
+    DevLevel &L = ctx->L[l];
+    DevLevel &C = ctx->L[l - 1];
+    const int64_t n = 2 * L.n_int;
+    T *g = Prec<T>::g(L), *u = Prec<T>::u(L), *r = Prec<T>::r(L);
+    if (zero_init) CK(launch_fill<T>(u, T(0), n, s));
+    for (int j = 0; j < m; ++j) sweep<T>(ctx, L, L.op0, g, u, false, s);
+    CK(launch_apply<T>(L, L.op0, Prec<T>::A(L.op0), u, g, r, s));
+    CK(launch_restrict<T>(L, C, Prec<T>::W(L), Prec<T>::H(L), r, Prec<T>::c1(L), Prec<T>::c2(L),
+                          Prec<T>::g(C), s));
+    const int q = ctx->prm.cycle;
+    const int mc = (q == 1) ? m * ctx->prm.vcycle_growth : m;
+    for (int it = 0; it < q; ++it) mg_h<T>(ctx, l - 1, mc, it == 0, s);
+    CK(launch_prolong_add<T>(L, C, Prec<T>::W(L), Prec<T>::H(L), Prec<T>::u(C), Prec<T>::t(L), u, s));
+    for (int j = 0; j < m; ++j) sweep<T>(ctx, L, L.op0, g, u, true, s);
+}
+
+// z = MG_hp(r, 0) (Algorithm 2); r, z FP64 of size n_dof
+template <class T>
+void mg_hp_impl(hdg_ctx *ctx, const T *r, T *z, cudaStream_t s) {
+    const int J = ctx->n_levels - 1;
+    DevLevel &LJ = ctx->L[J];
+    const int k = ctx->prm.k;
+    if (k == 0) {
+        // Algorithm 2 with k = 0 is MG_h on the finest level
+        CK(cudaMemcpyAsync(Prec<T>::g(LJ), r, sizeof(T) * ctx->n_dof, cudaMemcpyDeviceToDevice, s));
+        mg_h<T>(ctx, J, ctx->prm.m_h, true, s);
+        CK(cudaMemcpyAsync(z, Prec<T>::u(LJ), sizeof(T) * ctx->n_dof, cudaMemcpyDeviceToDevice, s));
+        return;
+    }
+    const DevOperator &op = ctx->opk;
+    T *res = std::is_same<T, double>::value ? (T *)ctx->kr.p : (T *)ctx->krf.p;
+    CK(launch_fill<T>(z, T(0), ctx->n_dof, s));
+    for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, false, s);
+    CK(launch_apply<T>(LJ, op, Prec<T>::A(op), z, r, res, s));
+    CK(launch_hp_restrict<T>(k, LJ.n_int, res, Prec<T>::g(LJ), s));
+    mg_h<T>(ctx, J, ctx->prm.m_h, true, s);
+    CK(launch_hp_prolong_add<T>(k, LJ.n_int, Prec<T>::u(LJ), z, s));
+    for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, true, s);
+}
+
+void precond(hdg_ctx *ctx, const double *r, double *z, cudaStream_t s) {
+    if (ctx->prm.precision == HDG_FP64) {
+        mg_hp_impl<double>(ctx, r, z, s);
+    } else {
+        CK(launch_d2f(r, ctx->kgf.p, ctx->n_dof, s));
+        mg_hp_impl<float>(ctx, ctx->kgf.p, ctx->kuf.p, s);
+        CK(launch_f2d(ctx->kuf.p, z, ctx->n_dof, s));
+    }
+}
+
+void apply_k(hdg_ctx *ctx, const double *x, const double *g, double *y, cudaStream_t s) {
+    DevLevel &LJ = ctx->L[ctx->n_levels - 1];
+    CK(launch_apply<double>(LJ, ctx->opk, ctx->opk.A.p, x, g, y, s));
+}
+
+double norm2(hdg_ctx *ctx, const double *x, int64_t n, cudaStream_t s) {
+    SmallLayout Ly{ctx->restart_alloc};
+    CK(launch_dots(x, 1, 0, x, n, ctx->partials.p, s));
+    CK(launch_reduce_partials(ctx->partials.p, 1, ctx->small.p + Ly.nrm2(), 0, s));
+    return std::sqrt(std::max(read_scalar(ctx, ctx->small.p + Ly.nrm2(), s), 0.0));
+}
+
+void ensure_krylov(hdg_ctx *ctx, int R) {
+    const int64_t n = ctx->n_dof;
+    if (ctx->restart_alloc != R || ctx->V.n < (size_t)(R + 1) * n) {
+        dfree(ctx->V);
+        dfree(ctx->Z);
+        dfree(ctx->small);
+        dalloc(ctx, ctx->V, (size_t)(R + 1) * n);
+        dalloc(ctx, ctx->Z, (size_t)R * n);
+        SmallLayout Ly{R};
+        dalloc(ctx, ctx->small, (size_t)Ly.total());
+        ctx->restart_alloc = R;
+    }
+    dalloc(ctx, ctx->w, n);
+    dalloc(ctx, ctx->partials, (size_t)(MAX_RESTART + 2) * krylov_partial_blocks());
+}
+
+struct FgmresOut {
+    int its;
+    double res;
+};
+
+// flexible GMRES on A^eps x = b: stop at |r| <= max(rtol |r0|, atol)
+FgmresOut fgmres(hdg_ctx *ctx, const double *b, double *x, double rtol, double atol, int R,
+                 int max_it, cudaStream_t s) {
+    const int64_t n = ctx->n_dof;
+    SmallLayout Ly{R};
+    double *V = ctx->V.p, *Z = ctx->Z.p, *w = ctx->w.p, *sm = ctx->small.p, *pt = ctx->partials.p;
+    int total = 0;
+    double tol = -1.0, beta = 0.0;
+    while (true) {
+        apply_k(ctx, x, b, V, s);   // V0 = b - A x
+        CK(launch_dots(V, 1, 0, V, n, pt, s));
+        CK(launch_reduce_partials(pt, 1, sm + Ly.nrm2(), 0, s));
+        beta = std::sqrt(std::max(read_scalar(ctx, sm + Ly.nrm2(), s), 0.0));
+        if (!std::isfinite(beta)) {
+            ctx->err = "non-finite residual";
+            throw Fail{HDG_ERR_NONFINITE};
+        }
+        if (tol < 0) tol = std::max(rtol * beta, atol);
+        if (beta <= tol || total >= max_it) break;
+        CK(launch_init_cycle(V, V, n, sm, R, s));
+        int m = 0;
+        for (int j = 0; j < R; ++j) {
+            double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
+            precond(ctx, vj, zj, s);
+            apply_k(ctx, zj, nullptr, w, s);
+            CK(launch_dots(V, j + 1, n, w, n, pt, s));
+            CK(launch_reduce_partials(pt, j + 1, sm + Ly.h1(), 0, s));
+            CK(launch_update_dots(V, j + 1, n, w, n, sm + Ly.h1(), pt, 1, s));
+            CK(launch_reduce_partials(pt, j + 1, sm + Ly.h2(), 0, s));
+            CK(launch_update_dots(V, j + 1, n, w, n, sm + Ly.h2(), pt, 2, s));
+            CK(launch_reduce_partials(pt, 1, sm + Ly.nrm2(), 0, s));
+            CK(launch_givens(sm, j, R, nullptr, s));
+            CK(launch_scale_next(w, V + (size_t)(j + 1) * n, n, sm, j, R, s));
+            CK(cudaMemcpyAsync(ctx->h_pinned, sm + Ly.res(), 2 * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            double res = ctx->h_pinned[0], hn = ctx->h_pinned[1];
+            ++total;
+            m = j + 1;
+            if (!std::isfinite(res)) {
+                ctx->err = "non-finite residual estimate";
+                throw Fail{HDG_ERR_NONFINITE};
+            }
+            if (res <= tol || total >= max_it || hn == 0.0) break;
+        }
+        CK(launch_solve_update(sm, m, R, Z, n, x, n, s));
+    }
+    return {total, beta};
+}
+
+} // namespace
+
+// =====================================================================================
+extern "C" {
+
+void hdg_default_solve_opts(hdg_solve_opts *o) {
+    if (!o) return;
+    o->rtol = 1e-8;
+    o->atol = 1e-10;
+    o->floor_rel = 1e-9;
+    o->uzawa_tol = 1e-8;
+    o->restart = 30;
+    o->max_it = 1000;
+    o->max_uzawa = 64;
+}
+
+const char *hdg_status_string(hdg_status s) {
+    switch (s) {
+    case HDG_OK: return "ok";
+    case HDG_ERR_INVALID_ARG: return "invalid argument";
+    case HDG_ERR_OOM: return "out of memory";
+    case HDG_ERR_CUDA: return "CUDA error";
+    case HDG_ERR_SINGULAR: return "singular factorisation";
+    case HDG_ERR_NOT_CONVERGED: return "not converged";
+    case HDG_ERR_BREAKDOWN: return "Krylov breakdown";
+    case HDG_ERR_NONFINITE: return "non-finite value";
+    case HDG_ERR_UNSUPPORTED: return "unsupported";
+    case HDG_ERR_STATE: return "call order violated";
+    }
+    return "unknown status";
+}
+
+const char *hdg_last_error(const hdg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+uint64_t hdg_kernel_launches(void) { return (uint64_t)launch_count(); }
+
+int64_t hdg_reference_tables(int k, double *out) {
+    if (k < 0 || k > MAX_K) return -1;
+    try {
+        RefTables t;
+        build_reference_tables(k, t);
+        int64_t n = 0;
+        for (auto *v : {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6}) {
+            if (out) std::memcpy(out + n, v->data(), sizeof(double) * v->size());
+            n += (int64_t)v->size();
+        }
+        return n;
+    } catch (...) {
+        return -1;
+    }
+}
+
+hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_ctx **out) {
+    if (!out) return HDG_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!desc) return HDG_ERR_INVALID_ARG;
+    hdg_ctx *ctx = new hdg_ctx();
+    hdg_status st = guard(ctx, [&] {
+        REQUIRE(desc->dim == 2, "only dim = 2 is supported");
+        REQUIRE(desc->n_levels >= 1 && desc->n_levels <= MAX_LEVELS, "n_levels out of range 1..16");
+        REQUIRE(desc->n_vertices && desc->n_cells && desc->coords && desc->cells, "null mesh arrays");
+        int ndev = 0;
+        CK(cudaGetDeviceCount(&ndev));
+        REQUIRE(device >= 0 && device < ndev, "device ordinal out of range");
+        ctx->device = device;
+        CK(cudaSetDevice(device));
+        const int nl = desc->n_levels;
+        ctx->n_levels = nl;
+        ctx->H.resize(nl);
+        ctx->T.resize(nl);
+        ctx->L.resize(nl);
+        for (int l = 0; l < nl; ++l) {
+            HostLevel &H = ctx->H[l];
+            H.nv = desc->n_vertices[l];
+            H.nc = desc->n_cells[l];
+            REQUIRE(H.nv >= 3 && H.nc >= 1 && H.nc < (1LL << 26), "level sizes out of range");
+            REQUIRE(desc->coords[l] && desc->cells[l], "null level array");
+            H.coords.assign(desc->coords[l], desc->coords[l] + 2 * H.nv);
+            H.cells.assign(desc->cells[l], desc->cells[l] + 3 * H.nc);
+            const int32_t *col = (desc->vertex_colour && desc->vertex_colour[l]) ? desc->vertex_colour[l] : nullptr;
+            std::string e = build_level_topology(H, col);
+            REQUIRE(e.empty(), "level " + std::to_string(l) + ": " + e);
+            if (l > 0) {
+                REQUIRE(desc->parent && desc->parent[l], "parent map required on levels >= 1");
+                H.parent.assign(desc->parent[l], desc->parent[l] + H.nc);
+                std::string e2 = build_transfer(ctx->H[l - 1], H, ctx->T[l]);
+                REQUIRE(e2.empty(), "level " + std::to_string(l) + ": " + e2);
+            }
+        }
+        // upload
+        for (int l = 0; l < nl; ++l) {
+            HostLevel &H = ctx->H[l];
+            DevLevel &L = ctx->L[l];
+            L.nv = H.nv;
+            L.nc = H.nc;
+            L.n_int = H.n_int;
+            upload(ctx, L.coords, H.coords);
+            upload(ctx, L.cells, H.cells);
+            std::vector<int32_t> ci(3 * H.nc), fa(2 * H.n_int);
+            for (int64_t c = 0; c < H.nc; ++c)
+                for (int f = 0; f < 3; ++f) ci[3 * c + f] = H.interior_index[H.cell_facet[3 * c + f]];
+            for (int64_t i = 0; i < H.n_int; ++i) {
+                int F = H.interior_facets[i];
+                for (int q = 0; q < 2; ++q) fa[2 * i + q] = (H.facet_cells[2 * F + q] << 2) | H.facet_lf[2 * F + q];
+            }
+            upload(ctx, L.cell_int, ci);
+            upload(ctx, L.facet_adj, fa);
+            dalloc(ctx, L.cell_d, 3 * H.nc);
+            dalloc(ctx, L.cell_area, H.nc);
+            CK(launch_cell_geometry(L, 0));
+            L.n_patches = H.n_patches;
+            L.n_colours = H.n_colours;
+            L.pf_max = H.pf_max;
+            L.pc_max = H.pc_max;
+            L.colour_ptr = H.colour_ptr;
+            upload(ctx, L.patch_nf, H.patch_nf);
+            upload(ctx, L.patch_facets, H.patch_facets);
+            upload(ctx, L.patch_nc, H.patch_nc);
+            upload(ctx, L.patch_cells, H.patch_cells);
+            upload(ctx, L.patch_slot_src, H.patch_slot_src);
+            if (l > 0) {
+                HostTransfer &T = ctx->T[l];
+                L.nc_coarse = T.nc_coarse;
+                L.nB = T.nB;
+                upload(ctx, L.tr_slots, T.slots);
+                upload(ctx, L.tr_nbr, T.nbr);
+                upload(ctx, L.tr_children, T.children);
+                upload(ctx, L.tr_child_slot, T.child_slot);
+                upload(ctx, L.tr_fineB, T.fineB);
+                upload(ctx, L.tr_fineB_src, T.fineB_src);
+                upload(ctx, L.tr_W, T.W);
+                std::vector<float> Wf(T.W.begin(), T.W.end());
+                upload(ctx, L.tr_Wf, Wf);
+                dalloc(ctx, L.tr_H, 72 * T.nc_coarse);
+                dalloc(ctx, L.tr_Hf, 72 * T.nc_coarse);
+                dalloc(ctx, L.ct1, 12 * T.nc_coarse);
+                dalloc(ctx, L.ct2, 6 * T.nc_coarse);
+                dalloc(ctx, L.ct1f, 12 * T.nc_coarse);
+                dalloc(ctx, L.ct2f, 6 * T.nc_coarse);
+            }
+            const int64_t n0 = std::max<int64_t>(2 * H.n_int, 1);
+            dalloc(ctx, L.g, n0); dalloc(ctx, L.u, n0); dalloc(ctx, L.r, n0); dalloc(ctx, L.t, n0);
+            dalloc(ctx, L.gf, n0); dalloc(ctx, L.uf, n0); dalloc(ctx, L.rf, n0); dalloc(ctx, L.tf, n0);
+        }
+        dalloc(ctx, ctx->status_flag, 1);
+        CK(cudaMallocHost((void **)&ctx->h_pinned, 8 * sizeof(double)));
+        CK(cudaDeviceSynchronize());
+    });
+    if (st != HDG_OK) {
+        // keep the message reachable through a minimal context
+        *out = ctx;
+        return st;
+    }
+    *out = ctx;
+    return HDG_OK;
+}
+
+void hdg_destroy(hdg_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    for (auto &L : ctx->L) free_level(L);
+    free_operator(ctx->opk);
+    dfree(ctx->refk_dev); dfree(ctx->ref0_dev);
+    dfree(ctx->kr); dfree(ctx->ku); dfree(ctx->kt); dfree(ctx->krf); dfree(ctx->kuf); dfree(ctx->kgf);
+    dfree(ctx->coarse_inv); dfree(ctx->status_flag);
+    dfree(ctx->V); dfree(ctx->Z); dfree(ctx->w); dfree(ctx->partials); dfree(ctx->small);
+    dfree(ctx->uz_partials);
+    if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    delete ctx;
+}
+
+hdg_status hdg_get_sizes(const hdg_ctx *cctx, hdg_sizes *out) {
+    if (!cctx || !out) return HDG_ERR_INVALID_ARG;
+    std::memset(out, 0, sizeof(*out));
+    const hdg_ctx *ctx = cctx;
+    if (ctx->n_levels < 1) return HDG_ERR_STATE;
+    const HostLevel &H = ctx->H[ctx->n_levels - 1];
+    out->k = ctx->condensed ? ctx->prm.k : -1;
+    out->n_levels = ctx->n_levels;
+    out->n_cells = H.nc;
+    out->n_interior_facets = H.n_int;
+    out->n_dof = ctx->condensed ? ctx->n_dof : 0;
+    for (int l = 0; l < ctx->n_levels; ++l) {
+        out->n_dof_level[l] = 2 * ctx->H[l].n_int;
+        out->n_colours_level[l] = ctx->H[l].n_colours;
+    }
+    out->n_lat = ctx->condensed ? (ctx->prm.k + 2) * (ctx->prm.k + 3) / 2 : 0;
+    return HDG_OK;
+}
+
+static void upload_ref(hdg_ctx *ctx, RefTables &t, DBuf<double> &d, int k) {
+    if (t.k == k && d.p) return;
+    build_reference_tables(k, t);
+    std::vector<double> packed;
+    for (auto *v : {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6}) packed.insert(packed.end(), v->begin(), v->end());
+    dfree(d);
+    upload(ctx, d, packed);
+}
+
+hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forcing, double *rhs_out,
+                        hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        REQUIRE(prm, "null params");
+        REQUIRE(prm->k >= 0 && prm->k <= MAX_K, "k out of range 0..4");
+        REQUIRE(prm->nu > 0 && std::isfinite(prm->nu), "nu must be positive");
+        REQUIRE(prm->beta >= 0 && std::isfinite(prm->beta), "beta must be >= 0");
+        REQUIRE(prm->gamma >= 0 && std::isfinite(prm->gamma), "gamma must be >= 0");
+        REQUIRE(prm->m_p >= 1 && prm->m_h >= 1, "m_p, m_h must be >= 1");
+        REQUIRE(prm->cycle == 1 || prm->cycle == 2, "cycle must be 1 (V) or 2 (W)");
+        REQUIRE(prm->vcycle_growth >= 1 && prm->vcycle_growth <= 4, "vcycle_growth out of range 1..4");
+        REQUIRE(prm->precision == HDG_FP64 || prm->precision == HDG_MIXED_FP32, "unknown precision");
+        CK(cudaSetDevice(ctx->device));
+        cudaStream_t s = (cudaStream_t)stream;
+        ctx->condensed = false;
+        ctx->prm = *prm;
+        const int k = prm->k;
+        const double eps_inv = prm->gamma * prm->nu;
+        upload_ref(ctx, ctx->ref0, ctx->ref0_dev, 0);
+        upload_ref(ctx, ctx->refk, ctx->refk_dev, k);
+        CK(cudaMemsetAsync(ctx->status_flag.p, 0, sizeof(int), s));
+        const int nl = ctx->n_levels;
+        for (int l = 0; l < nl; ++l) {
+            DevLevel &L = ctx->L[l];
+            DevOperator &op = L.op0;
+            op.k = 0; op.dpf = 2; op.nloc = 6; op.np_max = L.pf_max * 2;
+            dalloc(ctx, op.A, 36 * L.nc);
+            dalloc(ctx, op.Af, 36 * L.nc);
+            dalloc(ctx, op.Pinv, (size_t)L.n_patches * op.np_max * op.np_max);
+            dalloc(ctx, op.Pinvf, (size_t)L.n_patches * op.np_max * op.np_max);
+            CK(launch_condense(0, L, ctx->ref0_dev.p, ctx->ref0, prm->nu, prm->beta, eps_inv, nullptr,
+                               op.A.p, op.Af.p, nullptr, ctx->status_flag.p, s));
+            CK(launch_patch_inverse(L, op, ctx->status_flag.p, s));
+        }
+        DevLevel &LJ = ctx->L[nl - 1];
+        DevOperator &op = ctx->opk;
+        op.k = k; op.dpf = 2 * (k + 1); op.nloc = 3 * op.dpf; op.np_max = LJ.pf_max * op.dpf;
+        dalloc(ctx, op.A, (size_t)op.nloc * op.nloc * LJ.nc);
+        dalloc(ctx, op.Af, (size_t)op.nloc * op.nloc * LJ.nc);
+        dalloc(ctx, op.Fel, (size_t)op.nloc * LJ.nc);
+        dalloc(ctx, op.Pinv, (size_t)LJ.n_patches * op.np_max * op.np_max);
+        dalloc(ctx, op.Pinvf, (size_t)LJ.n_patches * op.np_max * op.np_max);
+        CK(launch_condense(k, LJ, ctx->refk_dev.p, ctx->refk, prm->nu, prm->beta, eps_inv, forcing,
+                           op.A.p, op.Af.p, op.Fel.p, ctx->status_flag.p, s));
+        CK(launch_patch_inverse(LJ, op, ctx->status_flag.p, s));
+        for (int l = 1; l < nl; ++l) CK(launch_transfer_H(ctx->L[l], ctx->status_flag.p, s));
+        ctx->n0 = 2 * ctx->L[0].n_int;
+        dalloc(ctx, ctx->coarse_inv, std::max<int64_t>(ctx->n0 * ctx->n0, 1));
+        CK(launch_coarse_inverse(ctx->L[0], ctx->coarse_inv.p, ctx->n0, ctx->status_flag.p, s));
+        ctx->n_dof = LJ.n_int * op.dpf;
+        const int64_t nd = std::max<int64_t>(ctx->n_dof, 1);
+        dalloc(ctx, ctx->kr, nd); dalloc(ctx, ctx->ku, nd); dalloc(ctx, ctx->kt, nd);
+        dalloc(ctx, ctx->krf, nd); dalloc(ctx, ctx->kuf, nd); dalloc(ctx, ctx->kgf, nd);
+        if (rhs_out) {
+            if (forcing) CK(launch_assemble_load(LJ, op, rhs_out, s));
+            else CK(cudaMemsetAsync(rhs_out, 0, sizeof(double) * ctx->n_dof, s));
+        }
+        check_flag(ctx, s);
+        ctx->condensed = true;
+    });
+}
+
+hdg_status hdg_load(hdg_ctx *ctx, const double *forcing, double *rhs_out, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        if (!ctx->condensed) { ctx->err = "hdg_load before hdg_condense"; throw Fail{HDG_ERR_STATE}; }
+        REQUIRE(forcing && rhs_out, "null forcing or rhs_out");
+        cudaStream_t s = (cudaStream_t)stream;
+        DevLevel &LJ = ctx->L[ctx->n_levels - 1];
+        const double eps_inv = ctx->prm.gamma * ctx->prm.nu;
+        CK(launch_condense(ctx->prm.k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, ctx->prm.beta, eps_inv,
+                           forcing, ctx->opk.A.p, ctx->opk.Af.p, ctx->opk.Fel.p, ctx->status_flag.p, s));
+        CK(launch_assemble_load(LJ, ctx->opk, rhs_out, s));
+    });
+}
+
+#define NEED_CONDENSED()                                                                     \
+    do {                                                                                     \
+        if (!ctx->condensed) {                                                               \
+            ctx->err = "operator used before hdg_condense";                                  \
+            throw Fail{HDG_ERR_STATE};                                                       \
+        }                                                                                    \
+    } while (0)
+
+hdg_status hdg_apply(hdg_ctx *ctx, const double *x, double *y, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(x && y && x != y, "x, y must be distinct non-null device pointers");
+        apply_k(ctx, x, nullptr, y, (cudaStream_t)stream);
+    });
+}
+
+hdg_status hdg_precond_apply(hdg_ctx *ctx, const double *r, double *z, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(r && z && r != z, "r, z must be distinct non-null device pointers");
+        precond(ctx, r, z, (cudaStream_t)stream);
+    });
+}
+
+hdg_status hdg_level_apply(hdg_ctx *ctx, int level, const double *x, double *y, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(level >= -1 && level < ctx->n_levels, "level out of range");
+        REQUIRE(x && y && x != y, "x, y must be distinct non-null device pointers");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (level < 0) apply_k(ctx, x, nullptr, y, s);
+        else CK(launch_apply<double>(ctx->L[level], ctx->L[level].op0, ctx->L[level].op0.A.p, x, nullptr, y, s));
+    });
+}
+
+hdg_status hdg_smooth(hdg_ctx *ctx, int level, const double *g, double *u, int n_sweeps, int reverse,
+                      hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(level >= -1 && level < ctx->n_levels, "level out of range");
+        REQUIRE(g && u && n_sweeps >= 0, "bad arguments");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int J = ctx->n_levels - 1;
+        DevLevel &L = ctx->L[level < 0 ? J : level];
+        const DevOperator &op = level < 0 ? ctx->opk : L.op0;
+        const int64_t n = L.n_int * op.dpf;
+        if (ctx->prm.precision == HDG_FP64) {
+            for (int i = 0; i < n_sweeps; ++i) sweep<double>(ctx, L, op, g, u, reverse != 0, s);
+        } else {
+            float *gf = level < 0 ? ctx->kgf.p : L.gf.p, *uf = level < 0 ? ctx->kuf.p : L.uf.p;
+            CK(launch_d2f(g, gf, n, s));
+            CK(launch_d2f(u, uf, n, s));
+            for (int i = 0; i < n_sweeps; ++i) sweep<float>(ctx, L, op, gf, uf, reverse != 0, s);
+            CK(launch_f2d(uf, u, n, s));
+        }
+    });
+}
+
+hdg_status hdg_prolong_add(hdg_ctx *ctx, int level, const double *uc, double *uf, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(level >= 1 && level < ctx->n_levels, "level out of range 1..n_levels-1");
+        REQUIRE(uc && uf, "null vector");
+        DevLevel &F = ctx->L[level];
+        CK(launch_prolong_add<double>(F, ctx->L[level - 1], F.tr_W.p, F.tr_H.p, uc, F.t.p, uf,
+                                      (cudaStream_t)stream));
+    });
+}
+
+hdg_status hdg_restrict(hdg_ctx *ctx, int level, const double *rf, double *rc, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(level >= 1 && level < ctx->n_levels, "level out of range 1..n_levels-1");
+        REQUIRE(rf && rc, "null vector");
+        DevLevel &F = ctx->L[level];
+        CK(launch_restrict<double>(F, ctx->L[level - 1], F.tr_W.p, F.tr_H.p, rf, F.ct1.p, F.ct2.p, rc,
+                                   (cudaStream_t)stream));
+    });
+}
+
+hdg_status hdg_coarse_solve(hdg_ctx *ctx, const double *g, double *u, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(g && u && g != u, "g, u must be distinct non-null device pointers");
+        CK(launch_coarse_apply(ctx->coarse_inv.p, ctx->n0, g, u, (cudaStream_t)stream));
+    });
+}
+
+hdg_status hdg_mg_h(hdg_ctx *ctx, const double *g, double *u, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(g && u, "null vector");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int J = ctx->n_levels - 1;
+        DevLevel &L = ctx->L[J];
+        const int64_t n = 2 * L.n_int;
+        if (ctx->prm.precision == HDG_FP64) {
+            CK(cudaMemcpyAsync(L.g.p, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+            mg_h<double>(ctx, J, ctx->prm.m_h, true, s);
+            CK(cudaMemcpyAsync(u, L.u.p, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        } else {
+            CK(launch_d2f(g, L.gf.p, n, s));
+            mg_h<float>(ctx, J, ctx->prm.m_h, true, s);
+            CK(launch_f2d(L.uf.p, u, n, s));
+        }
+    });
+}
+
+hdg_status hdg_get_element_matrices(hdg_ctx *ctx, int level, double *out, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(level >= -1 && level < ctx->n_levels, "level out of range");
+        REQUIRE(out, "null output");
+        const DevOperator &op = level < 0 ? ctx->opk : ctx->L[level].op0;
+        const int64_t nc = ctx->L[level < 0 ? ctx->n_levels - 1 : level].nc;
+        CK(cudaMemcpyAsync(out, op.A.p, sizeof(double) * op.nloc * op.nloc * nc, cudaMemcpyDeviceToDevice,
+                           (cudaStream_t)stream));
+    });
+}
+
+hdg_status hdg_solve(hdg_ctx *ctx, const double *F, double *u, double *p, const hdg_solve_opts *opts_in,
+                     hdg_solve_info *info, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    hdg_solve_info loc{};
+    hdg_status conv = HDG_OK;
+    hdg_status st = guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(F && u && p, "null vector");
+        hdg_solve_opts o;
+        hdg_default_solve_opts(&o);
+        if (opts_in) o = *opts_in;
+        REQUIRE(o.restart >= 1 && o.restart <= 32, "restart out of range 1..32");
+        REQUIRE(o.max_uzawa >= 1 && o.max_uzawa <= 64, "max_uzawa out of range 1..64");
+        REQUIRE(o.max_it >= 1 && o.rtol >= 0 && o.atol >= 0 && o.floor_rel >= 0 && o.uzawa_tol >= 0,
+                "bad tolerances");
+        cudaStream_t s = (cudaStream_t)stream;
+        ensure_krylov(ctx, o.restart);
+        const int J = ctx->n_levels - 1;
+        DevLevel &LJ = ctx->L[J];
+        const int k = ctx->prm.k;
+        const double eps_inv = ctx->prm.gamma * ctx->prm.nu;
+        const double normF = norm2(ctx, F, ctx->n_dof, s);
+        loc.normF = normF;
+        const double floor_abs = std::max(o.floor_rel * normF, o.atol);
+        double *g = ctx->kt.p;
+        double ndp_prev = -1.0;
+        bool done = false;
+        for (int it = 0; it < o.max_uzawa; ++it) {
+            CK(launch_uzawa_rhs(LJ, k, F, p, g, s));
+            FgmresOut fo = fgmres(ctx, g, u, o.rtol, floor_abs, o.restart, o.max_it, s);
+            loc.krylov_its[it] = fo.its;
+            loc.krylov_its_total += fo.its;
+            loc.uzawa_its = it + 1;
+            loc.res_mom = fo.res;
+            if (fo.its >= o.max_it) conv = HDG_ERR_NOT_CONVERGED;
+            CK(launch_uzawa_update(LJ, k, u, p, eps_inv, ctx->partials.p, s));
+            SmallLayout Ly{o.restart};
+            CK(launch_reduce_partials(ctx->partials.p, 3, ctx->small.p + Ly.h1(), 0, s));
+            CK(cudaMemcpyAsync(ctx->h_pinned, ctx->small.p + Ly.h1(), 3 * sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            const double ndp = std::sqrt(std::max(ctx->h_pinned[0], 0.0));
+            const double npn = std::sqrt(std::max(ctx->h_pinned[1], 0.0));
+            loc.dp_rel = npn > 0 ? ndp / npn : 0.0;
+            if (!std::isfinite(ndp) || !std::isfinite(npn)) {
+                ctx->err = "non-finite pressure update";
+                throw Fail{HDG_ERR_NONFINITE};
+            }
+            if (ndp <= o.atol || (it > 0 && fo.its == 0)) { done = true; break; }
+            if (ndp_prev >= 0) {
+                double rho = std::min(ndp / ndp_prev, 0.99);
+                if (rho / (1.0 - rho) * ndp <= o.uzawa_tol * npn) { done = true; break; }
+            }
+            ndp_prev = ndp;
+        }
+        if (!done && conv == HDG_OK) conv = HDG_ERR_NOT_CONVERGED;
+    });
+    if (info) *info = loc;
+    if (st != HDG_OK) return st;
+    if (conv != HDG_OK) ctx->err = "iteration limit reached";
+    return conv;
+}
+
+} // extern "C"

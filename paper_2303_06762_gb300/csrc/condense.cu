@@ -1,0 +1,641 @@
+// Device-side setup in FP64: static condensation, patch inverses, harmonic
+// extension blocks, coarsest dense inverse, element geometry and loads.
+//
+// Static condensation (Section 3.2): on every cell the local system of
+// eq. stWeak is formed from reference tables (reference.cpp) and the
+// element Jacobian J: with the Piola map phi = J phi^/det J the tensor
+// C(G; u, û) = (∇u, G) − <tng u, G n> + <tng û, G n> is a contraction of the
+// reference integrals R1, R2, R3; the mass, divergence and load blocks are
+// contractions of R4, R5, R6.  The flux L is eliminated in closed form
+// (orthonormal P^k basis: mass ν⁻¹|det J| I), leaving
+//     K = (ν/|det J|) CᵀC + β M_u     on (u, û).
+// The interior RT unknowns u_i and the mean-free pressure p_o are then
+// eliminated by block Cholesky:
+//     Y = K_ii⁻¹[K_ig | D_oiᵀ | F_i],  S_p = D_oi Y_D,  W = D_oi Y_g − D_og,
+//     A_K = K_gg − K_gi Y_g + Wᵀ S_p⁻¹ W,
+//     F_K = F_g − K_gi Y_F + Wᵀ S_p⁻¹ D_oi Y_F,
+// and the augmented-Lagrangian term ε⁻¹|K|⁻¹ d dᵀ (eq. stALform; d = the
+// cell's flux functional) is added.  Facet unknowns are expressed in the
+// global facet basis of include/hdg.h: the reference facet moments map to
+// the global ones by the factor sqrt|F|·σ·sgn(det J)·o^m (σ = n_F·n_K,
+// o = ±1 the orientation of the facet parameter).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+
+#include "hdg_internal.h"
+
+namespace hdg {
+namespace {
+
+__constant__ int c_FV[3][2] = {{1, 2}, {0, 2}, {0, 1}};
+
+template <int K>
+struct Dims {
+    static constexpr int NPK = (K + 1) * (K + 2) / 2;
+    static constexpr int NRT = (K + 1) * (K + 3);
+    static constexpr int NF = K + 1;
+    static constexpr int NL = 4 * NPK;
+    static constexpr int NCOL = NRT + 3 * NF;
+    static constexpr int NG = 6 * NF;
+    static constexpr int NRI = K * (K + 1);
+    static constexpr int NPO = NPK - 1;
+    static constexpr int NLAT = (K + 2) * (K + 3) / 2;
+    static constexpr int NY = NG + NPO + 1;
+    // shared memory layout (doubles)
+    static constexpr int O_GEO = 0;                    // 64 doubles of geometry
+    static constexpr int O_S = 64;                     // NRT facet scaling
+    static constexpr int O_C = O_S + NRT;
+    static constexpr int O_K = O_C + NL * NCOL;
+    static constexpr int O_D = O_K + NCOL * NCOL;
+    static constexpr int O_F = O_D + NRT * NPK;
+    static constexpr int O_FN = O_F + NRT;
+    static constexpr int O_Y = O_FN + 2 * NLAT;
+    static constexpr int O_SP = O_Y + NRI * NY;
+    static constexpr int O_W = O_SP + NPO * NPO;
+    static constexpr int O_Z = O_W + NPO * NG;
+    static constexpr int O_LII = O_Z + NPO * (NG + 1);
+    static constexpr int TOTAL = O_LII + NRI * NRI;
+};
+
+// geometry slots inside the O_GEO block
+enum { G_J = 0, G_JI = 4, G_DET = 8, G_SGN = 9, G_LEN = 10, G_NK = 13, G_TF = 19, G_SIG = 25,
+       G_O = 28, G_AREA = 31 };
+
+__device__ void cell_geometry(const double *coords, const int *cells, int64_t c, double *geo) {
+    int v[3];
+    double X[3][2];
+    for (int i = 0; i < 3; ++i) {
+        v[i] = cells[3 * c + i];
+        X[i][0] = coords[2 * v[i]];
+        X[i][1] = coords[2 * v[i] + 1];
+    }
+    double J00 = X[1][0] - X[0][0], J01 = X[2][0] - X[0][0];
+    double J10 = X[1][1] - X[0][1], J11 = X[2][1] - X[0][1];
+    double det = J00 * J11 - J01 * J10;
+    geo[G_J + 0] = J00; geo[G_J + 1] = J01; geo[G_J + 2] = J10; geo[G_J + 3] = J11;
+    geo[G_JI + 0] = J11 / det; geo[G_JI + 1] = -J01 / det;
+    geo[G_JI + 2] = -J10 / det; geo[G_JI + 3] = J00 / det;
+    geo[G_DET] = det;
+    geo[G_SGN] = det > 0 ? 1.0 : -1.0;
+    geo[G_AREA] = 0.5 * fabs(det);
+    for (int f = 0; f < 3; ++f) {
+        int a = c_FV[f][0], b = c_FV[f][1];
+        double dx = X[b][0] - X[a][0], dy = X[b][1] - X[a][1];
+        double len = sqrt(dx * dx + dy * dy);
+        double o = v[a] < v[b] ? 1.0 : -1.0;
+        double tx = o * dx / len, ty = o * dy / len;
+        double nx = ty, ny = -tx;
+        double mx = 0.5 * (X[a][0] + X[b][0]) - X[f][0], my = 0.5 * (X[a][1] + X[b][1]) - X[f][1];
+        double sig = (nx * mx + ny * my) > 0 ? 1.0 : -1.0;
+        geo[G_LEN + f] = len;
+        geo[G_NK + 2 * f] = sig * nx; geo[G_NK + 2 * f + 1] = sig * ny;
+        geo[G_TF + 2 * f] = tx; geo[G_TF + 2 * f + 1] = ty;
+        geo[G_SIG + f] = sig;
+        geo[G_O + f] = o;
+    }
+}
+
+// in-place Cholesky of the n x n matrix in sm (row-major, leading dim ld), serial;
+// returns false on a non-positive pivot
+__device__ bool chol_serial(double *sm, int n, int ld) {
+    for (int j = 0; j < n; ++j) {
+        double d = sm[j * ld + j];
+        for (int p = 0; p < j; ++p) d -= sm[j * ld + p] * sm[j * ld + p];
+        if (!(d > 0.0)) return false;
+        d = sqrt(d);
+        sm[j * ld + j] = d;
+        for (int i = j + 1; i < n; ++i) {
+            double s = sm[i * ld + j];
+            for (int p = 0; p < j; ++p) s -= sm[i * ld + p] * sm[j * ld + p];
+            sm[i * ld + j] = s / d;
+        }
+    }
+    return true;
+}
+
+// solve L Lᵀ x = b for column `col` of the row-major RHS block B (n x nb, ld ldb)
+__device__ void chol_solve_col(const double *Lm, int n, int ld, double *B, int ldb, int col) {
+    for (int i = 0; i < n; ++i) {
+        double s = B[i * ldb + col];
+        for (int p = 0; p < i; ++p) s -= Lm[i * ld + p] * B[p * ldb + col];
+        B[i * ldb + col] = s / Lm[i * ld + i];
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = B[i * ldb + col];
+        for (int p = i + 1; p < n; ++p) s -= Lm[p * ld + i] * B[p * ldb + col];
+        B[i * ldb + col] = s / Lm[i * ld + i];
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(128)
+condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__restrict__ cells,
+                const double *__restrict__ R1, const double *__restrict__ R2,
+                const double *__restrict__ R3, const double *__restrict__ R4,
+                const double *__restrict__ R5, const double *__restrict__ R6, double nu,
+                double beta, double eps_inv, const double *__restrict__ forcing,
+                double *__restrict__ Aout, float *__restrict__ Afout, double *__restrict__ Fout,
+                int *flag) {
+    using D = Dims<K>;
+    extern __shared__ double sm[];
+    double *geo = sm + D::O_GEO;
+    double *sc = sm + D::O_S;
+    double *C = sm + D::O_C;
+    double *Km = sm + D::O_K;
+    double *Dm = sm + D::O_D;
+    double *Fl = sm + D::O_F;
+    double *Fn = sm + D::O_FN;
+    double *Y = sm + D::O_Y;
+    double *Sp = sm + D::O_SP;
+    double *Wm = sm + D::O_W;
+    double *Zm = sm + D::O_Z;
+    double *Lii = sm + D::O_LII;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    __shared__ int s_ok;
+
+    for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
+        if (tid == 0) {
+            cell_geometry(coords, cells, c, geo);
+            s_ok = 1;
+        }
+        if (forcing)
+            for (int i = tid; i < 2 * D::NLAT; i += nt) Fn[i] = forcing[c * 2 * D::NLAT + i];
+        __syncthreads();
+        const double det = geo[G_DET], sgn = geo[G_SGN], adet = fabs(det);
+        for (int i = tid; i < D::NRT; i += nt) {
+            double s = 1.0;
+            if (i < 3 * D::NF) {
+                int f = i / D::NF, m = i % D::NF;
+                s = sqrt(geo[G_LEN + f]) * geo[G_SIG + f] * sgn * ((m & 1) ? geo[G_O + f] : 1.0);
+            }
+            sc[i] = s;
+        }
+        __syncthreads();
+        // C = [C_u | C_hat], rows (c, e, j) with flux component (c, e) and g_j
+        for (int idx = tid; idx < D::NL * D::NCOL; idx += nt) {
+            int row = idx / D::NCOL, col = idx % D::NCOL;
+            int ce = row / D::NPK, j = row % D::NPK, cc = ce >> 1, e = ce & 1;
+            double val;
+            if (col < D::NRT) {
+                int i = col;
+                double vol = 0.0;
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b)
+                        vol += geo[G_J + 2 * cc + a] * geo[G_JI + 2 * b + e] *
+                               R1[((i * 2 + a) * 2 + b) * D::NPK + j];
+                vol *= sgn;
+                double bnd = 0.0;
+                const double fl[3] = {1.4142135623730951, 1.0, 1.0};
+                for (int f = 0; f < 3; ++f) {
+                    double nx = geo[G_NK + 2 * f], ny = geo[G_NK + 2 * f + 1];
+                    double ne = e == 0 ? nx : ny, nc_ = cc == 0 ? nx : ny;
+                    double acc = 0.0;
+                    for (int a = 0; a < 2; ++a) {
+                        double nJ = nx * geo[G_J + a] + ny * geo[G_J + 2 + a];
+                        double P = geo[G_J + 2 * cc + a] - nc_ * nJ;
+                        acc += P * R2[((f * D::NRT + i) * 2 + a) * D::NPK + j];
+                    }
+                    bnd += geo[G_LEN + f] / fl[f] / det * ne * acc;
+                }
+                val = (vol - bnd) * sc[i];
+            } else {
+                int h = col - D::NRT, f = h / D::NF, m = h % D::NF;
+                double ne = geo[G_NK + 2 * f + e];
+                double tc = geo[G_TF + 2 * f + cc];
+                double om = (m & 1) ? geo[G_O + f] : 1.0;
+                val = ne * tc * sqrt(geo[G_LEN + f]) * om * R3[(f * D::NPK + j) * D::NF + m];
+            }
+            C[idx] = val;
+        }
+        for (int idx = tid; idx < D::NRT * D::NPK; idx += nt) {
+            int i = idx / D::NPK;
+            Dm[idx] = sgn * R5[idx] * sc[i];
+        }
+        for (int i = tid; i < D::NRT; i += nt) {
+            double s = 0.0;
+            if (forcing) {
+                for (int n = 0; n < D::NLAT; ++n)
+                    for (int a = 0; a < 2; ++a) {
+                        double JtF = geo[G_J + a] * Fn[2 * n] + geo[G_J + 2 + a] * Fn[2 * n + 1];
+                        s += JtF * R6[(i * 2 + a) * D::NLAT + n];
+                    }
+            }
+            Fl[i] = sgn * s * sc[i];
+        }
+        __syncthreads();
+        // K = (nu/|det|) CᵀC + beta M_u
+        {
+            double JtJ[4];
+            JtJ[0] = geo[G_J + 0] * geo[G_J + 0] + geo[G_J + 2] * geo[G_J + 2];
+            JtJ[1] = geo[G_J + 0] * geo[G_J + 1] + geo[G_J + 2] * geo[G_J + 3];
+            JtJ[2] = JtJ[1];
+            JtJ[3] = geo[G_J + 1] * geo[G_J + 1] + geo[G_J + 3] * geo[G_J + 3];
+            for (int idx = tid; idx < D::NCOL * D::NCOL; idx += nt) {
+                int p = idx / D::NCOL, q = idx % D::NCOL;
+                double s = 0.0;
+                for (int r = 0; r < D::NL; ++r) s += C[r * D::NCOL + p] * C[r * D::NCOL + q];
+                s *= nu / adet;
+                if (p < D::NRT && q < D::NRT && beta != 0.0) {
+                    double m = 0.0;
+                    for (int a = 0; a < 2; ++a)
+                        for (int b = 0; b < 2; ++b)
+                            m += JtJ[2 * a + b] * R4[((p * 2 + a) * D::NRT + q) * 2 + b];
+                    s += beta / adet * m * sc[p] * sc[q];
+                }
+                Km[idx] = s;
+            }
+        }
+        __syncthreads();
+        // global column of output unknown o: facet f, t = normal/tangential, m
+        auto gcol = [&](int o) {
+            int f = o / (2 * D::NF), t = (o / D::NF) & 1, m = o % D::NF;
+            return t == 0 ? f * D::NF + m : D::NRT + f * D::NF + m;
+        };
+        if constexpr (D::NRI > 0) {
+            for (int idx = tid; idx < D::NRI * D::NRI; idx += nt) {
+                int r = idx / D::NRI, s = idx % D::NRI;
+                Lii[idx] = Km[(3 * D::NF + r) * D::NCOL + 3 * D::NF + s];
+            }
+            for (int idx = tid; idx < D::NRI * D::NY; idx += nt) {
+                int r = idx / D::NY, col = idx % D::NY;
+                double v;
+                if (col < D::NG) v = Km[(3 * D::NF + r) * D::NCOL + gcol(col)];
+                else if (col < D::NG + D::NPO) v = Dm[(3 * D::NF + r) * D::NPK + (col - D::NG + 1)];
+                else v = Fl[3 * D::NF + r];
+                Y[idx] = v;
+            }
+            __syncthreads();
+            if (tid == 0 && !chol_serial(Lii, D::NRI, D::NRI)) s_ok = 0;
+            __syncthreads();
+            for (int col = tid; col < D::NY; col += nt) chol_solve_col(Lii, D::NRI, D::NRI, Y, D::NY, col);
+            __syncthreads();
+            // S_p, W, v
+            for (int idx = tid; idx < D::NPO * D::NPO; idx += nt) {
+                int j = idx / D::NPO, j2 = idx % D::NPO;
+                double s = 0.0;
+                for (int r = 0; r < D::NRI; ++r)
+                    s += Dm[(3 * D::NF + r) * D::NPK + j + 1] * Y[r * D::NY + D::NG + j2];
+                Sp[idx] = s;
+            }
+            for (int idx = tid; idx < D::NPO * (D::NG + 1); idx += nt) {
+                int j = idx / (D::NG + 1), col = idx % (D::NG + 1);
+                double s = 0.0;
+                int ycol = col < D::NG ? col : D::NG + D::NPO;
+                for (int r = 0; r < D::NRI; ++r)
+                    s += Dm[(3 * D::NF + r) * D::NPK + j + 1] * Y[r * D::NY + ycol];
+                if (col < D::NG) {
+                    int gc = gcol(col);
+                    if (gc < D::NRT) s -= Dm[gc * D::NPK + j + 1];
+                    Wm[j * D::NG + col] = s;
+                }
+                Zm[j * (D::NG + 1) + col] = s;
+            }
+            __syncthreads();
+            if (tid == 0 && !chol_serial(Sp, D::NPO, D::NPO)) s_ok = 0;
+            __syncthreads();
+            for (int col = tid; col < D::NG + 1; col += nt) chol_solve_col(Sp, D::NPO, D::NPO, Zm, D::NG + 1, col);
+            __syncthreads();
+        }
+        // A = K_gg − K_gi Y_g + Wᵀ Z_W (+ AL),  F = F_g − K_gi Y_F + Wᵀ Z_v
+        const double al = eps_inv / geo[G_AREA];
+        for (int idx = tid; idx < D::NG * D::NG; idx += nt) {
+            int p = idx / D::NG, q = idx % D::NG;
+            int gp = gcol(p), gq = gcol(q);
+            double s = Km[gp * D::NCOL + gq];
+            for (int r = 0; r < D::NRI; ++r) s -= Km[gp * D::NCOL + 3 * D::NF + r] * Y[r * D::NY + q];
+            for (int j = 0; j < D::NPO; ++j) s += Wm[j * D::NG + p] * Zm[j * (D::NG + 1) + q];
+            int fp = p / (2 * D::NF), fq = q / (2 * D::NF);
+            if (p % (2 * D::NF) == 0 && q % (2 * D::NF) == 0)
+                s += al * geo[G_SIG + fp] * sqrt(geo[G_LEN + fp]) * geo[G_SIG + fq] * sqrt(geo[G_LEN + fq]);
+            Aout[c * D::NG * D::NG + idx] = s;
+            if (Afout) Afout[c * D::NG * D::NG + idx] = (float)s;
+        }
+        if (Fout)
+            for (int p = tid; p < D::NG; p += nt) {
+                int gp = gcol(p);
+                double s = gp < D::NRT ? Fl[gp] : 0.0;
+                for (int r = 0; r < D::NRI; ++r)
+                    s -= Km[gp * D::NCOL + 3 * D::NF + r] * Y[r * D::NY + D::NG + D::NPO];
+                for (int j = 0; j < D::NPO; ++j) s += Wm[j * D::NG + p] * Zm[j * (D::NG + 1) + D::NG];
+                Fout[c * D::NG + p] = s;
+            }
+        __syncthreads();
+        if (tid == 0 && !s_ok) atomicOr(flag, 1);
+        __syncthreads();
+    }
+}
+
+template <int K>
+cudaError_t launch_condense_k(const DevLevel &L, const double *ref, const RefTables &rt, double nu,
+                              double beta, double eps_inv, const double *forcing, double *A,
+                              float *Af, double *Fel, int *flag, cudaStream_t s) {
+    using D = Dims<K>;
+    size_t smem = sizeof(double) * D::TOTAL;
+    auto kern = condense_kernel<K>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const double *R[6];
+    for (int i = 0; i < 6; ++i) R[i] = ref + ref_table_offset(rt, i);
+    int64_t grid = L.nc < 152 * 64 ? L.nc : 152 * 64;
+    if (grid < 1) return cudaSuccess;
+    note_launches(1);
+    kern<<<(unsigned)grid, 128, smem, s>>>(L.nc, L.coords.p, L.cells.p, R[0], R[1], R[2], R[3], R[4],
+                                           R[5], nu, beta, eps_inv, forcing, A, Af, Fel, flag);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ patch inverses
+// Patch matrix A_ss assembled from the cells of the vertex star (slots = patch
+// facets), then inverted by Gauss-Jordan without pivoting (A_ss is SPD).
+__global__ void patch_inverse_kernel(int n_patches, int pf_max, int pc_max, int dpf, int nloc,
+                                     int np_max, const int *__restrict__ patch_nf,
+                                     const int *__restrict__ patch_nc,
+                                     const int *__restrict__ patch_cells,
+                                     const int *__restrict__ slot_src, const double *__restrict__ A,
+                                     double *__restrict__ Pinv, float *__restrict__ Pinvf,
+                                     int *flag) {
+    extern __shared__ double sm[];
+    int p = blockIdx.x;
+    if (p >= n_patches) return;
+    int nf = patch_nf[p], ncell = patch_nc[p];
+    int np = nf * dpf;
+    double *M = sm;                           // np_max*np_max
+    double *colp = M + np_max * np_max;       // np_max
+    double *rowp = colp + np_max;             // np_max
+    int *lfmap = (int *)(rowp + np_max);      // pc_max*pf_max: local facet of slot j in star cell si
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < pc_max * pf_max; i += nt) lfmap[i] = -1;
+    __syncthreads();
+    if (tid == 0)
+        for (int j = 0; j < nf; ++j)
+            for (int q = 0; q < 2; ++q) {
+                int src = slot_src[((size_t)p * pf_max + j) * 2 + q];
+                lfmap[(src >> 2) * pf_max + j] = src & 3;
+            }
+    __syncthreads();
+    for (int idx = tid; idx < np * np; idx += nt) {
+        int P = idx / np, Q = idx % np;
+        int j1 = P / dpf, d1 = P % dpf, j2 = Q / dpf, d2 = Q % dpf;
+        double s = 0.0;
+        for (int si = 0; si < ncell; ++si) {
+            int l1 = lfmap[si * pf_max + j1], l2 = lfmap[si * pf_max + j2];
+            if (l1 < 0 || l2 < 0) continue;
+            int c = patch_cells[(size_t)p * pc_max + si];
+            s += A[(size_t)c * nloc * nloc + (l1 * dpf + d1) * nloc + l2 * dpf + d2];
+        }
+        M[P * np + Q] = s;
+    }
+    __syncthreads();
+    __shared__ int ok;
+    if (tid == 0) ok = 1;
+    for (int piv = 0; piv < np; ++piv) {
+        __syncthreads();
+        double d = M[piv * np + piv];
+        if (!(d > 0.0)) {
+            if (tid == 0) ok = 0;
+            d = 1.0;
+        }
+        for (int i = tid; i < np; i += nt) {
+            colp[i] = M[i * np + piv];
+            rowp[i] = M[piv * np + i];
+        }
+        __syncthreads();
+        for (int idx = tid; idx < np * np; idx += nt) {
+            int i = idx / np, j = idx % np;
+            double v;
+            if (i == piv && j == piv) v = 1.0 / d;
+            else if (i == piv) v = rowp[j] / d;
+            else if (j == piv) v = -colp[i] / d;
+            else v = M[idx] - colp[i] * rowp[j] / d;
+            M[idx] = v;
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < np_max * np_max; idx += nt) {
+        int i = idx / np_max, j = idx % np_max;
+        double v = (i < np && j < np) ? M[i * np + j] : 0.0;
+        Pinv[(size_t)p * np_max * np_max + idx] = v;
+        if (Pinvf) Pinvf[(size_t)p * np_max * np_max + idx] = (float)v;
+    }
+    if (tid == 0 && !ok) atomicOr(flag, 2);
+}
+
+// ------------------------------------------------------------------ harmonic extension
+// Per coarse cell: A_TT, A_TB from the four children's lowest-order matrices
+// (slots 6..8 = T, 0..5 = B, two unknowns per slot), H = -A_TT^{-1} A_TB.
+__global__ void transfer_H_kernel(int64_t ncc, const int *__restrict__ children,
+                                  const int *__restrict__ child_slot, const int *__restrict__ slots,
+                                  const double *__restrict__ A0, double *__restrict__ Hout,
+                                  float *__restrict__ Hf, int *flag) {
+    int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (P >= ncc) return;
+    double M[18][18];
+    for (int i = 0; i < 18; ++i)
+        for (int j = 0; j < 18; ++j) M[i][j] = 0.0;
+    for (int ch = 0; ch < 4; ++ch) {
+        int c = children[4 * P + ch];
+        const double *Ac = A0 + (size_t)c * 36;
+        for (int l1 = 0; l1 < 3; ++l1) {
+            int s1 = child_slot[12 * P + 3 * ch + l1];
+            for (int l2 = 0; l2 < 3; ++l2) {
+                int s2 = child_slot[12 * P + 3 * ch + l2];
+                for (int a = 0; a < 2; ++a)
+                    for (int b = 0; b < 2; ++b) M[2 * s1 + a][2 * s2 + b] += Ac[(2 * l1 + a) * 6 + 2 * l2 + b];
+            }
+        }
+    }
+    // Cholesky of A_TT (rows/cols 12..17)
+    double Lm[6][6];
+    bool ok = true;
+    for (int i = 0; i < 6; ++i)
+        for (int j = 0; j < 6; ++j) Lm[i][j] = M[12 + i][12 + j];
+    for (int j = 0; j < 6; ++j) {
+        double d = Lm[j][j];
+        for (int p = 0; p < j; ++p) d -= Lm[j][p] * Lm[j][p];
+        if (!(d > 0.0)) { ok = false; d = 1.0; }
+        d = sqrt(d);
+        Lm[j][j] = d;
+        for (int i = j + 1; i < 6; ++i) {
+            double s = Lm[i][j];
+            for (int p = 0; p < j; ++p) s -= Lm[i][p] * Lm[j][p];
+            Lm[i][j] = s / d;
+        }
+    }
+    for (int col = 0; col < 12; ++col) {
+        int s = col / 2;
+        bool has = slots[9 * P + s] >= 0;
+        double x[6];
+        for (int i = 0; i < 6; ++i) x[i] = has ? -M[12 + i][col] : 0.0;
+        for (int i = 0; i < 6; ++i) {
+            double v = x[i];
+            for (int p = 0; p < i; ++p) v -= Lm[i][p] * x[p];
+            x[i] = v / Lm[i][i];
+        }
+        for (int i = 5; i >= 0; --i) {
+            double v = x[i];
+            for (int p = i + 1; p < 6; ++p) v -= Lm[p][i] * x[p];
+            x[i] = v / Lm[i][i];
+        }
+        for (int i = 0; i < 6; ++i) {
+            Hout[72 * P + i * 12 + col] = x[i];
+            Hf[72 * P + i * 12 + col] = (float)x[i];
+        }
+    }
+    if (!ok) atomicOr(flag, 4);
+}
+
+// ------------------------------------------------------------------ coarse dense inverse
+__global__ void coarse_assemble_kernel(int64_t n_int, const int *__restrict__ facet_adj,
+                                       const int *__restrict__ cell_int, const double *__restrict__ A0,
+                                       double *__restrict__ M, int64_t n) {
+    int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (row >= n) return;
+    int64_t i = row / 2;
+    int d = row % 2;
+    double *Mr = M + row * n;
+    for (int64_t j = 0; j < n; ++j) Mr[j] = 0.0;
+    for (int q = 0; q < 2; ++q) {
+        int adj = facet_adj[2 * i + q];
+        if (adj < 0) continue;
+        int c = adj >> 2, lf = adj & 3;
+        for (int col = 0; col < 6; ++col) {
+            int jf = cell_int[3 * c + col / 2];
+            if (jf < 0) continue;
+            Mr[2 * jf + col % 2] += A0[(size_t)c * 36 + (2 * lf + d) * 6 + col];
+        }
+    }
+}
+
+__global__ void gj_save_kernel(const double *M, int64_t n, int64_t piv, double *colp, double *rowp,
+                               int *flag) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) {
+        colp[i] = M[i * n + piv];
+        rowp[i] = M[piv * n + i];
+    }
+    if (i == 0 && !(M[piv * n + piv] > 0.0)) atomicOr(flag, 8);
+}
+
+__global__ void gj_update_kernel(double *M, int64_t n, int64_t piv, const double *colp,
+                                 const double *rowp) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int64_t i = idx / n, j = idx % n;
+    double d = rowp[piv];
+    if (!(d > 0.0)) d = 1.0;
+    double v;
+    if (i == piv && j == piv) v = 1.0 / d;
+    else if (i == piv) v = rowp[j] / d;
+    else if (j == piv) v = -colp[i] / d;
+    else v = M[idx] - colp[i] * rowp[j] / d;
+    M[idx] = v;
+}
+
+// ------------------------------------------------------------------ geometry, loads
+__global__ void cell_geometry_kernel(int64_t nc, const double *coords, const int *cells,
+                                     double *cell_d, double *cell_area) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    double geo[64];
+    cell_geometry(coords, cells, c, geo);
+    for (int f = 0; f < 3; ++f) cell_d[3 * c + f] = geo[G_SIG + f] * sqrt(geo[G_LEN + f]);
+    cell_area[c] = geo[G_AREA];
+}
+
+__global__ void assemble_load_kernel(int64_t n_int, int dpf, const int *__restrict__ facet_adj,
+                                     const double *__restrict__ Fel, double *__restrict__ F) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n_int * dpf) return;
+    int64_t i = idx / dpf;
+    int d = idx % dpf;
+    double s = 0.0;
+    for (int q = 0; q < 2; ++q) {
+        int adj = facet_adj[2 * i + q];
+        if (adj < 0) continue;
+        int c = adj >> 2, lf = adj & 3;
+        s += Fel[(size_t)c * 3 * dpf + lf * dpf + d];
+    }
+    F[idx] = s;
+}
+
+unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+} // namespace
+
+cudaError_t launch_condense(int k, const DevLevel &L, const double *ref, const RefTables &rt, double nu,
+                            double beta, double eps_inv, const double *forcing, double *A, float *Af,
+                            double *Fel, int *flag, cudaStream_t s) {
+    switch (k) {
+    case 0: return launch_condense_k<0>(L, ref, rt, nu, beta, eps_inv, forcing, A, Af, Fel, flag, s);
+    case 1: return launch_condense_k<1>(L, ref, rt, nu, beta, eps_inv, forcing, A, Af, Fel, flag, s);
+    case 2: return launch_condense_k<2>(L, ref, rt, nu, beta, eps_inv, forcing, A, Af, Fel, flag, s);
+    case 3: return launch_condense_k<3>(L, ref, rt, nu, beta, eps_inv, forcing, A, Af, Fel, flag, s);
+    case 4: return launch_condense_k<4>(L, ref, rt, nu, beta, eps_inv, forcing, A, Af, Fel, flag, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_patch_inverse(const DevLevel &L, const DevOperator &op, int *flag, cudaStream_t s) {
+    if (L.n_patches == 0) return cudaSuccess;
+    size_t smem = sizeof(double) * ((size_t)op.np_max * op.np_max + 2 * op.np_max) +
+                  sizeof(int) * (size_t)L.pc_max * L.pf_max;
+    cudaError_t e = cudaFuncSetAttribute(patch_inverse_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    patch_inverse_kernel<<<L.n_patches, 256, smem, s>>>(
+        L.n_patches, L.pf_max, L.pc_max, op.dpf, op.nloc, op.np_max, L.patch_nf.p, L.patch_nc.p,
+        L.patch_cells.p, L.patch_slot_src.p, op.A.p, op.Pinv.p, op.Pinvf.p, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transfer_H(const DevLevel &F, int *flag, cudaStream_t s) {
+    if (F.nc_coarse == 0) return cudaSuccess;
+    note_launches(1);
+    transfer_H_kernel<<<blocks_for(F.nc_coarse, 64), 64, 0, s>>>(
+        F.nc_coarse, F.tr_children.p, F.tr_child_slot.p, F.tr_slots.p, F.op0.A.p, F.tr_H.p,
+        F.tr_Hf.p, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_inverse(const DevLevel &L0, double *inv, int64_t n, int *flag,
+                                  cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    coarse_assemble_kernel<<<blocks_for(n, 128), 128, 0, s>>>(L0.n_int, L0.facet_adj.p, L0.cell_int.p,
+                                                              L0.op0.A.p, inv, n);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    double *tmp = nullptr;
+    e = cudaMallocAsync(&tmp, sizeof(double) * 2 * n, s);
+    if (e != cudaSuccess) return e;
+    for (int64_t piv = 0; piv < n; ++piv) {
+        note_launches(1);
+        gj_save_kernel<<<blocks_for(n, 256), 256, 0, s>>>(inv, n, piv, tmp, tmp + n, flag);
+        note_launches(1);
+        gj_update_kernel<<<blocks_for(n * n, 256), 256, 0, s>>>(inv, n, piv, tmp, tmp + n);
+    }
+    e = cudaGetLastError();
+    cudaFreeAsync(tmp, s);
+    return e;
+}
+
+cudaError_t launch_cell_geometry(DevLevel &L, cudaStream_t s) {
+    if (L.nc == 0) return cudaSuccess;
+    note_launches(1);
+    cell_geometry_kernel<<<blocks_for(L.nc, 128), 128, 0, s>>>(L.nc, L.coords.p, L.cells.p,
+                                                               L.cell_d.p, L.cell_area.p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_load(const DevLevel &L, const DevOperator &op, double *F, cudaStream_t s) {
+    int64_t n = L.n_int * op.dpf;
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    assemble_load_kernel<<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, op.dpf, L.facet_adj.p, op.Fel.p, F);
+    return cudaGetLastError();
+}
+
+} // namespace hdg

@@ -1,0 +1,226 @@
+// Internal declarations of the GB300 H(div)-HDG hp-multigrid library.
+//
+// Host side: topology (facets, orientation, patches, colouring, transfer
+// maps) and reference-element tables, built once per mesh hierarchy.
+// Device side: condensed element matrices, patch inverses, transfer blocks
+// and all hot-path kernels.  See include/hdg.h for the public layouts.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "hdg.h"
+
+namespace hdg {
+
+constexpr int MAX_K = 4;
+constexpr int MAX_LEVELS = 16;
+constexpr int MAX_RESTART = 64;
+
+// ---------------------------------------------------------------- host data
+struct HostLevel {
+    int64_t nv = 0, nc = 0;
+    std::vector<double> coords;          // nv*2
+    std::vector<int32_t> cells;          // nc*3
+    std::vector<int32_t> parent;         // nc (level > 0)
+    std::vector<int32_t> colour;         // nv
+    // facets
+    int64_t nf = 0, n_int = 0;
+    std::vector<int32_t> facet_v;        // nf*2 sorted vertex pair
+    std::vector<int32_t> cell_facet;     // nc*3 facet opposite local vertex f
+    std::vector<int32_t> facet_cells;    // nf*2 (second = -1 on boundary)
+    std::vector<int32_t> facet_lf;       // nf*2 local facet index in each cell
+    std::vector<int32_t> interior_index; // nf -> interior number or -1
+    std::vector<int32_t> interior_facets;// n_int
+    // vertex patches, sorted by (colour, vertex id); only non-empty patches
+    int n_patches = 0, n_colours = 0, pf_max = 0, pc_max = 0;
+    std::vector<int32_t> colour_ptr;     // n_colours+1 offsets into patch order
+    std::vector<int32_t> patch_nf;       // n_patches
+    std::vector<int32_t> patch_facets;   // n_patches*pf_max interior facet ids (-1 pad)
+    std::vector<int32_t> patch_nc;       // n_patches
+    std::vector<int32_t> patch_cells;    // n_patches*pc_max
+    // for slot j of patch p: the two (star-cell index << 2 | local facet) pairs
+    std::vector<int32_t> patch_slot_src; // n_patches*pf_max*2
+};
+
+// transfer data between level l-1 (coarse) and l (fine), stored on level l
+struct HostTransfer {
+    int64_t nc_coarse = 0;
+    std::vector<int32_t> slots;      // nc_coarse*9: fine interior facet id per slot or -1
+    std::vector<int32_t> nbr;        // nc_coarse*6: (other coarse cell << 4 | its slot) or -1
+    std::vector<int32_t> children;   // nc_coarse*4
+    std::vector<int32_t> child_slot; // nc_coarse*4*3: slot of each child's local facet
+    std::vector<double> W;           // nc_coarse*12*6 averaging weights (eq. avgOpt)
+    int64_t nB = 0;
+    std::vector<int32_t> fineB;      // nB: fine interior facet id of each B facet
+    std::vector<int32_t> fineB_src;  // nB*2: (coarse cell << 4 | slot)
+};
+
+// reference-element tables for order k (FP64), see reference.cpp
+struct RefTables {
+    int k = -1, npk = 0, nrt = 0, nf = 0, nlat = 0;
+    std::vector<double> R1, R2, R3, R4, R5, R6;
+};
+
+// layout of the small Krylov block (restart R):
+//   H: (R+1) x R column-major at 0; cs, sn: R; g: R+1; y: R; h1, h2: R+1; nrm2, res, hn
+struct SmallLayout {
+    int R;
+    __host__ __device__ int H() const { return 0; }
+    __host__ __device__ int cs() const { return (R + 1) * R; }
+    __host__ __device__ int sn() const { return cs() + R; }
+    __host__ __device__ int g() const { return sn() + R; }
+    __host__ __device__ int y() const { return g() + R + 1; }
+    __host__ __device__ int h1() const { return y() + R; }
+    __host__ __device__ int h2() const { return h1() + R + 1; }
+    __host__ __device__ int nrm2() const { return h2() + R + 1; }
+    __host__ __device__ int res() const { return nrm2() + 1; }
+    __host__ __device__ int hn() const { return res() + 1; }
+    __host__ __device__ int total() const { return hn() + 1; }
+};
+
+
+// ---------------------------------------------------------------- device data
+template <class T>
+struct DBuf {
+    T *p = nullptr;
+    size_t n = 0;
+};
+
+struct DevOperator {
+    int k = -1, dpf = 0, nloc = 0, np_max = 0;
+    DBuf<double> A;      // nc*nloc*nloc
+    DBuf<float> Af;
+    DBuf<double> Fel;    // nc*nloc element loads
+    DBuf<double> Pinv;   // n_patches*np_max*np_max
+    DBuf<float> Pinvf;
+};
+
+struct DevLevel {
+    int64_t nv = 0, nc = 0, n_int = 0;
+    DBuf<double> coords;       // nv*2
+    DBuf<int32_t> cells;       // nc*3
+    DBuf<int32_t> cell_int;    // nc*3 interior facet id or -1
+    DBuf<int32_t> facet_adj;   // n_int*2 (cell << 2 | lf) or -1
+    DBuf<double> cell_d;       // nc*3 flux weights sigma*sqrt|F| of each local facet
+    DBuf<double> cell_area;    // nc
+    // patches
+    int n_patches = 0, n_colours = 0, pf_max = 0, pc_max = 0;
+    std::vector<int32_t> colour_ptr;
+    DBuf<int32_t> patch_nf, patch_facets, patch_nc, patch_cells, patch_slot_src;
+    DevOperator op0;           // lowest-order condensed operator of this level
+    // transfer from level-1
+    int64_t nc_coarse = 0, nB = 0;
+    DBuf<int32_t> tr_slots, tr_nbr, tr_children, tr_child_slot, tr_fineB, tr_fineB_src;
+    DBuf<double> tr_W, tr_H;
+    DBuf<float> tr_Wf, tr_Hf;
+    // MG work vectors (FP64 and FP32 variants), 2 per interior facet
+    DBuf<double> g, u, r, t;
+    DBuf<float> gf, uf, rf, tf;
+    DBuf<double> ct1, ct2;     // coarse-cell temps for restriction (nc_coarse*12, *6)
+    DBuf<float> ct1f, ct2f;
+};
+
+} // namespace hdg
+
+struct hdg_ctx {
+    int device = 0;
+    std::string err;
+    int n_levels = 0;
+    std::vector<hdg::HostLevel> H;
+    std::vector<hdg::HostTransfer> T;   // T[l] for l >= 1
+    std::vector<hdg::DevLevel> L;
+    bool condensed = false;
+    hdg_params prm{};
+    hdg::RefTables refk, ref0;
+    hdg::DBuf<double> refk_dev, ref0_dev;   // packed R1..R6
+    hdg::DevOperator opk;                    // order-k operator on the finest mesh
+    int64_t n_dof = 0;
+    // order-k vectors (finest)
+    hdg::DBuf<double> kr, ku, kt;            // FP64 residual/solution/temp
+    hdg::DBuf<float> krf, kuf, kgf;          // FP32 copies
+    // coarsest dense inverse
+    int64_t n0 = 0;
+    hdg::DBuf<double> coarse_inv;
+    hdg::DBuf<int> status_flag;              // device error flag
+    // Krylov workspace
+    int restart_alloc = 0;
+    hdg::DBuf<double> V, Z, w, partials, small;   // small: Hessenberg, rotations, g, y
+    hdg::DBuf<double> uz_partials;
+    double *h_pinned = nullptr;              // host pinned scalars
+};
+
+namespace hdg {
+
+// kernel-launch counter (ops.cu): every launcher adds the kernels it enqueues
+void note_launches(int n);
+unsigned long long launch_count();
+
+// reference.cpp
+void build_reference_tables(int k, RefTables &out);
+size_t ref_table_offset(const RefTables &t, int which);   // offset of R1..R6 in packed buffer
+
+// topology.cpp
+std::string build_level_topology(HostLevel &L, const int32_t *colour_or_null);
+std::string build_transfer(const HostLevel &coarse, const HostLevel &fine, HostTransfer &T);
+
+// kernels: condensation and setup (condense.cu)
+cudaError_t launch_condense(int k, const DevLevel &L, const double *ref, const RefTables &rt,
+                            double nu, double beta, double eps_inv, const double *forcing,
+                            double *A, float *Af, double *Fel, int *flag, cudaStream_t s);
+cudaError_t launch_patch_inverse(const DevLevel &L, const DevOperator &op, int *flag, cudaStream_t s);
+cudaError_t launch_transfer_H(const DevLevel &fine, int *flag, cudaStream_t s);
+cudaError_t launch_coarse_inverse(const DevLevel &L0, double *inv, int64_t n, int *flag,
+                                  cudaStream_t s);
+cudaError_t launch_assemble_load(const DevLevel &L, const DevOperator &op, double *F, cudaStream_t s);
+cudaError_t launch_cell_geometry(DevLevel &L, cudaStream_t s);
+
+// kernels: hot path (ops.cu)
+template <class T>
+cudaError_t launch_apply(const DevLevel &L, const DevOperator &op, const T *A, const T *x,
+                         const T *g, T *y, cudaStream_t s);   // y = A x, or y = g - A x if g
+template <class T>
+cudaError_t launch_gs_colour(const DevLevel &L, const DevOperator &op, const T *A, const T *Pinv,
+                             int colour, const T *g, T *u, cudaStream_t s);
+template <class T>
+cudaError_t launch_prolong_add(const DevLevel &fine, const DevLevel &coarse, const T *W,
+                               const T *Hm, const T *uc, T *tmp, T *uf, cudaStream_t s);
+template <class T>
+cudaError_t launch_restrict(const DevLevel &fine, const DevLevel &coarse, const T *W,
+                            const T *Hm, const T *rf, T *t1, T *t2, T *rc, cudaStream_t s);
+template <class T>
+cudaError_t launch_hp_restrict(int k, int64_t n_int, const T *r, T *r0, cudaStream_t s);
+template <class T>
+cudaError_t launch_hp_prolong_add(int k, int64_t n_int, const T *d0, T *u, cudaStream_t s);
+cudaError_t launch_coarse_apply(const double *inv, int64_t n, const double *g, double *u,
+                                cudaStream_t s);
+cudaError_t launch_d2f(const double *x, float *y, int64_t n, cudaStream_t s);
+cudaError_t launch_f2d(const float *x, double *y, int64_t n, cudaStream_t s);
+template <class T>
+cudaError_t launch_fill(T *x, T v, int64_t n, cudaStream_t s);
+cudaError_t launch_axpby(double a, const double *x, double b, double *y, int64_t n, cudaStream_t s);
+
+// Krylov and Uzawa (ops.cu)
+int krylov_partial_blocks();
+cudaError_t launch_dots(const double *V, int nv, int64_t ld, const double *w, int64_t n,
+                        double *partials, cudaStream_t s);
+cudaError_t launch_update_dots(const double *V, int nv, int64_t ld, double *w, int64_t n,
+                               const double *h, double *partials, int mode, cudaStream_t s);
+cudaError_t launch_reduce_partials(const double *partials, int nv, double *out, int accumulate,
+                                   cudaStream_t s);
+cudaError_t launch_givens(double *small, int j, int restart, double *host_mirror, cudaStream_t s);
+cudaError_t launch_scale_next(const double *w, double *v, int64_t n, const double *small, int j,
+                              int restart, cudaStream_t s);
+cudaError_t launch_init_cycle(const double *r, double *v0, int64_t n, double *small, int restart,
+                              cudaStream_t s);
+cudaError_t launch_solve_update(double *small, int m, int restart, const double *Z, int64_t ld,
+                                double *x, int64_t n, cudaStream_t s);
+cudaError_t launch_uzawa_rhs(const DevLevel &L, int k, const double *F, const double *p, double *g,
+                             cudaStream_t s);
+cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p,
+                                double eps_inv, double *partials, cudaStream_t s);
+
+} // namespace hdg

@@ -1,0 +1,691 @@
+// Hot-path kernels of the hp-multigrid preconditioned FGMRES (FP64 / FP32).
+//
+// * apply: y = Σ_K E_Kᵀ A_K E_K x (eqs. stOptForm, stALform), computed per
+//   skeleton unknown: the row of every interior facet is the sum of the rows
+//   of the two adjacent cells' condensed matrices against the gathered facet
+//   values of those cells.  No atomics; every output written once.
+// * gs_colour: one phase of multicolour block Gauss–Seidel over vertex
+//   patches (eq. bjac with GS, Section 5): every patch of the colour forms its
+//   residual rows from the cells of its star, multiplies by the stored patch
+//   inverse and updates its unknowns.  Patches of one colour share no cell, so
+//   the phase equals the sequential sweep over those patches.
+// * hp transfers (Section 3.5): Π_k^0 takes the m = 0 normal and tangential
+//   coefficient of every facet; Π_0^k adds them back.
+// * CR transfers (eqs. avgOpt, div-transfer, harmonic-ex): prolongation
+//   = averaging of the coarse Π^CR values at fine boundary-facet midpoints
+//   followed by the harmonic extension H = −A_TT⁻¹A_TB inside every coarse
+//   cell; restriction = its exact transpose.
+// * Krylov: fused classical Gram–Schmidt passes (dots, update+dots,
+//   update+norm) with deterministic two-stage reductions, Givens rotations
+//   and the triangular solve on the device.
+// * Uzawa (eq. stOpEq-ALU): load F + Dᵀp and the cell-wise pressure update.
+//
+// Symmetric element and patch matrices are read as their transposes so that
+// consecutive threads (consecutive rows) touch consecutive addresses.
+#include <cuda_runtime.h>
+
+#include <atomic>
+
+#include "hdg_internal.h"
+
+namespace hdg {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+
+namespace {
+
+constexpr int KRYLOV_BLOCKS = 456;    // 3 x 152 SMs
+constexpr int KRYLOV_THREADS = 256;
+constexpr int MAXV = 33;              // restart <= 32: up to 33 basis vectors
+
+unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+template <class T, int DPF>
+__global__ void __launch_bounds__(256)
+apply_kernel(int64_t n_int, const int *__restrict__ facet_adj, const int *__restrict__ cell_int,
+             const T *__restrict__ A, const T *__restrict__ x, const T *__restrict__ g,
+             T *__restrict__ y) {
+    constexpr int NLOC = 3 * DPF;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n_int * DPF) return;
+    int64_t i = idx / DPF;
+    int d = (int)(idx - i * DPF);
+    T acc = 0;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        int adj = facet_adj[2 * i + q];
+        if (adj < 0) continue;
+        int c = adj >> 2, lf = adj & 3;
+        const T *Ac = A + (size_t)c * NLOC * NLOC + lf * DPF + d;
+#pragma unroll
+        for (int f2 = 0; f2 < 3; ++f2) {
+            int j = cell_int[3 * c + f2];
+            if (j < 0) continue;
+            const T *xs = x + (size_t)j * DPF;
+#pragma unroll
+            for (int d2 = 0; d2 < DPF; ++d2) acc += Ac[(f2 * DPF + d2) * NLOC] * xs[d2];
+        }
+    }
+    y[idx] = g ? g[idx] - acc : acc;
+}
+
+template <class T, int DPF>
+__global__ void gs_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
+                          const int *__restrict__ patch_nf, const int *__restrict__ patch_facets,
+                          const int *__restrict__ patch_nc, const int *__restrict__ patch_cells,
+                          const int *__restrict__ slot_src, const int *__restrict__ cell_int,
+                          const T *__restrict__ A, const T *__restrict__ Pinv,
+                          const T *__restrict__ g, T *__restrict__ u) {
+    constexpr int NLOC = 3 * DPF;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *xs = reinterpret_cast<T *>(smraw);     // pc_max * NLOC
+    T *r = xs + pc_max * NLOC;                 // np_max
+    const int p = p0 + blockIdx.x;
+    if (p >= p1) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
+    for (int t = tid; t < ncell * NLOC; t += nt) {
+        int si = t / NLOC, l = t % NLOC;
+        int c = patch_cells[(size_t)p * pc_max + si];
+        int j = cell_int[3 * c + l / DPF];
+        xs[t] = j >= 0 ? u[(size_t)j * DPF + l % DPF] : T(0);
+    }
+    __syncthreads();
+    for (int t = tid; t < np; t += nt) {
+        int js = t / DPF, d = t % DPF;
+        int F = patch_facets[(size_t)p * pf_max + js];
+        T acc = g[(size_t)F * DPF + d];
+        for (int q = 0; q < 2; ++q) {
+            int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
+            int si = src >> 2, lf = src & 3;
+            int c = patch_cells[(size_t)p * pc_max + si];
+            const T *Ac = A + (size_t)c * NLOC * NLOC + lf * DPF + d;
+            const T *xc = xs + si * NLOC;
+#pragma unroll
+            for (int col = 0; col < NLOC; ++col) acc -= Ac[col * NLOC] * xc[col];
+        }
+        r[t] = acc;
+    }
+    __syncthreads();
+    const T *Pi = Pinv + (size_t)p * np_max * np_max;
+    for (int t = tid; t < np; t += nt) {
+        T acc = 0;
+        for (int j = 0; j < np; ++j) acc += Pi[(size_t)j * np_max + t] * r[j];
+        int F = patch_facets[(size_t)p * pf_max + t / DPF];
+        u[(size_t)F * DPF + t % DPF] += acc;
+    }
+}
+
+template <class T>
+__global__ void hp_restrict_kernel(int k, int64_t n_int, const T *r, T *r0) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    int dpf = 2 * (k + 1);
+    r0[2 * i] = r[i * dpf];
+    r0[2 * i + 1] = r[i * dpf + k + 1];
+}
+
+template <class T>
+__global__ void hp_prolong_kernel(int k, int64_t n_int, const T *d0, T *u) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    int dpf = 2 * (k + 1);
+    u[i * dpf] += d0[2 * i];
+    u[i * dpf + k + 1] += d0[2 * i + 1];
+}
+
+template <class T>
+__global__ void prolong_B_kernel(int64_t nB, const int *__restrict__ fineB,
+                                 const int *__restrict__ fineB_src, const int *__restrict__ ccell_int,
+                                 const T *__restrict__ W, const T *__restrict__ uc, T *__restrict__ tmp,
+                                 T *__restrict__ uf) {
+    int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nB) return;
+    T v0 = 0, v1 = 0;
+    for (int q = 0; q < 2; ++q) {
+        int src = fineB_src[2 * b + q];
+        int P = src >> 4, s = src & 15;
+        const T *Wk = W + (size_t)P * 72;
+        for (int fp = 0; fp < 3; ++fp) {
+            int j = ccell_int[3 * P + fp];
+            if (j < 0) continue;
+            for (int cq = 0; cq < 2; ++cq) {
+                T u = uc[2 * (size_t)j + cq];
+                v0 += Wk[(2 * s) * 6 + 2 * fp + cq] * u;
+                v1 += Wk[(2 * s + 1) * 6 + 2 * fp + cq] * u;
+            }
+        }
+    }
+    int i = fineB[b];
+    tmp[2 * (size_t)i] = v0;
+    tmp[2 * (size_t)i + 1] = v1;
+    uf[2 * (size_t)i] += v0;
+    uf[2 * (size_t)i + 1] += v1;
+}
+
+template <class T>
+__global__ void prolong_T_kernel(int64_t ncc, const int *__restrict__ slots, const T *__restrict__ H,
+                                 const T *__restrict__ tmp, T *__restrict__ uf) {
+    int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (P >= ncc) return;
+    T b[12];
+    for (int s = 0; s < 6; ++s) {
+        int i = slots[9 * P + s];
+        b[2 * s] = i >= 0 ? tmp[2 * (size_t)i] : T(0);
+        b[2 * s + 1] = i >= 0 ? tmp[2 * (size_t)i + 1] : T(0);
+    }
+    const T *Hk = H + (size_t)P * 72;
+    for (int t = 0; t < 6; ++t) {
+        T acc = 0;
+        for (int c = 0; c < 12; ++c) acc += Hk[t * 12 + c] * b[c];
+        int i = slots[9 * P + 6 + t / 2];
+        uf[2 * (size_t)i + (t & 1)] += acc;
+    }
+}
+
+template <class T>
+__global__ void restrict_T_kernel(int64_t ncc, const int *__restrict__ slots, const T *__restrict__ H,
+                                  const T *__restrict__ rf, T *__restrict__ t1) {
+    int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (P >= ncc) return;
+    T rT[6];
+    for (int t = 0; t < 6; ++t) rT[t] = rf[2 * (size_t)slots[9 * P + 6 + t / 2] + (t & 1)];
+    const T *Hk = H + (size_t)P * 72;
+    for (int c = 0; c < 12; ++c) {
+        T acc = 0;
+        for (int t = 0; t < 6; ++t) acc += Hk[t * 12 + c] * rT[t];
+        t1[12 * P + c] = acc;
+    }
+}
+
+template <class T>
+__global__ void restrict_B_kernel(int64_t ncc, const int *__restrict__ slots, const int *__restrict__ nbr,
+                                  const T *__restrict__ W, const T *__restrict__ rf,
+                                  const T *__restrict__ t1, T *__restrict__ t2) {
+    int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (P >= ncc) return;
+    T z[12];
+    for (int s = 0; s < 6; ++s) {
+        int i = slots[9 * P + s];
+        if (i < 0) {
+            z[2 * s] = z[2 * s + 1] = 0;
+            continue;
+        }
+        int nb = nbr[6 * P + s];
+        int Q = nb >> 4, s2 = nb & 15;
+        for (int c = 0; c < 2; ++c)
+            z[2 * s + c] = rf[2 * (size_t)i + c] + t1[12 * P + 2 * s + c] + t1[12 * (size_t)Q + 2 * s2 + c];
+    }
+    const T *Wk = W + (size_t)P * 72;
+    for (int col = 0; col < 6; ++col) {
+        T acc = 0;
+        for (int row = 0; row < 12; ++row) acc += Wk[row * 6 + col] * z[row];
+        t2[6 * P + col] = acc;
+    }
+}
+
+template <class T>
+__global__ void restrict_C_kernel(int64_t n_int_c, const int *__restrict__ facet_adj_c,
+                                  const T *__restrict__ t2, T *__restrict__ rc) {
+    int64_t G = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (G >= n_int_c) return;
+    T a0 = 0, a1 = 0;
+    for (int q = 0; q < 2; ++q) {
+        int adj = facet_adj_c[2 * G + q];
+        int K = adj >> 2, lf = adj & 3;
+        a0 += t2[6 * (size_t)K + 2 * lf];
+        a1 += t2[6 * (size_t)K + 2 * lf + 1];
+    }
+    rc[2 * G] = a0;
+    rc[2 * G + 1] = a1;
+}
+
+__global__ void coarse_apply_kernel(const double *__restrict__ inv, int64_t n,
+                                    const double *__restrict__ g, double *__restrict__ u) {
+    int64_t row = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    int lane = threadIdx.x & 31;
+    if (row >= n) return;
+    double acc = 0.0;
+    for (int64_t j = lane; j < n; j += 32) acc += inv[row * n + j] * g[j];
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if (lane == 0) u[row] = acc;
+}
+
+__global__ void d2f_kernel(const double *x, float *y, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (float)x[i];
+}
+__global__ void f2d_kernel(const float *x, double *y, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = (double)x[i];
+}
+template <class T>
+__global__ void fill_kernel(T *x, T v, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+__global__ void axpby_kernel(double a, const double *x, double b, double *y, int64_t n) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = a * x[i] + b * y[i];
+}
+
+// ---------------------------------------------------------------- Krylov
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// block-reduce acc[0..nv) and write partials[i*gridDim.x + block]
+__device__ void block_reduce_store(double *acc, int nv, double *partials) {
+    __shared__ double red[KRYLOV_THREADS / 32][MAXV];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) {
+        if (i < nv) {
+            double v = warp_sum(acc[i]);
+            if (lane == 0) red[wid][i] = v;
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < KRYLOV_THREADS / 32; ++w) s += red[w][i];
+        partials[(size_t)i * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// partials of h_i = <V_i, w>
+__global__ void __launch_bounds__(KRYLOV_THREADS)
+dots_kernel(const double *__restrict__ V, int nv, int64_t ld, const double *__restrict__ w, int64_t n,
+            double *__restrict__ partials) {
+    double acc[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) acc[i] = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double we = w[e];
+#pragma unroll
+        for (int i = 0; i < MAXV; ++i)
+            if (i < nv) acc[i] += V[(size_t)i * ld + e] * we;
+    }
+    block_reduce_store(acc, nv, partials);
+}
+
+// w -= Σ_i h_i V_i, then (mode 1) partials of <V_i, w> or (mode 2) of <w, w>
+__global__ void __launch_bounds__(KRYLOV_THREADS)
+update_dots_kernel(const double *__restrict__ V, int nv, int64_t ld, double *__restrict__ w, int64_t n,
+                   const double *__restrict__ h, double *__restrict__ partials, int mode) {
+    __shared__ double hs[MAXV];
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
+    __syncthreads();
+    double acc[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) acc[i] = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        double v[MAXV];
+        double we = w[e];
+#pragma unroll
+        for (int i = 0; i < MAXV; ++i)
+            if (i < nv) {
+                v[i] = V[(size_t)i * ld + e];
+                we -= hs[i] * v[i];
+            }
+        w[e] = we;
+        if (mode == 1) {
+#pragma unroll
+            for (int i = 0; i < MAXV; ++i)
+                if (i < nv) acc[i] += v[i] * we;
+        } else {
+            acc[0] += we * we;
+        }
+    }
+    block_reduce_store(acc, mode == 1 ? nv : 1, partials);
+}
+
+__global__ void reduce_partials_kernel(const double *__restrict__ partials, int nv, int nb,
+                                       double *__restrict__ out, int accumulate) {
+    int i = blockIdx.x;
+    if (i >= nv) return;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) s += partials[(size_t)i * nb + b];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) out[i] = accumulate ? out[i] + s : s;
+}
+
+__global__ void givens_kernel(double *sm, int j, int R) {
+    SmallLayout Ly{R};
+    double *H = sm + Ly.H(), *cs = sm + Ly.cs(), *sn = sm + Ly.sn(), *g = sm + Ly.g();
+    double col[MAXV + 1];
+    for (int i = 0; i <= j; ++i) col[i] = sm[Ly.h1() + i] + sm[Ly.h2() + i];
+    double hn = sqrt(fmax(sm[Ly.nrm2()], 0.0));
+    col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+        double a = col[i], b = col[i + 1];
+        col[i] = cs[i] * a + sn[i] * b;
+        col[i + 1] = -sn[i] * a + cs[i] * b;
+    }
+    double den = hypot(col[j], col[j + 1]);
+    double c = den > 0.0 ? col[j] / den : 1.0, s = den > 0.0 ? col[j + 1] / den : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    for (int i = 0; i <= j + 1; ++i) H[(size_t)j * (R + 1) + i] = col[i];
+    sm[Ly.res()] = fabs(g[j + 1]);
+    sm[Ly.hn()] = hn;
+}
+
+__global__ void scale_next_kernel(const double *__restrict__ w, double *__restrict__ v, int64_t n,
+                                  const double *__restrict__ sm, int hn_off) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double hn = sm[hn_off];
+    if (i < n) v[i] = hn > 0.0 ? w[i] / hn : 0.0;
+}
+
+__global__ void init_cycle_kernel(const double *__restrict__ r, double *__restrict__ v0, int64_t n,
+                                  double *__restrict__ sm, int R) {
+    SmallLayout Ly{R};
+    double beta = sqrt(fmax(sm[Ly.nrm2()], 0.0));
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) v0[i] = beta > 0.0 ? r[i] / beta : 0.0;
+    if (i <= R) sm[Ly.g() + i] = (i == 0) ? beta : 0.0;
+}
+
+__global__ void backsolve_kernel(double *sm, int m, int R) {
+    SmallLayout Ly{R};
+    const double *H = sm + Ly.H(), *g = sm + Ly.g();
+    double *y = sm + Ly.y();
+    for (int i = m - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int p = i + 1; p < m; ++p) s -= H[(size_t)p * (R + 1) + i] * y[p];
+        y[i] = s / H[(size_t)i * (R + 1) + i];
+    }
+}
+
+__global__ void update_x_kernel(const double *__restrict__ Z, int m, int64_t ld, const double *__restrict__ sm,
+                                int y_off, double *__restrict__ x, int64_t n) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double s = x[e];
+    for (int j = 0; j < m; ++j) s += sm[y_off + j] * Z[(size_t)j * ld + e];
+    x[e] = s;
+}
+
+// ---------------------------------------------------------------- Uzawa
+__global__ void uzawa_rhs_kernel(int64_t n_int, int dpf, const int *__restrict__ facet_adj,
+                                 const double *__restrict__ cell_d, const double *__restrict__ F,
+                                 const double *__restrict__ p, double *__restrict__ g) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n_int * dpf) return;
+    int64_t i = idx / dpf;
+    int d = (int)(idx - i * dpf);
+    double v = F[idx];
+    if (d == 0)
+        for (int q = 0; q < 2; ++q) {
+            int adj = facet_adj[2 * i + q];
+            if (adj < 0) continue;
+            int c = adj >> 2, lf = adj & 3;
+            v += p[c] * cell_d[3 * c + lf];
+        }
+    g[idx] = v;
+}
+
+__global__ void __launch_bounds__(KRYLOV_THREADS)
+uzawa_update_kernel(int64_t nc, int dpf, const int *__restrict__ cell_int,
+                    const double *__restrict__ cell_d, const double *__restrict__ area,
+                    const double *__restrict__ u, double *__restrict__ p, double eps_inv,
+                    double *__restrict__ partials) {
+    double acc[MAXV];
+#pragma unroll
+    for (int i = 0; i < MAXV; ++i) acc[i] = 0.0;
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        double du = 0.0;
+        for (int f = 0; f < 3; ++f) {
+            int j = cell_int[3 * c + f];
+            if (j >= 0) du += cell_d[3 * c + f] * u[(size_t)j * dpf];
+        }
+        double a = area[c];
+        double dp = eps_inv * du / a;
+        double pn = p[c] - dp;
+        p[c] = pn;
+        acc[0] += a * dp * dp;
+        acc[1] += a * pn * pn;
+        acc[2] += du * du;
+    }
+    block_reduce_store(acc, 3, partials);
+}
+
+template <class T>
+cudaError_t apply_dispatch(const DevLevel &L, int dpf, const T *A, const T *x, const T *g, T *y,
+                           cudaStream_t s) {
+    int64_t n = L.n_int * dpf;
+    if (n == 0) return cudaSuccess;
+    unsigned nb = blocks_for(n, 256);
+    switch (dpf) {
+    case 2: note_launches(1); apply_kernel<T, 2><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
+    case 4: note_launches(1); apply_kernel<T, 4><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
+    case 6: note_launches(1); apply_kernel<T, 6><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
+    case 8: note_launches(1); apply_kernel<T, 8><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
+    case 10: note_launches(1); apply_kernel<T, 10><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <class T, int DPF>
+cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, const T *Pinv, int colour,
+                      const T *g, T *u, cudaStream_t s) {
+    int p0 = L.colour_ptr[colour], p1 = L.colour_ptr[colour + 1];
+    if (p1 <= p0) return cudaSuccess;
+    int nt = ((op.np_max + 31) / 32) * 32;
+    if (nt > 256) nt = 256;
+    if (nt < 32) nt = 32;
+    size_t smem = sizeof(T) * ((size_t)L.pc_max * 3 * DPF + op.np_max);
+    note_launches(1);
+    gs_kernel<T, DPF><<<p1 - p0, nt, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
+                                                L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
+                                                L.patch_slot_src.p, L.cell_int.p, A, Pinv, g, u);
+    return cudaGetLastError();
+}
+
+} // namespace
+
+template <class T>
+cudaError_t launch_apply(const DevLevel &L, const DevOperator &op, const T *A, const T *x, const T *g,
+                         T *y, cudaStream_t s) {
+    return apply_dispatch<T>(L, op.dpf, A, x, g, y, s);
+}
+
+template <class T>
+cudaError_t launch_gs_colour(const DevLevel &L, const DevOperator &op, const T *A, const T *Pinv,
+                             int colour, const T *g, T *u, cudaStream_t s) {
+    switch (op.dpf) {
+    case 2: return gs_launch<T, 2>(L, op, A, Pinv, colour, g, u, s);
+    case 4: return gs_launch<T, 4>(L, op, A, Pinv, colour, g, u, s);
+    case 6: return gs_launch<T, 6>(L, op, A, Pinv, colour, g, u, s);
+    case 8: return gs_launch<T, 8>(L, op, A, Pinv, colour, g, u, s);
+    case 10: return gs_launch<T, 10>(L, op, A, Pinv, colour, g, u, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <class T>
+cudaError_t launch_prolong_add(const DevLevel &F, const DevLevel &C, const T *W, const T *Hm, const T *uc,
+                               T *tmp, T *uf, cudaStream_t s) {
+    if (F.nB > 0)
+        note_launches(1);
+        prolong_B_kernel<T><<<blocks_for(F.nB, 128), 128, 0, s>>>(F.nB, F.tr_fineB.p, F.tr_fineB_src.p,
+                                                                 C.cell_int.p, W, uc, tmp, uf);
+    if (F.nc_coarse > 0)
+        note_launches(1);
+        prolong_T_kernel<T><<<blocks_for(F.nc_coarse, 128), 128, 0, s>>>(F.nc_coarse, F.tr_slots.p, Hm,
+                                                                         tmp, uf);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_restrict(const DevLevel &F, const DevLevel &C, const T *W, const T *Hm, const T *rf,
+                            T *t1, T *t2, T *rc, cudaStream_t s) {
+    if (F.nc_coarse > 0) {
+        note_launches(1);
+        restrict_T_kernel<T><<<blocks_for(F.nc_coarse, 128), 128, 0, s>>>(F.nc_coarse, F.tr_slots.p, Hm,
+                                                                          rf, t1);
+        note_launches(1);
+        restrict_B_kernel<T><<<blocks_for(F.nc_coarse, 128), 128, 0, s>>>(F.nc_coarse, F.tr_slots.p,
+                                                                          F.tr_nbr.p, W, rf, t1, t2);
+    }
+    if (C.n_int > 0)
+        note_launches(1);
+        restrict_C_kernel<T><<<blocks_for(C.n_int, 128), 128, 0, s>>>(C.n_int, C.facet_adj.p, t2, rc);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_hp_restrict(int k, int64_t n_int, const T *r, T *r0, cudaStream_t s) {
+    if (n_int == 0) return cudaSuccess;
+    note_launches(1);
+    hp_restrict_kernel<T><<<blocks_for(n_int, 256), 256, 0, s>>>(k, n_int, r, r0);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_hp_prolong_add(int k, int64_t n_int, const T *d0, T *u, cudaStream_t s) {
+    if (n_int == 0) return cudaSuccess;
+    note_launches(1);
+    hp_prolong_kernel<T><<<blocks_for(n_int, 256), 256, 0, s>>>(k, n_int, d0, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_apply(const double *inv, int64_t n, const double *g, double *u, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    coarse_apply_kernel<<<blocks_for(n * 32, 256), 256, 0, s>>>(inv, n, g, u);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_d2f(const double *x, float *y, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    d2f_kernel<<<blocks_for(n, 256), 256, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_f2d(const float *x, double *y, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    f2d_kernel<<<blocks_for(n, 256), 256, 0, s>>>(x, y, n);
+    return cudaGetLastError();
+}
+template <class T>
+cudaError_t launch_fill(T *x, T v, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    fill_kernel<T><<<blocks_for(n, 256), 256, 0, s>>>(x, v, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_axpby(double a, const double *x, double b, double *y, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    axpby_kernel<<<blocks_for(n, 256), 256, 0, s>>>(a, x, b, y, n);
+    return cudaGetLastError();
+}
+
+int krylov_partial_blocks() { return KRYLOV_BLOCKS; }
+
+cudaError_t launch_dots(const double *V, int nv, int64_t ld, const double *w, int64_t n, double *partials,
+                        cudaStream_t s) {
+    if (nv > MAXV) return cudaErrorInvalidValue;
+    note_launches(1);
+    dots_kernel<<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(V, nv, ld, w, n, partials);
+    return cudaGetLastError();
+}
+cudaError_t launch_update_dots(const double *V, int nv, int64_t ld, double *w, int64_t n, const double *h,
+                               double *partials, int mode, cudaStream_t s) {
+    if (nv > MAXV) return cudaErrorInvalidValue;
+    note_launches(1);
+    update_dots_kernel<<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(V, nv, ld, w, n, h, partials, mode);
+    return cudaGetLastError();
+}
+cudaError_t launch_reduce_partials(const double *partials, int nv, double *out, int accumulate,
+                                   cudaStream_t s) {
+    note_launches(1);
+    reduce_partials_kernel<<<nv, 32, 0, s>>>(partials, nv, KRYLOV_BLOCKS, out, accumulate);
+    return cudaGetLastError();
+}
+cudaError_t launch_givens(double *small, int j, int restart, double *, cudaStream_t s) {
+    note_launches(1);
+    givens_kernel<<<1, 1, 0, s>>>(small, j, restart);
+    return cudaGetLastError();
+}
+cudaError_t launch_scale_next(const double *w, double *v, int64_t n, const double *small, int,
+                              int restart, cudaStream_t s) {
+    SmallLayout Ly{restart};
+    note_launches(1);
+    scale_next_kernel<<<blocks_for(n, 256), 256, 0, s>>>(w, v, n, small, Ly.hn());
+    return cudaGetLastError();
+}
+cudaError_t launch_init_cycle(const double *r, double *v0, int64_t n, double *small, int restart,
+                              cudaStream_t s) {
+    int64_t m = n > restart + 1 ? n : restart + 1;
+    note_launches(1);
+    init_cycle_kernel<<<blocks_for(m, 256), 256, 0, s>>>(r, v0, n, small, restart);
+    return cudaGetLastError();
+}
+cudaError_t launch_solve_update(double *small, int m, int restart, const double *Z, int64_t ld, double *x,
+                                int64_t n, cudaStream_t s) {
+    SmallLayout Ly{restart};
+    note_launches(1);
+    backsolve_kernel<<<1, 1, 0, s>>>(small, m, restart);
+    note_launches(1);
+    update_x_kernel<<<blocks_for(n, 256), 256, 0, s>>>(Z, m, ld, small, Ly.y(), x, n);
+    return cudaGetLastError();
+}
+cudaError_t launch_uzawa_rhs(const DevLevel &L, int k, const double *F, const double *p, double *g,
+                             cudaStream_t s) {
+    int dpf = 2 * (k + 1);
+    int64_t n = L.n_int * dpf;
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    uzawa_rhs_kernel<<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, dpf, L.facet_adj.p, L.cell_d.p, F, p, g);
+    return cudaGetLastError();
+}
+cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p, double eps_inv,
+                                double *partials, cudaStream_t s) {
+    note_launches(1);
+    uzawa_update_kernel<<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(L.nc, 2 * (k + 1), L.cell_int.p, L.cell_d.p,
+                                                                 L.cell_area.p, u, p, eps_inv, partials);
+    return cudaGetLastError();
+}
+
+// explicit instantiations
+template cudaError_t launch_apply<double>(const DevLevel &, const DevOperator &, const double *,
+                                          const double *, const double *, double *, cudaStream_t);
+template cudaError_t launch_apply<float>(const DevLevel &, const DevOperator &, const float *, const float *,
+                                         const float *, float *, cudaStream_t);
+template cudaError_t launch_gs_colour<double>(const DevLevel &, const DevOperator &, const double *,
+                                              const double *, int, const double *, double *, cudaStream_t);
+template cudaError_t launch_gs_colour<float>(const DevLevel &, const DevOperator &, const float *,
+                                             const float *, int, const float *, float *, cudaStream_t);
+template cudaError_t launch_prolong_add<double>(const DevLevel &, const DevLevel &, const double *,
+                                                const double *, const double *, double *, double *,
+                                                cudaStream_t);
+template cudaError_t launch_prolong_add<float>(const DevLevel &, const DevLevel &, const float *,
+                                               const float *, const float *, float *, float *, cudaStream_t);
+template cudaError_t launch_restrict<double>(const DevLevel &, const DevLevel &, const double *,
+                                             const double *, const double *, double *, double *, double *,
+                                             cudaStream_t);
+template cudaError_t launch_restrict<float>(const DevLevel &, const DevLevel &, const float *, const float *,
+                                            const float *, float *, float *, float *, cudaStream_t);
+template cudaError_t launch_hp_restrict<double>(int, int64_t, const double *, double *, cudaStream_t);
+template cudaError_t launch_hp_restrict<float>(int, int64_t, const float *, float *, cudaStream_t);
+template cudaError_t launch_hp_prolong_add<double>(int, int64_t, const double *, double *, cudaStream_t);
+template cudaError_t launch_hp_prolong_add<float>(int, int64_t, const float *, float *, cudaStream_t);
+template cudaError_t launch_fill<double>(double *, double, int64_t, cudaStream_t);
+template cudaError_t launch_fill<float>(float *, float, int64_t, cudaStream_t);
+
+} // namespace hdg
