@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--nu", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="condense, then one warm-up and one timed mixed-precision solve only "
+                         "(the command profiled for the kernel launch list)")
     return ap.parse_args()
 
 
@@ -429,8 +432,27 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes):
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
 
 
+def profile_solve(args):
+    import torch
+    import paper_2303_06762_gb300 as hdg
+    ms, fv = workload(args)
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma,
+                     precision=hdg.HDG_MIXED_FP32)
+    F = hdg.hdg_condense(ctx, prm, torch.tensor(fv, device="cuda:0"))
+    for _ in range(max(args.warmup, 0) + 1):
+        u, p, info = hdg.hdg_solve(ctx, F)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve": True, "N": args.N, "k": args.k, "launches": hdg.hdg_kernel_launches(),
+                      "info": info}))
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.profile_solve:
+        profile_solve(args)
+        return
     if args.impl == "reference":
         reference_arm(args)
         return

@@ -156,7 +156,8 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
  * every level, in FP64 on the device; then the patch inverses of the block
  * smoothers (eq. bjac, Sections 3.4.2, 3.5), the harmonic-extension blocks of
  * the transfer (eqs. div-transfer, harmonic-ex) and the dense inverse of the
- * coarsest operator.  forcing: device [n_cells][n_lat][2] (layout above) or
+ * coarsest operator (at most 16384 coarsest unknowns, else
+ * HDG_ERR_INVALID_ARG).  forcing: device [n_cells][n_lat][2] (layout above) or
  * NULL; rhs_out: device [n_dof] condensed load F, or NULL.  May be called
  * again with new parameters or forcing.  Returns HDG_ERR_SINGULAR if a
  * factorisation meets a non-positive pivot. */

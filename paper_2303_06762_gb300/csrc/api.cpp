@@ -523,6 +523,10 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
         REQUIRE(prm->cycle == 1 || prm->cycle == 2, "cycle must be 1 (V) or 2 (W)");
         REQUIRE(prm->vcycle_growth >= 1 && prm->vcycle_growth <= 4, "vcycle_growth out of range 1..4");
         REQUIRE(prm->precision == HDG_FP64 || prm->precision == HDG_MIXED_FP32, "unknown precision");
+        REQUIRE(2 * ctx->L[0].n_int <= MAX_COARSE_DOFS,
+                "coarsest level has " + std::to_string(2 * ctx->L[0].n_int) +
+                " unknowns; the dense coarse solve allows at most " + std::to_string(MAX_COARSE_DOFS) +
+                " (add coarser levels)");
         CK(cudaSetDevice(ctx->device));
         cudaStream_t s = (cudaStream_t)stream;
         ctx->condensed = false;

@@ -19,6 +19,7 @@ namespace hdg {
 constexpr int MAX_K = 4;
 constexpr int MAX_LEVELS = 16;
 constexpr int MAX_RESTART = 64;
+constexpr int64_t MAX_COARSE_DOFS = 16384;   // dense inverse of the coarsest level: <= 2 GB
 
 // ---------------------------------------------------------------- host data
 struct HostLevel {
