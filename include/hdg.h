@@ -222,6 +222,27 @@ hdg_status hdg_coarse_solve(hdg_ctx *ctx, const double *g, double *u, hdg_stream
  * the finest level L. */
 hdg_status hdg_mg_h(hdg_ctx *ctx, const double *g, double *u, hdg_stream_t stream);
 
+/* Capacity, in coarse cells, of the fixed scratch array of hdg_restrict_noalloc. */
+#define HDG_NOALLOC_MAX_COARSE_CELLS 32768
+
+/* rc = (I_{l-1}^l)^T rf, exactly like hdg_restrict, for callers that cannot
+ * allocate device memory when they call (for example code whose device memory
+ * is owned by another allocator, or that must not grow its footprint after
+ * set-up): the call allocates nothing and uses none of the context's work
+ * buffers.  Its temporaries live in one array of HDG_NOALLOC_MAX_COARSE_CELLS
+ * x 18 doubles (4.7 MB) compiled into the library, which every GPU that loads
+ * the library holds until the process exits.  The paper has no counterpart.
+ *   - The first call on a device (made with that device current) looks up the
+ *     array's device address; make that first call before any stream capture.
+ *   - Levels whose coarse mesh has more than HDG_NOALLOC_MAX_COARSE_CELLS cells
+ *     are rejected with HDG_ERR_INVALID_ARG.
+ *   - All calls share the one array: calls that overlap on the GPU (other
+ *     streams, other host threads, other contexts) race and must be ordered
+ *     by the caller.  The array keeps the last call's contents; every call
+ *     overwrites what it reads, so nothing needs clearing.
+ * Arguments as hdg_restrict (rf, rc device FP64, level >= 1). */
+hdg_status hdg_restrict_noalloc(hdg_ctx *ctx, int level, const double *rf, double *rc, hdg_stream_t stream);
+
 /* Host-side reference-element integrals that hdg_condense contracts with each
  * cell's Jacobian to form the local system of eq. stWeak (Section 3.2) for
  * order k: the blocks R1..R6 packed in that order (layouts in the library

@@ -38,7 +38,7 @@ EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense",
            "hdg_apply", "hdg_precond_apply", "hdg_solve", "hdg_get_sizes",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
-           "hdg_reference_tables", "hdg_destroy",
+           "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_destroy",
            "hdg_status_string", "hdg_last_error")
 
 
@@ -135,6 +135,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "hdg_smooth": (I, [P, I, P, P, I, I, P]),
         "hdg_prolong_add": (I, [P, I, P, P, P]),
         "hdg_restrict": (I, [P, I, P, P, P]),
+        "hdg_restrict_noalloc": (I, [P, I, P, P, P]),
         "hdg_coarse_solve": (I, [P, P, P, P]),
         "hdg_mg_h": (I, [P, P, P, P]),
         "hdg_kernel_launches": (ctypes.c_uint64, []),
@@ -330,6 +331,13 @@ def hdg_restrict(ctx: Context, level: int, rf, rc=None, stream=None):
     if rc is None:
         rc = torch.empty(int(ctx.sizes().n_dof_level[level - 1]), dtype=torch.float64, device=rf.device)
     ctx.check(load_library().hdg_restrict(ctx.handle, level, _ptr(rf), _ptr(rc), _stream(stream)))
+    return rc
+
+
+def hdg_restrict_noalloc(ctx: Context, level: int, rf, rc, stream=None):
+    """hdg_restrict with its temporaries in the library's fixed scratch array (no allocation)."""
+    ctx.check(load_library().hdg_restrict_noalloc(ctx.handle, level, _ptr(rf), _ptr(rc),
+                                                  _stream(stream)))
     return rc
 
 
