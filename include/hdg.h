@@ -106,6 +106,8 @@ typedef struct {
     int cycle;               /* q of Algorithm 1: 1 = variable V, 2 = W            */
     int vcycle_growth;       /* m(l-1) = growth * m(l) for q = 1 (2 = doubling)    */
     hdg_precision precision; /* precision of the preconditioner                    */
+    int fused_coarse_cells;  /* run MG_h on the coarsest levels with at most this  */
+                             /* many cells in one thread block (0 = off; <= 2048)  */
 } hdg_params;
 
 typedef struct {

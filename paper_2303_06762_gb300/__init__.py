@@ -61,7 +61,8 @@ class _MeshDesc(ctypes.Structure):
 class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nu", ctypes.c_double), ("beta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("m_p", ctypes.c_int), ("m_h", ctypes.c_int),
-                ("cycle", ctypes.c_int), ("vcycle_growth", ctypes.c_int), ("precision", ctypes.c_int)]
+                ("cycle", ctypes.c_int), ("vcycle_growth", ctypes.c_int), ("precision", ctypes.c_int),
+                ("fused_coarse_cells", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -100,10 +101,11 @@ class Params:
     cycle: int = 1
     vcycle_growth: int = 2
     precision: int = HDG_FP64
+    fused_coarse_cells: int = 0
 
     def to_c(self) -> _Params:
         return _Params(self.k, self.nu, self.beta, self.gamma, self.m_p, self.m_h, self.cycle,
-                       self.vcycle_growth, self.precision)
+                       self.vcycle_growth, self.precision, self.fused_coarse_cells)
 
 
 _lib = None

@@ -171,9 +171,82 @@ void coarse_solve(hdg_ctx *ctx, cudaStream_t s) {
     }
 }
 
+template <class T>
+SmallParams<T> &small_of(hdg_ctx *ctx);
+template <>
+SmallParams<double> &small_of<double>(hdg_ctx *ctx) { return ctx->small_d; }
+template <>
+SmallParams<float> &small_of<float>(hdg_ctx *ctx) { return ctx->small_f; }
+
+template <class T>
+size_t fill_small(hdg_ctx *ctx, int Ls) {
+    SmallParams<T> &S = small_of<T>(ctx);
+    S = SmallParams<T>();
+    S.inv = ctx->coarse_inv.p;
+    S.g0d = ctx->L[0].g.p;
+    S.q = ctx->prm.cycle;
+    S.growth = ctx->prm.vcycle_growth;
+    size_t smem = 0;
+    for (int l = 0; l <= Ls; ++l) {
+        DevLevel &L = ctx->L[l];
+        SmallLevel<T> &V = S.lv[l];
+        V.n_int = (int)L.n_int;
+        V.n_colours = L.n_colours;
+        V.pf_max = L.pf_max;
+        V.pc_max = L.pc_max;
+        V.np_max = L.op0.np_max;
+        for (int c = 0; c <= L.n_colours; ++c) V.colour_ptr[c] = L.colour_ptr[c];
+        V.cell_int = L.cell_int.p;
+        V.facet_adj = L.facet_adj.p;
+        V.patch_nf = L.patch_nf.p;
+        V.patch_facets = L.patch_facets.p;
+        V.patch_cells = L.patch_cells.p;
+        V.slot_src = L.patch_slot_src.p;
+        V.A = Prec<T>::A(L.op0);
+        V.Pinv = Prec<T>::P(L.op0);
+        V.g = Prec<T>::g(L);
+        V.u = Prec<T>::u(L);
+        V.r = Prec<T>::r(L);
+        V.t = Prec<T>::t(L);
+        if (l > 0) {
+            V.ncc = (int)L.nc_coarse;
+            V.nB = (int)L.nB;
+            V.tr_slots = L.tr_slots.p;
+            V.tr_nbr = L.tr_nbr.p;
+            V.tr_fineB = L.tr_fineB.p;
+            V.tr_fineB_src = L.tr_fineB_src.p;
+            V.W = Prec<T>::W(L);
+            V.H = Prec<T>::H(L);
+            V.ct1 = Prec<T>::c1(L);
+            V.ct2 = Prec<T>::c2(L);
+            for (int c = 0; c < L.n_colours; ++c)
+                smem = std::max(smem, (size_t)(L.colour_ptr[c + 1] - L.colour_ptr[c]) * L.op0.np_max * sizeof(T));
+        }
+    }
+    return std::max<size_t>(smem, 16);
+}
+
+// largest level Ls >= 1 whose levels 0..Ls all fit the single-block kernel, else -1
+int small_levels(hdg_ctx *ctx) {
+    int Ls = -1;
+    for (int l = 0; l < std::min(ctx->n_levels, SMALL_MAX_LEVELS); ++l) {
+        const DevLevel &L = ctx->L[l];
+        if (L.nc > ctx->prm.fused_coarse_cells || L.nc > SMALL_MAX_CELLS ||
+            L.n_colours > SMALL_MAX_COLOURS)
+            break;
+        Ls = l;
+    }
+    return Ls >= 1 ? Ls : -1;
+}
+
 // u_l = MG_h(l, g_l, u_l (zero_init ? 0 : as is), m, q)
 template <class T>
 void mg_h(hdg_ctx *ctx, int l, int m, bool zero_init, cudaStream_t s) {
+    if (l >= 1 && l <= ctx->small_Ls) {
+        const size_t smem = std::is_same<T, double>::value ? ctx->small_smem_d : ctx->small_smem_f;
+        CK(launch_mg_small<T>(small_of<T>(ctx), l, m, zero_init, smem, s));
+        return;
+    }
     if (l == 0) {
         coarse_solve<T>(ctx, s);
         return;
@@ -218,7 +291,7 @@ void mg_hp_impl(hdg_ctx *ctx, const T *r, T *z, cudaStream_t s) {
     for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, true, s);
 }
 
-void precond(hdg_ctx *ctx, const double *r, double *z, cudaStream_t s) {
+void precond_direct(hdg_ctx *ctx, const double *r, double *z, cudaStream_t s) {
     if (ctx->prm.precision == HDG_FP64) {
         mg_hp_impl<double>(ctx, r, z, s);
     } else {
@@ -226,6 +299,61 @@ void precond(hdg_ctx *ctx, const double *r, double *z, cudaStream_t s) {
         mg_hp_impl<float>(ctx, ctx->kgf.p, ctx->kuf.p, s);
         CK(launch_f2d(ctx->kuf.p, z, ctx->n_dof, s));
     }
+}
+
+void drop_graph(hdg_ctx *ctx) {
+    if (ctx->pc_exec) cudaGraphExecDestroy(ctx->pc_exec);
+    ctx->pc_exec = nullptr;
+    ctx->pc_prec = -1;
+    ctx->pc_kernels = 0;
+}
+
+// z = MG_hp(r): replays a CUDA graph of the whole preconditioner (several hundred
+// small launches per application on deep hierarchies) captured once per
+// condensation, with fixed staging buffers; direct launches when the caller's
+// stream is itself being captured.
+void precond(hdg_ctx *ctx, const double *r, double *z, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+        precond_direct(ctx, r, z, s);
+        return;
+    }
+    const size_t bytes = sizeof(double) * ctx->n_dof;
+    if (!ctx->pc_exec || ctx->pc_prec != (int)ctx->prm.precision) {
+        drop_graph(ctx);
+        dalloc(ctx, ctx->pc_in, ctx->n_dof);
+        dalloc(ctx, ctx->pc_out, ctx->n_dof);
+        if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        // the capture stream starts after everything already queued on s
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, s));
+        CK(cudaStreamWaitEvent(ctx->cap_stream, ev, 0));
+        CK(cudaEventDestroy(ev));
+        cudaStream_t cs2 = ctx->cap_stream;
+        const unsigned long long l0 = launch_count();
+        CK(cudaStreamBeginCapture(cs2, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t g = nullptr;
+        try {
+            precond_direct(ctx, ctx->pc_in.p, ctx->pc_out.p, cs2);
+        } catch (...) {
+            cudaStreamEndCapture(cs2, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        CK(cudaStreamEndCapture(cs2, &g));
+        cudaError_t e = cudaGraphInstantiate(&ctx->pc_exec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        ctx->pc_kernels = (long long)(launch_count() - l0);
+        note_launches(-ctx->pc_kernels);          // captured, not executed
+        ctx->pc_prec = (int)ctx->prm.precision;
+    }
+    CK(cudaMemcpyAsync(ctx->pc_in.p, r, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaGraphLaunch(ctx->pc_exec, s));
+    note_launches(ctx->pc_kernels);
+    CK(cudaMemcpyAsync(z, ctx->pc_out.p, bytes, cudaMemcpyDeviceToDevice, s));
 }
 
 void apply_k(hdg_ctx *ctx, const double *x, const double *g, double *y, cudaStream_t s) {
@@ -478,6 +606,9 @@ void hdg_destroy(hdg_ctx *ctx) {
     dfree(ctx->coarse_inv); dfree(ctx->status_flag);
     dfree(ctx->V); dfree(ctx->Z); dfree(ctx->w); dfree(ctx->partials); dfree(ctx->small);
     dfree(ctx->uz_partials);
+    drop_graph(ctx);
+    dfree(ctx->pc_in); dfree(ctx->pc_out);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     delete ctx;
 }
@@ -523,6 +654,7 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
         REQUIRE(prm->cycle == 1 || prm->cycle == 2, "cycle must be 1 (V) or 2 (W)");
         REQUIRE(prm->vcycle_growth >= 1 && prm->vcycle_growth <= 4, "vcycle_growth out of range 1..4");
         REQUIRE(prm->precision == HDG_FP64 || prm->precision == HDG_MIXED_FP32, "unknown precision");
+        REQUIRE(prm->fused_coarse_cells >= 0, "fused_coarse_cells must be >= 0");
         REQUIRE(2 * ctx->L[0].n_int <= MAX_COARSE_DOFS,
                 "coarsest level has " + std::to_string(2 * ctx->L[0].n_int) +
                 " unknowns; the dense coarse solve allows at most " + std::to_string(MAX_COARSE_DOFS) +
@@ -530,6 +662,7 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
         CK(cudaSetDevice(ctx->device));
         cudaStream_t s = (cudaStream_t)stream;
         ctx->condensed = false;
+        drop_graph(ctx);
         ctx->prm = *prm;
         const int k = prm->k;
         const double eps_inv = prm->gamma * prm->nu;
@@ -564,6 +697,12 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
         ctx->n0 = 2 * ctx->L[0].n_int;
         dalloc(ctx, ctx->coarse_inv, std::max<int64_t>(ctx->n0 * ctx->n0, 1));
         CK(launch_coarse_inverse(ctx->L[0], ctx->coarse_inv.p, ctx->n0, ctx->status_flag.p, s));
+        ctx->small_Ls = small_levels(ctx);
+        if (ctx->small_Ls >= 1) {
+            ctx->small_smem_d = fill_small<double>(ctx, ctx->small_Ls);
+            ctx->small_smem_f = fill_small<float>(ctx, ctx->small_Ls);
+            if (ctx->small_smem_d > 200 * 1024) ctx->small_Ls = -1;
+        }
         ctx->n_dof = LJ.n_int * op.dpf;
         const int64_t nd = std::max<int64_t>(ctx->n_dof, 1);
         dalloc(ctx, ctx->kr, nd); dalloc(ctx, ctx->ku, nd); dalloc(ctx, ctx->kt, nd);

@@ -84,6 +84,33 @@ struct SmallLayout {
 };
 
 
+// views of the smallest lowest-order levels for the single-block MG kernel (mg_small.cu)
+constexpr int SMALL_MAX_LEVELS = 6;
+constexpr int SMALL_MAX_COLOURS = 15;
+constexpr int64_t SMALL_MAX_CELLS = 2048;
+
+template <class T>
+struct SmallLevel {
+    int n_int = 0, n_colours = 0, pf_max = 0, pc_max = 0, np_max = 0;
+    int colour_ptr[SMALL_MAX_COLOURS + 1] = {};
+    const int *cell_int = nullptr, *facet_adj = nullptr, *patch_nf = nullptr, *patch_facets = nullptr,
+              *patch_cells = nullptr, *slot_src = nullptr;
+    const T *A = nullptr, *Pinv = nullptr;
+    T *g = nullptr, *u = nullptr, *r = nullptr, *t = nullptr;
+    int ncc = 0, nB = 0;
+    const int *tr_slots = nullptr, *tr_nbr = nullptr, *tr_fineB = nullptr, *tr_fineB_src = nullptr;
+    const T *W = nullptr, *H = nullptr;
+    T *ct1 = nullptr, *ct2 = nullptr;
+};
+
+template <class T>
+struct SmallParams {
+    SmallLevel<T> lv[SMALL_MAX_LEVELS];
+    const double *inv = nullptr;   // dense inverse of the coarsest operator (FP64)
+    double *g0d = nullptr;         // FP64 staging of the coarsest right-hand side
+    int q = 1, growth = 2;
+};
+
 // ---------------------------------------------------------------- device data
 template <class T>
 struct DBuf {
@@ -152,12 +179,23 @@ struct hdg_ctx {
     hdg::DBuf<double> V, Z, w, partials, small;   // small: Hessenberg, rotations, g, y
     hdg::DBuf<double> uz_partials;
     double *h_pinned = nullptr;              // host pinned scalars
+    // CUDA graph of one preconditioner application (fixed staging buffers)
+    cudaGraphExec_t pc_exec = nullptr;
+    cudaStream_t cap_stream = nullptr;       // private stream used only for graph capture
+    int pc_prec = -1;
+    long long pc_kernels = 0;
+    hdg::DBuf<double> pc_in, pc_out;
+    // fused MG_h on levels 0..small_Ls (one thread block), -1 when not used
+    int small_Ls = -1;
+    size_t small_smem_d = 0, small_smem_f = 0;
+    hdg::SmallParams<double> small_d;
+    hdg::SmallParams<float> small_f;
 };
 
 namespace hdg {
 
 // kernel-launch counter (ops.cu): every launcher adds the kernels it enqueues
-void note_launches(int n);
+void note_launches(long long n);
 unsigned long long launch_count();
 
 // reference.cpp
@@ -198,6 +236,9 @@ template <class T>
 cudaError_t launch_hp_prolong_add(int k, int64_t n_int, const T *d0, T *u, cudaStream_t s);
 cudaError_t launch_coarse_apply(const double *inv, int64_t n, const double *g, double *u,
                                 cudaStream_t s);
+template <class T>
+cudaError_t launch_mg_small(const SmallParams<T> &S, int l, int m, bool zero_init, size_t smem_bytes,
+                            cudaStream_t s);
 cudaError_t launch_d2f(const double *x, float *y, int64_t n, cudaStream_t s);
 cudaError_t launch_f2d(const float *x, double *y, int64_t n, cudaStream_t s);
 template <class T>

@@ -31,7 +31,7 @@
 namespace hdg {
 
 static std::atomic<unsigned long long> g_launches{0};
-void note_launches(int n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+void note_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
@@ -111,10 +111,19 @@ __global__ void gs_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
     __syncthreads();
     const T *Pi = Pinv + (size_t)p * np_max * np_max;
     for (int t = tid; t < np; t += nt) {
-        T acc = 0;
-        for (int j = 0; j < np; ++j) acc += Pi[(size_t)j * np_max + t] * r[j];
+        // four partial sums keep several independent loads in flight per thread
+        T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int j = 0;
+#pragma unroll 2
+        for (; j + 4 <= np; j += 4) {
+            a0 += Pi[(size_t)(j + 0) * np_max + t] * r[j + 0];
+            a1 += Pi[(size_t)(j + 1) * np_max + t] * r[j + 1];
+            a2 += Pi[(size_t)(j + 2) * np_max + t] * r[j + 2];
+            a3 += Pi[(size_t)(j + 3) * np_max + t] * r[j + 3];
+        }
+        for (; j < np; ++j) a0 += Pi[(size_t)j * np_max + t] * r[j];
         int F = patch_facets[(size_t)p * pf_max + t / DPF];
-        u[(size_t)F * DPF + t % DPF] += acc;
+        u[(size_t)F * DPF + t % DPF] += (a0 + a1) + (a2 + a3);
     }
 }
 
@@ -277,12 +286,14 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// block-reduce acc[0..nv) and write partials[i*gridDim.x + block]
-__device__ void block_reduce_store(double *acc, int nv, double *partials) {
-    __shared__ double red[KRYLOV_THREADS / 32][MAXV];
+// block-reduce acc[0..nv) (warp shuffles, then one shared-memory pass) and
+// write partials[i*gridDim.x + block]
+template <int NVB>
+__device__ void block_reduce_store(const double *acc, int nv, double *partials) {
+    __shared__ double red[KRYLOV_THREADS / 32][NVB];
     int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < MAXV; ++i) {
+    for (int i = 0; i < NVB; ++i) {
         if (i < nv) {
             double v = warp_sum(acc[i]);
             if (lane == 0) red[wid][i] = v;
@@ -296,53 +307,62 @@ __device__ void block_reduce_store(double *acc, int nv, double *partials) {
     }
 }
 
-// partials of h_i = <V_i, w>
+// partials of h_i = <V_i, w> for the vectors i0 = 16*blockIdx.y .. i0+nvb-1 (nvb <= NVB <= 16);
+// one register accumulator per vector, w read once per chunk of vectors
+template <int NVB>
 __global__ void __launch_bounds__(KRYLOV_THREADS)
 dots_kernel(const double *__restrict__ V, int nv, int64_t ld, const double *__restrict__ w, int64_t n,
             double *__restrict__ partials) {
-    double acc[MAXV];
+    const int i0 = 16 * blockIdx.y;
+    const int nvb = min(nv - i0, NVB);
+    const double *Vb = V + (size_t)i0 * ld;
+    double acc[NVB];
 #pragma unroll
-    for (int i = 0; i < MAXV; ++i) acc[i] = 0.0;
+    for (int i = 0; i < NVB; ++i) acc[i] = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        double we = w[e];
+        const double we = w[e];
 #pragma unroll
-        for (int i = 0; i < MAXV; ++i)
-            if (i < nv) acc[i] += V[(size_t)i * ld + e] * we;
+        for (int i = 0; i < NVB; ++i)
+            if (i < nvb) acc[i] = fma(Vb[(size_t)i * ld + e], we, acc[i]);
     }
-    block_reduce_store(acc, nv, partials);
+    block_reduce_store<NVB>(acc, nvb, partials + (size_t)i0 * gridDim.x);
 }
 
-// w -= Σ_i h_i V_i, then (mode 1) partials of <V_i, w> or (mode 2) of <w, w>
+// w -= Σ_{i<nv} h_i V_i; MODE 1: also partials of <V_i, w_new> (nv <= NVB <= 8, the second
+// read of V_i(e) hits L1); MODE 2: partials of <w_new, w_new>; MODE 0: update only
+template <int NVB, int MODE>
 __global__ void __launch_bounds__(KRYLOV_THREADS)
 update_dots_kernel(const double *__restrict__ V, int nv, int64_t ld, double *__restrict__ w, int64_t n,
-                   const double *__restrict__ h, double *__restrict__ partials, int mode) {
+                   const double *__restrict__ h, double *__restrict__ partials) {
     __shared__ double hs[MAXV];
     for (int i = threadIdx.x; i < nv; i += blockDim.x) hs[i] = h[i];
     __syncthreads();
-    double acc[MAXV];
+    constexpr int NA = MODE == 1 ? NVB : 1;
+    double acc[NA];
 #pragma unroll
-    for (int i = 0; i < MAXV; ++i) acc[i] = 0.0;
+    for (int i = 0; i < NA; ++i) acc[i] = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
-        double v[MAXV];
         double we = w[e];
+        if (MODE == 1) {
 #pragma unroll
-        for (int i = 0; i < MAXV; ++i)
-            if (i < nv) {
-                v[i] = V[(size_t)i * ld + e];
-                we -= hs[i] * v[i];
-            }
-        w[e] = we;
-        if (mode == 1) {
-#pragma unroll
-            for (int i = 0; i < MAXV; ++i)
-                if (i < nv) acc[i] += v[i] * we;
+            for (int i = 0; i < NVB; ++i)
+                if (i < nv) we = fma(-hs[i], V[(size_t)i * ld + e], we);
         } else {
-            acc[0] += we * we;
+#pragma unroll 4
+            for (int i = 0; i < nv; ++i) we = fma(-hs[i], V[(size_t)i * ld + e], we);
+        }
+        w[e] = we;
+        if (MODE == 1) {
+#pragma unroll
+            for (int i = 0; i < NVB; ++i)
+                if (i < nv) acc[i] = fma(V[(size_t)i * ld + e], we, acc[i]);
+        } else if (MODE == 2) {
+            acc[0] = fma(we, we, acc[0]);
         }
     }
-    block_reduce_store(acc, mode == 1 ? nv : 1, partials);
+    if (MODE != 0) block_reduce_store<NA>(acc, MODE == 1 ? nv : 1, partials);
 }
 
 __global__ void reduce_partials_kernel(const double *__restrict__ partials, int nv, int nb,
@@ -440,9 +460,7 @@ uzawa_update_kernel(int64_t nc, int dpf, const int *__restrict__ cell_int,
                     const double *__restrict__ cell_d, const double *__restrict__ area,
                     const double *__restrict__ u, double *__restrict__ p, double eps_inv,
                     double *__restrict__ partials) {
-    double acc[MAXV];
-#pragma unroll
-    for (int i = 0; i < MAXV; ++i) acc[i] = 0.0;
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
          c += (int64_t)gridDim.x * blockDim.x) {
         double du = 0.0;
@@ -458,7 +476,7 @@ uzawa_update_kernel(int64_t nc, int dpf, const int *__restrict__ cell_int,
         acc[1] += a * pn * pn;
         acc[2] += du * du;
     }
-    block_reduce_store(acc, 3, partials);
+    block_reduce_store<4>(acc, 3, partials);
 }
 
 template <class T>
@@ -597,20 +615,49 @@ cudaError_t launch_axpby(double a, const double *x, double b, double *y, int64_t
 
 int krylov_partial_blocks() { return KRYLOV_BLOCKS; }
 
+template <int NVB>
+static void dots_nvb(const double *V, int nv, int64_t ld, const double *w, int64_t n, double *partials,
+                     cudaStream_t s) {
+    note_launches(1);
+    dim3 grid(KRYLOV_BLOCKS, (nv + 15) / 16);
+    dots_kernel<NVB><<<grid, KRYLOV_THREADS, 0, s>>>(V, nv, ld, w, n, partials);
+}
+
 cudaError_t launch_dots(const double *V, int nv, int64_t ld, const double *w, int64_t n, double *partials,
                         cudaStream_t s) {
-    if (nv > MAXV) return cudaErrorInvalidValue;
-    note_launches(1);
-    dots_kernel<<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(V, nv, ld, w, n, partials);
+    if (nv < 1 || nv > MAXV) return cudaErrorInvalidValue;
+    if (nv <= 1) dots_nvb<1>(V, nv, ld, w, n, partials, s);
+    else if (nv <= 2) dots_nvb<2>(V, nv, ld, w, n, partials, s);
+    else if (nv <= 4) dots_nvb<4>(V, nv, ld, w, n, partials, s);
+    else if (nv <= 8) dots_nvb<8>(V, nv, ld, w, n, partials, s);
+    else dots_nvb<16>(V, nv, ld, w, n, partials, s);
     return cudaGetLastError();
 }
+
+template <int NVB, int MODE>
+static void upd(const double *V, int nv, int64_t ld, double *w, int64_t n, const double *h, double *partials,
+                cudaStream_t s) {
+    note_launches(1);
+    update_dots_kernel<NVB, MODE><<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(V, nv, ld, w, n, h, partials);
+}
+
+// mode 1: w -= V h and partial dots <V_i, w>; mode 2: w -= V h and partial <w, w>
 cudaError_t launch_update_dots(const double *V, int nv, int64_t ld, double *w, int64_t n, const double *h,
                                double *partials, int mode, cudaStream_t s) {
-    if (nv > MAXV) return cudaErrorInvalidValue;
-    note_launches(1);
-    update_dots_kernel<<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(V, nv, ld, w, n, h, partials, mode);
+    if (nv < 1 || nv > MAXV) return cudaErrorInvalidValue;
+    if (mode == 2) {
+        upd<1, 2>(V, nv, ld, w, n, h, partials, s);
+    } else if (nv <= 4) {
+        upd<4, 1>(V, nv, ld, w, n, h, partials, s);
+    } else if (nv <= 8) {
+        upd<8, 1>(V, nv, ld, w, n, h, partials, s);
+    } else {
+        upd<1, 0>(V, nv, ld, w, n, h, partials, s);
+        return launch_dots(V, nv, ld, w, n, partials, s);
+    }
     return cudaGetLastError();
 }
+
 cudaError_t launch_reduce_partials(const double *partials, int nv, double *out, int accumulate,
                                    cudaStream_t s) {
     note_launches(1);

@@ -28,12 +28,13 @@ def _hdg():
     return hdg
 
 
-def setup_case(N0, nl, k, gamma=100.0, beta=1.0, nu=1.0, precision=0, **meshkw):
+def setup_case(N0, nl, k, gamma=100.0, beta=1.0, nu=1.0, precision=0, fused=0, **meshkw):
     hdg = _hdg()
     ms, ts, ps = hierarchy(N0, nl, **meshkw)
     fv = forcing(ms[-1], k, curl_bubble_2d(), nu, beta)
     ctx = hdg.hdg_setup_mesh_hierarchy(ms)
-    prm = hdg.Params(k=k, nu=nu, beta=beta, gamma=gamma, precision=precision)
+    prm = hdg.Params(k=k, nu=nu, beta=beta, gamma=gamma, precision=precision,
+                     fused_coarse_cells=fused)
     F = hdg.hdg_condense(ctx, prm, torch.tensor(fv, device=DEV))
     return ms, ts, ps, fv, ctx, F
 
@@ -123,11 +124,12 @@ def _oracle_mg(ts, ps, k, gamma, beta=1.0, q=1):
 
 
 @pytest.mark.parametrize("q", [1, 2])
-def test_mg_h_and_mg_hp(q):
+@pytest.mark.parametrize("fused", [0, 2048])
+def test_mg_h_and_mg_hp(q, fused):
     hdg = _hdg()
     k = 2
     ms, ts, ps, fv, ctx, F = setup_case(2, 4, k, shuffle_seed=11)
-    hdg.hdg_condense(ctx, hdg.Params(k=k, beta=1.0, gamma=100.0, cycle=q))
+    hdg.hdg_condense(ctx, hdg.Params(k=k, beta=1.0, gamma=100.0, cycle=q, fused_coarse_cells=fused))
     M = _oracle_mg(ts, ps, k, 100.0, q=q)
     rng = np.random.default_rng(4)
     g0 = rng.standard_normal(2 * ts[-1].n_interior)
@@ -254,3 +256,24 @@ def test_full_size_sampled_parity():
             lf = list(topo.cell_facets[c]).index(F)
             acc += Ao[lf * dpf:(lf + 1) * dpf] @ xl
         assert rel(y[i * dpf:(i + 1) * dpf], acc) < 1e-11
+
+
+_BIG_ORACLE = {}
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mg_h_fused_and_multiblock_levels(precision):
+    """Hierarchy 4x4..128x128 with the single-block kernel on levels up to 32x32
+    and the multi-block kernels on 64x64 and 128x128: MG_h and MG_hp against the oracle."""
+    hdg = _hdg()
+    k = 1
+    ms, ts, ps, fv, ctx, F = setup_case(4, 6, k, precision=precision, fused=2048)
+    if "M" not in _BIG_ORACLE:
+        _BIG_ORACLE["M"] = _oracle_mg(ts, ps, k, 100.0)
+    M = _BIG_ORACLE["M"]
+    rng = np.random.default_rng(8)
+    g0 = rng.standard_normal(2 * ts[-1].n_interior)
+    tol = 1e-10 if precision == 0 else 1e-4
+    assert rel(host(hdg.hdg_mg_h(ctx, dev(g0))), M.mgh(g0, 1, 1)) < tol
+    r = rng.standard_normal(M.A.shape[0])
+    assert rel(host(hdg.hdg_precond_apply(ctx, dev(r))), M(r)) < tol
