@@ -108,6 +108,9 @@ typedef struct {
     hdg_precision precision; /* precision of the preconditioner                    */
     int fused_coarse_cells;  /* run MG_h on the coarsest levels with at most this  */
                              /* many cells in one thread block (0 = off; <= 2048)  */
+    const double *nu_elem;   /* device [n_cells finest] per-cell viscosity, or     */
+                             /* NULL for the scalar nu; coarser levels use the     */
+                             /* mean over each cell's children                     */
 } hdg_params;
 
 typedef struct {
@@ -189,6 +192,39 @@ hdg_status hdg_precond_apply(hdg_ctx *ctx, const double *r, double *z, hdg_strea
 hdg_status hdg_solve(hdg_ctx *ctx, const double *F, double *u, double *p,
                      const hdg_solve_opts *opts, hdg_solve_info *info, hdg_stream_t stream);
 
+/* Local fields of a skeleton solution (Section 3.2: "we recover the local
+ * variables in an element-by-element manner"): the cell unknowns eliminated
+ * by hdg_condense are recomputed from u (device [n_dof]) and the forcing
+ * (device lattice layout, or NULL for zero forcing) with the current
+ * parameters.  Outputs (device, each may be NULL):
+ *   L_out    [n_cells][4][npk]: coefficients of L_h = -nu grad u in the
+ *            orthonormal P^k basis of each cell, components (xx, xy, yx, yy),
+ *            npk = (k+1)(k+2)/2 (basis: csrc/reference.cpp);
+ *   ulat_out [n_cells][n_lat][2]: u_h at the degree-(k+1) lattice points, which
+ *            determine u_h exactly (RT_k is contained in [P^{k+1}]^2). */
+hdg_status hdg_recover(hdg_ctx *ctx, const double *u, const double *forcing, double *L_out,
+                       double *ulat_out, hdg_stream_t stream);
+
+/* Adjoint gradients of J = 1/2 ||u_h - u_target||^2_{L2(Omega)} with respect
+ * to the forcing lattice values and the per-cell viscosity (Section 3.2 scheme,
+ * differentiated through the discrete solution).  For the generalized Stokes
+ * system the transposed local system equals the primal one with the signs of
+ * the flux and pressure blocks flipped, so the adjoint is solved with the same
+ * condensed operator and hp-multigrid preconditioner (hdg_solve with opts) for
+ * the load (u_h - u_target, v); then dJ/dnu_K = -nu_K^{-2} (L_h, L^a)_K and
+ * dJ/df_h = (u^a, lambda_n e_c)_K.  The discrete solution, hence J, does not
+ * depend on the augmented-Lagrangian weight.
+ *   forcing:  device lattice layout, the forcing of the primal solve;
+ *   u:        device [n_dof], the primal skeleton solution (from hdg_solve);
+ *   u_target: device [n_cells][n_lat][2], lattice samples of the target;
+ *   grad_forcing: device out, lattice layout, or NULL;
+ *   grad_nu:  device out [n_cells], or NULL;
+ *   J:        host out (the objective), or NULL;
+ *   opts/info as hdg_solve (info describes the adjoint solve). */
+hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, const double *u_target,
+                       double *grad_forcing, double *grad_nu, double *J, const hdg_solve_opts *opts,
+                       hdg_solve_info *info, hdg_stream_t stream);
+
 /* Sizes after hdg_setup_mesh_hierarchy (k-dependent fields after hdg_condense). */
 hdg_status hdg_get_sizes(const hdg_ctx *ctx, hdg_sizes *out);
 
@@ -247,8 +283,8 @@ hdg_status hdg_restrict_noalloc(hdg_ctx *ctx, int level, const double *rf, doubl
 
 /* Host-side reference-element integrals that hdg_condense contracts with each
  * cell's Jacobian to form the local system of eq. stWeak (Section 3.2) for
- * order k: the blocks R1..R6 packed in that order (layouts in the library
- * source, csrc/reference.cpp).  Returns the number of doubles; writes them to
+ * order k, and to evaluate recovered fields: the blocks R1..R8 packed in that
+ * order (layouts in the library source, csrc/reference.cpp).  Returns the number of doubles; writes them to
  * out (host memory) when out is not NULL; returns -1 for k outside 0..4.
  * Needs no GPU. */
 int64_t hdg_reference_tables(int k, double *out);

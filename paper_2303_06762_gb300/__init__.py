@@ -35,7 +35,7 @@ _STATUS = {0: "HDG_OK", 1: "HDG_ERR_INVALID_ARG", 2: "HDG_ERR_OOM", 3: "HDG_ERR_
 
 # every exported entry point of include/hdg.h
 EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense", "hdg_load",
-           "hdg_apply", "hdg_precond_apply", "hdg_solve", "hdg_get_sizes",
+           "hdg_apply", "hdg_precond_apply", "hdg_solve", "hdg_recover", "hdg_adjoint", "hdg_get_sizes",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
            "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_destroy",
@@ -62,7 +62,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nu", ctypes.c_double), ("beta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("m_p", ctypes.c_int), ("m_h", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("vcycle_growth", ctypes.c_int), ("precision", ctypes.c_int),
-                ("fused_coarse_cells", ctypes.c_int)]
+                ("fused_coarse_cells", ctypes.c_int), ("nu_elem", ctypes.c_void_p)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -102,10 +102,12 @@ class Params:
     vcycle_growth: int = 2
     precision: int = HDG_FP64
     fused_coarse_cells: int = 0
+    nu_elem: object = None          # optional CUDA float64 tensor [n_cells] of per-cell viscosity
 
     def to_c(self) -> _Params:
+        ne = None if self.nu_elem is None else _ptr(self.nu_elem)
         return _Params(self.k, self.nu, self.beta, self.gamma, self.m_p, self.m_h, self.cycle,
-                       self.vcycle_growth, self.precision, self.fused_coarse_cells)
+                       self.vcycle_growth, self.precision, self.fused_coarse_cells, ne)
 
 
 _lib = None
@@ -131,6 +133,9 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "hdg_apply": (I, [P, P, P, P]),
         "hdg_precond_apply": (I, [P, P, P, P]),
         "hdg_solve": (I, [P, P, P, P, ctypes.POINTER(SolveOpts), ctypes.POINTER(SolveInfo), P]),
+        "hdg_recover": (I, [P, P, P, P, P, P]),
+        "hdg_adjoint": (I, [P, P, P, P, P, P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(SolveOpts),
+                            ctypes.POINTER(SolveInfo), P]),
         "hdg_get_sizes": (I, [P, ctypes.POINTER(Sizes)]),
         "hdg_get_element_matrices": (I, [P, I, P, P]),
         "hdg_level_apply": (I, [P, I, P, P, P]),
@@ -292,6 +297,34 @@ def hdg_solve(ctx: Context, F, u=None, p=None, opts: Optional[SolveOpts] = None,
     return u, p, info.as_dict()
 
 
+def hdg_recover(ctx: Context, u, forcing=None, stream=None):
+    """Local fields of a skeleton solution: (L coefficients [nc, 4, npk], u at the lattice [nc, nlat, 2])."""
+    import torch
+    s = ctx.sizes()
+    k = s.k
+    npk, nlat = (k + 1) * (k + 2) // 2, (k + 2) * (k + 3) // 2
+    L = torch.empty((s.n_cells, 4, npk), dtype=torch.float64, device=u.device)
+    ul = torch.empty((s.n_cells, nlat, 2), dtype=torch.float64, device=u.device)
+    ctx.check(load_library().hdg_recover(ctx.handle, _ptr(u), _ptr(forcing), _ptr(L), _ptr(ul),
+                                         _stream(stream)))
+    return L, ul
+
+
+def hdg_adjoint(ctx: Context, forcing, u, u_target, opts: Optional[SolveOpts] = None, stream=None):
+    """Adjoint gradients of J = 1/2 ||u_h - u_target||^2: returns (J, dJ/dforcing, dJ/dnu_cell, info)."""
+    import torch
+    s = ctx.sizes()
+    gf = torch.empty_like(forcing)
+    gn = torch.empty(s.n_cells, dtype=torch.float64, device=forcing.device)
+    J = ctypes.c_double()
+    info = SolveInfo()
+    o = opts if opts is not None else default_solve_opts()
+    ctx.check(load_library().hdg_adjoint(ctx.handle, _ptr(forcing), _ptr(u), _ptr(u_target), _ptr(gf),
+                                         _ptr(gn), ctypes.byref(J), ctypes.byref(o), ctypes.byref(info),
+                                         _stream(stream)))
+    return J.value, gf, gn, info.as_dict()
+
+
 def hdg_get_element_matrices(ctx: Context, level: int = -1, stream=None):
     import torch
     s = ctx.sizes()
@@ -358,7 +391,7 @@ def hdg_mg_h(ctx: Context, g, u=None, stream=None):
 
 
 def hdg_reference_tables(k: int) -> dict:
-    """Reference-element integrals R1..R6 used by the device condensation (host call)."""
+    """Reference-element tables R1..R8 used by the device condensation and recovery (host call)."""
     lib = load_library()
     n = lib.hdg_reference_tables(k, None)
     if n < 0:
@@ -367,7 +400,7 @@ def hdg_reference_tables(k: int) -> dict:
     lib.hdg_reference_tables(k, buf.ctypes.data_as(ctypes.c_void_p))
     npk, nrt, nf, nlat = (k + 1) * (k + 2) // 2, (k + 1) * (k + 3), k + 1, (k + 2) * (k + 3) // 2
     shapes = dict(R1=(nrt, 2, 2, npk), R2=(3, nrt, 2, npk), R3=(3, npk, nf), R4=(nrt, 2, nrt, 2),
-                  R5=(nrt, npk), R6=(nrt, 2, nlat))
+                  R5=(nrt, npk), R6=(nrt, 2, nlat), R7=(nrt, 2, nlat), R8=(nlat, nlat))
     out, o = {}, 0
     for name, shp in shapes.items():
         m = int(np.prod(shp))

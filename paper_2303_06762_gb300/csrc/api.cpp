@@ -74,7 +74,7 @@ void free_operator(DevOperator &op) {
 }
 
 void free_level(DevLevel &L) {
-    dfree(L.coords); dfree(L.cells); dfree(L.cell_int); dfree(L.facet_adj); dfree(L.cell_d);
+    dfree(L.coords); dfree(L.cells); dfree(L.cell_int); dfree(L.facet_adj); dfree(L.cell_d); dfree(L.cell_nu);
     dfree(L.cell_area); dfree(L.patch_nf); dfree(L.patch_facets); dfree(L.patch_nc);
     dfree(L.patch_cells); dfree(L.patch_slot_src);
     free_operator(L.op0);
@@ -439,6 +439,94 @@ FgmresOut fgmres(hdg_ctx *ctx, const double *b, double *x, double rtol, double a
     return {total, beta};
 }
 
+const double *cell_nu_of(hdg_ctx *ctx, int l) {
+    return ctx->prm.nu_elem ? ctx->L[l].cell_nu.p : nullptr;
+}
+
+// condensed load F from lattice forcing (the element matrices are left untouched)
+void load_impl(hdg_ctx *ctx, const double *forcing, double *rhs_out, cudaStream_t s) {
+    DevLevel &LJ = ctx->L[ctx->n_levels - 1];
+    CK(launch_condense(ctx->prm.k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, ctx->n_levels - 1),
+                       ctx->prm.beta, ctx->prm.gamma, forcing, nullptr, nullptr, ctx->opk.Fel.p,
+                       ctx->status_flag.p, RecoverArgs(), s));
+    CK(launch_assemble_load(LJ, ctx->opk, rhs_out, s));
+}
+
+void recover_impl(hdg_ctx *ctx, const double *u, const double *forcing, double *L, double *rt, double *ulat,
+                  cudaStream_t s) {
+    DevLevel &LJ = ctx->L[ctx->n_levels - 1];
+    RecoverArgs rec;
+    rec.x = u;
+    rec.cell_int = LJ.cell_int.p;
+    rec.L = L;
+    rec.rt = rt;
+    rec.ulat = ulat;
+    CK(launch_condense(ctx->prm.k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, ctx->n_levels - 1),
+                       ctx->prm.beta, ctx->prm.gamma, forcing, nullptr, nullptr, nullptr, ctx->status_flag.p, rec,
+                       s));
+}
+
+// Augmented-Lagrangian Uzawa loop with FGMRES inner solves (eq. stOpEq-ALU); returns
+// HDG_OK or HDG_ERR_NOT_CONVERGED, throws on other failures
+hdg_status uzawa_solve(hdg_ctx *ctx, const double *F, double *u, double *p, const hdg_solve_opts *opts_in,
+                       hdg_solve_info &loc, cudaStream_t s) {
+    hdg_status conv = HDG_OK;
+    hdg_solve_opts o;
+    hdg_default_solve_opts(&o);
+    if (opts_in) o = *opts_in;
+    REQUIRE(o.restart >= 1 && o.restart <= 32, "restart out of range 1..32");
+    REQUIRE(o.max_uzawa >= 1 && o.max_uzawa <= 64, "max_uzawa out of range 1..64");
+    REQUIRE(o.max_it >= 1 && o.rtol >= 0 && o.atol >= 0 && o.floor_rel >= 0 && o.uzawa_tol >= 0,
+            "bad tolerances");
+    ensure_krylov(ctx, o.restart);
+    const int J = ctx->n_levels - 1;
+    DevLevel &LJ = ctx->L[J];
+    const int k = ctx->prm.k;
+    const double normF = norm2(ctx, F, ctx->n_dof, s);
+    loc = hdg_solve_info{};
+    loc.normF = normF;
+    const double floor_abs = std::max(o.floor_rel * normF, o.atol);
+    double *g = ctx->kt.p;
+    double ndp_prev = -1.0;
+    bool done = false;
+    for (int it = 0; it < o.max_uzawa; ++it) {
+        CK(launch_uzawa_rhs(LJ, k, F, p, g, s));
+        FgmresOut fo = fgmres(ctx, g, u, o.rtol, floor_abs, o.restart, o.max_it, s);
+        loc.krylov_its[it] = fo.its;
+        loc.krylov_its_total += fo.its;
+        loc.uzawa_its = it + 1;
+        loc.res_mom = fo.res;
+        if (fo.its >= o.max_it) conv = HDG_ERR_NOT_CONVERGED;
+        CK(launch_uzawa_update(LJ, k, u, p, ctx->prm.gamma, ctx->prm.nu, cell_nu_of(ctx, J), ctx->partials.p, s));
+        SmallLayout Ly{o.restart};
+        CK(launch_reduce_partials(ctx->partials.p, 3, ctx->small.p + Ly.h1(), 0, s));
+        CK(cudaMemcpyAsync(ctx->h_pinned, ctx->small.p + Ly.h1(), 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        const double ndp = std::sqrt(std::max(ctx->h_pinned[0], 0.0));
+        const double npn = std::sqrt(std::max(ctx->h_pinned[1], 0.0));
+        loc.dp_rel = npn > 0 ? ndp / npn : 0.0;
+        if (!std::isfinite(ndp) || !std::isfinite(npn)) {
+            ctx->err = "non-finite pressure update";
+            throw Fail{HDG_ERR_NONFINITE};
+        }
+        if (ndp <= o.atol || (it > 0 && fo.its == 0)) { done = true; break; }
+        if (ndp_prev >= 0) {
+            double rho = std::min(ndp / ndp_prev, 0.99);
+            if (rho / (1.0 - rho) * ndp <= o.uzawa_tol * npn) { done = true; break; }
+        }
+        ndp_prev = ndp;
+    }
+    if (!done && conv == HDG_OK) conv = HDG_ERR_NOT_CONVERGED;
+    return conv;
+}
+
+double device_sum(hdg_ctx *ctx, const double *x, int64_t n, cudaStream_t s) {
+    SmallLayout Ly{ctx->restart_alloc};
+    CK(launch_sum(x, n, ctx->partials.p, s));
+    CK(launch_reduce_partials(ctx->partials.p, 1, ctx->small.p + Ly.nrm2(), 0, s));
+    return read_scalar(ctx, ctx->small.p + Ly.nrm2(), s);
+}
+
 } // namespace
 
 // =====================================================================================
@@ -481,7 +569,7 @@ int64_t hdg_reference_tables(int k, double *out) {
         RefTables t;
         build_reference_tables(k, t);
         int64_t n = 0;
-        for (auto *v : {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6}) {
+        for (auto *v : {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6, &t.R7, &t.R8}) {
             if (out) std::memcpy(out + n, v->data(), sizeof(double) * v->size());
             n += (int64_t)v->size();
         }
@@ -606,6 +694,9 @@ void hdg_destroy(hdg_ctx *ctx) {
     dfree(ctx->coarse_inv); dfree(ctx->status_flag);
     dfree(ctx->V); dfree(ctx->Z); dfree(ctx->w); dfree(ctx->partials); dfree(ctx->small);
     dfree(ctx->uz_partials);
+    for (auto *b : {&ctx->rec_L, &ctx->rec_La, &ctx->rec_rt, &ctx->rec_ulat, &ctx->rec_e, &ctx->rec_j, &ctx->adj_F,
+                    &ctx->adj_u, &ctx->adj_p})
+        dfree(*b);
     drop_graph(ctx);
     dfree(ctx->pc_in); dfree(ctx->pc_out);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
@@ -636,7 +727,7 @@ static void upload_ref(hdg_ctx *ctx, RefTables &t, DBuf<double> &d, int k) {
     if (t.k == k && d.p) return;
     build_reference_tables(k, t);
     std::vector<double> packed;
-    for (auto *v : {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6}) packed.insert(packed.end(), v->begin(), v->end());
+    for (auto *v : {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6, &t.R7, &t.R8}) packed.insert(packed.end(), v->begin(), v->end());
     dfree(d);
     upload(ctx, d, packed);
 }
@@ -665,11 +756,21 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
         drop_graph(ctx);
         ctx->prm = *prm;
         const int k = prm->k;
-        const double eps_inv = prm->gamma * prm->nu;
         upload_ref(ctx, ctx->ref0, ctx->ref0_dev, 0);
         upload_ref(ctx, ctx->refk, ctx->refk_dev, k);
         CK(cudaMemsetAsync(ctx->status_flag.p, 0, sizeof(int), s));
         const int nl = ctx->n_levels;
+        // per-cell viscosity: the caller's on the finest level, child means below
+        const bool per_cell = prm->nu_elem != nullptr;
+        if (per_cell) {
+            DevLevel &F = ctx->L[nl - 1];
+            dalloc(ctx, F.cell_nu, F.nc);
+            CK(cudaMemcpyAsync(F.cell_nu.p, prm->nu_elem, sizeof(double) * F.nc, cudaMemcpyDeviceToDevice, s));
+            for (int l = nl - 1; l >= 1; --l) {
+                dalloc(ctx, ctx->L[l - 1].cell_nu, ctx->L[l - 1].nc);
+                CK(launch_nu_average(ctx->L[l], ctx->L[l].cell_nu.p, ctx->L[l - 1].cell_nu.p, s));
+            }
+        }
         for (int l = 0; l < nl; ++l) {
             DevLevel &L = ctx->L[l];
             DevOperator &op = L.op0;
@@ -678,8 +779,9 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
             dalloc(ctx, op.Af, 36 * L.nc);
             dalloc(ctx, op.Pinv, (size_t)L.n_patches * op.np_max * op.np_max);
             dalloc(ctx, op.Pinvf, (size_t)L.n_patches * op.np_max * op.np_max);
-            CK(launch_condense(0, L, ctx->ref0_dev.p, ctx->ref0, prm->nu, prm->beta, eps_inv, nullptr,
-                               op.A.p, op.Af.p, nullptr, ctx->status_flag.p, s));
+            CK(launch_condense(0, L, ctx->ref0_dev.p, ctx->ref0, prm->nu, per_cell ? L.cell_nu.p : nullptr,
+                               prm->beta, prm->gamma, nullptr, op.A.p, op.Af.p, nullptr, ctx->status_flag.p,
+                               RecoverArgs(), s));
             CK(launch_patch_inverse(L, op, ctx->status_flag.p, s));
         }
         DevLevel &LJ = ctx->L[nl - 1];
@@ -690,8 +792,9 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
         dalloc(ctx, op.Fel, (size_t)op.nloc * LJ.nc);
         dalloc(ctx, op.Pinv, (size_t)LJ.n_patches * op.np_max * op.np_max);
         dalloc(ctx, op.Pinvf, (size_t)LJ.n_patches * op.np_max * op.np_max);
-        CK(launch_condense(k, LJ, ctx->refk_dev.p, ctx->refk, prm->nu, prm->beta, eps_inv, forcing,
-                           op.A.p, op.Af.p, op.Fel.p, ctx->status_flag.p, s));
+        CK(launch_condense(k, LJ, ctx->refk_dev.p, ctx->refk, prm->nu, per_cell ? LJ.cell_nu.p : nullptr,
+                           prm->beta, prm->gamma, forcing, op.A.p, op.Af.p, op.Fel.p, ctx->status_flag.p,
+                           RecoverArgs(), s));
         CK(launch_patch_inverse(LJ, op, ctx->status_flag.p, s));
         for (int l = 1; l < nl; ++l) CK(launch_transfer_H(ctx->L[l], ctx->status_flag.p, s));
         ctx->n0 = 2 * ctx->L[0].n_int;
@@ -722,11 +825,7 @@ hdg_status hdg_load(hdg_ctx *ctx, const double *forcing, double *rhs_out, hdg_st
         if (!ctx->condensed) { ctx->err = "hdg_load before hdg_condense"; throw Fail{HDG_ERR_STATE}; }
         REQUIRE(forcing && rhs_out, "null forcing or rhs_out");
         cudaStream_t s = (cudaStream_t)stream;
-        DevLevel &LJ = ctx->L[ctx->n_levels - 1];
-        const double eps_inv = ctx->prm.gamma * ctx->prm.nu;
-        CK(launch_condense(ctx->prm.k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, ctx->prm.beta, eps_inv,
-                           forcing, ctx->opk.A.p, ctx->opk.Af.p, ctx->opk.Fel.p, ctx->status_flag.p, s));
-        CK(launch_assemble_load(LJ, ctx->opk, rhs_out, s));
+        load_impl(ctx, forcing, rhs_out, s);
     });
 }
 
@@ -867,58 +966,78 @@ hdg_status hdg_solve(hdg_ctx *ctx, const double *F, double *u, double *p, const 
     hdg_status st = guard(ctx, [&] {
         NEED_CONDENSED();
         REQUIRE(F && u && p, "null vector");
-        hdg_solve_opts o;
-        hdg_default_solve_opts(&o);
-        if (opts_in) o = *opts_in;
-        REQUIRE(o.restart >= 1 && o.restart <= 32, "restart out of range 1..32");
-        REQUIRE(o.max_uzawa >= 1 && o.max_uzawa <= 64, "max_uzawa out of range 1..64");
-        REQUIRE(o.max_it >= 1 && o.rtol >= 0 && o.atol >= 0 && o.floor_rel >= 0 && o.uzawa_tol >= 0,
-                "bad tolerances");
-        cudaStream_t s = (cudaStream_t)stream;
-        ensure_krylov(ctx, o.restart);
-        const int J = ctx->n_levels - 1;
-        DevLevel &LJ = ctx->L[J];
-        const int k = ctx->prm.k;
-        const double eps_inv = ctx->prm.gamma * ctx->prm.nu;
-        const double normF = norm2(ctx, F, ctx->n_dof, s);
-        loc.normF = normF;
-        const double floor_abs = std::max(o.floor_rel * normF, o.atol);
-        double *g = ctx->kt.p;
-        double ndp_prev = -1.0;
-        bool done = false;
-        for (int it = 0; it < o.max_uzawa; ++it) {
-            CK(launch_uzawa_rhs(LJ, k, F, p, g, s));
-            FgmresOut fo = fgmres(ctx, g, u, o.rtol, floor_abs, o.restart, o.max_it, s);
-            loc.krylov_its[it] = fo.its;
-            loc.krylov_its_total += fo.its;
-            loc.uzawa_its = it + 1;
-            loc.res_mom = fo.res;
-            if (fo.its >= o.max_it) conv = HDG_ERR_NOT_CONVERGED;
-            CK(launch_uzawa_update(LJ, k, u, p, eps_inv, ctx->partials.p, s));
-            SmallLayout Ly{o.restart};
-            CK(launch_reduce_partials(ctx->partials.p, 3, ctx->small.p + Ly.h1(), 0, s));
-            CK(cudaMemcpyAsync(ctx->h_pinned, ctx->small.p + Ly.h1(), 3 * sizeof(double),
-                               cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
-            const double ndp = std::sqrt(std::max(ctx->h_pinned[0], 0.0));
-            const double npn = std::sqrt(std::max(ctx->h_pinned[1], 0.0));
-            loc.dp_rel = npn > 0 ? ndp / npn : 0.0;
-            if (!std::isfinite(ndp) || !std::isfinite(npn)) {
-                ctx->err = "non-finite pressure update";
-                throw Fail{HDG_ERR_NONFINITE};
-            }
-            if (ndp <= o.atol || (it > 0 && fo.its == 0)) { done = true; break; }
-            if (ndp_prev >= 0) {
-                double rho = std::min(ndp / ndp_prev, 0.99);
-                if (rho / (1.0 - rho) * ndp <= o.uzawa_tol * npn) { done = true; break; }
-            }
-            ndp_prev = ndp;
-        }
-        if (!done && conv == HDG_OK) conv = HDG_ERR_NOT_CONVERGED;
+        conv = uzawa_solve(ctx, F, u, p, opts_in, loc, (cudaStream_t)stream);
     });
     if (info) *info = loc;
     if (st != HDG_OK) return st;
     if (conv != HDG_OK) ctx->err = "iteration limit reached";
+    return conv;
+}
+
+hdg_status hdg_recover(hdg_ctx *ctx, const double *u, const double *forcing, double *L_out, double *ulat_out,
+                       hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(u, "null skeleton vector");
+        cudaStream_t s = (cudaStream_t)stream;
+        if (!forcing) {
+            const int64_t nlat = (ctx->prm.k + 2) * (ctx->prm.k + 3) / 2;
+            dalloc(ctx, ctx->rec_e, (size_t)ctx->L[ctx->n_levels - 1].nc * 2 * nlat);
+            CK(cudaMemsetAsync(ctx->rec_e.p, 0, sizeof(double) * ctx->rec_e.n, s));
+            forcing = ctx->rec_e.p;
+        }
+        recover_impl(ctx, u, forcing, L_out, nullptr, ulat_out, s);
+    });
+}
+
+hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, const double *u_target,
+                       double *grad_forcing, double *grad_nu, double *J, const hdg_solve_opts *opts,
+                       hdg_solve_info *info, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    hdg_solve_info loc{};
+    hdg_status conv = HDG_OK;
+    hdg_status st = guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(forcing && u && u_target, "null input");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int Jl = ctx->n_levels - 1;
+        DevLevel &LJ = ctx->L[Jl];
+        const int k = ctx->prm.k;
+        const int64_t nc = LJ.nc;
+        const int64_t npk = (k + 1) * (k + 2) / 2, nrt = (k + 1) * (k + 3), nlat = (k + 2) * (k + 3) / 2;
+        dalloc(ctx, ctx->rec_L, nc * 4 * npk);
+        dalloc(ctx, ctx->rec_La, nc * 4 * npk);
+        dalloc(ctx, ctx->rec_rt, nc * nrt);
+        dalloc(ctx, ctx->rec_ulat, nc * 2 * nlat);
+        dalloc(ctx, ctx->rec_e, nc * 2 * nlat);
+        dalloc(ctx, ctx->rec_j, nc);
+        dalloc(ctx, ctx->adj_F, ctx->n_dof);
+        dalloc(ctx, ctx->adj_u, ctx->n_dof);
+        dalloc(ctx, ctx->adj_p, nc);
+        // primal local fields, the objective and the adjoint load u_h - u_target
+        recover_impl(ctx, u, forcing, ctx->rec_L.p, nullptr, ctx->rec_ulat.p, s);
+        CK(launch_objective(k, LJ, ctx->refk_dev.p, ctx->refk, ctx->rec_ulat.p, u_target, ctx->rec_e.p,
+                            ctx->rec_j.p, s));
+        hdg_solve_opts o;
+        hdg_default_solve_opts(&o);
+        if (opts) o = *opts;
+        ensure_krylov(ctx, std::max(1, std::min(o.restart, 32)));
+        const double Jval = device_sum(ctx, ctx->rec_j.p, nc, s);
+        if (J) *J = Jval;
+        load_impl(ctx, ctx->rec_e.p, ctx->adj_F.p, s);
+        CK(cudaMemsetAsync(ctx->adj_u.p, 0, sizeof(double) * ctx->n_dof, s));
+        CK(cudaMemsetAsync(ctx->adj_p.p, 0, sizeof(double) * nc, s));
+        conv = uzawa_solve(ctx, ctx->adj_F.p, ctx->adj_u.p, ctx->adj_p.p, &o, loc, s);
+        // adjoint local fields, then the contractions
+        recover_impl(ctx, ctx->adj_u.p, ctx->rec_e.p, ctx->rec_La.p, ctx->rec_rt.p, nullptr, s);
+        CK(launch_adjoint_gradient(k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, Jl),
+                                   ctx->rec_L.p, ctx->rec_La.p, ctx->rec_rt.p, grad_nu, grad_forcing, s));
+        CK(cudaStreamSynchronize(s));
+    });
+    if (info) *info = loc;
+    if (st != HDG_OK) return st;
+    if (conv != HDG_OK) ctx->err = "adjoint solve: iteration limit reached";
     return conv;
 }
 

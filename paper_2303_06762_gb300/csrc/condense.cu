@@ -56,7 +56,10 @@ struct Dims {
     static constexpr int O_W = O_SP + NPO * NPO;
     static constexpr int O_Z = O_W + NPO * NG;
     static constexpr int O_LII = O_Z + NPO * (NG + 1);
-    static constexpr int TOTAL = O_LII + NRI * NRI;
+    static constexpr int O_XG = O_LII + NRI * NRI;       // recovery: gathered skeleton values
+    static constexpr int O_XF = O_XG + NG;                // recovery: all (u, û) coefficients
+    static constexpr int O_PO = O_XF + NCOL;              // recovery: mean-free pressure
+    static constexpr int TOTAL = O_PO + NPO + 1;
 };
 
 // geometry slots inside the O_GEO block
@@ -134,10 +137,11 @@ __global__ void __launch_bounds__(128)
 condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__restrict__ cells,
                 const double *__restrict__ R1, const double *__restrict__ R2,
                 const double *__restrict__ R3, const double *__restrict__ R4,
-                const double *__restrict__ R5, const double *__restrict__ R6, double nu,
-                double beta, double eps_inv, const double *__restrict__ forcing,
+                const double *__restrict__ R5, const double *__restrict__ R6,
+                const double *__restrict__ R7, double nu_scalar, const double *__restrict__ nu_cell,
+                double beta, double gamma, const double *__restrict__ forcing,
                 double *__restrict__ Aout, float *__restrict__ Afout, double *__restrict__ Fout,
-                int *flag) {
+                int *flag, RecoverArgs rec) {
     using D = Dims<K>;
     extern __shared__ double sm[];
     double *geo = sm + D::O_GEO;
@@ -152,6 +156,9 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
     double *Wm = sm + D::O_W;
     double *Zm = sm + D::O_Z;
     double *Lii = sm + D::O_LII;
+    double *xg = sm + D::O_XG;
+    double *xf = sm + D::O_XF;
+    double *po = sm + D::O_PO;
     const int tid = threadIdx.x, nt = blockDim.x;
     __shared__ int s_ok;
 
@@ -164,6 +171,8 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
             for (int i = tid; i < 2 * D::NLAT; i += nt) Fn[i] = forcing[c * 2 * D::NLAT + i];
         __syncthreads();
         const double det = geo[G_DET], sgn = geo[G_SGN], adet = fabs(det);
+        const double nu = nu_cell ? nu_cell[c] : nu_scalar;
+        const double eps_inv = gamma * nu;
         for (int i = tid; i < D::NRT; i += nt) {
             double s = 1.0;
             if (i < 3 * D::NF) {
@@ -298,8 +307,62 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
             for (int col = tid; col < D::NG + 1; col += nt) chol_solve_col(Sp, D::NPO, D::NPO, Zm, D::NG + 1, col);
             __syncthreads();
         }
+        if (rec.x) {
+            // recovery of the local unknowns from the skeleton values x_g:
+            //   p_o = S_p^{-1}(W x_g - D_oi Y_F),  u_i = Y_F - Y_g x_g + Y_D p_o,
+            //   L = -(nu/|det J|) C [u; û]   (orthonormal P^k coefficients)
+            for (int p = tid; p < D::NG; p += nt) {
+                int f = p / (2 * D::NF);
+                int j = rec.cell_int[3 * c + f];
+                xg[p] = j >= 0 ? rec.x[(size_t)j * 2 * D::NF + p % (2 * D::NF)] : 0.0;
+            }
+            __syncthreads();
+            for (int j = tid; j < D::NPO; j += nt) {
+                double v = -Zm[j * (D::NG + 1) + D::NG];
+                for (int q = 0; q < D::NG; ++q) v += Zm[j * (D::NG + 1) + q] * xg[q];
+                po[j] = v;
+            }
+            __syncthreads();
+            for (int col = tid; col < D::NCOL; col += nt) {
+                double v = 0.0;
+                if (col < 3 * D::NF) {
+                    int f = col / D::NF, m = col % D::NF;
+                    v = xg[f * 2 * D::NF + m];
+                } else if (col < D::NRT) {
+                    int r = col - 3 * D::NF;
+                    v = Y[r * D::NY + D::NG + D::NPO];
+                    for (int q = 0; q < D::NG; ++q) v -= Y[r * D::NY + q] * xg[q];
+                    for (int j = 0; j < D::NPO; ++j) v += Y[r * D::NY + D::NG + j] * po[j];
+                } else {
+                    int h = col - D::NRT, f = h / D::NF, m = h % D::NF;
+                    v = xg[f * 2 * D::NF + D::NF + m];
+                }
+                xf[col] = v;
+            }
+            __syncthreads();
+            if (rec.L)
+                for (int row = tid; row < D::NL; row += nt) {
+                    double v = 0.0;
+                    for (int col = 0; col < D::NCOL; ++col) v += C[row * D::NCOL + col] * xf[col];
+                    rec.L[c * D::NL + row] = -nu / adet * v;
+                }
+            if (rec.rt)
+                for (int i = tid; i < D::NRT; i += nt) rec.rt[c * D::NRT + i] = xf[i] * sc[i];
+            if (rec.po)
+                for (int j = tid; j < D::NPO; j += nt) rec.po[c * D::NPO + j] = po[j];
+            if (rec.ulat)
+                for (int idx = tid; idx < 2 * D::NLAT; idx += nt) {
+                    int n = idx >> 1, cc = idx & 1;
+                    double v = 0.0;
+                    for (int i = 0; i < D::NRT; ++i)
+                        for (int a = 0; a < 2; ++a)
+                            v += geo[G_J + 2 * cc + a] * xf[i] * sc[i] * R7[(i * 2 + a) * D::NLAT + n];
+                    rec.ulat[c * 2 * D::NLAT + idx] = v / det;
+                }
+        }
         // A = K_gg − K_gi Y_g + Wᵀ Z_W (+ AL),  F = F_g − K_gi Y_F + Wᵀ Z_v
         const double al = eps_inv / geo[G_AREA];
+        if (Aout)
         for (int idx = tid; idx < D::NG * D::NG; idx += nt) {
             int p = idx / D::NG, q = idx % D::NG;
             int gp = gcol(p), gq = gcol(q);
@@ -329,20 +392,22 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
 
 template <int K>
 cudaError_t launch_condense_k(const DevLevel &L, const double *ref, const RefTables &rt, double nu,
-                              double beta, double eps_inv, const double *forcing, double *A,
-                              float *Af, double *Fel, int *flag, cudaStream_t s) {
+                              const double *nu_cell, double beta, double gamma, const double *forcing,
+                              double *A, float *Af, double *Fel, int *flag, const RecoverArgs &rec,
+                              cudaStream_t s) {
     using D = Dims<K>;
     size_t smem = sizeof(double) * D::TOTAL;
     auto kern = condense_kernel<K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const double *R[6];
-    for (int i = 0; i < 6; ++i) R[i] = ref + ref_table_offset(rt, i);
+    const double *R[7];
+    for (int i = 0; i < 7; ++i) R[i] = ref + ref_table_offset(rt, i);
     int64_t grid = L.nc < 152 * 64 ? L.nc : 152 * 64;
     if (grid < 1) return cudaSuccess;
     note_launches(1);
     kern<<<(unsigned)grid, 128, smem, s>>>(L.nc, L.coords.p, L.cells.p, R[0], R[1], R[2], R[3], R[4],
-                                           R[5], nu, beta, eps_inv, forcing, A, Af, Fel, flag);
+                                           R[5], R[6], nu, nu_cell, beta, gamma, forcing, A, Af, Fel,
+                                           flag, rec);
     return cudaGetLastError();
 }
 
@@ -562,17 +627,122 @@ __global__ void assemble_load_kernel(int64_t n_int, int dpf, const int *__restri
 
 unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
+// coarse-cell viscosity = mean over its four children (equal areas under red refinement)
+__global__ void nu_average_kernel(int64_t ncc, const int *__restrict__ children, const double *__restrict__ nu_f,
+                                  double *__restrict__ nu_c) {
+    int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (P >= ncc) return;
+    double s = 0.0;
+    for (int ch = 0; ch < 4; ++ch) s += nu_f[children[4 * P + ch]];
+    nu_c[P] = 0.25 * s;
+}
+
+// Adjoint gradients (Stokes: the transposed local system equals the primal one with the
+// signs of the flux and pressure blocks flipped, so lambda_L = -L^a, lambda_u = u^a):
+//   dJ/dnu_K = -nu_K^{-2} (L_h, L^a)_K = -nu_K^{-2} |det J| sum_r L_r L^a_r   (orthonormal P^k)
+//   dJ/dF_{K,n,c} = (u^a, lam_n e_c)_K = sgn(det J) sum_i rt^a_i sum_a J[c][a] R6[i][a][n]
+template <int K>
+__global__ void adjoint_gradient_kernel(int64_t nc, const double *__restrict__ coords, const int *__restrict__ cells,
+                                        const double *__restrict__ R6, double nu_scalar,
+                                        const double *__restrict__ nu_cell, const double *__restrict__ Lp,
+                                        const double *__restrict__ La, const double *__restrict__ rta,
+                                        double *__restrict__ grad_nu, double *__restrict__ grad_f) {
+    using D = Dims<K>;
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    double geo[64];
+    cell_geometry(coords, cells, c, geo);
+    const double nu = nu_cell ? nu_cell[c] : nu_scalar;
+    if (grad_nu) {
+        double s = 0.0;
+        for (int r = 0; r < D::NL; ++r) s += Lp[c * D::NL + r] * La[c * D::NL + r];
+        grad_nu[c] = -fabs(geo[G_DET]) * s / (nu * nu);
+    }
+    if (grad_f)
+        for (int n = 0; n < D::NLAT; ++n)
+            for (int cc = 0; cc < 2; ++cc) {
+                double v = 0.0;
+                for (int i = 0; i < D::NRT; ++i)
+                    for (int a = 0; a < 2; ++a) v += rta[c * D::NRT + i] * geo[G_J + 2 * cc + a] * R6[(i * 2 + a) * D::NLAT + n];
+                grad_f[(c * D::NLAT + n) * 2 + cc] = geo[G_SGN] * v;
+            }
+}
+
+// per-cell 0.5 ||u_h - u_target||^2_K for lattice samples of two [P^{k+1}]^2 fields, and e = u_h - u_t
+template <int K>
+__global__ void objective_kernel(int64_t nc, const double *__restrict__ coords, const int *__restrict__ cells,
+                                 const double *__restrict__ R8, const double *__restrict__ ulat,
+                                 const double *__restrict__ utgt, double *__restrict__ e_out,
+                                 double *__restrict__ jcell) {
+    using D = Dims<K>;
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    double geo[64];
+    cell_geometry(coords, cells, c, geo);
+    double e[2 * D::NLAT];
+    for (int i = 0; i < 2 * D::NLAT; ++i) {
+        e[i] = ulat[c * 2 * D::NLAT + i] - utgt[c * 2 * D::NLAT + i];
+        e_out[c * 2 * D::NLAT + i] = e[i];
+    }
+    double s = 0.0;
+    for (int n = 0; n < D::NLAT; ++n)
+        for (int m = 0; m < D::NLAT; ++m)
+            s += R8[n * D::NLAT + m] * (e[2 * n] * e[2 * m] + e[2 * n + 1] * e[2 * m + 1]);
+    jcell[c] = 0.5 * fabs(geo[G_DET]) * s;
+}
+
 } // namespace
 
-cudaError_t launch_condense(int k, const DevLevel &L, const double *ref, const RefTables &rt, double nu,
-                            double beta, double eps_inv, const double *forcing, double *A, float *Af,
-                            double *Fel, int *flag, cudaStream_t s) {
+cudaError_t launch_nu_average(const DevLevel &fine, const double *nu_f, double *nu_c, cudaStream_t s) {
+    if (fine.nc_coarse == 0) return cudaSuccess;
+    note_launches(1);
+    nu_average_kernel<<<blocks_for(fine.nc_coarse, 128), 128, 0, s>>>(fine.nc_coarse, fine.tr_children.p, nu_f, nu_c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_gradient(int k, const DevLevel &L, const double *ref, const RefTables &rt,
+                                    double nu, const double *nu_cell, const double *Lp, const double *La,
+                                    const double *rta, double *grad_nu, double *grad_f, cudaStream_t s) {
+    const double *R6 = ref + ref_table_offset(rt, 5);
+    unsigned nb = blocks_for(L.nc, 64);
+    note_launches(1);
     switch (k) {
-    case 0: return launch_condense_k<0>(L, ref, rt, nu, beta, eps_inv, forcing, A, Af, Fel, flag, s);
-    case 1: return launch_condense_k<1>(L, ref, rt, nu, beta, eps_inv, forcing, A, Af, Fel, flag, s);
-    case 2: return launch_condense_k<2>(L, ref, rt, nu, beta, eps_inv, forcing, A, Af, Fel, flag, s);
-    case 3: return launch_condense_k<3>(L, ref, rt, nu, beta, eps_inv, forcing, A, Af, Fel, flag, s);
-    case 4: return launch_condense_k<4>(L, ref, rt, nu, beta, eps_inv, forcing, A, Af, Fel, flag, s);
+    case 0: adjoint_gradient_kernel<0><<<nb, 64, 0, s>>>(L.nc, L.coords.p, L.cells.p, R6, nu, nu_cell, Lp, La, rta, grad_nu, grad_f); break;
+    case 1: adjoint_gradient_kernel<1><<<nb, 64, 0, s>>>(L.nc, L.coords.p, L.cells.p, R6, nu, nu_cell, Lp, La, rta, grad_nu, grad_f); break;
+    case 2: adjoint_gradient_kernel<2><<<nb, 64, 0, s>>>(L.nc, L.coords.p, L.cells.p, R6, nu, nu_cell, Lp, La, rta, grad_nu, grad_f); break;
+    case 3: adjoint_gradient_kernel<3><<<nb, 64, 0, s>>>(L.nc, L.coords.p, L.cells.p, R6, nu, nu_cell, Lp, La, rta, grad_nu, grad_f); break;
+    case 4: adjoint_gradient_kernel<4><<<nb, 64, 0, s>>>(L.nc, L.coords.p, L.cells.p, R6, nu, nu_cell, Lp, La, rta, grad_nu, grad_f); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_objective(int k, const DevLevel &L, const double *ref, const RefTables &rt, const double *ulat,
+                             const double *utgt, double *e_out, double *jcell, cudaStream_t s) {
+    const double *R8 = ref + ref_table_offset(rt, 7);
+    unsigned nb = blocks_for(L.nc, 64);
+    note_launches(1);
+    switch (k) {
+    case 0: objective_kernel<0><<<nb, 64, 0, s>>>(L.nc, L.coords.p, L.cells.p, R8, ulat, utgt, e_out, jcell); break;
+    case 1: objective_kernel<1><<<nb, 64, 0, s>>>(L.nc, L.coords.p, L.cells.p, R8, ulat, utgt, e_out, jcell); break;
+    case 2: objective_kernel<2><<<nb, 64, 0, s>>>(L.nc, L.coords.p, L.cells.p, R8, ulat, utgt, e_out, jcell); break;
+    case 3: objective_kernel<3><<<nb, 64, 0, s>>>(L.nc, L.coords.p, L.cells.p, R8, ulat, utgt, e_out, jcell); break;
+    case 4: objective_kernel<4><<<nb, 64, 0, s>>>(L.nc, L.coords.p, L.cells.p, R8, ulat, utgt, e_out, jcell); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_condense(int k, const DevLevel &L, const double *ref, const RefTables &rt, double nu,
+                            const double *nu_cell, double beta, double gamma, const double *forcing,
+                            double *A, float *Af, double *Fel, int *flag, const RecoverArgs &rec,
+                            cudaStream_t s) {
+    switch (k) {
+    case 0: return launch_condense_k<0>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, A, Af, Fel, flag, rec, s);
+    case 1: return launch_condense_k<1>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, A, Af, Fel, flag, rec, s);
+    case 2: return launch_condense_k<2>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, A, Af, Fel, flag, rec, s);
+    case 3: return launch_condense_k<3>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, A, Af, Fel, flag, rec, s);
+    case 4: return launch_condense_k<4>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, A, Af, Fel, flag, rec, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -63,7 +63,7 @@ struct HostTransfer {
 // reference-element tables for order k (FP64), see reference.cpp
 struct RefTables {
     int k = -1, npk = 0, nrt = 0, nf = 0, nlat = 0;
-    std::vector<double> R1, R2, R3, R4, R5, R6;
+    std::vector<double> R1, R2, R3, R4, R5, R6, R7, R8;
 };
 
 // layout of the small Krylov block (restart R):
@@ -111,6 +111,16 @@ struct SmallParams {
     int q = 1, growth = 2;
 };
 
+// outputs of the recovery mode of the condensation kernel (all device, nullable)
+struct RecoverArgs {
+    const double *x = nullptr;      // skeleton solution [n_int][dpf]; null = no recovery
+    const int *cell_int = nullptr;  // cell -> interior facet
+    double *L = nullptr;            // [nc][4*npk] flux coefficients (orthonormal P^k, per component)
+    double *rt = nullptr;           // [nc][nrt] RT coefficients in the reference dual basis
+    double *po = nullptr;           // [nc][npk-1] mean-free pressure coefficients
+    double *ulat = nullptr;         // [nc][nlat][2] velocity at the degree-(k+1) lattice
+};
+
 // ---------------------------------------------------------------- device data
 template <class T>
 struct DBuf {
@@ -134,6 +144,7 @@ struct DevLevel {
     DBuf<int32_t> cell_int;    // nc*3 interior facet id or -1
     DBuf<int32_t> facet_adj;   // n_int*2 (cell << 2 | lf) or -1
     DBuf<double> cell_d;       // nc*3 flux weights sigma*sqrt|F| of each local facet
+    DBuf<double> cell_nu;      // nc per-cell viscosity (when the caller gives one)
     DBuf<double> cell_area;    // nc
     // patches
     int n_patches = 0, n_colours = 0, pf_max = 0, pc_max = 0;
@@ -185,6 +196,8 @@ struct hdg_ctx {
     int pc_prec = -1;
     long long pc_kernels = 0;
     hdg::DBuf<double> pc_in, pc_out;
+    // recovery / adjoint workspaces
+    hdg::DBuf<double> rec_L, rec_La, rec_rt, rec_ulat, rec_e, rec_j, adj_F, adj_u, adj_p;
     // fused MG_h on levels 0..small_Ls (one thread block), -1 when not used
     int small_Ls = -1;
     size_t small_smem_d = 0, small_smem_f = 0;
@@ -200,7 +213,7 @@ unsigned long long launch_count();
 
 // reference.cpp
 void build_reference_tables(int k, RefTables &out);
-size_t ref_table_offset(const RefTables &t, int which);   // offset of R1..R6 in packed buffer
+size_t ref_table_offset(const RefTables &t, int which);   // offset of R1..R8 in packed buffer
 
 // topology.cpp
 std::string build_level_topology(HostLevel &L, const int32_t *colour_or_null);
@@ -208,13 +221,20 @@ std::string build_transfer(const HostLevel &coarse, const HostLevel &fine, HostT
 
 // kernels: condensation and setup (condense.cu)
 cudaError_t launch_condense(int k, const DevLevel &L, const double *ref, const RefTables &rt,
-                            double nu, double beta, double eps_inv, const double *forcing,
-                            double *A, float *Af, double *Fel, int *flag, cudaStream_t s);
+                            double nu, const double *nu_cell, double beta, double gamma,
+                            const double *forcing, double *A, float *Af, double *Fel, int *flag,
+                            const RecoverArgs &rec, cudaStream_t s);
 cudaError_t launch_patch_inverse(const DevLevel &L, const DevOperator &op, int *flag, cudaStream_t s);
 cudaError_t launch_transfer_H(const DevLevel &fine, int *flag, cudaStream_t s);
 cudaError_t launch_coarse_inverse(const DevLevel &L0, double *inv, int64_t n, int *flag,
                                   cudaStream_t s);
 cudaError_t launch_assemble_load(const DevLevel &L, const DevOperator &op, double *F, cudaStream_t s);
+cudaError_t launch_nu_average(const DevLevel &fine, const double *nu_f, double *nu_c, cudaStream_t s);
+cudaError_t launch_adjoint_gradient(int k, const DevLevel &L, const double *ref, const RefTables &rt,
+                                    double nu, const double *nu_cell, const double *Lp, const double *La,
+                                    const double *rta, double *grad_nu, double *grad_f, cudaStream_t s);
+cudaError_t launch_objective(int k, const DevLevel &L, const double *ref, const RefTables &rt, const double *ulat,
+                             const double *utgt, double *e_out, double *jcell, cudaStream_t s);
 cudaError_t launch_cell_geometry(DevLevel &L, cudaStream_t s);
 
 // kernels: hot path (ops.cu)
@@ -262,7 +282,8 @@ cudaError_t launch_solve_update(double *small, int m, int restart, const double 
                                 double *x, int64_t n, cudaStream_t s);
 cudaError_t launch_uzawa_rhs(const DevLevel &L, int k, const double *F, const double *p, double *g,
                              cudaStream_t s);
-cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p,
-                                double eps_inv, double *partials, cudaStream_t s);
+cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p, double gamma,
+                                double nu, const double *nu_cell, double *partials, cudaStream_t s);
+cudaError_t launch_sum(const double *x, int64_t n, double *partials, cudaStream_t s);
 
 } // namespace hdg

@@ -458,8 +458,8 @@ __global__ void uzawa_rhs_kernel(int64_t n_int, int dpf, const int *__restrict__
 __global__ void __launch_bounds__(KRYLOV_THREADS)
 uzawa_update_kernel(int64_t nc, int dpf, const int *__restrict__ cell_int,
                     const double *__restrict__ cell_d, const double *__restrict__ area,
-                    const double *__restrict__ u, double *__restrict__ p, double eps_inv,
-                    double *__restrict__ partials) {
+                    const double *__restrict__ u, double *__restrict__ p, double gamma, double nu,
+                    const double *__restrict__ nu_cell, double *__restrict__ partials) {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -469,7 +469,7 @@ uzawa_update_kernel(int64_t nc, int dpf, const int *__restrict__ cell_int,
             if (j >= 0) du += cell_d[3 * c + f] * u[(size_t)j * dpf];
         }
         double a = area[c];
-        double dp = eps_inv * du / a;
+        double dp = gamma * (nu_cell ? nu_cell[c] : nu) * du / a;
         double pn = p[c] - dp;
         p[c] = pn;
         acc[0] += a * dp * dp;
@@ -701,11 +701,25 @@ cudaError_t launch_uzawa_rhs(const DevLevel &L, int k, const double *F, const do
     uzawa_rhs_kernel<<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, dpf, L.facet_adj.p, L.cell_d.p, F, p, g);
     return cudaGetLastError();
 }
-cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p, double eps_inv,
-                                double *partials, cudaStream_t s) {
+__global__ void __launch_bounds__(KRYLOV_THREADS)
+sum_kernel(const double *__restrict__ x, int64_t n, double *__restrict__ partials) {
+    double acc[1] = {0.0};
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        acc[0] += x[e];
+    block_reduce_store<1>(acc, 1, partials);
+}
+
+cudaError_t launch_sum(const double *x, int64_t n, double *partials, cudaStream_t s) {
+    note_launches(1);
+    sum_kernel<<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(x, n, partials);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p, double gamma, double nu,
+                                const double *nu_cell, double *partials, cudaStream_t s) {
     note_launches(1);
     uzawa_update_kernel<<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(L.nc, 2 * (k + 1), L.cell_int.p, L.cell_d.p,
-                                                                 L.cell_area.p, u, p, eps_inv, partials);
+                                                                 L.cell_area.p, u, p, gamma, nu, nu_cell, partials);
     return cudaGetLastError();
 }
 

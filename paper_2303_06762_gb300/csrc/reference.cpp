@@ -22,6 +22,7 @@
 //   R1[i][a][b][j] = ∫ d_b phi_{i,a} g_j          R4[i][a][i'][b] = ∫ phi_{i,a} phi_{i',b}
 //   R2[f][i][a][j] = ∫_{F^_f} phi_{i,a} g_j ds^   R5[i][j] = ∫ div phi_i g_j
 //   R3[f][j][m]    = ∫_0^1 g_j(x_f(s)) l_m(s) ds  R6[i][a][n] = ∫ phi_{i,a} lam_n
+//   R7[i][a][n]    = phi_{i,a} at lattice point n  R8[n][n'] = ∫ lam_n lam_n'
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -384,6 +385,17 @@ void build_reference_tables(int k, RefTables &t) {
     t.R4.assign((size_t)nrt * 2 * nrt * 2, 0.0);
     t.R5.assign((size_t)nrt * npk, 0.0);
     t.R6.assign((size_t)nrt * 2 * nlat, 0.0);
+    t.R7.assign((size_t)nrt * 2 * nlat, 0.0);
+    t.R8.assign((size_t)nlat * nlat, 0.0);
+    {
+        int pidx = 0;
+        for (int a2 = 0; a2 <= q; ++a2)
+            for (int a1 = 0; a1 <= q - a2; ++a1, ++pidx) {
+                mono_at(double(a1) / q, double(a2) / q, mv, mdx, mdy);
+                for (int i = 0; i < nrt; ++i)
+                    for (int a = 0; a < 2; ++a) t.R7[(i * 2 + a) * nlat + pidx] = phi_val(i, a, mv);
+            }
+    }
     for (int p = 0; p < nq; ++p) {
         const auto &mvp = MV[p], &dxp = MDX[p], &dyp = MDY[p];
         std::vector<double> gv(npk), lv(nlat), pv(nrt * 2), dv(nrt * 4);
@@ -409,6 +421,8 @@ void build_reference_tables(int k, RefTables &t) {
             for (int a = 0; a < 2; ++a)
                 for (int nn = 0; nn < nlat; ++nn) t.R6[(i * 2 + a) * nlat + nn] += wq * pv[2 * i + a] * lv[nn];
         }
+        for (int n1 = 0; n1 < nlat; ++n1)
+            for (int n2 = 0; n2 < nlat; ++n2) t.R8[n1 * nlat + n2] += wq * lv[n1] * lv[n2];
     }
     for (int f = 0; f < 3; ++f)
         for (int p = 0; p < n; ++p) {
@@ -427,7 +441,7 @@ void build_reference_tables(int k, RefTables &t) {
 
 size_t ref_table_offset(const RefTables &t, int which) {
     size_t off = 0;
-    const std::vector<double> *tabs[6] = {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6};
+    const std::vector<double> *tabs[8] = {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6, &t.R7, &t.R8};
     for (int i = 0; i < which; ++i) off += tabs[i]->size();
     return off;
 }
