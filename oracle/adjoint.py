@@ -15,6 +15,12 @@ lambda_L = -L^a.  The only nu-dependent block is (nu^{-1} L, G)_K, hence
 and the forcing enters through (f_h, v)_K, hence
   dJ/df_{K,n,c} = (u^a, lam_n e_c)_K   (lam_n: lattice Lagrange basis).
 Both solves are exact (sparse direct) solves of the condensed saddle point.
+
+Oseen (Section 4.1, Picard field w_h fixed): only the (u, û) block gains the
+upwind convection C, and S acts as the identity there, so
+M^T = S (M_Stokes + C^T) S: the adjoint is the problem whose local
+convection block is transposed (HDG(conv_transpose=True)), loaded with
+u_h - u_target, with the same two gradient formulas.
 """
 
 from __future__ import annotations
@@ -42,9 +48,11 @@ def _lattice_function(h: HDG, c: int, vals, xq):
     return cc.el.mono(xq, h.k + 1) @ (cc.lat_inv @ np.asarray(vals))
 
 
-def objective_and_gradient(topo, k, fvals, u_target, nu_elem, beta=0.0, gamma=0.0):
+def objective_and_gradient(topo, k, fvals, u_target, nu_elem, beta=0.0, gamma=0.0, conv=None):
     """Returns (J, dJ/dfvals (n_cells, n_lat, 2), dJ/dnu (n_cells,), u, p, ua)."""
-    h = HDG(topo, k, nu=1.0, beta=beta, gamma=gamma, nu_elem=nu_elem)
+    h = HDG(topo, k, nu=1.0, beta=beta, gamma=gamma, nu_elem=nu_elem, conv=conv)
+    ha = h if conv is None else HDG(topo, k, nu=1.0, beta=beta, gamma=gamma, nu_elem=nu_elem,
+                                    conv=conv, conv_transpose=True)
     nc = topo.n_cells
     u, p = h.solve_direct(h.load(fvals))
     prim = [h.recover_cell(c, u, p[c], fvals[c]) for c in range(nc)]
@@ -54,12 +62,12 @@ def objective_and_gradient(topo, k, fvals, u_target, nu_elem, beta=0.0, gamma=0.
         xq, wq = triangle_points(h.cells[c].el.X, k + 4)
         ev = _lattice_function(h, c, e[c], xq)
         J += 0.5 * wq @ np.sum(ev ** 2, axis=1)
-    ua, pa = h.solve_direct(h.load(e))
+    ua, pa = ha.solve_direct(ha.load(e))
     gnu = np.zeros(nc)
     gf = np.zeros_like(np.asarray(fvals, dtype=float))
     npk = len(exponents(k))
     for c in range(nc):
-        adj = h.recover_cell(c, ua, pa[c], e[c])
+        adj = ha.recover_cell(c, ua, pa[c], e[c])
         el = h.cells[c].el
         xq, wq = triangle_points(el.X, k + 4)
         Lp, _, _, _ = h.fields_at(c, prim[c], xq)
@@ -71,8 +79,8 @@ def objective_and_gradient(topo, k, fvals, u_target, nu_elem, beta=0.0, gamma=0.
     return J, gf, gnu, u, p, ua
 
 
-def objective(topo, k, fvals, u_target, nu_elem, beta=0.0, gamma=0.0):
-    h = HDG(topo, k, nu=1.0, beta=beta, gamma=gamma, nu_elem=nu_elem)
+def objective(topo, k, fvals, u_target, nu_elem, beta=0.0, gamma=0.0, conv=None):
+    h = HDG(topo, k, nu=1.0, beta=beta, gamma=gamma, nu_elem=nu_elem, conv=conv)
     u, p = h.solve_direct(h.load(fvals))
     J = 0.0
     for c in range(topo.n_cells):

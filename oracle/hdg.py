@@ -39,10 +39,24 @@ from .spaces import Element, exponents
 from .topology import Topology
 
 
-def _signature(X, gv, k, nu, beta):
+def _signature(X, gv, k, nu, beta, conv=None, conv_t=False):
     rel = np.ascontiguousarray(X - X[0])
     ranks = tuple(np.argsort(np.argsort(np.asarray(gv))).tolist())
-    return (rel.tobytes(), ranks, k, float(nu), float(beta))
+    cb = None if conv is None else np.ascontiguousarray(conv, dtype=float).tobytes()
+    return (rel.tobytes(), ranks, k, float(nu), float(beta), cb, bool(conv_t))
+
+
+def lattice_degree(n_lat: int) -> int:
+    q = 0
+    while (q + 1) * (q + 2) // 2 < n_lat:
+        q += 1
+    assert (q + 1) * (q + 2) // 2 == n_lat, "not a triangle lattice size"
+    return q
+
+
+def upwind_facet_points(k: int, q_w: int) -> int:
+    """Gauss–Legendre points per facet for the upwind terms: exact for degree q_w + 2k + 2."""
+    return (q_w + 2 * k + 4) // 2
 
 
 @dataclass
@@ -59,15 +73,27 @@ class CondensedCell:
     lat_inv: np.ndarray  # lattice Vandermonde inverse (monomials of degree k+1)
 
 
-def local_system(el: Element, nu: float, beta: float):
-    """Full local matrix over (L, u, û, p), forcing map and index sets."""
+def local_system(el: Element, nu: float, beta: float, conv=None, conv_transpose: bool = False):
+    """Full local matrix over (L, u, û, p), forcing map and index sets.
+
+    conv: optional lattice values (n_lat_w, 2) of the convecting field w_h on
+    this cell (degree q_w lattice, same ordering as the forcing).  It adds the
+    upwind form of Section 4.1 with the Picard field w_h (eq. nsWeak):
+      -(u, (w·∇)v)_K + <(w·n)^+ tng u + (w·n)^- tng û, tng(v - v̂)>_{∂K},
+    i.e. u^up takes the trace of u where w·n_K > 0 and of û where w·n_K < 0,
+    switched pointwise at the Gauss points of upwind_facet_points(k, q_w).
+    conv_transpose: use the transpose of that (u, û) block instead.  Because
+    the remaining blocks satisfy Mᵀ = S M S with S = diag(-I_L, I_u, I_û, -I_p),
+    the local system with the transposed convection block is S Mᵀ S: the
+    system whose solution gives the adjoint (Section 4.1 with A10's objective).
+    """
     k = el.k
     npk = len(exponents(k))
     nL, nrt, nh, npp = 4 * npk, el.n_rt, 3 * (k + 1), npk
     oL, ou, oh, op = 0, nL, nL + nrt, nL + nrt + nh
     n = op + npp
     M = np.zeros((n, n))
-    xq, wq = triangle_points(el.X, k + 3)
+    xq, wq = triangle_points(el.X, k + 3 if conv is None else k + 4)
     Pk = el.mono(xq, k)
     mean = (wq @ Pk) / el.area
     pv = Pk - mean[None, :]
@@ -107,6 +133,34 @@ def local_system(el: Element, nu: float, beta: float):
     Bd = np.einsum("q,qi,qj->ij", wq, DU, pv)
     M[ou:ou + nrt, op:op + npp] = -Bd
     M[op:op + npp, ou:ou + nrt] = Bd.T
+    if conv is not None:
+        conv = np.asarray(conv, dtype=float)
+        q_w = lattice_degree(conv.shape[0])
+        lam_w = lattice_barycentric_2d(q_w)
+        w_inv = np.linalg.inv(el.mono(lam_w @ el.X, q_w))
+        wc = w_inv @ conv                                   # monomial coefficients of w
+        wq_v = el.mono(xq, q_w) @ wc                        # w at volume points
+        # -(u, (w·∇)v): rows v_i, cols u_j
+        wgrad = np.einsum("qicd,qd->qic", GU, wq_v)         # ((w·∇)φ_i)_c
+        Cv = np.zeros((n, n))
+        Cv[ou:ou + nrt, ou:ou + nrt] -= np.einsum("q,qic,qjc->ij", wq, wgrad, U)
+        nF = upwind_facet_points(k, q_w)
+        for f in range(3):
+            fd = el.facets[f]
+            s, xf, wf = el.facet_points(f, nF)
+            nK = fd["nK"]
+            wn = (el.mono(xf, q_w) @ wc) @ nK
+            wp, wm = np.maximum(wn, 0.0), np.minimum(wn, 0.0)
+            Uf = el.rt_values(xf)
+            tngU = Uf - np.einsum("qi,c->qic", Uf @ nK, nK)
+            lm = el.facet_legendre(f, s)
+            Hf = np.einsum("qm,c->qmc", lm, fd["t"])       # û basis on this facet
+            hs = slice(oh + f * (k + 1), oh + (f + 1) * (k + 1))
+            Cv[ou:ou + nrt, ou:ou + nrt] += np.einsum("q,qic,qjc->ij", wf * wp, tngU, tngU)
+            Cv[ou:ou + nrt, hs] += np.einsum("q,qic,qmc->im", wf * wm, tngU, Hf)
+            Cv[hs, ou:ou + nrt] -= np.einsum("q,qmc,qjc->mj", wf * wp, Hf, tngU)
+            Cv[hs, hs] -= np.einsum("q,qmc,qnc->mn", wf * wm, Hf, Hf)
+        M += Cv.T if conv_transpose else Cv
     # forcing: f_h ∈ [P^{k+1}]² from its values at the degree-(k+1) lattice
     lam = lattice_barycentric_2d(k + 1)
     Xl = lam @ el.X
@@ -125,9 +179,10 @@ def local_system(el: Element, nu: float, beta: float):
         dict(oL=oL, ou=ou, oh=oh, op=op, npk=npk, nrt=nrt)
 
 
-def condense_cell(el: Element, nu: float, beta: float) -> CondensedCell:
+def condense_cell(el: Element, nu: float, beta: float, conv=None,
+                  conv_transpose: bool = False) -> CondensedCell:
     """Static condensation of one cell by a dense Schur complement."""
-    M, rhs_map, g, loc, p0, lat_inv, _ = local_system(el, nu, beta)
+    M, rhs_map, g, loc, p0, lat_inv, _ = local_system(el, nu, beta, conv, conv_transpose)
     Mll = M[np.ix_(loc, loc)]
     Mlg = M[np.ix_(loc, g)]
     Mgl = M[np.ix_(g, loc)]
@@ -146,7 +201,8 @@ class HDG:
 
     def __init__(self, topo: Topology, k: int, nu: float = 1.0, beta: float = 0.0,
                  gamma: float = 0.0, nu_elem: Optional[np.ndarray] = None,
-                 cache: bool = True):
+                 cache: bool = True, conv: Optional[np.ndarray] = None,
+                 conv_transpose: bool = False):
         self.topo, self.k = topo, k
         self.dpf = 2 * (k + 1)
         self.ng = 3 * self.dpf
@@ -156,17 +212,20 @@ class HDG:
         nc = topo.n_cells
         self.nu_elem = np.full(nc, self.nu) if nu_elem is None else np.asarray(nu_elem, float)
         self.n_dof = topo.n_interior * self.dpf
+        self.conv = None if conv is None else np.asarray(conv, dtype=float)
+        self.conv_transpose = bool(conv_transpose)
         self.cells = []
         memo = {}
         for c in range(nc):
             gv = topo.cells[c]
             X = topo.coords[gv]
-            key = _signature(X, gv, k, self.nu_elem[c], beta) if cache else None
+            cv = None if self.conv is None else self.conv[c]
+            key = _signature(X, gv, k, self.nu_elem[c], beta, cv, conv_transpose) if cache else None
             if key is not None and key in memo:
                 cc = memo[key]
             else:
                 el = Element(X - X[0], gv, k)
-                cc = condense_cell(el, self.nu_elem[c], beta)
+                cc = condense_cell(el, self.nu_elem[c], beta, cv, conv_transpose)
                 if key is not None:
                     memo[key] = cc
             self.cells.append(cc)

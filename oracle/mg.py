@@ -20,6 +20,12 @@ matrices with plain sequential loops, in the order the paper states.
   unknowns on facets inside coarse cells.  Restriction = 𝓘ᵀ.
 * Algorithm 1 (MG_h) with q = 1 (variable V-cycle, m(l−1) = growth·m(l)) or
   q = 2 (W-cycle), exact solve on the coarsest level.
+* Oseen (Section 4.2: the same smoothers and transfers applied to A^{c,ε}):
+  every lowest-order level carries its own convecting field, the RT_0 field
+  whose facet fluxes are those of the finest field w_h (the mean of the two
+  sides of each facet), summed over the two fine facets that make up each
+  coarse facet (``lowest_order_convection``).  The coarsest solve is a dense
+  LU factorisation instead of Cholesky.
 * Algorithm 2 (MG_hp): m_p forward sweeps on A^ε_k, residual restricted by
   Π_k^0 (the transpose of the inclusion: the m = 0 normal and tangential
   coefficient of each facet), MG_h on the lowest-order operator of the same
@@ -143,7 +149,8 @@ class Level:
 class MGh:
     """Algorithm 1 on lowest-order levels 1..J (index 0 = coarsest)."""
 
-    def __init__(self, levels: List[Level], parents: List[np.ndarray], growth: int = 2):
+    def __init__(self, levels: List[Level], parents: List[np.ndarray], growth: int = 2,
+                 symmetric: bool = True):
         self.levels = levels
         self.growth = growth
         for l in range(1, len(levels)):
@@ -151,11 +158,14 @@ class MGh:
             T = interior_fine_dofs(levels[l].hdg.topo, parents[l])
             levels[l].P = harmonic_prolongation(levels[l].A, Ia, T)
         A0 = levels[0].A.toarray()
-        self.coarse = sla.cho_factor(A0)
+        self.symmetric = symmetric
+        self.coarse = sla.cho_factor(A0) if symmetric else sla.lu_factor(A0)
 
     def cycle(self, l: int, g, u0, m: int, q: int = 1):
         if l == 0:
-            return sla.cho_solve(self.coarse, g)
+            if self.symmetric:
+                return sla.cho_solve(self.coarse, g)
+            return sla.lu_solve(self.coarse, g)
         L = self.levels[l]
         u = u0.copy()
         for _ in range(m):
@@ -211,12 +221,116 @@ class MGhp:
         return u
 
 
+def _outward_normal(X: np.ndarray, f: int):
+    a, b = [v for v in range(3) if v != f]
+    t = X[b] - X[a]
+    L = float(np.hypot(t[0], t[1]))
+    n = np.array([t[1], -t[0]]) / L
+    if n @ (0.5 * (X[a] + X[b]) - X[f]) < 0:
+        n = -n
+    return a, b, L, n
+
+
+def _lattice_values_at(q: int, vals: np.ndarray, lam_pts: np.ndarray) -> np.ndarray:
+    """Evaluate the degree-q polynomial with lattice values `vals` (n_lat, 2) at
+    points given by barycentric coordinates lam_pts (m, 3)."""
+    from workloads.manufactured import lattice_barycentric_2d
+    lat = lattice_barycentric_2d(q)
+    ex = [(d - b, b) for d in range(q + 1) for b in range(d + 1)]
+
+    def V(lam):
+        return np.stack([lam[:, 1] ** a * lam[:, 2] ** b for a, b in ex], axis=1)
+    return V(lam_pts) @ np.linalg.solve(V(lat), vals)
+
+
+def lowest_order_convection(topos: List[Topology], parents: List[np.ndarray],
+                            conv: np.ndarray) -> List[np.ndarray]:
+    """Convecting field of every lowest-order level, (n_cells_l, 3, 2) values at
+    the cell vertices (the degree-1 lattice), index 0 = coarsest.
+
+    Reading of Section 4.2 for the coarse operators A^{c,ε}_{0,l}: on the finest
+    mesh the field is the RT_0 function with the facet fluxes ∫_F w_h·n of the
+    given order-k field (mean of the two adjacent cells), and on each coarser
+    mesh the RT_0 function whose flux through a coarse facet is the sum of the
+    fluxes through its two fine halves.  Divergence-free, normal-continuous
+    fields with w·n = 0 on ∂Ω stay so on every level.
+    """
+    J = len(topos) - 1
+    conv = np.asarray(conv, dtype=float)
+    q = 0
+    while (q + 1) * (q + 2) // 2 < conv.shape[1]:
+        q += 1
+    s_gl, w_gl = np.polynomial.legendre.leggauss(q + 2)
+    s_gl, w_gl = 0.5 * (s_gl + 1.0), 0.5 * w_gl
+    fine = topos[J]
+    flux = np.zeros((fine.n_cells, 3))            # outward flux per (cell, local facet)
+    for c in range(fine.n_cells):
+        X = fine.coords[fine.cells[c]]
+        for f in range(3):
+            a, b, L, n = _outward_normal(X, f)
+            lam = np.zeros((len(s_gl), 3))
+            lam[:, a] = 1.0 - s_gl
+            lam[:, b] = s_gl
+            w = _lattice_values_at(q, conv[c], lam)
+            flux[c, f] = L * (w_gl @ (w @ n))
+    for F in fine.interior_facets:
+        c0, c1 = fine.facet_cells[F]
+        f0 = int(np.where(fine.cell_facets[c0] == F)[0][0])
+        f1 = int(np.where(fine.cell_facets[c1] == F)[0][0])
+        v = 0.5 * (flux[c0, f0] - flux[c1, f1])
+        flux[c0, f0], flux[c1, f1] = v, -v
+    fluxes = [None] * (J + 1)
+    fluxes[J] = flux
+    for l in range(J, 0, -1):
+        tf, tc = topos[l], topos[l - 1]
+        fc = np.zeros((tc.n_cells, 3))
+        for c in range(tf.n_cells):
+            P = int(parents[l][c])
+            Xc = tc.coords[tc.cells[P]]
+            for lf in range(3):
+                F = tf.cell_facets[c, lf]
+                o = tf.facet_cells[F]
+                if o[1] >= 0 and parents[l][o[0]] == parents[l][o[1]]:
+                    continue                      # facet inside the coarse cell
+                lo, hi = tf.facets[F]
+                mid = 0.5 * (tf.coords[lo] + tf.coords[hi])
+                lamc = _bary_point(Xc, mid)
+                fc[P, int(np.argmin(np.abs(lamc)))] += fluxes[l][c, lf]
+        fluxes[l - 1] = fc
+    out = []
+    for l in range(J + 1):
+        t = topos[l]
+        vals = np.zeros((t.n_cells, 3, 2))
+        for c in range(t.n_cells):
+            X = t.coords[t.cells[c]]
+            area = t.cell_area(c)
+            for v in range(3):
+                for f in range(3):
+                    if f != v:
+                        vals[c, v] += fluxes[l][c, f] * (X[v] - X[f]) / (2.0 * area)
+        out.append(vals)
+    return out
+
+
+def _bary_point(X: np.ndarray, x: np.ndarray) -> np.ndarray:
+    T = np.array([[X[0, 0], X[1, 0], X[2, 0]], [X[0, 1], X[1, 1], X[2, 1]], [1.0, 1.0, 1.0]])
+    return np.linalg.solve(T, np.array([x[0], x[1], 1.0]))
+
+
 def build_hpmg(topos: List[Topology], parents: List[np.ndarray], k: int, nu: float, beta: float,
                gamma: float, m_p: int = 1, m_h: int = 1, q: int = 1, growth: int = 2,
-               hdg_k: Optional[HDG] = None) -> MGhp:
-    """hp-multigrid on the hierarchy topos[0] (coarsest) .. topos[-1] (finest)."""
-    levels = [Level(HDG(t, 0, nu=nu, beta=beta, gamma=gamma)) for t in topos]
-    mgh = MGh(levels, parents, growth=growth)
+               hdg_k: Optional[HDG] = None, conv: Optional[np.ndarray] = None,
+               conv_transpose: bool = False) -> MGhp:
+    """hp-multigrid on the hierarchy topos[0] (coarsest) .. topos[-1] (finest).
+
+    conv: lattice values (n_cells_fine, n_lat(k+1), 2) of the convecting field
+    on the finest mesh (Oseen), or None (generalized Stokes).
+    """
+    conv_l = [None] * len(topos) if conv is None else lowest_order_convection(topos, parents, conv)
+    levels = [Level(HDG(t, 0, nu=nu, beta=beta, gamma=gamma, conv=cl, conv_transpose=conv_transpose))
+              for t, cl in zip(topos, conv_l)]
+    mgh = MGh(levels, parents, growth=growth, symmetric=conv is None)
     if hdg_k is None:
-        hdg_k = HDG(topos[-1], k, nu=nu, beta=beta, gamma=gamma)
+        hdg_k = HDG(topos[-1], k, nu=nu, beta=beta, gamma=gamma, conv=conv,
+                    conv_transpose=conv_transpose)
     return MGhp(hdg_k, mgh, m_p=m_p, m_h=m_h, q=q)

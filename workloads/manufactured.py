@@ -187,3 +187,61 @@ def gradient_field_2d(a: np.ndarray):
 def seeded_vector(n: int, seed: int, dtype=np.float64) -> np.ndarray:
     """Standard-normal test vector from numpy's PCG64 with the given seed."""
     return np.random.default_rng(seed).standard_normal(n).astype(dtype)
+
+
+
+def convecting_stream_2d(scale: float = 1.0):
+    """(psi, b) with psi = c sin²(pi x) sin²(pi y) and b = curl psi = (d psi/dy, -d psi/dx).
+
+    c is chosen so that max|b| = scale on the unit square.  b is divergence
+    free and b·n = 0 on the boundary (psi vanishes there).
+    """
+    bub = curl_bubble_2d()
+    g = np.linspace(0.0, 1.0, 801)
+    X, Y = np.meshgrid(g, g)
+    pts = np.stack([X.ravel(), Y.ravel()], axis=1)
+    c = scale / float(np.sqrt((bub.u(pts) ** 2).sum(axis=1)).max())
+
+    def psi(x):
+        return c * (np.sin(PI * x[:, 0]) * np.sin(PI * x[:, 1])) ** 2
+
+    def b(x):
+        return c * bub.u(x)
+
+    return psi, b
+
+
+def _lattice_lagrange_gradients(q: int) -> np.ndarray:
+    """(n, n, 2): reference-triangle gradient of Lagrange basis function n' at lattice point n."""
+    lam = lattice_barycentric_2d(q)
+    xy = lam[:, 1:]                                   # reference coordinates (lambda1, lambda2)
+    ex = [(d - b, b) for d in range(q + 1) for b in range(d + 1)]
+    V = np.stack([xy[:, 0] ** a * xy[:, 1] ** b for a, b in ex], axis=1)
+    Vx = np.stack([a * xy[:, 0] ** max(a - 1, 0) * xy[:, 1] ** b if a else 0 * xy[:, 0]
+                   for a, b in ex], axis=1)
+    Vy = np.stack([b * xy[:, 0] ** a * xy[:, 1] ** max(b - 1, 0) if b else 0 * xy[:, 0]
+                   for a, b in ex], axis=1)
+    Vi = np.linalg.inv(V)
+    return np.stack([Vx @ Vi, Vy @ Vi], axis=2)
+
+
+def curl_lattice_2d(coords: np.ndarray, cells: np.ndarray, q: int,
+                    psi: Callable[[np.ndarray], np.ndarray]) -> np.ndarray:
+    """(n_cells, n_lattice(q), 2): curl of the continuous degree-q Lagrange
+    interpolant psi_h of psi, sampled at each cell's degree-q lattice.
+
+    curl psi_h = (d psi_h/dy, -d psi_h/dx) is a piecewise polynomial of degree
+    q-1 with single-valued normal component across cells and zero divergence,
+    and it is tangential on the boundary wherever psi vanishes there: a
+    divergence-free member of the Raviart–Thomas space RT_{q-1}.
+    """
+    X = lattice_points_2d(coords, cells, q)               # (nc, n, 2)
+    nc, n, _ = X.shape
+    vals = psi(X.reshape(-1, 2)).reshape(nc, n)
+    D = _lattice_lagrange_gradients(q)                    # (n, n', 2) reference gradients
+    gref = np.einsum("mnd,cn->cmd", D, vals)              # (nc, n, 2) reference gradient
+    V = coords[cells]
+    J = np.stack([V[:, 1] - V[:, 0], V[:, 2] - V[:, 0]], axis=2)   # (nc, 2, 2) columns = edges
+    Jinv = np.linalg.inv(J)
+    grad = np.einsum("cdi,cmd->cmi", Jinv, gref)          # J^{-T} ∇̂
+    return np.stack([grad[..., 1], -grad[..., 0]], axis=2)
