@@ -1,8 +1,9 @@
 /*
  * hdg.h — C ABI of the GB300 library for the hp-multigrid preconditioned
  * flexible GMRES solver of the statically condensed H(div)-HDG discretisation
- * of the generalized Stokes equation with an augmented-Lagrangian term
- * (G. Fu & W. Kuang, "hp-multigrid preconditioner for a divergence-conforming
+ * of the generalized Stokes equation and of the Oseen equation (the Picard
+ * linearisation of the Navier-Stokes equations, Section 4) with an
+ * augmented-Lagrangian term (G. Fu & W. Kuang, "hp-multigrid preconditioner for a divergence-conforming
  * HDG scheme for the incompressible flow problems").
  *
  * Conventions shared by every entry point
@@ -111,6 +112,18 @@ typedef struct {
     const double *nu_elem;   /* device [n_cells finest] per-cell viscosity, or     */
                              /* NULL for the scalar nu; coarser levels use the     */
                              /* mean over each cell's children                     */
+    const double *conv;      /* Oseen problem (Section 4.1, Picard form of eq.     */
+                             /* nsWeak with a fixed convecting field w_h): device  */
+                             /* [n_cells finest][n_lat][2], physical components of */
+                             /* w_h at each cell's degree-(k+1) lattice (the       */
+                             /* forcing layout); copied by hdg_condense.  w_h      */
+                             /* should be divergence free, normal-continuous and   */
+                             /* tangential on the boundary (e.g. the curl of a     */
+                             /* continuous stream function).  Lowest-order levels  */
+                             /* use the RT_0 field with the facet fluxes of w_h    */
+                             /* (mean of the two sides), summed over the fine      */
+                             /* halves of each coarse facet.  NULL = generalized   */
+                             /* Stokes.                                            */
 } hdg_params;
 
 typedef struct {
@@ -162,7 +175,9 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
  * smoothers (eq. bjac, Sections 3.4.2, 3.5), the harmonic-extension blocks of
  * the transfer (eqs. div-transfer, harmonic-ex) and the dense inverse of the
  * coarsest operator (at most 16384 coarsest unknowns, else
- * HDG_ERR_INVALID_ARG).  forcing: device [n_cells][n_lat][2] (layout above) or
+ * HDG_ERR_INVALID_ARG).  With params->conv the local systems carry the upwind
+ * convection of Section 4.1 and are eliminated by LU; the patch, transfer and
+ * coarse factorisations are the same (Section 4.2).  forcing: device [n_cells][n_lat][2] (layout above) or
  * NULL; rhs_out: device [n_dof] condensed load F, or NULL.  May be called
  * again with new parameters or forcing.  Returns HDG_ERR_SINGULAR if a
  * factorisation meets a non-positive pivot. */
@@ -214,6 +229,10 @@ hdg_status hdg_recover(hdg_ctx *ctx, const double *u, const double *forcing, dou
  * the load (u_h - u_target, v); then dJ/dnu_K = -nu_K^{-2} (L_h, L^a)_K and
  * dJ/df_h = (u^a, lambda_n e_c)_K.  The discrete solution, hence J, does not
  * depend on the augmented-Lagrangian weight.
+ * Oseen: the transposed local system is the primal one with the convection
+ * block transposed (the other blocks as above), so hdg_adjoint rebuilds every
+ * level's operators from the transposed convection, solves, and rebuilds the
+ * primal operators before returning (two extra condensations per call).
  *   forcing:  device lattice layout, the forcing of the primal solve;
  *   u:        device [n_dof], the primal skeleton solution (from hdg_solve);
  *   u_target: device [n_cells][n_lat][2], lattice samples of the target;

@@ -62,7 +62,7 @@ class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nu", ctypes.c_double), ("beta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("m_p", ctypes.c_int), ("m_h", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("vcycle_growth", ctypes.c_int), ("precision", ctypes.c_int),
-                ("fused_coarse_cells", ctypes.c_int), ("nu_elem", ctypes.c_void_p)]
+                ("fused_coarse_cells", ctypes.c_int), ("nu_elem", ctypes.c_void_p), ("conv", ctypes.c_void_p)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -103,11 +103,13 @@ class Params:
     precision: int = HDG_FP64
     fused_coarse_cells: int = 0
     nu_elem: object = None          # optional CUDA float64 tensor [n_cells] of per-cell viscosity
+    conv: object = None             # optional CUDA float64 tensor [n_cells, n_lat, 2]: Oseen field w_h
 
     def to_c(self) -> _Params:
         ne = None if self.nu_elem is None else _ptr(self.nu_elem)
+        cv = None if self.conv is None else _ptr(self.conv)
         return _Params(self.k, self.nu, self.beta, self.gamma, self.m_p, self.m_h, self.cycle,
-                       self.vcycle_growth, self.precision, self.fused_coarse_cells, ne)
+                       self.vcycle_growth, self.precision, self.fused_coarse_cells, ne, cv)
 
 
 _lib = None

@@ -75,7 +75,7 @@ void free_operator(DevOperator &op) {
 
 void free_level(DevLevel &L) {
     dfree(L.coords); dfree(L.cells); dfree(L.cell_int); dfree(L.facet_adj); dfree(L.cell_d); dfree(L.cell_nu);
-    dfree(L.cell_area); dfree(L.patch_nf); dfree(L.patch_facets); dfree(L.patch_nc);
+    dfree(L.cell_area); dfree(L.conv_flux); dfree(L.conv_lat); dfree(L.patch_nf); dfree(L.patch_facets); dfree(L.patch_nc);
     dfree(L.patch_cells); dfree(L.patch_slot_src);
     free_operator(L.op0);
     dfree(L.tr_slots); dfree(L.tr_nbr); dfree(L.tr_children); dfree(L.tr_child_slot);
@@ -443,12 +443,15 @@ const double *cell_nu_of(hdg_ctx *ctx, int l) {
     return ctx->prm.nu_elem ? ctx->L[l].cell_nu.p : nullptr;
 }
 
+// finest-level convecting field (library copy), NULL for the generalized Stokes problem
+const double *conv_of(hdg_ctx *ctx) { return ctx->has_conv ? ctx->conv_k.p : nullptr; }
+
 // condensed load F from lattice forcing (the element matrices are left untouched)
 void load_impl(hdg_ctx *ctx, const double *forcing, double *rhs_out, cudaStream_t s) {
     DevLevel &LJ = ctx->L[ctx->n_levels - 1];
     CK(launch_condense(ctx->prm.k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, ctx->n_levels - 1),
-                       ctx->prm.beta, ctx->prm.gamma, forcing, nullptr, nullptr, ctx->opk.Fel.p,
-                       ctx->status_flag.p, RecoverArgs(), s));
+                       ctx->prm.beta, ctx->prm.gamma, forcing, conv_of(ctx), ctx->conv_t, nullptr, nullptr,
+                       ctx->opk.Fel.p, ctx->status_flag.p, RecoverArgs(), s));
     CK(launch_assemble_load(LJ, ctx->opk, rhs_out, s));
 }
 
@@ -462,8 +465,8 @@ void recover_impl(hdg_ctx *ctx, const double *u, const double *forcing, double *
     rec.rt = rt;
     rec.ulat = ulat;
     CK(launch_condense(ctx->prm.k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, ctx->n_levels - 1),
-                       ctx->prm.beta, ctx->prm.gamma, forcing, nullptr, nullptr, nullptr, ctx->status_flag.p, rec,
-                       s));
+                       ctx->prm.beta, ctx->prm.gamma, forcing, conv_of(ctx), ctx->conv_t, nullptr, nullptr, nullptr,
+                       ctx->status_flag.p, rec, s));
 }
 
 // Augmented-Lagrangian Uzawa loop with FGMRES inner solves (eq. stOpEq-ALU); returns
@@ -691,7 +694,7 @@ void hdg_destroy(hdg_ctx *ctx) {
     free_operator(ctx->opk);
     dfree(ctx->refk_dev); dfree(ctx->ref0_dev);
     dfree(ctx->kr); dfree(ctx->ku); dfree(ctx->kt); dfree(ctx->krf); dfree(ctx->kuf); dfree(ctx->kgf);
-    dfree(ctx->coarse_inv); dfree(ctx->status_flag);
+    dfree(ctx->coarse_inv); dfree(ctx->status_flag); dfree(ctx->conv_k);
     dfree(ctx->V); dfree(ctx->Z); dfree(ctx->w); dfree(ctx->partials); dfree(ctx->small);
     dfree(ctx->uz_partials);
     for (auto *b : {&ctx->rec_L, &ctx->rec_La, &ctx->rec_rt, &ctx->rec_ulat, &ctx->rec_e, &ctx->rec_j, &ctx->adj_F,
@@ -727,9 +730,82 @@ static void upload_ref(hdg_ctx *ctx, RefTables &t, DBuf<double> &d, int k) {
     if (t.k == k && d.p) return;
     build_reference_tables(k, t);
     std::vector<double> packed;
-    for (auto *v : {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6, &t.R7, &t.R8}) packed.insert(packed.end(), v->begin(), v->end());
+    for (int i = 0; i < N_REF_TABLES; ++i) {
+        const std::vector<double> *v = ref_table(t, i);
+        packed.insert(packed.end(), v->begin(), v->end());
+    }
     dfree(d);
     upload(ctx, d, packed);
+}
+
+// Element matrices, patch inverses, transfer blocks and the coarsest inverse of
+// every level from ctx->prm (and ctx->conv_k / ctx->conv_t for Oseen); the
+// order-k element loads of `forcing` (NULL = zero).
+static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
+    const hdg_params *prm = &ctx->prm;
+    ctx->condensed = false;
+    drop_graph(ctx);
+    const int k = prm->k;
+    upload_ref(ctx, ctx->ref0, ctx->ref0_dev, 0);
+    upload_ref(ctx, ctx->refk, ctx->refk_dev, k);
+    CK(cudaMemsetAsync(ctx->status_flag.p, 0, sizeof(int), s));
+    const int nl = ctx->n_levels;
+    const bool per_cell = prm->nu_elem != nullptr;
+    if (ctx->has_conv) {
+        // RT_0 convecting fields of the lowest-order levels from the finest field's fluxes
+        DevLevel &F = ctx->L[nl - 1];
+        dalloc(ctx, F.conv_flux, 3 * F.nc);
+        CK(launch_conv_flux(F, ctx->refk_dev.p, ctx->refk, ctx->conv_k.p, F.conv_flux.p, s));
+        for (int l = nl - 1; l >= 1; --l) {
+            dalloc(ctx, ctx->L[l - 1].conv_flux, 3 * ctx->L[l - 1].nc);
+            CK(launch_flux_restrict(ctx->L[l], ctx->L[l].conv_flux.p, ctx->L[l - 1].conv_flux.p, s));
+        }
+        for (int l = 0; l < nl; ++l) {
+            dalloc(ctx, ctx->L[l].conv_lat, 6 * ctx->L[l].nc);
+            CK(launch_rt0_vertex(ctx->L[l], ctx->L[l].conv_flux.p, ctx->L[l].conv_lat.p, s));
+        }
+    }
+    for (int l = 0; l < nl; ++l) {
+        DevLevel &L = ctx->L[l];
+        DevOperator &op = L.op0;
+        op.k = 0; op.dpf = 2; op.nloc = 6; op.np_max = L.pf_max * 2;
+        dalloc(ctx, op.A, 36 * L.nc);
+        dalloc(ctx, op.Af, 36 * L.nc);
+        dalloc(ctx, op.Pinv, (size_t)L.n_patches * op.np_max * op.np_max);
+        dalloc(ctx, op.Pinvf, (size_t)L.n_patches * op.np_max * op.np_max);
+        CK(launch_condense(0, L, ctx->ref0_dev.p, ctx->ref0, prm->nu, per_cell ? L.cell_nu.p : nullptr,
+                           prm->beta, prm->gamma, nullptr, ctx->has_conv ? L.conv_lat.p : nullptr, ctx->conv_t,
+                           op.A.p, op.Af.p, nullptr, ctx->status_flag.p, RecoverArgs(), s));
+        CK(launch_patch_inverse(L, op, ctx->status_flag.p, s));
+    }
+    DevLevel &LJ = ctx->L[nl - 1];
+    DevOperator &op = ctx->opk;
+    op.k = k; op.dpf = 2 * (k + 1); op.nloc = 3 * op.dpf; op.np_max = LJ.pf_max * op.dpf;
+    dalloc(ctx, op.A, (size_t)op.nloc * op.nloc * LJ.nc);
+    dalloc(ctx, op.Af, (size_t)op.nloc * op.nloc * LJ.nc);
+    dalloc(ctx, op.Fel, (size_t)op.nloc * LJ.nc);
+    dalloc(ctx, op.Pinv, (size_t)LJ.n_patches * op.np_max * op.np_max);
+    dalloc(ctx, op.Pinvf, (size_t)LJ.n_patches * op.np_max * op.np_max);
+    CK(launch_condense(k, LJ, ctx->refk_dev.p, ctx->refk, prm->nu, per_cell ? LJ.cell_nu.p : nullptr,
+                       prm->beta, prm->gamma, forcing, conv_of(ctx), ctx->conv_t, op.A.p, op.Af.p, op.Fel.p,
+                       ctx->status_flag.p, RecoverArgs(), s));
+    CK(launch_patch_inverse(LJ, op, ctx->status_flag.p, s));
+    for (int l = 1; l < nl; ++l) CK(launch_transfer_H(ctx->L[l], ctx->status_flag.p, s));
+    ctx->n0 = 2 * ctx->L[0].n_int;
+    dalloc(ctx, ctx->coarse_inv, std::max<int64_t>(ctx->n0 * ctx->n0, 1));
+    CK(launch_coarse_inverse(ctx->L[0], ctx->coarse_inv.p, ctx->n0, ctx->status_flag.p, s));
+    ctx->small_Ls = small_levels(ctx);
+    if (ctx->small_Ls >= 1) {
+        ctx->small_smem_d = fill_small<double>(ctx, ctx->small_Ls);
+        ctx->small_smem_f = fill_small<float>(ctx, ctx->small_Ls);
+        if (ctx->small_smem_d > 200 * 1024) ctx->small_Ls = -1;
+    }
+    ctx->n_dof = LJ.n_int * op.dpf;
+    const int64_t nd = std::max<int64_t>(ctx->n_dof, 1);
+    dalloc(ctx, ctx->kr, nd); dalloc(ctx, ctx->ku, nd); dalloc(ctx, ctx->kt, nd);
+    dalloc(ctx, ctx->krf, nd); dalloc(ctx, ctx->kuf, nd); dalloc(ctx, ctx->kgf, nd);
+    check_flag(ctx, s);
+    ctx->condensed = true;
 }
 
 hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forcing, double *rhs_out,
@@ -753,16 +829,10 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
         CK(cudaSetDevice(ctx->device));
         cudaStream_t s = (cudaStream_t)stream;
         ctx->condensed = false;
-        drop_graph(ctx);
         ctx->prm = *prm;
-        const int k = prm->k;
-        upload_ref(ctx, ctx->ref0, ctx->ref0_dev, 0);
-        upload_ref(ctx, ctx->refk, ctx->refk_dev, k);
-        CK(cudaMemsetAsync(ctx->status_flag.p, 0, sizeof(int), s));
         const int nl = ctx->n_levels;
         // per-cell viscosity: the caller's on the finest level, child means below
-        const bool per_cell = prm->nu_elem != nullptr;
-        if (per_cell) {
+        if (prm->nu_elem) {
             DevLevel &F = ctx->L[nl - 1];
             dalloc(ctx, F.cell_nu, F.nc);
             CK(cudaMemcpyAsync(F.cell_nu.p, prm->nu_elem, sizeof(double) * F.nc, cudaMemcpyDeviceToDevice, s));
@@ -771,51 +841,19 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
                 CK(launch_nu_average(ctx->L[l], ctx->L[l].cell_nu.p, ctx->L[l - 1].cell_nu.p, s));
             }
         }
-        for (int l = 0; l < nl; ++l) {
-            DevLevel &L = ctx->L[l];
-            DevOperator &op = L.op0;
-            op.k = 0; op.dpf = 2; op.nloc = 6; op.np_max = L.pf_max * 2;
-            dalloc(ctx, op.A, 36 * L.nc);
-            dalloc(ctx, op.Af, 36 * L.nc);
-            dalloc(ctx, op.Pinv, (size_t)L.n_patches * op.np_max * op.np_max);
-            dalloc(ctx, op.Pinvf, (size_t)L.n_patches * op.np_max * op.np_max);
-            CK(launch_condense(0, L, ctx->ref0_dev.p, ctx->ref0, prm->nu, per_cell ? L.cell_nu.p : nullptr,
-                               prm->beta, prm->gamma, nullptr, op.A.p, op.Af.p, nullptr, ctx->status_flag.p,
-                               RecoverArgs(), s));
-            CK(launch_patch_inverse(L, op, ctx->status_flag.p, s));
+        // convecting field (Oseen): kept for the load, recovery and adjoint passes
+        ctx->has_conv = prm->conv != nullptr;
+        ctx->conv_t = 0;
+        if (ctx->has_conv) {
+            const size_t n = (size_t)ctx->L[nl - 1].nc * (prm->k + 2) * (prm->k + 3);
+            dalloc(ctx, ctx->conv_k, n);
+            CK(cudaMemcpyAsync(ctx->conv_k.p, prm->conv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         }
-        DevLevel &LJ = ctx->L[nl - 1];
-        DevOperator &op = ctx->opk;
-        op.k = k; op.dpf = 2 * (k + 1); op.nloc = 3 * op.dpf; op.np_max = LJ.pf_max * op.dpf;
-        dalloc(ctx, op.A, (size_t)op.nloc * op.nloc * LJ.nc);
-        dalloc(ctx, op.Af, (size_t)op.nloc * op.nloc * LJ.nc);
-        dalloc(ctx, op.Fel, (size_t)op.nloc * LJ.nc);
-        dalloc(ctx, op.Pinv, (size_t)LJ.n_patches * op.np_max * op.np_max);
-        dalloc(ctx, op.Pinvf, (size_t)LJ.n_patches * op.np_max * op.np_max);
-        CK(launch_condense(k, LJ, ctx->refk_dev.p, ctx->refk, prm->nu, per_cell ? LJ.cell_nu.p : nullptr,
-                           prm->beta, prm->gamma, forcing, op.A.p, op.Af.p, op.Fel.p, ctx->status_flag.p,
-                           RecoverArgs(), s));
-        CK(launch_patch_inverse(LJ, op, ctx->status_flag.p, s));
-        for (int l = 1; l < nl; ++l) CK(launch_transfer_H(ctx->L[l], ctx->status_flag.p, s));
-        ctx->n0 = 2 * ctx->L[0].n_int;
-        dalloc(ctx, ctx->coarse_inv, std::max<int64_t>(ctx->n0 * ctx->n0, 1));
-        CK(launch_coarse_inverse(ctx->L[0], ctx->coarse_inv.p, ctx->n0, ctx->status_flag.p, s));
-        ctx->small_Ls = small_levels(ctx);
-        if (ctx->small_Ls >= 1) {
-            ctx->small_smem_d = fill_small<double>(ctx, ctx->small_Ls);
-            ctx->small_smem_f = fill_small<float>(ctx, ctx->small_Ls);
-            if (ctx->small_smem_d > 200 * 1024) ctx->small_Ls = -1;
-        }
-        ctx->n_dof = LJ.n_int * op.dpf;
-        const int64_t nd = std::max<int64_t>(ctx->n_dof, 1);
-        dalloc(ctx, ctx->kr, nd); dalloc(ctx, ctx->ku, nd); dalloc(ctx, ctx->kt, nd);
-        dalloc(ctx, ctx->krf, nd); dalloc(ctx, ctx->kuf, nd); dalloc(ctx, ctx->kgf, nd);
+        condense_all(ctx, forcing, s);
         if (rhs_out) {
-            if (forcing) CK(launch_assemble_load(LJ, op, rhs_out, s));
+            if (forcing) CK(launch_assemble_load(ctx->L[nl - 1], ctx->opk, rhs_out, s));
             else CK(cudaMemsetAsync(rhs_out, 0, sizeof(double) * ctx->n_dof, s));
         }
-        check_flag(ctx, s);
-        ctx->condensed = true;
     });
 }
 
@@ -953,8 +991,8 @@ hdg_status hdg_get_element_matrices(hdg_ctx *ctx, int level, double *out, hdg_st
         REQUIRE(out, "null output");
         const DevOperator &op = level < 0 ? ctx->opk : ctx->L[level].op0;
         const int64_t nc = ctx->L[level < 0 ? ctx->n_levels - 1 : level].nc;
-        CK(cudaMemcpyAsync(out, op.A.p, sizeof(double) * op.nloc * op.nloc * nc, cudaMemcpyDeviceToDevice,
-                           (cudaStream_t)stream));
+        // the library keeps each A_K transposed; hand out the row-major A_K[p][q]
+        CK(launch_transpose_blocks(nc, op.nloc, op.A.p, out, (cudaStream_t)stream));
     });
 }
 
@@ -1025,14 +1063,32 @@ hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, con
         ensure_krylov(ctx, std::max(1, std::min(o.restart, 32)));
         const double Jval = device_sum(ctx, ctx->rec_j.p, nc, s);
         if (J) *J = Jval;
-        load_impl(ctx, ctx->rec_e.p, ctx->adj_F.p, s);
-        CK(cudaMemsetAsync(ctx->adj_u.p, 0, sizeof(double) * ctx->n_dof, s));
-        CK(cudaMemsetAsync(ctx->adj_p.p, 0, sizeof(double) * nc, s));
-        conv = uzawa_solve(ctx, ctx->adj_F.p, ctx->adj_u.p, ctx->adj_p.p, &o, loc, s);
-        // adjoint local fields, then the contractions
-        recover_impl(ctx, ctx->adj_u.p, ctx->rec_e.p, ctx->rec_La.p, ctx->rec_rt.p, nullptr, s);
-        CK(launch_adjoint_gradient(k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, Jl),
-                                   ctx->rec_L.p, ctx->rec_La.p, ctx->rec_rt.p, grad_nu, grad_forcing, s));
+        // Oseen: operators of the transposed convection for the adjoint system
+        const bool transposed = ctx->has_conv;
+        if (transposed) {
+            ctx->conv_t = 1;
+            condense_all(ctx, nullptr, s);
+        }
+        try {
+            load_impl(ctx, ctx->rec_e.p, ctx->adj_F.p, s);
+            CK(cudaMemsetAsync(ctx->adj_u.p, 0, sizeof(double) * ctx->n_dof, s));
+            CK(cudaMemsetAsync(ctx->adj_p.p, 0, sizeof(double) * nc, s));
+            conv = uzawa_solve(ctx, ctx->adj_F.p, ctx->adj_u.p, ctx->adj_p.p, &o, loc, s);
+            // adjoint local fields, then the contractions
+            recover_impl(ctx, ctx->adj_u.p, ctx->rec_e.p, ctx->rec_La.p, ctx->rec_rt.p, nullptr, s);
+            CK(launch_adjoint_gradient(k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, Jl),
+                                       ctx->rec_L.p, ctx->rec_La.p, ctx->rec_rt.p, grad_nu, grad_forcing, s));
+        } catch (...) {
+            if (transposed) {
+                ctx->conv_t = 0;
+                ctx->condensed = false;   // the primal operators are gone; hdg_condense again
+            }
+            throw;
+        }
+        if (transposed) {
+            ctx->conv_t = 0;
+            condense_all(ctx, nullptr, s);
+        }
         CK(cudaStreamSynchronize(s));
     });
     if (info) *info = loc;

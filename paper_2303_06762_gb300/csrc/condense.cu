@@ -15,7 +15,17 @@
 //     A_K = K_gg − K_gi Y_g + Wᵀ S_p⁻¹ W,
 //     F_K = F_g − K_gi Y_F + Wᵀ S_p⁻¹ D_oi Y_F,
 // and the augmented-Lagrangian term ε⁻¹|K|⁻¹ d dᵀ (eq. stALform; d = the
-// cell's flux functional) is added.  Facet unknowns are expressed in the
+// cell's flux functional) is added.
+// Oseen (Section 4.1): with a convecting field w_h the upwind form
+//     −(u, (w·∇)v)_K + ⟨(w·n)⁺ tng u + (w·n)⁻ tng û, tng(v − v̂)⟩_∂K
+// is added to K from point values (tables R9–R16; the facet switch is taken
+// at the Gauss–Legendre nodes).  K is then non-symmetric, the two
+// eliminations use LU without pivoting (K_ii and S_p have positive definite
+// symmetric parts), and with W₂ = K_gi Y_D − D_ogᵀ in place of Wᵀ:
+//     A_K = K_gg − K_gi Y_g + W₂ S_p⁻¹ W,   F_K = F_g − K_gi Y_F + W₂ S_p⁻¹ D_oi Y_F.
+// With conv_t the transposed convection block is used (the adjoint system).
+// Element matrices are stored transposed, A_K[q][p] = (A_K)_pq, so that the
+// row-gathering kernels read consecutive addresses.  Facet unknowns are expressed in the
 // global facet basis of include/hdg.h: the reference facet moments map to
 // the global ones by the factor sqrt|F|·σ·sgn(det J)·o^m (σ = n_F·n_K,
 // o = ±1 the orientation of the facet parameter).
@@ -60,6 +70,17 @@ struct Dims {
     static constexpr int O_XF = O_XG + NG;                // recovery: all (u, û) coefficients
     static constexpr int O_PO = O_XF + NCOL;              // recovery: mean-free pressure
     static constexpr int TOTAL = O_PO + NPO + 1;
+    // convection (only when a field is given)
+    static constexpr int NQ = (K + 5) * (K + 5);           // volume nodes
+    static constexpr int NFQ = (3 * K + 5) / 2;            // nodes per facet
+    static constexpr int O_W2 = TOTAL;                     // W2 (NPO x NG, stored [j][p])
+    static constexpr int O_WL = O_W2 + NPO * NG;           // lattice values of w
+    static constexpr int O_WH = O_WL + 2 * NLAT;           // J^{-1} w at volume nodes
+    static constexpr int O_GQ = O_WH + 2 * NQ;             // weight * (w^·∇^) phi^_i
+    static constexpr int O_HQ = O_GQ + NQ * NRT * 2;       // JᵀJ phi^_j
+    static constexpr int O_TAU = O_HQ + NQ * NRT * 2;      // tangential traces at facet nodes
+    static constexpr int O_AW = O_TAU + 3 * NFQ * NCOL;    // |F| weight (w·n_K) at facet nodes
+    static constexpr int TOTAL_CONV = O_AW + 3 * NFQ;
 };
 
 // geometry slots inside the O_GEO block
@@ -118,6 +139,36 @@ __device__ bool chol_serial(double *sm, int n, int ld) {
     return true;
 }
 
+// in-place LU factorisation without pivoting (unit lower L), serial; returns
+// false on a non-positive pivot (matrices with a positive definite symmetric
+// part have positive pivots)
+__device__ bool lu_serial(double *sm, int n, int ld) {
+    for (int j = 0; j < n; ++j) {
+        double d = sm[j * ld + j];
+        if (!(d > 0.0)) return false;
+        for (int i = j + 1; i < n; ++i) {
+            double l = sm[i * ld + j] / d;
+            sm[i * ld + j] = l;
+            for (int c = j + 1; c < n; ++c) sm[i * ld + c] -= l * sm[j * ld + c];
+        }
+    }
+    return true;
+}
+
+// solve (LU) x = b for column `col` of the row-major RHS block B (n x nb, ld ldb)
+__device__ void lu_solve_col(const double *LU, int n, int ld, double *B, int ldb, int col) {
+    for (int i = 0; i < n; ++i) {
+        double s = B[i * ldb + col];
+        for (int p = 0; p < i; ++p) s -= LU[i * ld + p] * B[p * ldb + col];
+        B[i * ldb + col] = s;
+    }
+    for (int i = n - 1; i >= 0; --i) {
+        double s = B[i * ldb + col];
+        for (int p = i + 1; p < n; ++p) s -= LU[i * ld + p] * B[p * ldb + col];
+        B[i * ldb + col] = s / LU[i * ld + i];
+    }
+}
+
 // solve L Lᵀ x = b for column `col` of the row-major RHS block B (n x nb, ld ldb)
 __device__ void chol_solve_col(const double *Lm, int n, int ld, double *B, int ldb, int col) {
     for (int i = 0; i < n; ++i) {
@@ -132,17 +183,124 @@ __device__ void chol_solve_col(const double *Lm, int n, int ld, double *B, int l
     }
 }
 
+struct RefPtrs {
+    const double *R[N_REF_TABLES];
+};
+
+// Upwind convection of Section 4.1 on the (u, û) block of K (rows = test
+// functions, columns = trial functions, the basis of Km), added to Km; with
+// conv_t its transpose is added instead.
+//   volume:  −(sc_i sc_j/|det J|) Σ_q ω_q (ŵ·∇̂ φ̂_i)ᵀ JᵀJ φ̂_j,   ŵ = J⁻¹ w
+//   facets:  |F| ω_g (w·n_K) at node g switches between the traces of u (w·n_K > 0)
+//            and û (w·n_K < 0); tangential traces t_F·φ_i = o sc_i t̂ᵀJᵀJ φ̂_i/(|F| det J)
+//            and, for û, o^m l_m(s_g)/sqrt|F|.
+template <int K>
+__device__ void convection_block(int64_t c, const double *__restrict__ conv, int conv_t, const RefPtrs &T,
+                                 const double *geo, const double *sc, double *Km, double *sm) {
+    using D = Dims<K>;
+    const double *__restrict__ R9 = T.R[8];
+    const double *__restrict__ R10 = T.R[9];
+    const double *__restrict__ R11 = T.R[10];
+    const double *__restrict__ R12 = T.R[11];
+    const double *__restrict__ R13 = T.R[12];
+    const double *__restrict__ R14 = T.R[13];
+    const double *__restrict__ R15 = T.R[14];
+    const double *__restrict__ R16 = T.R[15];
+    double *wl = sm + D::O_WL, *wh = sm + D::O_WH, *Gq = sm + D::O_GQ, *Hq = sm + D::O_HQ;
+    double *tau = sm + D::O_TAU, *aw = sm + D::O_AW;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int i = tid; i < 2 * D::NLAT; i += nt) wl[i] = conv[c * 2 * D::NLAT + i];
+    __syncthreads();
+    const double det = geo[G_DET], adet = fabs(det);
+    for (int q = tid; q < D::NQ; q += nt) {
+        double wx = 0.0, wy = 0.0;
+        for (int n = 0; n < D::NLAT; ++n) {
+            const double l = R11[q * D::NLAT + n];
+            wx += l * wl[2 * n];
+            wy += l * wl[2 * n + 1];
+        }
+        wh[2 * q] = geo[G_JI + 0] * wx + geo[G_JI + 1] * wy;
+        wh[2 * q + 1] = geo[G_JI + 2] * wx + geo[G_JI + 3] * wy;
+    }
+    for (int fg = tid; fg < 3 * D::NFQ; fg += nt) {
+        const int f = fg / D::NFQ, g = fg % D::NFQ;
+        double wx = 0.0, wy = 0.0;
+        for (int n = 0; n < D::NLAT; ++n) {
+            const double l = R14[fg * D::NLAT + n];
+            wx += l * wl[2 * n];
+            wy += l * wl[2 * n + 1];
+        }
+        aw[fg] = geo[G_LEN + f] * R16[g] * (wx * geo[G_NK + 2 * f] + wy * geo[G_NK + 2 * f + 1]);
+    }
+    __syncthreads();
+    double JtJ[4];
+    JtJ[0] = geo[G_J + 0] * geo[G_J + 0] + geo[G_J + 2] * geo[G_J + 2];
+    JtJ[1] = geo[G_J + 0] * geo[G_J + 1] + geo[G_J + 2] * geo[G_J + 3];
+    JtJ[2] = JtJ[1];
+    JtJ[3] = geo[G_J + 1] * geo[G_J + 1] + geo[G_J + 3] * geo[G_J + 3];
+    for (int idx = tid; idx < D::NQ * D::NRT * 2; idx += nt) {
+        const int a = idx & 1, qi = idx >> 1, q = qi / D::NRT;
+        const double *d = R10 + (size_t)idx * 2;
+        Gq[idx] = R12[q] * (wh[2 * q] * d[0] + wh[2 * q + 1] * d[1]);
+        const double *ph = R9 + (size_t)qi * 2;
+        Hq[idx] = JtJ[2 * a] * ph[0] + JtJ[2 * a + 1] * ph[1];
+    }
+    for (int idx = tid; idx < 3 * D::NFQ * D::NCOL; idx += nt) {
+        const int fg = idx / D::NCOL, col = idx % D::NCOL, f = fg / D::NFQ, g = fg % D::NFQ;
+        double v = 0.0;
+        if (col < D::NRT) {
+            const double *ph = R13 + ((size_t)fg * D::NRT + col) * 2;
+            // reference edge vector of facet f (from its lower to its higher local vertex)
+            const double tx = f == 0 ? -1.0 : (f == 1 ? 0.0 : 1.0);
+            const double ty = f == 2 ? 0.0 : 1.0;
+            const double j0 = JtJ[0] * ph[0] + JtJ[1] * ph[1], j1 = JtJ[2] * ph[0] + JtJ[3] * ph[1];
+            v = sc[col] * geo[G_O + f] / (geo[G_LEN + f] * det) * (tx * j0 + ty * j1);
+        } else {
+            const int h = col - D::NRT, f2 = h / D::NF, m = h % D::NF;
+            if (f2 == f) v = ((m & 1) ? geo[G_O + f] : 1.0) * R15[g * D::NF + m] / sqrt(geo[G_LEN + f]);
+        }
+        tau[idx] = v;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < D::NCOL * D::NCOL; idx += nt) {
+        const int r = idx / D::NCOL, s2 = idx % D::NCOL;
+        const int i = conv_t ? s2 : r, j = conv_t ? r : s2;
+        double v = 0.0;
+        if (i < D::NRT && j < D::NRT) {
+            double acc = 0.0;
+            for (int q = 0; q < D::NQ; ++q) {
+                const double *gi = Gq + (q * D::NRT + i) * 2, *hj = Hq + (q * D::NRT + j) * 2;
+                acc += gi[0] * hj[0] + gi[1] * hj[1];
+            }
+            v = -sc[i] * sc[j] / adet * acc;
+        }
+        for (int fg = 0; fg < 3 * D::NFQ; ++fg) {
+            const double a = aw[fg];
+            const double ap = a > 0.0 ? a : 0.0, am = a < 0.0 ? a : 0.0;
+            const double coef = i < D::NRT ? (j < D::NRT ? ap : am) : (j < D::NRT ? -ap : -am);
+            v += coef * tau[fg * D::NCOL + i] * tau[fg * D::NCOL + j];
+        }
+        Km[idx] += v;
+    }
+    __syncthreads();
+}
+
 template <int K>
 __global__ void __launch_bounds__(128)
 condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__restrict__ cells,
-                const double *__restrict__ R1, const double *__restrict__ R2,
-                const double *__restrict__ R3, const double *__restrict__ R4,
-                const double *__restrict__ R5, const double *__restrict__ R6,
-                const double *__restrict__ R7, double nu_scalar, const double *__restrict__ nu_cell,
+                RefPtrs T, double nu_scalar, const double *__restrict__ nu_cell,
                 double beta, double gamma, const double *__restrict__ forcing,
+                const double *__restrict__ conv, int conv_t,
                 double *__restrict__ Aout, float *__restrict__ Afout, double *__restrict__ Fout,
                 int *flag, RecoverArgs rec) {
     using D = Dims<K>;
+    const double *__restrict__ R1 = T.R[0];
+    const double *__restrict__ R2 = T.R[1];
+    const double *__restrict__ R3 = T.R[2];
+    const double *__restrict__ R4 = T.R[3];
+    const double *__restrict__ R5 = T.R[4];
+    const double *__restrict__ R6 = T.R[5];
+    const double *__restrict__ R7 = T.R[6];
     extern __shared__ double sm[];
     double *geo = sm + D::O_GEO;
     double *sc = sm + D::O_S;
@@ -159,6 +317,7 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
     double *xg = sm + D::O_XG;
     double *xf = sm + D::O_XF;
     double *po = sm + D::O_PO;
+    double *W2 = sm + D::O_W2;
     const int tid = threadIdx.x, nt = blockDim.x;
     __shared__ int s_ok;
 
@@ -257,6 +416,7 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
             }
         }
         __syncthreads();
+        if (conv) convection_block<K>(c, conv, conv_t, T, geo, sc, Km, sm);
         // global column of output unknown o: facet f, t = normal/tangential, m
         auto gcol = [&](int o) {
             int f = o / (2 * D::NF), t = (o / D::NF) & 1, m = o % D::NF;
@@ -276,9 +436,12 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
                 Y[idx] = v;
             }
             __syncthreads();
-            if (tid == 0 && !chol_serial(Lii, D::NRI, D::NRI)) s_ok = 0;
+            if (tid == 0 && !(conv ? lu_serial(Lii, D::NRI, D::NRI) : chol_serial(Lii, D::NRI, D::NRI))) s_ok = 0;
             __syncthreads();
-            for (int col = tid; col < D::NY; col += nt) chol_solve_col(Lii, D::NRI, D::NRI, Y, D::NY, col);
+            for (int col = tid; col < D::NY; col += nt) {
+                if (conv) lu_solve_col(Lii, D::NRI, D::NRI, Y, D::NY, col);
+                else chol_solve_col(Lii, D::NRI, D::NRI, Y, D::NY, col);
+            }
             __syncthreads();
             // S_p, W, v
             for (int idx = tid; idx < D::NPO * D::NPO; idx += nt) {
@@ -301,10 +464,22 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
                 }
                 Zm[j * (D::NG + 1) + col] = s;
             }
+            if (conv)   // W2 = K_gi Y_D - D_ogᵀ, stored [j][p]
+                for (int idx = tid; idx < D::NPO * D::NG; idx += nt) {
+                    int j = idx / D::NG, p = idx % D::NG;
+                    int gp = gcol(p);
+                    double s = 0.0;
+                    for (int r = 0; r < D::NRI; ++r) s += Km[gp * D::NCOL + 3 * D::NF + r] * Y[r * D::NY + D::NG + j];
+                    if (gp < D::NRT) s -= Dm[gp * D::NPK + j + 1];
+                    W2[idx] = s;
+                }
             __syncthreads();
-            if (tid == 0 && !chol_serial(Sp, D::NPO, D::NPO)) s_ok = 0;
+            if (tid == 0 && !(conv ? lu_serial(Sp, D::NPO, D::NPO) : chol_serial(Sp, D::NPO, D::NPO))) s_ok = 0;
             __syncthreads();
-            for (int col = tid; col < D::NG + 1; col += nt) chol_solve_col(Sp, D::NPO, D::NPO, Zm, D::NG + 1, col);
+            for (int col = tid; col < D::NG + 1; col += nt) {
+                if (conv) lu_solve_col(Sp, D::NPO, D::NPO, Zm, D::NG + 1, col);
+                else chol_solve_col(Sp, D::NPO, D::NPO, Zm, D::NG + 1, col);
+            }
             __syncthreads();
         }
         if (rec.x) {
@@ -362,13 +537,14 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
         }
         // A = K_gg − K_gi Y_g + Wᵀ Z_W (+ AL),  F = F_g − K_gi Y_F + Wᵀ Z_v
         const double al = eps_inv / geo[G_AREA];
+        const double *Wl = conv ? W2 : Wm;     // [j][p]: Wᵀ (symmetric K) or W2
         if (Aout)
         for (int idx = tid; idx < D::NG * D::NG; idx += nt) {
-            int p = idx / D::NG, q = idx % D::NG;
+            int q = idx / D::NG, p = idx % D::NG;    // stored transposed: A[q][p] = A_pq
             int gp = gcol(p), gq = gcol(q);
             double s = Km[gp * D::NCOL + gq];
             for (int r = 0; r < D::NRI; ++r) s -= Km[gp * D::NCOL + 3 * D::NF + r] * Y[r * D::NY + q];
-            for (int j = 0; j < D::NPO; ++j) s += Wm[j * D::NG + p] * Zm[j * (D::NG + 1) + q];
+            for (int j = 0; j < D::NPO; ++j) s += Wl[j * D::NG + p] * Zm[j * (D::NG + 1) + q];
             int fp = p / (2 * D::NF), fq = q / (2 * D::NF);
             if (p % (2 * D::NF) == 0 && q % (2 * D::NF) == 0)
                 s += al * geo[G_SIG + fp] * sqrt(geo[G_LEN + fp]) * geo[G_SIG + fq] * sqrt(geo[G_LEN + fq]);
@@ -381,7 +557,7 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
                 double s = gp < D::NRT ? Fl[gp] : 0.0;
                 for (int r = 0; r < D::NRI; ++r)
                     s -= Km[gp * D::NCOL + 3 * D::NF + r] * Y[r * D::NY + D::NG + D::NPO];
-                for (int j = 0; j < D::NPO; ++j) s += Wm[j * D::NG + p] * Zm[j * (D::NG + 1) + D::NG];
+                for (int j = 0; j < D::NPO; ++j) s += Wl[j * D::NG + p] * Zm[j * (D::NG + 1) + D::NG];
                 Fout[c * D::NG + p] = s;
             }
         __syncthreads();
@@ -393,27 +569,29 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
 template <int K>
 cudaError_t launch_condense_k(const DevLevel &L, const double *ref, const RefTables &rt, double nu,
                               const double *nu_cell, double beta, double gamma, const double *forcing,
-                              double *A, float *Af, double *Fel, int *flag, const RecoverArgs &rec,
-                              cudaStream_t s) {
+                              const double *conv, int conv_t, double *A, float *Af, double *Fel, int *flag,
+                              const RecoverArgs &rec, cudaStream_t s) {
     using D = Dims<K>;
-    size_t smem = sizeof(double) * D::TOTAL;
+    if (conv && (rt.nq != D::NQ || rt.nfq != D::NFQ)) return cudaErrorInvalidValue;
+    size_t smem = sizeof(double) * (conv ? D::TOTAL_CONV : D::TOTAL);
     auto kern = condense_kernel<K>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(double) * D::TOTAL_CONV));
     if (e != cudaSuccess) return e;
-    const double *R[7];
-    for (int i = 0; i < 7; ++i) R[i] = ref + ref_table_offset(rt, i);
+    RefPtrs T;
+    for (int i = 0; i < N_REF_TABLES; ++i) T.R[i] = ref + ref_table_offset(rt, i);
     int64_t grid = L.nc < 152 * 64 ? L.nc : 152 * 64;
     if (grid < 1) return cudaSuccess;
     note_launches(1);
-    kern<<<(unsigned)grid, 128, smem, s>>>(L.nc, L.coords.p, L.cells.p, R[0], R[1], R[2], R[3], R[4],
-                                           R[5], R[6], nu, nu_cell, beta, gamma, forcing, A, Af, Fel,
-                                           flag, rec);
+    kern<<<(unsigned)grid, 128, smem, s>>>(L.nc, L.coords.p, L.cells.p, T, nu, nu_cell, beta, gamma, forcing,
+                                           conv, conv_t, A, Af, Fel, flag, rec);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ patch inverses
 // Patch matrix A_ss assembled from the cells of the vertex star (slots = patch
-// facets), then inverted by Gauss-Jordan without pivoting (A_ss is SPD).
+// facets), then inverted by Gauss-Jordan without pivoting (A_ss is SPD for
+// Stokes and has a positive definite symmetric part for Oseen).
 __global__ void patch_inverse_kernel(int n_patches, int pf_max, int pc_max, int dpf, int nloc,
                                      int np_max, const int *__restrict__ patch_nf,
                                      const int *__restrict__ patch_nc,
@@ -448,7 +626,7 @@ __global__ void patch_inverse_kernel(int n_patches, int pf_max, int pc_max, int 
             int l1 = lfmap[si * pf_max + j1], l2 = lfmap[si * pf_max + j2];
             if (l1 < 0 || l2 < 0) continue;
             int c = patch_cells[(size_t)p * pc_max + si];
-            s += A[(size_t)c * nloc * nloc + (l1 * dpf + d1) * nloc + l2 * dpf + d2];
+            s += A[(size_t)c * nloc * nloc + (l2 * dpf + d2) * nloc + l1 * dpf + d1];
         }
         M[P * np + Q] = s;
     }
@@ -478,8 +656,9 @@ __global__ void patch_inverse_kernel(int n_patches, int pf_max, int pc_max, int 
         }
     }
     __syncthreads();
+    // stored transposed, Pinv[j][i] = (A_ss^{-1})_ij, for the column-reading smoother
     for (int idx = tid; idx < np_max * np_max; idx += nt) {
-        int i = idx / np_max, j = idx % np_max;
+        int j = idx / np_max, i = idx % np_max;
         double v = (i < np && j < np) ? M[i * np + j] : 0.0;
         Pinv[(size_t)p * np_max * np_max + idx] = v;
         if (Pinvf) Pinvf[(size_t)p * np_max * np_max + idx] = (float)v;
@@ -507,25 +686,23 @@ __global__ void transfer_H_kernel(int64_t ncc, const int *__restrict__ children,
             for (int l2 = 0; l2 < 3; ++l2) {
                 int s2 = child_slot[12 * P + 3 * ch + l2];
                 for (int a = 0; a < 2; ++a)
-                    for (int b = 0; b < 2; ++b) M[2 * s1 + a][2 * s2 + b] += Ac[(2 * l1 + a) * 6 + 2 * l2 + b];
+                    for (int b = 0; b < 2; ++b) M[2 * s1 + a][2 * s2 + b] += Ac[(2 * l2 + b) * 6 + 2 * l1 + a];
             }
         }
     }
-    // Cholesky of A_TT (rows/cols 12..17)
+    // LU of A_TT (rows/cols 12..17) without pivoting: SPD for Stokes, positive
+    // definite symmetric part for Oseen
     double Lm[6][6];
     bool ok = true;
     for (int i = 0; i < 6; ++i)
         for (int j = 0; j < 6; ++j) Lm[i][j] = M[12 + i][12 + j];
     for (int j = 0; j < 6; ++j) {
         double d = Lm[j][j];
-        for (int p = 0; p < j; ++p) d -= Lm[j][p] * Lm[j][p];
-        if (!(d > 0.0)) { ok = false; d = 1.0; }
-        d = sqrt(d);
-        Lm[j][j] = d;
+        if (!(d > 0.0)) { ok = false; d = 1.0; Lm[j][j] = 1.0; }
         for (int i = j + 1; i < 6; ++i) {
-            double s = Lm[i][j];
-            for (int p = 0; p < j; ++p) s -= Lm[i][p] * Lm[j][p];
-            Lm[i][j] = s / d;
+            double l = Lm[i][j] / d;
+            Lm[i][j] = l;
+            for (int c2 = j + 1; c2 < 6; ++c2) Lm[i][c2] -= l * Lm[j][c2];
         }
     }
     for (int col = 0; col < 12; ++col) {
@@ -536,11 +713,11 @@ __global__ void transfer_H_kernel(int64_t ncc, const int *__restrict__ children,
         for (int i = 0; i < 6; ++i) {
             double v = x[i];
             for (int p = 0; p < i; ++p) v -= Lm[i][p] * x[p];
-            x[i] = v / Lm[i][i];
+            x[i] = v;
         }
         for (int i = 5; i >= 0; --i) {
             double v = x[i];
-            for (int p = i + 1; p < 6; ++p) v -= Lm[p][i] * x[p];
+            for (int p = i + 1; p < 6; ++p) v -= Lm[i][p] * x[p];
             x[i] = v / Lm[i][i];
         }
         for (int i = 0; i < 6; ++i) {
@@ -568,7 +745,7 @@ __global__ void coarse_assemble_kernel(int64_t n_int, const int *__restrict__ fa
         for (int col = 0; col < 6; ++col) {
             int jf = cell_int[3 * c + col / 2];
             if (jf < 0) continue;
-            Mr[2 * jf + col % 2] += A0[(size_t)c * 36 + (2 * lf + d) * 6 + col];
+            Mr[2 * jf + col % 2] += A0[(size_t)c * 36 + col * 6 + 2 * lf + d];
         }
     }
 }
@@ -626,6 +803,97 @@ __global__ void assemble_load_kernel(int64_t n_int, int dpf, const int *__restri
 }
 
 unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
+
+// ------------------------------------------------------------------ convecting field per level
+// Lowest-order levels carry the RT_0 field whose facet fluxes are those of the
+// finest field (mean of the two sides), summed over the two fine halves of
+// every coarse facet; it is handed to the condensation as values at the cell
+// vertices (the degree-1 lattice).
+
+// outward flux ∫_{F_f} w·n_K of the lattice field through each local facet
+__global__ void conv_flux_kernel(int64_t nc, const double *__restrict__ coords, const int *__restrict__ cells,
+                                 int nlat, int nfq, const double *__restrict__ R14, const double *__restrict__ R16,
+                                 const double *__restrict__ conv, double *__restrict__ flux) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    double geo[64];
+    cell_geometry(coords, cells, c, geo);
+    const double *w = conv + c * 2 * nlat;
+    for (int f = 0; f < 3; ++f) {
+        double s = 0.0;
+        for (int g = 0; g < nfq; ++g) {
+            double wx = 0.0, wy = 0.0;
+            for (int n = 0; n < nlat; ++n) {
+                const double l = R14[(f * nfq + g) * nlat + n];
+                wx += l * w[2 * n];
+                wy += l * w[2 * n + 1];
+            }
+            s += R16[g] * (wx * geo[G_NK + 2 * f] + wy * geo[G_NK + 2 * f + 1]);
+        }
+        flux[3 * c + f] = geo[G_LEN + f] * s;
+    }
+}
+
+// both sides of an interior facet take the mean of their (opposite) fluxes
+__global__ void flux_consistent_kernel(int64_t n_int, const int *__restrict__ facet_adj, double *__restrict__ flux) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_int) return;
+    const int a0 = facet_adj[2 * i], a1 = facet_adj[2 * i + 1];
+    if (a0 < 0 || a1 < 0) return;
+    const int64_t e0 = 3 * (int64_t)(a0 >> 2) + (a0 & 3), e1 = 3 * (int64_t)(a1 >> 2) + (a1 & 3);
+    const double v = 0.5 * (flux[e0] - flux[e1]);
+    flux[e0] = v;
+    flux[e1] = -v;
+}
+
+// coarse outward flux through local facet f = sum over the fine facets in slots 2f, 2f+1
+__global__ void flux_restrict_kernel(int64_t ncc, const int *__restrict__ children,
+                                     const int *__restrict__ child_slot, const double *__restrict__ ff,
+                                     double *__restrict__ fc) {
+    int64_t P = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (P >= ncc) return;
+    double s[3] = {0.0, 0.0, 0.0};
+    for (int ch = 0; ch < 4; ++ch) {
+        const int64_t c = children[4 * P + ch];
+        for (int lf = 0; lf < 3; ++lf) {
+            const int slot = child_slot[12 * P + 3 * ch + lf];
+            if (slot >= 0 && slot < 6) s[slot / 2] += ff[3 * c + lf];
+        }
+    }
+    for (int f = 0; f < 3; ++f) fc[3 * P + f] = s[f];
+}
+
+// RT_0 field with outward fluxes Φ_f at the vertices: w(X_v) = Σ_{f≠v} Φ_f (X_v − X_f) / (2|K|)
+__global__ void rt0_vertex_kernel(int64_t nc, const double *__restrict__ coords, const int *__restrict__ cells,
+                                  const double *__restrict__ flux, double *__restrict__ out) {
+    int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    double X[3][2];
+    for (int i = 0; i < 3; ++i) {
+        const int v = cells[3 * c + i];
+        X[i][0] = coords[2 * v];
+        X[i][1] = coords[2 * v + 1];
+    }
+    const double det = (X[1][0] - X[0][0]) * (X[2][1] - X[0][1]) - (X[2][0] - X[0][0]) * (X[1][1] - X[0][1]);
+    const double two_area = fabs(det);
+    for (int v = 0; v < 3; ++v)
+        for (int d = 0; d < 2; ++d) {
+            double s = 0.0;
+            for (int f = 0; f < 3; ++f)
+                if (f != v) s += flux[3 * c + f] * (X[v][d] - X[f][d]);
+            out[6 * c + 2 * v + d] = s / two_area;
+        }
+}
+
+// out[b][i][j] = in[b][j][i] for nblk square blocks of size n
+__global__ void transpose_blocks_kernel(int64_t nblk, int n, const double *__restrict__ in, double *__restrict__ out) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t nn = (int64_t)n * n;
+    if (idx >= nblk * nn) return;
+    const int64_t b = idx / nn;
+    const int r = (int)(idx - b * nn), i = r / n, j = r % n;
+    out[idx] = in[b * nn + (int64_t)j * n + i];
+}
 
 // coarse-cell viscosity = mean over its four children (equal areas under red refinement)
 __global__ void nu_average_kernel(int64_t ncc, const int *__restrict__ children, const double *__restrict__ nu_f,
@@ -735,14 +1003,19 @@ cudaError_t launch_objective(int k, const DevLevel &L, const double *ref, const 
 
 cudaError_t launch_condense(int k, const DevLevel &L, const double *ref, const RefTables &rt, double nu,
                             const double *nu_cell, double beta, double gamma, const double *forcing,
-                            double *A, float *Af, double *Fel, int *flag, const RecoverArgs &rec,
-                            cudaStream_t s) {
+                            const double *conv, int conv_t, double *A, float *Af, double *Fel, int *flag,
+                            const RecoverArgs &rec, cudaStream_t s) {
     switch (k) {
-    case 0: return launch_condense_k<0>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, A, Af, Fel, flag, rec, s);
-    case 1: return launch_condense_k<1>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, A, Af, Fel, flag, rec, s);
-    case 2: return launch_condense_k<2>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, A, Af, Fel, flag, rec, s);
-    case 3: return launch_condense_k<3>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, A, Af, Fel, flag, rec, s);
-    case 4: return launch_condense_k<4>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, A, Af, Fel, flag, rec, s);
+#define HDG_CONDENSE_CASE(KK)                                                                         \
+    case KK:                                                                                          \
+        return launch_condense_k<KK>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, conv, conv_t, A, Af, \
+                                     Fel, flag, rec, s);
+        HDG_CONDENSE_CASE(0)
+        HDG_CONDENSE_CASE(1)
+        HDG_CONDENSE_CASE(2)
+        HDG_CONDENSE_CASE(3)
+        HDG_CONDENSE_CASE(4)
+#undef HDG_CONDENSE_CASE
     default: return cudaErrorInvalidValue;
     }
 }
@@ -805,6 +1078,40 @@ cudaError_t launch_assemble_load(const DevLevel &L, const DevOperator &op, doubl
     if (n == 0) return cudaSuccess;
     note_launches(1);
     assemble_load_kernel<<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, op.dpf, L.facet_adj.p, op.Fel.p, F);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_conv_flux(const DevLevel &L, const double *ref, const RefTables &rt, const double *conv,
+                             double *flux, cudaStream_t s) {
+    if (L.nc == 0) return cudaSuccess;
+    note_launches(L.n_int > 0 ? 2 : 1);
+    conv_flux_kernel<<<blocks_for(L.nc, 128), 128, 0, s>>>(L.nc, L.coords.p, L.cells.p, rt.nlat, rt.nfq,
+                                                           ref + ref_table_offset(rt, 13),
+                                                           ref + ref_table_offset(rt, 15), conv, flux);
+    if (L.n_int > 0) flux_consistent_kernel<<<blocks_for(L.n_int, 256), 256, 0, s>>>(L.n_int, L.facet_adj.p, flux);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_flux_restrict(const DevLevel &fine, const double *ff, double *fc, cudaStream_t s) {
+    if (fine.nc_coarse == 0) return cudaSuccess;
+    note_launches(1);
+    flux_restrict_kernel<<<blocks_for(fine.nc_coarse, 128), 128, 0, s>>>(fine.nc_coarse, fine.tr_children.p,
+                                                                         fine.tr_child_slot.p, ff, fc);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rt0_vertex(const DevLevel &L, const double *flux, double *out, cudaStream_t s) {
+    if (L.nc == 0) return cudaSuccess;
+    note_launches(1);
+    rt0_vertex_kernel<<<blocks_for(L.nc, 128), 128, 0, s>>>(L.nc, L.coords.p, L.cells.p, flux, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_transpose_blocks(int64_t nblk, int n, const double *in, double *out, cudaStream_t s) {
+    const int64_t total = nblk * (int64_t)n * n;
+    if (total == 0) return cudaSuccess;
+    note_launches(1);
+    transpose_blocks_kernel<<<blocks_for(total, 256), 256, 0, s>>>(nblk, n, in, out);
     return cudaGetLastError();
 }
 

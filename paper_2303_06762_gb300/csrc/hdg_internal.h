@@ -62,9 +62,12 @@ struct HostTransfer {
 
 // reference-element tables for order k (FP64), see reference.cpp
 struct RefTables {
-    int k = -1, npk = 0, nrt = 0, nf = 0, nlat = 0;
+    int k = -1, npk = 0, nrt = 0, nf = 0, nlat = 0, nq = 0, nfq = 0;
     std::vector<double> R1, R2, R3, R4, R5, R6, R7, R8;
+    // point values for the upwind convection (reference.cpp)
+    std::vector<double> R9, R10, R11, R12, R13, R14, R15, R16;
 };
+constexpr int N_REF_TABLES = 16;
 
 // layout of the small Krylov block (restart R):
 //   H: (R+1) x R column-major at 0; cs, sn: R; g: R+1; y: R; h1, h2: R+1; nrm2, res, hn
@@ -146,6 +149,8 @@ struct DevLevel {
     DBuf<double> cell_d;       // nc*3 flux weights sigma*sqrt|F| of each local facet
     DBuf<double> cell_nu;      // nc per-cell viscosity (when the caller gives one)
     DBuf<double> cell_area;    // nc
+    DBuf<double> conv_flux;    // nc*3 outward fluxes of the convecting field (Oseen)
+    DBuf<double> conv_lat;     // nc*3*2 lowest-order convecting field at the vertices
     // patches
     int n_patches = 0, n_colours = 0, pf_max = 0, pc_max = 0;
     std::vector<int32_t> colour_ptr;
@@ -174,6 +179,9 @@ struct hdg_ctx {
     std::vector<hdg::DevLevel> L;
     bool condensed = false;
     hdg_params prm{};
+    bool has_conv = false;                   // Oseen: convecting field given
+    int conv_t = 0;                          // operators built from the transposed convection
+    hdg::DBuf<double> conv_k;                // finest convecting field, lattice layout (copy)
     hdg::RefTables refk, ref0;
     hdg::DBuf<double> refk_dev, ref0_dev;   // packed R1..R6
     hdg::DevOperator opk;                    // order-k operator on the finest mesh
@@ -213,17 +221,25 @@ unsigned long long launch_count();
 
 // reference.cpp
 void build_reference_tables(int k, RefTables &out);
-size_t ref_table_offset(const RefTables &t, int which);   // offset of R1..R8 in packed buffer
+size_t ref_table_offset(const RefTables &t, int which);   // offset of R1..R16 in packed buffer
+const std::vector<double> *ref_table(const RefTables &t, int which);   // R(which+1)
 
 // topology.cpp
 std::string build_level_topology(HostLevel &L, const int32_t *colour_or_null);
 std::string build_transfer(const HostLevel &coarse, const HostLevel &fine, HostTransfer &T);
 
 // kernels: condensation and setup (condense.cu)
+// conv: lattice values of the convecting field (NULL = Stokes); conv_t: use the
+// transposed convection block (adjoint system)
 cudaError_t launch_condense(int k, const DevLevel &L, const double *ref, const RefTables &rt,
                             double nu, const double *nu_cell, double beta, double gamma,
-                            const double *forcing, double *A, float *Af, double *Fel, int *flag,
-                            const RecoverArgs &rec, cudaStream_t s);
+                            const double *forcing, const double *conv, int conv_t, double *A, float *Af,
+                            double *Fel, int *flag, const RecoverArgs &rec, cudaStream_t s);
+cudaError_t launch_conv_flux(const DevLevel &L, const double *ref, const RefTables &rt, const double *conv,
+                             double *flux, cudaStream_t s);
+cudaError_t launch_flux_restrict(const DevLevel &fine, const double *ff, double *fc, cudaStream_t s);
+cudaError_t launch_rt0_vertex(const DevLevel &L, const double *flux, double *out, cudaStream_t s);
+cudaError_t launch_transpose_blocks(int64_t nblk, int n, const double *in, double *out, cudaStream_t s);
 cudaError_t launch_patch_inverse(const DevLevel &L, const DevOperator &op, int *flag, cudaStream_t s);
 cudaError_t launch_transfer_H(const DevLevel &fine, int *flag, cudaStream_t s);
 cudaError_t launch_coarse_inverse(const DevLevel &L0, double *inv, int64_t n, int *flag,

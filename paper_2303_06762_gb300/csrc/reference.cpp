@@ -23,6 +23,14 @@
 //   R2[f][i][a][j] = ∫_{F^_f} phi_{i,a} g_j ds^   R5[i][j] = ∫ div phi_i g_j
 //   R3[f][j][m]    = ∫_0^1 g_j(x_f(s)) l_m(s) ds  R6[i][a][n] = ∫ phi_{i,a} lam_n
 //   R7[i][a][n]    = phi_{i,a} at lattice point n  R8[n][n'] = ∫ lam_n lam_n'
+// Point values for the upwind convection of Section 4.1 (its facet switch is
+// pointwise, so the device evaluates it at fixed nodes):
+//   R9[q][i][a]  = phi_{i,a}(x_q)                  R10[q][i][a][b] = d_b phi_{i,a}(x_q)
+//   R11[q][n]    = lam_n(x_q)                      R12[q] = weight of node x_q
+//   R13[f][g][i][a] = phi_{i,a}(x_f(s_g))          R14[f][g][n] = lam_n(x_f(s_g))
+//   R15[g][m]    = l_m(s_g)                        R16[g] = weight of s_g on [0,1]
+// with the volume nodes of the Duffy rule above and nfq = (3k+5)/2 Gauss-Legendre
+// nodes s_g per facet (exact for the facet terms away from a switch, degree 3k+3).
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -387,6 +395,17 @@ void build_reference_tables(int k, RefTables &t) {
     t.R6.assign((size_t)nrt * 2 * nlat, 0.0);
     t.R7.assign((size_t)nrt * 2 * nlat, 0.0);
     t.R8.assign((size_t)nlat * nlat, 0.0);
+    const int nfq = (3 * k + 5) / 2;
+    t.nq = nq;
+    t.nfq = nfq;
+    t.R9.assign((size_t)nq * nrt * 2, 0.0);
+    t.R10.assign((size_t)nq * nrt * 4, 0.0);
+    t.R11.assign((size_t)nq * nlat, 0.0);
+    t.R12.assign((size_t)nq, 0.0);
+    t.R13.assign((size_t)3 * nfq * nrt * 2, 0.0);
+    t.R14.assign((size_t)3 * nfq * nlat, 0.0);
+    t.R15.assign((size_t)nfq * nf, 0.0);
+    t.R16.assign((size_t)nfq, 0.0);
     {
         int pidx = 0;
         for (int a2 = 0; a2 <= q; ++a2)
@@ -407,6 +426,13 @@ void build_reference_tables(int k, RefTables &t) {
                 for (int b = 0; b < 2; ++b) dv[(2 * i + a) * 2 + b] = phi_der(i, a, b, dxp, dyp);
             }
         const double wq = QW[p];
+        for (int i = 0; i < nrt; ++i)
+            for (int a = 0; a < 2; ++a) {
+                t.R9[((size_t)p * nrt + i) * 2 + a] = pv[2 * i + a];
+                for (int b = 0; b < 2; ++b) t.R10[(((size_t)p * nrt + i) * 2 + a) * 2 + b] = dv[(2 * i + a) * 2 + b];
+            }
+        for (int nn = 0; nn < nlat; ++nn) t.R11[(size_t)p * nlat + nn] = lv[nn];
+        t.R12[p] = wq;
         for (int i = 0; i < nrt; ++i) {
             for (int a = 0; a < 2; ++a)
                 for (int b = 0; b < 2; ++b)
@@ -437,12 +463,34 @@ void build_reference_tables(int k, RefTables &t) {
                 for (int m = 0; m < nf; ++m) t.R3[(f * npk + j) * nf + m] += gw[p] * gj * leg(m, gx[p]);
             }
         }
+    {
+        std::vector<double> fx, fw;
+        gauss_legendre01(nfq, fx, fw);
+        for (int g = 0; g < nfq; ++g) {
+            t.R16[g] = fw[g];
+            for (int m = 0; m < nf; ++m) t.R15[g * nf + m] = leg(m, fx[g]);
+            for (int f = 0; f < 3; ++f) {
+                double x = FVX[f][0][0] + fx[g] * (FVX[f][1][0] - FVX[f][0][0]);
+                double y = FVX[f][0][1] + fx[g] * (FVX[f][1][1] - FVX[f][0][1]);
+                mono_at(x, y, mv, mdx, mdy);
+                for (int i = 0; i < nrt; ++i)
+                    for (int a = 0; a < 2; ++a)
+                        t.R13[(((size_t)f * nfq + g) * nrt + i) * 2 + a] = phi_val(i, a, mv);
+                for (int nn = 0; nn < nlat; ++nn) t.R14[((size_t)f * nfq + g) * nlat + nn] = lam_val(nn, mv);
+            }
+        }
+    }
+}
+
+const std::vector<double> *ref_table(const RefTables &t, int which) {
+    const std::vector<double> *tabs[16] = {&t.R1,  &t.R2,  &t.R3,  &t.R4,  &t.R5,  &t.R6,  &t.R7,  &t.R8,
+                                           &t.R9,  &t.R10, &t.R11, &t.R12, &t.R13, &t.R14, &t.R15, &t.R16};
+    return tabs[which];
 }
 
 size_t ref_table_offset(const RefTables &t, int which) {
     size_t off = 0;
-    const std::vector<double> *tabs[8] = {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6, &t.R7, &t.R8};
-    for (int i = 0; i < which; ++i) off += tabs[i]->size();
+    for (int i = 0; i < which; ++i) off += ref_table(t, i)->size();
     return off;
 }
 
