@@ -244,6 +244,29 @@ hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, con
                        double *grad_forcing, double *grad_nu, double *J, const hdg_solve_opts *opts,
                        hdg_solve_info *info, hdg_stream_t stream);
 
+/* Multi-right-hand-side (batched) forms: nrhs systems with the one condensed
+ * operator of the last hdg_condense (several loads on one mesh).  Vectors are
+ * right-hand-side major, x[r * n + i] for r < nrhs (1 <= nrhs <= 64), device
+ * FP64, n = n_dof (pressures: n = n_cells).  Internally the columns are
+ * interleaved row by row, with nrhs padded to a power of two by zero columns,
+ * so that every element-matrix and patch-inverse entry read from memory serves
+ * all columns; each column keeps its own FGMRES least-squares problem,
+ * tolerances and Uzawa stopping decisions, exactly as hdg_solve applies them
+ * to one load.  Results match nrhs calls of the single forms up to rounding. */
+#define HDG_MAX_NRHS 64
+
+/* Y = A^eps X. */
+hdg_status hdg_apply_multi(hdg_ctx *ctx, int nrhs, const double *x, double *y, hdg_stream_t stream);
+
+/* Z = MG_hp(R) column by column, in the precision chosen at hdg_condense. */
+hdg_status hdg_precond_apply_multi(hdg_ctx *ctx, int nrhs, const double *r, double *z, hdg_stream_t stream);
+
+/* hdg_solve for nrhs loads F[r] at once; u, p are initial guesses in and
+ * solutions out; info: host array [nrhs] or NULL.  Returns
+ * HDG_ERR_NOT_CONVERGED when some column reaches max_uzawa or max_it. */
+hdg_status hdg_solve_multi(hdg_ctx *ctx, int nrhs, const double *F, double *u, double *p,
+                           const hdg_solve_opts *opts, hdg_solve_info *info, hdg_stream_t stream);
+
 /* Sizes after hdg_setup_mesh_hierarchy (k-dependent fields after hdg_condense). */
 hdg_status hdg_get_sizes(const hdg_ctx *ctx, hdg_sizes *out);
 

@@ -38,7 +38,8 @@ EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense",
            "hdg_apply", "hdg_precond_apply", "hdg_solve", "hdg_recover", "hdg_adjoint", "hdg_get_sizes",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
-           "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_destroy",
+           "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_apply_multi",
+           "hdg_precond_apply_multi", "hdg_solve_multi", "hdg_destroy",
            "hdg_status_string", "hdg_last_error")
 
 
@@ -130,6 +131,9 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     sigs = {
         "hdg_default_solve_opts": (None, [ctypes.POINTER(SolveOpts)]),
         "hdg_setup_mesh_hierarchy": (I, [ctypes.POINTER(_MeshDesc), I, ctypes.POINTER(P)]),
+        "hdg_apply_multi": (I, [P, I, P, P, P]),
+        "hdg_precond_apply_multi": (I, [P, I, P, P, P]),
+        "hdg_solve_multi": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
         "hdg_condense": (I, [P, ctypes.POINTER(_Params), P, P, P]),
         "hdg_load": (I, [P, P, P, P]),
         "hdg_apply": (I, [P, P, P, P]),
@@ -263,6 +267,15 @@ def hdg_condense(ctx: Context, params: Params, forcing=None, stream=None):
     return F
 
 
+def hdg_load(ctx: Context, forcing, F=None, stream=None):
+    """Condensed load of lattice forcing [n_cells, n_lat, 2] with the current condensed operator."""
+    import torch
+    n = ctx.sizes().n_dof
+    F = torch.empty(n, dtype=torch.float64, device=forcing.device) if F is None else F
+    ctx.check(load_library().hdg_load(ctx.handle, _ptr(forcing), _ptr(F), _stream(stream)))
+    return F
+
+
 def hdg_apply(ctx: Context, x, y=None, stream=None):
     import torch
     y = torch.empty_like(x) if y is None else y
@@ -297,6 +310,39 @@ def hdg_solve(ctx: Context, F, u=None, p=None, opts: Optional[SolveOpts] = None,
     if st != 0 and (st != 5 or raise_on_nonconvergence):
         ctx.check(st)
     return u, p, info.as_dict()
+
+
+def hdg_apply_multi(ctx: Context, x, y=None, stream=None):
+    """Y = A^eps X for X of shape [nrhs, n_dof] (CUDA float64)."""
+    import torch
+    y = torch.empty_like(x) if y is None else y
+    ctx.check(load_library().hdg_apply_multi(ctx.handle, x.shape[0], _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def hdg_precond_apply_multi(ctx: Context, r, z=None, stream=None):
+    """Z = MG_hp(R) column by column for R of shape [nrhs, n_dof]."""
+    import torch
+    z = torch.empty_like(r) if z is None else z
+    ctx.check(load_library().hdg_precond_apply_multi(ctx.handle, r.shape[0], _ptr(r), _ptr(z), _stream(stream)))
+    return z
+
+
+def hdg_solve_multi(ctx: Context, F, u=None, p=None, opts: Optional[SolveOpts] = None, stream=None,
+                    raise_on_nonconvergence: bool = True):
+    """hdg_solve for F of shape [nrhs, n_dof]; returns (u [nrhs, n_dof], p [nrhs, n_cells], [info dicts])."""
+    import torch
+    s = ctx.sizes()
+    nrhs = F.shape[0]
+    u = torch.zeros((nrhs, s.n_dof), dtype=torch.float64, device=F.device) if u is None else u
+    p = torch.zeros((nrhs, s.n_cells), dtype=torch.float64, device=F.device) if p is None else p
+    infos = (SolveInfo * nrhs)()
+    o = opts if opts is not None else default_solve_opts()
+    st = load_library().hdg_solve_multi(ctx.handle, nrhs, _ptr(F), _ptr(u), _ptr(p), ctypes.byref(o),
+                                        ctypes.cast(infos, ctypes.c_void_p), _stream(stream))
+    if st != 0 and (st != 5 or raise_on_nonconvergence):
+        ctx.check(st)
+    return u, p, [infos[r].as_dict() for r in range(nrhs)]
 
 
 def hdg_recover(ctx: Context, u, forcing=None, stream=None):

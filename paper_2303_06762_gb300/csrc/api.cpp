@@ -84,6 +84,8 @@ void free_level(DevLevel &L) {
     dfree(L.g); dfree(L.u); dfree(L.r); dfree(L.t);
     dfree(L.gf); dfree(L.uf); dfree(L.rf); dfree(L.tf);
     dfree(L.ct1); dfree(L.ct2); dfree(L.ct1f); dfree(L.ct2f);
+    for (auto *b : {&L.mg, &L.mu, &L.mr, &L.mt, &L.mc1, &L.mc2}) dfree(*b);
+    for (auto *b : {&L.mgf, &L.muf, &L.mrf, &L.mtf, &L.mc1f, &L.mc2f}) dfree(*b);
 }
 
 template <class Fn>
@@ -306,6 +308,11 @@ void drop_graph(hdg_ctx *ctx) {
     ctx->pc_exec = nullptr;
     ctx->pc_prec = -1;
     ctx->pc_kernels = 0;
+    if (ctx->pcm_exec) cudaGraphExecDestroy(ctx->pcm_exec);
+    ctx->pcm_exec = nullptr;
+    ctx->pcm_prec = -1;
+    ctx->pcm_R = 0;
+    ctx->pcm_kernels = 0;
 }
 
 // z = MG_hp(r): replays a CUDA graph of the whole preconditioner (several hundred
@@ -530,6 +537,369 @@ double device_sum(hdg_ctx *ctx, const double *x, int64_t n, cudaStream_t s) {
     return read_scalar(ctx, ctx->small.p + Ly.nrm2(), s);
 }
 
+// ===================================================================== multi-RHS
+// R columns (a power of two, the caller's nrhs padded with zero columns) run
+// the same Algorithms 1 and 2, FGMRES and Uzawa steps as the single solve, in
+// lockstep: every kernel works on multi-vectors [rows][R], and each column keeps
+// its own Krylov least-squares problem, tolerances and stopping decisions.
+
+int pad_width(int nrhs) {
+    int R = 1;
+    while (R < nrhs) R <<= 1;
+    return R;
+}
+
+template <class T>
+struct PrecM;
+template <>
+struct PrecM<double> {
+    static double *g(DevLevel &L) { return L.mg.p; }
+    static double *u(DevLevel &L) { return L.mu.p; }
+    static double *r(DevLevel &L) { return L.mr.p; }
+    static double *t(DevLevel &L) { return L.mt.p; }
+    static double *c1(DevLevel &L) { return L.mc1.p; }
+    static double *c2(DevLevel &L) { return L.mc2.p; }
+    static void alloc(hdg_ctx *ctx, DevLevel &L, int R) {
+        const size_t n = (size_t)std::max<int64_t>(2 * L.n_int, 1) * R;
+        dalloc(ctx, L.mg, n); dalloc(ctx, L.mu, n); dalloc(ctx, L.mr, n); dalloc(ctx, L.mt, n);
+        dalloc(ctx, L.mc1, (size_t)std::max<int64_t>(12 * L.nc_coarse, 1) * R);
+        dalloc(ctx, L.mc2, (size_t)std::max<int64_t>(6 * L.nc_coarse, 1) * R);
+    }
+};
+template <>
+struct PrecM<float> {
+    static float *g(DevLevel &L) { return L.mgf.p; }
+    static float *u(DevLevel &L) { return L.muf.p; }
+    static float *r(DevLevel &L) { return L.mrf.p; }
+    static float *t(DevLevel &L) { return L.mtf.p; }
+    static float *c1(DevLevel &L) { return L.mc1f.p; }
+    static float *c2(DevLevel &L) { return L.mc2f.p; }
+    static void alloc(hdg_ctx *ctx, DevLevel &L, int R) {
+        const size_t n = (size_t)std::max<int64_t>(2 * L.n_int, 1) * R;
+        dalloc(ctx, L.mgf, n); dalloc(ctx, L.muf, n); dalloc(ctx, L.mrf, n); dalloc(ctx, L.mtf, n);
+        dalloc(ctx, L.mc1f, (size_t)std::max<int64_t>(12 * L.nc_coarse, 1) * R);
+        dalloc(ctx, L.mc2f, (size_t)std::max<int64_t>(6 * L.nc_coarse, 1) * R);
+    }
+};
+
+template <class T>
+void sweep_m(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, int R, const T *g, T *u, bool reverse,
+             cudaStream_t s) {
+    for (int i = 0; i < L.n_colours; ++i) {
+        const int c = reverse ? L.n_colours - 1 - i : i;
+        CK(launch_gs_colour_m<T>(L, op, R, Prec<T>::A(op), Prec<T>::P(op), c, g, u, s));
+    }
+}
+
+template <class T>
+void mg_h_m(hdg_ctx *ctx, int l, int m, bool zero_init, int R, cudaStream_t s) {
+    DevLevel &L = ctx->L[l];
+    if (l == 0) {
+        CK(launch_coarse_apply_m<T>(ctx->coarse_inv.p, 2 * L.n_int, R, PrecM<T>::g(L), PrecM<T>::u(L), s));
+        return;
+    }
+    DevLevel &C = ctx->L[l - 1];
+    const int64_t n = 2 * L.n_int * R;
+    T *g = PrecM<T>::g(L), *u = PrecM<T>::u(L), *r = PrecM<T>::r(L);
+    if (zero_init) CK(cudaMemsetAsync(u, 0, sizeof(T) * n, s));
+    for (int j = 0; j < m; ++j) sweep_m<T>(ctx, L, L.op0, R, g, u, false, s);
+    CK(launch_apply_m<T>(L, L.op0, R, Prec<T>::A(L.op0), u, g, r, s));
+    CK(launch_restrict_m<T>(L, C, R, Prec<T>::W(L), Prec<T>::H(L), r, PrecM<T>::c1(L), PrecM<T>::c2(L),
+                            PrecM<T>::g(C), s));
+    const int q = ctx->prm.cycle;
+    const int mc = (q == 1) ? m * ctx->prm.vcycle_growth : m;
+    for (int it = 0; it < q; ++it) mg_h_m<T>(ctx, l - 1, mc, it == 0, R, s);
+    CK(launch_prolong_add_m<T>(L, C, R, Prec<T>::W(L), Prec<T>::H(L), PrecM<T>::u(C), PrecM<T>::t(L), u, s));
+    for (int j = 0; j < m; ++j) sweep_m<T>(ctx, L, L.op0, R, g, u, true, s);
+}
+
+// z = MG_hp(r, 0) for R columns (r, z of type T, [n_dof][R])
+template <class T>
+void mg_hp_m(hdg_ctx *ctx, const T *r, T *z, T *res, int R, cudaStream_t s) {
+    const int J = ctx->n_levels - 1;
+    DevLevel &LJ = ctx->L[J];
+    const int k = ctx->prm.k;
+    const size_t bytes = sizeof(T) * ctx->n_dof * R;
+    if (k == 0) {
+        CK(cudaMemcpyAsync(PrecM<T>::g(LJ), r, bytes, cudaMemcpyDeviceToDevice, s));
+        mg_h_m<T>(ctx, J, ctx->prm.m_h, true, R, s);
+        CK(cudaMemcpyAsync(z, PrecM<T>::u(LJ), bytes, cudaMemcpyDeviceToDevice, s));
+        return;
+    }
+    const DevOperator &op = ctx->opk;
+    CK(cudaMemsetAsync(z, 0, bytes, s));
+    for (int j = 0; j < ctx->prm.m_p; ++j) sweep_m<T>(ctx, LJ, op, R, r, z, false, s);
+    CK(launch_apply_m<T>(LJ, op, R, Prec<T>::A(op), z, r, res, s));
+    CK(launch_hp_restrict_m<T>(k, LJ.n_int, R, res, PrecM<T>::g(LJ), s));
+    mg_h_m<T>(ctx, J, ctx->prm.m_h, true, R, s);
+    CK(launch_hp_prolong_add_m<T>(k, LJ.n_int, R, PrecM<T>::u(LJ), z, s));
+    for (int j = 0; j < ctx->prm.m_p; ++j) sweep_m<T>(ctx, LJ, op, R, r, z, true, s);
+}
+
+// work buffers of the multi preconditioner and operator for width R
+void ensure_multi_work(hdg_ctx *ctx, int R) {
+    const size_t n = (size_t)std::max<int64_t>(ctx->n_dof, 1) * R;
+    const bool fp64 = ctx->prm.precision == HDG_FP64;
+    for (auto &L : ctx->L) {
+        if (fp64) PrecM<double>::alloc(ctx, L, R);
+        else PrecM<float>::alloc(ctx, L, R);
+    }
+    for (const DevLevel *L : {&ctx->L[ctx->n_levels - 1]}) {
+        const DevOperator &op = ctx->prm.k > 0 ? ctx->opk : L->op0;
+        REQUIRE(gs_m_smem(*L, op, R, fp64 ? 8 : 4) <= 200 * 1024,
+                "too many right-hand sides for the patch size (shared memory)");
+    }
+    dalloc(ctx, ctx->mkr, n);
+    if (!fp64) {
+        dalloc(ctx, ctx->mkgf, n);
+        dalloc(ctx, ctx->mkuf, n);
+        dalloc(ctx, ctx->mkrf, n);
+    }
+}
+
+void precond_m_direct(hdg_ctx *ctx, const double *r, double *z, int R, cudaStream_t s) {
+    const int64_t n = ctx->n_dof * R;
+    if (ctx->prm.precision == HDG_FP64) {
+        mg_hp_m<double>(ctx, r, z, ctx->mkr.p, R, s);
+    } else {
+        CK((launch_convert_m<double, float>(r, ctx->mkgf.p, n, s)));
+        mg_hp_m<float>(ctx, ctx->mkgf.p, ctx->mkuf.p, ctx->mkrf.p, R, s);
+        CK((launch_convert_m<float, double>(ctx->mkuf.p, z, n, s)));
+    }
+}
+
+// z = MG_hp(r) for R columns through a CUDA graph captured once per (precision, R)
+void precond_m(hdg_ctx *ctx, const double *r, double *z, int R, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    ensure_multi_work(ctx, R);
+    if (cs != cudaStreamCaptureStatusNone) {
+        precond_m_direct(ctx, r, z, R, s);
+        return;
+    }
+    const size_t bytes = sizeof(double) * ctx->n_dof * R;
+    if (!ctx->pcm_exec || ctx->pcm_prec != (int)ctx->prm.precision || ctx->pcm_R != R) {
+        if (ctx->pcm_exec) cudaGraphExecDestroy(ctx->pcm_exec);
+        ctx->pcm_exec = nullptr;
+        dalloc(ctx, ctx->pcm_in, ctx->n_dof * R);
+        dalloc(ctx, ctx->pcm_out, ctx->n_dof * R);
+        if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        cudaEvent_t ev;
+        CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        CK(cudaEventRecord(ev, s));
+        CK(cudaStreamWaitEvent(ctx->cap_stream, ev, 0));
+        CK(cudaEventDestroy(ev));
+        cudaStream_t cs2 = ctx->cap_stream;
+        const unsigned long long l0 = launch_count();
+        CK(cudaStreamBeginCapture(cs2, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t g = nullptr;
+        try {
+            precond_m_direct(ctx, ctx->pcm_in.p, ctx->pcm_out.p, R, cs2);
+        } catch (...) {
+            cudaStreamEndCapture(cs2, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        CK(cudaStreamEndCapture(cs2, &g));
+        cudaError_t e = cudaGraphInstantiate(&ctx->pcm_exec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        ctx->pcm_kernels = (long long)(launch_count() - l0);
+        note_launches(-ctx->pcm_kernels);
+        ctx->pcm_prec = (int)ctx->prm.precision;
+        ctx->pcm_R = R;
+    }
+    CK(cudaMemcpyAsync(ctx->pcm_in.p, r, bytes, cudaMemcpyDeviceToDevice, s));
+    CK(cudaGraphLaunch(ctx->pcm_exec, s));
+    note_launches(ctx->pcm_kernels);
+    CK(cudaMemcpyAsync(z, ctx->pcm_out.p, bytes, cudaMemcpyDeviceToDevice, s));
+}
+
+void ensure_krylov_m(hdg_ctx *ctx, int Rst, int R) {
+    const size_t n = (size_t)std::max<int64_t>(ctx->n_dof, 1) * R;
+    SmallLayout Ly{Rst};
+    if (ctx->mRst != Rst || ctx->mR != R || ctx->mV.n < (size_t)(Rst + 1) * n) {
+        dfree(ctx->mV);
+        dfree(ctx->mZ);
+        dalloc(ctx, ctx->mV, (size_t)(Rst + 1) * n);
+        dalloc(ctx, ctx->mZ, (size_t)Rst * n);
+        ctx->mRst = Rst;
+        ctx->mR = R;
+    }
+    dalloc(ctx, ctx->msmall, (size_t)Ly.total() * R);
+    dalloc(ctx, ctx->mhbuf, (size_t)(Rst + 2) * R);
+    dalloc(ctx, ctx->mw, n);
+    dalloc(ctx, ctx->mG, n);
+    dalloc(ctx, ctx->mpart, (size_t)(MAX_RESTART + 2) * R * krylov_m_blocks());
+    dalloc(ctx, ctx->mint, 2 * (size_t)R);
+    if (!ctx->h_multi) CK(cudaMallocHost((void **)&ctx->h_multi, sizeof(double) * 4 * MAX_NRHS));
+}
+
+// per-column squared norms of x ([n][R]) -> host out[r]
+void norms2_m(hdg_ctx *ctx, const double *x, int64_t n, int R, double *out, cudaStream_t s) {
+    SmallLayout Ly{ctx->mRst};
+    const int stride = Ly.total();
+    CK(launch_dots_m(x, 1, 0, x, n * R, R, ctx->mpart.p, s));
+    CK(launch_reduce_partials_m(ctx->mpart.p, 1, R, ctx->msmall.p, stride, Ly.nrm2(), nullptr, s));
+    CK(cudaMemcpy2DAsync(ctx->h_multi, sizeof(double), ctx->msmall.p + Ly.nrm2(), sizeof(double) * stride,
+                         sizeof(double), R, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int r = 0; r < R; ++r) out[r] = ctx->h_multi[r];
+}
+
+struct FgmresOutM {
+    int its;                    // lockstep iterations
+    std::vector<int> its_r;     // iterations each column was active
+    std::vector<double> res_r;  // last true residual norm per column
+};
+
+// flexible GMRES on A^eps X = B for R columns; column r stops at |r_r| <= max(rtol |r_r0|, atol_r[r])
+FgmresOutM fgmres_m(hdg_ctx *ctx, const double *b, double *x, double rtol, const std::vector<double> &atol_r,
+                    const std::vector<char> &skip, int Rst, int max_it, int R, cudaStream_t s) {
+    const int64_t n = ctx->n_dof * R;
+    SmallLayout Ly{Rst};
+    const int stride = Ly.total();
+    DevLevel &LJ = ctx->L[ctx->n_levels - 1];
+    double *V = ctx->mV.p, *Z = ctx->mZ.p, *w = ctx->mw.p, *sm = ctx->msmall.p, *pt = ctx->mpart.p;
+    double *hb = ctx->mhbuf.p;
+    FgmresOutM out{0, std::vector<int>(R, 0), std::vector<double>(R, 0.0)};
+    std::vector<double> tol(R, -1.0), beta(R);
+    std::vector<int> m_r(R);
+    std::vector<char> done(R);
+    while (true) {
+        CK(launch_apply_m<double>(LJ, ctx->opk, R, ctx->opk.A.p, x, b, V, s));   // V0 = b - A x
+        norms2_m(ctx, V, ctx->n_dof, R, beta.data(), s);
+        bool any = false;
+        for (int r = 0; r < R; ++r) {
+            beta[r] = std::sqrt(std::max(beta[r], 0.0));
+            if (!std::isfinite(beta[r])) {
+                ctx->err = "non-finite residual";
+                throw Fail{HDG_ERR_NONFINITE};
+            }
+            if (tol[r] < 0) tol[r] = std::max(rtol * beta[r], atol_r[r]);
+            out.res_r[r] = beta[r];
+            done[r] = skip[r] || beta[r] <= tol[r];
+            any = any || !done[r];
+        }
+        if (!any || out.its >= max_it) break;
+        CK(launch_init_cycle_m(V, V, n, R, sm, stride, Rst, s));
+        std::fill(m_r.begin(), m_r.end(), 0);
+        int mmax = 0;
+        for (int j = 0; j < Rst; ++j) {
+            double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
+            precond_m(ctx, vj, zj, R, s);
+            CK(launch_apply_m<double>(LJ, ctx->opk, R, ctx->opk.A.p, zj, nullptr, w, s));
+            CK(launch_dots_m(V, j + 1, n, w, n, R, pt, s));
+            CK(launch_reduce_partials_m(pt, j + 1, R, sm, stride, Ly.h1(), hb, s));
+            CK(launch_update_dots_m(V, j + 1, n, w, n, R, hb, pt, 1, s));
+            CK(launch_reduce_partials_m(pt, j + 1, R, sm, stride, Ly.h2(), hb, s));
+            CK(launch_update_dots_m(V, j + 1, n, w, n, R, hb, pt, 2, s));
+            CK(launch_reduce_partials_m(pt, 1, R, sm, stride, Ly.nrm2(), nullptr, s));
+            CK(launch_givens_m(sm, stride, j, Rst, R, s));
+            CK(launch_scale_next_m(w, V + (size_t)(j + 1) * n, n, R, sm, stride, Ly.hn(), s));
+            CK(cudaMemcpy2DAsync(ctx->h_multi, 2 * sizeof(double), sm + Ly.res(), sizeof(double) * stride,
+                                 2 * sizeof(double), R, cudaMemcpyDeviceToHost, s));
+            CK(cudaStreamSynchronize(s));
+            ++out.its;
+            mmax = j + 1;
+            bool all = true;
+            for (int r = 0; r < R; ++r) {
+                if (done[r]) continue;
+                const double res = ctx->h_multi[2 * r], hn = ctx->h_multi[2 * r + 1];
+                if (!std::isfinite(res)) {
+                    ctx->err = "non-finite residual estimate";
+                    throw Fail{HDG_ERR_NONFINITE};
+                }
+                m_r[r] = j + 1;
+                out.its_r[r] += 1;
+                if (res <= tol[r] || hn == 0.0) done[r] = 1;
+                else all = false;
+            }
+            if (all || out.its >= max_it) break;
+        }
+        // pageable source: staged before cudaMemcpyAsync returns
+        CK(cudaMemcpyAsync(ctx->mint.p, m_r.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
+        CK(launch_solve_update_m(sm, stride, ctx->mint.p, mmax, Rst, Z, n, x, n, R, s));
+    }
+    return out;
+}
+
+// Uzawa for R columns (eq. stOpEq-ALU), each with the stopping rule of uzawa_solve
+hdg_status uzawa_solve_m(hdg_ctx *ctx, int nrhs, int R, const double *F, double *u, double *p,
+                         const hdg_solve_opts *opts_in, std::vector<hdg_solve_info> &info, cudaStream_t s) {
+    hdg_status conv = HDG_OK;
+    hdg_solve_opts o;
+    hdg_default_solve_opts(&o);
+    if (opts_in) o = *opts_in;
+    REQUIRE(o.restart >= 1 && o.restart <= 32, "restart out of range 1..32");
+    REQUIRE(o.max_uzawa >= 1 && o.max_uzawa <= 64, "max_uzawa out of range 1..64");
+    REQUIRE(o.max_it >= 1 && o.rtol >= 0 && o.atol >= 0 && o.floor_rel >= 0 && o.uzawa_tol >= 0,
+            "bad tolerances");
+    ensure_krylov_m(ctx, o.restart, R);
+    ensure_multi_work(ctx, R);
+    const int J = ctx->n_levels - 1;
+    DevLevel &LJ = ctx->L[J];
+    const int k = ctx->prm.k;
+    std::vector<double> normF(R);
+    norms2_m(ctx, F, ctx->n_dof, R, normF.data(), s);
+    info.assign(R, hdg_solve_info{});
+    std::vector<double> floor_abs(R), ndp_prev(R, -1.0);
+    std::vector<char> fin(R, 0);
+    for (int r = 0; r < R; ++r) {
+        normF[r] = std::sqrt(std::max(normF[r], 0.0));
+        info[r].normF = normF[r];
+        floor_abs[r] = std::max(o.floor_rel * normF[r], o.atol);
+        if (r >= nrhs) fin[r] = 1;
+    }
+    double *g = ctx->mG.p;
+    SmallLayout Ly{o.restart};
+    const int stride = Ly.total();
+    for (int it = 0; it < o.max_uzawa; ++it) {
+        CK(launch_uzawa_rhs_m(LJ, k, R, F, p, g, s));
+        FgmresOutM fo = fgmres_m(ctx, g, u, o.rtol, floor_abs, fin, o.restart, o.max_it, R, s);
+        std::vector<int> frozen(R);
+        for (int r = 0; r < R; ++r) frozen[r] = fin[r];
+        CK(cudaMemcpyAsync(ctx->mint.p + R, frozen.data(), sizeof(int) * R, cudaMemcpyHostToDevice, s));
+        CK(launch_uzawa_update_m(LJ, k, R, u, p, ctx->prm.gamma, ctx->prm.nu, cell_nu_of(ctx, J), ctx->mint.p + R,
+                                 ctx->mpart.p, s));
+        CK(launch_reduce_partials_m(ctx->mpart.p, 3, R, ctx->msmall.p, stride, Ly.h1(), nullptr, s));
+        CK(cudaMemcpy2DAsync(ctx->h_multi, 3 * sizeof(double), ctx->msmall.p + Ly.h1(), sizeof(double) * stride,
+                             3 * sizeof(double), R, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        bool all = true;
+        for (int r = 0; r < R; ++r) {
+            if (fin[r]) continue;
+            hdg_solve_info &in = info[r];
+            const int its = fo.its_r[r];
+            in.krylov_its[it] = its;
+            in.krylov_its_total += its;
+            in.uzawa_its = it + 1;
+            in.res_mom = fo.res_r[r];
+            if (its >= o.max_it) conv = HDG_ERR_NOT_CONVERGED;
+            const double ndp = std::sqrt(std::max(ctx->h_multi[3 * r], 0.0));
+            const double npn = std::sqrt(std::max(ctx->h_multi[3 * r + 1], 0.0));
+            in.dp_rel = npn > 0 ? ndp / npn : 0.0;
+            if (!std::isfinite(ndp) || !std::isfinite(npn)) {
+                ctx->err = "non-finite pressure update";
+                throw Fail{HDG_ERR_NONFINITE};
+            }
+            bool d = ndp <= o.atol || (it > 0 && its == 0);
+            if (!d && ndp_prev[r] >= 0) {
+                const double rho = std::min(ndp / ndp_prev[r], 0.99);
+                d = rho / (1.0 - rho) * ndp <= o.uzawa_tol * npn;
+            }
+            ndp_prev[r] = ndp;
+            if (d) fin[r] = 1;
+            else all = false;
+        }
+        if (fo.its >= o.max_it) conv = HDG_ERR_NOT_CONVERGED;
+        if (all) break;
+    }
+    for (int r = 0; r < nrhs; ++r)
+        if (!fin[r] && conv == HDG_OK) conv = HDG_ERR_NOT_CONVERGED;
+    return conv;
+}
+
 } // namespace
 
 // =====================================================================================
@@ -702,8 +1072,13 @@ void hdg_destroy(hdg_ctx *ctx) {
         dfree(*b);
     drop_graph(ctx);
     dfree(ctx->pc_in); dfree(ctx->pc_out);
+    for (auto *b : {&ctx->mV, &ctx->mZ, &ctx->mw, &ctx->mpart, &ctx->msmall, &ctx->mhbuf, &ctx->mF, &ctx->mU,
+                    &ctx->mP, &ctx->mG, &ctx->mkr, &ctx->mkt, &ctx->mrd, &ctx->mzd, &ctx->pcm_in, &ctx->pcm_out})
+        dfree(*b);
+    dfree(ctx->mkgf); dfree(ctx->mkuf); dfree(ctx->mkrf); dfree(ctx->mint);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+    if (ctx->h_multi) cudaFreeHost(ctx->h_multi);
     delete ctx;
 }
 
@@ -1094,6 +1469,72 @@ hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, con
     if (info) *info = loc;
     if (st != HDG_OK) return st;
     if (conv != HDG_OK) ctx->err = "adjoint solve: iteration limit reached";
+    return conv;
+}
+
+// ------------------------------------------------------------------ multi-RHS
+hdg_status hdg_apply_multi(hdg_ctx *ctx, int nrhs, const double *x, double *y, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, "nrhs out of range 1..64");
+        REQUIRE(x && y, "null vector");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int R = pad_width(nrhs);
+        const int64_t n = ctx->n_dof;
+        dalloc(ctx, ctx->mrd, (size_t)std::max<int64_t>(n, 1) * R);
+        dalloc(ctx, ctx->mzd, (size_t)std::max<int64_t>(n, 1) * R);
+        CK(launch_pack_m(x, nrhs, n, R, ctx->mrd.p, s));
+        CK(launch_apply_m<double>(ctx->L[ctx->n_levels - 1], ctx->opk, R, ctx->opk.A.p, ctx->mrd.p, nullptr,
+                                  ctx->mzd.p, s));
+        CK(launch_unpack_m(ctx->mzd.p, nrhs, n, R, y, s));
+    });
+}
+
+hdg_status hdg_precond_apply_multi(hdg_ctx *ctx, int nrhs, const double *r, double *z, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, "nrhs out of range 1..64");
+        REQUIRE(r && z, "null vector");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int R = pad_width(nrhs);
+        const int64_t n = ctx->n_dof;
+        dalloc(ctx, ctx->mrd, (size_t)std::max<int64_t>(n, 1) * R);
+        dalloc(ctx, ctx->mzd, (size_t)std::max<int64_t>(n, 1) * R);
+        CK(launch_pack_m(r, nrhs, n, R, ctx->mrd.p, s));
+        precond_m(ctx, ctx->mrd.p, ctx->mzd.p, R, s);
+        CK(launch_unpack_m(ctx->mzd.p, nrhs, n, R, z, s));
+    });
+}
+
+hdg_status hdg_solve_multi(hdg_ctx *ctx, int nrhs, const double *F, double *u, double *p,
+                           const hdg_solve_opts *opts, hdg_solve_info *info, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    std::vector<hdg_solve_info> loc;
+    hdg_status conv = HDG_OK;
+    hdg_status st = guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, "nrhs out of range 1..64");
+        REQUIRE(F && u && p, "null vector");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int R = pad_width(nrhs);
+        const int64_t n = ctx->n_dof, nc = ctx->L[ctx->n_levels - 1].nc;
+        dalloc(ctx, ctx->mF, (size_t)std::max<int64_t>(n, 1) * R);
+        dalloc(ctx, ctx->mU, (size_t)std::max<int64_t>(n, 1) * R);
+        dalloc(ctx, ctx->mP, (size_t)std::max<int64_t>(nc, 1) * R);
+        CK(launch_pack_m(F, nrhs, n, R, ctx->mF.p, s));
+        CK(launch_pack_m(u, nrhs, n, R, ctx->mU.p, s));
+        CK(launch_pack_m(p, nrhs, nc, R, ctx->mP.p, s));
+        conv = uzawa_solve_m(ctx, nrhs, R, ctx->mF.p, ctx->mU.p, ctx->mP.p, opts, loc, s);
+        CK(launch_unpack_m(ctx->mU.p, nrhs, n, R, u, s));
+        CK(launch_unpack_m(ctx->mP.p, nrhs, nc, R, p, s));
+        CK(cudaStreamSynchronize(s));
+    });
+    if (info)
+        for (int r = 0; r < nrhs && r < (int)loc.size(); ++r) info[r] = loc[r];
+    if (st != HDG_OK) return st;
+    if (conv != HDG_OK) ctx->err = "iteration limit reached";
     return conv;
 }
 

@@ -166,6 +166,9 @@ struct DevLevel {
     DBuf<float> gf, uf, rf, tf;
     DBuf<double> ct1, ct2;     // coarse-cell temps for restriction (nc_coarse*12, *6)
     DBuf<float> ct1f, ct2f;
+    // multi-right-hand-side MG work (R columns), FP64 and FP32
+    DBuf<double> mg, mu, mr, mt, mc1, mc2;
+    DBuf<float> mgf, muf, mrf, mtf, mc1f, mc2f;
 };
 
 } // namespace hdg
@@ -198,6 +201,7 @@ struct hdg_ctx {
     hdg::DBuf<double> V, Z, w, partials, small;   // small: Hessenberg, rotations, g, y
     hdg::DBuf<double> uz_partials;
     double *h_pinned = nullptr;              // host pinned scalars
+    double *h_multi = nullptr;               // host pinned per-column scalars (multi-RHS)
     // CUDA graph of one preconditioner application (fixed staging buffers)
     cudaGraphExec_t pc_exec = nullptr;
     cudaStream_t cap_stream = nullptr;       // private stream used only for graph capture
@@ -206,6 +210,15 @@ struct hdg_ctx {
     hdg::DBuf<double> pc_in, pc_out;
     // recovery / adjoint workspaces
     hdg::DBuf<double> rec_L, rec_La, rec_rt, rec_ulat, rec_e, rec_j, adj_F, adj_u, adj_p;
+    // multi-right-hand-side solves (width mR, restart mRst)
+    int mR = 0, mRst = 0;
+    hdg::DBuf<double> mV, mZ, mw, mpart, msmall, mhbuf, mF, mU, mP, mG, mkr, mkt, mrd, mzd;
+    hdg::DBuf<float> mkgf, mkuf, mkrf;
+    hdg::DBuf<int> mint;                      // per-column ints (m_r, frozen flags)
+    cudaGraphExec_t pcm_exec = nullptr;      // graph of one multi preconditioner application
+    int pcm_prec = -1, pcm_R = 0;
+    long long pcm_kernels = 0;
+    hdg::DBuf<double> pcm_in, pcm_out;
     // fused MG_h on levels 0..small_Ls (one thread block), -1 when not used
     int small_Ls = -1;
     size_t small_smem_d = 0, small_smem_f = 0;
@@ -301,5 +314,49 @@ cudaError_t launch_uzawa_rhs(const DevLevel &L, int k, const double *F, const do
 cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p, double gamma,
                                 double nu, const double *nu_cell, double *partials, cudaStream_t s);
 cudaError_t launch_sum(const double *x, int64_t n, double *partials, cudaStream_t s);
+
+// multi-right-hand-side kernels (multi.cu): multi-vectors [rows][R], R a power of two <= 64
+constexpr int MAX_NRHS = 64;
+int krylov_m_blocks();
+size_t gs_m_smem(const DevLevel &L, const DevOperator &op, int R, size_t word);
+template <class T>
+cudaError_t launch_apply_m(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *x, const T *g, T *y,
+                           cudaStream_t s);
+template <class T>
+cudaError_t launch_gs_colour_m(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *Pinv,
+                               int colour, const T *g, T *u, cudaStream_t s);
+template <class T>
+cudaError_t launch_hp_restrict_m(int k, int64_t n_int, int R, const T *r, T *r0, cudaStream_t s);
+template <class T>
+cudaError_t launch_hp_prolong_add_m(int k, int64_t n_int, int R, const T *d0, T *u, cudaStream_t s);
+template <class T>
+cudaError_t launch_prolong_add_m(const DevLevel &F, const DevLevel &C, int R, const T *W, const T *Hm, const T *uc,
+                                 T *tmp, T *uf, cudaStream_t s);
+template <class T>
+cudaError_t launch_restrict_m(const DevLevel &F, const DevLevel &C, int R, const T *W, const T *Hm, const T *rf,
+                              T *t1, T *t2, T *rc, cudaStream_t s);
+template <class T>
+cudaError_t launch_coarse_apply_m(const double *inv, int64_t n, int R, const T *g, T *u, cudaStream_t s);
+cudaError_t launch_pack_m(const double *in, int nrhs, int64_t n, int R, double *out, cudaStream_t s);
+cudaError_t launch_unpack_m(const double *in, int nrhs, int64_t n, int R, double *out, cudaStream_t s);
+template <class Ti, class To>
+cudaError_t launch_convert_m(const Ti *x, To *y, int64_t n, cudaStream_t s);
+cudaError_t launch_dots_m(const double *V, int nv, int64_t ld, const double *w, int64_t n, int R, double *partials,
+                          cudaStream_t s);
+cudaError_t launch_update_dots_m(const double *V, int nv, int64_t ld, double *w, int64_t n, int R, const double *h,
+                                 double *partials, int mode, cudaStream_t s);
+cudaError_t launch_reduce_partials_m(const double *partials, int nv, int R, double *small, int stride, int off,
+                                     double *hbuf, cudaStream_t s);
+cudaError_t launch_givens_m(double *small, int stride, int j, int Rst, int R, cudaStream_t s);
+cudaError_t launch_scale_next_m(const double *w, double *v, int64_t n, int R, const double *small, int stride,
+                                int hn_off, cudaStream_t s);
+cudaError_t launch_init_cycle_m(const double *r, double *v0, int64_t n, int R, double *small, int stride, int Rst,
+                                cudaStream_t s);
+cudaError_t launch_solve_update_m(double *small, int stride, const int *m_r, int mmax, int Rst, const double *Z,
+                                  int64_t ld, double *x, int64_t n, int R, cudaStream_t s);
+cudaError_t launch_uzawa_rhs_m(const DevLevel &L, int k, int R, const double *F, const double *p, double *g,
+                               cudaStream_t s);
+cudaError_t launch_uzawa_update_m(const DevLevel &L, int k, int R, const double *u, double *p, double gamma, double nu,
+                                  const double *nu_cell, const int *frozen, double *partials, cudaStream_t s);
 
 } // namespace hdg

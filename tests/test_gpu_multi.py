@@ -1,0 +1,112 @@
+"""GPU parity of the multi-right-hand-side (batched) forms: hdg_apply_multi,
+hdg_precond_apply_multi and hdg_solve_multi against the single-load forms
+column by column and against the oracle's exact solution.
+
+Loads follow the many-right-hand-side workload: seeded sums of Fourier modes
+plus gradient fields (workloads.manufactured.fourier_forcing_2d).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from workloads import forcing_at_lattice
+from workloads.manufactured import fourier_forcing_2d, convecting_stream_2d, curl_lattice_2d
+from oracle.hdg import HDG
+from _util import hierarchy, rel
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _hdg():
+    import paper_2303_06762_gb300 as hdg
+    return hdg
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def _opts(hdg):
+    # one decade below the default stopping rule, so that the solution (not only the
+    # residual) is within 1e-8 of the exact discrete solution for these rough loads
+    o = hdg.default_solve_opts()
+    o.rtol, o.floor_rel, o.uzawa_tol = 1e-10, 1e-11, 1e-10
+    return o
+
+
+def _setup(N0, nl, k, nrhs, precision=0, gamma=100.0, beta=1.0, nu=1.0, conv=False, **meshkw):
+    hdg = _hdg()
+    ms, ts, ps = hierarchy(N0, nl, **meshkw)
+    fine = ms[-1]
+    fvs = [forcing_at_lattice(fine.coords, fine.cells, k, fourier_forcing_2d(j)) for j in range(nrhs)]
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    cv = None
+    if conv:
+        psi, _ = convecting_stream_2d(1.0)
+        cv = curl_lattice_2d(fine.coords, fine.cells, k + 1, psi)
+    prm = hdg.Params(k=k, nu=nu, beta=beta, gamma=gamma, precision=precision,
+                     conv=None if cv is None else dev(cv))
+    hdg.hdg_condense(ctx, prm)
+    F = torch.stack([hdg.hdg_load(ctx, dev(fv)) for fv in fvs])
+    return ms, ts, ps, fvs, ctx, F, cv
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 8])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_apply_and_precond_multi_match_single(nrhs, precision):
+    hdg = _hdg()
+    ms, ts, ps, fvs, ctx, F, _ = _setup(2, 3, 2, nrhs, precision=precision, shuffle_seed=3)
+    X = torch.randn(F.shape, dtype=torch.float64, device=DEV)
+    Y = hdg.hdg_apply_multi(ctx, X)
+    Z = hdg.hdg_precond_apply_multi(ctx, X)
+    for r in range(nrhs):
+        assert rel(host(Y[r]), host(hdg.hdg_apply(ctx, X[r].contiguous()))) < 1e-14
+        zs = host(hdg.hdg_precond_apply(ctx, X[r].contiguous()))
+        assert rel(host(Z[r]), zs) < (1e-12 if precision == 0 else 1e-5)
+
+
+@pytest.mark.parametrize("k,nrhs,precision,mesh", [(1, 4, 0, {}), (2, 5, 1, dict(shuffle_seed=2)),
+                                                   (3, 8, 1, dict(jitter=0.2, seed=1))])
+def test_solve_multi_matches_single_and_direct(k, nrhs, precision, mesh):
+    hdg = _hdg()
+    ms, ts, ps, fvs, ctx, F, _ = _setup(2, 3, k, nrhs, precision=precision, **mesh)
+    U, P, infos = hdg.hdg_solve_multi(ctx, F, opts=_opts(hdg))
+    oh = HDG(ts[-1], k, nu=1.0, beta=1.0, gamma=100.0)
+    for r in range(nrhs):
+        u1, p1, info1 = hdg.hdg_solve(ctx, F[r].contiguous(), opts=_opts(hdg))
+        if precision == 0:
+            assert infos[r]["krylov_its"] == info1["krylov_its"]
+            assert rel(host(U[r]), host(u1)) < 1e-9
+        else:
+            assert abs(infos[r]["krylov_its_total"] - info1["krylov_its_total"]) <= infos[r]["uzawa_its"]
+        ud, pd = oh.solve_direct(oh.load(fvs[r]))
+        assert np.linalg.norm(host(U[r]) - ud) < 1e-8 * np.linalg.norm(ud)
+        pr = host(P[r])
+        assert np.linalg.norm(pr - pd) < 1e-6 * np.linalg.norm(pd)
+
+
+def test_solve_multi_oseen_and_wide_batch():
+    hdg = _hdg()
+    nrhs = 64
+    ms, ts, ps, fvs, ctx, F, cv = _setup(4, 2, 3, nrhs, precision=1, nu=0.01, beta=0.0, conv=True)
+    U, P, infos = hdg.hdg_solve_multi(ctx, F, opts=_opts(hdg))
+    oh = HDG(ts[-1], 3, nu=0.01, beta=0.0, gamma=100.0, conv=cv)
+    for r in (0, 17, 63):
+        ud, pd = oh.solve_direct(oh.load(fvs[r]))
+        assert np.linalg.norm(host(U[r]) - ud) < 1e-8 * np.linalg.norm(ud)
+    assert all(i["uzawa_its"] >= 1 for i in infos)
+
+
+def test_multi_error_paths():
+    hdg = _hdg()
+    ms, ts, ps, fvs, ctx, F, _ = _setup(2, 2, 1, 2)
+    lib = hdg.load_library()
+    assert lib.hdg_apply_multi(ctx.handle, 0, None, None, None) == 1
+    assert lib.hdg_apply_multi(ctx.handle, 65, None, None, None) == 1

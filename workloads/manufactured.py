@@ -245,3 +245,30 @@ def curl_lattice_2d(coords: np.ndarray, cells: np.ndarray, q: int,
     Jinv = np.linalg.inv(J)
     grad = np.einsum("cdi,cmd->cmi", Jinv, gref)          # J^{-T} ∇̂
     return np.stack([grad[..., 1], -grad[..., 0]], axis=2)
+
+
+def fourier_forcing_2d(j: int, n_modes: int = 8, seed0: int = 20230312):
+    """Seeded forcing number j of the many-right-hand-side workload:
+    f_j = Σ_m a_m sin(2π(p_m x + q_m y) + θ_m) + ∇φ_j,
+    φ_j = Σ_m b_m cos(2π(r_m x + s_m y) + η_m),
+    a_m ~ N(0, I_2), b_m ~ N(0, 1), integer wavenumbers p, q, r, s in 1..8 and
+    phases θ, η ~ U[0, 2π), all drawn from numpy.random.default_rng(seed0 + j)."""
+    rng = np.random.default_rng(seed0 + j)
+    a = rng.standard_normal((n_modes, 2))
+    pq = rng.integers(1, 9, size=(n_modes, 2))
+    th = rng.uniform(0.0, 2 * PI, n_modes)
+    b = rng.standard_normal(n_modes)
+    rs = rng.integers(1, 9, size=(n_modes, 2))
+    eta = rng.uniform(0.0, 2 * PI, n_modes)
+
+    def f(x):
+        out = np.zeros((x.shape[0], 2))
+        for m in range(n_modes):
+            arg = 2 * PI * (pq[m, 0] * x[:, 0] + pq[m, 1] * x[:, 1]) + th[m]
+            out += np.sin(arg)[:, None] * a[m][None, :]
+            argp = 2 * PI * (rs[m, 0] * x[:, 0] + rs[m, 1] * x[:, 1]) + eta[m]
+            # ∇ of b cos(argp)
+            out += (-b[m] * np.sin(argp) * 2 * PI)[:, None] * rs[m][None, :]
+        return out
+
+    return f
