@@ -14,6 +14,9 @@ hot path) from a zero initial guess on the condensed load resident in HBM.
 Two forms are timed: FP64 throughout, and the mixed form (FP32
 preconditioner inside FP64 FGMRES).  The headline value is the mixed form's
 skeleton-DOF·iterations/s; both forms' time-to-tolerance are in the line.
+Two further forms follow in "forms": the batched form (64 seeded loads on a
+256x256 mesh solved together by hdg_solve_multi, against one load alone) and
+the Oseen form (128x128, k = 2, Re = 1, 1e2, 1e3).
 
     python bench.py [--gpus 1] [--steps K] [--warmup W] [--impl reference]
 
@@ -52,6 +55,8 @@ def parse():
     ap.add_argument("--nu", type=float, default=1.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra-forms", action="store_true",
+                    help="skip the batched (64 loads) and Oseen forms")
     ap.add_argument("--profile-solve", action="store_true",
                     help="condense, then one warm-up and one timed mixed-precision solve only "
                          "(the command profiled for the kernel launch list)")
@@ -377,14 +382,100 @@ def gpu_arm(args):
 
     # ---------------------------------------------------------------- roofline of the dominant kernel
     line["roofline"] = roofline(args, ctx, hdg, torch, dev, stream, sizes)
+    ctx.close()
+    if not args.no_extra_forms:
+        line["forms"]["batched_mixed_fp32"] = batched_form(args, hdg, torch, dev, stream, world)
+        line["forms"]["oseen_mixed_fp32"] = oseen_form(args, hdg, torch, dev, stream)
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
-    ctx.close()
     if rank == 0:
         print(json.dumps(line))
     if dist:
         tdist.destroy_process_group()
+
+
+def _timed(torch, stream, fn):
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    out = fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / 1e3, out
+
+
+def batched_form(args, hdg, torch, dev, stream, world):
+    """Many loads on one mesh: 2D 256x256 (131,072 triangles), k = 3, gamma = 1e2,
+    beta = 1, nu = 1, 64 right-hand sides f_j = seeded Fourier sums plus gradient
+    fields, solved together by hdg_solve_multi (mixed FP32 preconditioner), against
+    one load solved alone by hdg_solve on the same operator."""
+    from workloads import unit_square_hierarchy
+    from workloads.manufactured import fourier_forcing_2d, lattice_points_2d
+    N, N0, k, nrhs = 256, 8, 3, 64
+    nl = 1
+    while N0 * 2 ** (nl - 1) < N:
+        nl += 1
+    ms = unit_square_hierarchy(N0, nl)
+    fine = ms[-1]
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=dev.index or 0)
+    prm = hdg.Params(k=k, nu=1.0, beta=1.0, gamma=1e2, precision=hdg.HDG_MIXED_FP32)
+    hdg.hdg_condense(ctx, prm)
+    X = torch.tensor(lattice_points_2d(fine.coords, fine.cells, k + 1), device=dev)
+    shp = X.shape
+    Xf = X.reshape(-1, 2)
+    F = torch.stack([hdg.hdg_load(ctx, fourier_forcing_2d(j)(Xf, xp=torch).reshape(shp).contiguous())
+                     for j in range(nrhs)])
+    del X, Xf
+    sizes = ctx.sizes()
+    hdg.hdg_solve_multi(ctx, F)                      # warm-up (graph capture, allocation)
+    t, (U, P, infos) = _timed(torch, stream, lambda: hdg.hdg_solve_multi(ctx, F))
+    its = sum(i["krylov_its_total"] for i in infos)
+    F0 = F[0].contiguous()
+    hdg.hdg_solve(ctx, F0)
+    t1, (_, _, info1) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F0))
+    ctx.close()
+    return {"workload": f"2D generalized Stokes {N}x{N} ({2 * N * N} triangles), k={k}, gamma=1e2, beta=1, nu=1, "
+                        f"{nrhs} seeded Fourier+gradient loads, CR levels {N0}x{N0}..{N}x{N}, hdg_solve_multi",
+            "nrhs": nrhs, "skeleton_dofs": int(sizes.n_dof), "time_to_tol_s": t,
+            "fgmres_iters_total": its, "uzawa_steps_max": max(i["uzawa_its"] for i in infos),
+            "dof_iters_per_s": sizes.n_dof * its * world / t,
+            "single_load_time_to_tol_s": t1, "single_load_fgmres_iters": info1["krylov_its_total"],
+            "single_load_dof_iters_per_s": sizes.n_dof * info1["krylov_its_total"] / t1,
+            "throughput_ratio_vs_single": (sizes.n_dof * its / t) / (sizes.n_dof * info1["krylov_its_total"] / t1)}
+
+
+def oseen_form(args, hdg, torch, dev, stream):
+    """Oseen: 128x128 (32,768 triangles), k = 2, gamma = 1e2, beta = 0, upwind
+    convection by b = curl(sin^2(pi x) sin^2(pi y)) scaled to max|b| = 1, nu = 1/Re."""
+    from workloads import unit_square_hierarchy, curl_bubble_2d, forcing_at_lattice
+    from workloads.manufactured import convecting_stream_2d, curl_lattice_2d
+    N, N0, k = 128, 8, 2
+    nl = 1
+    while N0 * 2 ** (nl - 1) < N:
+        nl += 1
+    ms = unit_square_hierarchy(N0, nl)
+    fine = ms[-1]
+    psi, b = convecting_stream_2d(1.0)
+    conv = torch.tensor(curl_lattice_2d(fine.coords, fine.cells, k + 1, psi), device=dev)
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=dev.index or 0)
+    out = {"workload": f"2D Oseen {N}x{N} ({2 * N * N} triangles), k={k}, gamma=1e2, beta=0, "
+                       f"b=curl(sin^2 pi x sin^2 pi y) with max|b|=1, nu=1/Re, CR levels {N0}x{N0}..{N}x{N}"}
+    for Re in (1.0, 1e2, 1e3):
+        nu = 1.0 / Re
+        fv = forcing_at_lattice(fine.coords, fine.cells, k, curl_bubble_2d().forcing(nu, 0.0, conv=b))
+        prm = hdg.Params(k=k, nu=nu, beta=0.0, gamma=1e2, precision=hdg.HDG_MIXED_FP32, conv=conv)
+        F = hdg.hdg_condense(ctx, prm, torch.tensor(fv, device=dev))
+        hdg.hdg_solve(ctx, F, raise_on_nonconvergence=False)
+        t, (_, _, info) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F, raise_on_nonconvergence=False))
+        n = ctx.sizes().n_dof
+        out[f"Re={Re:g}"] = {"time_to_tol_s": t, "fgmres_iters": info["krylov_its_total"],
+                             "uzawa_steps": info["uzawa_its"], "dp_rel": info["dp_rel"],
+                             "dof_iters_per_s": n * info["krylov_its_total"] / t}
+    out["skeleton_dofs"] = int(ctx.sizes().n_dof)
+    ctx.close()
+    return out
 
 
 def roofline(args, ctx, hdg, torch, dev, stream, sizes):

@@ -648,6 +648,7 @@ void ensure_multi_work(hdg_ctx *ctx, int R) {
         const DevOperator &op = ctx->prm.k > 0 ? ctx->opk : L->op0;
         REQUIRE(gs_m_smem(*L, op, R, fp64 ? 8 : 4) <= 200 * 1024,
                 "too many right-hand sides for the patch size (shared memory)");
+        REQUIRE(L->nc * (int64_t)op.nloc * op.nloc < ((int64_t)1 << 31), "mesh too large for the batched smoother");
     }
     dalloc(ctx, ctx->mkr, n);
     if (!fp64) {

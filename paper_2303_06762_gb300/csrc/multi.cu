@@ -25,90 +25,170 @@ constexpr int MAXVM = 33;        // Krylov basis vectors (restart <= 32)
 unsigned nblk(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
 // ---------------------------------------------------------------- operator apply
-// y = A x (or y = g - A x) for R columns, pull style per facet row
-template <class T, int DPF>
+// y = A x (or y = g - A x) for R = 2^lgR columns, pull style per facet row.  A
+// thread owns RB consecutive rows of one facet and one column: every x value it
+// loads feeds RB products.
+template <class T, int DPF, int RB>
 __global__ void __launch_bounds__(MT)
-apply_m_kernel(int64_t n_int, int R, const int *__restrict__ facet_adj, const int *__restrict__ cell_int,
+apply_m_kernel(int64_t n_int, int lgR, const int *__restrict__ facet_adj, const int *__restrict__ cell_int,
                const T *__restrict__ A, const T *__restrict__ x, const T *__restrict__ g, T *__restrict__ y) {
     constexpr int NLOC = 3 * DPF;
+    const int R = 1 << lgR;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= n_int * DPF * R) return;
-    const int64_t row = idx / R;
-    const int r = (int)(idx - row * R);
-    const int64_t i = row / DPF;
-    const int d = (int)(row - i * DPF);
-    T acc = 0;
+    if (idx >= (n_int * (DPF / RB)) << lgR) return;
+    const int64_t rb = idx >> lgR;
+    const int r = (int)(idx & (R - 1));
+    const int64_t i = rb / (DPF / RB);
+    const int d0 = (int)(rb - i * (DPF / RB)) * RB;
+    T acc[RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) acc[b] = 0;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const int adj = facet_adj[2 * i + q];
         if (adj < 0) continue;
         const int c = adj >> 2, lf = adj & 3;
-        const T *Ac = A + (size_t)c * NLOC * NLOC + lf * DPF + d;
+        const T *Ac = A + (size_t)c * NLOC * NLOC + lf * DPF + d0;
 #pragma unroll
         for (int f2 = 0; f2 < 3; ++f2) {
             const int j = cell_int[3 * c + f2];
             if (j < 0) continue;
-            const T *xs = x + (size_t)j * DPF * R + r;
+            const T *xs = x + ((size_t)j * DPF << lgR) + r;
 #pragma unroll
-            for (int d2 = 0; d2 < DPF; ++d2) acc += Ac[(f2 * DPF + d2) * NLOC] * xs[(size_t)d2 * R];
+            for (int d2 = 0; d2 < DPF; ++d2) {
+                const T xv = xs[(size_t)d2 << lgR];
+                const T *a = Ac + (f2 * DPF + d2) * NLOC;
+#pragma unroll
+                for (int b = 0; b < RB; ++b) acc[b] += a[b] * xv;
+            }
         }
     }
-    y[idx] = g ? g[idx] - acc : acc;
+    const size_t o = (((size_t)i * DPF + d0) << lgR) + r;
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+        const size_t e = o + ((size_t)b << lgR);
+        y[e] = g ? g[e] - acc[b] : acc[b];
+    }
 }
 
 // ---------------------------------------------------------------- block Gauss-Seidel, one colour
-// u_s += A_ss^{-1} (g - A u)_s for every patch s of the colour, R columns at once
-template <class T, int DPF>
+template <class T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
+};
+
+// u_s += A_ss^{-1} (g - A u)_s for every patch s of the colour, R = 2^lgR columns at
+// once.  The patch's index tables, the element-matrix rows of its facets and its
+// block inverse are first staged in shared memory with independent, coalesced
+// pair-wide loads; the residual and the block solve then read only shared memory
+// (one broadcast entry per R columns).  A thread owns RB rows of one column.
+template <class T, int DPF, int RB>
 __global__ void __launch_bounds__(MT)
-gs_m_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int R, const int *__restrict__ patch_nf,
+gs_m_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const int *__restrict__ patch_nf,
             const int *__restrict__ patch_facets, const int *__restrict__ patch_nc,
             const int *__restrict__ patch_cells, const int *__restrict__ slot_src,
             const int *__restrict__ cell_int, const T *__restrict__ A, const T *__restrict__ Pinv,
             const T *__restrict__ g, T *__restrict__ u) {
+    using T2 = typename Pair<T>::type;
     constexpr int NLOC = 3 * DPF;
+    const int R = 1 << lgR;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *xs = reinterpret_cast<T *>(smraw);          // pc_max * NLOC * R
-    T *rs = xs + (size_t)pc_max * NLOC * R;         // np_max * R
+    T *xs = reinterpret_cast<T *>(smraw);                       // pc_max * NLOC * R
+    T *rs = xs + ((size_t)pc_max * NLOC << lgR);                // np_max * R
+    T *As = rs + ((size_t)np_max << lgR);                       // pf_max * 2 * NLOC * DPF
+    T *Ps = As + (size_t)pf_max * 2 * NLOC * DPF;               // np_max * np_max
+    int *jt = reinterpret_cast<int *>(Ps + (size_t)np_max * np_max);   // pc_max * 3
+    int *rowF = jt + pc_max * 3;                                // pf_max
+    int *rowA = rowF + pf_max;                                  // pf_max * 2
+    int *rowS = rowA + pf_max * 2;                              // pf_max * 2
     const int p = p0 + blockIdx.x;
     if (p >= p1) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
-    for (int t = tid; t < ncell * NLOC * R; t += nt) {
-        const int r = t % R, sl = t / R, si = sl / NLOC, l = sl % NLOC;
-        const int c = patch_cells[(size_t)p * pc_max + si];
-        const int j = cell_int[3 * c + l / DPF];
-        xs[t] = j >= 0 ? u[((size_t)j * DPF + l % DPF) * R + r] : T(0);
+    for (int i = tid; i < ncell * 3; i += nt) {
+        const int c = patch_cells[(size_t)p * pc_max + i / 3];
+        jt[i] = cell_int[3 * c + i % 3];
     }
-    __syncthreads();
-    for (int t = tid; t < np * R; t += nt) {
-        const int r = t % R, row = t / R, js = row / DPF, d = row % DPF;
-        const int F = patch_facets[(size_t)p * pf_max + js];
-        T acc = g[((size_t)F * DPF + d) * R + r];
-#pragma unroll
+    for (int js = tid; js < nf; js += nt) {
+        rowF[js] = patch_facets[(size_t)p * pf_max + js];
         for (int q = 0; q < 2; ++q) {
             const int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
             const int si = src >> 2, lf = src & 3;
             const int c = patch_cells[(size_t)p * pc_max + si];
-            const T *Ac = A + (size_t)c * NLOC * NLOC + lf * DPF + d;
-            const T *xc = xs + (size_t)si * NLOC * R + r;
-#pragma unroll
-            for (int col = 0; col < NLOC; ++col) acc -= Ac[col * NLOC] * xc[col * R];
+            rowA[2 * js + q] = c * NLOC * NLOC + lf * DPF;
+            rowS[2 * js + q] = si;
         }
-        rs[t] = acc;
+    }
+    {   // block inverse, whole np_max x np_max block (contiguous)
+        const T2 *src = reinterpret_cast<const T2 *>(Pinv + (size_t)p * np_max * np_max);
+        T2 *dst = reinterpret_cast<T2 *>(Ps);
+        const int n2 = np_max * np_max / 2;
+#pragma unroll 4
+        for (int i = tid; i < n2; i += nt) dst[i] = src[i];
     }
     __syncthreads();
-    const T *Pi = Pinv + (size_t)p * np_max * np_max;
-    for (int t = tid; t < np * R; t += nt) {
-        const int r = t % R, row = t / R;
-        T a0 = 0, a1 = 0;
-        int j = 0;
-        for (; j + 2 <= np; j += 2) {
-            a0 += Pi[(size_t)j * np_max + row] * rs[j * R + r];
-            a1 += Pi[(size_t)(j + 1) * np_max + row] * rs[(j + 1) * R + r];
+    {   // rows (lf, 0..DPF) of every column of the two cells of each patch facet
+        constexpr int U = DPF / 2;              // pairs per column
+        const int n2 = nf * 2 * NLOC * U;
+#pragma unroll 4
+        for (int i = tid; i < n2; i += nt) {
+            const int h = i % U, col = (i / U) % NLOC, jq = i / (U * NLOC);
+            const T2 *src = reinterpret_cast<const T2 *>(A + rowA[jq] + col * NLOC) + h;
+            reinterpret_cast<T2 *>(As)[i] = *src;
         }
-        if (j < np) a0 += Pi[(size_t)j * np_max + row] * rs[j * R + r];
-        const int F = patch_facets[(size_t)p * pf_max + row / DPF];
-        u[((size_t)F * DPF + row % DPF) * R + r] += a0 + a1;
+    }
+#pragma unroll 4
+    for (int t = tid; t < (ncell * NLOC) << lgR; t += nt) {
+        const int r = t & (R - 1), sl = t >> lgR, si = sl / NLOC, l = sl - si * NLOC;
+        const int j = jt[si * 3 + l / DPF];
+        xs[t] = j >= 0 ? u[(((size_t)j * DPF + l % DPF) << lgR) + r] : T(0);
+    }
+    __syncthreads();
+    const int nrb = np / RB;
+    for (int t = tid; t < nrb << lgR; t += nt) {
+        const int r = t & (R - 1), row0 = (t >> lgR) * RB, js = row0 / DPF, d0 = row0 - js * DPF;
+        const int F = rowF[js];
+        T acc[RB];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) acc[b] = g[(((size_t)F * DPF + d0 + b) << lgR) + r];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const T *Ac = As + (size_t)(2 * js + q) * NLOC * DPF + d0;
+            const T *xc = xs + ((size_t)rowS[2 * js + q] * NLOC << lgR) + r;
+#pragma unroll
+            for (int col = 0; col < NLOC; ++col) {
+                const T xv = xc[col << lgR];
+                const T *a = Ac + col * DPF;
+#pragma unroll
+                for (int b = 0; b < RB; ++b) acc[b] -= a[b] * xv;
+            }
+        }
+#pragma unroll
+        for (int b = 0; b < RB; ++b) rs[((row0 + b) << lgR) + r] = acc[b];
+    }
+    __syncthreads();
+    for (int t = tid; t < nrb << lgR; t += nt) {
+        const int r = t & (R - 1), row0 = (t >> lgR) * RB;
+        T acc[RB];
+#pragma unroll
+        for (int b = 0; b < RB; ++b) acc[b] = 0;
+#pragma unroll 4
+        for (int j = 0; j < np; ++j) {
+            const T xv = rs[(j << lgR) + r];
+            const T *pj = Ps + j * np_max + row0;
+#pragma unroll
+            for (int b = 0; b < RB; ++b) acc[b] += pj[b] * xv;
+        }
+        const int js = row0 / DPF, d0 = row0 - js * DPF;
+        const size_t o = (((size_t)rowF[js] * DPF + d0) << lgR) + r;
+#pragma unroll
+        for (int b = 0; b < RB; ++b) u[o + ((size_t)b << lgR)] += acc[b];
     }
 }
 
@@ -546,41 +626,55 @@ uzawa_update_m_kernel(int64_t nc, int dpf, int R, const int *__restrict__ cell_i
 // covers whole rows of every R (a power of two <= 64), so each thread keeps one column
 int krylov_m_blocks() { return 608; }
 
+int log2_width(int R) {
+    int l = 0;
+    while ((1 << l) < R) ++l;
+    return l;
+}
+
 template <class T>
 cudaError_t launch_apply_m(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *x, const T *g, T *y,
                            cudaStream_t s) {
-    const int64_t n = L.n_int * op.dpf * R;
-    if (n == 0) return cudaSuccess;
-    const unsigned nb = nblk(n, MT);
+    const int lg = log2_width(R);
+    if (L.n_int == 0) return cudaSuccess;
     note_launches(1);
+#define HDG_APPLY_M(D, B)                                                                                      \
+    case D:                                                                                                    \
+        apply_m_kernel<T, D, B><<<nblk((L.n_int * (D / B)) << lg, MT), MT, 0, s>>>(L.n_int, lg, L.facet_adj.p, \
+                                                                                L.cell_int.p, A, x, g, y);     \
+        break;
     switch (op.dpf) {
-    case 2: apply_m_kernel<T, 2><<<nb, MT, 0, s>>>(L.n_int, R, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
-    case 4: apply_m_kernel<T, 4><<<nb, MT, 0, s>>>(L.n_int, R, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
-    case 6: apply_m_kernel<T, 6><<<nb, MT, 0, s>>>(L.n_int, R, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
-    case 8: apply_m_kernel<T, 8><<<nb, MT, 0, s>>>(L.n_int, R, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
-    case 10: apply_m_kernel<T, 10><<<nb, MT, 0, s>>>(L.n_int, R, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
+        HDG_APPLY_M(2, 2)
+        HDG_APPLY_M(4, 4)
+        HDG_APPLY_M(6, 2)
+        HDG_APPLY_M(8, 4)
+        HDG_APPLY_M(10, 2)
     default: return cudaErrorInvalidValue;
     }
+#undef HDG_APPLY_M
     return cudaGetLastError();
 }
 
 size_t gs_m_smem(const DevLevel &L, const DevOperator &op, int R, size_t word) {
-    return word * ((size_t)L.pc_max * op.nloc + op.np_max) * R;
+    return word * (((size_t)L.pc_max * op.nloc + op.np_max) * R + (size_t)L.pf_max * 2 * op.nloc * op.dpf +
+                   (size_t)op.np_max * op.np_max) +
+           sizeof(int) * ((size_t)L.pc_max * 3 + (size_t)L.pf_max * 5);
 }
 
 namespace {
-template <class T, int DPF>
+template <class T, int DPF, int RB>
 cudaError_t gs_m_launch(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *Pinv, int colour,
                         const T *g, T *u, cudaStream_t s) {
     const int p0 = L.colour_ptr[colour], p1 = L.colour_ptr[colour + 1];
     if (p1 <= p0) return cudaSuccess;
     const size_t smem = gs_m_smem(L, op, R, sizeof(T));
-    auto kern = gs_m_kernel<T, DPF>;
+    auto kern = gs_m_kernel<T, DPF, RB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launches(1);
-    kern<<<p1 - p0, MT, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, R, L.patch_nf.p, L.patch_facets.p,
-                                   L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, A, Pinv, g, u);
+    kern<<<p1 - p0, MT, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, log2_width(R), L.patch_nf.p,
+                                   L.patch_facets.p, L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p,
+                                   A, Pinv, g, u);
     return cudaGetLastError();
 }
 } // namespace
@@ -589,11 +683,11 @@ template <class T>
 cudaError_t launch_gs_colour_m(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *Pinv,
                                int colour, const T *g, T *u, cudaStream_t s) {
     switch (op.dpf) {
-    case 2: return gs_m_launch<T, 2>(L, op, R, A, Pinv, colour, g, u, s);
-    case 4: return gs_m_launch<T, 4>(L, op, R, A, Pinv, colour, g, u, s);
-    case 6: return gs_m_launch<T, 6>(L, op, R, A, Pinv, colour, g, u, s);
-    case 8: return gs_m_launch<T, 8>(L, op, R, A, Pinv, colour, g, u, s);
-    case 10: return gs_m_launch<T, 10>(L, op, R, A, Pinv, colour, g, u, s);
+    case 2: return gs_m_launch<T, 2, 2>(L, op, R, A, Pinv, colour, g, u, s);
+    case 4: return gs_m_launch<T, 4, 4>(L, op, R, A, Pinv, colour, g, u, s);
+    case 6: return gs_m_launch<T, 6, 2>(L, op, R, A, Pinv, colour, g, u, s);
+    case 8: return gs_m_launch<T, 8, 4>(L, op, R, A, Pinv, colour, g, u, s);
+    case 10: return gs_m_launch<T, 10, 2>(L, op, R, A, Pinv, colour, g, u, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -261,14 +261,19 @@ def fourier_forcing_2d(j: int, n_modes: int = 8, seed0: int = 20230312):
     rs = rng.integers(1, 9, size=(n_modes, 2))
     eta = rng.uniform(0.0, 2 * PI, n_modes)
 
-    def f(x):
-        out = np.zeros((x.shape[0], 2))
+    def f(x, xp=np):
+        """x: (n, 2) points; xp: the array module of x (numpy, or torch for device arrays)."""
+        out = xp.zeros_like(x)
         for m in range(n_modes):
-            arg = 2 * PI * (pq[m, 0] * x[:, 0] + pq[m, 1] * x[:, 1]) + th[m]
-            out += np.sin(arg)[:, None] * a[m][None, :]
-            argp = 2 * PI * (rs[m, 0] * x[:, 0] + rs[m, 1] * x[:, 1]) + eta[m]
+            arg = 2 * PI * (float(pq[m, 0]) * x[:, 0] + float(pq[m, 1]) * x[:, 1]) + float(th[m])
+            s = xp.sin(arg)
+            out[:, 0] += float(a[m, 0]) * s
+            out[:, 1] += float(a[m, 1]) * s
             # ∇ of b cos(argp)
-            out += (-b[m] * np.sin(argp) * 2 * PI)[:, None] * rs[m][None, :]
+            argp = 2 * PI * (float(rs[m, 0]) * x[:, 0] + float(rs[m, 1]) * x[:, 1]) + float(eta[m])
+            sp = (-2 * PI * float(b[m])) * xp.sin(argp)
+            out[:, 0] += float(rs[m, 0]) * sp
+            out[:, 1] += float(rs[m, 1]) * sp
         return out
 
     return f
