@@ -245,8 +245,9 @@ int small_levels(hdg_ctx *ctx) {
 template <class T>
 void mg_h(hdg_ctx *ctx, int l, int m, bool zero_init, cudaStream_t s) {
     if (l >= 1 && l <= ctx->small_Ls) {
-        const size_t smem = std::is_same<T, double>::value ? ctx->small_smem_d : ctx->small_smem_f;
-        CK(launch_mg_small<T>(small_of<T>(ctx), l, m, zero_init, smem, s));
+        const bool dbl = std::is_same<T, double>::value;
+        CK(launch_mg_small<T>(small_of<T>(ctx), l, m, zero_init, dbl ? ctx->small_smem_d : ctx->small_smem_f,
+                              dbl ? ctx->small_cs_d : ctx->small_cs_f, s));
         return;
     }
     if (l == 0) {
@@ -1172,9 +1173,15 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
     CK(launch_coarse_inverse(ctx->L[0], ctx->coarse_inv.p, ctx->n0, ctx->status_flag.p, s));
     ctx->small_Ls = small_levels(ctx);
     if (ctx->small_Ls >= 1) {
-        ctx->small_smem_d = fill_small<double>(ctx, ctx->small_Ls);
-        ctx->small_smem_f = fill_small<float>(ctx, ctx->small_Ls);
-        if (ctx->small_smem_d > 200 * 1024) ctx->small_Ls = -1;
+        const size_t cb_d = fill_small<double>(ctx, ctx->small_Ls);
+        const size_t cb_f = fill_small<float>(ctx, ctx->small_Ls);
+        int npm = 2;
+        for (int l = 1; l <= ctx->small_Ls; ++l) npm = std::max(npm, ctx->L[l].op0.np_max);
+        ctx->small_cs_d = mg_small_cluster_size<double>(cb_d, npm * (int)sizeof(double));
+        ctx->small_cs_f = mg_small_cluster_size<float>(cb_f, npm * (int)sizeof(float));
+        ctx->small_smem_d = mg_small_smem(cb_d, std::max(ctx->small_cs_d, 1), npm * (int)sizeof(double));
+        ctx->small_smem_f = mg_small_smem(cb_f, std::max(ctx->small_cs_f, 1), npm * (int)sizeof(float));
+        if (ctx->small_cs_d == 0 || ctx->small_cs_f == 0) ctx->small_Ls = -1;
     }
     ctx->n_dof = LJ.n_int * op.dpf;
     const int64_t nd = std::max<int64_t>(ctx->n_dof, 1);

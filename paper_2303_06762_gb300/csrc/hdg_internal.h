@@ -90,7 +90,7 @@ struct SmallLayout {
 // views of the smallest lowest-order levels for the single-block MG kernel (mg_small.cu)
 constexpr int SMALL_MAX_LEVELS = 6;
 constexpr int SMALL_MAX_COLOURS = 15;
-constexpr int64_t SMALL_MAX_CELLS = 2048;
+constexpr int64_t SMALL_MAX_CELLS = 32768;
 
 template <class T>
 struct SmallLevel {
@@ -221,7 +221,8 @@ struct hdg_ctx {
     hdg::DBuf<double> pcm_in, pcm_out;
     // fused MG_h on levels 0..small_Ls (one thread block), -1 when not used
     int small_Ls = -1;
-    size_t small_smem_d = 0, small_smem_f = 0;
+    size_t small_smem_d = 0, small_smem_f = 0;   // per-CTA shared memory of the fused kernel
+    int small_cs_d = 1, small_cs_f = 1;          // its cluster size
     hdg::SmallParams<double> small_d;
     hdg::SmallParams<float> small_f;
 };
@@ -286,8 +287,12 @@ cudaError_t launch_hp_prolong_add(int k, int64_t n_int, const T *d0, T *u, cudaS
 cudaError_t launch_coarse_apply(const double *inv, int64_t n, const double *g, double *u,
                                 cudaStream_t s);
 template <class T>
-cudaError_t launch_mg_small(const SmallParams<T> &S, int l, int m, bool zero_init, size_t smem_bytes,
-                            cudaStream_t s);
+cudaError_t launch_mg_small(const SmallParams<T> &S, int l, int m, bool zero_init, size_t smem_per_cta,
+                            int cluster_size, cudaStream_t s);
+// per-CTA shared memory and cluster size (16/8/4/2 CTAs, 1 = one block, 0 = does not fit)
+size_t mg_small_smem(size_t colour_bytes, int csize, int np_max_bytes);
+template <class T>
+int mg_small_cluster_size(size_t colour_bytes, int np_max_bytes);
 cudaError_t launch_d2f(const double *x, float *y, int64_t n, cudaStream_t s);
 cudaError_t launch_f2d(const float *x, double *y, int64_t n, cudaStream_t s);
 template <class T>

@@ -1,38 +1,78 @@
-// Algorithm 1 (MG_h) on the smallest lowest-order levels in one thread block.
+// Algorithm 1 (MG_h) on the smallest lowest-order levels in one launch of a
+// thread-block cluster.
 //
 // On the coarse levels of a deep hierarchy each colour phase of the block
-// Gauss-Seidel smoother touches a few hundred patches, and the variable
-// V-cycle doubles the smoothing steps per level (m(l-1) = 2 m(l)), so these
-// levels produce most of the launches of a preconditioner application while
-// moving little data.  Here one 1024-thread block runs the whole recursion
-// below a level Ls (pre-smoothing colour by colour, residual, restriction,
-// recursion, the FP64 dense coarse solve, prolongation with harmonic extension,
-// post-smoothing in reverse colour order) with a block barrier between steps
-// instead of a kernel boundary.  The arithmetic of every step is the one of the
-// multi-block kernels in ops.cu (same formulas, same order per unknown).
+// Gauss-Seidel smoother touches a few hundred to a few thousand patches, and
+// the variable V-cycle doubles the smoothing steps per level (m(l-1) = 2 m(l)),
+// so these levels produce most of the launches of a preconditioner
+// application while moving little data.  Here one cluster of up to 16 CTAs
+// (one per SM, 1024 threads each) runs the whole recursion below a level Ls:
+// pre-smoothing colour by colour, residual, restriction, recursion, the FP64
+// dense coarse solve, prolongation with harmonic extension, post-smoothing in
+// reverse colour order.  Steps are separated by the hardware cluster barrier
+// (barrier.cluster arrive.release / wait.acquire) instead of kernel
+// boundaries.  Values written inside the kernel are read through L2 (ld.cg),
+// since the CTAs of a cluster sit on different SMs.  Every CTA executes the same
+// sequence of barriers: the control flow depends on kernel arguments only.
+// The arithmetic of every step is the one of the multi-block kernels in ops.cu
+// (same formulas, same order per unknown).
 #include <cuda_runtime.h>
+
+#include <algorithm>
 
 #include "hdg_internal.h"
 
 namespace hdg {
 namespace {
 
+// the CTAs of the launch (a cluster, or one block) acting as one team
+struct Team {
+    int rank, size;
+    __device__ int tid() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
+    __device__ int nthreads() const { return size * (int)blockDim.x; }
+    __device__ void sync() const {
+        if (size == 1) {
+            __syncthreads();
+        } else {
+            // non-.aligned forms: no assumption on warp convergence at the call
+            asm volatile("barrier.cluster.arrive.release;\n"
+                         "barrier.cluster.wait.acquire;\n" ::: "memory");
+        }
+    }
+};
+
+__device__ __forceinline__ Team make_team() {
+    unsigned r, n;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+    return Team{(int)r, (int)n};
+}
+
+// loads of values written during the kernel (possibly by another SM): through L2
 template <class T>
-__device__ void blk_fill(T *u, int n) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) u[i] = T(0);
+__device__ __forceinline__ T ld(const T *p) {
+    return __ldcg(p);
 }
 
 template <class T>
-__device__ void blk_gs_colour(const SmallLevel<T> &L, int c, const T *g, T *u, T *rs) {
+__device__ void blk_fill(const Team &tm, T *u, int n) {
+    for (int i = tm.tid(); i < n; i += tm.nthreads()) u[i] = T(0);
+}
+
+// one colour phase: CTA `rank` owns the patches p0 + rank + i*size, and its
+// residual rows stay in its shared memory between the two passes
+template <class T>
+__device__ void blk_gs_colour(const Team &tm, const SmallLevel<T> &L, int c, const T *g, T *u, T *rs) {
     const int p0 = L.colour_ptr[c], p1 = L.colour_ptr[c + 1];
-    const int items = (p1 - p0) * L.np_max;
+    const int mine = (p1 - p0 - tm.rank + tm.size - 1) / tm.size;
+    const int items = (mine > 0 ? mine : 0) * L.np_max;
     for (int w = threadIdx.x; w < items; w += blockDim.x) {
-        const int p = p0 + w / L.np_max, t = w % L.np_max;
+        const int p = p0 + tm.rank + (w / L.np_max) * tm.size, t = w % L.np_max;
         const int np = 2 * L.patch_nf[p];
         if (t >= np) continue;
         const int js = t >> 1, d = t & 1;
         const int F = L.patch_facets[p * L.pf_max + js];
-        T acc = g[2 * F + d];
+        T acc = ld(g + 2 * F + d);
         for (int q = 0; q < 2; ++q) {
             const int src = L.slot_src[(p * L.pf_max + js) * 2 + q];
             const int si = src >> 2, lf = src & 3;
@@ -41,34 +81,34 @@ __device__ void blk_gs_colour(const SmallLevel<T> &L, int c, const T *g, T *u, T
 #pragma unroll
             for (int col = 0; col < 6; ++col) {
                 const int j = L.cell_int[3 * cell + col / 2];
-                if (j >= 0) acc -= Ac[col * 6] * u[2 * j + (col & 1)];
+                if (j >= 0) acc -= Ac[col * 6] * ld(u + 2 * j + (col & 1));
             }
         }
         rs[w] = acc;
     }
     __syncthreads();
     for (int w = threadIdx.x; w < items; w += blockDim.x) {
-        const int p = p0 + w / L.np_max, t = w % L.np_max;
+        const int p = p0 + tm.rank + (w / L.np_max) * tm.size, t = w % L.np_max;
         const int np = 2 * L.patch_nf[p];
         if (t >= np) continue;
         const T *Pi = L.Pinv + (size_t)p * L.np_max * L.np_max;
         const T *rp = rs + (w / L.np_max) * L.np_max;
         T acc = 0;
         for (int j = 0; j < np; ++j) acc += Pi[j * L.np_max + t] * rp[j];
-        const int F = L.patch_facets[p * L.pf_max + (t >> 1)];
-        u[2 * F + (t & 1)] += acc;
+        T *dst = u + 2 * L.patch_facets[p * L.pf_max + (t >> 1)] + (t & 1);
+        *dst = ld(dst) + acc;
     }
-    __syncthreads();
+    tm.sync();
 }
 
 template <class T>
-__device__ void blk_sweep(const SmallLevel<T> &L, const T *g, T *u, bool reverse, T *rs) {
-    for (int i = 0; i < L.n_colours; ++i) blk_gs_colour(L, reverse ? L.n_colours - 1 - i : i, g, u, rs);
+__device__ void blk_sweep(const Team &tm, const SmallLevel<T> &L, const T *g, T *u, bool reverse, T *rs) {
+    for (int i = 0; i < L.n_colours; ++i) blk_gs_colour(tm, L, reverse ? L.n_colours - 1 - i : i, g, u, rs);
 }
 
 template <class T>
-__device__ void blk_residual(const SmallLevel<T> &L, const T *g, const T *u, T *r) {
-    for (int idx = threadIdx.x; idx < 2 * L.n_int; idx += blockDim.x) {
+__device__ void blk_residual(const Team &tm, const SmallLevel<T> &L, const T *g, const T *u, T *r) {
+    for (int idx = tm.tid(); idx < 2 * L.n_int; idx += tm.nthreads()) {
         const int i = idx >> 1, d = idx & 1;
         T acc = 0;
         for (int q = 0; q < 2; ++q) {
@@ -79,20 +119,20 @@ __device__ void blk_residual(const SmallLevel<T> &L, const T *g, const T *u, T *
 #pragma unroll
             for (int col = 0; col < 6; ++col) {
                 const int j = L.cell_int[3 * cell + col / 2];
-                if (j >= 0) acc += Ac[col * 6] * u[2 * j + (col & 1)];
+                if (j >= 0) acc += Ac[col * 6] * ld(u + 2 * j + (col & 1));
             }
         }
-        r[idx] = g[idx] - acc;
+        r[idx] = ld(g + idx) - acc;
     }
-    __syncthreads();
+    tm.sync();
 }
 
 // g_c = (I_{l-1}^l)^T r_f  (F = fine level l, C = coarse level l-1)
 template <class T>
-__device__ void blk_restrict(const SmallLevel<T> &F, const SmallLevel<T> &C, const T *rf, T *gc) {
-    for (int P = threadIdx.x; P < F.ncc; P += blockDim.x) {
+__device__ void blk_restrict(const Team &tm, const SmallLevel<T> &F, const SmallLevel<T> &C, const T *rf, T *gc) {
+    for (int P = tm.tid(); P < F.ncc; P += tm.nthreads()) {
         T rT[6];
-        for (int t = 0; t < 6; ++t) rT[t] = rf[2 * F.tr_slots[9 * P + 6 + t / 2] + (t & 1)];
+        for (int t = 0; t < 6; ++t) rT[t] = ld(rf + 2 * F.tr_slots[9 * P + 6 + t / 2] + (t & 1));
         const T *Hk = F.H + (size_t)P * 72;
         for (int c = 0; c < 12; ++c) {
             T acc = 0;
@@ -100,8 +140,8 @@ __device__ void blk_restrict(const SmallLevel<T> &F, const SmallLevel<T> &C, con
             F.ct1[12 * P + c] = acc;
         }
     }
-    __syncthreads();
-    for (int P = threadIdx.x; P < F.ncc; P += blockDim.x) {
+    tm.sync();
+    for (int P = tm.tid(); P < F.ncc; P += tm.nthreads()) {
         T z[12];
         for (int s = 0; s < 6; ++s) {
             const int i = F.tr_slots[9 * P + s];
@@ -109,7 +149,7 @@ __device__ void blk_restrict(const SmallLevel<T> &F, const SmallLevel<T> &C, con
             const int nb = F.tr_nbr[6 * P + s];
             const int Q = nb >> 4, s2 = nb & 15;
             for (int c = 0; c < 2; ++c)
-                z[2 * s + c] = rf[2 * i + c] + F.ct1[12 * P + 2 * s + c] + F.ct1[12 * Q + 2 * s2 + c];
+                z[2 * s + c] = ld(rf + 2 * i + c) + ld(F.ct1 + 12 * P + 2 * s + c) + ld(F.ct1 + 12 * Q + 2 * s2 + c);
         }
         const T *Wk = F.W + (size_t)P * 72;
         for (int col = 0; col < 6; ++col) {
@@ -118,25 +158,26 @@ __device__ void blk_restrict(const SmallLevel<T> &F, const SmallLevel<T> &C, con
             F.ct2[6 * P + col] = acc;
         }
     }
-    __syncthreads();
-    for (int G = threadIdx.x; G < C.n_int; G += blockDim.x) {
+    tm.sync();
+    for (int G = tm.tid(); G < C.n_int; G += tm.nthreads()) {
         T a0 = 0, a1 = 0;
         for (int q = 0; q < 2; ++q) {
             const int adj = C.facet_adj[2 * G + q];
             const int K = adj >> 2, lf = adj & 3;
-            a0 += F.ct2[6 * K + 2 * lf];
-            a1 += F.ct2[6 * K + 2 * lf + 1];
+            a0 += ld(F.ct2 + 6 * K + 2 * lf);
+            a1 += ld(F.ct2 + 6 * K + 2 * lf + 1);
         }
         gc[2 * G] = a0;
         gc[2 * G + 1] = a1;
     }
-    __syncthreads();
+    tm.sync();
 }
 
 // u_f += I_{l-1}^l u_c
 template <class T>
-__device__ void blk_prolong_add(const SmallLevel<T> &F, const SmallLevel<T> &C, const T *uc, T *uf, T *tmp) {
-    for (int b = threadIdx.x; b < F.nB; b += blockDim.x) {
+__device__ void blk_prolong_add(const Team &tm, const SmallLevel<T> &F, const SmallLevel<T> &C, const T *uc, T *uf,
+                                T *tmp) {
+    for (int b = tm.tid(); b < F.nB; b += tm.nthreads()) {
         T v0 = 0, v1 = 0;
         for (int q = 0; q < 2; ++q) {
             const int src = F.tr_fineB_src[2 * b + q];
@@ -146,7 +187,7 @@ __device__ void blk_prolong_add(const SmallLevel<T> &F, const SmallLevel<T> &C, 
                 const int j = C.cell_int[3 * P + fp];
                 if (j < 0) continue;
                 for (int cq = 0; cq < 2; ++cq) {
-                    const T u = uc[2 * j + cq];
+                    const T u = ld(uc + 2 * j + cq);
                     v0 += Wk[(2 * s) * 6 + 2 * fp + cq] * u;
                     v1 += Wk[(2 * s + 1) * 6 + 2 * fp + cq] * u;
                 }
@@ -155,49 +196,50 @@ __device__ void blk_prolong_add(const SmallLevel<T> &F, const SmallLevel<T> &C, 
         const int i = F.tr_fineB[b];
         tmp[2 * i] = v0;
         tmp[2 * i + 1] = v1;
-        uf[2 * i] += v0;
-        uf[2 * i + 1] += v1;
+        uf[2 * i] = ld(uf + 2 * i) + v0;
+        uf[2 * i + 1] = ld(uf + 2 * i + 1) + v1;
     }
-    __syncthreads();
-    for (int P = threadIdx.x; P < F.ncc; P += blockDim.x) {
+    tm.sync();
+    for (int P = tm.tid(); P < F.ncc; P += tm.nthreads()) {
         T bb[12];
         for (int s = 0; s < 6; ++s) {
             const int i = F.tr_slots[9 * P + s];
-            bb[2 * s] = i >= 0 ? tmp[2 * i] : T(0);
-            bb[2 * s + 1] = i >= 0 ? tmp[2 * i + 1] : T(0);
+            bb[2 * s] = i >= 0 ? ld(tmp + 2 * i) : T(0);
+            bb[2 * s + 1] = i >= 0 ? ld(tmp + 2 * i + 1) : T(0);
         }
         const T *Hk = F.H + (size_t)P * 72;
         for (int t = 0; t < 6; ++t) {
             T acc = 0;
             for (int c = 0; c < 12; ++c) acc += Hk[t * 12 + c] * bb[c];
-            uf[2 * F.tr_slots[9 * P + 6 + t / 2] + (t & 1)] += acc;
+            T *dst = uf + 2 * F.tr_slots[9 * P + 6 + t / 2] + (t & 1);
+            *dst = ld(dst) + acc;
         }
     }
-    __syncthreads();
+    tm.sync();
 }
 
 // u_0 = inv g_0 in FP64 (one warp per row)
 template <class T>
-__device__ void blk_coarse(const SmallParams<T> &S) {
+__device__ void blk_coarse(const Team &tm, const SmallParams<T> &S) {
     const SmallLevel<T> &L0 = S.lv[0];
     const int n = 2 * L0.n_int;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.g0d[i] = (double)L0.g[i];
-    __syncthreads();
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int i = tm.tid(); i < n; i += tm.nthreads()) S.g0d[i] = (double)ld(L0.g + i);
+    tm.sync();
+    const int lane = threadIdx.x & 31, wid = tm.tid() >> 5, nw = tm.nthreads() >> 5;
     for (int row = wid; row < n; row += nw) {
         double acc = 0.0;
-        for (int j = lane; j < n; j += 32) acc += S.inv[(size_t)row * n + j] * S.g0d[j];
+        for (int j = lane; j < n; j += 32) acc += S.inv[(size_t)row * n + j] * ld(S.g0d + j);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         if (lane == 0) L0.u[row] = (T)acc;
     }
-    __syncthreads();
+    tm.sync();
 }
 
 // MG_h(l_top, g, u, m, q) without recursion: an explicit walk down and up the
 // levels, where visit[l] counts the coarse-grid corrections done at level l (q of
 // them: 1 for the V-cycle, 2 for the W-cycle).  Every thread holds the same state.
 template <class T>
-__device__ void blk_mg(const SmallParams<T> &S, int top, int m_top, bool zero_top, T *rs) {
+__device__ void blk_mg(const Team &tm, const SmallParams<T> &S, int top, int m_top, bool zero_top, T *rs) {
     int mlev[SMALL_MAX_LEVELS];
     int visit[SMALL_MAX_LEVELS];
     int l = top;
@@ -207,7 +249,7 @@ __device__ void blk_mg(const SmallParams<T> &S, int top, int m_top, bool zero_to
     while (true) {
         if (descending) {
             if (l == 0) {
-                blk_coarse(S);
+                blk_coarse(tm, S);
                 descending = false;
                 l = 1;
                 continue;
@@ -215,12 +257,12 @@ __device__ void blk_mg(const SmallParams<T> &S, int top, int m_top, bool zero_to
             const SmallLevel<T> &L = S.lv[l];
             const SmallLevel<T> &C = S.lv[l - 1];
             if (zero) {
-                blk_fill(L.u, 2 * L.n_int);
-                __syncthreads();
+                blk_fill(tm, L.u, 2 * L.n_int);
+                tm.sync();
             }
-            for (int j = 0; j < mlev[l]; ++j) blk_sweep(L, L.g, L.u, false, rs);
-            blk_residual(L, L.g, L.u, L.r);
-            blk_restrict(L, C, L.r, C.g);
+            for (int j = 0; j < mlev[l]; ++j) blk_sweep(tm, L, L.g, L.u, false, rs);
+            blk_residual(tm, L, L.g, L.u, L.r);
+            blk_restrict(tm, L, C, L.r, C.g);
             visit[l] = 0;
             mlev[l - 1] = S.q == 1 ? mlev[l] * S.growth : mlev[l];
             zero = true;
@@ -236,8 +278,8 @@ __device__ void blk_mg(const SmallParams<T> &S, int top, int m_top, bool zero_to
             }
             const SmallLevel<T> &L = S.lv[l];
             const SmallLevel<T> &C = S.lv[l - 1];
-            blk_prolong_add(L, C, C.u, L.u, L.t);
-            for (int j = 0; j < mlev[l]; ++j) blk_sweep(L, L.g, L.u, true, rs);
+            blk_prolong_add(tm, L, C, C.u, L.u, L.t);
+            for (int j = 0; j < mlev[l]; ++j) blk_sweep(tm, L, L.g, L.u, true, rs);
             if (l == top) break;
             l = l + 1;
         }
@@ -248,23 +290,74 @@ template <class T>
 __global__ void __launch_bounds__(1024) mg_small_kernel(SmallParams<T> S, int l, int m, int zero_init) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *rs = reinterpret_cast<T *>(smraw);
-    blk_mg(S, l, m, zero_init != 0, rs);
+    const Team tm = make_team();
+    blk_mg(tm, S, l, m, zero_init != 0, rs);
+}
+
+cudaLaunchConfig_t cluster_config(int csize, size_t smem, cudaStream_t s, cudaLaunchAttribute &at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(csize);
+    cfg.blockDim = dim3(1024);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    at.id = cudaLaunchAttributeClusterDimension;
+    at.val.clusterDim.x = csize;
+    at.val.clusterDim.y = 1;
+    at.val.clusterDim.z = 1;
+    cfg.attrs = &at;
+    cfg.numAttrs = 1;
+    return cfg;
 }
 
 } // namespace
 
-template <class T>
-cudaError_t launch_mg_small(const SmallParams<T> &S, int l, int m, bool zero_init, size_t smem_bytes,
-                            cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(mg_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem_bytes);
-    if (e != cudaSuccess) return e;
-    note_launches(1);
-    mg_small_kernel<T><<<1, 1024, smem_bytes, s>>>(S, l, m, zero_init ? 1 : 0);
-    return cudaGetLastError();
+// shared memory per CTA when the largest colour phase (colour_bytes of residual
+// rows) is split over csize CTAs; slack covers the rounding to whole patches
+size_t mg_small_smem(size_t colour_bytes, int csize, int np_max_bytes) {
+    return (colour_bytes + csize - 1) / csize + (size_t)np_max_bytes + 16;
 }
 
-template cudaError_t launch_mg_small<double>(const SmallParams<double> &, int, int, bool, size_t, cudaStream_t);
-template cudaError_t launch_mg_small<float>(const SmallParams<float> &, int, int, bool, size_t, cudaStream_t);
+// largest cluster (16, 8, 4, 2 CTAs of 1024 threads) this device can run with the
+// shared memory of that split, or 1 (a single block); 0 if even one block does not fit
+template <class T>
+int mg_small_cluster_size(size_t colour_bytes, int np_max_bytes) {
+    if (cudaFuncSetAttribute(mg_small_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        cudaGetLastError();
+    for (int want : {16, 8, 4, 2}) {
+        const size_t smem = mg_small_smem(colour_bytes, want, np_max_bytes);
+        if (smem > 200 * 1024) continue;
+        if (cudaFuncSetAttribute(mg_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchAttribute at;
+        cudaLaunchConfig_t cfg = cluster_config(want, smem, nullptr, at);
+        int n = 0;
+        if (cudaOccupancyMaxActiveClusters(&n, mg_small_kernel<T>, &cfg) == cudaSuccess && n >= 1) return want;
+        cudaGetLastError();
+    }
+    return mg_small_smem(colour_bytes, 1, np_max_bytes) <= 200 * 1024 ? 1 : 0;
+}
+
+template <class T>
+cudaError_t launch_mg_small(const SmallParams<T> &S, int l, int m, bool zero_init, size_t smem, int csize,
+                            cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(mg_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    if (csize <= 1) {
+        mg_small_kernel<T><<<1, 1024, smem, s>>>(S, l, m, zero_init ? 1 : 0);
+        return cudaGetLastError();
+    }
+    cudaLaunchAttribute at;
+    cudaLaunchConfig_t cfg = cluster_config(csize, smem, s, at);
+    return cudaLaunchKernelEx(&cfg, mg_small_kernel<T>, S, l, m, zero_init ? 1 : 0);
+}
+
+template int mg_small_cluster_size<double>(size_t, int);
+template int mg_small_cluster_size<float>(size_t, int);
+template cudaError_t launch_mg_small<double>(const SmallParams<double> &, int, int, bool, size_t, int, cudaStream_t);
+template cudaError_t launch_mg_small<float>(const SmallParams<float> &, int, int, bool, size_t, int, cudaStream_t);
 
 } // namespace hdg
