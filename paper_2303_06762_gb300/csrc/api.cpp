@@ -68,6 +68,7 @@ void upload(hdg_ctx *ctx, DBuf<T> &b, const std::vector<T> &h) {
 void free_operator(DevOperator &op) {
     dfree(op.A);
     dfree(op.Af);
+    dfree(op.Alo);
     dfree(op.Fel);
     dfree(op.Pinv);
     dfree(op.Pinvf);
@@ -768,8 +769,21 @@ FgmresOutM fgmres_m(hdg_ctx *ctx, const double *b, double *x, double rtol, const
     std::vector<double> tol(R, -1.0), beta(R);
     std::vector<int> m_r(R);
     std::vector<char> done(R);
+    // outer operator: FP64, or double-FP32 with the mixed preconditioner
+    const bool df = ctx->prm.precision == HDG_MIXED_FP32;
+    if (df && !ctx->opk.alo_valid) {
+        const size_t na = (size_t)ctx->opk.nloc * ctx->opk.nloc * LJ.nc;
+        dalloc(ctx, ctx->opk.Alo, na);
+        CK(launch_split_lo(ctx->opk.A.p, ctx->opk.Af.p, ctx->opk.Alo.p, (int64_t)na, s));
+        ctx->opk.alo_valid = true;
+    }
+    if (df) dalloc(ctx, ctx->mxs, (size_t)std::max<int64_t>(n, 1));
+    auto outer = [&](const double *xx, const double *gg, double *yy) {
+        if (df) CK(launch_apply_df_m(LJ, ctx->opk, R, ctx->opk.Af.p, ctx->opk.Alo.p, xx, ctx->mxs.p, gg, yy, s));
+        else CK(launch_apply_m<double>(LJ, ctx->opk, R, ctx->opk.A.p, xx, gg, yy, s));
+    };
     while (true) {
-        CK(launch_apply_m<double>(LJ, ctx->opk, R, ctx->opk.A.p, x, b, V, s));   // V0 = b - A x
+        outer(x, b, V);   // V0 = b - A x
         norms2_m(ctx, V, ctx->n_dof, R, beta.data(), s);
         bool any = false;
         for (int r = 0; r < R; ++r) {
@@ -790,7 +804,7 @@ FgmresOutM fgmres_m(hdg_ctx *ctx, const double *b, double *x, double rtol, const
         for (int j = 0; j < Rst; ++j) {
             double *vj = V + (size_t)j * n, *zj = Z + (size_t)j * n;
             precond_m(ctx, vj, zj, R, s);
-            CK(launch_apply_m<double>(LJ, ctx->opk, R, ctx->opk.A.p, zj, nullptr, w, s));
+            outer(zj, nullptr, w);
             CK(launch_dots_m(V, j + 1, n, w, n, R, pt, s));
             CK(launch_reduce_partials_m(pt, j + 1, R, sm, stride, Ly.h1(), hb, s));
             CK(launch_update_dots_m(V, j + 1, n, w, n, R, hb, pt, 1, s));
@@ -1077,7 +1091,7 @@ void hdg_destroy(hdg_ctx *ctx) {
     for (auto *b : {&ctx->mV, &ctx->mZ, &ctx->mw, &ctx->mpart, &ctx->msmall, &ctx->mhbuf, &ctx->mF, &ctx->mU,
                     &ctx->mP, &ctx->mG, &ctx->mkr, &ctx->mkt, &ctx->mrd, &ctx->mzd, &ctx->pcm_in, &ctx->pcm_out})
         dfree(*b);
-    dfree(ctx->mkgf); dfree(ctx->mkuf); dfree(ctx->mkrf); dfree(ctx->mint);
+    dfree(ctx->mkgf); dfree(ctx->mkuf); dfree(ctx->mkrf); dfree(ctx->mint); dfree(ctx->mxs);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_multi) cudaFreeHost(ctx->h_multi);
@@ -1158,6 +1172,7 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
     DevLevel &LJ = ctx->L[nl - 1];
     DevOperator &op = ctx->opk;
     op.k = k; op.dpf = 2 * (k + 1); op.nloc = 3 * op.dpf; op.np_max = LJ.pf_max * op.dpf;
+    op.alo_valid = false;
     dalloc(ctx, op.A, (size_t)op.nloc * op.nloc * LJ.nc);
     dalloc(ctx, op.Af, (size_t)op.nloc * op.nloc * LJ.nc);
     dalloc(ctx, op.Fel, (size_t)op.nloc * LJ.nc);

@@ -135,6 +135,8 @@ struct DevOperator {
     int k = -1, dpf = 0, nloc = 0, np_max = 0;
     DBuf<double> A;      // nc*nloc*nloc
     DBuf<float> Af;
+    DBuf<float> Alo;     // A - (double)Af, for the double-FP32 apply of the batched solver
+    bool alo_valid = false;
     DBuf<double> Fel;    // nc*nloc element loads
     DBuf<double> Pinv;   // n_patches*np_max*np_max
     DBuf<float> Pinvf;
@@ -214,6 +216,7 @@ struct hdg_ctx {
     int mR = 0, mRst = 0;
     hdg::DBuf<double> mV, mZ, mw, mpart, msmall, mhbuf, mF, mU, mP, mG, mkr, mkt, mrd, mzd;
     hdg::DBuf<float> mkgf, mkuf, mkrf;
+    hdg::DBuf<float2> mxs;                    // (hi, lo) split of the outer operator's input
     hdg::DBuf<int> mint;                      // per-column ints (m_r, frozen flags)
     cudaGraphExec_t pcm_exec = nullptr;      // graph of one multi preconditioner application
     int pcm_prec = -1, pcm_R = 0;
@@ -324,6 +327,10 @@ cudaError_t launch_sum(const double *x, int64_t n, double *partials, cudaStream_
 constexpr int MAX_NRHS = 64;
 int krylov_m_blocks();
 size_t gs_m_smem(const DevLevel &L, const DevOperator &op, int R, size_t word);
+// double-FP32 apply of the order-k operator (A = hi + lo), R columns
+cudaError_t launch_apply_df_m(const DevLevel &L, const DevOperator &op, int R, const float *Ahi, const float *Alo,
+                              const double *x, float2 *xsplit, const double *g, double *y, cudaStream_t s);
+cudaError_t launch_split_lo(const double *A, const float *hi, float *lo, int64_t n, cudaStream_t s);
 template <class T>
 cudaError_t launch_apply_m(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *x, const T *g, T *y,
                            cudaStream_t s);

@@ -71,6 +71,86 @@ apply_m_kernel(int64_t n_int, int lgR, const int *__restrict__ facet_adj, const 
     }
 }
 
+// y = A x (or g - A x) in double-FP32 arithmetic: A = A_hi + A_lo (two FP32 words),
+// each x value split the same way, products formed exactly (FMA residual) plus
+// the two cross terms, sums kept as unevaluated FP32 pairs (two-sum).  The result
+// carries about 44 significant bits at the FP32 issue rate, where GB300's FP64
+// units would bound the same apply at a few percent of that rate.
+__device__ __forceinline__ void df_add(float &sh, float &sl, float p, float c) {
+    const float t = sh + p;
+    const float z = t - sh;
+    const float err = (sh - (t - z)) + (p - z);
+    sh = t;
+    sl += err + c;
+}
+
+template <int DPF, int RB>
+__global__ void __launch_bounds__(MT)
+apply_df_m_kernel(int64_t n_int, int lgR, const int *__restrict__ facet_adj, const int *__restrict__ cell_int,
+                  const float *__restrict__ Ahi, const float *__restrict__ Alo, const float2 *__restrict__ xp,
+                  const double *__restrict__ g, double *__restrict__ y) {
+    constexpr int NLOC = 3 * DPF;
+    const int R = 1 << lgR;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (n_int * (DPF / RB)) << lgR) return;
+    const int64_t rb = idx >> lgR;
+    const int r = (int)(idx & (R - 1));
+    const int64_t i = rb / (DPF / RB);
+    const int d0 = (int)(rb - i * (DPF / RB)) * RB;
+    float sh[RB], sl[RB];
+#pragma unroll
+    for (int b = 0; b < RB; ++b) sh[b] = sl[b] = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int adj = facet_adj[2 * i + q];
+        if (adj < 0) continue;
+        const int c = adj >> 2, lf = adj & 3;
+        const size_t base = (size_t)c * NLOC * NLOC + lf * DPF + d0;
+#pragma unroll
+        for (int f2 = 0; f2 < 3; ++f2) {
+            const int j = cell_int[3 * c + f2];
+            if (j < 0) continue;
+            const float2 *xs = xp + ((size_t)j * DPF << lgR) + r;
+#pragma unroll
+            for (int d2 = 0; d2 < DPF; ++d2) {
+                const float2 xv = xs[(size_t)d2 << lgR];      // (hi, lo) of x
+                const size_t o = base + (size_t)(f2 * DPF + d2) * NLOC;
+#pragma unroll
+                for (int b = 0; b < RB; ++b) {
+                    const float ah = Ahi[o + b], al = Alo[o + b];
+                    const float p = ah * xv.x;
+                    const float e = fmaf(ah, xv.x, -p);
+                    const float cr = fmaf(ah, xv.y, fmaf(al, xv.x, e));
+                    df_add(sh[b], sl[b], p, cr);
+                }
+            }
+        }
+    }
+    const size_t o = (((size_t)i * DPF + d0) << lgR) + r;
+#pragma unroll
+    for (int b = 0; b < RB; ++b) {
+        const size_t e = o + ((size_t)b << lgR);
+        const double v = (double)sh[b] + (double)sl[b];
+        y[e] = g ? g[e] - v : v;
+    }
+}
+
+// x -> (hi, lo) FP32 pairs, hi = fl32(x), lo = fl32(x - hi)
+__global__ void split_x_kernel(const double *__restrict__ x, float2 *__restrict__ xp, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double v = x[i];
+    const float h = (float)v;
+    xp[i] = make_float2(h, (float)(v - (double)h));
+}
+
+// lo = (float)(A - (double)hi): the FP32 remainder of the FP32 copy hi of A
+__global__ void split_lo_kernel(const double *__restrict__ A, const float *__restrict__ hi, float *__restrict__ lo,
+                                int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) lo[i] = (float)(A[i] - (double)hi[i]);
+}
+
 // ---------------------------------------------------------------- block Gauss-Seidel, one colour
 template <class T>
 struct Pair;
@@ -652,6 +732,38 @@ cudaError_t launch_apply_m(const DevLevel &L, const DevOperator &op, int R, cons
     default: return cudaErrorInvalidValue;
     }
 #undef HDG_APPLY_M
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_df_m(const DevLevel &L, const DevOperator &op, int R, const float *Ahi, const float *Alo,
+                              const double *x, float2 *xsplit, const double *g, double *y, cudaStream_t s) {
+    const int lg = log2_width(R);
+    if (L.n_int == 0) return cudaSuccess;
+    const int64_t nx = (L.n_int * op.dpf) << lg;
+    note_launches(2);
+    split_x_kernel<<<nblk(nx, MT), MT, 0, s>>>(x, xsplit, nx);
+    const float2 *xp = xsplit;
+#define HDG_APPLY_DF(D, B)                                                                                     \
+    case D:                                                                                                    \
+        apply_df_m_kernel<D, B><<<nblk((L.n_int * (D / B)) << lg, MT), MT, 0, s>>>(L.n_int, lg, L.facet_adj.p, \
+                                                                                L.cell_int.p, Ahi, Alo, xp, g, y); \
+        break;
+    switch (op.dpf) {
+        HDG_APPLY_DF(2, 2)
+        HDG_APPLY_DF(4, 4)
+        HDG_APPLY_DF(6, 2)
+        HDG_APPLY_DF(8, 4)
+        HDG_APPLY_DF(10, 2)
+    default: return cudaErrorInvalidValue;
+    }
+#undef HDG_APPLY_DF
+    return cudaGetLastError();
+}
+
+cudaError_t launch_split_lo(const double *A, const float *hi, float *lo, int64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    split_lo_kernel<<<nblk(n, MT), MT, 0, s>>>(A, hi, lo, n);
     return cudaGetLastError();
 }
 
