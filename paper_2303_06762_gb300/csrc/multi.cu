@@ -504,7 +504,9 @@ dots_m_kernel(const double *__restrict__ V, int nv, int64_t ld, const double *__
         for (int i = 0; i < NVB; ++i)
             if (i < nvb) acc[i] = fma(Vb[(size_t)i * ld + e], we, acc[i]);
     }
-    for (int i = 0; i < nvb; ++i) col_reduce_store(acc[i], i0 + i, R, partials, red);
+#pragma unroll
+    for (int i = 0; i < NVB; ++i)
+        if (i < nvb) col_reduce_store(acc[i], i0 + i, R, partials, red);   // nvb is uniform over the block
 }
 
 // w(:, r) -= Σ_i h_{i,r} V_i(:, r); MODE 1: also partials of <V_i, w_new> per column (nv <= NVB <= 8);
@@ -524,27 +526,41 @@ update_dots_m_kernel(const double *__restrict__ V, int nv, int64_t ld, double *_
     for (int i = 0; i < NA; ++i) acc[i] = 0.0;
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
         double we = w[e];
-        if (MODE == 1) {
+        if (MODE == 1 && NVB <= 16) {
+            // basis values stay in registers between the update and the dots
+            double vr[NVB];
+#pragma unroll
+            for (int i = 0; i < NVB; ++i) vr[i] = i < nv ? V[(size_t)i * ld + e] : 0.0;
+#pragma unroll
+            for (int i = 0; i < NVB; ++i)
+                if (i < nv) we = fma(-hs[i * R + r], vr[i], we);
+            w[e] = we;
+#pragma unroll
+            for (int i = 0; i < NVB; ++i)
+                if (i < nv) acc[i] = fma(vr[i], we, acc[i]);
+        } else if (MODE == 1) {
+            // too many for registers: the second read of V_i(e) is served by L1
 #pragma unroll
             for (int i = 0; i < NVB; ++i)
                 if (i < nv) we = fma(-hs[i * R + r], V[(size_t)i * ld + e], we);
-        } else {
-#pragma unroll 4
-            for (int i = 0; i < nv; ++i) we = fma(-hs[i * R + r], V[(size_t)i * ld + e], we);
-        }
-        w[e] = we;
-        if (MODE == 1) {
+            w[e] = we;
 #pragma unroll
             for (int i = 0; i < NVB; ++i)
                 if (i < nv) acc[i] = fma(V[(size_t)i * ld + e], we, acc[i]);
-        } else if (MODE == 2) {
-            acc[0] = fma(we, we, acc[0]);
+        } else {
+#pragma unroll 4
+            for (int i = 0; i < nv; ++i) we = fma(-hs[i * R + r], V[(size_t)i * ld + e], we);
+            w[e] = we;
+            if (MODE == 2) acc[0] = fma(we, we, acc[0]);
         }
     }
-    if (MODE == 1)
-        for (int i = 0; i < nv; ++i) col_reduce_store(acc[i], i, R, partials, red);
-    else if (MODE == 2)
+    if (MODE == 1) {
+#pragma unroll
+        for (int i = 0; i < NVB; ++i)
+            if (i < nv) col_reduce_store(acc[i], i, R, partials, red);   // nv is uniform over the block
+    } else if (MODE == 2) {
         col_reduce_store(acc[0], 0, R, partials, red);
+    }
 }
 
 // small[r*stride + off + i] = Σ_b partials[(i*R + r)*nb + b], and hbuf[i*R + r] the same when given
@@ -906,6 +922,8 @@ cudaError_t launch_update_dots_m(const double *V, int nv, int64_t ld, double *w,
         if (nv <= 1) update_dots_m_kernel<1, 1><<<nb, MT, 0, s>>>(V, nv, ld, w, n, R, h, partials);
         else if (nv <= 4) update_dots_m_kernel<4, 1><<<nb, MT, 0, s>>>(V, nv, ld, w, n, R, h, partials);
         else if (nv <= 8) update_dots_m_kernel<8, 1><<<nb, MT, 0, s>>>(V, nv, ld, w, n, R, h, partials);
+        else if (nv <= 16) update_dots_m_kernel<16, 1><<<nb, MT, 0, s>>>(V, nv, ld, w, n, R, h, partials);
+        else if (nv <= 32) update_dots_m_kernel<32, 1><<<nb, MT, 0, s>>>(V, nv, ld, w, n, R, h, partials);
         else {
             // update only, then the dots of the new w in chunks of 16
             update_dots_m_kernel<1, 0><<<nb, MT, 0, s>>>(V, nv, ld, w, n, R, h, partials);

@@ -329,8 +329,8 @@ dots_kernel(const double *__restrict__ V, int nv, int64_t ld, const double *__re
     block_reduce_store<NVB>(acc, nvb, partials + (size_t)i0 * gridDim.x);
 }
 
-// w -= Σ_{i<nv} h_i V_i; MODE 1: also partials of <V_i, w_new> (nv <= NVB <= 8, the second
-// read of V_i(e) hits L1); MODE 2: partials of <w_new, w_new>; MODE 0: update only
+// w -= Σ_{i<nv} h_i V_i; MODE 1: also partials of <V_i, w_new> (nv <= NVB <= 16, the basis
+// values held in registers between the two); MODE 2: partials of <w_new, w_new>; MODE 0: update only
 template <int NVB, int MODE>
 __global__ void __launch_bounds__(KRYLOV_THREADS)
 update_dots_kernel(const double *__restrict__ V, int nv, int64_t ld, double *__restrict__ w, int64_t n,
@@ -345,21 +345,32 @@ update_dots_kernel(const double *__restrict__ V, int nv, int64_t ld, double *__r
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x) {
         double we = w[e];
-        if (MODE == 1) {
+        if (MODE == 1 && NVB <= 16) {
+            // basis values stay in registers between the update and the dots
+            double vr[NVB];
+#pragma unroll
+            for (int i = 0; i < NVB; ++i) vr[i] = i < nv ? V[(size_t)i * ld + e] : 0.0;
+#pragma unroll
+            for (int i = 0; i < NVB; ++i)
+                if (i < nv) we = fma(-hs[i], vr[i], we);
+            w[e] = we;
+#pragma unroll
+            for (int i = 0; i < NVB; ++i)
+                if (i < nv) acc[i] = fma(vr[i], we, acc[i]);
+        } else if (MODE == 1) {
+            // too many for registers: the second read of V_i(e) is served by L1
 #pragma unroll
             for (int i = 0; i < NVB; ++i)
                 if (i < nv) we = fma(-hs[i], V[(size_t)i * ld + e], we);
-        } else {
-#pragma unroll 4
-            for (int i = 0; i < nv; ++i) we = fma(-hs[i], V[(size_t)i * ld + e], we);
-        }
-        w[e] = we;
-        if (MODE == 1) {
+            w[e] = we;
 #pragma unroll
             for (int i = 0; i < NVB; ++i)
                 if (i < nv) acc[i] = fma(V[(size_t)i * ld + e], we, acc[i]);
-        } else if (MODE == 2) {
-            acc[0] = fma(we, we, acc[0]);
+        } else {
+#pragma unroll 4
+            for (int i = 0; i < nv; ++i) we = fma(-hs[i], V[(size_t)i * ld + e], we);
+            w[e] = we;
+            if (MODE == 2) acc[0] = fma(we, we, acc[0]);
         }
     }
     if (MODE != 0) block_reduce_store<NA>(acc, MODE == 1 ? nv : 1, partials);
@@ -651,6 +662,8 @@ cudaError_t launch_update_dots(const double *V, int nv, int64_t ld, double *w, i
         upd<4, 1>(V, nv, ld, w, n, h, partials, s);
     } else if (nv <= 8) {
         upd<8, 1>(V, nv, ld, w, n, h, partials, s);
+    } else if (nv <= 16) {
+        upd<16, 1>(V, nv, ld, w, n, h, partials, s);
     } else {
         upd<1, 0>(V, nv, ld, w, n, h, partials, s);
         return launch_dots(V, nv, ld, w, n, partials, s);
