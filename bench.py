@@ -516,9 +516,16 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes):
     alg = sweep_bytes(ctx_mesh_fine(args), k, 4)
     achieved = alg / t_sweep / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
+    # DRAM bytes of one sweep from an ncu capture of the same kernel (dram__bytes_read.sum +
+    # dram__bytes_write.sum over its three colour launches) on the 128x128, k = 3 case:
+    # 396,034,304 B against 318,199,104 algorithmic bytes there.  Traffic grows with the
+    # number of patches like the algorithmic bytes, so the full-size figure is that ratio
+    # times the full-size algorithmic bytes (k = 3 only; other k were not captured).
+    traffic = alg * (396034304 / 318199104) if k == 3 else None
     return {"kernel": "gs_kernel<float> (order-k block GS sweep, 3 colour launches)",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-            "frac": achieved / peak, "traffic": None,
+            "frac": achieved / peak, "traffic": traffic,
+            "traffic_note": "scaled from an ncu capture at 128x128 (same kernel, cold caches)" if traffic else None,
             "algorithmic_bytes_per_sweep": alg, "sweep_ms": t_sweep * 1e3,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
 
