@@ -436,7 +436,9 @@ def batched_form(args, hdg, torch, dev, stream, world):
     hdg.hdg_solve(ctx, F0)
     t1, (_, _, info1) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F0))
     ctx.close()
-    return {"workload": f"2D generalized Stokes {N}x{N} ({2 * N * N} triangles), k={k}, gamma=1e2, beta=1, nu=1, "
+    uneven = uneven_meshes_form(hdg, torch, dev, stream, world)
+    return {"uneven_meshes": uneven,
+            "workload": f"2D generalized Stokes {N}x{N} ({2 * N * N} triangles), k={k}, gamma=1e2, beta=1, nu=1, "
                         f"{nrhs} seeded Fourier+gradient loads, CR levels {N0}x{N0}..{N}x{N}, hdg_solve_multi",
             "nrhs": nrhs, "skeleton_dofs": int(sizes.n_dof), "time_to_tol_s": t,
             "fgmres_iters_total": its, "uzawa_steps_max": max(i["uzawa_its"] for i in infos),
@@ -444,6 +446,47 @@ def batched_form(args, hdg, torch, dev, stream, world):
             "single_load_time_to_tol_s": t1, "single_load_fgmres_iters": info1["krylov_its_total"],
             "single_load_dof_iters_per_s": sizes.n_dof * info1["krylov_its_total"] / t1,
             "throughput_ratio_vs_single": (sizes.n_dof * its / t) / (sizes.n_dof * info1["krylov_its_total"] / t1)}
+
+
+def uneven_meshes_form(hdg, torch, dev, stream, world):
+    """Eight meshes N = 32, 64, ..., 256 (coarsest 2, 2, 3, 2, 5, 3, 7, 2), k = 3, one load each (the
+    manufactured curl solution), mixed preconditioner: solved one after the other with hdg_solve, and
+    concurrently with hdg_solve_batched (one host thread and stream per mesh)."""
+    from workloads import unit_square_hierarchy, curl_bubble_2d, forcing_at_lattice
+    k = 3
+    ctxs, Fs = [], []
+    for N, N0 in ((32, 2), (64, 2), (96, 3), (128, 2), (160, 5), (192, 3), (224, 7), (256, 2)):
+        nl = 1
+        while N0 * 2 ** (nl - 1) < N:
+            nl += 1
+        ms = unit_square_hierarchy(N0, nl)
+        fine = ms[-1]
+        fv = forcing_at_lattice(fine.coords, fine.cells, k, curl_bubble_2d().forcing(1.0, 1.0))
+        ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=dev.index or 0)
+        Fs.append(hdg.hdg_condense(ctx, hdg.Params(k=k, nu=1.0, beta=1.0, gamma=1e2,
+                                                     precision=hdg.HDG_MIXED_FP32), torch.tensor(fv, device=dev)))
+        ctxs.append(ctx)
+    dofs = [c.sizes().n_dof for c in ctxs]
+    for c, F in zip(ctxs, Fs):
+        hdg.hdg_solve(c, F)
+    hdg.hdg_solve_batched(ctxs, Fs)
+    t_seq, its_seq = 0.0, []
+    for c, F in zip(ctxs, Fs):
+        t, (_, _, info) = _timed(torch, stream, lambda c=c, F=F: hdg.hdg_solve(c, F))
+        t_seq += t
+        its_seq.append(info["krylov_its_total"])
+    t0 = time.perf_counter()
+    _, _, infos, stat = hdg.hdg_solve_batched(ctxs, Fs)
+    t_par = time.perf_counter() - t0
+    its = [i["krylov_its_total"] for i in infos]
+    work = sum(d * i for d, i in zip(dofs, its))
+    for c in ctxs:
+        c.close()
+    return {"meshes": [32, 64, 96, 128, 160, 192, 224, 256], "skeleton_dofs": dofs, "fgmres_iters": its,
+            "sequential_s": t_seq, "concurrent_s": t_par,
+            "dof_iters_per_s_sequential": sum(d * i for d, i in zip(dofs, its_seq)) * world / t_seq,
+            "dof_iters_per_s_concurrent": work * world / t_par, "speedup": t_seq / t_par,
+            "timing": "concurrent time is host wall clock around hdg_solve_batched, which synchronises"}
 
 
 def oseen_form(args, hdg, torch, dev, stream):

@@ -267,6 +267,17 @@ hdg_status hdg_precond_apply_multi(hdg_ctx *ctx, int nrhs, const double *r, doub
 hdg_status hdg_solve_multi(hdg_ctx *ctx, int nrhs, const double *F, double *u, double *p,
                            const hdg_solve_opts *opts, hdg_solve_info *info, hdg_stream_t stream);
 
+/* One load on each of n independent contexts (several meshes, for instance of
+ * different sizes) solved concurrently: one host thread and one private
+ * non-blocking CUDA stream per context, so that the kernels of the meshes
+ * overlap on the GPU.  ctxs[i]: distinct condensed contexts on one device;
+ * F[i], u[i], p[i]: as for hdg_solve on ctxs[i]; opts: shared, NULL =
+ * defaults; info, status: host arrays [n] or NULL.  Synchronises before
+ * returning; returns the first non-OK per-context status. */
+hdg_status hdg_solve_batched(hdg_ctx *const *ctxs, int n, const double *const *F, double *const *u,
+                             double *const *p, const hdg_solve_opts *opts, hdg_solve_info *info,
+                             hdg_status *status);
+
 /* Sizes after hdg_setup_mesh_hierarchy (k-dependent fields after hdg_condense). */
 hdg_status hdg_get_sizes(const hdg_ctx *ctx, hdg_sizes *out);
 

@@ -39,7 +39,7 @@ EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
            "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_apply_multi",
-           "hdg_precond_apply_multi", "hdg_solve_multi", "hdg_destroy",
+           "hdg_precond_apply_multi", "hdg_solve_multi", "hdg_solve_batched", "hdg_destroy",
            "hdg_status_string", "hdg_last_error")
 
 
@@ -134,6 +134,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "hdg_apply_multi": (I, [P, I, P, P, P]),
         "hdg_precond_apply_multi": (I, [P, I, P, P, P]),
         "hdg_solve_multi": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
+        "hdg_solve_batched": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
         "hdg_condense": (I, [P, ctypes.POINTER(_Params), P, P, P]),
         "hdg_load": (I, [P, P, P, P]),
         "hdg_apply": (I, [P, P, P, P]),
@@ -343,6 +344,36 @@ def hdg_solve_multi(ctx: Context, F, u=None, p=None, opts: Optional[SolveOpts] =
     if st != 0 and (st != 5 or raise_on_nonconvergence):
         ctx.check(st)
     return u, p, [infos[r].as_dict() for r in range(nrhs)]
+
+
+def hdg_solve_batched(ctxs: Sequence, Fs: Sequence, opts: Optional[SolveOpts] = None):
+    """One load per context, all solved concurrently (one host thread and stream each).
+    Returns ([u], [p], [info dicts], [status])."""
+    import torch
+    n = len(ctxs)
+    us, ps = [], []
+    for c, F in zip(ctxs, Fs):
+        s = c.sizes()
+        us.append(torch.zeros(s.n_dof, dtype=torch.float64, device=F.device))
+        ps.append(torch.zeros(s.n_cells, dtype=torch.float64, device=F.device))
+    P = ctypes.c_void_p
+    handles = (P * n)(*[c.handle for c in ctxs])
+    fp = (P * n)(*[F.data_ptr() for F in Fs])
+    up = (P * n)(*[u.data_ptr() for u in us])
+    pp = (P * n)(*[p.data_ptr() for p in ps])
+    infos = (SolveInfo * n)()
+    stat = (ctypes.c_int * n)()
+    o = opts if opts is not None else default_solve_opts()
+    torch.cuda.synchronize()
+    st = load_library().hdg_solve_batched(ctypes.cast(handles, P), n, ctypes.cast(fp, P), ctypes.cast(up, P),
+                                          ctypes.cast(pp, P), ctypes.byref(o), ctypes.cast(infos, P),
+                                          ctypes.cast(stat, P))
+    if st not in (0, 5):
+        for c, sv in zip(ctxs, stat):
+            if sv not in (0, 5):
+                c.check(sv)
+        raise HdgError(st, "hdg_solve_batched failed")
+    return us, ps, [infos[i].as_dict() for i in range(n)], list(stat)
 
 
 def hdg_recover(ctx: Context, u, forcing=None, stream=None):

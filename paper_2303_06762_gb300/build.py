@@ -70,7 +70,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if ptxas_verbose:
                 cmd += ["-Xptxas", "-v"]
         else:
-            cmd = ["g++", "-O2", "-std=c++20", "-fPIC", "-Wall", "-Wno-unused-function",
+            cmd = ["g++", "-O2", "-std=c++20", "-fPIC", "-pthread", "-Wall", "-Wno-unused-function",
                    "-I", INC, "-I", CSRC, "-I", os.path.join(cuda, "include"), "-c", src, "-o", obj]
         jobs.append((cmd, obj))
     with ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
@@ -80,7 +80,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_verbose: bool = Fals
             if o.strip():
                 print(o)
     tmp = LIB + ".tmp"
-    _run([nvcc, *ARCH, "-shared", "-o", tmp] + [o for _, o in jobs] + ["-cudart", "static"])
+    _run([nvcc, *ARCH, "-shared", "-o", tmp] + [o for _, o in jobs] + ["-cudart", "static", "-lpthread"])
     os.replace(tmp, LIB)
     return LIB
 

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "hdg_internal.h"
@@ -341,7 +342,7 @@ void precond(hdg_ctx *ctx, const double *r, double *z, cudaStream_t s) {
         CK(cudaStreamWaitEvent(ctx->cap_stream, ev, 0));
         CK(cudaEventDestroy(ev));
         cudaStream_t cs2 = ctx->cap_stream;
-        const unsigned long long l0 = launch_count();
+        const unsigned long long l0 = thread_launch_count();
         CK(cudaStreamBeginCapture(cs2, cudaStreamCaptureModeThreadLocal));
         cudaGraph_t g = nullptr;
         try {
@@ -355,7 +356,7 @@ void precond(hdg_ctx *ctx, const double *r, double *z, cudaStream_t s) {
         cudaError_t e = cudaGraphInstantiate(&ctx->pc_exec, g, 0);
         cudaGraphDestroy(g);
         CK(e);
-        ctx->pc_kernels = (long long)(launch_count() - l0);
+        ctx->pc_kernels = (long long)(thread_launch_count() - l0);
         note_launches(-ctx->pc_kernels);          // captured, not executed
         ctx->pc_prec = (int)ctx->prm.precision;
     }
@@ -693,7 +694,7 @@ void precond_m(hdg_ctx *ctx, const double *r, double *z, int R, cudaStream_t s) 
         CK(cudaStreamWaitEvent(ctx->cap_stream, ev, 0));
         CK(cudaEventDestroy(ev));
         cudaStream_t cs2 = ctx->cap_stream;
-        const unsigned long long l0 = launch_count();
+        const unsigned long long l0 = thread_launch_count();
         CK(cudaStreamBeginCapture(cs2, cudaStreamCaptureModeThreadLocal));
         cudaGraph_t g = nullptr;
         try {
@@ -707,7 +708,7 @@ void precond_m(hdg_ctx *ctx, const double *r, double *z, int R, cudaStream_t s) 
         cudaError_t e = cudaGraphInstantiate(&ctx->pcm_exec, g, 0);
         cudaGraphDestroy(g);
         CK(e);
-        ctx->pcm_kernels = (long long)(launch_count() - l0);
+        ctx->pcm_kernels = (long long)(thread_launch_count() - l0);
         note_launches(-ctx->pcm_kernels);
         ctx->pcm_prec = (int)ctx->prm.precision;
         ctx->pcm_R = R;
@@ -1093,6 +1094,7 @@ void hdg_destroy(hdg_ctx *ctx) {
         dfree(*b);
     dfree(ctx->mkgf); dfree(ctx->mkuf); dfree(ctx->mkrf); dfree(ctx->mint); dfree(ctx->mxs);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     if (ctx->h_multi) cudaFreeHost(ctx->h_multi);
     delete ctx;
@@ -1559,6 +1561,56 @@ hdg_status hdg_solve_multi(hdg_ctx *ctx, int nrhs, const double *F, double *u, d
     if (st != HDG_OK) return st;
     if (conv != HDG_OK) ctx->err = "iteration limit reached";
     return conv;
+}
+
+// ------------------------------------------------------------------ several meshes
+hdg_status hdg_solve_batched(hdg_ctx *const *ctxs, int n, const double *const *F, double *const *u,
+                             double *const *p, const hdg_solve_opts *opts, hdg_solve_info *info,
+                             hdg_status *status) {
+    if (!ctxs || n < 1 || !F || !u || !p) return HDG_ERR_INVALID_ARG;
+    for (int i = 0; i < n; ++i) {
+        if (!ctxs[i]) return HDG_ERR_INVALID_ARG;
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return HDG_ERR_INVALID_ARG;   // one thread per context
+    }
+    std::vector<hdg_status> st(n, HDG_OK);
+    std::vector<hdg_solve_info> inf(n);
+    for (int i = 0; i < n; ++i) {
+        hdg_ctx *ctx = ctxs[i];
+        if (!ctx->batch_stream) {
+            cudaSetDevice(ctx->device);
+            if (cudaStreamCreateWithFlags(&ctx->batch_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                ctx->batch_stream = nullptr;
+                ctx->err = "stream creation failed";
+                return HDG_ERR_CUDA;
+            }
+        }
+    }
+    auto work = [&](int i) {
+        hdg_ctx *ctx = ctxs[i];
+        if (cudaSetDevice(ctx->device) != cudaSuccess) {
+            st[i] = HDG_ERR_CUDA;
+            return;
+        }
+        st[i] = hdg_solve(ctx, F[i], u[i], p[i], opts, &inf[i], (hdg_stream_t)ctx->batch_stream);
+    };
+    std::vector<std::thread> th;
+    th.reserve(n);
+    try {
+        for (int i = 1; i < n; ++i) th.emplace_back(work, i);
+    } catch (...) {
+        for (auto &t : th) t.join();
+        return HDG_ERR_OOM;
+    }
+    work(0);
+    for (auto &t : th) t.join();
+    hdg_status first = HDG_OK;
+    for (int i = 0; i < n; ++i) {
+        if (info) info[i] = inf[i];
+        if (status) status[i] = st[i];
+        if (first == HDG_OK && st[i] != HDG_OK) first = st[i];
+    }
+    return first;
 }
 
 } // extern "C"

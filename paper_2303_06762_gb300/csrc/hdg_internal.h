@@ -222,6 +222,7 @@ struct hdg_ctx {
     int pcm_prec = -1, pcm_R = 0;
     long long pcm_kernels = 0;
     hdg::DBuf<double> pcm_in, pcm_out;
+    cudaStream_t batch_stream = nullptr;     // private stream for hdg_solve_batched
     // fused MG_h on levels 0..small_Ls (one thread block), -1 when not used
     int small_Ls = -1;
     size_t small_smem_d = 0, small_smem_f = 0;   // per-CTA shared memory of the fused kernel
@@ -235,6 +236,7 @@ namespace hdg {
 // kernel-launch counter (ops.cu): every launcher adds the kernels it enqueues
 void note_launches(long long n);
 unsigned long long launch_count();
+unsigned long long thread_launch_count();   // this host thread's share (graph capture bookkeeping)
 
 // reference.cpp
 void build_reference_tables(int k, RefTables &out);

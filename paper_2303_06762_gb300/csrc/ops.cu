@@ -31,8 +31,13 @@
 namespace hdg {
 
 static std::atomic<unsigned long long> g_launches{0};
-void note_launches(long long n) { g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed); }
+thread_local unsigned long long t_launches = 0;   // launches enqueued by this host thread
+void note_launches(long long n) {
+    g_launches.fetch_add((unsigned long long)n, std::memory_order_relaxed);
+    t_launches += (unsigned long long)n;
+}
 unsigned long long launch_count() { return g_launches.load(std::memory_order_relaxed); }
+unsigned long long thread_launch_count() { return t_launches; }
 
 namespace {
 

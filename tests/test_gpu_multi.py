@@ -110,3 +110,33 @@ def test_multi_error_paths():
     lib = hdg.load_library()
     assert lib.hdg_apply_multi(ctx.handle, 0, None, None, None) == 1
     assert lib.hdg_apply_multi(ctx.handle, 65, None, None, None) == 1
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_solve_batched_uneven_meshes(precision):
+    """Several meshes of different sizes solved concurrently equal their separate solves."""
+    from workloads import curl_bubble_2d
+    hdg = _hdg()
+    k = 2
+    ctxs, Fs, ohs, fvs = [], [], [], []
+    for N0, nl in ((2, 2), (3, 2), (2, 3)):
+        ms, ts, ps = hierarchy(N0, nl)
+        fine = ms[-1]
+        fv = forcing_at_lattice(fine.coords, fine.cells, k, curl_bubble_2d().forcing(1.0, 1.0))
+        ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+        Fs.append(hdg.hdg_condense(ctx, hdg.Params(k=k, beta=1.0, gamma=100.0, precision=precision), dev(fv)))
+        ctxs.append(ctx)
+        ohs.append(HDG(ts[-1], k, nu=1.0, beta=1.0, gamma=100.0))
+        fvs.append(fv)
+    us, ps_, infos, stat = hdg.hdg_solve_batched(ctxs, Fs)
+    assert stat == [0, 0, 0]
+    for ctx, F, u, p, info, oh, fv in zip(ctxs, Fs, us, ps_, infos, ohs, fvs):
+        u1, p1, info1 = hdg.hdg_solve(ctx, F)
+        assert info["krylov_its"] == info1["krylov_its"]
+        assert rel(host(u), host(u1)) < 1e-13
+        ud, pd = oh.solve_direct(oh.load(fv))
+        assert np.linalg.norm(host(u) - ud) < 1e-8 * np.linalg.norm(ud)
+    lib = hdg.load_library()
+    import ctypes
+    same = (ctypes.c_void_p * 2)(ctxs[0].handle, ctxs[0].handle)
+    assert lib.hdg_solve_batched(ctypes.cast(same, ctypes.c_void_p), 2, None, None, None, None, None, None) == 1
