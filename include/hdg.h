@@ -278,6 +278,20 @@ hdg_status hdg_solve_batched(hdg_ctx *const *ctxs, int n, const double *const *F
                              double *const *p, const hdg_solve_opts *opts, hdg_solve_info *info,
                              hdg_status *status);
 
+/* Steady Navier-Stokes by Picard iteration (Section 4.2, Algorithm 3 part (i)):
+ * u^(0) solves the generalized Stokes problem with the data of params (its conv
+ * is ignored); step n condenses and solves the Oseen problem of eq. nsWeak
+ * whose convecting field is u_h^(n-1) (its values at the degree-(k+1) lattice,
+ * recovered on the device), warm-started from the previous step, until
+ * ||u_h^(n) - u_h^(n-1)||_{L2} < tol or max_steps steps.
+ *   forcing: device lattice layout; u: device out [n_dof]; p: device out [n_cells];
+ *   opts: inner solves (NULL = defaults); steps_out, dist_out: host out or NULL.
+ * On return the context holds the condensed operator of the last Oseen step.
+ * Returns HDG_ERR_NOT_CONVERGED when max_steps or an inner limit is reached. */
+hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forcing, double tol, int max_steps,
+                      double *u, double *p, const hdg_solve_opts *opts, int *steps_out, double *dist_out,
+                      hdg_stream_t stream);
+
 /* Sizes after hdg_setup_mesh_hierarchy (k-dependent fields after hdg_condense). */
 hdg_status hdg_get_sizes(const hdg_ctx *ctx, hdg_sizes *out);
 

@@ -39,7 +39,7 @@ EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
            "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_apply_multi",
-           "hdg_precond_apply_multi", "hdg_solve_multi", "hdg_solve_batched", "hdg_destroy",
+           "hdg_precond_apply_multi", "hdg_solve_multi", "hdg_solve_batched", "hdg_picard", "hdg_destroy",
            "hdg_status_string", "hdg_last_error")
 
 
@@ -135,6 +135,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "hdg_precond_apply_multi": (I, [P, I, P, P, P]),
         "hdg_solve_multi": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
         "hdg_solve_batched": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
+        "hdg_picard": (I, [P, ctypes.POINTER(_Params), P, ctypes.c_double, I, P, P, ctypes.POINTER(SolveOpts),
+                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P]),
         "hdg_condense": (I, [P, ctypes.POINTER(_Params), P, P, P]),
         "hdg_load": (I, [P, P, P, P]),
         "hdg_apply": (I, [P, P, P, P]),
@@ -374,6 +376,26 @@ def hdg_solve_batched(ctxs: Sequence, Fs: Sequence, opts: Optional[SolveOpts] = 
                 c.check(sv)
         raise HdgError(st, "hdg_solve_batched failed")
     return us, ps, [infos[i].as_dict() for i in range(n)], list(stat)
+
+
+def hdg_picard(ctx: Context, params: Params, forcing, tol: float = 1e-8, max_steps: int = 50,
+               opts: Optional[SolveOpts] = None, stream=None, raise_on_nonconvergence: bool = True):
+    """Steady Navier-Stokes by Picard iteration; returns (u, p, steps, last ||u^n - u^(n-1)||)."""
+    import torch
+    s = ctx.sizes()
+    k = params.k
+    n_dof = s.n_interior_facets * 2 * (k + 1)
+    u = torch.empty(n_dof, dtype=torch.float64, device=forcing.device)
+    p = torch.empty(s.n_cells, dtype=torch.float64, device=forcing.device)
+    steps = ctypes.c_int()
+    dist = ctypes.c_double()
+    c = params.to_c()
+    o = opts if opts is not None else default_solve_opts()
+    st = load_library().hdg_picard(ctx.handle, ctypes.byref(c), _ptr(forcing), tol, max_steps, _ptr(u), _ptr(p),
+                                   ctypes.byref(o), ctypes.byref(steps), ctypes.byref(dist), _stream(stream))
+    if st != 0 and (st != 5 or raise_on_nonconvergence):
+        ctx.check(st)
+    return u, p, steps.value, dist.value
 
 
 def hdg_recover(ctx: Context, u, forcing=None, stream=None):

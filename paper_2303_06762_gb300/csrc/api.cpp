@@ -1085,7 +1085,7 @@ void hdg_destroy(hdg_ctx *ctx) {
     dfree(ctx->V); dfree(ctx->Z); dfree(ctx->w); dfree(ctx->partials); dfree(ctx->small);
     dfree(ctx->uz_partials);
     for (auto *b : {&ctx->rec_L, &ctx->rec_La, &ctx->rec_rt, &ctx->rec_ulat, &ctx->rec_e, &ctx->rec_j, &ctx->adj_F,
-                    &ctx->adj_u, &ctx->adj_p})
+                    &ctx->adj_u, &ctx->adj_p, &ctx->pic_F, &ctx->pic_w0, &ctx->pic_w1, &ctx->pic_e, &ctx->pic_j})
         dfree(*b);
     drop_graph(ctx);
     dfree(ctx->pc_in); dfree(ctx->pc_out);
@@ -1611,6 +1611,67 @@ hdg_status hdg_solve_batched(hdg_ctx *const *ctxs, int n, const double *const *F
         if (first == HDG_OK && st[i] != HDG_OK) first = st[i];
     }
     return first;
+}
+
+// ------------------------------------------------------------------ steady Navier-Stokes (Picard)
+hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forcing, double tol, int max_steps,
+                      double *u, double *p, const hdg_solve_opts *opts, int *steps_out, double *dist_out,
+                      hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    hdg_status conv = HDG_OK;
+    int steps = 0;
+    double dist = 0.0;
+    hdg_status st = guard(ctx, [&] {
+        REQUIRE(params && forcing && u && p, "null argument");
+        REQUIRE(max_steps >= 1 && tol >= 0 && std::isfinite(tol), "bad tol or max_steps");
+        REQUIRE(params->k >= 0 && params->k <= MAX_K, "k out of range 0..4");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int J = ctx->n_levels - 1;
+        DevLevel &LJ = ctx->L[J];
+        const int k = params->k;
+        const int64_t nc = LJ.nc, nlat = (k + 2) * (k + 3) / 2, n_dof = LJ.n_int * 2 * (k + 1);
+        dalloc(ctx, ctx->pic_F, std::max<int64_t>(n_dof, 1));
+        dalloc(ctx, ctx->pic_w0, nc * 2 * nlat);
+        dalloc(ctx, ctx->pic_w1, nc * 2 * nlat);
+        dalloc(ctx, ctx->pic_e, nc * 2 * nlat);
+        dalloc(ctx, ctx->pic_j, std::max<int64_t>(nc, 1));
+        auto check = [&](hdg_status r) {
+            if (r == HDG_ERR_NOT_CONVERGED) conv = r;
+            else if (r != HDG_OK) throw Fail{r};
+        };
+        // u^(0): the generalized Stokes problem with the same data
+        hdg_params prm = *params;
+        prm.conv = nullptr;
+        check(hdg_condense(ctx, &prm, forcing, ctx->pic_F.p, stream));
+        CK(cudaMemsetAsync(u, 0, sizeof(double) * n_dof, s));
+        CK(cudaMemsetAsync(p, 0, sizeof(double) * nc, s));
+        check(hdg_solve(ctx, ctx->pic_F.p, u, p, opts, nullptr, stream));
+        double *wp = ctx->pic_w0.p, *wc = ctx->pic_w1.p;
+        recover_impl(ctx, u, forcing, nullptr, nullptr, wp, s);
+        // Oseen steps with w_h = u_h^(n-1) until ||u^(n) - u^(n-1)|| < tol
+        for (int n = 1; n <= max_steps; ++n) {
+            prm.conv = wp;
+            check(hdg_condense(ctx, &prm, forcing, ctx->pic_F.p, stream));
+            check(hdg_solve(ctx, ctx->pic_F.p, u, p, opts, nullptr, stream));
+            recover_impl(ctx, u, forcing, nullptr, nullptr, wc, s);
+            CK(launch_objective(k, LJ, ctx->refk_dev.p, ctx->refk, wc, wp, ctx->pic_e.p, ctx->pic_j.p, s));
+            dist = std::sqrt(std::max(2.0 * device_sum(ctx, ctx->pic_j.p, nc, s), 0.0));
+            steps = n;
+            std::swap(wp, wc);
+            if (!std::isfinite(dist)) {
+                ctx->err = "non-finite Picard update";
+                throw Fail{HDG_ERR_NONFINITE};
+            }
+            if (dist < tol) break;
+        }
+        if (!(dist < tol) && conv == HDG_OK) conv = HDG_ERR_NOT_CONVERGED;
+        CK(cudaStreamSynchronize(s));
+    });
+    if (steps_out) *steps_out = steps;
+    if (dist_out) *dist_out = dist;
+    if (st != HDG_OK) return st;
+    if (conv != HDG_OK) ctx->err = "Picard iteration or an inner solve reached its limit";
+    return conv;
 }
 
 } // extern "C"
