@@ -140,3 +140,47 @@ def test_solve_batched_uneven_meshes(precision):
     import ctypes
     same = (ctypes.c_void_p * 2)(ctxs[0].handle, ctxs[0].handle)
     assert lib.hdg_solve_batched(ctypes.cast(same, ctypes.c_void_p), 2, None, None, None, None, None, None) == 1
+
+
+def test_full_size_batched_sampled_parity():
+    """The batched benchmark configuration (256x256, k = 3, 64 loads): sampled rows of the batched
+    operator apply against the oracle's condensed cell matrices computed one by one, and two columns of
+    the batched preconditioner against single-column applications."""
+    from oracle.spaces import Element
+    from oracle.hdg import condense_cell
+    from oracle.topology import build_topology
+    from workloads import unit_square_hierarchy
+    hdg = _hdg()
+    k, nu, beta, gamma, R = 3, 1.0, 1.0, 100.0, 64
+    ms = unit_square_hierarchy(8, 6)            # 8 .. 256
+    fine = ms[-1]
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    hdg.hdg_condense(ctx, hdg.Params(k=k, nu=nu, beta=beta, gamma=gamma, precision=1))
+    s = ctx.sizes()
+    rng = np.random.default_rng(5)
+    X = torch.tensor(rng.standard_normal((R, s.n_dof)), device=DEV)
+    Y = host(hdg.hdg_apply_multi(ctx, X))
+    Xh = host(X)
+    topo = build_topology(fine.coords, fine.cells, fine.vertex_colour)
+    dpf = 2 * (k + 1)
+    for i in rng.choice(topo.n_interior, 12, replace=False):
+        F = topo.interior_facets[i]
+        acc = np.zeros((dpf, R))
+        for c in topo.facet_cells[F]:
+            gv = fine.cells[c]
+            X0 = fine.coords[gv]
+            cc = condense_cell(Element(X0 - X0[0], gv, k), nu, beta)
+            Ao = cc.A + (gamma * nu / cc.area) * np.outer(cc.d, cc.d)
+            xl = np.zeros((3 * dpf, R))
+            for f in range(3):
+                j = topo.interior_index[topo.cell_facets[c, f]]
+                if j >= 0:
+                    xl[f * dpf:(f + 1) * dpf] = Xh[:, j * dpf:(j + 1) * dpf].T
+            lf = list(topo.cell_facets[c]).index(F)
+            acc += Ao[lf * dpf:(lf + 1) * dpf] @ xl
+        assert rel(Y[:, i * dpf:(i + 1) * dpf].T, acc) < 1e-11
+    # FP32 preconditioner: the batched and single kernels sum in different orders, and
+    # six levels of V-cycle amplify the FP32 rounding differences to about 1e-5
+    Z = hdg.hdg_precond_apply_multi(ctx, X)
+    for r in (0, 63):
+        assert rel(host(Z[r]), host(hdg.hdg_precond_apply(ctx, X[r].contiguous()))) < 1e-4

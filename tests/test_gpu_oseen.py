@@ -171,3 +171,27 @@ def test_oseen_adjoint_gradients(k, Re):
     assert rel(host(gn), gno) < 1e-7
     # the primal operators are back after the transposed adjoint solve
     assert np.array_equal(host(hdg.hdg_get_element_matrices(ctx, -1)), A_before)
+
+
+def test_full_size_oseen_sampled_parity():
+    """The Oseen benchmark configuration (128x128, k = 2, Re = 100): sampled cells' condensed matrices
+    against the oracle computed cell by cell."""
+    from oracle.spaces import Element
+    from oracle.hdg import condense_cell
+    from workloads import unit_square_hierarchy
+    hdg = _hdg()
+    k, Re, gamma = 2, 100.0, 100.0
+    nu = 1.0 / Re
+    ms = unit_square_hierarchy(8, 5)            # 8 .. 128
+    fine = ms[-1]
+    conv = curl_lattice_2d(fine.coords, fine.cells, k + 1, PSI)
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    hdg.hdg_condense(ctx, hdg.Params(k=k, nu=nu, beta=0.0, gamma=gamma, conv=dev(conv)))
+    A = hdg.hdg_get_element_matrices(ctx, -1)
+    rng = np.random.default_rng(17)
+    for c in rng.choice(fine.n_cells, 40, replace=False):
+        gv = fine.cells[c]
+        X = fine.coords[gv]
+        cc = condense_cell(Element(X - X[0], gv, k), nu, 0.0, conv[c])
+        Ao = cc.A + (gamma * nu / cc.area) * np.outer(cc.d, cc.d)
+        assert rel(host(A[c]), Ao) < 1e-11
