@@ -71,9 +71,12 @@ class CondensedCell:
     Rp: np.ndarray
     el: Element
     lat_inv: np.ndarray  # lattice Vandermonde inverse (monomials of degree k+1)
+    Fextra: Optional[np.ndarray] = None   # condensed fixed load (Newton), (ng,)
+    Rextra: Optional[np.ndarray] = None   # its contribution to the local unknowns
 
 
-def local_system(el: Element, nu: float, beta: float, conv=None, conv_transpose: bool = False):
+def local_system(el: Element, nu: float, beta: float, conv=None, conv_transpose: bool = False,
+                 newton_uhat=None):
     """Full local matrix over (L, u, û, p), forcing map and index sets.
 
     conv: optional lattice values (n_lat_w, 2) of the convecting field w_h on
@@ -86,6 +89,14 @@ def local_system(el: Element, nu: float, beta: float, conv=None, conv_transpose:
     the remaining blocks satisfy Mᵀ = S M S with S = diag(-I_L, I_u, I_û, -I_p),
     the local system with the transposed convection block is S Mᵀ S: the
     system whose solution gives the adjoint (Section 4.1 with A10's objective).
+    newton_uhat: with conv = u_old (the previous velocity at the lattice), the
+    (3, k+1) facet coefficients of the previous û_old on this cell's facets.
+    It adds the Newton term of Section 4.2, C_h(δu; u_old, v): the derivative of
+    the upwind form in its convecting argument with the switch frozen at
+    u_old·n_K, i.e. -(u_old, (δu·∇)v) + <(δu·n_K) u_old^up, tng(v - v̂)> with
+    u_old^up = tng u_old where u_old·n_K > 0 and tng û_old elsewhere.  The
+    unknowns are then the new iterate itself: the right-hand side gains
+    C_h(u_old; u_old, v), returned as info["rhs_extra"].
     """
     k = el.k
     npk = len(exponents(k))
@@ -161,6 +172,33 @@ def local_system(el: Element, nu: float, beta: float, conv=None, conv_transpose:
             Cv[hs, ou:ou + nrt] -= np.einsum("q,qmc,qjc->mj", wf * wp, Hf, tngU)
             Cv[hs, hs] -= np.einsum("q,qmc,qnc->mn", wf * wm, Hf, Hf)
         M += Cv.T if conv_transpose else Cv
+        if newton_uhat is not None:
+            uh = np.asarray(newton_uhat, dtype=float)
+            Cp = np.zeros((n, n))
+            # -(u_old, (φ_j·∇)φ_i): rows v_i, cols δu_j
+            Cp[ou:ou + nrt, ou:ou + nrt] -= np.einsum("q,qc,qjd,qicd->ij", wq, wq_v, U, GU)
+            extra = np.zeros(n)
+            extra[ou:ou + nrt] -= np.einsum("q,qc,qd,qicd->i", wq, wq_v, wq_v, GU)
+            for f in range(3):
+                fd = el.facets[f]
+                s_, xf, wf = el.facet_points(f, nF)
+                nK = fd["nK"]
+                wf_v = el.mono(xf, q_w) @ wc                           # u_old at the facet points
+                an = wf_v @ nK
+                lm = el.facet_legendre(f, s_)
+                Hf = np.einsum("qm,c->qmc", lm, fd["t"])
+                tng_old = wf_v - np.outer(an, nK)
+                tng_hat = np.einsum("qm,m,c->qc", lm, uh[f], fd["t"])
+                wup = np.where((an > 0.0)[:, None], tng_old, tng_hat)
+                Uf = el.rt_values(xf)
+                nU = Uf @ nK                                             # (q, nrt) φ_j·n_K
+                tngU = Uf - np.einsum("qi,c->qic", nU, nK)
+                hs = slice(oh + f * (k + 1), oh + (f + 1) * (k + 1))
+                Cp[ou:ou + nrt, ou:ou + nrt] += np.einsum("q,qj,qc,qic->ij", wf, nU, wup, tngU)
+                Cp[hs, ou:ou + nrt] -= np.einsum("q,qj,qc,qmc->mj", wf, nU, wup, Hf)
+                extra[ou:ou + nrt] += np.einsum("q,q,qc,qic->i", wf, an, wup, tngU)
+                extra[hs] -= np.einsum("q,q,qc,qmc->m", wf, an, wup, Hf)
+            M += Cp
     # forcing: f_h ∈ [P^{k+1}]² from its values at the degree-(k+1) lattice
     lam = lattice_barycentric_2d(k + 1)
     Xl = lam @ el.X
@@ -175,25 +213,36 @@ def local_system(el: Element, nu: float, beta: float, conv=None, conv_transpose:
         g += [oh + f * (k + 1) + m for m in range(k + 1)]
     loc = list(range(oL, oL + nL)) + list(range(ou + 3 * (k + 1), ou + nrt)) + \
         list(range(op + 1, op + npp))
-    return M, rhs_map, np.asarray(g), np.asarray(loc), op, lat_inv, \
-        dict(oL=oL, ou=ou, oh=oh, op=op, npk=npk, nrt=nrt)
+    info = dict(oL=oL, ou=ou, oh=oh, op=op, npk=npk, nrt=nrt)
+    if conv is not None and newton_uhat is not None:
+        info["rhs_extra"] = extra
+    return M, rhs_map, np.asarray(g), np.asarray(loc), op, lat_inv, info
 
 
 def condense_cell(el: Element, nu: float, beta: float, conv=None,
-                  conv_transpose: bool = False) -> CondensedCell:
+                  conv_transpose: bool = False, newton_uhat=None) -> CondensedCell:
     """Static condensation of one cell by a dense Schur complement."""
-    M, rhs_map, g, loc, p0, lat_inv, _ = local_system(el, nu, beta, conv, conv_transpose)
+    M, rhs_map, g, loc, p0, lat_inv, info = local_system(el, nu, beta, conv, conv_transpose, newton_uhat)
     Mll = M[np.ix_(loc, loc)]
     Mlg = M[np.ix_(loc, g)]
     Mgl = M[np.ix_(g, loc)]
-    X = np.linalg.solve(Mll, np.hstack([Mlg, M[loc, p0][:, None], rhs_map[loc]]))
+    extra = info.get("rhs_extra")
+    cols = [Mlg, M[loc, p0][:, None], rhs_map[loc]]
+    if extra is not None:
+        cols.append(extra[loc][:, None])
+    X = np.linalg.solve(Mll, np.hstack(cols))
     ng = len(g)
-    Xg, Xp, Xf = X[:, :ng], X[:, ng], X[:, ng + 1:]
+    nf = rhs_map.shape[1]
+    Xg, Xp, Xf = X[:, :ng], X[:, ng], X[:, ng + 1:ng + 1 + nf]
     A = M[np.ix_(g, g)] - Mgl @ Xg
     d = M[p0, g] - M[p0, loc] @ Xg
     Fmap = rhs_map[g] - Mgl @ Xf
+    Fextra = Rextra = None
+    if extra is not None:
+        Rextra = X[:, ng + 1 + nf]
+        Fextra = extra[g] - Mgl @ Rextra
     return CondensedCell(A=A, d=d, Fmap=Fmap, area=el.area, Rf=Xf, Rg=Xg, Rp=Xp,
-                         el=el, lat_inv=lat_inv)
+                         el=el, lat_inv=lat_inv, Fextra=Fextra, Rextra=Rextra)
 
 
 class HDG:
@@ -202,7 +251,7 @@ class HDG:
     def __init__(self, topo: Topology, k: int, nu: float = 1.0, beta: float = 0.0,
                  gamma: float = 0.0, nu_elem: Optional[np.ndarray] = None,
                  cache: bool = True, conv: Optional[np.ndarray] = None,
-                 conv_transpose: bool = False):
+                 conv_transpose: bool = False, newton_uhat: Optional[np.ndarray] = None):
         self.topo, self.k = topo, k
         self.dpf = 2 * (k + 1)
         self.ng = 3 * self.dpf
@@ -214,6 +263,9 @@ class HDG:
         self.n_dof = topo.n_interior * self.dpf
         self.conv = None if conv is None else np.asarray(conv, dtype=float)
         self.conv_transpose = bool(conv_transpose)
+        self.newton_uhat = None if newton_uhat is None else np.asarray(newton_uhat, dtype=float)
+        if self.newton_uhat is not None:
+            cache = False
         self.cells = []
         memo = {}
         for c in range(nc):
@@ -225,7 +277,8 @@ class HDG:
                 cc = memo[key]
             else:
                 el = Element(X - X[0], gv, k)
-                cc = condense_cell(el, self.nu_elem[c], beta, cv, conv_transpose)
+                nh = None if self.newton_uhat is None else self.newton_uhat[c]
+                cc = condense_cell(el, self.nu_elem[c], beta, cv, conv_transpose, nh)
                 if key is not None:
                     memo[key] = cc
             self.cells.append(cc)
@@ -248,7 +301,9 @@ class HDG:
         return A
 
     def element_load(self, c: int, fvals_c: np.ndarray) -> np.ndarray:
-        return self.cells[c].Fmap @ np.asarray(fvals_c).reshape(-1)
+        cc = self.cells[c]
+        F = cc.Fmap @ np.asarray(fvals_c).reshape(-1)
+        return F if cc.Fextra is None else F + cc.Fextra
 
     # ------------------------------------------------------------ global
     def matrix(self, with_al: bool = True) -> sp.csr_matrix:
@@ -291,6 +346,15 @@ class HDG:
         out[idx >= 0] = x[idx[idx >= 0]]
         return out
 
+    def facet_tangential(self, x: np.ndarray) -> np.ndarray:
+        """(n_cells, 3, k+1): each cell's facet tangential coefficients of the skeleton vector x."""
+        out = np.zeros((self.topo.n_cells, 3, self.k + 1))
+        for c in range(self.topo.n_cells):
+            xg = self.gather(x, c)
+            for f in range(3):
+                out[c, f] = xg[f * self.dpf + self.k + 1:(f + 1) * self.dpf]
+        return out
+
     # ------------------------------------------------------------ exact solve
     def solve_direct(self, F: np.ndarray):
         """Exact discrete solution of A u − Dᵀp = F, D u = 0, Σ|K|p_K = 0.
@@ -316,6 +380,8 @@ class HDG:
         npk = len(exponents(k))
         xg = self.gather(u, c)
         y = cc.Rf @ np.asarray(fvals_c).reshape(-1) - cc.Rg @ xg - cc.Rp * pK
+        if cc.Rextra is not None:
+            y = y + cc.Rextra
         nL = 4 * npk
         Lc = y[:nL].reshape(4, npk)
         nrt = cc.el.n_rt

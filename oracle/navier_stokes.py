@@ -1,4 +1,4 @@
-"""Picard iteration for the steady Navier–Stokes equations (oracle).
+"""Picard and Newton iterations for the steady Navier–Stokes equations (oracle).
 
 TEST INFRASTRUCTURE ONLY.
 
@@ -9,6 +9,12 @@ the iteration stops when ||u_h^(n) - u_h^(n-1)||_{L2(Ω)} < tol.  The velocity
 u_h ∈ RT_k ⊂ [P^{k+1}]² is handed to the next step as its values at each cell's
 degree-(k+1) lattice (exact), the layout of the convecting field.  Every solve
 is a sparse direct solve of the condensed saddle point.
+
+Part (ii), Newton: with the previous iterate (u_old, û_old), solve the scheme
+with C_h(u_old; u, v) + C_h(u; u_old, v) in place of the convection term and
+C_h(u_old; u_old, v) added to the load: the Newton step of eq. nsWeak written for
+the new iterate u = u_old + δu (the switch of the upwind trace frozen at
+u_old·n_K), until ||u^(n) - u^(n-1)||_{L2} < tol.
 """
 
 from __future__ import annotations
@@ -59,3 +65,22 @@ def picard(topo, k, fvals, nu, beta=0.0, gamma=0.0, tol=1e-8, max_steps=50):
         if dist < tol:
             break
     return u, p, n, dist, h, prev
+
+
+def newton(topo, k, fvals, nu, h_start, u_start, p_start, beta=0.0, gamma=0.0, tol=1e-10, max_steps=20):
+    """Newton iteration from the skeleton iterate (u_start, p_start) computed with the
+    HDG object h_start (e.g. the last Picard step, whose local systems recover it).
+    Returns (u, p, steps, distances per step, HDG of the last step)."""
+    u, p, hp = u_start, p_start, h_start
+    dists = []
+    for _ in range(max_steps):
+        w = lattice_velocity(hp, u, p, fvals)
+        uh = hp.facet_tangential(u)
+        h_new = HDG(topo, k, nu=nu, beta=beta, gamma=gamma, conv=w, newton_uhat=uh)
+        un, pn = h_new.solve_direct(h_new.load(fvals))
+        wn = lattice_velocity(h_new, un, pn, fvals)
+        dists.append(l2_distance(h_new, wn, w))
+        u, p, hp = un, pn, h_new
+        if dists[-1] < tol:
+            break
+    return u, p, len(dists), dists, hp

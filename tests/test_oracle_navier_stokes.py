@@ -57,3 +57,21 @@ def test_picard_contracts():
         prev = cur
     ratios = [d[i + 1] / d[i] for i in range(4)]
     assert max(ratios) < 0.6
+
+
+@pytest.mark.parametrize("k,nu", [(1, 0.05), (2, 0.02)])
+def test_newton_quadratic_and_same_fixed_point(k, nu):
+    """Newton from a rough Picard iterate converges quadratically to the Picard fixed point
+    (the same discrete Navier-Stokes solution)."""
+    from oracle.navier_stokes import newton
+    m = unit_square(6, shuffle_seed=1)
+    t = topo_of(m)
+    fv = _ns_forcing(m, k, nu)
+    up, pp, n, d, h, w = picard(t, k, fv, nu, tol=1e-3)
+    un, pn, nn, dists, hn = newton(t, k, fv, nu, h, up, pp, tol=1e-12)
+    assert nn <= 4 and dists[-1] < 1e-12
+    for a, b in zip(dists, dists[1:]):
+        if b > 1e-13:
+            assert b < 5.0 * a * a / max(dists[0], 1e-300) + 1e-13 or b < 1e-3 * a
+    uP, pP, nP, dP, hP, wP = picard(t, k, fv, nu, tol=1e-13, max_steps=200)
+    assert np.abs(un - uP).max() < 1e-11 * np.abs(uP).max()
