@@ -124,6 +124,14 @@ typedef struct {
                              /* (mean of the two sides), summed over the fine      */
                              /* halves of each coarse facet.  NULL = generalized   */
                              /* Stokes.                                            */
+    const double *newton_u;  /* Newton step of Algorithm 3 (Section 4.2): device   */
+                             /* [n_dof], the previous skeleton iterate u_old, with */
+                             /* conv = u_old at the lattice.  Adds the derivative  */
+                             /* of the upwind form in its convecting argument (the */
+                             /* switch frozen at u_old·n) to the order-k operator  */
+                             /* and C_h(u_old; u_old, v) to the load, so that the  */
+                             /* solution is the new iterate.  Lowest-order levels  */
+                             /* keep the Picard form.  NULL = no Newton term.      */
 } hdg_params;
 
 typedef struct {
@@ -292,6 +300,17 @@ hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forc
                       double *u, double *p, const hdg_solve_opts *opts, int *steps_out, double *dist_out,
                       hdg_stream_t stream);
 
+/* Newton iteration for steady Navier-Stokes (Section 4.2, Algorithm 3 part (ii)),
+ * starting from the iterate (u, p) that the context's current operator produced
+ * (for instance after hdg_picard): each step condenses with newton_u = u_old and
+ * conv = u_old at the lattice, solves warm-started, and stops when
+ * ||u_h^(n) - u_h^(n-1)||_{L2} < tol or after max_steps.  u, p: device in/out.
+ * params: the data (its conv and newton_u are replaced).  Other arguments as
+ * hdg_picard.  hdg_adjoint is not available for a Newton-step operator. */
+hdg_status hdg_newton(hdg_ctx *ctx, const hdg_params *params, const double *forcing, double tol, int max_steps,
+                      double *u, double *p, const hdg_solve_opts *opts, int *steps_out, double *dist_out,
+                      hdg_stream_t stream);
+
 /* Sizes after hdg_setup_mesh_hierarchy (k-dependent fields after hdg_condense). */
 hdg_status hdg_get_sizes(const hdg_ctx *ctx, hdg_sizes *out);
 
@@ -350,8 +369,9 @@ hdg_status hdg_restrict_noalloc(hdg_ctx *ctx, int level, const double *rf, doubl
 
 /* Host-side reference-element integrals that hdg_condense contracts with each
  * cell's Jacobian to form the local system of eq. stWeak (Section 3.2) for
- * order k, and to evaluate recovered fields: the blocks R1..R8 packed in that
- * order (layouts in the library source, csrc/reference.cpp).  Returns the number of doubles; writes them to
+ * order k, and to evaluate recovered fields: the blocks R1..R16 packed in that
+ * order (R9..R16: point values for the upwind convection; layouts in the
+ * library source, csrc/reference.cpp).  Returns the number of doubles; writes them to
  * out (host memory) when out is not NULL; returns -1 for k outside 0..4.
  * Needs no GPU. */
 int64_t hdg_reference_tables(int k, double *out);

@@ -54,6 +54,10 @@ def lattice_degree(n_lat: int) -> int:
     return q
 
 
+# relative threshold below which w·n counts as zero in the frozen Newton switch
+NEWTON_TIE = 1e-10
+
+
 def upwind_facet_points(k: int, q_w: int) -> int:
     """Gauss–Legendre points per facet for the upwind terms: exact for degree q_w + 2k + 2."""
     return (q_w + 2 * k + 4) // 2
@@ -76,7 +80,7 @@ class CondensedCell:
 
 
 def local_system(el: Element, nu: float, beta: float, conv=None, conv_transpose: bool = False,
-                 newton_uhat=None):
+                 newton_uhat=None, newton_boundary=(False, False, False)):
     """Full local matrix over (L, u, û, p), forcing map and index sets.
 
     conv: optional lattice values (n_lat_w, 2) of the convecting field w_h on
@@ -94,7 +98,9 @@ def local_system(el: Element, nu: float, beta: float, conv=None, conv_transpose:
     It adds the Newton term of Section 4.2, C_h(δu; u_old, v): the derivative of
     the upwind form in its convecting argument with the switch frozen at
     u_old·n_K, i.e. -(u_old, (δu·∇)v) + <(δu·n_K) u_old^up, tng(v - v̂)> with
-    u_old^up = tng u_old where u_old·n_K > 0 and tng û_old elsewhere.  The
+    u_old^up = tng u_old where u_old·n_K > NEWTON_TIE·max|w| (the lattice values)
+    and tng û_old elsewhere and on the facets flagged in newton_boundary
+    (Dirichlet facets).  The
     unknowns are then the new iterate itself: the right-hand side gains
     C_h(u_old; u_old, v), returned as info["rhs_extra"].
     """
@@ -189,7 +195,10 @@ def local_system(el: Element, nu: float, beta: float, conv=None, conv_transpose:
                 Hf = np.einsum("qm,c->qmc", lm, fd["t"])
                 tng_old = wf_v - np.outer(an, nK)
                 tng_hat = np.einsum("qm,m,c->qc", lm, uh[f], fd["t"])
-                wup = np.where((an > 0.0)[:, None], tng_old, tng_hat)
+                # ties: where |w·n| is at rounding level (Dirichlet facets, symmetric nodes)
+                # the trace of û is taken, so the switch does not follow rounding noise
+                up = (an > NEWTON_TIE * np.abs(conv).max()) & (not newton_boundary[f])
+                wup = np.where(up[:, None], tng_old, tng_hat)
                 Uf = el.rt_values(xf)
                 nU = Uf @ nK                                             # (q, nrt) φ_j·n_K
                 tngU = Uf - np.einsum("qi,c->qic", nU, nK)
@@ -220,9 +229,11 @@ def local_system(el: Element, nu: float, beta: float, conv=None, conv_transpose:
 
 
 def condense_cell(el: Element, nu: float, beta: float, conv=None,
-                  conv_transpose: bool = False, newton_uhat=None) -> CondensedCell:
+                  conv_transpose: bool = False, newton_uhat=None,
+                  newton_boundary=(False, False, False)) -> CondensedCell:
     """Static condensation of one cell by a dense Schur complement."""
-    M, rhs_map, g, loc, p0, lat_inv, info = local_system(el, nu, beta, conv, conv_transpose, newton_uhat)
+    M, rhs_map, g, loc, p0, lat_inv, info = local_system(el, nu, beta, conv, conv_transpose, newton_uhat,
+                                                         newton_boundary)
     Mll = M[np.ix_(loc, loc)]
     Mlg = M[np.ix_(loc, g)]
     Mgl = M[np.ix_(g, loc)]
@@ -278,7 +289,8 @@ class HDG:
             else:
                 el = Element(X - X[0], gv, k)
                 nh = None if self.newton_uhat is None else self.newton_uhat[c]
-                cc = condense_cell(el, self.nu_elem[c], beta, cv, conv_transpose, nh)
+                bnd = tuple(bool(topo.interior_index[topo.cell_facets[c, f]] < 0) for f in range(3))
+                cc = condense_cell(el, self.nu_elem[c], beta, cv, conv_transpose, nh, bnd)
                 if key is not None:
                     memo[key] = cc
             self.cells.append(cc)

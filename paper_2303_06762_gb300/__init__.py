@@ -39,7 +39,8 @@ EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
            "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_apply_multi",
-           "hdg_precond_apply_multi", "hdg_solve_multi", "hdg_solve_batched", "hdg_picard", "hdg_destroy",
+           "hdg_precond_apply_multi", "hdg_solve_multi", "hdg_solve_batched", "hdg_picard", "hdg_newton",
+           "hdg_destroy",
            "hdg_status_string", "hdg_last_error")
 
 
@@ -63,7 +64,8 @@ class _Params(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("nu", ctypes.c_double), ("beta", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("m_p", ctypes.c_int), ("m_h", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("vcycle_growth", ctypes.c_int), ("precision", ctypes.c_int),
-                ("fused_coarse_cells", ctypes.c_int), ("nu_elem", ctypes.c_void_p), ("conv", ctypes.c_void_p)]
+                ("fused_coarse_cells", ctypes.c_int), ("nu_elem", ctypes.c_void_p), ("conv", ctypes.c_void_p),
+                ("newton_u", ctypes.c_void_p)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -105,12 +107,14 @@ class Params:
     fused_coarse_cells: int = 0
     nu_elem: object = None          # optional CUDA float64 tensor [n_cells] of per-cell viscosity
     conv: object = None             # optional CUDA float64 tensor [n_cells, n_lat, 2]: Oseen field w_h
+    newton_u: object = None         # optional CUDA float64 tensor [n_dof]: previous iterate (Newton step)
 
     def to_c(self) -> _Params:
         ne = None if self.nu_elem is None else _ptr(self.nu_elem)
         cv = None if self.conv is None else _ptr(self.conv)
+        nw = None if self.newton_u is None else _ptr(self.newton_u)
         return _Params(self.k, self.nu, self.beta, self.gamma, self.m_p, self.m_h, self.cycle,
-                       self.vcycle_growth, self.precision, self.fused_coarse_cells, ne, cv)
+                       self.vcycle_growth, self.precision, self.fused_coarse_cells, ne, cv, nw)
 
 
 _lib = None
@@ -136,6 +140,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "hdg_solve_multi": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
         "hdg_solve_batched": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
         "hdg_picard": (I, [P, ctypes.POINTER(_Params), P, ctypes.c_double, I, P, P, ctypes.POINTER(SolveOpts),
+                           ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P]),
+        "hdg_newton": (I, [P, ctypes.POINTER(_Params), P, ctypes.c_double, I, P, P, ctypes.POINTER(SolveOpts),
                            ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double), P]),
         "hdg_condense": (I, [P, ctypes.POINTER(_Params), P, P, P]),
         "hdg_load": (I, [P, P, P, P]),
@@ -398,6 +404,21 @@ def hdg_picard(ctx: Context, params: Params, forcing, tol: float = 1e-8, max_ste
     return u, p, steps.value, dist.value
 
 
+def hdg_newton(ctx: Context, params: Params, forcing, u, p, tol: float = 1e-10, max_steps: int = 20,
+               opts: Optional[SolveOpts] = None, stream=None, raise_on_nonconvergence: bool = True):
+    """Newton steps from the iterate (u, p) of the context's current operator (updated in place);
+    returns (u, p, steps, last ||u^n - u^(n-1)||)."""
+    steps = ctypes.c_int()
+    dist = ctypes.c_double()
+    c = params.to_c()
+    o = opts if opts is not None else default_solve_opts()
+    st = load_library().hdg_newton(ctx.handle, ctypes.byref(c), _ptr(forcing), tol, max_steps, _ptr(u), _ptr(p),
+                                   ctypes.byref(o), ctypes.byref(steps), ctypes.byref(dist), _stream(stream))
+    if st != 0 and (st != 5 or raise_on_nonconvergence):
+        ctx.check(st)
+    return u, p, steps.value, dist.value
+
+
 def hdg_recover(ctx: Context, u, forcing=None, stream=None):
     """Local fields of a skeleton solution: (L coefficients [nc, 4, npk], u at the lattice [nc, nlat, 2])."""
     import torch
@@ -492,7 +513,7 @@ def hdg_mg_h(ctx: Context, g, u=None, stream=None):
 
 
 def hdg_reference_tables(k: int) -> dict:
-    """Reference-element tables R1..R8 used by the device condensation and recovery (host call)."""
+    """Reference-element tables R1..R16 used by the device condensation and recovery (host call)."""
     lib = load_library()
     n = lib.hdg_reference_tables(k, None)
     if n < 0:
@@ -500,8 +521,11 @@ def hdg_reference_tables(k: int) -> dict:
     buf = np.empty(n, dtype=np.float64)
     lib.hdg_reference_tables(k, buf.ctypes.data_as(ctypes.c_void_p))
     npk, nrt, nf, nlat = (k + 1) * (k + 2) // 2, (k + 1) * (k + 3), k + 1, (k + 2) * (k + 3) // 2
+    nq, nfq = (k + 5) ** 2, (3 * k + 5) // 2
     shapes = dict(R1=(nrt, 2, 2, npk), R2=(3, nrt, 2, npk), R3=(3, npk, nf), R4=(nrt, 2, nrt, 2),
-                  R5=(nrt, npk), R6=(nrt, 2, nlat), R7=(nrt, 2, nlat), R8=(nlat, nlat))
+                  R5=(nrt, npk), R6=(nrt, 2, nlat), R7=(nrt, 2, nlat), R8=(nlat, nlat),
+                  R9=(nq, nrt, 2), R10=(nq, nrt, 2, 2), R11=(nq, nlat), R12=(nq,),
+                  R13=(3, nfq, nrt, 2), R14=(3, nfq, nlat), R15=(nfq, nf), R16=(nfq,))
     out, o = {}, 0
     for name, shp in shapes.items():
         m = int(np.prod(shp))

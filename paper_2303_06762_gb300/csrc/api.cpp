@@ -456,12 +456,15 @@ const double *cell_nu_of(hdg_ctx *ctx, int l) {
 // finest-level convecting field (library copy), NULL for the generalized Stokes problem
 const double *conv_of(hdg_ctx *ctx) { return ctx->has_conv ? ctx->conv_k.p : nullptr; }
 
+// previous skeleton iterate of a Newton step (library copy), or NULL
+const double *newton_of(hdg_ctx *ctx) { return ctx->has_newton ? ctx->newton_x.p : nullptr; }
+
 // condensed load F from lattice forcing (the element matrices are left untouched)
 void load_impl(hdg_ctx *ctx, const double *forcing, double *rhs_out, cudaStream_t s) {
     DevLevel &LJ = ctx->L[ctx->n_levels - 1];
     CK(launch_condense(ctx->prm.k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, ctx->n_levels - 1),
-                       ctx->prm.beta, ctx->prm.gamma, forcing, conv_of(ctx), ctx->conv_t, nullptr, nullptr,
-                       ctx->opk.Fel.p, ctx->status_flag.p, RecoverArgs(), s));
+                       ctx->prm.beta, ctx->prm.gamma, forcing, conv_of(ctx), ctx->conv_t, newton_of(ctx), nullptr,
+                       nullptr, ctx->opk.Fel.p, ctx->status_flag.p, RecoverArgs(), s));
     CK(launch_assemble_load(LJ, ctx->opk, rhs_out, s));
 }
 
@@ -475,8 +478,8 @@ void recover_impl(hdg_ctx *ctx, const double *u, const double *forcing, double *
     rec.rt = rt;
     rec.ulat = ulat;
     CK(launch_condense(ctx->prm.k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, ctx->n_levels - 1),
-                       ctx->prm.beta, ctx->prm.gamma, forcing, conv_of(ctx), ctx->conv_t, nullptr, nullptr, nullptr,
-                       ctx->status_flag.p, rec, s));
+                       ctx->prm.beta, ctx->prm.gamma, forcing, conv_of(ctx), ctx->conv_t, newton_of(ctx), nullptr,
+                       nullptr, nullptr, ctx->status_flag.p, rec, s));
 }
 
 // Augmented-Lagrangian Uzawa loop with FGMRES inner solves (eq. stOpEq-ALU); returns
@@ -959,7 +962,8 @@ int64_t hdg_reference_tables(int k, double *out) {
         RefTables t;
         build_reference_tables(k, t);
         int64_t n = 0;
-        for (auto *v : {&t.R1, &t.R2, &t.R3, &t.R4, &t.R5, &t.R6, &t.R7, &t.R8}) {
+        for (int i = 0; i < N_REF_TABLES; ++i) {
+            const std::vector<double> *v = ref_table(t, i);
             if (out) std::memcpy(out + n, v->data(), sizeof(double) * v->size());
             n += (int64_t)v->size();
         }
@@ -1081,11 +1085,12 @@ void hdg_destroy(hdg_ctx *ctx) {
     free_operator(ctx->opk);
     dfree(ctx->refk_dev); dfree(ctx->ref0_dev);
     dfree(ctx->kr); dfree(ctx->ku); dfree(ctx->kt); dfree(ctx->krf); dfree(ctx->kuf); dfree(ctx->kgf);
-    dfree(ctx->coarse_inv); dfree(ctx->status_flag); dfree(ctx->conv_k);
+    dfree(ctx->coarse_inv); dfree(ctx->status_flag); dfree(ctx->conv_k); dfree(ctx->newton_x);
     dfree(ctx->V); dfree(ctx->Z); dfree(ctx->w); dfree(ctx->partials); dfree(ctx->small);
     dfree(ctx->uz_partials);
     for (auto *b : {&ctx->rec_L, &ctx->rec_La, &ctx->rec_rt, &ctx->rec_ulat, &ctx->rec_e, &ctx->rec_j, &ctx->adj_F,
-                    &ctx->adj_u, &ctx->adj_p, &ctx->pic_F, &ctx->pic_w0, &ctx->pic_w1, &ctx->pic_e, &ctx->pic_j})
+                    &ctx->adj_u, &ctx->adj_p, &ctx->pic_F, &ctx->pic_w0, &ctx->pic_w1, &ctx->pic_e, &ctx->pic_j,
+                    &ctx->pic_x})
         dfree(*b);
     drop_graph(ctx);
     dfree(ctx->pc_in); dfree(ctx->pc_out);
@@ -1168,8 +1173,8 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
         dalloc(ctx, op.Pinvf, (size_t)L.n_patches * op.np_max * op.np_max);
         CK(launch_condense(0, L, ctx->ref0_dev.p, ctx->ref0, prm->nu, per_cell ? L.cell_nu.p : nullptr,
                            prm->beta, prm->gamma, nullptr, ctx->has_conv ? L.conv_lat.p : nullptr, ctx->conv_t,
-                           op.A.p, op.Af.p, nullptr, ctx->status_flag.p, RecoverArgs(), s));
-        CK(launch_patch_inverse(L, op, ctx->status_flag.p, s));
+                           nullptr, op.A.p, op.Af.p, nullptr, ctx->status_flag.p, RecoverArgs(), s));
+        CK(launch_patch_inverse(L, op, ctx->has_conv ? 1 : 0, ctx->status_flag.p, s));
     }
     DevLevel &LJ = ctx->L[nl - 1];
     DevOperator &op = ctx->opk;
@@ -1181,9 +1186,9 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
     dalloc(ctx, op.Pinv, (size_t)LJ.n_patches * op.np_max * op.np_max);
     dalloc(ctx, op.Pinvf, (size_t)LJ.n_patches * op.np_max * op.np_max);
     CK(launch_condense(k, LJ, ctx->refk_dev.p, ctx->refk, prm->nu, per_cell ? LJ.cell_nu.p : nullptr,
-                       prm->beta, prm->gamma, forcing, conv_of(ctx), ctx->conv_t, op.A.p, op.Af.p, op.Fel.p,
-                       ctx->status_flag.p, RecoverArgs(), s));
-    CK(launch_patch_inverse(LJ, op, ctx->status_flag.p, s));
+                       prm->beta, prm->gamma, forcing, conv_of(ctx), ctx->conv_t, newton_of(ctx), op.A.p, op.Af.p,
+                       op.Fel.p, ctx->status_flag.p, RecoverArgs(), s));
+    CK(launch_patch_inverse(LJ, op, ctx->has_conv ? 1 : 0, ctx->status_flag.p, s));
     for (int l = 1; l < nl; ++l) CK(launch_transfer_H(ctx->L[l], ctx->status_flag.p, s));
     ctx->n0 = 2 * ctx->L[0].n_int;
     dalloc(ctx, ctx->coarse_inv, std::max<int64_t>(ctx->n0 * ctx->n0, 1));
@@ -1242,12 +1247,19 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
             }
         }
         // convecting field (Oseen): kept for the load, recovery and adjoint passes
+        REQUIRE(!prm->newton_u || prm->conv, "newton_u needs conv (the previous velocity at the lattice)");
         ctx->has_conv = prm->conv != nullptr;
         ctx->conv_t = 0;
         if (ctx->has_conv) {
             const size_t n = (size_t)ctx->L[nl - 1].nc * (prm->k + 2) * (prm->k + 3);
             dalloc(ctx, ctx->conv_k, n);
             CK(cudaMemcpyAsync(ctx->conv_k.p, prm->conv, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        }
+        ctx->has_newton = prm->newton_u != nullptr;
+        if (ctx->has_newton) {
+            const size_t n = (size_t)ctx->L[nl - 1].n_int * 2 * (prm->k + 1);
+            dalloc(ctx, ctx->newton_x, std::max<size_t>(n, 1));
+            CK(cudaMemcpyAsync(ctx->newton_x.p, prm->newton_u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         }
         condense_all(ctx, forcing, s);
         if (rhs_out) {
@@ -1438,6 +1450,10 @@ hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, con
     hdg_status st = guard(ctx, [&] {
         NEED_CONDENSED();
         REQUIRE(forcing && u && u_target, "null input");
+        if (ctx->has_newton) {
+            ctx->err = "hdg_adjoint of a Newton-step operator is not implemented";
+            throw Fail{HDG_ERR_UNSUPPORTED};
+        }
         cudaStream_t s = (cudaStream_t)stream;
         const int Jl = ctx->n_levels - 1;
         DevLevel &LJ = ctx->L[Jl];
@@ -1642,6 +1658,7 @@ hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forc
         // u^(0): the generalized Stokes problem with the same data
         hdg_params prm = *params;
         prm.conv = nullptr;
+        prm.newton_u = nullptr;
         check(hdg_condense(ctx, &prm, forcing, ctx->pic_F.p, stream));
         CK(cudaMemsetAsync(u, 0, sizeof(double) * n_dof, s));
         CK(cudaMemsetAsync(p, 0, sizeof(double) * nc, s));
@@ -1671,6 +1688,63 @@ hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forc
     if (dist_out) *dist_out = dist;
     if (st != HDG_OK) return st;
     if (conv != HDG_OK) ctx->err = "Picard iteration or an inner solve reached its limit";
+    return conv;
+}
+
+hdg_status hdg_newton(hdg_ctx *ctx, const hdg_params *params, const double *forcing, double tol, int max_steps,
+                      double *u, double *p, const hdg_solve_opts *opts, int *steps_out, double *dist_out,
+                      hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    hdg_status conv = HDG_OK;
+    int steps = 0;
+    double dist = 0.0;
+    hdg_status st = guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(params && forcing && u && p, "null argument");
+        REQUIRE(max_steps >= 1 && tol >= 0 && std::isfinite(tol), "bad tol or max_steps");
+        REQUIRE(params->k == ctx->prm.k, "params->k differs from the condensed operator's k");
+        cudaStream_t s = (cudaStream_t)stream;
+        DevLevel &LJ = ctx->L[ctx->n_levels - 1];
+        const int k = params->k;
+        const int64_t nc = LJ.nc, nlat = (k + 2) * (k + 3) / 2, n_dof = ctx->n_dof;
+        dalloc(ctx, ctx->pic_F, std::max<int64_t>(n_dof, 1));
+        dalloc(ctx, ctx->pic_w0, nc * 2 * nlat);
+        dalloc(ctx, ctx->pic_w1, nc * 2 * nlat);
+        dalloc(ctx, ctx->pic_e, nc * 2 * nlat);
+        dalloc(ctx, ctx->pic_j, std::max<int64_t>(nc, 1));
+        dalloc(ctx, ctx->pic_x, std::max<int64_t>(n_dof, 1));   // previous skeleton iterate
+        auto check = [&](hdg_status r) {
+            if (r == HDG_ERR_NOT_CONVERGED) conv = r;
+            else if (r != HDG_OK) throw Fail{r};
+        };
+        double *wp = ctx->pic_w0.p, *wc = ctx->pic_w1.p;
+        // the iterate (u, p) was computed with the operator the context holds: recover it with that
+        recover_impl(ctx, u, forcing, nullptr, nullptr, wp, s);
+        hdg_params prm = *params;
+        for (int n = 1; n <= max_steps; ++n) {
+            CK(cudaMemcpyAsync(ctx->pic_x.p, u, sizeof(double) * n_dof, cudaMemcpyDeviceToDevice, s));
+            prm.conv = wp;
+            prm.newton_u = ctx->pic_x.p;
+            check(hdg_condense(ctx, &prm, forcing, ctx->pic_F.p, stream));
+            check(hdg_solve(ctx, ctx->pic_F.p, u, p, opts, nullptr, stream));
+            recover_impl(ctx, u, forcing, nullptr, nullptr, wc, s);
+            CK(launch_objective(k, LJ, ctx->refk_dev.p, ctx->refk, wc, wp, ctx->pic_e.p, ctx->pic_j.p, s));
+            dist = std::sqrt(std::max(2.0 * device_sum(ctx, ctx->pic_j.p, nc, s), 0.0));
+            steps = n;
+            std::swap(wp, wc);
+            if (!std::isfinite(dist)) {
+                ctx->err = "non-finite Newton update";
+                throw Fail{HDG_ERR_NONFINITE};
+            }
+            if (dist < tol) break;
+        }
+        if (!(dist < tol) && conv == HDG_OK) conv = HDG_ERR_NOT_CONVERGED;
+        CK(cudaStreamSynchronize(s));
+    });
+    if (steps_out) *steps_out = steps;
+    if (dist_out) *dist_out = dist;
+    if (st != HDG_OK) return st;
+    if (conv != HDG_OK) ctx->err = "Newton iteration or an inner solve reached its limit";
     return conv;
 }
 

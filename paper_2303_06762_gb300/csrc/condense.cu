@@ -20,10 +20,14 @@
 //     −(u, (w·∇)v)_K + ⟨(w·n)⁺ tng u + (w·n)⁻ tng û, tng(v − v̂)⟩_∂K
 // is added to K from point values (tables R9–R16; the facet switch is taken
 // at the Gauss–Legendre nodes).  K is then non-symmetric, the two
-// eliminations use LU without pivoting (K_ii and S_p have positive definite
-// symmetric parts), and with W₂ = K_gi Y_D − D_ogᵀ in place of Wᵀ:
+// eliminations use LU with partial pivoting, and with W₂ = K_gi Y_D − D_ogᵀ
+// in place of Wᵀ:
 //     A_K = K_gg − K_gi Y_g + W₂ S_p⁻¹ W,   F_K = F_g − K_gi Y_F + W₂ S_p⁻¹ D_oi Y_F.
 // With conv_t the transposed convection block is used (the adjoint system).
+// A Newton step (Section 4.2, Algorithm 3) adds the derivative of the upwind
+// form in its convecting argument, with the switch frozen at u_old·n_K, and
+// the load C_h(u_old; u_old, v) on the (u, û) rows (newton_x = the previous
+// skeleton iterate, conv = u_old at the lattice).
 // Element matrices are stored transposed, A_K[q][p] = (A_K)_pq, so that the
 // row-gathering kernels read consecutive addresses.  Facet unknowns are expressed in the
 // global facet basis of include/hdg.h: the reference facet moments map to
@@ -60,7 +64,7 @@ struct Dims {
     static constexpr int O_K = O_C + NL * NCOL;
     static constexpr int O_D = O_K + NCOL * NCOL;
     static constexpr int O_F = O_D + NRT * NPK;
-    static constexpr int O_FN = O_F + NRT;
+    static constexpr int O_FN = O_F + NCOL;                // load over all (u, û) rows
     static constexpr int O_Y = O_FN + 2 * NLAT;
     static constexpr int O_SP = O_Y + NRI * NY;
     static constexpr int O_W = O_SP + NPO * NPO;
@@ -81,6 +85,13 @@ struct Dims {
     static constexpr int O_TAU = O_HQ + NQ * NRT * 2;      // tangential traces at facet nodes
     static constexpr int O_AW = O_TAU + 3 * NFQ * NCOL;    // |F| weight (w·n_K) at facet nodes
     static constexpr int TOTAL_CONV = O_AW + 3 * NFQ;
+    // Newton term (only with a previous skeleton iterate); G2 reuses the GQ region, which
+    // the Picard part no longer needs when the Newton part starts
+    static constexpr int O_G2 = O_GQ;                       // weight (Jᵀu_old)·∇^ phi^_i at volume nodes
+    static constexpr int O_NRM = TOTAL_CONV;                // phi_j·n_K at facet nodes
+    static constexpr int O_WUP = O_NRM + 3 * NFQ * NRT;     // upwinded tangential u_old at facet nodes
+    static constexpr int O_UH = O_WUP + 3 * NFQ;            // û_old tangential coefficients (3 x NF)
+    static constexpr int TOTAL_NEWTON = O_UH + 3 * NF;
 };
 
 // geometry slots inside the O_GEO block
@@ -139,15 +150,29 @@ __device__ bool chol_serial(double *sm, int n, int ld) {
     return true;
 }
 
-// in-place LU factorisation without pivoting (unit lower L), serial; returns
-// false on a non-positive pivot (matrices with a positive definite symmetric
-// part have positive pivots)
-__device__ bool lu_serial(double *sm, int n, int ld) {
+// in-place LU factorisation with partial pivoting (unit lower L), serial: row j
+// of the factors is row perm[j] swapped in at step j; returns false on a zero or
+// non-finite pivot
+__device__ bool lu_serial(double *sm, int n, int ld, int *perm) {
     for (int j = 0; j < n; ++j) {
-        double d = sm[j * ld + j];
-        if (!(d > 0.0)) return false;
+        int p = j;
+        double best = fabs(sm[j * ld + j]);
+        for (int i = j + 1; i < n; ++i)
+            if (fabs(sm[i * ld + j]) > best) {
+                best = fabs(sm[i * ld + j]);
+                p = i;
+            }
+        perm[j] = p;
+        if (!(best > 1e-300) || !isfinite(best)) return false;
+        if (p != j)
+            for (int c = 0; c < n; ++c) {
+                const double t = sm[j * ld + c];
+                sm[j * ld + c] = sm[p * ld + c];
+                sm[p * ld + c] = t;
+            }
+        const double d = sm[j * ld + j];
         for (int i = j + 1; i < n; ++i) {
-            double l = sm[i * ld + j] / d;
+            const double l = sm[i * ld + j] / d;
             sm[i * ld + j] = l;
             for (int c = j + 1; c < n; ++c) sm[i * ld + c] -= l * sm[j * ld + c];
         }
@@ -155,8 +180,16 @@ __device__ bool lu_serial(double *sm, int n, int ld) {
     return true;
 }
 
-// solve (LU) x = b for column `col` of the row-major RHS block B (n x nb, ld ldb)
-__device__ void lu_solve_col(const double *LU, int n, int ld, double *B, int ldb, int col) {
+// solve (LU) x = P b for column `col` of the row-major RHS block B (n x nb, ld ldb)
+__device__ void lu_solve_col(const double *LU, int n, int ld, const int *perm, double *B, int ldb, int col) {
+    for (int j = 0; j < n; ++j) {
+        const int p = perm[j];
+        if (p != j) {
+            const double t = B[j * ldb + col];
+            B[j * ldb + col] = B[p * ldb + col];
+            B[p * ldb + col] = t;
+        }
+    }
     for (int i = 0; i < n; ++i) {
         double s = B[i * ldb + col];
         for (int p = 0; p < i; ++p) s -= LU[i * ld + p] * B[p * ldb + col];
@@ -195,8 +228,10 @@ struct RefPtrs {
 //            and û (w·n_K < 0); tangential traces t_F·φ_i = o sc_i t̂ᵀJᵀJ φ̂_i/(|F| det J)
 //            and, for û, o^m l_m(s_g)/sqrt|F|.
 template <int K>
-__device__ void convection_block(int64_t c, const double *__restrict__ conv, int conv_t, const RefPtrs &T,
-                                 const double *geo, const double *sc, double *Km, double *sm) {
+__device__ void convection_block(int64_t c, const double *__restrict__ conv, int conv_t,
+                                 const double *__restrict__ newton_x, const int *__restrict__ cell_int,
+                                 const RefPtrs &T, const double *geo, const double *sc, double *Km, double *Fl,
+                                 double *sm) {
     using D = Dims<K>;
     const double *__restrict__ R9 = T.R[8];
     const double *__restrict__ R10 = T.R[9];
@@ -283,6 +318,100 @@ __device__ void convection_block(int64_t c, const double *__restrict__ conv, int
         Km[idx] += v;
     }
     __syncthreads();
+    if (!newton_x) return;
+    // Newton term of Algorithm 3 (derivative of the upwind form in its convecting argument, the
+    // switch frozen at u_old·n_K), on rows (v, v̂) and columns δu:
+    //   -(u_old, (φ_j·∇)φ_i) + <(φ_j·n_K) u_old^up, tng(v - v̂)>,
+    // and the load C_h(u_old; u_old, v) (the same form at δu = u_old), with u_old = w (lattice
+    // values) and u_old^up = tng u_old where u_old·n_K > 0, tng û_old elsewhere.
+    double *G2 = sm + D::O_G2, *nrm = sm + D::O_NRM, *wup = sm + D::O_WUP, *uh = sm + D::O_UH;
+    __shared__ double s_tie;
+    if (tid == 0) {
+        double mx = 0.0;
+        for (int i = 0; i < 2 * D::NLAT; ++i) mx = fmax(mx, fabs(wl[i]));
+        s_tie = 1e-10 * mx;     // |w·n| at rounding level counts as zero (same rule as the oracle)
+    }
+    for (int i = tid; i < 3 * D::NF; i += nt) {
+        const int f = i / D::NF, m = i % D::NF;
+        const int j = cell_int[3 * c + f];
+        uh[i] = j >= 0 ? newton_x[(size_t)j * 2 * D::NF + D::NF + m] : 0.0;
+    }
+    for (int idx = tid; idx < D::NQ * D::NRT * 2; idx += nt) {
+        // G2[q][i][b] = ω_q Σ_a (Jᵀ u_old)_a d_b phi^_{i,a}
+        const int b = idx & 1, qi = idx >> 1, q = qi / D::NRT, i = qi % D::NRT;
+        double wx = 0.0, wy = 0.0;
+        for (int n = 0; n < D::NLAT; ++n) {
+            const double l = R11[q * D::NLAT + n];
+            wx += l * wl[2 * n];
+            wy += l * wl[2 * n + 1];
+        }
+        const double t0 = geo[G_J + 0] * wx + geo[G_J + 2] * wy, t1 = geo[G_J + 1] * wx + geo[G_J + 3] * wy;
+        const double *d = R10 + ((size_t)(q * D::NRT + i) * 2) * 2;   // [a][b]
+        G2[idx] = R12[q] * (t0 * d[0 * 2 + b] + t1 * d[1 * 2 + b]);
+    }
+    for (int idx = tid; idx < 3 * D::NFQ * D::NRT; idx += nt) {
+        const int fg = idx / D::NRT, j = idx % D::NRT, f = fg / D::NFQ;
+        const double *ph = R13 + ((size_t)fg * D::NRT + j) * 2;
+        const double px = geo[G_J + 0] * ph[0] + geo[G_J + 1] * ph[1], py = geo[G_J + 2] * ph[0] + geo[G_J + 3] * ph[1];
+        nrm[idx] = sc[j] * (px * geo[G_NK + 2 * f] + py * geo[G_NK + 2 * f + 1]) / det;
+    }
+    __syncthreads();
+    for (int fg = tid; fg < 3 * D::NFQ; fg += nt) {
+        const int f = fg / D::NFQ;
+        double wx = 0.0, wy = 0.0;
+        for (int n = 0; n < D::NLAT; ++n) {
+            const double l = R14[fg * D::NLAT + n];
+            wx += l * wl[2 * n];
+            wy += l * wl[2 * n + 1];
+        }
+        double v;
+        // ties: where |w·n| is at rounding level (Dirichlet facets, symmetric nodes) the
+        // trace of û is taken, so the switch does not follow rounding noise
+        const double wn = wx * geo[G_NK + 2 * f] + wy * geo[G_NK + 2 * f + 1];
+        if (wn > s_tie && cell_int[3 * c + f] >= 0) {
+            v = wx * geo[G_TF + 2 * f] + wy * geo[G_TF + 2 * f + 1];
+        } else {
+            v = 0.0;
+            for (int m = 0; m < D::NF; ++m) v += uh[f * D::NF + m] * tau[fg * D::NCOL + D::NRT + f * D::NF + m];
+        }
+        wup[fg] = v;
+    }
+    __syncthreads();
+    for (int idx = tid; idx < D::NCOL * D::NRT; idx += nt) {
+        const int row = idx / D::NRT, j = idx % D::NRT;
+        double v = 0.0;
+        if (row < D::NRT) {
+            double acc = 0.0;
+            for (int q = 0; q < D::NQ; ++q) {
+                const double *g2 = G2 + (q * D::NRT + row) * 2;
+                const double *ph = R9 + ((size_t)q * D::NRT + j) * 2;
+                acc += g2[0] * ph[0] + g2[1] * ph[1];
+            }
+            v = -sc[row] * sc[j] / adet * acc;
+        }
+        const double sr = row < D::NRT ? 1.0 : -1.0;
+        for (int fg = 0; fg < 3 * D::NFQ; ++fg) {
+            const int f = fg / D::NFQ, g = fg % D::NFQ;
+            const double lw = geo[G_LEN + f] * R16[g];
+            v += sr * lw * nrm[fg * D::NRT + j] * wup[fg] * tau[fg * D::NCOL + row];
+        }
+        Km[row * D::NCOL + j] += v;
+    }
+    for (int row = tid; row < D::NCOL; row += nt) {
+        double v = 0.0;
+        if (row < D::NRT) {
+            double acc = 0.0;
+            for (int q = 0; q < D::NQ; ++q) {
+                const double *g2 = G2 + (q * D::NRT + row) * 2;
+                acc += g2[0] * wh[2 * q] + g2[1] * wh[2 * q + 1];
+            }
+            v = -sc[row] * (det > 0.0 ? 1.0 : -1.0) * acc;
+        }
+        const double sr = row < D::NRT ? 1.0 : -1.0;
+        for (int fg = 0; fg < 3 * D::NFQ; ++fg) v += sr * aw[fg] * wup[fg] * tau[fg * D::NCOL + row];
+        Fl[row] += v;
+    }
+    __syncthreads();
 }
 
 template <int K>
@@ -290,7 +419,8 @@ __global__ void __launch_bounds__(128)
 condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__restrict__ cells,
                 RefPtrs T, double nu_scalar, const double *__restrict__ nu_cell,
                 double beta, double gamma, const double *__restrict__ forcing,
-                const double *__restrict__ conv, int conv_t,
+                const double *__restrict__ conv, int conv_t, const double *__restrict__ newton_x,
+                const int *__restrict__ cell_int,
                 double *__restrict__ Aout, float *__restrict__ Afout, double *__restrict__ Fout,
                 int *flag, RecoverArgs rec) {
     using D = Dims<K>;
@@ -320,6 +450,7 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
     double *W2 = sm + D::O_W2;
     const int tid = threadIdx.x, nt = blockDim.x;
     __shared__ int s_ok;
+    __shared__ int s_perm[32];   // row interchanges of the LU factorisations (NRI, NPO <= 20)
 
     for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
         if (tid == 0) {
@@ -392,6 +523,7 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
             }
             Fl[i] = sgn * s * sc[i];
         }
+        for (int i = D::NRT + tid; i < D::NCOL; i += nt) Fl[i] = 0.0;
         __syncthreads();
         // K = (nu/|det|) CᵀC + beta M_u
         {
@@ -416,7 +548,7 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
             }
         }
         __syncthreads();
-        if (conv) convection_block<K>(c, conv, conv_t, T, geo, sc, Km, sm);
+        if (conv) convection_block<K>(c, conv, conv_t, newton_x, cell_int, T, geo, sc, Km, Fl, sm);
         // global column of output unknown o: facet f, t = normal/tangential, m
         auto gcol = [&](int o) {
             int f = o / (2 * D::NF), t = (o / D::NF) & 1, m = o % D::NF;
@@ -436,10 +568,11 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
                 Y[idx] = v;
             }
             __syncthreads();
-            if (tid == 0 && !(conv ? lu_serial(Lii, D::NRI, D::NRI) : chol_serial(Lii, D::NRI, D::NRI))) s_ok = 0;
+            if (tid == 0 && !(conv ? lu_serial(Lii, D::NRI, D::NRI, s_perm) : chol_serial(Lii, D::NRI, D::NRI)))
+                s_ok = 0;
             __syncthreads();
             for (int col = tid; col < D::NY; col += nt) {
-                if (conv) lu_solve_col(Lii, D::NRI, D::NRI, Y, D::NY, col);
+                if (conv) lu_solve_col(Lii, D::NRI, D::NRI, s_perm, Y, D::NY, col);
                 else chol_solve_col(Lii, D::NRI, D::NRI, Y, D::NY, col);
             }
             __syncthreads();
@@ -474,10 +607,11 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
                     W2[idx] = s;
                 }
             __syncthreads();
-            if (tid == 0 && !(conv ? lu_serial(Sp, D::NPO, D::NPO) : chol_serial(Sp, D::NPO, D::NPO))) s_ok = 0;
+            if (tid == 0 && !(conv ? lu_serial(Sp, D::NPO, D::NPO, s_perm) : chol_serial(Sp, D::NPO, D::NPO)))
+                s_ok = 0;
             __syncthreads();
             for (int col = tid; col < D::NG + 1; col += nt) {
-                if (conv) lu_solve_col(Sp, D::NPO, D::NPO, Zm, D::NG + 1, col);
+                if (conv) lu_solve_col(Sp, D::NPO, D::NPO, s_perm, Zm, D::NG + 1, col);
                 else chol_solve_col(Sp, D::NPO, D::NPO, Zm, D::NG + 1, col);
             }
             __syncthreads();
@@ -554,7 +688,7 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
         if (Fout)
             for (int p = tid; p < D::NG; p += nt) {
                 int gp = gcol(p);
-                double s = gp < D::NRT ? Fl[gp] : 0.0;
+                double s = Fl[gp];
                 for (int r = 0; r < D::NRI; ++r)
                     s -= Km[gp * D::NCOL + 3 * D::NF + r] * Y[r * D::NY + D::NG + D::NPO];
                 for (int j = 0; j < D::NPO; ++j) s += Wl[j * D::NG + p] * Zm[j * (D::NG + 1) + D::NG];
@@ -569,14 +703,15 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
 template <int K>
 cudaError_t launch_condense_k(const DevLevel &L, const double *ref, const RefTables &rt, double nu,
                               const double *nu_cell, double beta, double gamma, const double *forcing,
-                              const double *conv, int conv_t, double *A, float *Af, double *Fel, int *flag,
-                              const RecoverArgs &rec, cudaStream_t s) {
+                              const double *conv, int conv_t, const double *newton_x, double *A, float *Af,
+                              double *Fel, int *flag, const RecoverArgs &rec, cudaStream_t s) {
     using D = Dims<K>;
     if (conv && (rt.nq != D::NQ || rt.nfq != D::NFQ)) return cudaErrorInvalidValue;
-    size_t smem = sizeof(double) * (conv ? D::TOTAL_CONV : D::TOTAL);
+    if (newton_x && !conv) return cudaErrorInvalidValue;
+    size_t smem = sizeof(double) * (newton_x ? D::TOTAL_NEWTON : conv ? D::TOTAL_CONV : D::TOTAL);
     auto kern = condense_kernel<K>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(double) * D::TOTAL_CONV));
+                                         (int)(sizeof(double) * D::TOTAL_NEWTON));
     if (e != cudaSuccess) return e;
     RefPtrs T;
     for (int i = 0; i < N_REF_TABLES; ++i) T.R[i] = ref + ref_table_offset(rt, i);
@@ -584,21 +719,22 @@ cudaError_t launch_condense_k(const DevLevel &L, const double *ref, const RefTab
     if (grid < 1) return cudaSuccess;
     note_launches(1);
     kern<<<(unsigned)grid, 128, smem, s>>>(L.nc, L.coords.p, L.cells.p, T, nu, nu_cell, beta, gamma, forcing,
-                                           conv, conv_t, A, Af, Fel, flag, rec);
+                                           conv, conv_t, newton_x, L.cell_int.p, A, Af, Fel, flag, rec);
     return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ patch inverses
 // Patch matrix A_ss assembled from the cells of the vertex star (slots = patch
-// facets), then inverted by Gauss-Jordan without pivoting (A_ss is SPD for
-// Stokes and has a positive definite symmetric part for Oseen).
+// facets), then inverted by Gauss-Jordan with partial pivoting (A_ss is SPD for
+// Stokes and has a positive definite symmetric part for Oseen; a Newton-step
+// operator need not).
 __global__ void patch_inverse_kernel(int n_patches, int pf_max, int pc_max, int dpf, int nloc,
                                      int np_max, const int *__restrict__ patch_nf,
                                      const int *__restrict__ patch_nc,
                                      const int *__restrict__ patch_cells,
                                      const int *__restrict__ slot_src, const double *__restrict__ A,
                                      double *__restrict__ Pinv, float *__restrict__ Pinvf,
-                                     int *flag) {
+                                     int pivot, int *flag) {
     extern __shared__ double sm[];
     int p = blockIdx.x;
     if (p >= n_patches) return;
@@ -608,6 +744,7 @@ __global__ void patch_inverse_kernel(int n_patches, int pf_max, int pc_max, int 
     double *colp = M + np_max * np_max;       // np_max
     double *rowp = colp + np_max;             // np_max
     int *lfmap = (int *)(rowp + np_max);      // pc_max*pf_max: local facet of slot j in star cell si
+    int *ipiv = lfmap + pc_max * pf_max;      // np_max: row interchanged at each step
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int i = tid; i < pc_max * pf_max; i += nt) lfmap[i] = -1;
     __syncthreads();
@@ -631,15 +768,38 @@ __global__ void patch_inverse_kernel(int n_patches, int pf_max, int pc_max, int 
         M[P * np + Q] = s;
     }
     __syncthreads();
+    // in-place Gauss-Jordan; with `pivot` partial pivoting (the row interchanges are undone on
+    // the columns of the result at the end), without it the SPD pivots are checked positive
     __shared__ int ok;
     if (tid == 0) ok = 1;
     for (int piv = 0; piv < np; ++piv) {
         __syncthreads();
-        double d = M[piv * np + piv];
-        if (!(d > 0.0)) {
-            if (tid == 0) ok = 0;
-            d = 1.0;
+        if (tid == 0) {
+            int best = piv;
+            double bv = fabs(M[piv * np + piv]);
+            if (pivot) {
+                for (int i = piv + 1; i < np; ++i)
+                    if (fabs(M[i * np + piv]) > bv) {
+                        bv = fabs(M[i * np + piv]);
+                        best = i;
+                    }
+                if (!(bv > 1e-300) || !isfinite(bv)) ok = 0;
+            } else if (!(M[piv * np + piv] > 0.0)) {
+                ok = 0;
+            }
+            ipiv[piv] = best;
         }
+        __syncthreads();
+        const int best = ipiv[piv];
+        if (best != piv)
+            for (int j = tid; j < np; j += nt) {
+                const double t = M[piv * np + j];
+                M[piv * np + j] = M[best * np + j];
+                M[best * np + j] = t;
+            }
+        __syncthreads();
+        double d = M[piv * np + piv];
+        if (!(fabs(d) > 1e-300) || !isfinite(d)) d = 1.0;
         for (int i = tid; i < np; i += nt) {
             colp[i] = M[i * np + piv];
             rowp[i] = M[piv * np + i];
@@ -656,6 +816,16 @@ __global__ void patch_inverse_kernel(int n_patches, int pf_max, int pc_max, int 
         }
     }
     __syncthreads();
+    for (int piv = np - 1; piv >= 0; --piv) {
+        const int q = ipiv[piv];
+        if (q != piv)
+            for (int i = tid; i < np; i += nt) {
+                const double t = M[i * np + piv];
+                M[i * np + piv] = M[i * np + q];
+                M[i * np + q] = t;
+            }
+        __syncthreads();
+    }
     // stored transposed, Pinv[j][i] = (A_ss^{-1})_ij, for the column-reading smoother
     for (int idx = tid; idx < np_max * np_max; idx += nt) {
         int j = idx / np_max, i = idx % np_max;
@@ -1003,13 +1173,13 @@ cudaError_t launch_objective(int k, const DevLevel &L, const double *ref, const 
 
 cudaError_t launch_condense(int k, const DevLevel &L, const double *ref, const RefTables &rt, double nu,
                             const double *nu_cell, double beta, double gamma, const double *forcing,
-                            const double *conv, int conv_t, double *A, float *Af, double *Fel, int *flag,
-                            const RecoverArgs &rec, cudaStream_t s) {
+                            const double *conv, int conv_t, const double *newton_x, double *A, float *Af,
+                            double *Fel, int *flag, const RecoverArgs &rec, cudaStream_t s) {
     switch (k) {
 #define HDG_CONDENSE_CASE(KK)                                                                         \
     case KK:                                                                                          \
-        return launch_condense_k<KK>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, conv, conv_t, A, Af, \
-                                     Fel, flag, rec, s);
+        return launch_condense_k<KK>(L, ref, rt, nu, nu_cell, beta, gamma, forcing, conv, conv_t, newton_x, \
+                                     A, Af, Fel, flag, rec, s);
         HDG_CONDENSE_CASE(0)
         HDG_CONDENSE_CASE(1)
         HDG_CONDENSE_CASE(2)
@@ -1020,17 +1190,17 @@ cudaError_t launch_condense(int k, const DevLevel &L, const double *ref, const R
     }
 }
 
-cudaError_t launch_patch_inverse(const DevLevel &L, const DevOperator &op, int *flag, cudaStream_t s) {
+cudaError_t launch_patch_inverse(const DevLevel &L, const DevOperator &op, int pivot, int *flag, cudaStream_t s) {
     if (L.n_patches == 0) return cudaSuccess;
     size_t smem = sizeof(double) * ((size_t)op.np_max * op.np_max + 2 * op.np_max) +
-                  sizeof(int) * (size_t)L.pc_max * L.pf_max;
+                  sizeof(int) * ((size_t)L.pc_max * L.pf_max + op.np_max);
     cudaError_t e = cudaFuncSetAttribute(patch_inverse_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launches(1);
     patch_inverse_kernel<<<L.n_patches, 256, smem, s>>>(
         L.n_patches, L.pf_max, L.pc_max, op.dpf, op.nloc, op.np_max, L.patch_nf.p, L.patch_nc.p,
-        L.patch_cells.p, L.patch_slot_src.p, op.A.p, op.Pinv.p, op.Pinvf.p, flag);
+        L.patch_cells.p, L.patch_slot_src.p, op.A.p, op.Pinv.p, op.Pinvf.p, pivot, flag);
     return cudaGetLastError();
 }
 

@@ -187,6 +187,8 @@ struct hdg_ctx {
     bool has_conv = false;                   // Oseen: convecting field given
     int conv_t = 0;                          // operators built from the transposed convection
     hdg::DBuf<double> conv_k;                // finest convecting field, lattice layout (copy)
+    bool has_newton = false;                 // Newton step: previous skeleton iterate below
+    hdg::DBuf<double> newton_x;
     hdg::RefTables refk, ref0;
     hdg::DBuf<double> refk_dev, ref0_dev;   // packed R1..R6
     hdg::DevOperator opk;                    // order-k operator on the finest mesh
@@ -223,7 +225,7 @@ struct hdg_ctx {
     long long pcm_kernels = 0;
     hdg::DBuf<double> pcm_in, pcm_out;
     cudaStream_t batch_stream = nullptr;     // private stream for hdg_solve_batched
-    hdg::DBuf<double> pic_F, pic_w0, pic_w1, pic_e, pic_j;   // Picard iteration work
+    hdg::DBuf<double> pic_F, pic_w0, pic_w1, pic_e, pic_j, pic_x;   // Picard / Newton iteration work
     // fused MG_h on levels 0..small_Ls (one thread block), -1 when not used
     int small_Ls = -1;
     size_t small_smem_d = 0, small_smem_f = 0;   // per-CTA shared memory of the fused kernel
@@ -251,16 +253,18 @@ std::string build_transfer(const HostLevel &coarse, const HostLevel &fine, HostT
 // kernels: condensation and setup (condense.cu)
 // conv: lattice values of the convecting field (NULL = Stokes); conv_t: use the
 // transposed convection block (adjoint system)
+// newton_x: previous skeleton iterate [n_int][dpf] for the Newton term (requires conv), or NULL
 cudaError_t launch_condense(int k, const DevLevel &L, const double *ref, const RefTables &rt,
                             double nu, const double *nu_cell, double beta, double gamma,
-                            const double *forcing, const double *conv, int conv_t, double *A, float *Af,
-                            double *Fel, int *flag, const RecoverArgs &rec, cudaStream_t s);
+                            const double *forcing, const double *conv, int conv_t, const double *newton_x,
+                            double *A, float *Af, double *Fel, int *flag, const RecoverArgs &rec, cudaStream_t s);
 cudaError_t launch_conv_flux(const DevLevel &L, const double *ref, const RefTables &rt, const double *conv,
                              double *flux, cudaStream_t s);
 cudaError_t launch_flux_restrict(const DevLevel &fine, const double *ff, double *fc, cudaStream_t s);
 cudaError_t launch_rt0_vertex(const DevLevel &L, const double *flux, double *out, cudaStream_t s);
 cudaError_t launch_transpose_blocks(int64_t nblk, int n, const double *in, double *out, cudaStream_t s);
-cudaError_t launch_patch_inverse(const DevLevel &L, const DevOperator &op, int *flag, cudaStream_t s);
+// pivot: partial pivoting (non-symmetric patch matrices); without it SPD pivots are checked positive
+cudaError_t launch_patch_inverse(const DevLevel &L, const DevOperator &op, int pivot, int *flag, cudaStream_t s);
 cudaError_t launch_transfer_H(const DevLevel &fine, int *flag, cudaStream_t s);
 cudaError_t launch_coarse_inverse(const DevLevel &L0, double *inv, int64_t n, int *flag,
                                   cudaStream_t s);
