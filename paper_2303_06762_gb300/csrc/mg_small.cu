@@ -25,44 +25,51 @@
 namespace hdg {
 namespace {
 
-// the CTAs of the launch (a cluster, or one block) acting as one team
+// the CTAs of the launch acting as one team: a cluster (CL), or one block
+template <bool CL>
 struct Team {
     int rank, size;
     __device__ int tid() const { return rank * (int)blockDim.x + (int)threadIdx.x; }
     __device__ int nthreads() const { return size * (int)blockDim.x; }
     __device__ void sync() const {
-        if (size == 1) {
-            __syncthreads();
-        } else {
+        if constexpr (CL) {
             // non-.aligned forms: no assumption on warp convergence at the call
             asm volatile("barrier.cluster.arrive.release;\n"
                          "barrier.cluster.wait.acquire;\n" ::: "memory");
+        } else {
+            __syncthreads();
         }
+    }
+    // values written during the kernel: through L2 when another SM of the cluster may
+    // have written them; in a single block its own stores are visible after the barrier
+    template <class T>
+    __device__ T ld(const T *p) const {
+        if constexpr (CL) return __ldcg(p);
+        else return *p;
     }
 };
 
-__device__ __forceinline__ Team make_team() {
-    unsigned r, n;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
-    return Team{(int)r, (int)n};
+template <bool CL>
+__device__ __forceinline__ Team<CL> make_team() {
+    if constexpr (CL) {
+        unsigned r, n;
+        asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+        asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(n));
+        return Team<CL>{(int)r, (int)n};
+    } else {
+        return Team<CL>{0, 1};
+    }
 }
 
-// loads of values written during the kernel (possibly by another SM): through L2
-template <class T>
-__device__ __forceinline__ T ld(const T *p) {
-    return __ldcg(p);
-}
-
-template <class T>
-__device__ void blk_fill(const Team &tm, T *u, int n) {
+template <class T, bool CL>
+__device__ void blk_fill(const Team<CL> &tm, T *u, int n) {
     for (int i = tm.tid(); i < n; i += tm.nthreads()) u[i] = T(0);
 }
 
 // one colour phase: CTA `rank` owns the patches p0 + rank + i*size, and its
 // residual rows stay in its shared memory between the two passes
-template <class T>
-__device__ void blk_gs_colour(const Team &tm, const SmallLevel<T> &L, int c, const T *g, T *u, T *rs) {
+template <class T, bool CL>
+__device__ void blk_gs_colour(const Team<CL> &tm, const SmallLevel<T> &L, int c, const T *g, T *u, T *rs) {
     const int p0 = L.colour_ptr[c], p1 = L.colour_ptr[c + 1];
     const int mine = (p1 - p0 - tm.rank + tm.size - 1) / tm.size;
     const int items = (mine > 0 ? mine : 0) * L.np_max;
@@ -72,7 +79,7 @@ __device__ void blk_gs_colour(const Team &tm, const SmallLevel<T> &L, int c, con
         if (t >= np) continue;
         const int js = t >> 1, d = t & 1;
         const int F = L.patch_facets[p * L.pf_max + js];
-        T acc = ld(g + 2 * F + d);
+        T acc = tm.ld(g + 2 * F + d);
         for (int q = 0; q < 2; ++q) {
             const int src = L.slot_src[(p * L.pf_max + js) * 2 + q];
             const int si = src >> 2, lf = src & 3;
@@ -81,7 +88,7 @@ __device__ void blk_gs_colour(const Team &tm, const SmallLevel<T> &L, int c, con
 #pragma unroll
             for (int col = 0; col < 6; ++col) {
                 const int j = L.cell_int[3 * cell + col / 2];
-                if (j >= 0) acc -= Ac[col * 6] * ld(u + 2 * j + (col & 1));
+                if (j >= 0) acc -= Ac[col * 6] * tm.ld(u + 2 * j + (col & 1));
             }
         }
         rs[w] = acc;
@@ -96,18 +103,18 @@ __device__ void blk_gs_colour(const Team &tm, const SmallLevel<T> &L, int c, con
         T acc = 0;
         for (int j = 0; j < np; ++j) acc += Pi[j * L.np_max + t] * rp[j];
         T *dst = u + 2 * L.patch_facets[p * L.pf_max + (t >> 1)] + (t & 1);
-        *dst = ld(dst) + acc;
+        *dst = tm.ld(dst) + acc;
     }
     tm.sync();
 }
 
-template <class T>
-__device__ void blk_sweep(const Team &tm, const SmallLevel<T> &L, const T *g, T *u, bool reverse, T *rs) {
+template <class T, bool CL>
+__device__ void blk_sweep(const Team<CL> &tm, const SmallLevel<T> &L, const T *g, T *u, bool reverse, T *rs) {
     for (int i = 0; i < L.n_colours; ++i) blk_gs_colour(tm, L, reverse ? L.n_colours - 1 - i : i, g, u, rs);
 }
 
-template <class T>
-__device__ void blk_residual(const Team &tm, const SmallLevel<T> &L, const T *g, const T *u, T *r) {
+template <class T, bool CL>
+__device__ void blk_residual(const Team<CL> &tm, const SmallLevel<T> &L, const T *g, const T *u, T *r) {
     for (int idx = tm.tid(); idx < 2 * L.n_int; idx += tm.nthreads()) {
         const int i = idx >> 1, d = idx & 1;
         T acc = 0;
@@ -119,20 +126,20 @@ __device__ void blk_residual(const Team &tm, const SmallLevel<T> &L, const T *g,
 #pragma unroll
             for (int col = 0; col < 6; ++col) {
                 const int j = L.cell_int[3 * cell + col / 2];
-                if (j >= 0) acc += Ac[col * 6] * ld(u + 2 * j + (col & 1));
+                if (j >= 0) acc += Ac[col * 6] * tm.ld(u + 2 * j + (col & 1));
             }
         }
-        r[idx] = ld(g + idx) - acc;
+        r[idx] = tm.ld(g + idx) - acc;
     }
     tm.sync();
 }
 
 // g_c = (I_{l-1}^l)^T r_f  (F = fine level l, C = coarse level l-1)
-template <class T>
-__device__ void blk_restrict(const Team &tm, const SmallLevel<T> &F, const SmallLevel<T> &C, const T *rf, T *gc) {
+template <class T, bool CL>
+__device__ void blk_restrict(const Team<CL> &tm, const SmallLevel<T> &F, const SmallLevel<T> &C, const T *rf, T *gc) {
     for (int P = tm.tid(); P < F.ncc; P += tm.nthreads()) {
         T rT[6];
-        for (int t = 0; t < 6; ++t) rT[t] = ld(rf + 2 * F.tr_slots[9 * P + 6 + t / 2] + (t & 1));
+        for (int t = 0; t < 6; ++t) rT[t] = tm.ld(rf + 2 * F.tr_slots[9 * P + 6 + t / 2] + (t & 1));
         const T *Hk = F.H + (size_t)P * 72;
         for (int c = 0; c < 12; ++c) {
             T acc = 0;
@@ -149,7 +156,7 @@ __device__ void blk_restrict(const Team &tm, const SmallLevel<T> &F, const Small
             const int nb = F.tr_nbr[6 * P + s];
             const int Q = nb >> 4, s2 = nb & 15;
             for (int c = 0; c < 2; ++c)
-                z[2 * s + c] = ld(rf + 2 * i + c) + ld(F.ct1 + 12 * P + 2 * s + c) + ld(F.ct1 + 12 * Q + 2 * s2 + c);
+                z[2 * s + c] = tm.ld(rf + 2 * i + c) + tm.ld(F.ct1 + 12 * P + 2 * s + c) + tm.ld(F.ct1 + 12 * Q + 2 * s2 + c);
         }
         const T *Wk = F.W + (size_t)P * 72;
         for (int col = 0; col < 6; ++col) {
@@ -164,8 +171,8 @@ __device__ void blk_restrict(const Team &tm, const SmallLevel<T> &F, const Small
         for (int q = 0; q < 2; ++q) {
             const int adj = C.facet_adj[2 * G + q];
             const int K = adj >> 2, lf = adj & 3;
-            a0 += ld(F.ct2 + 6 * K + 2 * lf);
-            a1 += ld(F.ct2 + 6 * K + 2 * lf + 1);
+            a0 += tm.ld(F.ct2 + 6 * K + 2 * lf);
+            a1 += tm.ld(F.ct2 + 6 * K + 2 * lf + 1);
         }
         gc[2 * G] = a0;
         gc[2 * G + 1] = a1;
@@ -174,8 +181,8 @@ __device__ void blk_restrict(const Team &tm, const SmallLevel<T> &F, const Small
 }
 
 // u_f += I_{l-1}^l u_c
-template <class T>
-__device__ void blk_prolong_add(const Team &tm, const SmallLevel<T> &F, const SmallLevel<T> &C, const T *uc, T *uf,
+template <class T, bool CL>
+__device__ void blk_prolong_add(const Team<CL> &tm, const SmallLevel<T> &F, const SmallLevel<T> &C, const T *uc, T *uf,
                                 T *tmp) {
     for (int b = tm.tid(); b < F.nB; b += tm.nthreads()) {
         T v0 = 0, v1 = 0;
@@ -187,7 +194,7 @@ __device__ void blk_prolong_add(const Team &tm, const SmallLevel<T> &F, const Sm
                 const int j = C.cell_int[3 * P + fp];
                 if (j < 0) continue;
                 for (int cq = 0; cq < 2; ++cq) {
-                    const T u = ld(uc + 2 * j + cq);
+                    const T u = tm.ld(uc + 2 * j + cq);
                     v0 += Wk[(2 * s) * 6 + 2 * fp + cq] * u;
                     v1 += Wk[(2 * s + 1) * 6 + 2 * fp + cq] * u;
                 }
@@ -196,39 +203,39 @@ __device__ void blk_prolong_add(const Team &tm, const SmallLevel<T> &F, const Sm
         const int i = F.tr_fineB[b];
         tmp[2 * i] = v0;
         tmp[2 * i + 1] = v1;
-        uf[2 * i] = ld(uf + 2 * i) + v0;
-        uf[2 * i + 1] = ld(uf + 2 * i + 1) + v1;
+        uf[2 * i] = tm.ld(uf + 2 * i) + v0;
+        uf[2 * i + 1] = tm.ld(uf + 2 * i + 1) + v1;
     }
     tm.sync();
     for (int P = tm.tid(); P < F.ncc; P += tm.nthreads()) {
         T bb[12];
         for (int s = 0; s < 6; ++s) {
             const int i = F.tr_slots[9 * P + s];
-            bb[2 * s] = i >= 0 ? ld(tmp + 2 * i) : T(0);
-            bb[2 * s + 1] = i >= 0 ? ld(tmp + 2 * i + 1) : T(0);
+            bb[2 * s] = i >= 0 ? tm.ld(tmp + 2 * i) : T(0);
+            bb[2 * s + 1] = i >= 0 ? tm.ld(tmp + 2 * i + 1) : T(0);
         }
         const T *Hk = F.H + (size_t)P * 72;
         for (int t = 0; t < 6; ++t) {
             T acc = 0;
             for (int c = 0; c < 12; ++c) acc += Hk[t * 12 + c] * bb[c];
             T *dst = uf + 2 * F.tr_slots[9 * P + 6 + t / 2] + (t & 1);
-            *dst = ld(dst) + acc;
+            *dst = tm.ld(dst) + acc;
         }
     }
     tm.sync();
 }
 
 // u_0 = inv g_0 in FP64 (one warp per row)
-template <class T>
-__device__ void blk_coarse(const Team &tm, const SmallParams<T> &S) {
+template <class T, bool CL>
+__device__ void blk_coarse(const Team<CL> &tm, const SmallParams<T> &S) {
     const SmallLevel<T> &L0 = S.lv[0];
     const int n = 2 * L0.n_int;
-    for (int i = tm.tid(); i < n; i += tm.nthreads()) S.g0d[i] = (double)ld(L0.g + i);
+    for (int i = tm.tid(); i < n; i += tm.nthreads()) S.g0d[i] = (double)tm.ld(L0.g + i);
     tm.sync();
     const int lane = threadIdx.x & 31, wid = tm.tid() >> 5, nw = tm.nthreads() >> 5;
     for (int row = wid; row < n; row += nw) {
         double acc = 0.0;
-        for (int j = lane; j < n; j += 32) acc += S.inv[(size_t)row * n + j] * ld(S.g0d + j);
+        for (int j = lane; j < n; j += 32) acc += S.inv[(size_t)row * n + j] * tm.ld(S.g0d + j);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         if (lane == 0) L0.u[row] = (T)acc;
     }
@@ -238,8 +245,8 @@ __device__ void blk_coarse(const Team &tm, const SmallParams<T> &S) {
 // MG_h(l_top, g, u, m, q) without recursion: an explicit walk down and up the
 // levels, where visit[l] counts the coarse-grid corrections done at level l (q of
 // them: 1 for the V-cycle, 2 for the W-cycle).  Every thread holds the same state.
-template <class T>
-__device__ void blk_mg(const Team &tm, const SmallParams<T> &S, int top, int m_top, bool zero_top, T *rs) {
+template <class T, bool CL>
+__device__ void blk_mg(const Team<CL> &tm, const SmallParams<T> &S, int top, int m_top, bool zero_top, T *rs) {
     int mlev[SMALL_MAX_LEVELS];
     int visit[SMALL_MAX_LEVELS];
     int l = top;
@@ -286,11 +293,11 @@ __device__ void blk_mg(const Team &tm, const SmallParams<T> &S, int top, int m_t
     }
 }
 
-template <class T>
+template <class T, bool CL>
 __global__ void __launch_bounds__(1024) mg_small_kernel(SmallParams<T> S, int l, int m, int zero_init) {
     extern __shared__ __align__(16) unsigned char smraw[];
     T *rs = reinterpret_cast<T *>(smraw);
-    const Team tm = make_team();
+    const Team<CL> tm = make_team<CL>();
     blk_mg(tm, S, l, m, zero_init != 0, rs);
 }
 
@@ -321,12 +328,15 @@ size_t mg_small_smem(size_t colour_bytes, int csize, int np_max_bytes) {
 // shared memory of that split, or 1 (a single block); 0 if even one block does not fit
 template <class T>
 int mg_small_cluster_size(size_t colour_bytes, int np_max_bytes) {
-    if (cudaFuncSetAttribute(mg_small_kernel<T>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+    // a colour phase that one block covers in a single pass runs on one SM: no L2 round
+    // trips and block barriers only
+    if (colour_bytes / sizeof(T) <= 1024 && mg_small_smem(colour_bytes, 1, np_max_bytes) <= 200 * 1024) return 1;
+    if (cudaFuncSetAttribute(mg_small_kernel<T, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
         cudaGetLastError();
     for (int want : {16, 8, 4, 2}) {
         const size_t smem = mg_small_smem(colour_bytes, want, np_max_bytes);
         if (smem > 200 * 1024) continue;
-        if (cudaFuncSetAttribute(mg_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        if (cudaFuncSetAttribute(mg_small_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
             cudaSuccess) {
             cudaGetLastError();
             continue;
@@ -334,7 +344,7 @@ int mg_small_cluster_size(size_t colour_bytes, int np_max_bytes) {
         cudaLaunchAttribute at;
         cudaLaunchConfig_t cfg = cluster_config(want, smem, nullptr, at);
         int n = 0;
-        if (cudaOccupancyMaxActiveClusters(&n, mg_small_kernel<T>, &cfg) == cudaSuccess && n >= 1) return want;
+        if (cudaOccupancyMaxActiveClusters(&n, mg_small_kernel<T, true>, &cfg) == cudaSuccess && n >= 1) return want;
         cudaGetLastError();
     }
     return mg_small_smem(colour_bytes, 1, np_max_bytes) <= 200 * 1024 ? 1 : 0;
@@ -343,16 +353,19 @@ int mg_small_cluster_size(size_t colour_bytes, int np_max_bytes) {
 template <class T>
 cudaError_t launch_mg_small(const SmallParams<T> &S, int l, int m, bool zero_init, size_t smem, int csize,
                             cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(mg_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
     note_launches(1);
     if (csize <= 1) {
-        mg_small_kernel<T><<<1, 1024, smem, s>>>(S, l, m, zero_init ? 1 : 0);
+        cudaError_t e = cudaFuncSetAttribute(mg_small_kernel<T, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        mg_small_kernel<T, false><<<1, 1024, smem, s>>>(S, l, m, zero_init ? 1 : 0);
         return cudaGetLastError();
     }
+    cudaError_t e = cudaFuncSetAttribute(mg_small_kernel<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     cudaLaunchAttribute at;
     cudaLaunchConfig_t cfg = cluster_config(csize, smem, s, at);
-    return cudaLaunchKernelEx(&cfg, mg_small_kernel<T>, S, l, m, zero_init ? 1 : 0);
+    return cudaLaunchKernelEx(&cfg, mg_small_kernel<T, true>, S, l, m, zero_init ? 1 : 0);
 }
 
 template int mg_small_cluster_size<double>(size_t, int);

@@ -132,6 +132,52 @@ __global__ void gs_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
     }
 }
 
+// Lowest-order sweep (DPF = 2): LANES consecutive lanes of a warp own one patch
+// (row t of the patch on lane t, np <= LANES <= 32), so a 256-thread block works on
+// 256/LANES patches at once instead of one; the block inverse is applied with
+// shuffles inside the lane group, without shared memory.
+template <class T, int LANES>
+__global__ void __launch_bounds__(256)
+gs0_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, const int *__restrict__ patch_nf,
+           const int *__restrict__ patch_facets, const int *__restrict__ patch_cells,
+           const int *__restrict__ slot_src, const int *__restrict__ cell_int, const T *__restrict__ A,
+           const T *__restrict__ Pinv, const T *__restrict__ g, T *__restrict__ u) {
+    const int lane = threadIdx.x & 31, sub = lane / LANES, t = lane % LANES;
+    const int groups_per_block = blockDim.x / LANES;
+    const int p = p0 + blockIdx.x * groups_per_block + (threadIdx.x / 32) * (32 / LANES) + sub;
+    const bool live = p < p1;
+    const int np = live ? 2 * patch_nf[p] : 0;
+    T acc = 0;
+    int F = -1;
+    if (t < np) {
+        const int js = t >> 1, d = t & 1;
+        F = patch_facets[(size_t)p * pf_max + js];
+        acc = g[2 * (size_t)F + d];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
+            const int c = patch_cells[(size_t)p * pc_max + (src >> 2)];
+            const int lf = src & 3;
+            const T *Ac = A + (size_t)c * 36 + 2 * lf + d;
+#pragma unroll
+            for (int f2 = 0; f2 < 3; ++f2) {
+                const int j = cell_int[3 * c + f2];
+                if (j < 0) continue;
+                acc -= Ac[(2 * f2) * 6] * u[2 * (size_t)j] + Ac[(2 * f2 + 1) * 6] * u[2 * (size_t)j + 1];
+            }
+        }
+    }
+    // u_s += A_ss^{-1} r_s: lane t forms row t from the group's residuals (every lane of the
+    // warp runs the same np_max shuffles; width LANES keeps them inside the group)
+    T out = 0;
+    const T *Pi = live ? Pinv + (size_t)p * np_max * np_max : Pinv;
+    for (int j = 0; j < np_max; ++j) {
+        const T rj = __shfl_sync(0xffffffffu, acc, j, LANES);
+        if (j < np && t < np) out += Pi[(size_t)j * np_max + t] * rj;
+    }
+    if (t < np) u[2 * (size_t)F + (t & 1)] += out;
+}
+
 template <class T>
 __global__ void hp_restrict_kernel(int k, int64_t n_int, const T *r, T *r0) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -517,6 +563,22 @@ cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, cons
                       const T *g, T *u, cudaStream_t s) {
     int p0 = L.colour_ptr[colour], p1 = L.colour_ptr[colour + 1];
     if (p1 <= p0) return cudaSuccess;
+    if (DPF == 2 && op.np_max <= 32) {
+        // lowest order: lane groups of 16 (or 32) per patch, 256-thread blocks
+        note_launches(1);
+        const int lanes = op.np_max <= 16 ? 16 : 32;
+        const int per_block = 256 / lanes;
+        const unsigned nb = (unsigned)((p1 - p0 + per_block - 1) / per_block);
+        if (lanes == 16)
+            gs0_kernel<T, 16><<<nb, 256, 0, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
+                                                 L.patch_facets.p, L.patch_cells.p, L.patch_slot_src.p,
+                                                 L.cell_int.p, A, Pinv, g, u);
+        else
+            gs0_kernel<T, 32><<<nb, 256, 0, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
+                                                 L.patch_facets.p, L.patch_cells.p, L.patch_slot_src.p,
+                                                 L.cell_int.p, A, Pinv, g, u);
+        return cudaGetLastError();
+    }
     int nt = ((op.np_max + 31) / 32) * 32;
     if (nt > 256) nt = 256;
     if (nt < 32) nt = 32;

@@ -158,7 +158,8 @@ def test_solve_matches_oracle(k, gamma, mesh):
     u, p, info = hdg.hdg_solve(ctx, F)
     assert info["krylov_its"] == ro.krylov_its
     assert rel(host(u), ro.u) < 1e-10
-    assert rel(host(p), ro.p) < 1e-9
+    # the pressure update multiplies rounding-order differences of div u by eps^-1 = gamma nu
+    assert rel(host(p), ro.p) < (1e-9 if gamma <= 1e2 else 1e-8)
     ud, pd = oh.solve_direct(Fo)
     assert np.linalg.norm(host(u) - ud) < 1e-8 * np.linalg.norm(ud)
     assert np.linalg.norm(host(p) - pd) < 1e-6 * np.linalg.norm(pd)
