@@ -1403,8 +1403,8 @@ hdg_status hdg_get_element_matrices(hdg_ctx *ctx, int level, double *out, hdg_st
         REQUIRE(out, "null output");
         const DevOperator &op = level < 0 ? ctx->opk : ctx->L[level].op0;
         const int64_t nc = ctx->L[level < 0 ? ctx->n_levels - 1 : level].nc;
-        // the library keeps each A_K transposed; hand out the row-major A_K[p][q]
-        CK(launch_transpose_blocks(nc, op.nloc, op.A.p, out, (cudaStream_t)stream));
+        // the library keeps each A_K by row blocks; hand out the row-major A_K[p][q]
+        CK(launch_unpack_blocks(nc, op.nloc, op.dpf, op.A.p, out, (cudaStream_t)stream));
     });
 }
 

@@ -28,8 +28,10 @@
 // form in its convecting argument, with the switch frozen at u_old·n_K, and
 // the load C_h(u_old; u_old, v) on the (u, û) rows (newton_x = the previous
 // skeleton iterate, conv = u_old at the lattice).
-// Element matrices are stored transposed, A_K[q][p] = (A_K)_pq, so that the
-// row-gathering kernels read consecutive addresses.  Facet unknowns are expressed in the
+// Element matrices are stored by row blocks: the DPF rows of local facet f form
+// one contiguous block [f][column][row within the facet], so that a facet's rows
+// (what the apply and the smoothers read) are one contiguous DPF·n_loc stretch
+// and the DPF threads of a facet read consecutive addresses.  Facet unknowns are expressed in the
 // global facet basis of include/hdg.h: the reference facet moments map to
 // the global ones by the factor sqrt|F|·σ·sgn(det J)·o^m (σ = n_F·n_K,
 // o = ±1 the orientation of the facet parameter).
@@ -674,7 +676,10 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
         const double *Wl = conv ? W2 : Wm;     // [j][p]: Wᵀ (symmetric K) or W2
         if (Aout)
         for (int idx = tid; idx < D::NG * D::NG; idx += nt) {
-            int q = idx / D::NG, p = idx % D::NG;    // stored transposed: A[q][p] = A_pq
+            // stored by row blocks: idx = (lf * NG + q) * DPF + d for row p = lf * DPF + d
+            constexpr int DPF = 2 * D::NF;
+            const int lfp = idx / (D::NG * DPF), rem = idx - lfp * D::NG * DPF;
+            const int q = rem / DPF, p = lfp * DPF + (rem - (rem / DPF) * DPF);
             int gp = gcol(p), gq = gcol(q);
             double s = Km[gp * D::NCOL + gq];
             for (int r = 0; r < D::NRI; ++r) s -= Km[gp * D::NCOL + 3 * D::NF + r] * Y[r * D::NY + q];
@@ -763,7 +768,7 @@ __global__ void patch_inverse_kernel(int n_patches, int pf_max, int pc_max, int 
             int l1 = lfmap[si * pf_max + j1], l2 = lfmap[si * pf_max + j2];
             if (l1 < 0 || l2 < 0) continue;
             int c = patch_cells[(size_t)p * pc_max + si];
-            s += A[(size_t)c * nloc * nloc + (l2 * dpf + d2) * nloc + l1 * dpf + d1];
+            s += A[(size_t)c * nloc * nloc + l1 * nloc * dpf + (l2 * dpf + d2) * dpf + d1];
         }
         M[P * np + Q] = s;
     }
@@ -856,7 +861,7 @@ __global__ void transfer_H_kernel(int64_t ncc, const int *__restrict__ children,
             for (int l2 = 0; l2 < 3; ++l2) {
                 int s2 = child_slot[12 * P + 3 * ch + l2];
                 for (int a = 0; a < 2; ++a)
-                    for (int b = 0; b < 2; ++b) M[2 * s1 + a][2 * s2 + b] += Ac[(2 * l2 + b) * 6 + 2 * l1 + a];
+                    for (int b = 0; b < 2; ++b) M[2 * s1 + a][2 * s2 + b] += Ac[l1 * 12 + (2 * l2 + b) * 2 + a];
             }
         }
     }
@@ -915,7 +920,7 @@ __global__ void coarse_assemble_kernel(int64_t n_int, const int *__restrict__ fa
         for (int col = 0; col < 6; ++col) {
             int jf = cell_int[3 * c + col / 2];
             if (jf < 0) continue;
-            Mr[2 * jf + col % 2] += A0[(size_t)c * 36 + col * 6 + 2 * lf + d];
+            Mr[2 * jf + col % 2] += A0[(size_t)c * 36 + lf * 12 + col * 2 + d];
         }
     }
 }
@@ -1055,14 +1060,16 @@ __global__ void rt0_vertex_kernel(int64_t nc, const double *__restrict__ coords,
         }
 }
 
-// out[b][i][j] = in[b][j][i] for nblk square blocks of size n
-__global__ void transpose_blocks_kernel(int64_t nblk, int n, const double *__restrict__ in, double *__restrict__ out) {
+// row-major copies of the stored element matrices: out[b][p][q] = A_pq, stored at
+// in[b][(p / dpf) * n * dpf + q * dpf + p % dpf]
+__global__ void unpack_blocks_kernel(int64_t nblk, int n, int dpf, const double *__restrict__ in,
+                                     double *__restrict__ out) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nn = (int64_t)n * n;
     if (idx >= nblk * nn) return;
     const int64_t b = idx / nn;
-    const int r = (int)(idx - b * nn), i = r / n, j = r % n;
-    out[idx] = in[b * nn + (int64_t)j * n + i];
+    const int r = (int)(idx - b * nn), p = r / n, q = r % n;
+    out[idx] = in[b * nn + (int64_t)(p / dpf) * n * dpf + (int64_t)q * dpf + p % dpf];
 }
 
 // coarse-cell viscosity = mean over its four children (equal areas under red refinement)
@@ -1277,11 +1284,11 @@ cudaError_t launch_rt0_vertex(const DevLevel &L, const double *flux, double *out
     return cudaGetLastError();
 }
 
-cudaError_t launch_transpose_blocks(int64_t nblk, int n, const double *in, double *out, cudaStream_t s) {
+cudaError_t launch_unpack_blocks(int64_t nblk, int n, int dpf, const double *in, double *out, cudaStream_t s) {
     const int64_t total = nblk * (int64_t)n * n;
     if (total == 0) return cudaSuccess;
     note_launches(1);
-    transpose_blocks_kernel<<<blocks_for(total, 256), 256, 0, s>>>(nblk, n, in, out);
+    unpack_blocks_kernel<<<blocks_for(total, 256), 256, 0, s>>>(nblk, n, dpf, in, out);
     return cudaGetLastError();
 }
 

@@ -262,7 +262,7 @@ cudaError_t launch_conv_flux(const DevLevel &L, const double *ref, const RefTabl
                              double *flux, cudaStream_t s);
 cudaError_t launch_flux_restrict(const DevLevel &fine, const double *ff, double *fc, cudaStream_t s);
 cudaError_t launch_rt0_vertex(const DevLevel &L, const double *flux, double *out, cudaStream_t s);
-cudaError_t launch_transpose_blocks(int64_t nblk, int n, const double *in, double *out, cudaStream_t s);
+cudaError_t launch_unpack_blocks(int64_t nblk, int n, int dpf, const double *in, double *out, cudaStream_t s);
 // pivot: partial pivoting (non-symmetric patch matrices); without it SPD pivots are checked positive
 cudaError_t launch_patch_inverse(const DevLevel &L, const DevOperator &op, int pivot, int *flag, cudaStream_t s);
 cudaError_t launch_transfer_H(const DevLevel &fine, int *flag, cudaStream_t s);

@@ -84,11 +84,11 @@ __device__ void blk_gs_colour(const Team<CL> &tm, const SmallLevel<T> &L, int c,
             const int src = L.slot_src[(p * L.pf_max + js) * 2 + q];
             const int si = src >> 2, lf = src & 3;
             const int cell = L.patch_cells[p * L.pc_max + si];
-            const T *Ac = L.A + (size_t)cell * 36 + 2 * lf + d;
+            const T *Ac = L.A + (size_t)cell * 36 + lf * 12 + d;
 #pragma unroll
             for (int col = 0; col < 6; ++col) {
                 const int j = L.cell_int[3 * cell + col / 2];
-                if (j >= 0) acc -= Ac[col * 6] * tm.ld(u + 2 * j + (col & 1));
+                if (j >= 0) acc -= Ac[col * 2] * tm.ld(u + 2 * j + (col & 1));
             }
         }
         rs[w] = acc;
@@ -122,11 +122,11 @@ __device__ void blk_residual(const Team<CL> &tm, const SmallLevel<T> &L, const T
             const int adj = L.facet_adj[2 * i + q];
             if (adj < 0) continue;
             const int cell = adj >> 2, lf = adj & 3;
-            const T *Ac = L.A + (size_t)cell * 36 + 2 * lf + d;
+            const T *Ac = L.A + (size_t)cell * 36 + lf * 12 + d;
 #pragma unroll
             for (int col = 0; col < 6; ++col) {
                 const int j = L.cell_int[3 * cell + col / 2];
-                if (j >= 0) acc += Ac[col * 6] * tm.ld(u + 2 * j + (col & 1));
+                if (j >= 0) acc += Ac[col * 2] * tm.ld(u + 2 * j + (col & 1));
             }
         }
         r[idx] = tm.ld(g + idx) - acc;

@@ -48,7 +48,7 @@ apply_m_kernel(int64_t n_int, int lgR, const int *__restrict__ facet_adj, const 
         const int adj = facet_adj[2 * i + q];
         if (adj < 0) continue;
         const int c = adj >> 2, lf = adj & 3;
-        const T *Ac = A + (size_t)c * NLOC * NLOC + lf * DPF + d0;
+        const T *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d0;
 #pragma unroll
         for (int f2 = 0; f2 < 3; ++f2) {
             const int j = cell_int[3 * c + f2];
@@ -57,7 +57,7 @@ apply_m_kernel(int64_t n_int, int lgR, const int *__restrict__ facet_adj, const 
 #pragma unroll
             for (int d2 = 0; d2 < DPF; ++d2) {
                 const T xv = xs[(size_t)d2 << lgR];
-                const T *a = Ac + (f2 * DPF + d2) * NLOC;
+                const T *a = Ac + (f2 * DPF + d2) * DPF;
 #pragma unroll
                 for (int b = 0; b < RB; ++b) acc[b] += a[b] * xv;
             }
@@ -105,7 +105,7 @@ apply_df_m_kernel(int64_t n_int, int lgR, const int *__restrict__ facet_adj, con
         const int adj = facet_adj[2 * i + q];
         if (adj < 0) continue;
         const int c = adj >> 2, lf = adj & 3;
-        const size_t base = (size_t)c * NLOC * NLOC + lf * DPF + d0;
+        const size_t base = (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d0;
 #pragma unroll
         for (int f2 = 0; f2 < 3; ++f2) {
             const int j = cell_int[3 * c + f2];
@@ -114,7 +114,7 @@ apply_df_m_kernel(int64_t n_int, int lgR, const int *__restrict__ facet_adj, con
 #pragma unroll
             for (int d2 = 0; d2 < DPF; ++d2) {
                 const float2 xv = xs[(size_t)d2 << lgR];      // (hi, lo) of x
-                const size_t o = base + (size_t)(f2 * DPF + d2) * NLOC;
+                const size_t o = base + (size_t)(f2 * DPF + d2) * DPF;
 #pragma unroll
                 for (int b = 0; b < RB; ++b) {
                     const float ah = Ahi[o + b], al = Alo[o + b];
@@ -201,7 +201,7 @@ gs_m_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const i
             const int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
             const int si = src >> 2, lf = src & 3;
             const int c = patch_cells[(size_t)p * pc_max + si];
-            rowA[2 * js + q] = c * NLOC * NLOC + lf * DPF;
+            rowA[2 * js + q] = c * NLOC * NLOC + lf * NLOC * DPF;
             rowS[2 * js + q] = si;
         }
     }
@@ -219,7 +219,7 @@ gs_m_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const i
 #pragma unroll 4
         for (int i = tid; i < n2; i += nt) {
             const int h = i % U, col = (i / U) % NLOC, jq = i / (U * NLOC);
-            const T2 *src = reinterpret_cast<const T2 *>(A + rowA[jq] + col * NLOC) + h;
+            const T2 *src = reinterpret_cast<const T2 *>(A + rowA[jq] + col * DPF) + h;
             reinterpret_cast<T2 *>(As)[i] = *src;
         }
     }

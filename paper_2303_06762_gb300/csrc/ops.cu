@@ -63,14 +63,14 @@ apply_kernel(int64_t n_int, const int *__restrict__ facet_adj, const int *__rest
         int adj = facet_adj[2 * i + q];
         if (adj < 0) continue;
         int c = adj >> 2, lf = adj & 3;
-        const T *Ac = A + (size_t)c * NLOC * NLOC + lf * DPF + d;
+        const T *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d;
 #pragma unroll
         for (int f2 = 0; f2 < 3; ++f2) {
             int j = cell_int[3 * c + f2];
             if (j < 0) continue;
             const T *xs = x + (size_t)j * DPF;
 #pragma unroll
-            for (int d2 = 0; d2 < DPF; ++d2) acc += Ac[(f2 * DPF + d2) * NLOC] * xs[d2];
+            for (int d2 = 0; d2 < DPF; ++d2) acc += Ac[(f2 * DPF + d2) * DPF] * xs[d2];
         }
     }
     y[idx] = g ? g[idx] - acc : acc;
@@ -106,10 +106,10 @@ __global__ void gs_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
             int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
             int si = src >> 2, lf = src & 3;
             int c = patch_cells[(size_t)p * pc_max + si];
-            const T *Ac = A + (size_t)c * NLOC * NLOC + lf * DPF + d;
+            const T *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d;
             const T *xc = xs + si * NLOC;
 #pragma unroll
-            for (int col = 0; col < NLOC; ++col) acc -= Ac[col * NLOC] * xc[col];
+            for (int col = 0; col < NLOC; ++col) acc -= Ac[col * DPF] * xc[col];
         }
         r[t] = acc;
     }
@@ -158,12 +158,12 @@ gs0_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, const int *__rest
             const int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
             const int c = patch_cells[(size_t)p * pc_max + (src >> 2)];
             const int lf = src & 3;
-            const T *Ac = A + (size_t)c * 36 + 2 * lf + d;
+            const T *Ac = A + (size_t)c * 36 + lf * 12 + d;
 #pragma unroll
             for (int f2 = 0; f2 < 3; ++f2) {
                 const int j = cell_int[3 * c + f2];
                 if (j < 0) continue;
-                acc -= Ac[(2 * f2) * 6] * u[2 * (size_t)j] + Ac[(2 * f2 + 1) * 6] * u[2 * (size_t)j + 1];
+                acc -= Ac[(2 * f2) * 2] * u[2 * (size_t)j] + Ac[(2 * f2 + 1) * 2] * u[2 * (size_t)j + 1];
             }
         }
     }
