@@ -561,10 +561,10 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes):
     peak = peaks.get("hbm_gbs", 6800.0)
     # DRAM bytes of one sweep from an ncu capture of the same kernel (dram__bytes_read.sum +
     # dram__bytes_write.sum over its three colour launches) on the 128x128, k = 3 case:
-    # 396,034,304 B against 318,199,104 algorithmic bytes there.  Traffic grows with the
+    # 317,834,240 B against 318,199,104 algorithmic bytes there.  Traffic grows with the
     # number of patches like the algorithmic bytes, so the full-size figure is that ratio
     # times the full-size algorithmic bytes (k = 3 only; other k were not captured).
-    traffic = alg * (396034304 / 318199104) if k == 3 else None
+    traffic = alg * (317834240 / 318199104) if k == 3 else None
     return {"kernel": "gs_kernel<float> (order-k block GS sweep, 3 colour launches)",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
