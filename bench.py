@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--profile-solve", action="store_true",
                     help="condense, then one warm-up and one timed mixed-precision solve only "
                          "(the command profiled for the kernel launch list)")
+    ap.add_argument("--precision", type=int, default=1,
+                    help="preconditioner precision of --profile-solve (hdg_precision value)")
     return ap.parse_args()
 
 
@@ -149,13 +151,15 @@ def ctx_mesh_fine(args):
     return _FINE["mesh"]
 
 
-def sweep_bytes(mesh, k, word):
+def sweep_bytes(mesh, k, word, mat_word=None):
     """Algorithmic bytes of one order-k block-GS sweep (all colours) on `mesh`.
 
     Per vertex patch with nf interior facets (np = nf dpf unknowns) and nc cells:
     residual rows read 2 cells x dpf rows x n_loc columns per facet, the gathered
     cell unknowns nc x n_loc, the patch inverse np^2, the right-hand side np and
-    the update np (read + write)."""
+    the update np (read + write).  Vectors take `word` bytes per value, matrix
+    entries `mat_word` (default `word`); 16-bit matrices add one 4-byte scale per
+    row read (2 x dpf per facet and np per patch inverse)."""
     import numpy as np
     dpf = 2 * (k + 1)
     nloc = 3 * dpf
@@ -169,8 +173,11 @@ def sweep_bytes(mesh, k, word):
     ncell = np.bincount(c.ravel(), minlength=nv)
     m = nf > 0
     npp = nf[m] * dpf
-    total = (nf[m] * 2 * dpf * nloc + ncell[m] * nloc + npp * npp + 3 * npp).sum()
-    return int(total) * word
+    mw = word if mat_word is None else mat_word
+    mat = (nf[m] * 2 * dpf * nloc + npp * npp).sum() * mw
+    vec = (ncell[m] * nloc + 3 * npp).sum() * word
+    scales = (nf[m] * 2 * dpf + npp).sum() * 4 if mw != word else 0
+    return int(mat + vec + scales)
 
 
 def measured_peaks():
@@ -294,7 +301,8 @@ def gpu_arm(args):
     stream = torch.cuda.current_stream(dev)
     results = {}
     sizes = None
-    for name, prec in (("fp64", hdg.HDG_FP64), ("mixed_fp32", hdg.HDG_MIXED_FP32)):
+    for name, prec in (("fp64", hdg.HDG_FP64), ("mixed_fp32", hdg.HDG_MIXED_FP32),
+                       ("mixed_fp16", hdg.HDG_MIXED_FP16), ("mixed_bf16", hdg.HDG_MIXED_BF16)):
         prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma, precision=prec)
         F = hdg.hdg_condense(ctx, prm, forcing)
         sizes = ctx.sizes()
@@ -382,6 +390,8 @@ def gpu_arm(args):
 
     # ---------------------------------------------------------------- roofline of the dominant kernel
     line["roofline"] = roofline(args, ctx, hdg, torch, dev, stream, sizes)
+    line["roofline_fp16_sweep"] = roofline(args, ctx, hdg, torch, dev, stream, sizes,
+                                           precision=hdg.HDG_MIXED_FP16)
     ctx.close()
     if not args.no_extra_forms:
         line["forms"]["batched_mixed_fp32"] = batched_form(args, hdg, torch, dev, stream, world)
@@ -521,9 +531,10 @@ def oseen_form(args, hdg, torch, dev, stream):
     return out
 
 
-def roofline(args, ctx, hdg, torch, dev, stream, sizes):
+def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
     """Order-k block Gauss-Seidel sweep in FP32 (the mixed form's dominant kernel),
-    timed with CUDA events on the launching stream over 20 sweeps.
+    timed with CUDA events on the launching stream over 20 sweeps; with
+    precision = HDG_MIXED_FP16 the same sweep on the binary16 matrix copies.
 
     Algorithmic bytes per sweep (one launch per colour, 3 colours): every cell's
     condensed matrix is read for the two facets at the patch vertex in each of the
@@ -534,7 +545,9 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes):
     k = args.k
     nloc = 6 * (k + 1)
     dpf = 2 * (k + 1)
-    prm = hdg.Params(k=k, nu=args.nu, beta=args.beta, gamma=args.gamma, precision=hdg.HDG_MIXED_FP32)
+    half = precision == hdg.HDG_MIXED_FP16
+    prm = hdg.Params(k=k, nu=args.nu, beta=args.beta, gamma=args.gamma,
+                     precision=hdg.HDG_MIXED_FP32 if precision is None else precision)
     hdg.hdg_condense(ctx, prm, None)
     g = torch.randn(sizes.n_dof, dtype=torch.float64, device=dev)
     u = torch.zeros_like(g)
@@ -556,7 +569,7 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes):
     ev3.record(stream)
     torch.cuda.synchronize()
     t_sweep = (ev0.elapsed_time(ev1) - ev2.elapsed_time(ev3)) / 1e3 / n_sweeps
-    alg = sweep_bytes(ctx_mesh_fine(args), k, 4)
+    alg = sweep_bytes(ctx_mesh_fine(args), k, 4, 2 if half else 4)
     achieved = alg / t_sweep / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     # DRAM bytes of one sweep from an ncu capture of the same kernel (dram__bytes_read.sum +
@@ -564,8 +577,10 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes):
     # 317,834,240 B against 318,199,104 algorithmic bytes there.  Traffic grows with the
     # number of patches like the algorithmic bytes, so the full-size figure is that ratio
     # times the full-size algorithmic bytes (k = 3 only; other k were not captured).
-    traffic = alg * (317834240 / 318199104) if k == 3 else None
-    return {"kernel": "gs_kernel<float> (order-k block GS sweep, 3 colour launches)",
+    traffic = alg * (317834240 / 318199104) if k == 3 and not half else None
+    kname = "gs_kernel<float, 8, __half> (order-k block GS sweep on binary16 copies" if half else \
+        "gs_kernel<float> (order-k block GS sweep"
+    return {"kernel": kname + ", 3 colour launches)",
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
             "traffic_note": "scaled from an ncu capture at 128x128 (same kernel, cold caches)" if traffic else None,
@@ -578,8 +593,7 @@ def profile_solve(args):
     import paper_2303_06762_gb300 as hdg
     ms, fv = workload(args)
     ctx = hdg.hdg_setup_mesh_hierarchy(ms)
-    prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma,
-                     precision=hdg.HDG_MIXED_FP32)
+    prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma, precision=args.precision)
     F = hdg.hdg_condense(ctx, prm, torch.tensor(fv, device="cuda:0"))
     for _ in range(max(args.warmup, 0) + 1):
         u, p, info = hdg.hdg_solve(ctx, F)
