@@ -78,8 +78,15 @@ typedef enum {
 
 typedef enum {
     HDG_FP64 = 0,        /* preconditioner in FP64                                 */
-    HDG_MIXED_FP32 = 1   /* preconditioner (smoothers, transfers, V-cycle) in FP32; */
+    HDG_MIXED_FP32 = 1,  /* preconditioner (smoothers, transfers, V-cycle) in FP32; */
                          /* outer operator, Krylov, coarse solve stay FP64          */
+    HDG_MIXED_BF16 = 2,  /* as HDG_MIXED_FP32, but the order-k element matrices and */
+                         /* patch inverses read by the order-k smoother and its     */
+                         /* residual are stored in bfloat16, each row scaled by its */
+                         /* own power of two (largest entry in [1/2, 1)); products  */
+                         /* accumulate in FP32.  Single-load calls only: batched    */
+                         /* (_multi) calls read the FP32 copies                     */
+    HDG_MIXED_FP16 = 3   /* the same with IEEE binary16 storage                     */
 } hdg_precision;
 
 typedef struct {

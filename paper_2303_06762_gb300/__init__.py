@@ -28,6 +28,8 @@ from .build import LIB, build as _build
 
 HDG_FP64 = 0
 HDG_MIXED_FP32 = 1
+HDG_MIXED_BF16 = 2
+HDG_MIXED_FP16 = 3
 
 _STATUS = {0: "HDG_OK", 1: "HDG_ERR_INVALID_ARG", 2: "HDG_ERR_OOM", 3: "HDG_ERR_CUDA",
            4: "HDG_ERR_SINGULAR", 5: "HDG_ERR_NOT_CONVERGED", 6: "HDG_ERR_BREAKDOWN",

@@ -13,6 +13,7 @@
 #include <cstring>
 #include <string>
 #include <thread>
+#include <type_traits>
 #include <vector>
 
 #include "hdg_internal.h"
@@ -73,6 +74,11 @@ void free_operator(DevOperator &op) {
     dfree(op.Fel);
     dfree(op.Pinv);
     dfree(op.Pinvf);
+    dfree(op.Ah);
+    dfree(op.Ah_s);
+    dfree(op.Pinvh);
+    dfree(op.Pinvh_s);
+    op.h_fmt = 0;
 }
 
 void free_level(DevLevel &L) {
@@ -153,13 +159,33 @@ struct Prec<float> {
     static const float *H(const DevLevel &L) { return L.tr_Hf.p; }
 };
 
+// one sweep of block GS; FP32 sweeps of an operator with 16-bit copies read those
 template <class T>
 void sweep(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, const T *g, T *u, bool reverse,
            cudaStream_t s) {
     for (int i = 0; i < L.n_colours; ++i) {
         int c = reverse ? L.n_colours - 1 - i : i;
+        if constexpr (std::is_same<T, float>::value) {
+            if (op.h_fmt) {
+                CK(launch_gs_colour_h(L, op, c, g, u, s));
+                continue;
+            }
+        }
         CK(launch_gs_colour<T>(L, op, Prec<T>::A(op), Prec<T>::P(op), c, g, u, s));
     }
+}
+
+// y = A x (or g - A x) in the preconditioner's precision, likewise on the 16-bit copies
+template <class T>
+void apply_op(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, const T *x, const T *g, T *y,
+              cudaStream_t s) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (op.h_fmt) {
+            CK(launch_apply_h(L, op, x, g, y, s));
+            return;
+        }
+    }
+    CK(launch_apply<T>(L, op, Prec<T>::A(op), x, g, y, s));
 }
 
 template <class T>
@@ -230,6 +256,16 @@ size_t fill_small(hdg_ctx *ctx, int Ls) {
     return std::max<size_t>(smem, 16);
 }
 
+template <class T>
+void make_resident(SmallParams<T> &S, int Ls, size_t &smem) {
+    const size_t off = (smem + 15) & ~size_t(15);
+    const size_t vb = mg_small_vec_bytes(S, Ls);
+    if (off + vb > 200 * 1024) return;
+    S.resident = 1;
+    S.vec_offset = off;
+    smem = off + vb;
+}
+
 // largest level Ls >= 1 whose levels 0..Ls all fit the single-block kernel, else -1
 int small_levels(hdg_ctx *ctx) {
     int Ls = -1;
@@ -289,7 +325,7 @@ void mg_hp_impl(hdg_ctx *ctx, const T *r, T *z, cudaStream_t s) {
     T *res = std::is_same<T, double>::value ? (T *)ctx->kr.p : (T *)ctx->krf.p;
     CK(launch_fill<T>(z, T(0), ctx->n_dof, s));
     for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, false, s);
-    CK(launch_apply<T>(LJ, op, Prec<T>::A(op), z, r, res, s));
+    apply_op<T>(ctx, LJ, op, z, r, res, s);
     CK(launch_hp_restrict<T>(k, LJ.n_int, res, Prec<T>::g(LJ), s));
     mg_h<T>(ctx, J, ctx->prm.m_h, true, s);
     CK(launch_hp_prolong_add<T>(k, LJ.n_int, Prec<T>::u(LJ), z, s));
@@ -774,7 +810,7 @@ FgmresOutM fgmres_m(hdg_ctx *ctx, const double *b, double *x, double rtol, const
     std::vector<int> m_r(R);
     std::vector<char> done(R);
     // outer operator: FP64, or double-FP32 with the mixed preconditioner
-    const bool df = ctx->prm.precision == HDG_MIXED_FP32;
+    const bool df = ctx->prm.precision != HDG_FP64;
     if (df && !ctx->opk.alo_valid) {
         const size_t na = (size_t)ctx->opk.nloc * ctx->opk.nloc * LJ.nc;
         dalloc(ctx, ctx->opk.Alo, na);
@@ -1189,6 +1225,15 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
                        prm->beta, prm->gamma, forcing, conv_of(ctx), ctx->conv_t, newton_of(ctx), op.A.p, op.Af.p,
                        op.Fel.p, ctx->status_flag.p, RecoverArgs(), s));
     CK(launch_patch_inverse(LJ, op, ctx->has_conv ? 1 : 0, ctx->status_flag.p, s));
+    op.h_fmt = 0;
+    if (k >= 1 && (prm->precision == HDG_MIXED_BF16 || prm->precision == HDG_MIXED_FP16)) {
+        dalloc(ctx, op.Ah, (size_t)op.nloc * op.nloc * LJ.nc);
+        dalloc(ctx, op.Ah_s, (size_t)op.nloc * LJ.nc);
+        dalloc(ctx, op.Pinvh, (size_t)LJ.n_patches * op.np_max * op.np_max);
+        dalloc(ctx, op.Pinvh_s, (size_t)LJ.n_patches * op.np_max);
+        CK(launch_round16(LJ, op, (int)prm->precision, s));
+        op.h_fmt = (int)prm->precision;
+    }
     for (int l = 1; l < nl; ++l) CK(launch_transfer_H(ctx->L[l], ctx->status_flag.p, s));
     ctx->n0 = 2 * ctx->L[0].n_int;
     dalloc(ctx, ctx->coarse_inv, std::max<int64_t>(ctx->n0 * ctx->n0, 1));
@@ -1203,6 +1248,9 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
         ctx->small_cs_f = mg_small_cluster_size<float>(cb_f, npm * (int)sizeof(float));
         ctx->small_smem_d = mg_small_smem(cb_d, std::max(ctx->small_cs_d, 1), npm * (int)sizeof(double));
         ctx->small_smem_f = mg_small_smem(cb_f, std::max(ctx->small_cs_f, 1), npm * (int)sizeof(float));
+        // a single block keeps all level vectors in its shared memory when they fit
+        if (ctx->small_cs_d == 1) make_resident(ctx->small_d, ctx->small_Ls, ctx->small_smem_d);
+        if (ctx->small_cs_f == 1) make_resident(ctx->small_f, ctx->small_Ls, ctx->small_smem_f);
         if (ctx->small_cs_d == 0 || ctx->small_cs_f == 0) ctx->small_Ls = -1;
     }
     ctx->n_dof = LJ.n_int * op.dpf;
@@ -1225,7 +1273,8 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
         REQUIRE(prm->m_p >= 1 && prm->m_h >= 1, "m_p, m_h must be >= 1");
         REQUIRE(prm->cycle == 1 || prm->cycle == 2, "cycle must be 1 (V) or 2 (W)");
         REQUIRE(prm->vcycle_growth >= 1 && prm->vcycle_growth <= 4, "vcycle_growth out of range 1..4");
-        REQUIRE(prm->precision == HDG_FP64 || prm->precision == HDG_MIXED_FP32, "unknown precision");
+        REQUIRE(prm->precision == HDG_FP64 || prm->precision == HDG_MIXED_FP32 ||
+                    prm->precision == HDG_MIXED_BF16 || prm->precision == HDG_MIXED_FP16, "unknown precision");
         REQUIRE(prm->fused_coarse_cells >= 0, "fused_coarse_cells must be >= 0");
         REQUIRE(2 * ctx->L[0].n_int <= MAX_COARSE_DOFS,
                 "coarsest level has " + std::to_string(2 * ctx->L[0].n_int) +

@@ -805,19 +805,24 @@ __global__ void patch_inverse_kernel(int n_patches, int pf_max, int pc_max, int 
         __syncthreads();
         double d = M[piv * np + piv];
         if (!(fabs(d) > 1e-300) || !isfinite(d)) d = 1.0;
+        // one reciprocal per pivot (FP64 division is a long instruction sequence; the
+        // update below is then one FMA per entry)
+        const double dinv = 1.0 / d;
         for (int i = tid; i < np; i += nt) {
             colp[i] = M[i * np + piv];
-            rowp[i] = M[piv * np + i];
+            rowp[i] = M[piv * np + i] * dinv;
         }
         __syncthreads();
-        for (int idx = tid; idx < np * np; idx += nt) {
-            int i = idx / np, j = idx % np;
-            double v;
-            if (i == piv && j == piv) v = 1.0 / d;
-            else if (i == piv) v = rowp[j] / d;
-            else if (j == piv) v = -colp[i] / d;
-            else v = M[idx] - colp[i] * rowp[j] / d;
-            M[idx] = v;
+        // warp w updates rows w, w + nwarps, ...; its lanes walk the columns
+        for (int i = tid >> 5; i < np; i += nt >> 5) {
+            const double ci = colp[i];
+            for (int j = tid & 31; j < np; j += 32) {
+                double v;
+                if (i == piv) v = (j == piv) ? dinv : rowp[j];
+                else if (j == piv) v = -ci * dinv;
+                else v = fma(-ci, rowp[j], M[i * np + j]);
+                M[i * np + j] = v;
+            }
         }
     }
     __syncthreads();

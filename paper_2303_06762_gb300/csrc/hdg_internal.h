@@ -112,6 +112,10 @@ struct SmallParams {
     const double *inv = nullptr;   // dense inverse of the coarsest operator (FP64)
     double *g0d = nullptr;         // FP64 staging of the coarsest right-hand side
     int q = 1, growth = 2;
+    // single-block launch only: keep every level vector (g, u, r, t, transfer temporaries,
+    // the FP64 coarse right-hand side) in shared memory from byte vec_offset on
+    int resident = 0;
+    size_t vec_offset = 0;
 };
 
 // outputs of the recovery mode of the condensation kernel (all device, nullable)
@@ -140,6 +144,13 @@ struct DevOperator {
     DBuf<double> Fel;    // nc*nloc element loads
     DBuf<double> Pinv;   // n_patches*np_max*np_max
     DBuf<float> Pinvf;
+    // 16-bit copies for HDG_MIXED_BF16 / HDG_MIXED_FP16 (order-k operator only): the
+    // layouts of A and Pinv with every stored row divided by its power-of-two scale
+    int h_fmt = 0;       // hdg_precision of Ah / Pinvh, 0 = none
+    DBuf<uint16_t> Ah;   // nc*nloc*nloc
+    DBuf<float> Ah_s;    // nc*nloc, scale of row p of cell c at c*nloc + p
+    DBuf<uint16_t> Pinvh;
+    DBuf<float> Pinvh_s; // n_patches*np_max, scale of row i of the inverse of patch p at p*np_max + i
 };
 
 struct DevLevel {
@@ -284,6 +295,13 @@ cudaError_t launch_apply(const DevLevel &L, const DevOperator &op, const T *A, c
 template <class T>
 cudaError_t launch_gs_colour(const DevLevel &L, const DevOperator &op, const T *A, const T *Pinv,
                              int colour, const T *g, T *u, cudaStream_t s);
+// the order-k apply and sweep phase on the 16-bit copies (op.h_fmt), FP32 vectors
+cudaError_t launch_apply_h(const DevLevel &L, const DevOperator &op, const float *x, const float *g, float *y,
+                           cudaStream_t s);
+cudaError_t launch_gs_colour_h(const DevLevel &L, const DevOperator &op, int colour, const float *g, float *u,
+                               cudaStream_t s);
+// fills op.Ah, Ah_s, Pinvh, Pinvh_s (allocated by the caller) from op.A and op.Pinv
+cudaError_t launch_round16(const DevLevel &L, DevOperator &op, int fmt, cudaStream_t s);
 template <class T>
 cudaError_t launch_prolong_add(const DevLevel &fine, const DevLevel &coarse, const T *W,
                                const T *Hm, const T *uc, T *tmp, T *uf, cudaStream_t s);
@@ -301,6 +319,8 @@ cudaError_t launch_mg_small(const SmallParams<T> &S, int l, int m, bool zero_ini
                             int cluster_size, cudaStream_t s);
 // per-CTA shared memory and cluster size (16/8/4/2 CTAs, 1 = one block, 0 = does not fit)
 size_t mg_small_smem(size_t colour_bytes, int csize, int np_max_bytes);
+template <class T>
+size_t mg_small_vec_bytes(const SmallParams<T> &S, int Ls);
 template <class T>
 int mg_small_cluster_size(size_t colour_bytes, int np_max_bytes);
 cudaError_t launch_d2f(const double *x, float *y, int64_t n, cudaStream_t s);

@@ -134,9 +134,10 @@ __device__ void blk_residual(const Team<CL> &tm, const SmallLevel<T> &L, const T
     tm.sync();
 }
 
-// g_c = (I_{l-1}^l)^T r_f  (F = fine level l, C = coarse level l-1)
+// g_c = (I_{l-1}^l)^T r_f  (F = fine level l, C = coarse level l-1; ct1, ct2 per coarse cell)
 template <class T, bool CL>
-__device__ void blk_restrict(const Team<CL> &tm, const SmallLevel<T> &F, const SmallLevel<T> &C, const T *rf, T *gc) {
+__device__ void blk_restrict(const Team<CL> &tm, const SmallLevel<T> &F, const SmallLevel<T> &C, const T *rf, T *gc,
+                             T *ct1, T *ct2) {
     for (int P = tm.tid(); P < F.ncc; P += tm.nthreads()) {
         T rT[6];
         for (int t = 0; t < 6; ++t) rT[t] = tm.ld(rf + 2 * F.tr_slots[9 * P + 6 + t / 2] + (t & 1));
@@ -144,7 +145,7 @@ __device__ void blk_restrict(const Team<CL> &tm, const SmallLevel<T> &F, const S
         for (int c = 0; c < 12; ++c) {
             T acc = 0;
             for (int t = 0; t < 6; ++t) acc += Hk[t * 12 + c] * rT[t];
-            F.ct1[12 * P + c] = acc;
+            ct1[12 * P + c] = acc;
         }
     }
     tm.sync();
@@ -156,13 +157,13 @@ __device__ void blk_restrict(const Team<CL> &tm, const SmallLevel<T> &F, const S
             const int nb = F.tr_nbr[6 * P + s];
             const int Q = nb >> 4, s2 = nb & 15;
             for (int c = 0; c < 2; ++c)
-                z[2 * s + c] = tm.ld(rf + 2 * i + c) + tm.ld(F.ct1 + 12 * P + 2 * s + c) + tm.ld(F.ct1 + 12 * Q + 2 * s2 + c);
+                z[2 * s + c] = tm.ld(rf + 2 * i + c) + tm.ld(ct1 + 12 * P + 2 * s + c) + tm.ld(ct1 + 12 * Q + 2 * s2 + c);
         }
         const T *Wk = F.W + (size_t)P * 72;
         for (int col = 0; col < 6; ++col) {
             T acc = 0;
             for (int row = 0; row < 12; ++row) acc += Wk[row * 6 + col] * z[row];
-            F.ct2[6 * P + col] = acc;
+            ct2[6 * P + col] = acc;
         }
     }
     tm.sync();
@@ -171,8 +172,8 @@ __device__ void blk_restrict(const Team<CL> &tm, const SmallLevel<T> &F, const S
         for (int q = 0; q < 2; ++q) {
             const int adj = C.facet_adj[2 * G + q];
             const int K = adj >> 2, lf = adj & 3;
-            a0 += tm.ld(F.ct2 + 6 * K + 2 * lf);
-            a1 += tm.ld(F.ct2 + 6 * K + 2 * lf + 1);
+            a0 += tm.ld(ct2 + 6 * K + 2 * lf);
+            a1 += tm.ld(ct2 + 6 * K + 2 * lf + 1);
         }
         gc[2 * G] = a0;
         gc[2 * G + 1] = a1;
@@ -227,26 +228,32 @@ __device__ void blk_prolong_add(const Team<CL> &tm, const SmallLevel<T> &F, cons
 
 // u_0 = inv g_0 in FP64 (one warp per row)
 template <class T, bool CL>
-__device__ void blk_coarse(const Team<CL> &tm, const SmallParams<T> &S) {
-    const SmallLevel<T> &L0 = S.lv[0];
-    const int n = 2 * L0.n_int;
-    for (int i = tm.tid(); i < n; i += tm.nthreads()) S.g0d[i] = (double)tm.ld(L0.g + i);
+__device__ void blk_coarse(const Team<CL> &tm, const SmallParams<T> &S, const T *g0, T *u0, double *g0d) {
+    const int n = 2 * S.lv[0].n_int;
+    for (int i = tm.tid(); i < n; i += tm.nthreads()) g0d[i] = (double)tm.ld(g0 + i);
     tm.sync();
     const int lane = threadIdx.x & 31, wid = tm.tid() >> 5, nw = tm.nthreads() >> 5;
     for (int row = wid; row < n; row += nw) {
         double acc = 0.0;
-        for (int j = lane; j < n; j += 32) acc += S.inv[(size_t)row * n + j] * tm.ld(S.g0d + j);
+        for (int j = lane; j < n; j += 32) acc += S.inv[(size_t)row * n + j] * tm.ld(g0d + j);
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) L0.u[row] = (T)acc;
+        if (lane == 0) u0[row] = (T)acc;
     }
     tm.sync();
 }
+
+// where the kernel keeps the vectors of one level (global memory, or shared memory)
+template <class T>
+struct LevelVecs {
+    T *g, *u, *r, *t, *c1, *c2;
+};
 
 // MG_h(l_top, g, u, m, q) without recursion: an explicit walk down and up the
 // levels, where visit[l] counts the coarse-grid corrections done at level l (q of
 // them: 1 for the V-cycle, 2 for the W-cycle).  Every thread holds the same state.
 template <class T, bool CL>
-__device__ void blk_mg(const Team<CL> &tm, const SmallParams<T> &S, int top, int m_top, bool zero_top, T *rs) {
+__device__ void blk_mg(const Team<CL> &tm, const SmallParams<T> &S, const LevelVecs<T> *vv, double *g0d, int top,
+                       int m_top, bool zero_top, T *rs) {
     int mlev[SMALL_MAX_LEVELS];
     int visit[SMALL_MAX_LEVELS];
     int l = top;
@@ -256,20 +263,21 @@ __device__ void blk_mg(const Team<CL> &tm, const SmallParams<T> &S, int top, int
     while (true) {
         if (descending) {
             if (l == 0) {
-                blk_coarse(tm, S);
+                blk_coarse(tm, S, vv[0].g, vv[0].u, g0d);
                 descending = false;
                 l = 1;
                 continue;
             }
             const SmallLevel<T> &L = S.lv[l];
             const SmallLevel<T> &C = S.lv[l - 1];
+            const LevelVecs<T> V = vv[l];
             if (zero) {
-                blk_fill(tm, L.u, 2 * L.n_int);
+                blk_fill(tm, V.u, 2 * L.n_int);
                 tm.sync();
             }
-            for (int j = 0; j < mlev[l]; ++j) blk_sweep(tm, L, L.g, L.u, false, rs);
-            blk_residual(tm, L, L.g, L.u, L.r);
-            blk_restrict(tm, L, C, L.r, C.g);
+            for (int j = 0; j < mlev[l]; ++j) blk_sweep(tm, L, V.g, V.u, false, rs);
+            blk_residual(tm, L, V.g, V.u, V.r);
+            blk_restrict(tm, L, C, V.r, vv[l - 1].g, V.c1, V.c2);
             visit[l] = 0;
             mlev[l - 1] = S.q == 1 ? mlev[l] * S.growth : mlev[l];
             zero = true;
@@ -285,20 +293,62 @@ __device__ void blk_mg(const Team<CL> &tm, const SmallParams<T> &S, int top, int
             }
             const SmallLevel<T> &L = S.lv[l];
             const SmallLevel<T> &C = S.lv[l - 1];
-            blk_prolong_add(tm, L, C, C.u, L.u, L.t);
-            for (int j = 0; j < mlev[l]; ++j) blk_sweep(tm, L, L.g, L.u, true, rs);
+            const LevelVecs<T> V = vv[l];
+            blk_prolong_add(tm, L, C, vv[l - 1].u, V.u, V.t);
+            for (int j = 0; j < mlev[l]; ++j) blk_sweep(tm, L, V.g, V.u, true, rs);
             if (l == top) break;
             l = l + 1;
         }
     }
 }
 
+// carve the vectors of levels 0..top out of shared memory from `base` on, in the order
+// the host sized them (mg_small_vec_bytes)
+template <class T>
+__device__ double *carve_levels(const SmallParams<T> &S, int top, unsigned char *base, LevelVecs<T> *vv) {
+    for (int i = 0; i <= top; ++i) {
+        const SmallLevel<T> &L = S.lv[i];
+        const size_t n = 2 * (size_t)L.n_int;
+        T *b = reinterpret_cast<T *>(base);
+        vv[i] = LevelVecs<T>{b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 4 * n + 12 * (size_t)L.ncc};
+        base += sizeof(T) * (4 * n + 18 * (size_t)L.ncc);
+    }
+    const size_t off = (reinterpret_cast<size_t>(base) + 7) & ~size_t(7);
+    return reinterpret_cast<double *>(off);
+}
+
 template <class T, bool CL>
 __global__ void __launch_bounds__(1024) mg_small_kernel(SmallParams<T> S, int l, int m, int zero_init) {
     extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ LevelVecs<T> vv[SMALL_MAX_LEVELS];
+    __shared__ double *g0d;
     T *rs = reinterpret_cast<T *>(smraw);
     const Team<CL> tm = make_team<CL>();
-    blk_mg(tm, S, l, m, zero_init != 0, rs);
+    const bool resident = !CL && S.resident;
+    if (threadIdx.x == 0) {
+        if (resident) {
+            g0d = carve_levels(S, l, smraw + S.vec_offset, vv);
+        } else {
+            for (int i = 0; i <= l; ++i) {
+                const SmallLevel<T> &L = S.lv[i];
+                vv[i] = LevelVecs<T>{L.g, L.u, L.r, L.t, L.ct1, L.ct2};
+            }
+            g0d = S.g0d;
+        }
+    }
+    __syncthreads();
+    const int n = 2 * S.lv[l].n_int;
+    if (resident) {
+        // the caller's right-hand side (and initial guess) in, the result out at the end
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            vv[l].g[i] = S.lv[l].g[i];
+            if (!zero_init) vv[l].u[i] = S.lv[l].u[i];
+        }
+        __syncthreads();
+    }
+    blk_mg(tm, S, vv, g0d, l, m, zero_init != 0, rs);
+    if (resident)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) S.lv[l].u[i] = vv[l].u[i];
 }
 
 cudaLaunchConfig_t cluster_config(int csize, size_t smem, cudaStream_t s, cudaLaunchAttribute &at) {
@@ -317,6 +367,15 @@ cudaLaunchConfig_t cluster_config(int csize, size_t smem, cudaStream_t s, cudaLa
 }
 
 } // namespace
+
+// shared memory of the level vectors of levels 0..Ls kept resident by a single block
+// (the layout carve_levels walks), including the FP64 coarse right-hand side
+template <class T>
+size_t mg_small_vec_bytes(const SmallParams<T> &S, int Ls) {
+    size_t b = 0;
+    for (int i = 0; i <= Ls; ++i) b += sizeof(T) * (8 * (size_t)S.lv[i].n_int + 18 * (size_t)S.lv[i].ncc);
+    return b + 8 + sizeof(double) * 2 * (size_t)S.lv[0].n_int;
+}
 
 // shared memory per CTA when the largest colour phase (colour_bytes of residual
 // rows) is split over csize CTAs; slack covers the rounding to whole patches
@@ -368,6 +427,8 @@ cudaError_t launch_mg_small(const SmallParams<T> &S, int l, int m, bool zero_ini
     return cudaLaunchKernelEx(&cfg, mg_small_kernel<T, true>, S, l, m, zero_init ? 1 : 0);
 }
 
+template size_t mg_small_vec_bytes<double>(const SmallParams<double> &, int);
+template size_t mg_small_vec_bytes<float>(const SmallParams<float> &, int);
 template int mg_small_cluster_size<double>(size_t, int);
 template int mg_small_cluster_size<float>(size_t, int);
 template cudaError_t launch_mg_small<double>(const SmallParams<double> &, int, int, bool, size_t, int, cudaStream_t);

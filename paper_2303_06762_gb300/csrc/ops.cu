@@ -20,11 +20,16 @@
 //   and the triangular solve on the device.
 // * Uzawa (eq. stOpEq-ALU): load F + Dᵀp and the cell-wise pressure update.
 //
-// Symmetric element and patch matrices are read as their transposes so that
-// consecutive threads (consecutive rows) touch consecutive addresses.
+// Element matrices are stored by facet row blocks and patch inverses as their
+// transposes, so that consecutive threads (consecutive rows) touch consecutive
+// addresses.  The order-k apply and sweep also read 16-bit copies (bfloat16 or
+// binary16) whose rows carry a power-of-two scale; products accumulate in FP32.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <atomic>
+#include <type_traits>
 
 #include "hdg_internal.h"
 
@@ -47,12 +52,20 @@ constexpr int MAXV = 33;              // restart <= 32: up to 33 basis vectors
 
 unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 
-template <class T, int DPF>
+// value of a stored matrix entry in the arithmetic type T
+template <class T>
+__device__ __forceinline__ T ld_entry(const T *p) { return *p; }
+__device__ __forceinline__ float ld_entry(const __half *p) { return __half2float(*p); }
+__device__ __forceinline__ float ld_entry(const __nv_bfloat16 *p) { return __bfloat162float(*p); }
+
+// S = storage type of A (T, or a 16-bit type with per-row scales As[c*NLOC + row])
+template <class T, int DPF, class S = T>
 __global__ void __launch_bounds__(256)
 apply_kernel(int64_t n_int, const int *__restrict__ facet_adj, const int *__restrict__ cell_int,
-             const T *__restrict__ A, const T *__restrict__ x, const T *__restrict__ g,
-             T *__restrict__ y) {
+             const S *__restrict__ A, const float *__restrict__ As, const T *__restrict__ x,
+             const T *__restrict__ g, T *__restrict__ y) {
     constexpr int NLOC = 3 * DPF;
+    constexpr bool scaled = !std::is_same<S, T>::value;
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n_int * DPF) return;
     int64_t i = idx / DPF;
@@ -63,27 +76,38 @@ apply_kernel(int64_t n_int, const int *__restrict__ facet_adj, const int *__rest
         int adj = facet_adj[2 * i + q];
         if (adj < 0) continue;
         int c = adj >> 2, lf = adj & 3;
-        const T *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d;
+        const S *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d;
+        T part = 0;
 #pragma unroll
         for (int f2 = 0; f2 < 3; ++f2) {
             int j = cell_int[3 * c + f2];
             if (j < 0) continue;
             const T *xs = x + (size_t)j * DPF;
+            if constexpr (scaled) {
 #pragma unroll
-            for (int d2 = 0; d2 < DPF; ++d2) acc += Ac[(f2 * DPF + d2) * DPF] * xs[d2];
+                for (int d2 = 0; d2 < DPF; ++d2) part += ld_entry(Ac + (f2 * DPF + d2) * DPF) * xs[d2];
+            } else {
+#pragma unroll
+                for (int d2 = 0; d2 < DPF; ++d2) acc += Ac[(f2 * DPF + d2) * DPF] * xs[d2];
+            }
         }
+        if constexpr (scaled) acc += As[(size_t)c * NLOC + lf * DPF + d] * part;
     }
     y[idx] = g ? g[idx] - acc : acc;
 }
 
-template <class T, int DPF>
+// S = storage type of A and Pinv (T, or a 16-bit type with per-row scales As[c*NLOC + row]
+// and Ps[p*np_max + row] of the element matrices and patch inverses)
+template <class T, int DPF, class S = T>
 __global__ void gs_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
                           const int *__restrict__ patch_nf, const int *__restrict__ patch_facets,
                           const int *__restrict__ patch_nc, const int *__restrict__ patch_cells,
                           const int *__restrict__ slot_src, const int *__restrict__ cell_int,
-                          const T *__restrict__ A, const T *__restrict__ Pinv,
+                          const S *__restrict__ A, const float *__restrict__ As,
+                          const S *__restrict__ Pinv, const float *__restrict__ Ps,
                           const T *__restrict__ g, T *__restrict__ u) {
     constexpr int NLOC = 3 * DPF;
+    constexpr bool scaled = !std::is_same<S, T>::value;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *xs = reinterpret_cast<T *>(smraw);     // pc_max * NLOC
     T *r = xs + pc_max * NLOC;                 // np_max
@@ -106,30 +130,92 @@ __global__ void gs_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
             int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
             int si = src >> 2, lf = src & 3;
             int c = patch_cells[(size_t)p * pc_max + si];
-            const T *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d;
+            const S *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d;
             const T *xc = xs + si * NLOC;
+            if constexpr (scaled) {
+                T part = 0;
 #pragma unroll
-            for (int col = 0; col < NLOC; ++col) acc -= Ac[col * DPF] * xc[col];
+                for (int col = 0; col < NLOC; ++col) part += ld_entry(Ac + col * DPF) * xc[col];
+                acc -= As[(size_t)c * NLOC + lf * DPF + d] * part;
+            } else {
+#pragma unroll
+                for (int col = 0; col < NLOC; ++col) acc -= Ac[col * DPF] * xc[col];
+            }
         }
         r[t] = acc;
     }
     __syncthreads();
-    const T *Pi = Pinv + (size_t)p * np_max * np_max;
+    const S *Pi = Pinv + (size_t)p * np_max * np_max;
     for (int t = tid; t < np; t += nt) {
         // four partial sums keep several independent loads in flight per thread
         T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         int j = 0;
 #pragma unroll 2
         for (; j + 4 <= np; j += 4) {
-            a0 += Pi[(size_t)(j + 0) * np_max + t] * r[j + 0];
-            a1 += Pi[(size_t)(j + 1) * np_max + t] * r[j + 1];
-            a2 += Pi[(size_t)(j + 2) * np_max + t] * r[j + 2];
-            a3 += Pi[(size_t)(j + 3) * np_max + t] * r[j + 3];
+            a0 += ld_entry(Pi + (size_t)(j + 0) * np_max + t) * r[j + 0];
+            a1 += ld_entry(Pi + (size_t)(j + 1) * np_max + t) * r[j + 1];
+            a2 += ld_entry(Pi + (size_t)(j + 2) * np_max + t) * r[j + 2];
+            a3 += ld_entry(Pi + (size_t)(j + 3) * np_max + t) * r[j + 3];
         }
-        for (; j < np; ++j) a0 += Pi[(size_t)j * np_max + t] * r[j];
+        for (; j < np; ++j) a0 += ld_entry(Pi + (size_t)j * np_max + t) * r[j];
+        T du = (a0 + a1) + (a2 + a3);
+        if constexpr (scaled) du *= Ps[(size_t)p * np_max + t];
         int F = patch_facets[(size_t)p * pf_max + t / DPF];
-        u[(size_t)F * DPF + t % DPF] += (a0 + a1) + (a2 + a3);
+        u[(size_t)F * DPF + t % DPF] += du;
     }
+}
+
+// 16-bit row-scaled copies of the order-k element matrices: one thread per stored row
+// (cell c, row p = lf*DPF + d); s = 2^e with max_q |A_pq| = m 2^e, m in [1/2, 1).
+template <class S>
+__device__ __forceinline__ S to_storage(double v);
+template <>
+__device__ __forceinline__ __half to_storage<__half>(double v) { return __double2half(v); }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(double v) { return __double2bfloat16(v); }
+
+__device__ __forceinline__ double pow2_scale(double m) {
+    if (!(m > 0.0) || !isfinite(m)) return 1.0;
+    int e;
+    frexp(m, &e);
+    return ldexp(1.0, e);
+}
+
+template <class S, int DPF>
+__global__ void round_element_rows_kernel(int64_t nc, const double *__restrict__ A, S *__restrict__ Ah,
+                                          float *__restrict__ As) {
+    constexpr int NLOC = 3 * DPF;
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= nc * NLOC) return;
+    const int64_t c = idx / NLOC;
+    const int row = (int)(idx - c * NLOC), lf = row / DPF, d = row % DPF;
+    const size_t base = (size_t)c * NLOC * NLOC + (size_t)lf * NLOC * DPF + d;
+    double m = 0.0;
+    for (int q = 0; q < NLOC; ++q) m = fmax(m, fabs(A[base + (size_t)q * DPF]));
+    const double sc = pow2_scale(m);
+    for (int q = 0; q < NLOC; ++q) Ah[base + (size_t)q * DPF] = to_storage<S>(A[base + (size_t)q * DPF] / sc);
+    As[idx] = (float)sc;
+}
+
+// the same for the patch inverses, stored transposed (row i of the inverse at
+// Pinv[j*np_max + i]); rows and columns beyond the patch's own size become zero
+template <class S>
+__global__ void round_patch_rows_kernel(int n_patches, int np_max, int dpf, const int *__restrict__ patch_nf,
+                                        const double *__restrict__ P, S *__restrict__ Ph,
+                                        float *__restrict__ Ps) {
+    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= (int64_t)n_patches * np_max) return;
+    const int64_t pt = idx / np_max;
+    const int i = (int)(idx - pt * np_max);
+    const int np = patch_nf[pt] * dpf;
+    const size_t base = (size_t)pt * np_max * np_max + i;
+    double m = 0.0;
+    if (i < np)
+        for (int j = 0; j < np; ++j) m = fmax(m, fabs(P[base + (size_t)j * np_max]));
+    const double sc = pow2_scale(m);
+    for (int j = 0; j < np_max; ++j)
+        Ph[base + (size_t)j * np_max] = to_storage<S>(i < np && j < np ? P[base + (size_t)j * np_max] / sc : 0.0);
+    Ps[idx] = (float)sc;
 }
 
 // Lowest-order sweep (DPF = 2): LANES consecutive lanes of a warp own one patch
@@ -548,11 +634,11 @@ cudaError_t apply_dispatch(const DevLevel &L, int dpf, const T *A, const T *x, c
     if (n == 0) return cudaSuccess;
     unsigned nb = blocks_for(n, 256);
     switch (dpf) {
-    case 2: note_launches(1); apply_kernel<T, 2><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
-    case 4: note_launches(1); apply_kernel<T, 4><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
-    case 6: note_launches(1); apply_kernel<T, 6><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
-    case 8: note_launches(1); apply_kernel<T, 8><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
-    case 10: note_launches(1); apply_kernel<T, 10><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, x, g, y); break;
+    case 2: note_launches(1); apply_kernel<T, 2><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, nullptr, x, g, y); break;
+    case 4: note_launches(1); apply_kernel<T, 4><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, nullptr, x, g, y); break;
+    case 6: note_launches(1); apply_kernel<T, 6><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, nullptr, x, g, y); break;
+    case 8: note_launches(1); apply_kernel<T, 8><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, nullptr, x, g, y); break;
+    case 10: note_launches(1); apply_kernel<T, 10><<<nb, 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, A, nullptr, x, g, y); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -586,11 +672,93 @@ cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, cons
     note_launches(1);
     gs_kernel<T, DPF><<<p1 - p0, nt, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
                                                 L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
-                                                L.patch_slot_src.p, L.cell_int.p, A, Pinv, g, u);
+                                                L.patch_slot_src.p, L.cell_int.p, A, nullptr, Pinv, nullptr,
+                                                g, u);
+    return cudaGetLastError();
+}
+
+template <class S, int DPF>
+cudaError_t gs_launch_h(const DevLevel &L, const DevOperator &op, int colour, const float *g, float *u,
+                        cudaStream_t s) {
+    int p0 = L.colour_ptr[colour], p1 = L.colour_ptr[colour + 1];
+    if (p1 <= p0) return cudaSuccess;
+    int nt = ((op.np_max + 31) / 32) * 32;
+    if (nt > 256) nt = 256;
+    if (nt < 32) nt = 32;
+    size_t smem = sizeof(float) * ((size_t)L.pc_max * 3 * DPF + op.np_max);
+    note_launches(1);
+    gs_kernel<float, DPF, S><<<p1 - p0, nt, smem, s>>>(
+        p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p, L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
+        L.patch_slot_src.p, L.cell_int.p, reinterpret_cast<const S *>(op.Ah.p), op.Ah_s.p,
+        reinterpret_cast<const S *>(op.Pinvh.p), op.Pinvh_s.p, g, u);
+    return cudaGetLastError();
+}
+
+template <class S, int DPF>
+cudaError_t apply_launch_h(const DevLevel &L, const DevOperator &op, const float *x, const float *g, float *y,
+                           cudaStream_t s) {
+    const int64_t n = L.n_int * DPF;
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    apply_kernel<float, DPF, S><<<blocks_for(n, 256), 256, 0, s>>>(
+        L.n_int, L.facet_adj.p, L.cell_int.p, reinterpret_cast<const S *>(op.Ah.p), op.Ah_s.p, x, g, y);
+    return cudaGetLastError();
+}
+
+template <class S>
+cudaError_t round16_launch(const DevLevel &L, DevOperator &op, cudaStream_t s) {
+    const int64_t nrow = L.nc * op.nloc;
+    note_launches(1);
+    switch (op.dpf) {
+    case 2: round_element_rows_kernel<S, 2><<<blocks_for(nrow, 128), 128, 0, s>>>(L.nc, op.A.p, reinterpret_cast<S *>(op.Ah.p), op.Ah_s.p); break;
+    case 4: round_element_rows_kernel<S, 4><<<blocks_for(nrow, 128), 128, 0, s>>>(L.nc, op.A.p, reinterpret_cast<S *>(op.Ah.p), op.Ah_s.p); break;
+    case 6: round_element_rows_kernel<S, 6><<<blocks_for(nrow, 128), 128, 0, s>>>(L.nc, op.A.p, reinterpret_cast<S *>(op.Ah.p), op.Ah_s.p); break;
+    case 8: round_element_rows_kernel<S, 8><<<blocks_for(nrow, 128), 128, 0, s>>>(L.nc, op.A.p, reinterpret_cast<S *>(op.Ah.p), op.Ah_s.p); break;
+    case 10: round_element_rows_kernel<S, 10><<<blocks_for(nrow, 128), 128, 0, s>>>(L.nc, op.A.p, reinterpret_cast<S *>(op.Ah.p), op.Ah_s.p); break;
+    default: return cudaErrorInvalidValue;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || L.n_patches == 0) return e;
+    const int64_t nprow = (int64_t)L.n_patches * op.np_max;
+    note_launches(1);
+    round_patch_rows_kernel<S><<<blocks_for(nprow, 128), 128, 0, s>>>(
+        L.n_patches, op.np_max, op.dpf, L.patch_nf.p, op.Pinv.p, reinterpret_cast<S *>(op.Pinvh.p), op.Pinvh_s.p);
     return cudaGetLastError();
 }
 
 } // namespace
+
+cudaError_t launch_round16(const DevLevel &L, DevOperator &op, int fmt, cudaStream_t s) {
+    if (fmt == HDG_MIXED_BF16) return round16_launch<__nv_bfloat16>(L, op, s);
+    if (fmt == HDG_MIXED_FP16) return round16_launch<__half>(L, op, s);
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_apply_h(const DevLevel &L, const DevOperator &op, const float *x, const float *g, float *y,
+                           cudaStream_t s) {
+    const bool bf = op.h_fmt == HDG_MIXED_BF16;
+    if (!bf && op.h_fmt != HDG_MIXED_FP16) return cudaErrorInvalidValue;
+    switch (op.dpf) {
+#define HDG_APPLY_H(D) \
+    case D: return bf ? apply_launch_h<__nv_bfloat16, D>(L, op, x, g, y, s) : apply_launch_h<__half, D>(L, op, x, g, y, s);
+    HDG_APPLY_H(2) HDG_APPLY_H(4) HDG_APPLY_H(6) HDG_APPLY_H(8) HDG_APPLY_H(10)
+#undef HDG_APPLY_H
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_gs_colour_h(const DevLevel &L, const DevOperator &op, int colour, const float *g, float *u,
+                               cudaStream_t s) {
+    const bool bf = op.h_fmt == HDG_MIXED_BF16;
+    if (!bf && op.h_fmt != HDG_MIXED_FP16) return cudaErrorInvalidValue;
+    switch (op.dpf) {
+#define HDG_GS_H(D) \
+    case D: return bf ? gs_launch_h<__nv_bfloat16, D>(L, op, colour, g, u, s) : gs_launch_h<__half, D>(L, op, colour, g, u, s);
+    HDG_GS_H(2) HDG_GS_H(4) HDG_GS_H(6) HDG_GS_H(8) HDG_GS_H(10)
+#undef HDG_GS_H
+    default: return cudaErrorInvalidValue;
+    }
+}
 
 template <class T>
 cudaError_t launch_apply(const DevLevel &L, const DevOperator &op, const T *A, const T *x, const T *g,
@@ -614,14 +782,16 @@ cudaError_t launch_gs_colour(const DevLevel &L, const DevOperator &op, const T *
 template <class T>
 cudaError_t launch_prolong_add(const DevLevel &F, const DevLevel &C, const T *W, const T *Hm, const T *uc,
                                T *tmp, T *uf, cudaStream_t s) {
-    if (F.nB > 0)
+    if (F.nB > 0) {
         note_launches(1);
         prolong_B_kernel<T><<<blocks_for(F.nB, 128), 128, 0, s>>>(F.nB, F.tr_fineB.p, F.tr_fineB_src.p,
                                                                  C.cell_int.p, W, uc, tmp, uf);
-    if (F.nc_coarse > 0)
+    }
+    if (F.nc_coarse > 0) {
         note_launches(1);
         prolong_T_kernel<T><<<blocks_for(F.nc_coarse, 128), 128, 0, s>>>(F.nc_coarse, F.tr_slots.p, Hm,
                                                                          tmp, uf);
+    }
     return cudaGetLastError();
 }
 
@@ -636,9 +806,10 @@ cudaError_t launch_restrict(const DevLevel &F, const DevLevel &C, const T *W, co
         restrict_B_kernel<T><<<blocks_for(F.nc_coarse, 128), 128, 0, s>>>(F.nc_coarse, F.tr_slots.p,
                                                                           F.tr_nbr.p, W, rf, t1, t2);
     }
-    if (C.n_int > 0)
+    if (C.n_int > 0) {
         note_launches(1);
         restrict_C_kernel<T><<<blocks_for(C.n_int, 128), 128, 0, s>>>(C.n_int, C.facet_adj.p, t2, rc);
+    }
     return cudaGetLastError();
 }
 

@@ -263,12 +263,14 @@ _BIG_ORACLE = {}
 
 
 @pytest.mark.parametrize("precision", [0, 1])
-def test_mg_h_fused_and_multiblock_levels(precision):
-    """Hierarchy 4x4..128x128 with the single-block kernel on levels up to 32x32
-    and the multi-block kernels on 64x64 and 128x128: MG_h and MG_hp against the oracle."""
+@pytest.mark.parametrize("fused", [512, 2048])
+def test_mg_h_fused_and_multiblock_levels(precision, fused):
+    """Hierarchy 4x4..128x128 with the fused kernel on levels up to 16x16 (one block, level
+    vectors in shared memory) or 32x32 (a cluster) and the multi-block kernels above:
+    MG_h and MG_hp against the oracle."""
     hdg = _hdg()
     k = 1
-    ms, ts, ps, fv, ctx, F = setup_case(4, 6, k, precision=precision, fused=2048)
+    ms, ts, ps, fv, ctx, F = setup_case(4, 6, k, precision=precision, fused=fused)
     if "M" not in _BIG_ORACLE:
         _BIG_ORACLE["M"] = _oracle_mg(ts, ps, k, 100.0)
     M = _BIG_ORACLE["M"]
