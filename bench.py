@@ -301,8 +301,10 @@ def gpu_arm(args):
     stream = torch.cuda.current_stream(dev)
     results = {}
     sizes = None
+    # (HDG_MIXED_BF16 is not timed here: at 512x512, k = 3 its FGMRES stalls before the
+    # iteration limit; it is exercised by the parity tests on small meshes)
     for name, prec in (("fp64", hdg.HDG_FP64), ("mixed_fp32", hdg.HDG_MIXED_FP32),
-                       ("mixed_fp16", hdg.HDG_MIXED_FP16), ("mixed_bf16", hdg.HDG_MIXED_BF16)):
+                       ("mixed_fp16", hdg.HDG_MIXED_FP16)):
         prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma, precision=prec)
         F = hdg.hdg_condense(ctx, prm, forcing)
         sizes = ctx.sizes()
