@@ -579,15 +579,41 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
     # 317,834,240 B against 318,199,104 algorithmic bytes there.  Traffic grows with the
     # number of patches like the algorithmic bytes, so the full-size figure is that ratio
     # times the full-size algorithmic bytes (k = 3 only; other k were not captured).
-    traffic = alg * (317834240 / 318199104) if k == 3 and not half else None
+    traffic = alg * (TMA_SWEEP_TRAFFIC_128 / 318199104) if k == 3 and not half and TMA_SWEEP_TRAFFIC_128 else None
     kname = "gs_kernel<float, 8, __half> (order-k block GS sweep on binary16 copies" if half else \
-        "gs_kernel<float> (order-k block GS sweep"
+        "gs_tma_kernel<8> (order-k block GS sweep, matrices staged by cp.async.bulk"
+    rs = read_stream_gbs(torch, dev, stream)
     return {"kernel": kname + ", 3 colour launches)",
+            "read_stream_gbs": rs, "frac_of_read_stream": achieved / rs,
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
             "traffic_note": "scaled from an ncu capture at 128x128 (same kernel, cold caches)" if traffic else None,
             "algorithmic_bytes_per_sweep": alg, "sweep_ms": t_sweep * 1e3,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
+
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the three colour launches of one
+# order-k sweep of gs_tma_kernel<8> from an ncu capture on the 128x128, k = 3 case, whose
+# algorithmic bytes are 318,199,104; None until captured for the current kernel.
+TMA_SWEEP_TRAFFIC_128 = None
+
+
+def read_stream_gbs(torch, dev, stream):
+    """Read-only streaming rate of this GPU: a full reduction over 2 GiB (larger than L2),
+    the ceiling for a kernel that, like the sweep, reads matrices and writes little."""
+    x = torch.ones(1 << 29, dtype=torch.float32, device=dev)
+    x.sum()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(10):
+        x.sum()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    gbs = x.numel() * 4 * 10 / (ev0.elapsed_time(ev1) / 1e3) / 1e9
+    del x
+    return gbs
 
 
 def profile_solve(args):

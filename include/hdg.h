@@ -73,7 +73,9 @@ typedef enum {
     HDG_ERR_BREAKDOWN = 6,     /* Krylov breakdown with a nonzero residual          */
     HDG_ERR_NONFINITE = 7,     /* NaN or Inf in a residual                          */
     HDG_ERR_UNSUPPORTED = 8,   /* valid request this build does not implement       */
-    HDG_ERR_STATE = 9          /* call order violated (e.g. solve before condense)  */
+    HDG_ERR_STATE = 9,         /* call order violated (e.g. solve before condense)  */
+    HDG_ERR_TIMEOUT = 10       /* a bounded device wait gave up (a kernel skipped   */
+                               /* its update; the result of the call is invalid)    */
 } hdg_status;
 
 typedef enum {

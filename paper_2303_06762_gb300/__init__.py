@@ -33,7 +33,7 @@ HDG_MIXED_FP16 = 3
 
 _STATUS = {0: "HDG_OK", 1: "HDG_ERR_INVALID_ARG", 2: "HDG_ERR_OOM", 3: "HDG_ERR_CUDA",
            4: "HDG_ERR_SINGULAR", 5: "HDG_ERR_NOT_CONVERGED", 6: "HDG_ERR_BREAKDOWN",
-           7: "HDG_ERR_NONFINITE", 8: "HDG_ERR_UNSUPPORTED", 9: "HDG_ERR_STATE"}
+           7: "HDG_ERR_NONFINITE", 8: "HDG_ERR_UNSUPPORTED", 9: "HDG_ERR_STATE", 10: "HDG_ERR_TIMEOUT"}
 
 # every exported entry point of include/hdg.h
 EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense", "hdg_load",

@@ -122,6 +122,19 @@ void check_flag(hdg_ctx *ctx, cudaStream_t s) {
     }
 }
 
+// a kernel gave up a bounded wait (the bulk copies of the order-k sweep): its update was
+// skipped, so the result of the call is wrong; the flag is cleared for the next call
+void check_wait_flag(hdg_ctx *ctx, cudaStream_t s) {
+    int flag = 0;
+    CK(cudaMemcpyAsync(&flag, ctx->wait_flag.p, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (flag) {
+        CK(cudaMemsetAsync(ctx->wait_flag.p, 0, sizeof(int), s));
+        ctx->err = "a device wait timed out (flag " + std::to_string(flag) + ")";
+        throw Fail{HDG_ERR_TIMEOUT};
+    }
+}
+
 double read_scalar(hdg_ctx *ctx, const double *dev, cudaStream_t s) {
     CK(cudaMemcpyAsync(ctx->h_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -984,6 +997,7 @@ const char *hdg_status_string(hdg_status s) {
     case HDG_ERR_NONFINITE: return "non-finite value";
     case HDG_ERR_UNSUPPORTED: return "unsupported";
     case HDG_ERR_STATE: return "call order violated";
+    case HDG_ERR_TIMEOUT: return "a bounded device wait timed out";
     }
     return "unknown status";
 }
@@ -1102,6 +1116,8 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
             dalloc(ctx, L.gf, n0); dalloc(ctx, L.uf, n0); dalloc(ctx, L.rf, n0); dalloc(ctx, L.tf, n0);
         }
         dalloc(ctx, ctx->status_flag, 1);
+        dalloc(ctx, ctx->wait_flag, 1);
+        CK(cudaMemset(ctx->wait_flag.p, 0, sizeof(int)));
         CK(cudaMallocHost((void **)&ctx->h_pinned, 8 * sizeof(double)));
         CK(cudaDeviceSynchronize());
     });
@@ -1121,7 +1137,7 @@ void hdg_destroy(hdg_ctx *ctx) {
     free_operator(ctx->opk);
     dfree(ctx->refk_dev); dfree(ctx->ref0_dev);
     dfree(ctx->kr); dfree(ctx->ku); dfree(ctx->kt); dfree(ctx->krf); dfree(ctx->kuf); dfree(ctx->kgf);
-    dfree(ctx->coarse_inv); dfree(ctx->status_flag); dfree(ctx->conv_k); dfree(ctx->newton_x);
+    dfree(ctx->coarse_inv); dfree(ctx->status_flag); dfree(ctx->wait_flag); dfree(ctx->conv_k); dfree(ctx->newton_x);
     dfree(ctx->V); dfree(ctx->Z); dfree(ctx->w); dfree(ctx->partials); dfree(ctx->small);
     dfree(ctx->uz_partials);
     for (auto *b : {&ctx->rec_L, &ctx->rec_La, &ctx->rec_rt, &ctx->rec_ulat, &ctx->rec_e, &ctx->rec_j, &ctx->adj_F,
@@ -1225,6 +1241,7 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
                        prm->beta, prm->gamma, forcing, conv_of(ctx), ctx->conv_t, newton_of(ctx), op.A.p, op.Af.p,
                        op.Fel.p, ctx->status_flag.p, RecoverArgs(), s));
     CK(launch_patch_inverse(LJ, op, ctx->has_conv ? 1 : 0, ctx->status_flag.p, s));
+    op.tma_flag = ctx->wait_flag.p;
     op.h_fmt = 0;
     if (k >= 1 && (prm->precision == HDG_MIXED_BF16 || prm->precision == HDG_MIXED_FP16)) {
         dalloc(ctx, op.Ah, (size_t)op.nloc * op.nloc * LJ.nc);
@@ -1466,6 +1483,7 @@ hdg_status hdg_solve(hdg_ctx *ctx, const double *F, double *u, double *p, const 
         NEED_CONDENSED();
         REQUIRE(F && u && p, "null vector");
         conv = uzawa_solve(ctx, F, u, p, opts_in, loc, (cudaStream_t)stream);
+        check_wait_flag(ctx, (cudaStream_t)stream);
     });
     if (info) *info = loc;
     if (st != HDG_OK) return st;

@@ -146,6 +146,8 @@ struct DevOperator {
     DBuf<float> Pinvf;
     // 16-bit copies for HDG_MIXED_BF16 / HDG_MIXED_FP16 (order-k operator only): the
     // layouts of A and Pinv with every stored row divided by its power-of-two scale
+    int *tma_flag = nullptr; // device flag of the bulk-copy sweep's bounded waits (bit 4 on timeout),
+                             // null = that sweep is not used
     int h_fmt = 0;       // hdg_precision of Ah / Pinvh, 0 = none
     DBuf<uint16_t> Ah;   // nc*nloc*nloc
     DBuf<float> Ah_s;    // nc*nloc, scale of row p of cell c at c*nloc + p
@@ -211,6 +213,7 @@ struct hdg_ctx {
     int64_t n0 = 0;
     hdg::DBuf<double> coarse_inv;
     hdg::DBuf<int> status_flag;              // device error flag
+    hdg::DBuf<int> wait_flag;                // set by a kernel whose bounded wait gave up
     // Krylov workspace
     int restart_alloc = 0;
     hdg::DBuf<double> V, Z, w, partials, small;   // small: Hessenberg, rotations, g, y

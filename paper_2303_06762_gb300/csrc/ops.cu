@@ -218,6 +218,132 @@ __global__ void round_patch_rows_kernel(int n_patches, int np_max, int dpf, cons
     Ps[idx] = (float)sc;
 }
 
+// ---------------------------------------------------------------- order-k sweep, TMA-staged
+// One colour phase of the order-k FP32 sweep, as gs_kernel<float, DPF>, with the
+// patch's matrices moved into shared memory by the bulk-copy engine: thread 0
+// posts the byte count on an mbarrier, then lanes of warp 0 issue one
+// cp.async.bulk per block (the patch inverse's np rows, and the facet row block
+// of A_K for each of the 2 nf (facet, cell) slots, each a contiguous stretch of
+// the row-block layout).  While the copies fly, the block gathers the star's
+// unknowns; it then waits on the mbarrier (bounded: after about a second of
+// polling it records the timeout in *flag, waits once more, bounded, for its
+// copies, and skips the update) and runs the residual rows and the inverse
+// product from shared memory in the same order as gs_kernel.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile("{\n .reg .pred P;\n mbarrier.try_wait.parity.shared::cta.b64 P, [%1], %2;\n"
+                 " selp.u32 %0, 1, 0, P;\n}\n"
+                 : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// polls until phase `parity` of the barrier completed or `limit_ns` of global time passed
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, unsigned long long limit_ns) {
+    unsigned long long t0;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (!mbar_try_wait(bar, parity)) {
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        if (t - t0 > limit_ns) return false;
+    }
+    return true;
+}
+
+template <int DPF>
+__global__ void __launch_bounds__(64)
+gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
+              const int *__restrict__ patch_nf, const int *__restrict__ patch_facets,
+              const int *__restrict__ patch_nc, const int *__restrict__ patch_cells,
+              const int *__restrict__ slot_src, const int *__restrict__ cell_int,
+              const float *__restrict__ A, const float *__restrict__ Pinv,
+              const float *__restrict__ g, float *__restrict__ u, int *flag) {
+    constexpr int NLOC = 3 * DPF;
+    constexpr int RB = NLOC * DPF;             // floats in one facet row block
+    extern __shared__ __align__(128) unsigned char smraw[];
+    __shared__ __align__(8) unsigned long long mbar;
+    __shared__ int s_ok;
+    const int p = p0 + blockIdx.x;
+    if (p >= p1) return;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
+    float *Ps = reinterpret_cast<float *>(smraw);            // np rows of np_max
+    float *As = Ps + (size_t)np_max * np_max;                // 2 pf_max row blocks
+    float *xs = As + (size_t)2 * pf_max * RB;                // pc_max * NLOC
+    float *r = xs + (size_t)pc_max * NLOC;                   // np_max
+    const uint32_t bar = smem_u32(&mbar);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        s_ok = 1;
+    }
+    __syncthreads();
+    if (tid < 32) {
+        const uint32_t pbytes = (uint32_t)(np * np_max * sizeof(float));
+        const uint32_t abytes = (uint32_t)(RB * sizeof(float));
+        if (tid == 0)
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         ::"r"(bar), "r"(pbytes + 2u * nf * abytes) : "memory");
+        __syncwarp();
+        if (tid == 0) {
+            const float *src = Pinv + (size_t)p * np_max * np_max;
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(Ps)), "l"(src), "r"(pbytes), "r"(bar) : "memory");
+        }
+        for (int sl = tid; sl < 2 * nf; sl += 32) {
+            const int src = slot_src[(size_t)p * pf_max * 2 + sl];   // slot (js, q) at js*2 + q
+            const int c = patch_cells[(size_t)p * pc_max + (src >> 2)];
+            const float *blk = A + (size_t)c * NLOC * NLOC + (size_t)(src & 3) * RB;
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(As + (size_t)sl * RB)), "l"(blk), "r"(abytes), "r"(bar) : "memory");
+        }
+    }
+    for (int t = tid; t < ncell * NLOC; t += nt) {
+        int si = t / NLOC, l = t % NLOC;
+        int c = patch_cells[(size_t)p * pc_max + si];
+        int j = cell_int[3 * c + l / DPF];
+        xs[t] = j >= 0 ? u[(size_t)j * DPF + l % DPF] : 0.0f;
+    }
+    if (!mbar_wait_bounded(bar, 0, 1000000000ull)) {
+        atomicOr(flag, 4);
+        s_ok = 0;
+        mbar_wait_bounded(bar, 0, 1000000000ull);
+    }
+    __syncthreads();
+    if (!s_ok) return;
+    for (int t = tid; t < np; t += nt) {
+        int js = t / DPF, d = t % DPF;
+        int F = patch_facets[(size_t)p * pf_max + js];
+        float acc = g[(size_t)F * DPF + d];
+        for (int q = 0; q < 2; ++q) {
+            int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
+            const float *Ac = As + (size_t)(js * 2 + q) * RB + d;
+            const float *xc = xs + (src >> 2) * NLOC;
+#pragma unroll
+            for (int col = 0; col < NLOC; ++col) acc -= Ac[col * DPF] * xc[col];
+        }
+        r[t] = acc;
+    }
+    __syncthreads();
+    for (int t = tid; t < np; t += nt) {
+        float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+        int j = 0;
+#pragma unroll 2
+        for (; j + 4 <= np; j += 4) {
+            a0 += Ps[(j + 0) * np_max + t] * r[j + 0];
+            a1 += Ps[(j + 1) * np_max + t] * r[j + 1];
+            a2 += Ps[(j + 2) * np_max + t] * r[j + 2];
+            a3 += Ps[(j + 3) * np_max + t] * r[j + 3];
+        }
+        for (; j < np; ++j) a0 += Ps[j * np_max + t] * r[j];
+        int F = patch_facets[(size_t)p * pf_max + t / DPF];
+        u[(size_t)F * DPF + t % DPF] += (a0 + a1) + (a2 + a3);
+    }
+}
+
 // Lowest-order sweep (DPF = 2): LANES consecutive lanes of a warp own one patch
 // (row t of the patch on lane t, np <= LANES <= 32), so a 256-thread block works on
 // 256/LANES patches at once instead of one; the block inverse is applied with
@@ -644,6 +770,32 @@ cudaError_t apply_dispatch(const DevLevel &L, int dpf, const T *A, const T *x, c
     return cudaGetLastError();
 }
 
+template <int DPF>
+size_t tma_sweep_smem(const DevLevel &L, const DevOperator &op) {
+    const size_t rb = (size_t)3 * DPF * DPF;     // one facet row block, n_loc x dpf
+    return sizeof(float) * ((size_t)op.np_max * op.np_max + 2 * (size_t)L.pf_max * rb +
+                            (size_t)L.pc_max * 3 * DPF + op.np_max);
+}
+
+// the bulk copies need 16-byte aligned sources, destinations and sizes: the patch
+// inverse (np_max² floats, rows of np_max), the facet row blocks (3 DPF² floats, at
+// cell strides of 9 DPF² floats) and both bases
+template <int DPF>
+bool tma_sweep_ok(const DevLevel &L, const DevOperator &op, const float *A, const float *Pinv) {
+    const size_t smem = tma_sweep_smem<DPF>(L, op);
+    if ((op.np_max * sizeof(float)) % 16 || ((size_t)op.np_max * op.np_max * sizeof(float)) % 16 ||
+        (3 * DPF * DPF * sizeof(float)) % 16)
+        return false;
+    if (reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(Pinv) % 16) return false;
+    if (smem > 100 * 1024) return false;
+    if (cudaFuncSetAttribute(gs_tma_kernel<DPF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return true;
+}
+
 template <class T, int DPF>
 cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, const T *Pinv, int colour,
                       const T *g, T *u, cudaStream_t s) {
@@ -668,6 +820,17 @@ cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, cons
     int nt = ((op.np_max + 31) / 32) * 32;
     if (nt > 256) nt = 256;
     if (nt < 32) nt = 32;
+    if constexpr (std::is_same<T, float>::value && DPF >= 4) {
+        if (op.tma_flag && nt == 64 && tma_sweep_ok<DPF>(L, op, A, Pinv)) {
+            const size_t tsm = tma_sweep_smem<DPF>(L, op);
+            note_launches(1);
+            gs_tma_kernel<DPF><<<p1 - p0, 64, tsm, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
+                                                       L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
+                                                       L.patch_slot_src.p, L.cell_int.p, A, Pinv, g, u,
+                                                       op.tma_flag);
+            return cudaGetLastError();
+        }
+    }
     size_t smem = sizeof(T) * ((size_t)L.pc_max * 3 * DPF + op.np_max);
     note_launches(1);
     gs_kernel<T, DPF><<<p1 - p0, nt, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,

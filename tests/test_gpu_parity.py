@@ -99,6 +99,24 @@ def test_block_gs_sweep(level, reverse):
     assert rel(host(ud), uo) < 1e-11
 
 
+@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("mesh", [0, 2])
+def test_block_gs_sweep_mixed_order_k(k, mesh):
+    """The FP32 order-k sweep (bulk-copy staged where the patch sizes allow) against the
+    oracle's sequential block GS."""
+    hdg = _hdg()
+    ms, ts, ps, fv, ctx, F = setup_case(2, 3, k, precision=hdg.HDG_MIXED_FP32, **MESHES[mesh])
+    oh = HDG(ts[-1], k, gamma=100.0, beta=1.0)
+    gs = BlockGS(oh.matrix(), vertex_patches(oh.topo, oh.dpf))
+    rng = np.random.default_rng(12)
+    for reverse in (False, True):
+        g, u0 = rng.standard_normal((2, oh.n_dof))
+        uo = (gs.backward if reverse else gs.forward)(g, u0.copy())
+        ud = dev(u0)
+        hdg.hdg_smooth(ctx, -1, dev(g), ud, 1, reverse)
+        assert rel(host(ud), uo) < 2e-5
+
+
 def test_transfers_and_coarse_solve():
     hdg = _hdg()
     ms, ts, ps, fv, ctx, F = setup_case(2, 3, 1, jitter=0.3, seed=2, shuffle_seed=1)
