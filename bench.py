@@ -574,11 +574,10 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
     alg = sweep_bytes(ctx_mesh_fine(args), k, 4, 2 if half else 4)
     achieved = alg / t_sweep / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
-    # DRAM bytes of one sweep from an ncu capture of the same kernel (dram__bytes_read.sum +
-    # dram__bytes_write.sum over its three colour launches) on the 128x128, k = 3 case:
-    # 317,834,240 B against 318,199,104 algorithmic bytes there.  Traffic grows with the
-    # number of patches like the algorithmic bytes, so the full-size figure is that ratio
-    # times the full-size algorithmic bytes (k = 3 only; other k were not captured).
+    # DRAM bytes of one sweep from an ncu capture of the same kernel on the 128x128, k = 3 case
+    # (TMA_SWEEP_TRAFFIC_128).  Traffic grows with the number of patches like the algorithmic
+    # bytes, so the full-size figure is that ratio times the full-size algorithmic bytes
+    # (k = 3 only; other k were not captured).
     traffic = alg * (TMA_SWEEP_TRAFFIC_128 / 318199104) if k == 3 and not half and TMA_SWEEP_TRAFFIC_128 else None
     kname = "gs_kernel<float, 8, __half> (order-k block GS sweep on binary16 copies" if half else \
         "gs_tma_kernel<8> (order-k block GS sweep, matrices staged by cp.async.bulk"
@@ -594,8 +593,9 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the three colour launches of one
 # order-k sweep of gs_tma_kernel<8> from an ncu capture on the 128x128, k = 3 case, whose
-# algorithmic bytes are 318,199,104; None until captured for the current kernel.
-TMA_SWEEP_TRAFFIC_128 = None
+# algorithmic bytes are 318,199,104: 104,263,424 + 104,260,096 + 104,269,056 B read and
+# 2,776,576 + 100,352 + 85,760 B written (315,755,264 B, 0.992x).
+TMA_SWEEP_TRAFFIC_128 = 315755264
 
 
 def read_stream_gbs(torch, dev, stream):
