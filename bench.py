@@ -447,6 +447,11 @@ def batched_form(args, hdg, torch, dev, stream, world):
     F0 = F[0].contiguous()
     hdg.hdg_solve(ctx, F0)
     t1, (_, _, info1) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F0))
+    # the same loads with the order-k batched sweep on tensor cores (binary16 operands)
+    hdg.hdg_condense(ctx, hdg.Params(k=k, nu=1.0, beta=1.0, gamma=1e2, precision=hdg.HDG_MIXED_FP16))
+    hdg.hdg_solve_multi(ctx, F)
+    th, (_, _, infos_h) = _timed(torch, stream, lambda: hdg.hdg_solve_multi(ctx, F))
+    its_h = sum(i["krylov_its_total"] for i in infos_h)
     ctx.close()
     uneven = uneven_meshes_form(hdg, torch, dev, stream, world)
     return {"uneven_meshes": uneven,
@@ -457,7 +462,12 @@ def batched_form(args, hdg, torch, dev, stream, world):
             "dof_iters_per_s": sizes.n_dof * its * world / t,
             "single_load_time_to_tol_s": t1, "single_load_fgmres_iters": info1["krylov_its_total"],
             "single_load_dof_iters_per_s": sizes.n_dof * info1["krylov_its_total"] / t1,
-            "throughput_ratio_vs_single": (sizes.n_dof * its / t) / (sizes.n_dof * info1["krylov_its_total"] / t1)}
+            "throughput_ratio_vs_single": (sizes.n_dof * its / t) / (sizes.n_dof * info1["krylov_its_total"] / t1),
+            "tensor_core_fp16": {"time_to_tol_s": th, "fgmres_iters_total": its_h,
+                                 "dof_iters_per_s": sizes.n_dof * its_h * world / th,
+                                 "speedup_time_to_tol_vs_fp32": t / th,
+                                 "note": "HDG_MIXED_FP16: order-k batched sweep as mma.sync m16n8k16 with binary16 "
+                                         "operands and FP32 accumulation"}}
 
 
 def uneven_meshes_form(hdg, torch, dev, stream, world):

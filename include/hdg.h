@@ -275,8 +275,20 @@ hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, con
 /* Y = A^eps X. */
 hdg_status hdg_apply_multi(hdg_ctx *ctx, int nrhs, const double *x, double *y, hdg_stream_t stream);
 
-/* Z = MG_hp(R) column by column, in the precision chosen at hdg_condense. */
+/* Z = MG_hp(R) column by column, in the precision chosen at hdg_condense.  With
+ * HDG_MIXED_FP16 / HDG_MIXED_BF16, k = 3 and 9..64 columns the order-k sweeps
+ * run on tensor cores (mma.sync, 16-bit operands, FP32 accumulation, eq. bjac
+ * with GS as in hdg_smooth): the element rows and patch inverses come from the
+ * 16-bit row-scaled copies, and per patch the gathered unknowns and the patch
+ * residual of each column are rounded to the 16-bit format after a power-of-
+ * two scale that brings the column's largest magnitude into [1/2, 1). */
 hdg_status hdg_precond_apply_multi(hdg_ctx *ctx, int nrhs, const double *r, double *z, hdg_stream_t stream);
+
+/* hdg_smooth for nrhs columns: n_sweeps block-GS sweeps of level `level`
+ * (-1 = the order-k level) on U[r] with right-hand side G[r], in the sweep
+ * kernels hdg_precond_apply_multi uses. */
+hdg_status hdg_smooth_multi(hdg_ctx *ctx, int level, int nrhs, const double *g, double *u, int n_sweeps,
+                            int reverse, hdg_stream_t stream);
 
 /* hdg_solve for nrhs loads F[r] at once; u, p are initial guesses in and
  * solutions out; info: host array [nrhs] or NULL.  Returns

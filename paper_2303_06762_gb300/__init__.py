@@ -41,7 +41,7 @@ EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
            "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_apply_multi",
-           "hdg_precond_apply_multi", "hdg_solve_multi", "hdg_solve_batched", "hdg_picard", "hdg_newton",
+           "hdg_precond_apply_multi", "hdg_smooth_multi", "hdg_solve_multi", "hdg_solve_batched", "hdg_picard", "hdg_newton",
            "hdg_destroy",
            "hdg_status_string", "hdg_last_error")
 
@@ -139,6 +139,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "hdg_setup_mesh_hierarchy": (I, [ctypes.POINTER(_MeshDesc), I, ctypes.POINTER(P)]),
         "hdg_apply_multi": (I, [P, I, P, P, P]),
         "hdg_precond_apply_multi": (I, [P, I, P, P, P]),
+        "hdg_smooth_multi": (I, [P, I, I, P, P, I, I, P]),
         "hdg_solve_multi": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
         "hdg_solve_batched": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
         "hdg_picard": (I, [P, ctypes.POINTER(_Params), P, ctypes.c_double, I, P, P, ctypes.POINTER(SolveOpts),
@@ -337,6 +338,13 @@ def hdg_precond_apply_multi(ctx: Context, r, z=None, stream=None):
     z = torch.empty_like(r) if z is None else z
     ctx.check(load_library().hdg_precond_apply_multi(ctx.handle, r.shape[0], _ptr(r), _ptr(z), _stream(stream)))
     return z
+
+
+def hdg_smooth_multi(ctx: Context, level: int, g, u, n_sweeps: int = 1, reverse: bool = False, stream=None):
+    """hdg_smooth for g, u of shape [nrhs, n] (u updated in place)."""
+    ctx.check(load_library().hdg_smooth_multi(ctx.handle, level, g.shape[0], _ptr(g), _ptr(u), n_sweeps,
+                                              1 if reverse else 0, _stream(stream)))
+    return u
 
 
 def hdg_solve_multi(ctx: Context, F, u=None, p=None, opts: Optional[SolveOpts] = None, stream=None,

@@ -640,8 +640,16 @@ struct PrecM<float> {
 template <class T>
 void sweep_m(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, int R, const T *g, T *u, bool reverse,
              cudaStream_t s) {
+    bool tc = false;
+    if constexpr (std::is_same<T, float>::value) tc = gs_tc_supported(L, op, R);
     for (int i = 0; i < L.n_colours; ++i) {
         const int c = reverse ? L.n_colours - 1 - i : i;
+        if constexpr (std::is_same<T, float>::value) {
+            if (tc) {
+                CK(launch_gs_colour_tc(L, op, R, c, g, u, s));
+                continue;
+            }
+        }
         CK(launch_gs_colour_m<T>(L, op, R, Prec<T>::A(op), Prec<T>::P(op), c, g, u, s));
     }
 }
@@ -1613,6 +1621,40 @@ hdg_status hdg_precond_apply_multi(hdg_ctx *ctx, int nrhs, const double *r, doub
         CK(launch_pack_m(r, nrhs, n, R, ctx->mrd.p, s));
         precond_m(ctx, ctx->mrd.p, ctx->mzd.p, R, s);
         CK(launch_unpack_m(ctx->mzd.p, nrhs, n, R, z, s));
+    });
+}
+
+hdg_status hdg_smooth_multi(hdg_ctx *ctx, int level, int nrhs, const double *g, double *u, int n_sweeps,
+                            int reverse, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(level >= -1 && level < ctx->n_levels, "level out of range");
+        REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, "nrhs out of range 1..64");
+        REQUIRE(g && u && n_sweeps >= 0, "bad arguments");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int R = pad_width(nrhs);
+        const int J = ctx->n_levels - 1;
+        const DevLevel &L = ctx->L[level < 0 ? J : level];
+        const DevOperator &op = level < 0 ? ctx->opk : L.op0;
+        const int64_t n = L.n_int * op.dpf;
+        const size_t nR = (size_t)std::max<int64_t>(n, 1) * R;
+        dalloc(ctx, ctx->mrd, nR);
+        dalloc(ctx, ctx->mzd, nR);
+        CK(launch_pack_m(g, nrhs, n, R, ctx->mrd.p, s));
+        CK(launch_pack_m(u, nrhs, n, R, ctx->mzd.p, s));
+        if (ctx->prm.precision == HDG_FP64) {
+            for (int i = 0; i < n_sweeps; ++i) sweep_m<double>(ctx, L, op, R, ctx->mrd.p, ctx->mzd.p, reverse != 0, s);
+        } else {
+            dalloc(ctx, ctx->mkgf, nR);
+            dalloc(ctx, ctx->mkuf, nR);
+            CK((launch_convert_m<double, float>(ctx->mrd.p, ctx->mkgf.p, (int64_t)nR, s)));
+            CK((launch_convert_m<double, float>(ctx->mzd.p, ctx->mkuf.p, (int64_t)nR, s)));
+            for (int i = 0; i < n_sweeps; ++i)
+                sweep_m<float>(ctx, L, op, R, ctx->mkgf.p, ctx->mkuf.p, reverse != 0, s);
+            CK((launch_convert_m<float, double>(ctx->mkuf.p, ctx->mzd.p, (int64_t)nR, s)));
+        }
+        CK(launch_unpack_m(ctx->mzd.p, nrhs, n, R, u, s));
     });
 }
 

@@ -364,6 +364,12 @@ cudaError_t launch_split_lo(const double *A, const float *hi, float *lo, int64_t
 template <class T>
 cudaError_t launch_apply_m(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *x, const T *g, T *y,
                            cudaStream_t s);
+// batched order-k colour phase on tensor cores (multi_tc.cu): for operators with 16-bit
+// copies (op.h_fmt), dpf = 8 and R in {16, 32, 64}
+bool gs_tc_supported(const DevLevel &L, const DevOperator &op, int R);
+cudaError_t launch_gs_colour_tc(const DevLevel &L, const DevOperator &op, int R, int colour, const float *g,
+                                float *u, cudaStream_t s);
+int log2_width(int R);
 template <class T>
 cudaError_t launch_gs_colour_m(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *Pinv,
                                int colour, const T *g, T *u, cudaStream_t s);

@@ -4,7 +4,7 @@ both round to nearest with ties to even."""
 import numpy as np
 import pytest
 
-from _round16 import round_sig, pow2_row_scale, stored_rows
+from _round16 import round_sig, pow2_row_scale, stored_rows, _col_round
 
 
 def _values(rng, n):
@@ -50,3 +50,14 @@ def test_row_scales_are_powers_of_two():
         Ms = stored_rows(M, fmt)
         # error at most half a unit of the row's leading binade (normal range of the scaled rows)
         assert np.all(np.abs(Ms - M) <= 0.5 * 2.0 ** -bits * s[:, None] * (1 + 1e-12))
+
+
+def test_column_rounding():
+    rng = np.random.default_rng(3)
+    v = rng.standard_normal(50) * 1e5
+    for fmt, bits in (("fp16", 11), ("bf16", 8)):
+        q = _col_round(v, fmt)
+        s = pow2_row_scale(v[None, :])[0]
+        assert np.all(np.abs(q - v) <= 0.5 * 2.0 ** -bits * s * (1 + 1e-12))
+        assert np.array_equal(_col_round(q, fmt), q)     # idempotent
+    assert np.array_equal(_col_round(np.zeros(4), "fp16"), np.zeros(4))
