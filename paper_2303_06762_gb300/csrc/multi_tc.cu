@@ -96,7 +96,7 @@ __device__ __forceinline__ float col_scale(unsigned mx, float &s) {
 }
 
 struct TcLayout {
-    size_t xt, as, ps, rs, rf, asc, psc, cmx, rmx, jt, rowF, sslot, total;
+    size_t xt, as, ps, rs, rf, asc, psc, cmx, rmx, xsc, rsc, roff, rowF, sslot, total;
 };
 
 // shared-memory layout (byte offsets, each a multiple of 16)
@@ -114,7 +114,9 @@ __host__ __device__ inline TcLayout tc_layout(int pf_max, int pc_max, int np_max
     o.psc = at;  at = up(at + 4 * (size_t)np_max);
     o.cmx = at;  at = up(at + 4 * (size_t)R);
     o.rmx = at;  at = up(at + 4 * (size_t)R);
-    o.jt = at;   at = up(at + 4 * (size_t)pc_max * 3);
+    o.xsc = at;  at = up(at + 4 * (size_t)2 * R);
+    o.rsc = at;  at = up(at + 4 * (size_t)2 * R);
+    o.roff = at; at = up(at + 4 * (size_t)pc_max * TC_NLOC);
     o.rowF = at; at = up(at + 4 * (size_t)pf_max);
     o.sslot = at; at = up(at + 4 * (size_t)2 * pf_max);
     o.total = at;
@@ -142,7 +144,9 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
     float *psc = reinterpret_cast<float *>(smraw + L.psc);
     unsigned *cmx = reinterpret_cast<unsigned *>(smraw + L.cmx);
     unsigned *rmx = reinterpret_cast<unsigned *>(smraw + L.rmx);
-    int *jt = reinterpret_cast<int *>(smraw + L.jt);
+    float *xsc = reinterpret_cast<float *>(smraw + L.xsc);   // [r]: scale, [R + r]: its inverse
+    float *rsc = reinterpret_cast<float *>(smraw + L.rsc);
+    int *roff = reinterpret_cast<int *>(smraw + L.roff);     // star slot -> first row of u, or -1
     int *rowF = reinterpret_cast<int *>(smraw + L.rowF);
     int *sslot = reinterpret_cast<int *>(smraw + L.sslot);
 
@@ -152,9 +156,11 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
     constexpr int NW = TC_THREADS / 32;
     const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
 
-    for (int i = tid; i < ncell * 3; i += TC_THREADS) {
-        const int c = patch_cells[(size_t)p * pc_max + i / 3];
-        jt[i] = cell_int[3 * c + i % 3];
+    for (int i = tid; i < ncell * NLOC; i += TC_THREADS) {
+        const int si = i / NLOC, l = i - si * NLOC;
+        const int c = patch_cells[(size_t)p * pc_max + si];
+        const int j = cell_int[3 * c + l / DPF];
+        roff[i] = j >= 0 ? (j * DPF + l % DPF) << lgR : -1;
     }
     for (int i = tid; i < R; i += TC_THREADS) cmx[i] = rmx[i] = 0u;
     for (int js = tid; js < nf; js += TC_THREADS) rowF[js] = patch_facets[(size_t)p * pf_max + js];
@@ -184,22 +190,30 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
     for (int i = tid; i < np; i += TC_THREADS) psc[i] = Ph_s[(size_t)p * np_max + i];
     __syncthreads();
 
-    // gathered unknowns of the star: column maxima, then the scaled 16-bit Xᵀ
+    // gathered unknowns of the star: column maxima (the thread's column is fixed, since
+    // the block size is a multiple of R: one shared atomic per thread), per-column scales,
+    // then the scaled 16-bit Xᵀ
     const int nx = (ncell * NLOC) << lgR;
-    for (int t = tid; t < nx; t += TC_THREADS) {
-        const int r = t & (R - 1), sl = t >> lgR, si = sl / NLOC, l = sl - si * NLOC;
-        const int j = jt[si * 3 + l / DPF];
-        const float v = j >= 0 ? u[(((size_t)j * DPF + l % DPF) << lgR) + r] : 0.f;
-        atomicMax(&cmx[r], __float_as_uint(fabsf(v)));
+    {
+        float m = 0.f;
+        for (int t = tid; t < nx; t += TC_THREADS) {
+            const int o = roff[t >> lgR];
+            if (o >= 0) m = fmaxf(m, fabsf(u[o + (t & (R - 1))]));
+        }
+        atomicMax(&cmx[tid & (R - 1)], __float_as_uint(m));
+    }
+    __syncthreads();
+    for (int r = tid; r < R; r += TC_THREADS) {
+        float sc;
+        xsc[R + r] = col_scale(cmx[r], sc);
+        xsc[r] = sc;
     }
     __syncthreads();
     for (int t = tid; t < nx; t += TC_THREADS) {
         const int r = t & (R - 1), sl = t >> lgR, si = sl / NLOC, l = sl - si * NLOC;
-        const int j = jt[si * 3 + l / DPF];
-        const float v = j >= 0 ? u[(((size_t)j * DPF + l % DPF) << lgR) + r] : 0.f;
-        float s;
-        const float inv = col_scale(cmx[r], s);
-        XT[((size_t)si * R + r) * TC_XS + l] = Mma<H>::from(v * inv);
+        const int o = roff[sl];
+        const float v = o >= 0 ? u[o + r] : 0.f;
+        XT[((size_t)si * R + r) * TC_XS + l] = Mma<H>::from(v * xsc[R + r]);
     }
     __syncthreads();
 
@@ -226,8 +240,8 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int r = rt * 16 + g8 + 8 * h;
-            float s;
-            col_scale(cmx[r], s);
+            const float s = xsc[r];
+            float m = 0.f;
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int d = 2 * t4 + e;
@@ -235,16 +249,24 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
                                    asc[(2 * js + 1) * DPF + d] * acc[1][2 * h + e];
                 const float v = g[(((size_t)F * DPF + d) << lgR) + r] - s * prod;
                 RF[(size_t)(js * DPF + d) * R + r] = v;
-                atomicMax(&rmx[r], __float_as_uint(fabsf(v)));
+                m = fmaxf(m, fabsf(v));
             }
+            // the four lanes of a quad hold the 8 rows of column r
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, 2));
+            if (t4 == 0) atomicMax(&rmx[r], __float_as_uint(m));
         }
+    }
+    __syncthreads();
+    for (int r = tid; r < R; r += TC_THREADS) {
+        float sc;
+        rsc[R + r] = col_scale(rmx[r], sc);
+        rsc[r] = sc;
     }
     __syncthreads();
     for (int t = tid; t < (np << lgR); t += TC_THREADS) {
         const int j = t >> lgR, r = t & (R - 1);
-        float s;
-        const float inv = col_scale(rmx[r], s);
-        RS[(size_t)r * psd + j] = Mma<H>::from(RF[t] * inv);
+        RS[(size_t)r * psd + j] = Mma<H>::from(RF[t] * rsc[R + r]);
     }
     __syncthreads();
 
@@ -270,8 +292,7 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int r = rt * 16 + g8 + 8 * h;
-            float s;
-            col_scale(rmx[r], s);
+            const float s = rsc[r];
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int n = nt * 8 + 2 * t4 + e;
