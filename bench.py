@@ -60,8 +60,12 @@ def parse():
     ap.add_argument("--profile-solve", action="store_true",
                     help="condense, then one warm-up and one timed mixed-precision solve only "
                          "(the command profiled for the kernel launch list)")
+    ap.add_argument("--profile-precond-multi", action="store_true",
+                    help="condense (--N, --k, --precision), then apply the batched preconditioner twice to 64 "
+                         "seeded random columns (the command profiled for the batched smoother)")
     ap.add_argument("--precision", type=int, default=1,
-                    help="preconditioner precision of --profile-solve (hdg_precision value)")
+                    help="preconditioner precision of --profile-solve / --profile-precond-multi "
+                         "(hdg_precision value)")
     return ap.parse_args()
 
 
@@ -641,10 +645,30 @@ def profile_solve(args):
     ctx.close()
 
 
+def profile_precond_multi(args):
+    import torch
+    import paper_2303_06762_gb300 as hdg
+    ms, _ = workload(args)
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    hdg.hdg_condense(ctx, hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma,
+                                     precision=args.precision))
+    gen = torch.Generator(device="cuda:0").manual_seed(1)
+    X = torch.randn((64, ctx.sizes().n_dof), dtype=torch.float64, device="cuda:0", generator=gen)
+    for _ in range(2):
+        Z = hdg.hdg_precond_apply_multi(ctx, X)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_precond_multi": True, "N": args.N, "k": args.k, "precision": args.precision,
+                      "max_abs": float(Z.abs().max())}))
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.profile_solve:
         profile_solve(args)
+        return
+    if args.profile_precond_multi:
+        profile_precond_multi(args)
         return
     if args.impl == "reference":
         reference_arm(args)
