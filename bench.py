@@ -445,6 +445,7 @@ def batched_form(args, hdg, torch, dev, stream, world):
                      for j in range(nrhs)])
     del X, Xf
     sizes = ctx.sizes()
+    rb, nt, tile_ms = hdg.hdg_tune_batched(ctx, nrhs)  # the tile the autotuner keeps for this width
     hdg.hdg_solve_multi(ctx, F)                      # warm-up (graph capture, allocation)
     t, (U, P, infos) = _timed(torch, stream, lambda: hdg.hdg_solve_multi(ctx, F))
     its = sum(i["krylov_its_total"] for i in infos)
@@ -467,6 +468,7 @@ def batched_form(args, hdg, torch, dev, stream, world):
             "single_load_time_to_tol_s": t1, "single_load_fgmres_iters": info1["krylov_its_total"],
             "single_load_dof_iters_per_s": sizes.n_dof * info1["krylov_its_total"] / t1,
             "throughput_ratio_vs_single": (sizes.n_dof * its / t) / (sizes.n_dof * info1["krylov_its_total"] / t1),
+            "autotuned_tile": {"rows_per_thread": rb, "threads": nt, "colour_phase_ms": tile_ms},
             "tensor_core_fp16": {"time_to_tol_s": th, "fgmres_iters_total": its_h,
                                  "dof_iters_per_s": sizes.n_dof * its_h * world / th,
                                  "speedup_time_to_tol_vs_fp32": t / th,

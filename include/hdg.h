@@ -290,6 +290,20 @@ hdg_status hdg_precond_apply_multi(hdg_ctx *ctx, int nrhs, const double *r, doub
 hdg_status hdg_smooth_multi(hdg_ctx *ctx, int level, int nrhs, const double *g, double *u, int n_sweeps,
                             int reverse, hdg_stream_t stream);
 
+/* Tile of the batched order-k sweep on CUDA cores (the FP64 and FP32 forms):
+ * rows of one column per thread (1, 2 or 4, dividing 2(k+1)) and threads per
+ * block (128 or 256).  By default an autotuner picks it at the first batched
+ * preconditioner application for each precision and padded width: it times one
+ * colour phase of the finest level for every pair on scratch vectors and keeps
+ * the fastest.  All pairs give bitwise-identical results.
+ * hdg_set_batched_tile forces a pair for this context (0, 0 = back to the
+ * autotuner).  hdg_tune_batched runs the autotuner now for width nrhs and
+ * returns its choice and the time of one colour phase in ms (0, 0, 0 when the
+ * sweep of that width runs on tensor cores or k = 0); outputs may be NULL. */
+hdg_status hdg_set_batched_tile(hdg_ctx *ctx, int rows_per_thread, int threads);
+hdg_status hdg_tune_batched(hdg_ctx *ctx, int nrhs, int *rows_per_thread, int *threads, double *ms,
+                            hdg_stream_t stream);
+
 /* hdg_solve for nrhs loads F[r] at once; u, p are initial guesses in and
  * solutions out; info: host array [nrhs] or NULL.  Returns
  * HDG_ERR_NOT_CONVERGED when some column reaches max_uzawa or max_it. */

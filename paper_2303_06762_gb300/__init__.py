@@ -41,7 +41,7 @@ EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
            "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_apply_multi",
-           "hdg_precond_apply_multi", "hdg_smooth_multi", "hdg_solve_multi", "hdg_solve_batched", "hdg_picard", "hdg_newton",
+           "hdg_precond_apply_multi", "hdg_smooth_multi", "hdg_set_batched_tile", "hdg_tune_batched", "hdg_solve_multi", "hdg_solve_batched", "hdg_picard", "hdg_newton",
            "hdg_destroy",
            "hdg_status_string", "hdg_last_error")
 
@@ -140,6 +140,9 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "hdg_apply_multi": (I, [P, I, P, P, P]),
         "hdg_precond_apply_multi": (I, [P, I, P, P, P]),
         "hdg_smooth_multi": (I, [P, I, I, P, P, I, I, P]),
+        "hdg_set_batched_tile": (I, [P, I, I]),
+        "hdg_tune_batched": (I, [P, I, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                 ctypes.POINTER(ctypes.c_double), P]),
         "hdg_solve_multi": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
         "hdg_solve_batched": (I, [P, I, P, P, P, ctypes.POINTER(SolveOpts), P, P]),
         "hdg_picard": (I, [P, ctypes.POINTER(_Params), P, ctypes.c_double, I, P, P, ctypes.POINTER(SolveOpts),
@@ -345,6 +348,19 @@ def hdg_smooth_multi(ctx: Context, level: int, g, u, n_sweeps: int = 1, reverse:
     ctx.check(load_library().hdg_smooth_multi(ctx.handle, level, g.shape[0], _ptr(g), _ptr(u), n_sweeps,
                                               1 if reverse else 0, _stream(stream)))
     return u
+
+
+def hdg_set_batched_tile(ctx: Context, rows_per_thread: int = 0, threads: int = 0):
+    """Force the batched order-k sweep's tile (0, 0 = autotuner)."""
+    ctx.check(load_library().hdg_set_batched_tile(ctx.handle, rows_per_thread, threads))
+
+
+def hdg_tune_batched(ctx: Context, nrhs: int, stream=None):
+    """Run the batched-sweep autotuner now; returns (rows_per_thread, threads, ms per colour phase)."""
+    rb, nt, ms = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_double(0.0)
+    ctx.check(load_library().hdg_tune_batched(ctx.handle, nrhs, ctypes.byref(rb), ctypes.byref(nt), ctypes.byref(ms),
+                                              _stream(stream)))
+    return rb.value, nt.value, ms.value
 
 
 def hdg_solve_multi(ctx: Context, F, u=None, p=None, opts: Optional[SolveOpts] = None, stream=None,

@@ -637,9 +637,85 @@ struct PrecM<float> {
     }
 };
 
+// tile of the batched order-k sweep for this precision and width (0, 0 = defaults)
+template <class T>
+void tile_of(const hdg_ctx *ctx, int R, int &rb, int &nt) {
+    if (ctx->tile_force_rb || ctx->tile_force_nt) {
+        rb = ctx->tile_force_rb;
+        nt = ctx->tile_force_nt;
+        return;
+    }
+    const int pi = std::is_same<T, double>::value ? 0 : 1, li = log2_width(R);
+    rb = ctx->tile_rb[pi][li];
+    nt = ctx->tile_nt[pi][li];
+}
+
+// Autotuner of the batched order-k sweep on CUDA cores: times one colour phase of the
+// finest level (the colour with the most patches) on scratch vectors for every rows-
+// per-thread / block-size pair and keeps the fastest for this precision and width.
+// The pairs give bitwise-identical results (each row's sums run in the same order).
+template <class T>
+void tune_gs_m(hdg_ctx *ctx, int R, cudaStream_t s) {
+    const int pi = std::is_same<T, double>::value ? 0 : 1, li = log2_width(R);
+    const DevLevel &L = ctx->L[ctx->n_levels - 1];
+    const DevOperator &op = ctx->opk;
+    const size_t n = (size_t)std::max<int64_t>(ctx->n_dof, 1) * R;
+    dalloc(ctx, ctx->tune_buf, sizeof(T) == sizeof(double) ? 2 * n : n);   // two T vectors of n values
+    T *g = reinterpret_cast<T *>(ctx->tune_buf.p), *u = g + n;
+    CK(cudaMemsetAsync(ctx->tune_buf.p, 0, 2 * n * sizeof(T), s));
+    int colour = 0;
+    for (int c = 1; c < L.n_colours; ++c)
+        if (L.colour_ptr[c + 1] - L.colour_ptr[c] > L.colour_ptr[colour + 1] - L.colour_ptr[colour]) colour = c;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int brb = 0, bnt = 0;
+    for (int rb : {1, 2, 4}) {
+        if (op.dpf % rb) continue;
+        for (int nt : {128, 256}) {
+            CK(launch_gs_colour_m<T>(L, op, R, Prec<T>::A(op), Prec<T>::P(op), colour, g, u, s, rb, nt));
+            CK(cudaEventRecord(e0, s));
+            for (int it = 0; it < 3; ++it)
+                CK(launch_gs_colour_m<T>(L, op, R, Prec<T>::A(op), Prec<T>::P(op), colour, g, u, s, rb, nt));
+            CK(cudaEventRecord(e1, s));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms / 3 < best) {
+                best = ms / 3;
+                brb = rb;
+                bnt = nt;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tile_rb[pi][li] = brb;
+    ctx->tile_nt[pi][li] = bnt;
+    ctx->tile_ms[pi][li] = best;
+}
+
+// tunes the batched order-k sweep of the current precision for width R unless it is
+// done, forced, or the sweep runs on tensor cores; false if the stream is capturing
+bool ensure_tuned(hdg_ctx *ctx, int R, cudaStream_t s) {
+    if (ctx->tile_force_rb || ctx->tile_force_nt || ctx->prm.k == 0) return true;
+    const bool fp64 = ctx->prm.precision == HDG_FP64;
+    if (!fp64 && gs_tc_supported(ctx->L[ctx->n_levels - 1], ctx->opk, R)) return true;
+    if (ctx->tile_rb[fp64 ? 0 : 1][log2_width(R)]) return true;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return false;
+    if (fp64) tune_gs_m<double>(ctx, R, s);
+    else tune_gs_m<float>(ctx, R, s);
+    return true;
+}
+
 template <class T>
 void sweep_m(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, int R, const T *g, T *u, bool reverse,
              cudaStream_t s) {
+    int rb = 0, nt = 0;
+    if (&op == &ctx->opk) tile_of<T>(ctx, R, rb, nt);
     bool tc = false;
     if constexpr (std::is_same<T, float>::value) tc = gs_tc_supported(L, op, R);
     for (int i = 0; i < L.n_colours; ++i) {
@@ -650,7 +726,7 @@ void sweep_m(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, int R, cons
                 continue;
             }
         }
-        CK(launch_gs_colour_m<T>(L, op, R, Prec<T>::A(op), Prec<T>::P(op), c, g, u, s));
+        CK(launch_gs_colour_m<T>(L, op, R, Prec<T>::A(op), Prec<T>::P(op), c, g, u, s, rb, nt));
     }
 }
 
@@ -737,6 +813,7 @@ void precond_m(hdg_ctx *ctx, const double *r, double *z, int R, cudaStream_t s) 
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(s, &cs));
     ensure_multi_work(ctx, R);
+    ensure_tuned(ctx, R, s);
     if (cs != cudaStreamCaptureStatusNone) {
         precond_m_direct(ctx, r, z, R, s);
         return;
@@ -1157,7 +1234,7 @@ void hdg_destroy(hdg_ctx *ctx) {
     for (auto *b : {&ctx->mV, &ctx->mZ, &ctx->mw, &ctx->mpart, &ctx->msmall, &ctx->mhbuf, &ctx->mF, &ctx->mU,
                     &ctx->mP, &ctx->mG, &ctx->mkr, &ctx->mkt, &ctx->mrd, &ctx->mzd, &ctx->pcm_in, &ctx->pcm_out})
         dfree(*b);
-    dfree(ctx->mkgf); dfree(ctx->mkuf); dfree(ctx->mkrf); dfree(ctx->mint); dfree(ctx->mxs);
+    dfree(ctx->mkgf); dfree(ctx->mkuf); dfree(ctx->mkrf); dfree(ctx->mint); dfree(ctx->mxs); dfree(ctx->tune_buf);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     if (ctx->batch_stream) cudaStreamDestroy(ctx->batch_stream);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
@@ -1203,6 +1280,9 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
     const hdg_params *prm = &ctx->prm;
     ctx->condensed = false;
     drop_graph(ctx);
+    std::memset(ctx->tile_rb, 0, sizeof ctx->tile_rb);   // a new operator is tuned afresh
+    std::memset(ctx->tile_nt, 0, sizeof ctx->tile_nt);
+    std::memset(ctx->tile_ms, 0, sizeof ctx->tile_ms);
     const int k = prm->k;
     upload_ref(ctx, ctx->ref0, ctx->ref0_dev, 0);
     upload_ref(ctx, ctx->refk, ctx->refk_dev, k);
@@ -1655,6 +1735,49 @@ hdg_status hdg_smooth_multi(hdg_ctx *ctx, int level, int nrhs, const double *g, 
             CK((launch_convert_m<float, double>(ctx->mkuf.p, ctx->mzd.p, (int64_t)nR, s)));
         }
         CK(launch_unpack_m(ctx->mzd.p, nrhs, n, R, u, s));
+    });
+}
+
+hdg_status hdg_set_batched_tile(hdg_ctx *ctx, int rows_per_thread, int threads) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        REQUIRE(rows_per_thread == 0 || rows_per_thread == 1 || rows_per_thread == 2 || rows_per_thread == 4,
+                "rows_per_thread must be 0, 1, 2 or 4");
+        REQUIRE(threads == 0 || threads == 128 || threads == 256, "threads must be 0, 128 or 256");
+        REQUIRE((rows_per_thread == 0) == (threads == 0), "give both or neither");
+        REQUIRE(rows_per_thread == 0 || ctx->prm.k == 0 || ctx->opk.dpf % rows_per_thread == 0 || !ctx->condensed,
+                "rows_per_thread must divide 2(k+1)");
+        ctx->tile_force_rb = rows_per_thread;
+        ctx->tile_force_nt = threads;
+        drop_graph(ctx);
+    });
+}
+
+hdg_status hdg_tune_batched(hdg_ctx *ctx, int nrhs, int *rows_per_thread, int *threads, double *ms,
+                            hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, "nrhs out of range 1..64");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int R = pad_width(nrhs), li = log2_width(R), pi = ctx->prm.precision == HDG_FP64 ? 0 : 1;
+        const int frb = ctx->tile_force_rb, fnt = ctx->tile_force_nt;
+        ctx->tile_force_rb = ctx->tile_force_nt = 0;
+        ctx->tile_rb[pi][li] = ctx->tile_nt[pi][li] = 0;
+        ctx->tile_ms[pi][li] = 0.0;
+        try {
+            ensure_tuned(ctx, R, s);
+        } catch (...) {
+            ctx->tile_force_rb = frb;
+            ctx->tile_force_nt = fnt;
+            throw;
+        }
+        ctx->tile_force_rb = frb;
+        ctx->tile_force_nt = fnt;
+        drop_graph(ctx);
+        if (rows_per_thread) *rows_per_thread = ctx->tile_rb[pi][li];
+        if (threads) *threads = ctx->tile_nt[pi][li];
+        if (ms) *ms = ctx->tile_ms[pi][li];
     });
 }
 

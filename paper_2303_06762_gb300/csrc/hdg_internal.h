@@ -236,6 +236,12 @@ struct hdg_ctx {
     hdg::DBuf<int> mint;                      // per-column ints (m_r, frozen flags)
     cudaGraphExec_t pcm_exec = nullptr;      // graph of one multi preconditioner application
     int pcm_prec = -1, pcm_R = 0;
+    // tile of the batched order-k sweep on CUDA cores (rows per thread, threads per block):
+    // forced by hdg_set_batched_tile, else chosen by the autotuner per (FP64 or FP32, log2 R)
+    int tile_force_rb = 0, tile_force_nt = 0;
+    int tile_rb[2][7] = {}, tile_nt[2][7] = {};
+    double tile_ms[2][7] = {};
+    hdg::DBuf<double> tune_buf;
     long long pcm_kernels = 0;
     hdg::DBuf<double> pcm_in, pcm_out;
     cudaStream_t batch_stream = nullptr;     // private stream for hdg_solve_batched
@@ -372,7 +378,8 @@ cudaError_t launch_gs_colour_tc(const DevLevel &L, const DevOperator &op, int R,
 int log2_width(int R);
 template <class T>
 cudaError_t launch_gs_colour_m(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *Pinv,
-                               int colour, const T *g, T *u, cudaStream_t s);
+                               int colour, const T *g, T *u, cudaStream_t s, int rb = 0, int nt = 0);
+                               // rb: rows per thread (divisor of dpf; 0 = default), nt: threads per block (0 = 256)
 template <class T>
 cudaError_t launch_hp_restrict_m(int k, int64_t n_int, int R, const T *r, T *r0, cudaStream_t s);
 template <class T>

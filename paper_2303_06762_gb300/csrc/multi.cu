@@ -792,7 +792,7 @@ size_t gs_m_smem(const DevLevel &L, const DevOperator &op, int R, size_t word) {
 namespace {
 template <class T, int DPF, int RB>
 cudaError_t gs_m_launch(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *Pinv, int colour,
-                        const T *g, T *u, cudaStream_t s) {
+                        const T *g, T *u, int nt, cudaStream_t s) {
     const int p0 = L.colour_ptr[colour], p1 = L.colour_ptr[colour + 1];
     if (p1 <= p0) return cudaSuccess;
     const size_t smem = gs_m_smem(L, op, R, sizeof(T));
@@ -800,22 +800,39 @@ cudaError_t gs_m_launch(const DevLevel &L, const DevOperator &op, int R, const T
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launches(1);
-    kern<<<p1 - p0, MT, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, log2_width(R), L.patch_nf.p,
+    kern<<<p1 - p0, nt, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, log2_width(R), L.patch_nf.p,
                                    L.patch_facets.p, L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p,
                                    A, Pinv, g, u);
     return cudaGetLastError();
+}
+
+// rows per thread (RB, a divisor of dpf) of the batched sweep: the tile shape the
+// autotuner chooses from; 0 picks the default of each dpf
+template <class T, int DPF>
+cudaError_t gs_m_rb(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *Pinv, int colour,
+                    const T *g, T *u, int rb, int nt, cudaStream_t s) {
+    if (rb == 0) rb = (DPF % 4 == 0) ? 4 : 2;
+    if (DPF % rb != 0) return cudaErrorInvalidValue;
+    switch (rb) {
+    case 1: return gs_m_launch<T, DPF, 1>(L, op, R, A, Pinv, colour, g, u, nt, s);
+    case 2: return gs_m_launch<T, DPF, (DPF % 2 == 0 ? 2 : 1)>(L, op, R, A, Pinv, colour, g, u, nt, s);
+    case 4: return gs_m_launch<T, DPF, (DPF % 4 == 0 ? 4 : 1)>(L, op, R, A, Pinv, colour, g, u, nt, s);
+    default: return cudaErrorInvalidValue;
+    }
 }
 } // namespace
 
 template <class T>
 cudaError_t launch_gs_colour_m(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *Pinv,
-                               int colour, const T *g, T *u, cudaStream_t s) {
+                               int colour, const T *g, T *u, cudaStream_t s, int rb, int nt) {
+    if (nt == 0) nt = MT;
+    if (nt % 32 != 0 || nt < 32 || nt > MT) return cudaErrorInvalidValue;   // MT: the launch bound
     switch (op.dpf) {
-    case 2: return gs_m_launch<T, 2, 2>(L, op, R, A, Pinv, colour, g, u, s);
-    case 4: return gs_m_launch<T, 4, 4>(L, op, R, A, Pinv, colour, g, u, s);
-    case 6: return gs_m_launch<T, 6, 2>(L, op, R, A, Pinv, colour, g, u, s);
-    case 8: return gs_m_launch<T, 8, 4>(L, op, R, A, Pinv, colour, g, u, s);
-    case 10: return gs_m_launch<T, 10, 2>(L, op, R, A, Pinv, colour, g, u, s);
+    case 2: return gs_m_rb<T, 2>(L, op, R, A, Pinv, colour, g, u, rb, nt, s);
+    case 4: return gs_m_rb<T, 4>(L, op, R, A, Pinv, colour, g, u, rb, nt, s);
+    case 6: return gs_m_rb<T, 6>(L, op, R, A, Pinv, colour, g, u, rb, nt, s);
+    case 8: return gs_m_rb<T, 8>(L, op, R, A, Pinv, colour, g, u, rb, nt, s);
+    case 10: return gs_m_rb<T, 10>(L, op, R, A, Pinv, colour, g, u, rb, nt, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -998,7 +1015,7 @@ cudaError_t launch_uzawa_update_m(const DevLevel &L, int k, int R, const double 
     template cudaError_t launch_apply_m<T>(const DevLevel &, const DevOperator &, int, const T *, const T *,        \
                                            const T *, T *, cudaStream_t);                                          \
     template cudaError_t launch_gs_colour_m<T>(const DevLevel &, const DevOperator &, int, const T *, const T *,    \
-                                               int, const T *, T *, cudaStream_t);                                 \
+                                               int, const T *, T *, cudaStream_t, int, int);                       \
     template cudaError_t launch_hp_restrict_m<T>(int, int64_t, int, const T *, T *, cudaStream_t);                  \
     template cudaError_t launch_hp_prolong_add_m<T>(int, int64_t, int, const T *, T *, cudaStream_t);               \
     template cudaError_t launch_prolong_add_m<T>(const DevLevel &, const DevLevel &, int, const T *, const T *,     \

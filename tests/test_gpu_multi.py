@@ -184,3 +184,24 @@ def test_full_size_batched_sampled_parity():
     Z = hdg.hdg_precond_apply_multi(ctx, X)
     for r in (0, 63):
         assert rel(host(Z[r]), host(hdg.hdg_precond_apply(ctx, X[r].contiguous()))) < 1e-4
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batched_tile_autotuner(precision):
+    """The autotuner returns one of the candidate tiles, and every tile of the batched
+    order-k sweep gives bitwise the same preconditioner."""
+    hdg = _hdg()
+    ms, ts, ps, fvs, ctx, F, _ = _setup(2, 3, 3, 8, precision=precision, shuffle_seed=5)
+    gen = torch.Generator(device=DEV).manual_seed(2)
+    X = torch.randn(F.shape, dtype=torch.float64, device=DEV, generator=gen)
+    rb, nt, t = hdg.hdg_tune_batched(ctx, 8)
+    assert rb in (1, 2, 4) and nt in (128, 256) and t > 0
+    Z = host(hdg.hdg_precond_apply_multi(ctx, X))
+    for rb2 in (1, 2, 4):
+        for nt2 in (128, 256):
+            hdg.hdg_set_batched_tile(ctx, rb2, nt2)
+            assert np.array_equal(host(hdg.hdg_precond_apply_multi(ctx, X)), Z)
+    hdg.hdg_set_batched_tile(ctx, 0, 0)
+    assert np.array_equal(host(hdg.hdg_precond_apply_multi(ctx, X)), Z)
+    with pytest.raises(hdg.HdgError):
+        hdg.hdg_set_batched_tile(ctx, 3, 128)
