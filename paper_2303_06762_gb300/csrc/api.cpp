@@ -84,7 +84,7 @@ void free_operator(DevOperator &op) {
 void free_level(DevLevel &L) {
     dfree(L.coords); dfree(L.cells); dfree(L.cell_int); dfree(L.facet_adj); dfree(L.cell_d); dfree(L.cell_nu);
     dfree(L.cell_area); dfree(L.conv_flux); dfree(L.conv_lat); dfree(L.patch_nf); dfree(L.patch_facets); dfree(L.patch_nc);
-    dfree(L.patch_cells); dfree(L.patch_slot_src);
+    dfree(L.patch_cells); dfree(L.patch_slot_src); dfree(L.gs0_table);
     free_operator(L.op0);
     dfree(L.tr_slots); dfree(L.tr_nbr); dfree(L.tr_children); dfree(L.tr_child_slot);
     dfree(L.tr_fineB); dfree(L.tr_fineB_src); dfree(L.tr_W); dfree(L.tr_H); dfree(L.tr_Wf);
@@ -1176,6 +1176,25 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
             upload(ctx, L.patch_nc, H.patch_nc);
             upload(ctx, L.patch_cells, H.patch_cells);
             upload(ctx, L.patch_slot_src, H.patch_slot_src);
+            if (H.nc <= GS0_TABLE_MAX_CELLS && 2 * H.pf_max <= 16) {
+                // lowest-order gather table: each lane of the sweep reads its row's whole
+                // gather pattern at once instead of chasing patch -> cell -> facet indices
+                const int npm = 2 * H.pf_max;
+                std::vector<int32_t> tb((size_t)H.n_patches * npm * GS0_TABLE_INTS, -1);
+                for (int p = 0; p < H.n_patches; ++p)
+                    for (int t = 0; t < 2 * H.patch_nf[p]; ++t) {
+                        int32_t *e = &tb[((size_t)p * npm + t) * GS0_TABLE_INTS];
+                        const int js = t >> 1, d = t & 1;
+                        e[0] = 2 * H.patch_facets[(size_t)p * H.pf_max + js] + d;
+                        for (int q = 0; q < 2; ++q) {
+                            const int src = H.patch_slot_src[((size_t)p * H.pf_max + js) * 2 + q];
+                            const int c = H.patch_cells[(size_t)p * H.pc_max + (src >> 2)];
+                            e[1 + q] = c * 36 + (src & 3) * 12 + d;
+                            for (int f2 = 0; f2 < 3; ++f2) e[3 + 3 * q + f2] = ci[3 * c + f2];
+                        }
+                    }
+                upload(ctx, L.gs0_table, tb);
+            }
             if (l > 0) {
                 HostTransfer &T = ctx->T[l];
                 L.nc_coarse = T.nc_coarse;

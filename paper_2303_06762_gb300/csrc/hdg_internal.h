@@ -89,6 +89,8 @@ struct SmallLayout {
 
 // views of the smallest lowest-order levels for the single-block MG kernel (mg_small.cu)
 constexpr int SMALL_MAX_LEVELS = 6;
+constexpr int64_t GS0_TABLE_MAX_CELLS = 32768;
+constexpr int GS0_TABLE_INTS = 12;
 constexpr int SMALL_MAX_COLOURS = 15;
 constexpr int64_t SMALL_MAX_CELLS = 32768;
 
@@ -170,6 +172,11 @@ struct DevLevel {
     int n_patches = 0, n_colours = 0, pf_max = 0, pc_max = 0;
     std::vector<int32_t> colour_ptr;
     DBuf<int32_t> patch_nf, patch_facets, patch_nc, patch_cells, patch_slot_src;
+    // lowest-order sweep gather table (levels with at most GS0_TABLE_MAX_CELLS cells): per
+    // patch row t < np_max, GS0_TABLE_INTS ints {row 2F+d, element-row offsets of the two
+    // cells c*36 + lf*12 + d, their interior facets (3 each, -1 on the boundary)}; rows
+    // t >= np carry row = -1
+    DBuf<int32_t> gs0_table;
     DevOperator op0;           // lowest-order condensed operator of this level
     // transfer from level-1
     int64_t nc_coarse = 0, nB = 0;

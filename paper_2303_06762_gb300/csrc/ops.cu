@@ -218,6 +218,60 @@ __global__ void round_patch_rows_kernel(int n_patches, int np_max, int dpf, cons
     Ps[idx] = (float)sc;
 }
 
+// Lowest-order sweep through the level's gather table (small levels): the same
+// arithmetic as gs0_kernel, but each lane reads its row's target, the two element-row
+// offsets and the six facet indices in three 16-byte loads, so the only dependent
+// loads left are those of the matrix entries and unknowns.
+template <class T, int LANES>
+__global__ void __launch_bounds__(256)
+gs0t_kernel(int p0, int p1, int np_max, const int *__restrict__ tbl, const T *__restrict__ A,
+            const T *__restrict__ Pinv, const T *__restrict__ g, T *__restrict__ u) {
+    const int lane = threadIdx.x & 31, sub = lane / LANES, t = lane % LANES;
+    const int groups_per_block = blockDim.x / LANES;
+    const int p = p0 + blockIdx.x * groups_per_block + (threadIdx.x / 32) * (32 / LANES) + sub;
+    const bool live = p < p1;
+    int e[GS0_TABLE_INTS];
+#pragma unroll
+    for (int i = 0; i < GS0_TABLE_INTS; ++i) e[i] = -1;
+    if (live && t < np_max) {
+        const int4 *rec = reinterpret_cast<const int4 *>(tbl + ((size_t)p * np_max + t) * GS0_TABLE_INTS);
+#pragma unroll
+        for (int v = 0; v < GS0_TABLE_INTS / 4; ++v) {
+            const int4 x = rec[v];
+            e[4 * v] = x.x;
+            e[4 * v + 1] = x.y;
+            e[4 * v + 2] = x.z;
+            e[4 * v + 3] = x.w;
+        }
+    }
+    const int row = e[0];
+    T acc = 0;
+    if (row >= 0) {
+        acc = g[row];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const T *Ac = A + e[1 + q];
+#pragma unroll
+            for (int f2 = 0; f2 < 3; ++f2) {
+                const int j = e[3 + 3 * q + f2];
+                if (j < 0) continue;
+                acc -= Ac[(2 * f2) * 2] * u[2 * (size_t)j] + Ac[(2 * f2 + 1) * 2] * u[2 * (size_t)j + 1];
+            }
+        }
+    }
+    // the valid rows of a patch are a prefix of its lane group
+    const unsigned vm = __ballot_sync(0xffffffffu, row >= 0);
+    const unsigned gm = LANES == 32 ? 0xffffffffu : ((1u << LANES) - 1u);
+    const int np = __popc((vm >> (sub * LANES)) & gm);
+    T out = 0;
+    const T *Pi = live ? Pinv + (size_t)p * np_max * np_max : Pinv;
+    for (int j = 0; j < np_max; ++j) {
+        const T rj = __shfl_sync(0xffffffffu, acc, j, LANES);
+        if (j < np && t < np) out += Pi[(size_t)j * np_max + t] * rj;
+    }
+    if (row >= 0) u[row] += out;
+}
+
 // ---------------------------------------------------------------- order-k sweep, TMA-staged
 // One colour phase of the order-k FP32 sweep, as gs_kernel<float, DPF>, with the
 // patch's matrices moved into shared memory by the bulk-copy engine: thread 0
@@ -807,7 +861,11 @@ cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, cons
         const int lanes = op.np_max <= 16 ? 16 : 32;
         const int per_block = 256 / lanes;
         const unsigned nb = (unsigned)((p1 - p0 + per_block - 1) / per_block);
-        if (lanes == 16)
+        // the gather table pays off in FP32 (about 4% of the mixed solve at 512x512); with FP64
+        // values the table-driven kernel measured slower than the index-chasing one
+        if (std::is_same<T, float>::value && lanes == 16 && L.gs0_table.p && op.np_max == 2 * L.pf_max)
+            gs0t_kernel<T, 16><<<nb, 256, 0, s>>>(p0, p1, op.np_max, L.gs0_table.p, A, Pinv, g, u);
+        else if (lanes == 16)
             gs0_kernel<T, 16><<<nb, 256, 0, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
                                                  L.patch_facets.p, L.patch_cells.p, L.patch_slot_src.p,
                                                  L.cell_int.p, A, Pinv, g, u);
