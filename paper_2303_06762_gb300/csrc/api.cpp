@@ -1117,11 +1117,6 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
         REQUIRE(desc->dim == 2, "only dim = 2 is supported");
         REQUIRE(desc->n_levels >= 1 && desc->n_levels <= MAX_LEVELS, "n_levels out of range 1..16");
         REQUIRE(desc->n_vertices && desc->n_cells && desc->coords && desc->cells, "null mesh arrays");
-        int ndev = 0;
-        CK(cudaGetDeviceCount(&ndev));
-        REQUIRE(device >= 0 && device < ndev, "device ordinal out of range");
-        ctx->device = device;
-        CK(cudaSetDevice(device));
         const int nl = desc->n_levels;
         ctx->n_levels = nl;
         ctx->H.resize(nl);
@@ -1145,7 +1140,12 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
                 REQUIRE(e2.empty(), "level " + std::to_string(l) + ": " + e2);
             }
         }
-        // upload
+        // the hierarchy is valid (checked on the host, before any device call): upload
+        int ndev = 0;
+        CK(cudaGetDeviceCount(&ndev));
+        REQUIRE(device >= 0 && device < ndev, "device ordinal out of range");
+        ctx->device = device;
+        CK(cudaSetDevice(device));
         for (int l = 0; l < nl; ++l) {
             HostLevel &H = ctx->H[l];
             DevLevel &L = ctx->L[l];
