@@ -9,7 +9,10 @@
 // Gauss-Seidel sweep and the transfers of Algorithms 1 and 2 become products
 // of the stored local matrices with R-column blocks.  Krylov reductions keep
 // one accumulator per (vector, column) and reduce each column separately, so
-// the R flexible GMRES iterations of hdg_solve_multi stay independent.
+// the R flexible GMRES iterations of hdg_solve_multi stay independent.  The
+// order-k sweep's tile (rows per thread, threads per block) is a launch
+// parameter chosen by the host autotuner; the 16-bit precisions run that sweep
+// on tensor cores instead (multi_tc.cu).
 #include <cuda_runtime.h>
 
 #include <algorithm>

@@ -8,7 +8,10 @@
 //   patches (eq. bjac with GS, Section 5): every patch of the colour forms its
 //   residual rows from the cells of its star, multiplies by the stored patch
 //   inverse and updates its unknowns.  Patches of one colour share no cell, so
-//   the phase equals the sequential sweep over those patches.
+//   the phase equals the sequential sweep over those patches.  Variants: the
+//   order-k FP32 phase with its matrices staged by cp.async.bulk
+//   (gs_tma_kernel), the lowest-order phase with lane groups per patch
+//   (gs0_kernel) and, on small levels, through a gather table (gs0t_kernel).
 // * hp transfers (Section 3.5): Π_k^0 takes the m = 0 normal and tangential
 //   coefficient of every facet; Π_0^k adds them back.
 // * CR transfers (eqs. avgOpt, div-transfer, harmonic-ex): prolongation
