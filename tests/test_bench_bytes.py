@@ -29,3 +29,11 @@ def test_sweep_bytes_counts_every_patch(N, k, shuffle):
     assert bench.sweep_bytes(mesh, k, 4) == 4 * (mat + vec)
     assert bench.sweep_bytes(mesh, k, 8) == 8 * (mat + vec)
     assert bench.sweep_bytes(mesh, k, 4, 2) == 2 * mat + 4 * vec + 4 * scales
+
+
+@pytest.mark.parametrize("N,k", [(4, 1), (8, 3), (6, 2)])
+def test_full_size_counts_match_the_mesh(N, k):
+    """The reference arm reports the GPU arm's config, whose skeleton size it computes
+    in closed form: check the formula against the mesh."""
+    t = topo_of(unit_square(N))
+    assert bench.full_skeleton_dofs(N, k) == len(t.interior_facets) * 2 * (k + 1)
