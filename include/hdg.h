@@ -177,6 +177,26 @@ typedef struct {
  * uzawa_tol 1e-8, restart 30, max_it 1000, max_uzawa 64. */
 void hdg_default_solve_opts(hdg_solve_opts *opts);
 
+/* Sizes of a checked hierarchy (finest level). */
+typedef struct {
+    int n_levels;
+    int64_t n_interior_facets;
+    int64_t n_dof;            /* n_interior_facets * 2(k+1)                           */
+    int n_patches;            /* vertex patches (vertices with an interior facet)     */
+    int n_colours;            /* colours of the vertex colouring (colour phases)      */
+    int max_patch_facets;     /* interior facets of the largest patch                 */
+    int max_patch_cells;      /* cells of the largest star                            */
+} hdg_hierarchy_info;
+
+/* Validates a mesh hierarchy on the host, with no device call: every check of
+ * hdg_setup_mesh_hierarchy (cell indices, manifold facets, a proper vertex
+ * colouring, red-refinement parent maps) and the construction of its vertex
+ * patches and transfer tables.  info (nullable) receives the finest level's
+ * sizes for polynomial order k; on failure msg (nullable, msg_len bytes)
+ * receives the reason.  Returns HDG_OK or HDG_ERR_INVALID_ARG. */
+hdg_status hdg_check_hierarchy(const hdg_mesh_desc *desc, int k, hdg_hierarchy_info *info, char *msg,
+                               int msg_len);
+
 /* Build the topology of every level: facets, orientations, interior-facet
  * numbering, vertex patches and their colouring, parent/child maps and the
  * coarse-facet/fine-facet relations needed by the averaging transfer of

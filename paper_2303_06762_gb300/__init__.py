@@ -36,7 +36,7 @@ _STATUS = {0: "HDG_OK", 1: "HDG_ERR_INVALID_ARG", 2: "HDG_ERR_OOM", 3: "HDG_ERR_
            7: "HDG_ERR_NONFINITE", 8: "HDG_ERR_UNSUPPORTED", 9: "HDG_ERR_STATE", 10: "HDG_ERR_TIMEOUT"}
 
 # every exported entry point of include/hdg.h
-EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_condense", "hdg_load",
+EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_check_hierarchy", "hdg_condense", "hdg_load",
            "hdg_apply", "hdg_precond_apply", "hdg_solve", "hdg_recover", "hdg_adjoint", "hdg_get_sizes",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
@@ -68,6 +68,12 @@ class _Params(ctypes.Structure):
                 ("cycle", ctypes.c_int), ("vcycle_growth", ctypes.c_int), ("precision", ctypes.c_int),
                 ("fused_coarse_cells", ctypes.c_int), ("nu_elem", ctypes.c_void_p), ("conv", ctypes.c_void_p),
                 ("newton_u", ctypes.c_void_p)]
+
+
+class HierarchyInfo(ctypes.Structure):
+    _fields_ = [("n_levels", ctypes.c_int), ("n_interior_facets", ctypes.c_int64), ("n_dof", ctypes.c_int64),
+                ("n_patches", ctypes.c_int), ("n_colours", ctypes.c_int), ("max_patch_facets", ctypes.c_int),
+                ("max_patch_cells", ctypes.c_int)]
 
 
 class SolveOpts(ctypes.Structure):
@@ -137,6 +143,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
     sigs = {
         "hdg_default_solve_opts": (None, [ctypes.POINTER(SolveOpts)]),
         "hdg_setup_mesh_hierarchy": (I, [ctypes.POINTER(_MeshDesc), I, ctypes.POINTER(P)]),
+        "hdg_check_hierarchy": (I, [ctypes.POINTER(_MeshDesc), I, ctypes.POINTER(HierarchyInfo), ctypes.c_char_p, I]),
         "hdg_apply_multi": (I, [P, I, P, P, P]),
         "hdg_precond_apply_multi": (I, [P, I, P, P, P]),
         "hdg_smooth_multi": (I, [P, I, I, P, P, I, I, P]),
@@ -230,10 +237,8 @@ class Context:
 
 
 # ------------------------------------------------------------------ C-ABI mirrors
-def hdg_setup_mesh_hierarchy(levels: Sequence, device: int = 0) -> Context:
-    """levels: objects with .coords (nv,2) float64, .cells (nc,3) int32, .parent (levels >= 1)
-    and optional .vertex_colour, coarsest first."""
-    lib = load_library()
+def _mesh_desc(levels: Sequence):
+    """The hdg_mesh_desc of `levels` and the arrays it points into (keep them alive)."""
     n = len(levels)
     keep = []
     nv = (ctypes.c_int64 * n)(*[int(m.coords.shape[0]) for m in levels])
@@ -257,7 +262,27 @@ def hdg_setup_mesh_hierarchy(levels: Sequence, device: int = 0) -> Context:
             c = np.ascontiguousarray(col, dtype=np.int32)
             keep.append(c)
             vc[l] = c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
-    desc = _MeshDesc(2, n, nv, nc, co, ce, pa, vc)
+    keep += [nv, nc, co, ce, pa, vc]
+    return _MeshDesc(2, n, nv, nc, co, ce, pa, vc), keep
+
+
+def hdg_check_hierarchy(levels: Sequence, k: int = 1) -> dict:
+    """Host-only validation of a hierarchy (no GPU needed); returns the finest level's sizes
+    for order k, raises HdgError with the reason otherwise."""
+    desc, keep = _mesh_desc(levels)
+    info = HierarchyInfo()
+    msg = ctypes.create_string_buffer(512)
+    st = load_library().hdg_check_hierarchy(ctypes.byref(desc), k, ctypes.byref(info), msg, len(msg))
+    if st != 0:
+        raise HdgError(st, msg.value.decode())
+    return {name: getattr(info, name) for name, _ in HierarchyInfo._fields_}
+
+
+def hdg_setup_mesh_hierarchy(levels: Sequence, device: int = 0) -> Context:
+    """levels: objects with .coords (nv,2) float64, .cells (nc,3) int32, .parent (levels >= 1)
+    and optional .vertex_colour, coarsest first."""
+    lib = load_library()
+    desc, keep = _mesh_desc(levels)
     h = ctypes.c_void_p()
     st = lib.hdg_setup_mesh_hierarchy(ctypes.byref(desc), device, ctypes.byref(h))
     ctx = Context(h, device)

@@ -1108,38 +1108,45 @@ int64_t hdg_reference_tables(int k, double *out) {
     }
 }
 
+// topology, vertex patches and transfer tables of every level, on the host only;
+// throws Fail{HDG_ERR_INVALID_ARG} (message in ctx->err) on an invalid hierarchy
+void build_host_hierarchy(hdg_ctx *ctx, const hdg_mesh_desc *desc) {
+    REQUIRE(desc->dim == 2, "only dim = 2 is supported");
+    REQUIRE(desc->n_levels >= 1 && desc->n_levels <= MAX_LEVELS, "n_levels out of range 1..16");
+    REQUIRE(desc->n_vertices && desc->n_cells && desc->coords && desc->cells, "null mesh arrays");
+    const int nl = desc->n_levels;
+    ctx->n_levels = nl;
+    ctx->H.assign(nl, HostLevel());
+    ctx->T.assign(nl, HostTransfer());
+    for (int l = 0; l < nl; ++l) {
+        HostLevel &H = ctx->H[l];
+        H.nv = desc->n_vertices[l];
+        H.nc = desc->n_cells[l];
+        REQUIRE(H.nv >= 3 && H.nc >= 1 && H.nc < (1LL << 26), "level sizes out of range");
+        REQUIRE(desc->coords[l] && desc->cells[l], "null level array");
+        H.coords.assign(desc->coords[l], desc->coords[l] + 2 * H.nv);
+        H.cells.assign(desc->cells[l], desc->cells[l] + 3 * H.nc);
+        const int32_t *col = (desc->vertex_colour && desc->vertex_colour[l]) ? desc->vertex_colour[l] : nullptr;
+        std::string e = build_level_topology(H, col);
+        REQUIRE(e.empty(), "level " + std::to_string(l) + ": " + e);
+        if (l > 0) {
+            REQUIRE(desc->parent && desc->parent[l], "parent map required on levels >= 1");
+            H.parent.assign(desc->parent[l], desc->parent[l] + H.nc);
+            std::string e2 = build_transfer(ctx->H[l - 1], H, ctx->T[l]);
+            REQUIRE(e2.empty(), "level " + std::to_string(l) + ": " + e2);
+        }
+    }
+}
+
 hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_ctx **out) {
     if (!out) return HDG_ERR_INVALID_ARG;
     *out = nullptr;
     if (!desc) return HDG_ERR_INVALID_ARG;
     hdg_ctx *ctx = new hdg_ctx();
     hdg_status st = guard(ctx, [&] {
-        REQUIRE(desc->dim == 2, "only dim = 2 is supported");
-        REQUIRE(desc->n_levels >= 1 && desc->n_levels <= MAX_LEVELS, "n_levels out of range 1..16");
-        REQUIRE(desc->n_vertices && desc->n_cells && desc->coords && desc->cells, "null mesh arrays");
-        const int nl = desc->n_levels;
-        ctx->n_levels = nl;
-        ctx->H.resize(nl);
-        ctx->T.resize(nl);
+        build_host_hierarchy(ctx, desc);
+        const int nl = ctx->n_levels;
         ctx->L.resize(nl);
-        for (int l = 0; l < nl; ++l) {
-            HostLevel &H = ctx->H[l];
-            H.nv = desc->n_vertices[l];
-            H.nc = desc->n_cells[l];
-            REQUIRE(H.nv >= 3 && H.nc >= 1 && H.nc < (1LL << 26), "level sizes out of range");
-            REQUIRE(desc->coords[l] && desc->cells[l], "null level array");
-            H.coords.assign(desc->coords[l], desc->coords[l] + 2 * H.nv);
-            H.cells.assign(desc->cells[l], desc->cells[l] + 3 * H.nc);
-            const int32_t *col = (desc->vertex_colour && desc->vertex_colour[l]) ? desc->vertex_colour[l] : nullptr;
-            std::string e = build_level_topology(H, col);
-            REQUIRE(e.empty(), "level " + std::to_string(l) + ": " + e);
-            if (l > 0) {
-                REQUIRE(desc->parent && desc->parent[l], "parent map required on levels >= 1");
-                H.parent.assign(desc->parent[l], desc->parent[l] + H.nc);
-                std::string e2 = build_transfer(ctx->H[l - 1], H, ctx->T[l]);
-                REQUIRE(e2.empty(), "level " + std::to_string(l) + ": " + e2);
-            }
-        }
         // the hierarchy is valid (checked on the host, before any device call): upload
         int ndev = 0;
         CK(cudaGetDeviceCount(&ndev));
@@ -1232,6 +1239,33 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
     }
     *out = ctx;
     return HDG_OK;
+}
+
+hdg_status hdg_check_hierarchy(const hdg_mesh_desc *desc, int k, hdg_hierarchy_info *info, char *msg,
+                               int msg_len) {
+    if (msg && msg_len > 0) msg[0] = 0;
+    if (!desc) return HDG_ERR_INVALID_ARG;
+    hdg_ctx tmp;
+    hdg_ctx *ctx = &tmp;
+    hdg_status st = guard(ctx, [&] {
+        REQUIRE(k >= 0 && k <= 4, "k out of range 0..4");
+        build_host_hierarchy(ctx, desc);
+        if (info) {
+            const HostLevel &F = ctx->H[ctx->n_levels - 1];
+            info->n_levels = ctx->n_levels;
+            info->n_interior_facets = F.n_int;
+            info->n_dof = (int64_t)F.n_int * 2 * (k + 1);
+            info->n_patches = F.n_patches;
+            info->n_colours = F.n_colours;
+            info->max_patch_facets = F.pf_max;
+            info->max_patch_cells = F.pc_max;
+        }
+    });
+    if (st != HDG_OK && msg && msg_len > 0) {
+        std::strncpy(msg, tmp.err.c_str(), (size_t)msg_len - 1);
+        msg[msg_len - 1] = 0;
+    }
+    return st;
 }
 
 void hdg_destroy(hdg_ctx *ctx) {
