@@ -75,7 +75,9 @@ typedef enum {
     HDG_ERR_UNSUPPORTED = 8,   /* valid request this build does not implement       */
     HDG_ERR_STATE = 9,         /* call order violated (e.g. solve before condense)  */
     HDG_ERR_TIMEOUT = 10       /* a bounded device wait gave up (a kernel skipped   */
-                               /* its update; the result of the call is invalid)    */
+                               /* its update; the result of the call is invalid);   */
+                               /* checked at the end of hdg_solve, hdg_picard,      */
+                               /* hdg_newton and hdg_adjoint                        */
 } hdg_status;
 
 typedef enum {

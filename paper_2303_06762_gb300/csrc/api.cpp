@@ -1714,6 +1714,7 @@ hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, con
             condense_all(ctx, nullptr, s);
         }
         CK(cudaStreamSynchronize(s));
+        check_wait_flag(ctx, s);
     });
     if (info) *info = loc;
     if (st != HDG_OK) return st;
@@ -1968,6 +1969,7 @@ hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forc
         }
         if (!(dist < tol) && conv == HDG_OK) conv = HDG_ERR_NOT_CONVERGED;
         CK(cudaStreamSynchronize(s));
+        check_wait_flag(ctx, s);
     });
     if (steps_out) *steps_out = steps;
     if (dist_out) *dist_out = dist;
@@ -2025,6 +2027,7 @@ hdg_status hdg_newton(hdg_ctx *ctx, const hdg_params *params, const double *forc
         }
         if (!(dist < tol) && conv == HDG_OK) conv = HDG_ERR_NOT_CONVERGED;
         CK(cudaStreamSynchronize(s));
+        check_wait_flag(ctx, s);
     });
     if (steps_out) *steps_out = steps;
     if (dist_out) *dist_out = dist;
