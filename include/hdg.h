@@ -77,7 +77,8 @@ typedef enum {
     HDG_ERR_TIMEOUT = 10       /* a bounded device wait gave up (a kernel skipped   */
                                /* its update; the result of the call is invalid);   */
                                /* checked at the end of hdg_solve, hdg_picard,      */
-                               /* hdg_newton and hdg_adjoint                        */
+                               /* hdg_newton, hdg_adjoint, hdg_precond_apply and    */
+                               /* hdg_smooth (see hdg_set_wait_limit)               */
 } hdg_status;
 
 typedef enum {
@@ -175,7 +176,7 @@ typedef struct {
     int n_lat;                  /* forcing lattice points per cell                  */
 } hdg_sizes;
 
-/* Fill the defaults of Section 5: rtol 1e-8, atol 1e-10, floor_rel 1e-9,
+/* Fill the defaults of Section 5: rtol 1e-8, atol 1e-10, floor_rel 1e-10,
  * uzawa_tol 1e-8, restart 30, max_it 1000, max_uzawa 64. */
 void hdg_default_solve_opts(hdg_solve_opts *opts);
 
@@ -402,6 +403,19 @@ hdg_status hdg_coarse_solve(hdg_ctx *ctx, const double *g, double *u, hdg_stream
 /* u = MG_h(L, g, 0, m_h, q) of Algorithm 1 on the lowest-order operator of
  * the finest level L. */
 hdg_status hdg_mg_h(hdg_ctx *ctx, const double *g, double *u, hdg_stream_t stream);
+
+/* Failure-detection hook.  The order-k FP32 sweep (HDG_MIXED_FP32) stages its
+ * matrices in shared memory by bulk copies and waits for them on an mbarrier
+ * with a time limit (default 1 s of global time).  When the limit passes, the
+ * thread block skips its patch update, records the timeout in a device flag
+ * and then waits, in bounded steps of at most 4 s in total, until its copies
+ * have landed before it exits; hdg_solve, hdg_picard, hdg_newton, hdg_adjoint,
+ * hdg_precond_apply and hdg_smooth (order-k level) read and clear the flag and
+ * return HDG_ERR_TIMEOUT, and the context stays usable.  hdg_set_wait_limit
+ * sets that first limit in nanoseconds for this context; 0 makes every first
+ * wait expire at once, so that a test can drive the timeout path without
+ * stalling the GPU.  Returns HDG_ERR_INVALID_ARG for a negative limit. */
+hdg_status hdg_set_wait_limit(hdg_ctx *ctx, int64_t first_wait_ns);
 
 /* Capacity, in coarse cells, of the fixed scratch array of hdg_restrict_noalloc. */
 #define HDG_NOALLOC_MAX_COARSE_CELLS 32768

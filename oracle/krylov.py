@@ -17,7 +17,7 @@ TEST INFRASTRUCTURE ONLY.
   the form above is the one whose error contracts by ε/(ε+μ0) per step
   (Lemma 3.1).  The inner solves are warm-started from the previous u and,
   as in Section 5, stop at relative 1e-8 / absolute 1e-10, but never below
-  floor_rel·‖F‖ (default 1e-9; Remark 3.1: much smaller residuals are
+  floor_rel·‖F‖ (default 1e-10; Remark 3.1: much smaller residuals are
   round-off at large ε⁻¹):
   ‖g − A^ε u‖ <= max(rtol·‖g − A^ε u_start‖, floor_rel·‖F‖, atol).
   The outer loop stops once the pressure error estimate of a linearly
@@ -111,7 +111,7 @@ class UzawaResult:
 
 def uzawa(Aeps, D, area, eps_inv, F, M: Callable, rtol: float = 1e-8, atol: float = 1e-10,
           restart: int = 30, max_it: int = 1000, max_uzawa: int = 200,
-          uzawa_tol: float = 1e-8, floor_rel: float = 1e-9, u0=None) -> UzawaResult:
+          uzawa_tol: float = 1e-8, floor_rel: float = 1e-10, u0=None) -> UzawaResult:
     """Augmented-Lagrangian Uzawa with FGMRES inner solves (eq. stOpEq-ALU)."""
     normF = float(np.linalg.norm(F))
     u = np.zeros_like(F) if u0 is None else np.array(u0, copy=True)

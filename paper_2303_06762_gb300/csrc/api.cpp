@@ -135,6 +135,17 @@ void check_wait_flag(hdg_ctx *ctx, cudaStream_t s) {
     }
 }
 
+// the same check for the step-level entry points that may run the bulk-copy sweep (the
+// order-k FP32 smoother): skipped when that sweep cannot have run, or while the caller's
+// stream is being captured (the capture owner checks at its own synchronisation point)
+void check_wait_flag_sweep(hdg_ctx *ctx, cudaStream_t s) {
+    if (!ctx->opk.tma_flag || ctx->prm.precision == HDG_FP64) return;
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CK(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) return;
+    check_wait_flag(ctx, s);
+}
+
 double read_scalar(hdg_ctx *ctx, const double *dev, cudaStream_t s) {
     CK(cudaMemcpyAsync(ctx->h_pinned, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
@@ -1063,7 +1074,7 @@ void hdg_default_solve_opts(hdg_solve_opts *o) {
     if (!o) return;
     o->rtol = 1e-8;
     o->atol = 1e-10;
-    o->floor_rel = 1e-9;
+    o->floor_rel = 1e-10;
     o->uzawa_tol = 1e-8;
     o->restart = 30;
     o->max_it = 1000;
@@ -1509,6 +1520,7 @@ hdg_status hdg_precond_apply(hdg_ctx *ctx, const double *r, double *z, hdg_strea
         NEED_CONDENSED();
         REQUIRE(r && z && r != z, "r, z must be distinct non-null device pointers");
         precond(ctx, r, z, (cudaStream_t)stream);
+        check_wait_flag_sweep(ctx, (cudaStream_t)stream);
     });
 }
 
@@ -1544,7 +1556,17 @@ hdg_status hdg_smooth(hdg_ctx *ctx, int level, const double *g, double *u, int n
             CK(launch_d2f(u, uf, n, s));
             for (int i = 0; i < n_sweeps; ++i) sweep<float>(ctx, L, op, gf, uf, reverse != 0, s);
             CK(launch_f2d(uf, u, n, s));
+            if (level < 0) check_wait_flag_sweep(ctx, s);
         }
+    });
+}
+
+hdg_status hdg_set_wait_limit(hdg_ctx *ctx, int64_t first_wait_ns) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        REQUIRE(first_wait_ns >= 0, "first_wait_ns must be >= 0");
+        ctx->opk.tma_wait_ns = (unsigned long long)first_wait_ns;
+        drop_graph(ctx);   // the captured preconditioner holds the old limit
     });
 }
 
@@ -1875,6 +1897,13 @@ hdg_status hdg_solve_batched(hdg_ctx *const *ctxs, int n, const double *const *F
         for (int j = 0; j < i; ++j)
             if (ctxs[j] == ctxs[i]) return HDG_ERR_INVALID_ARG;   // one thread per context
     }
+    // the calling thread runs context 0 and switches devices: its current device is restored
+    int caller_dev = -1;
+    if (cudaGetDevice(&caller_dev) != cudaSuccess) return HDG_ERR_CUDA;
+    struct RestoreDevice {
+        int d;
+        ~RestoreDevice() { cudaSetDevice(d); }
+    } restore{caller_dev};
     std::vector<hdg_status> st(n, HDG_OK);
     std::vector<hdg_solve_info> inf(n);
     for (int i = 0; i < n; ++i) {

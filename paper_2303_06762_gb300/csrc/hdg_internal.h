@@ -150,6 +150,7 @@ struct DevOperator {
     // layouts of A and Pinv with every stored row divided by its power-of-two scale
     int *tma_flag = nullptr; // device flag of the bulk-copy sweep's bounded waits (bit 4 on timeout),
                              // null = that sweep is not used
+    unsigned long long tma_wait_ns = 1000000000ull;   // limit of that sweep's first wait (0 = expire at once)
     int h_fmt = 0;       // hdg_precision of Ah / Pinvh, 0 = none
     DBuf<uint16_t> Ah;   // nc*nloc*nloc
     DBuf<float> Ah_s;    // nc*nloc, scale of row p of cell c at c*nloc + p

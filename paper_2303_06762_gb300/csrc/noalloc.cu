@@ -25,11 +25,8 @@ static __device__ __align__(256) double g_restrict_scratch[(size_t)HDG_NOALLOC_M
 std::mutex g_mutex;
 double *g_addr[kMaxDevices] = {nullptr};
 
-} // namespace
-
-extern "C" hdg_status hdg_restrict_noalloc(hdg_ctx *ctx, int level, const double *rf, double *rc,
-                                           hdg_stream_t stream) {
-    if (!ctx) return HDG_ERR_INVALID_ARG;
+// the body of hdg_restrict_noalloc; may throw only from the host string and lock operations
+hdg_status restrict_noalloc_impl(hdg_ctx *ctx, int level, const double *rf, double *rc, hdg_stream_t stream) {
     if (!ctx->condensed) {
         ctx->err = "hdg_restrict_noalloc: operator used before hdg_condense";
         return HDG_ERR_STATE;
@@ -80,4 +77,21 @@ extern "C" hdg_status hdg_restrict_noalloc(hdg_ctx *ctx, int level, const double
         return HDG_ERR_CUDA;
     }
     return HDG_OK;
+}
+
+} // namespace
+
+extern "C" hdg_status hdg_restrict_noalloc(hdg_ctx *ctx, int level, const double *rf, double *rc,
+                                           hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    // no exception may cross the C ABI (a failed string or lock operation is reported instead)
+    try {
+        return restrict_noalloc_impl(ctx, level, rf, rc, stream);
+    } catch (...) {
+        try {
+            ctx->err = "hdg_restrict_noalloc: host-side exception";
+        } catch (...) {
+        }
+        return HDG_ERR_INVALID_ARG;
+    }
 }

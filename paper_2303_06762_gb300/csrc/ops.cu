@@ -317,7 +317,7 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
               const int *__restrict__ patch_nc, const int *__restrict__ patch_cells,
               const int *__restrict__ slot_src, const int *__restrict__ cell_int,
               const float *__restrict__ A, const float *__restrict__ Pinv,
-              const float *__restrict__ g, float *__restrict__ u, int *flag) {
+              const float *__restrict__ g, float *__restrict__ u, int *flag, unsigned long long wait_ns) {
     constexpr int NLOC = 3 * DPF;
     constexpr int RB = NLOC * DPF;             // floats in one facet row block
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -364,10 +364,17 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
         int j = cell_int[3 * c + l / DPF];
         xs[t] = j >= 0 ? u[(size_t)j * DPF + l % DPF] : 0.0f;
     }
-    if (!mbar_wait_bounded(bar, 0, 1000000000ull)) {
+    // first wait: wait_ns of global time (0 = treated as expired at once, the testing hook of
+    // the timeout path).  On expiry the patch update is skipped and bit 4 of *flag is set; the
+    // bulk copies still target this CTA's shared memory, so the CTA keeps waiting for them in
+    // bounded one-second steps (at most four) before it returns, and sets bit 8 if they still
+    // have not landed (the shared memory may then be written after the CTA has exited).
+    if (!(wait_ns > 0 && mbar_wait_bounded(bar, 0, wait_ns))) {
         atomicOr(flag, 4);
         s_ok = 0;
-        mbar_wait_bounded(bar, 0, 1000000000ull);
+        bool drained = false;
+        for (int step = 0; step < 4 && !drained; ++step) drained = mbar_wait_bounded(bar, 0, 1000000000ull);
+        if (!drained) atomicOr(flag, 8);
     }
     __syncthreads();
     if (!s_ok) return;
@@ -888,7 +895,7 @@ cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, cons
             gs_tma_kernel<DPF><<<p1 - p0, 64, tsm, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
                                                        L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
                                                        L.patch_slot_src.p, L.cell_int.p, A, Pinv, g, u,
-                                                       op.tma_flag);
+                                                       op.tma_flag, op.tma_wait_ns);
             return cudaGetLastError();
         }
     }

@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 from workloads import forcing_at_lattice
 from workloads.manufactured import fourier_forcing_2d, convecting_stream_2d, curl_lattice_2d
 from oracle.hdg import HDG
-from _util import hierarchy, rel
+from _util import hierarchy, rel, relnorm
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -87,9 +87,9 @@ def test_solve_multi_matches_single_and_direct(k, nrhs, precision, mesh):
         else:
             assert abs(infos[r]["krylov_its_total"] - info1["krylov_its_total"]) <= infos[r]["uzawa_its"]
         ud, pd = oh.solve_direct(oh.load(fvs[r]))
-        assert np.linalg.norm(host(U[r]) - ud) < 1e-8 * np.linalg.norm(ud)
-        pr = host(P[r])
-        assert np.linalg.norm(pr - pd) < 1e-6 * np.linalg.norm(pd)
+        eu, ep = relnorm(host(U[r]), ud), relnorm(host(P[r]), pd)
+        print(f"batched k={k} column {r}: vs direct |du| {eu:.2e} |dp| {ep:.2e}")
+        assert eu < 1e-8 and ep < 1e-8
 
 
 def test_solve_multi_oseen_and_wide_batch():
@@ -100,7 +100,9 @@ def test_solve_multi_oseen_and_wide_batch():
     oh = HDG(ts[-1], 3, nu=0.01, beta=0.0, gamma=100.0, conv=cv)
     for r in (0, 17, 63):
         ud, pd = oh.solve_direct(oh.load(fvs[r]))
-        assert np.linalg.norm(host(U[r]) - ud) < 1e-8 * np.linalg.norm(ud)
+        eu, ep = relnorm(host(U[r]), ud), relnorm(host(P[r]), pd)
+        print(f"batched Oseen column {r}: vs direct |du| {eu:.2e} |dp| {ep:.2e}")
+        assert eu < 1e-8 and ep < 1e-8
     assert all(i["uzawa_its"] >= 1 for i in infos)
 
 
@@ -135,7 +137,9 @@ def test_solve_batched_uneven_meshes(precision):
         assert info["krylov_its"] == info1["krylov_its"]
         assert rel(host(u), host(u1)) < 1e-13
         ud, pd = oh.solve_direct(oh.load(fv))
-        assert np.linalg.norm(host(u) - ud) < 1e-8 * np.linalg.norm(ud)
+        eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
+        print(f"uneven meshes: vs direct |du| {eu:.2e} |dp| {ep:.2e}")
+        assert eu < 1e-8 and ep < 1e-8
     lib = hdg.load_library()
     import ctypes
     same = (ctypes.c_void_p * 2)(ctxs[0].handle, ctxs[0].handle)

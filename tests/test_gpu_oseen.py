@@ -17,7 +17,7 @@ from oracle.mg import (BlockGS, vertex_patches, averaging_prolongation, interior
                        harmonic_prolongation, build_hpmg, lowest_order_convection)
 from oracle.krylov import uzawa
 from oracle.adjoint import objective_and_gradient
-from _util import hierarchy, rel
+from _util import hierarchy, rel, relnorm, parity_opts
 
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
@@ -134,10 +134,14 @@ def test_oseen_solve_matches_oracle(k, Re, mesh):
     ro = uzawa(M.A, oh.flux_matrix(), oh.area, oh.eps_inv, Fo, M)
     u, p, info = hdg.hdg_solve(ctx, F)
     assert info["krylov_its"] == ro.krylov_its
-    assert rel(host(u), ro.u) < 1e-9
-    assert rel(host(p), ro.p) < 1e-8
+    eu, ep = relnorm(host(u), ro.u), relnorm(host(p), ro.p)
+    print(f"Oseen k={k} Re={Re:g}: vs oracle iteration |du| {eu:.2e} |dp| {ep:.2e}")
+    assert eu < 1e-10 and ep < 1e-10
     ud, pd = oh.solve_direct(Fo)
-    assert np.linalg.norm(host(u) - ud) < 1e-8 * np.linalg.norm(ud)
+    u, p, info = hdg.hdg_solve(ctx, F, opts=parity_opts(hdg, gamma))
+    eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
+    print(f"Oseen k={k} Re={Re:g}: vs direct |du| {eu:.2e} |dp| {ep:.2e}")
+    assert eu < 1e-10 and ep < 1e-10
 
 
 def test_oseen_mixed_precision_solve():
@@ -147,8 +151,9 @@ def test_oseen_mixed_precision_solve():
     oh = HDG(ts[-1], k, nu=nu, gamma=100.0, conv=conv)
     ud, pd = oh.solve_direct(oh.load(fv))
     u, p, info = hdg.hdg_solve(ctx, F)
-    assert np.linalg.norm(host(u) - ud) < 1e-8 * np.linalg.norm(ud)
-    assert np.linalg.norm(host(p) - pd) < 1e-6 * np.linalg.norm(pd)
+    eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
+    print(f"Oseen mixed: vs direct |du| {eu:.2e} |dp| {ep:.2e}")
+    assert eu < 1e-8 and ep < 1e-8
 
 
 @pytest.mark.parametrize("k,Re", [(1, 1.0), (2, 100.0)])

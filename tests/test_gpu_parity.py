@@ -16,7 +16,7 @@ from oracle.hdg import HDG
 from oracle.mg import (BlockGS, vertex_patches, averaging_prolongation, interior_fine_dofs,
                        harmonic_prolongation, build_hpmg, Level, MGh)
 from oracle.krylov import uzawa
-from _util import hierarchy, forcing, topo_of, rel
+from _util import hierarchy, forcing, topo_of, rel, relnorm, parity_opts
 
 pytestmark = pytest.mark.gpu
 
@@ -174,13 +174,22 @@ def test_solve_matches_oracle(k, gamma, mesh):
     Fo = oh.load(fv)
     ro = uzawa(M.A, oh.flux_matrix(), oh.area, oh.eps_inv, Fo, M)
     u, p, info = hdg.hdg_solve(ctx, F)
+    # the same iteration as the oracle's (default stopping rule): same counts, same iterates
     assert info["krylov_its"] == ro.krylov_its
-    assert rel(host(u), ro.u) < 1e-10
-    # the pressure update multiplies rounding-order differences of div u by eps^-1 = gamma nu
-    assert rel(host(p), ro.p) < (1e-9 if gamma <= 1e2 else 1e-8)
+    eu, ep = relnorm(host(u), ro.u), relnorm(host(p), ro.p)
+    print(f"k={k} gamma={gamma:g}: vs oracle iteration |du| {eu:.2e} |dp| {ep:.2e}")
+    assert eu < 1e-10
+    # at gamma = 1e4 the last inner solves stop on the residual floor, where the pressure
+    # update eps^-1 div u magnifies rounding-order differences of u (Remark 3.1)
+    assert ep < (1e-10 if gamma <= 1e2 else 1e-8)
+    # against the exact discrete solution (sparse direct solve of the condensed saddle point)
+    # with the parity stopping rule
     ud, pd = oh.solve_direct(Fo)
-    assert np.linalg.norm(host(u) - ud) < 1e-8 * np.linalg.norm(ud)
-    assert np.linalg.norm(host(p) - pd) < 1e-6 * np.linalg.norm(pd)
+    u, p, info = hdg.hdg_solve(ctx, F, opts=parity_opts(hdg, gamma))
+    eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
+    print(f"k={k} gamma={gamma:g}: vs direct |du| {eu:.2e} |dp| {ep:.2e}")
+    assert eu < 1e-10
+    assert ep < (1e-10 if gamma <= 1e2 else 1e-8)
 
 
 @pytest.mark.parametrize("k", [1, 3])
@@ -190,9 +199,15 @@ def test_mixed_precision_solve(k):
     oh = HDG(ts[-1], k, gamma=100.0, beta=1.0)
     ud, pd = oh.solve_direct(oh.load(fv))
     u, p, info = hdg.hdg_solve(ctx, F)
-    assert np.linalg.norm(host(u) - ud) < 1e-8 * np.linalg.norm(ud)
-    assert np.linalg.norm(host(p) - pd) < 1e-6 * np.linalg.norm(pd)
+    eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
+    print(f"mixed k={k}: vs direct |du| {eu:.2e} |dp| {ep:.2e} (default stopping rule)")
+    assert eu < 1e-8 and ep < 1e-8
     assert info["krylov_its_total"] > 0
+    # the FP64 outer iteration reaches the FP64 target with the parity stopping rule
+    u, p, info = hdg.hdg_solve(ctx, F, opts=parity_opts(hdg, 100.0))
+    eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
+    print(f"mixed k={k}: vs direct |du| {eu:.2e} |dp| {ep:.2e} (parity stopping rule)")
+    assert eu < 1e-10 and ep < 1e-10
 
 
 def test_single_level_and_coarsest_one_square():
@@ -201,7 +216,7 @@ def test_single_level_and_coarsest_one_square():
     oh = HDG(ts[0], 2, gamma=100.0, beta=1.0)
     u, p, info = hdg.hdg_solve(ctx, F)
     ud, pd = oh.solve_direct(oh.load(fv))
-    assert np.linalg.norm(host(u) - ud) < 1e-8 * np.linalg.norm(ud)
+    assert relnorm(host(u), ud) < 1e-8 and relnorm(host(p), pd) < 1e-8
     ms, ts, ps, fv, ctx, F = setup_case(1, 4, 1)       # coarsest mesh: 2 cells, 1 interior facet
     oh = HDG(ts[-1], 1, gamma=100.0, beta=1.0)
     M = build_hpmg(ts, ps, 1, 1.0, 1.0, 100.0, hdg_k=oh)

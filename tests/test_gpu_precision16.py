@@ -17,7 +17,7 @@ from workloads import curl_bubble_2d
 from workloads.manufactured import convecting_stream_2d, curl_lattice_2d
 from oracle.hdg import HDG
 from oracle.mg import BlockGS, vertex_patches, build_hpmg
-from _util import hierarchy, forcing, rel
+from _util import hierarchy, forcing, rel, relnorm
 from _round16 import round_hpmg, round_hpmg_tc, stored_rows, rounded_matrix
 
 pytestmark = pytest.mark.gpu
@@ -97,8 +97,9 @@ def test_solve_reaches_discrete_solution(precision, k):
     oh = M.hdg
     ud, pd = oh.solve_direct(oh.load(fv))
     u, p, info = hdg.hdg_solve(ctx, F)
-    assert np.linalg.norm(host(u) - ud) < 1e-8 * np.linalg.norm(ud)
-    assert np.linalg.norm(host(p) - pd) < 1e-6 * np.linalg.norm(pd)
+    eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
+    print(f"16-bit precision {precision} k={k}: vs direct |du| {eu:.2e} |dp| {ep:.2e}")
+    assert eu < 1e-8 and ep < 1e-8
     ctx32, F32, *_ = case(k, 1, jitter=0.2, seed=4)
     u32, p32, info32 = hdg.hdg_solve(ctx32, F32)
     # the 16-bit copies perturb the preconditioner, not the discrete problem
@@ -160,8 +161,9 @@ def test_batched_tensor_core_solve_reaches_discrete_solution(nrhs):
     oh = HDG(ts[-1], k, nu=1.0, beta=1.0, gamma=100.0)
     for r in (0, nrhs - 1):
         ud, pd = oh.solve_direct(oh.load(fvs[r]))
-        assert np.linalg.norm(host(U[r]) - ud) < 1e-8 * np.linalg.norm(ud)
-        assert np.linalg.norm(host(P[r]) - pd) < 1e-6 * np.linalg.norm(pd)
+        eu, ep = relnorm(host(U[r]), ud), relnorm(host(P[r]), pd)
+        print(f"tensor-core batched column {r}: vs direct |du| {eu:.2e} |dp| {ep:.2e}")
+        assert eu < 1e-8 and ep < 1e-8
     its = sum(i["krylov_its_total"] for i in infos)
     its32 = sum(i["krylov_its_total"] for i in infos32)
     assert its <= 1.5 * its32 + 4 * nrhs
