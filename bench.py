@@ -184,6 +184,64 @@ def sweep_bytes(mesh, k, word, mat_word=None):
     return int(mat + vec + scales)
 
 
+def patch_facet_counts(mesh):
+    """Interior facets of every vertex patch (vertices with at least one) and cells of its star."""
+    import numpy as np
+    c = mesh.cells
+    e = np.concatenate([c[:, [1, 2]], c[:, [0, 2]], c[:, [0, 1]]])
+    e.sort(axis=1)
+    uniq, cnt = np.unique(e, axis=0, return_counts=True)
+    interior = uniq[cnt == 2]
+    nv = mesh.coords.shape[0]
+    nf = np.bincount(interior.ravel(), minlength=nv)
+    ncell = np.bincount(c.ravel(), minlength=nv)
+    m = nf > 0
+    return nf[m], ncell[m], int(interior.shape[0])
+
+
+def survey_bytes(meshes, k, s_p=4, s_v=4, restart=30, m=1, growth=2):
+    """Algorithmic bytes of the hot path by the per-unit model of the scope table
+    (packed symmetric element matrices and patch inverses, each read once per use):
+      A1  outer apply (FP64):        B_A + 2 N 8
+      A2  one order-k sweep:         B_P + B_A' + 3 N s_v
+      residual before Pi_k^0:        B_A' + 2 N s_v
+      A4  MG_h, level l >= 1:        2 m(l) (B_P0 + B_A0 + 3 N_l s_v) + B_A0 + 4 N_l s_v,  m(J) = m,
+                                     m(l-1) = growth m(l); level 0: the dense FP64 inverse, n0^2 8
+      A6  CGS2 + flexible basis:     (4 restart/2 + 6) N 8
+    B_A = n_cells n_loc (n_loc+1)/2 x 8, B_A' the same at s_p bytes, B_P = sum over patches of
+    np (np+1)/2 x s_p; lowest-order quantities with dpf = 2."""
+    dpf = 2 * (k + 1)
+    nloc = 3 * dpf
+    fine = meshes[-1]
+    nf, _, n_int = patch_facet_counts(fine)
+    N = n_int * dpf
+    ncell = fine.cells.shape[0]
+    npp = nf * dpf
+    B_A = ncell * nloc * (nloc + 1) // 2 * 8
+    B_Ap = ncell * nloc * (nloc + 1) // 2 * s_p
+    B_P = int((npp * (npp + 1) // 2).sum()) * s_p
+    out = {"A1_apply_fp64": B_A + 2 * N * 8,
+           "A2_sweep": B_P + B_Ap + 3 * N * s_v,
+           "residual_fp32": B_Ap + 2 * N * s_v,
+           "A6_krylov": (4 * restart // 2 + 6) * N * 8}
+    a4 = 0
+    J = len(meshes) - 1
+    ml = m
+    for l in range(J, 0, -1):
+        nf0, _, n0 = patch_facet_counts(meshes[l])
+        N0 = 2 * n0
+        B_P0 = int((2 * nf0 * (2 * nf0 + 1) // 2).sum()) * s_p
+        B_A0 = meshes[l].cells.shape[0] * 21 * s_p
+        a4 += 2 * ml * (B_P0 + B_A0 + 3 * N0 * s_v) + B_A0 + 4 * N0 * s_v
+        ml *= growth
+    _, _, nc0 = patch_facet_counts(meshes[0])
+    a4 += (2 * nc0) ** 2 * 8
+    out["A4_mg_h"] = a4
+    out["B_it"] = (out["A1_apply_fp64"] + 2 * m * out["A2_sweep"] + out["residual_fp32"] + a4 + out["A6_krylov"])
+    out["skeleton_dofs"] = N
+    return out
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -283,8 +341,10 @@ def reference_arm(args):
     except Exception:
         cores = os.cpu_count()
     val = h.n_dof * its / dt
-    # the same config as the GPU arm (the full workload); the sample is described in cpu_baseline
-    cfg = config(args, full_skeleton_dofs(args.N, args.k), full_levels(args))
+    # the config of what this arm times: the 32x32 sample of the workload
+    sample_args = argparse.Namespace(**{**vars(args), "N": N, "N0": min(args.N0, N)})
+    cfg = config(sample_args, h.n_dof, nl)
+    cfg["sample_of"] = f"{args.N}x{args.N} workload of the GPU arm ({full_skeleton_dofs(args.N, args.k)} skeleton DOFs)"
     sample = (f"{N}x{N} triangulation, {h.n_dof} skeleton DOFs, {nl} levels: a bounded CPU sample of the "
               f"{args.N}x{args.N} workload, timed over {args.steps} full solve(s)")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
@@ -314,6 +374,7 @@ def gpu_arm(args):
     # replicas only: every rank solves its own copy of the workload (no data-path collective)
     ms, fv = workload(args)
     _FINE["mesh"] = ms[-1]
+    _FINE["meshes"] = ms
     ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=local)
     forcing = torch.tensor(fv, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -413,9 +474,15 @@ def gpu_arm(args):
     line["roofline_fp16_sweep"] = roofline(args, ctx, hdg, torch, dev, stream, sizes,
                                            precision=hdg.HDG_MIXED_FP16)
     ctx.close()
+    fp64 = fp64_peak(hdg, torch, dev, stream)
+    line["breakdown_mixed_iteration"] = breakdown(args, ms, hdg, torch, dev, stream, head["ms_per_iter"], fp64)
+    comp = line["breakdown_mixed_iteration"]["components"]
+    line["roofline"]["share_of_iteration"] = comp["order_k_sweeps"]["share_of_iteration"]
+    line["roofline"]["largest_share"] = max((c for c in comp), key=lambda c: comp[c]["ms"])
     if not args.no_extra_forms:
         line["forms"]["batched_mixed_fp32"] = batched_form(args, hdg, torch, dev, stream, world)
         line["forms"]["oseen_mixed_fp32"] = oseen_form(args, hdg, torch, dev, stream)
+        line["forms"]["coarsest_level_mixed_fp32"] = coarsest_form(args, hdg, torch, dev, stream)
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
@@ -531,6 +598,33 @@ def uneven_meshes_form(hdg, torch, dev, stream, world):
             "timing": "concurrent time is host wall clock around hdg_solve_batched, which synchronises"}
 
 
+def coarsest_form(args, hdg, torch, dev, stream):
+    """The headline workload (mixed form) with coarser or finer coarsest CR levels: fewer levels
+    trade colour-phase launches of the small levels for a larger dense FP64 coarse inverse."""
+    from workloads import unit_square_hierarchy, curl_bubble_2d, forcing_at_lattice
+    out = {}
+    for N0 in (4, 16, 32):
+        if N0 == args.N0 or args.N % N0:
+            continue
+        nl = 1
+        while N0 * 2 ** (nl - 1) < args.N:
+            nl += 1
+        ms = unit_square_hierarchy(N0, nl)
+        fine = ms[-1]
+        fv = forcing_at_lattice(fine.coords, fine.cells, args.k, curl_bubble_2d().forcing(args.nu, args.beta))
+        ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=dev.index or 0)
+        prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma, precision=hdg.HDG_MIXED_FP32)
+        F = hdg.hdg_condense(ctx, prm, torch.tensor(fv, device=dev))
+        hdg.hdg_solve(ctx, F)
+        t, (_, _, info) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F))
+        n = ctx.sizes().n_dof
+        out[f"{N0}x{N0}"] = {"levels": nl, "time_to_tol_s": t, "fgmres_iters": info["krylov_its_total"],
+                             "krylov_its": info["krylov_its"], "dof_iters_per_s": n * info["krylov_its_total"] / t,
+                             "ms_per_iter": 1e3 * t / info["krylov_its_total"]}
+        ctx.close()
+    return out
+
+
 def oseen_form(args, hdg, torch, dev, stream):
     """Oseen: 128x128 (32,768 triangles), k = 2, gamma = 1e2, beta = 0, upwind
     convection by b = curl(sin^2(pi x) sin^2(pi y)) scaled to max|b| = 1, nu = 1/Re."""
@@ -561,6 +655,97 @@ def oseen_form(args, hdg, torch, dev, stream):
     out["skeleton_dofs"] = int(ctx.sizes().n_dof)
     ctx.close()
     return out
+
+
+def _event_ms(torch, stream, fn, reps):
+    """Mean milliseconds of fn() over reps calls, CUDA events on `stream`, after one warm-up."""
+    fn()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(reps):
+        fn()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1) / reps
+
+
+def fp64_peak(hdg, torch, dev, stream):
+    """FP64 FMA rate of this GPU (TFLOP/s) from the library's probe kernel, best of 3."""
+    out = torch.zeros(1, dtype=torch.float64, device=dev)
+    best = 0.0
+    for _ in range(3):
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        flops = hdg.hdg_fp64_fma_probe(out, 8, 1 << 15)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, flops / (ev0.elapsed_time(ev1) / 1e3) / 1e12)
+    return best
+
+
+def breakdown(args, ms, hdg, torch, dev, stream, ms_per_iter, fp64_tflops):
+    """One FGMRES iteration of the mixed form taken apart with CUDA events: the preconditioner
+    application, its two order-k sweeps and its lowest-order V-cycle MG_h, the FP64 outer apply,
+    and the rest (Gram-Schmidt, Givens, the per-iteration residual read); each against the
+    scope table's algorithmic bytes (survey_bytes) and the measured HBM peak, the FP64 apply
+    also against the FP64 FMA rate."""
+    peaks = measured_peaks()
+    peak = peaks.get("hbm_gbs", 6800.0)
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=dev.index or 0)
+    prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma, precision=hdg.HDG_MIXED_FP32)
+    hdg.hdg_condense(ctx, prm, None)
+    n = ctx.sizes().n_dof
+    gen = torch.Generator(device=dev).manual_seed(3)
+    r = torch.randn(n, dtype=torch.float64, device=dev, generator=gen)
+    z = torch.empty_like(r)
+    n0 = int(ctx.sizes().n_dof_level[len(ms) - 1])
+    g0 = torch.randn(n0, dtype=torch.float64, device=dev, generator=gen)
+    u0 = torch.empty_like(g0)
+    t_pc = _event_ms(torch, stream, lambda: hdg.hdg_precond_apply(ctx, r, z), 10)
+    # MG_h is several hundred small launches: capture one application in a CUDA graph and time
+    # its replays, as the preconditioner's own graph runs it inside hdg_precond_apply
+    hdg.hdg_mg_h(ctx, g0, u0)
+    torch.cuda.synchronize()
+    side = torch.cuda.Stream(device=dev)
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side, capture_error_mode="relaxed"):
+        hdg.hdg_mg_h(ctx, g0, u0)
+    t_mgh = _event_ms(torch, stream, graph.replay, 10)
+    t_ap = _event_ms(torch, stream, lambda: hdg.hdg_apply(ctx, r, z), 10)
+    u = torch.zeros_like(r)
+    t_sw = _event_ms(torch, stream, lambda: hdg.hdg_smooth(ctx, -1, r, u, 4, False), 3) / 4
+    ctx.close()
+    b = survey_bytes(ms, args.k)
+    dpf = 2 * (args.k + 1)
+    nloc = 3 * dpf
+    ncell = ms[-1].cells.shape[0]
+    comp = {
+        "order_k_sweeps": {"ms": 2 * t_sw, "bytes": 2 * b["A2_sweep"],
+                           "kernel": "gs_tma_kernel<8> (x 2 sweeps x 3 colours)"},
+        "mg_h": {"ms": t_mgh, "bytes": b["A4_mg_h"],
+                 "kernel": "lowest-order V-cycle: gs0t_kernel/gs0_kernel<float,16>, transfers, coarse GEMV"},
+        "apply_fp64": {"ms": t_ap, "bytes": b["A1_apply_fp64"], "kernel": "apply_kernel<double,8>",
+                       "fp64_tflops": 2.0 * ncell * nloc * nloc / (t_ap / 1e3) / 1e12},
+    }
+    rest = ms_per_iter - t_pc - t_ap
+    comp["krylov_and_rest"] = {"ms": rest, "bytes": b["A6_krylov"],
+                               "kernel": "dots_kernel, update_dots_kernel, givens, scale (CGS2)"}
+    comp["precond_other"] = {"ms": t_pc - 2 * t_sw - t_mgh, "bytes": b["residual_fp32"],
+                             "kernel": "FP32 residual apply, Pi_k^0 transfers, conversions"}
+    for c in comp.values():
+        c["share_of_iteration"] = c["ms"] / ms_per_iter
+        c["achieved_gbs"] = c["bytes"] / (c["ms"] / 1e3) / 1e9 if c["ms"] > 0 else None
+        c["frac_of_hbm"] = c["achieved_gbs"] / peak if c["achieved_gbs"] else None
+    comp["apply_fp64"]["frac_of_fp64"] = comp["apply_fp64"]["fp64_tflops"] / fp64_tflops if fp64_tflops else None
+    return {"ms_per_iter": ms_per_iter, "precond_ms": t_pc, "components": comp,
+            "fp64_fma_tflops_measured": fp64_tflops,
+            "survey_bytes_per_iteration": b["B_it"],
+            "iteration_frac_of_hbm": b["B_it"] / (ms_per_iter / 1e3) / 1e9 / peak,
+            "ideal_ms_per_iter": b["B_it"] / (peak * 1e9) * 1e3}
 
 
 def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
@@ -601,14 +786,17 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
     ev3.record(stream)
     torch.cuda.synchronize()
     t_sweep = (ev0.elapsed_time(ev1) - ev2.elapsed_time(ev3)) / 1e3 / n_sweeps
-    alg = sweep_bytes(ctx_mesh_fine(args), k, 4, 2 if half else 4)
+    # algorithmic bytes by the scope table's per-unit model (packed symmetric element matrices
+    # and patch inverses read once per sweep), and by the kernel's own full-storage access count
+    alg = survey_bytes(_FINE["meshes"], k, s_p=2 if half else 4)["A2_sweep"]
+    alg_kernel = sweep_bytes(ctx_mesh_fine(args), k, 4, 2 if half else 4)
     achieved = alg / t_sweep / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     # DRAM bytes of one sweep from an ncu capture of the same kernel on the 128x128, k = 3 case
     # (TMA_SWEEP_TRAFFIC_128).  Traffic grows with the number of patches like the algorithmic
     # bytes, so the full-size figure is that ratio times the full-size algorithmic bytes
     # (k = 3 only; other k were not captured).
-    traffic = alg * (TMA_SWEEP_TRAFFIC_128 / 318199104) if k == 3 and not half and TMA_SWEEP_TRAFFIC_128 else None
+    traffic = alg_kernel * (TMA_SWEEP_TRAFFIC_128 / 318199104) if k == 3 and not half and TMA_SWEEP_TRAFFIC_128 else None
     kname = "gs_kernel<float, 8, __half> (order-k block GS sweep on binary16 copies" if half else \
         "gs_tma_kernel<8> (order-k block GS sweep, matrices staged by cp.async.bulk"
     rs = read_stream_gbs(torch, dev, stream)
@@ -617,7 +805,12 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
             "traffic_note": "scaled from an ncu capture at 128x128 (same kernel, cold caches)" if traffic else None,
-            "algorithmic_bytes_per_sweep": alg, "sweep_ms": t_sweep * 1e3,
+            "traffic_over_algorithmic": traffic / alg if traffic else None,
+            "algorithmic_bytes_per_sweep": alg,
+            "bytes_model": "scope table per-unit model: B_P + B_A' + 3 N s_v (packed symmetric)",
+            "kernel_access_bytes_per_sweep": alg_kernel,
+            "frac_by_kernel_access_bytes": alg_kernel / t_sweep / 1e9 / peak,
+            "sweep_ms": t_sweep * 1e3,
             "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if "hbm_gbs" in peaks else "fallback"}
 
 

@@ -447,6 +447,15 @@ hdg_status hdg_restrict_noalloc(hdg_ctx *ctx, int level, const double *rf, doubl
  * Needs no GPU. */
 int64_t hdg_reference_tables(int k, double *out);
 
+/* Measurement utility (no counterpart in the paper): enqueues on `stream` one
+ * kernel of FP64 fused multiply-adds on the current device, blocks_per_sm
+ * (1..64) blocks of 256 threads per SM, each thread running 8 independent FMA
+ * chains for iters iterations, and writes one double to out (device, >= 1
+ * double).  Returns the kernel's floating-point operations (2 per FMA), so a
+ * caller that times the launch with CUDA events on `stream` obtains the FP64
+ * arithmetic rate of the GPU; returns -1 for bad arguments or a launch error. */
+int64_t hdg_fp64_fma_probe(int blocks_per_sm, int64_t iters, double *out, hdg_stream_t stream);
+
 /* Number of CUDA kernels this library has enqueued in the calling process
  * (all contexts, all streams), for launch accounting in benchmarks. */
 uint64_t hdg_kernel_launches(void);

@@ -40,7 +40,7 @@ EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_check_hier
            "hdg_apply", "hdg_precond_apply", "hdg_solve", "hdg_recover", "hdg_adjoint", "hdg_get_sizes",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
-           "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_set_wait_limit", "hdg_apply_multi",
+           "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_set_wait_limit", "hdg_fp64_fma_probe", "hdg_apply_multi",
            "hdg_precond_apply_multi", "hdg_smooth_multi", "hdg_set_batched_tile", "hdg_tune_batched", "hdg_solve_multi", "hdg_solve_batched", "hdg_picard", "hdg_newton",
            "hdg_destroy",
            "hdg_status_string", "hdg_last_error")
@@ -172,6 +172,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "hdg_restrict": (I, [P, I, P, P, P]),
         "hdg_restrict_noalloc": (I, [P, I, P, P, P]),
         "hdg_set_wait_limit": (I, [P, ctypes.c_int64]),
+        "hdg_fp64_fma_probe": (ctypes.c_int64, [I, ctypes.c_int64, P, P]),
         "hdg_coarse_solve": (I, [P, P, P, P]),
         "hdg_mg_h": (I, [P, P, P, P]),
         "hdg_kernel_launches": (ctypes.c_uint64, []),
@@ -522,6 +523,14 @@ def hdg_level_apply(ctx: Context, level: int, x, y=None, stream=None):
     y = torch.empty_like(x) if y is None else y
     ctx.check(load_library().hdg_level_apply(ctx.handle, level, _ptr(x), _ptr(y), _stream(stream)))
     return y
+
+
+def hdg_fp64_fma_probe(out, blocks_per_sm: int = 8, iters: int = 1 << 16, stream=None) -> int:
+    """Enqueue the FP64 FMA-rate kernel (out: CUDA float64 tensor, >= 1 element); returns its FLOPs."""
+    n = load_library().hdg_fp64_fma_probe(blocks_per_sm, iters, _ptr(out), _stream(stream))
+    if n < 0:
+        raise HdgError(1, "hdg_fp64_fma_probe: bad arguments or launch error")
+    return int(n)
 
 
 def hdg_set_wait_limit(ctx: Context, first_wait_ns: int):

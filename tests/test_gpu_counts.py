@@ -1,0 +1,46 @@
+"""Iteration counts in mesh size on the device: h-robustness of the hp-multigrid.
+
+Theorem 3.2 makes the variable V-cycle on the lowest-order levels a preconditioner
+whose condition number is bounded independently of h and eps; Section 5.2.1 reports
+PCG counts that grow over the first refinements and then stay flat.  The library runs
+the same iteration as the oracle (same counts in FP64, tested elsewhere), so the trend
+is measured here at sizes the oracle cannot reach: the first augmented-Lagrangian
+Uzawa step (FGMRES on A^eps u = F from zero, relative 1e-8) for N = 32 .. 512 with the
+coarsest level 2x2, as in the paper's hierarchies.
+"""
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from workloads import unit_square_hierarchy, curl_bubble_2d, forcing_at_lattice
+
+pytestmark = pytest.mark.gpu
+
+
+def _first_step_its(hdg, N, k, gamma, precision):
+    nl = 1
+    while 2 * 2 ** (nl - 1) < N:
+        nl += 1
+    ms = unit_square_hierarchy(2, nl)
+    fine = ms[-1]
+    fv = forcing_at_lattice(fine.coords, fine.cells, k, curl_bubble_2d().forcing(1.0, 1.0))
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    F = hdg.hdg_condense(ctx, hdg.Params(k=k, beta=1.0, gamma=gamma, precision=precision),
+                         torch.tensor(fv, device="cuda:0"))
+    o = hdg.default_solve_opts()
+    o.max_uzawa = 1
+    _, _, info = hdg.hdg_solve(ctx, F, opts=o, raise_on_nonconvergence=False)
+    ctx.close()
+    return info["krylov_its"][0]
+
+
+@pytest.mark.parametrize("k,gamma", [(2, 1e2), (2, 1e4), (3, 1e2)])
+def test_counts_flatten_under_refinement(k, gamma):
+    import paper_2303_06762_gb300 as hdg
+    sizes = (32, 64, 128, 256, 512)
+    its = [_first_step_its(hdg, N, k, gamma, hdg.HDG_FP64) for N in sizes]
+    print(f"k={k} gamma={gamma:g}: first-step FGMRES iterations for N={sizes}: {its}")
+    tail = its[2:]
+    # flat over the last three refinements (N = 128 .. 512), and no growth beyond them
+    assert max(tail) - min(tail) <= 3, its
+    assert its[-1] - its[2] <= 3, its
