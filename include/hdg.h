@@ -163,6 +163,15 @@ typedef struct {
     double res_mom;             /* final |g - A^eps u| of the last inner solve      */
     double dp_rel;              /* last |p^n - p^{n-1}|_L2 / |p^n|_L2               */
     double normF;               /* |F|_2                                            */
+    double div_l2;              /* |div u_h|_L2(Omega) of the returned velocity     */
+                                /* (div u_h is constant on each cell: its facet     */
+                                /* fluxes over |K|); -1 from the batched solves     */
+    double res_floor;           /* the inner solves' final absolute floor: the      */
+                                /* larger of floor_rel |F|, atol and twice the      */
+                                /* residual at which an inner FGMRES stagnated on   */
+                                /* round-off (a restart cycle whose Givens estimate */
+                                /* met the tolerance but whose true residual fell   */
+                                /* by less than half; Remark 3.1)                   */
 } hdg_solve_info;
 
 typedef struct {

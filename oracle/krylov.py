@@ -20,6 +20,8 @@ TEST INFRASTRUCTURE ONLY.
   floor_rel·‖F‖ (default 1e-10; Remark 3.1: much smaller residuals are
   round-off at large ε⁻¹):
   ‖g − A^ε u‖ <= max(rtol·‖g − A^ε u_start‖, floor_rel·‖F‖, atol).
+  An inner solve that stagnates on round-off (see ``fgmres``) raises the floor
+  to twice its final residual for the later Uzawa steps.
   The outer loop stops once the pressure error estimate of a linearly
   converging iteration, ρ/(1−ρ)·‖p⁽ⁿ⁾ − p⁽ⁿ⁻¹⁾‖ with ρ the observed ratio of
   successive updates (Lemma 3.1 gives ρ = ε/(ε+μ0)), is <= uzawa_tol·‖p⁽ⁿ⁾‖
@@ -29,22 +31,30 @@ TEST INFRASTRUCTURE ONLY.
 from __future__ import annotations
 
 from dataclasses import dataclass, field
-from typing import Callable, List
+from typing import Callable, List, Optional
 
 import numpy as np
 import scipy.linalg as sla
 
 
 def fgmres(A, b, x0, M: Callable, rtol: float = 1e-8, atol: float = 1e-10,
-           restart: int = 30, max_it: int = 1000):
+           restart: int = 30, max_it: int = 1000, info: Optional[dict] = None):
     """Solve A x = b to ‖r‖ <= max(rtol‖r0‖, atol).
 
-    Returns (x, iterations, final residual norm, history of residual norms).
+    Returns (x, iterations, final residual norm, history of residual norms).  A
+    restart cycle that ends because the Givens estimate met the tolerance while the
+    true residual did not shows round-off in the residual (Remark 3.1); when the
+    next such cycle cuts the true residual by less than half the solve stops as
+    stagnated (info["stagnated"] = True when a dict is passed).
     """
     x = np.array(x0, dtype=np.float64, copy=True)
     total = 0
     hist = []
     tol = None
+    beta_prev = None
+    est_reached = False
+    if info is not None:
+        info["stagnated"] = False
     while True:
         r = b - A @ x
         beta = float(np.linalg.norm(r))
@@ -53,6 +63,12 @@ def fgmres(A, b, x0, M: Callable, rtol: float = 1e-8, atol: float = 1e-10,
         hist.append(beta)
         if beta <= tol or total >= max_it:
             return x, total, beta, hist
+        if est_reached and beta_prev is not None and beta > 0.5 * beta_prev:
+            if info is not None:
+                info["stagnated"] = True
+            return x, total, beta, hist
+        beta_prev = beta
+        est_reached = False
         n = b.shape[0]
         V = np.zeros((restart + 1, n))
         Z = np.zeros((restart, n))
@@ -90,6 +106,8 @@ def fgmres(A, b, x0, M: Callable, rtol: float = 1e-8, atol: float = 1e-10,
             total += 1
             j_end = j
             hist.append(abs(g[j + 1]))
+            if abs(g[j + 1]) <= tol:
+                est_reached = True
             if abs(g[j + 1]) <= tol or total >= max_it or hn == 0.0:
                 break
             V[j + 1] = w / hn
@@ -107,6 +125,8 @@ class UzawaResult:
     res_div: float = 0.0
     dp_rel: float = 0.0
     normF: float = 0.0
+    div_l2: float = 0.0      # ‖div u_h‖_L2: div u_h is the cell flux sum over |K| on every cell
+    res_floor: float = 0.0   # final inner floor (raised on stagnation)
 
 
 def uzawa(Aeps, D, area, eps_inv, F, M: Callable, rtol: float = 1e-8, atol: float = 1e-10,
@@ -121,9 +141,15 @@ def uzawa(Aeps, D, area, eps_inv, F, M: Callable, rtol: float = 1e-8, atol: floa
     ndp_prev = None
     for n in range(max_uzawa):
         g = F + D.T @ p
+        fi = {}
         u, its, rn, _ = fgmres(Aeps, g, u, M, rtol=rtol, atol=floor, restart=restart,
-                               max_it=max_it)
+                               max_it=max_it, info=fi)
+        # an inner solve that stagnated on round-off raises the floor of the later ones
+        if fi["stagnated"]:
+            floor = max(floor, 2.0 * rn)
+        res.res_floor = floor
         du = D @ u
+        res.div_l2 = float(np.sqrt(np.sum(du ** 2 / area)))
         dp = eps_inv * du / area
         p = p - dp
         res.krylov_its.append(its)

@@ -85,12 +85,13 @@ class SolveOpts(ctypes.Structure):
 class SolveInfo(ctypes.Structure):
     _fields_ = [("uzawa_its", ctypes.c_int), ("krylov_its_total", ctypes.c_int),
                 ("krylov_its", ctypes.c_int * 64), ("res_mom", ctypes.c_double),
-                ("dp_rel", ctypes.c_double), ("normF", ctypes.c_double)]
+                ("dp_rel", ctypes.c_double), ("normF", ctypes.c_double), ("div_l2", ctypes.c_double),
+                ("res_floor", ctypes.c_double)]
 
     def as_dict(self):
         return dict(uzawa_its=self.uzawa_its, krylov_its_total=self.krylov_its_total,
                     krylov_its=list(self.krylov_its[:self.uzawa_its]), res_mom=self.res_mom,
-                    dp_rel=self.dp_rel, normF=self.normF)
+                    dp_rel=self.dp_rel, normF=self.normF, div_l2=self.div_l2, res_floor=self.res_floor)
 
 
 class Sizes(ctypes.Structure):

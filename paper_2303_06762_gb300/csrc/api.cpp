@@ -74,6 +74,7 @@ void free_operator(DevOperator &op) {
     dfree(op.Fel);
     dfree(op.Pinv);
     dfree(op.Pinvf);
+    dfree(op.Pinvp);
     dfree(op.Ah);
     dfree(op.Ah_s);
     dfree(op.Pinvh);
@@ -457,16 +458,22 @@ void ensure_krylov(hdg_ctx *ctx, int R) {
 struct FgmresOut {
     int its;
     double res;
+    bool stagnated;
 };
 
-// flexible GMRES on A^eps x = b: stop at |r| <= max(rtol |r0|, atol)
+// flexible GMRES on A^eps x = b: stop at |r| <= max(rtol |r0|, atol).  A restart cycle that
+// ended because the Givens estimate reached the tolerance while the true residual did not
+// is the mark of round-off in the residual (Remark 3.1: the augmented-Lagrangian term
+// magnifies it); when the next such cycle reduces the true residual by less than half, the
+// solve stops as stagnated at the attainable level.
 FgmresOut fgmres(hdg_ctx *ctx, const double *b, double *x, double rtol, double atol, int R,
                  int max_it, cudaStream_t s) {
     const int64_t n = ctx->n_dof;
     SmallLayout Ly{R};
     double *V = ctx->V.p, *Z = ctx->Z.p, *w = ctx->w.p, *sm = ctx->small.p, *pt = ctx->partials.p;
     int total = 0;
-    double tol = -1.0, beta = 0.0;
+    double tol = -1.0, beta = 0.0, beta_prev = -1.0;
+    bool est_reached = false, stagnated = false;
     while (true) {
         apply_k(ctx, x, b, V, s);   // V0 = b - A x
         CK(launch_dots(V, 1, 0, V, n, pt, s));
@@ -478,6 +485,12 @@ FgmresOut fgmres(hdg_ctx *ctx, const double *b, double *x, double rtol, double a
         }
         if (tol < 0) tol = std::max(rtol * beta, atol);
         if (beta <= tol || total >= max_it) break;
+        if (est_reached && beta_prev >= 0 && beta > 0.5 * beta_prev) {
+            stagnated = true;
+            break;
+        }
+        beta_prev = beta;
+        est_reached = false;
         CK(launch_init_cycle(V, V, n, sm, R, s));
         int m = 0;
         for (int j = 0; j < R; ++j) {
@@ -502,11 +515,12 @@ FgmresOut fgmres(hdg_ctx *ctx, const double *b, double *x, double rtol, double a
                 ctx->err = "non-finite residual estimate";
                 throw Fail{HDG_ERR_NONFINITE};
             }
+            if (res <= tol) est_reached = true;
             if (res <= tol || total >= max_it || hn == 0.0) break;
         }
         CK(launch_solve_update(sm, m, R, Z, n, x, n, s));
     }
-    return {total, beta};
+    return {total, beta, stagnated};
 }
 
 const double *cell_nu_of(hdg_ctx *ctx, int l) {
@@ -561,7 +575,9 @@ hdg_status uzawa_solve(hdg_ctx *ctx, const double *F, double *u, double *p, cons
     const double normF = norm2(ctx, F, ctx->n_dof, s);
     loc = hdg_solve_info{};
     loc.normF = normF;
-    const double floor_abs = std::max(o.floor_rel * normF, o.atol);
+    // inner floor: floor_rel |F| (and atol), raised to twice the residual at which an inner
+    // solve stagnated on round-off, so that later Uzawa steps do not chase it again
+    double floor_abs = std::max(o.floor_rel * normF, o.atol);
     double *g = ctx->kt.p;
     double ndp_prev = -1.0;
     bool done = false;
@@ -573,13 +589,16 @@ hdg_status uzawa_solve(hdg_ctx *ctx, const double *F, double *u, double *p, cons
         loc.uzawa_its = it + 1;
         loc.res_mom = fo.res;
         if (fo.its >= o.max_it) conv = HDG_ERR_NOT_CONVERGED;
+        if (fo.stagnated) floor_abs = std::max(floor_abs, 2.0 * fo.res);
+        loc.res_floor = floor_abs;
         CK(launch_uzawa_update(LJ, k, u, p, ctx->prm.gamma, ctx->prm.nu, cell_nu_of(ctx, J), ctx->partials.p, s));
         SmallLayout Ly{o.restart};
-        CK(launch_reduce_partials(ctx->partials.p, 3, ctx->small.p + Ly.h1(), 0, s));
-        CK(cudaMemcpyAsync(ctx->h_pinned, ctx->small.p + Ly.h1(), 3 * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(launch_reduce_partials(ctx->partials.p, 4, ctx->small.p + Ly.h1(), 0, s));
+        CK(cudaMemcpyAsync(ctx->h_pinned, ctx->small.p + Ly.h1(), 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         const double ndp = std::sqrt(std::max(ctx->h_pinned[0], 0.0));
         const double npn = std::sqrt(std::max(ctx->h_pinned[1], 0.0));
+        loc.div_l2 = std::sqrt(std::max(ctx->h_pinned[3], 0.0));
         loc.dp_rel = npn > 0 ? ndp / npn : 0.0;
         if (!std::isfinite(ndp) || !std::isfinite(npn)) {
             ctx->err = "non-finite pressure update";
@@ -903,6 +922,7 @@ struct FgmresOutM {
     int its;                    // lockstep iterations
     std::vector<int> its_r;     // iterations each column was active
     std::vector<double> res_r;  // last true residual norm per column
+    std::vector<char> stag_r;   // column stopped as stagnated on round-off (see fgmres)
 };
 
 // flexible GMRES on A^eps X = B for R columns; column r stops at |r_r| <= max(rtol |r_r0|, atol_r[r])
@@ -914,8 +934,9 @@ FgmresOutM fgmres_m(hdg_ctx *ctx, const double *b, double *x, double rtol, const
     DevLevel &LJ = ctx->L[ctx->n_levels - 1];
     double *V = ctx->mV.p, *Z = ctx->mZ.p, *w = ctx->mw.p, *sm = ctx->msmall.p, *pt = ctx->mpart.p;
     double *hb = ctx->mhbuf.p;
-    FgmresOutM out{0, std::vector<int>(R, 0), std::vector<double>(R, 0.0)};
-    std::vector<double> tol(R, -1.0), beta(R);
+    FgmresOutM out{0, std::vector<int>(R, 0), std::vector<double>(R, 0.0), std::vector<char>(R, 0)};
+    std::vector<double> tol(R, -1.0), beta(R), beta_prev(R, -1.0);
+    std::vector<char> est(R, 0);   // the column's last cycle ended on the Givens estimate
     std::vector<int> m_r(R);
     std::vector<char> done(R);
     // outer operator: FP64, or double-FP32 with the mixed preconditioner
@@ -943,7 +964,13 @@ FgmresOutM fgmres_m(hdg_ctx *ctx, const double *b, double *x, double rtol, const
             }
             if (tol[r] < 0) tol[r] = std::max(rtol * beta[r], atol_r[r]);
             out.res_r[r] = beta[r];
-            done[r] = skip[r] || beta[r] <= tol[r];
+            done[r] = skip[r] || beta[r] <= tol[r] || out.stag_r[r];
+            if (!done[r] && est[r] && beta_prev[r] >= 0 && beta[r] > 0.5 * beta_prev[r]) {
+                out.stag_r[r] = 1;
+                done[r] = 1;
+            }
+            if (!done[r]) beta_prev[r] = beta[r];
+            est[r] = 0;
             any = any || !done[r];
         }
         if (!any || out.its >= max_it) break;
@@ -977,6 +1004,7 @@ FgmresOutM fgmres_m(hdg_ctx *ctx, const double *b, double *x, double rtol, const
                 }
                 m_r[r] = j + 1;
                 out.its_r[r] += 1;
+                if (res <= tol[r]) est[r] = 1;
                 if (res <= tol[r] || hn == 0.0) done[r] = 1;
                 else all = false;
             }
@@ -1041,6 +1069,9 @@ hdg_status uzawa_solve_m(hdg_ctx *ctx, int nrhs, int R, const double *F, double 
             in.uzawa_its = it + 1;
             in.res_mom = fo.res_r[r];
             if (its >= o.max_it) conv = HDG_ERR_NOT_CONVERGED;
+            if (fo.stag_r[r]) floor_abs[r] = std::max(floor_abs[r], 2.0 * fo.res_r[r]);
+            in.res_floor = floor_abs[r];
+            in.div_l2 = -1.0;   // not computed by the batched update
             const double ndp = std::sqrt(std::max(ctx->h_multi[3 * r], 0.0));
             const double npn = std::sqrt(std::max(ctx->h_multi[3 * r + 1], 0.0));
             in.dp_rel = npn > 0 ? ndp / npn : 0.0;
@@ -1394,6 +1425,13 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
                        op.Fel.p, ctx->status_flag.p, RecoverArgs(), s));
     CK(launch_patch_inverse(LJ, op, ctx->has_conv ? 1 : 0, ctx->status_flag.p, s));
     op.tma_flag = ctx->wait_flag.p;
+    if (!ctx->has_conv && k >= 1 && prm->precision != HDG_FP64) {
+        // symmetric patch inverses: the FP32 sweep reads packed triangles (half the bytes)
+        dalloc(ctx, op.Pinvp, (size_t)LJ.n_patches * packed_patch_size(op.np_max));
+        CK(launch_pack_sym(LJ, op, s));
+    } else {
+        dfree(op.Pinvp);
+    }
     op.h_fmt = 0;
     if (k >= 1 && (prm->precision == HDG_MIXED_BF16 || prm->precision == HDG_MIXED_FP16)) {
         dalloc(ctx, op.Ah, (size_t)op.nloc * op.nloc * LJ.nc);

