@@ -144,6 +144,15 @@ typedef struct {
                              /* and C_h(u_old; u_old, v) to the load, so that the  */
                              /* solution is the new iterate.  Lowest-order levels  */
                              /* keep the Picard form.  NULL = no Newton term.      */
+    int smoother;            /* block smoother of every level (eq. bjac): 0 = block */
+                             /* Gauss-Seidel in colour order (Section 5), 1 =      */
+                             /* damped block Jacobi (all patches against one       */
+                             /* residual, corrections summed, times the damping)   */
+    double jacobi_damping;   /* the damping of smoother 1; <= 0 selects 0.5        */
+    int hp_additive;         /* 0 = Algorithm 2 (multiplicative); 1 = its additive  */
+                             /* form (Remark 3.4): z = R_sym r + Pi_0^k MG_h(Pi_k^0 */
+                             /* r), R_sym = m_p forward then m_p backward sweeps    */
+                             /* from zero; single-load calls only                   */
 } hdg_params;
 
 typedef struct {
@@ -154,6 +163,12 @@ typedef struct {
     int restart;        /* FGMRES restart length, 1..32                             */
     int max_it;         /* FGMRES iterations per inner solve                        */
     int max_uzawa;      /* Uzawa steps, 1..64                                       */
+    int krylov;         /* inner Krylov method: 0 = flexible GMRES (restart);       */
+                        /* 1 = preconditioned CG (the paper's method for the        */
+                        /* generalized Stokes problem, Section 5; needs a symmetric */
+                        /* operator and preconditioner: no convection, FP64 or the  */
+                        /* FP32 preconditioner).  Same stopping norm and targets.   */
+                        /* Single-load solves only.                                 */
 } hdg_solve_opts;
 
 typedef struct {
@@ -186,7 +201,7 @@ typedef struct {
 } hdg_sizes;
 
 /* Fill the defaults of Section 5: rtol 1e-8, atol 1e-10, floor_rel 1e-10,
- * uzawa_tol 1e-8, restart 30, max_it 1000, max_uzawa 64. */
+ * uzawa_tol 1e-8, restart 30, max_it 1000, max_uzawa 64, krylov 0 (FGMRES). */
 void hdg_default_solve_opts(hdg_solve_opts *opts);
 
 /* Sizes of a checked hierarchy (finest level). */

@@ -7,8 +7,9 @@ TEST INFRASTRUCTURE ONLY.
   Hessenberg matrix, stop when the Euclidean norm of the residual vector
   is <= an absolute target (the caller derives it from the relative 1e-8 /
   absolute 1e-10 settings of Section 5), restart length 30.  The Krylov
-  method is GMRES throughout because the mixed-precision preconditioner is
-  not exactly linear; the paper uses PCG for Stokes (Section 3.3).
+  method is GMRES by default because the mixed-precision preconditioner is
+  not exactly linear; the paper uses PCG for Stokes (Section 5), available
+  as ``pcg`` (symmetric problems and preconditioners only).
 * Uzawa (eq. stOpEq-ALU): p⁰ = 0;  A^ε u⁽ⁿ⁾ = F − B*p⁽ⁿ⁻¹⁾;
   p⁽ⁿ⁾ = p⁽ⁿ⁻¹⁾ − ε⁻¹ div u⁽ⁿ⁾ on every cell.  With the flux matrix D
   ((D u)_K = ∫_{∂K} u·n) this is  A^ε u = F + Dᵀp,  p_K ← p_K − ε⁻¹ (Du)_K/|K|.
@@ -116,6 +117,43 @@ def fgmres(A, b, x0, M: Callable, rtol: float = 1e-8, atol: float = 1e-10,
         x = x + Z[:m].T @ y
 
 
+def pcg(A, b, x0, M: Callable, rtol: float = 1e-8, atol: float = 1e-10, max_it: int = 1000):
+    """Preconditioned conjugate gradients (the paper's Krylov method for the generalized
+    Stokes problem, Section 5) for symmetric positive definite A and a symmetric
+    preconditioner M: stop when the recursively updated residual has
+    ‖r‖ <= max(rtol‖r0‖, atol), the same norm and targets as ``fgmres``.
+
+    Returns (x, iterations, final residual norm, history of residual norms).
+    """
+    x = np.array(x0, dtype=np.float64, copy=True)
+    r = b - A @ x
+    beta0 = float(np.linalg.norm(r))
+    tol = max(rtol * beta0, atol)
+    hist = [beta0]
+    if beta0 <= tol:
+        return x, 0, beta0, hist
+    z = M(r)
+    p = z.copy()
+    rz = float(r @ z)
+    its = 0
+    rn = beta0
+    while its < max_it:
+        q = A @ p
+        alpha = rz / float(p @ q)
+        x = x + alpha * p
+        r = r - alpha * q
+        its += 1
+        rn = float(np.linalg.norm(r))
+        hist.append(rn)
+        if rn <= tol:
+            break
+        z = M(r)
+        rz_new = float(r @ z)
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return x, its, rn, hist
+
+
 @dataclass
 class UzawaResult:
     u: np.ndarray
@@ -131,8 +169,10 @@ class UzawaResult:
 
 def uzawa(Aeps, D, area, eps_inv, F, M: Callable, rtol: float = 1e-8, atol: float = 1e-10,
           restart: int = 30, max_it: int = 1000, max_uzawa: int = 200,
-          uzawa_tol: float = 1e-8, floor_rel: float = 1e-10, u0=None) -> UzawaResult:
-    """Augmented-Lagrangian Uzawa with FGMRES inner solves (eq. stOpEq-ALU)."""
+          uzawa_tol: float = 1e-8, floor_rel: float = 1e-10, u0=None,
+          krylov: str = "fgmres") -> UzawaResult:
+    """Augmented-Lagrangian Uzawa with FGMRES (or, krylov="pcg", PCG) inner solves
+    (eq. stOpEq-ALU)."""
     normF = float(np.linalg.norm(F))
     u = np.zeros_like(F) if u0 is None else np.array(u0, copy=True)
     p = np.zeros(D.shape[0])
@@ -141,9 +181,12 @@ def uzawa(Aeps, D, area, eps_inv, F, M: Callable, rtol: float = 1e-8, atol: floa
     ndp_prev = None
     for n in range(max_uzawa):
         g = F + D.T @ p
-        fi = {}
-        u, its, rn, _ = fgmres(Aeps, g, u, M, rtol=rtol, atol=floor, restart=restart,
-                               max_it=max_it, info=fi)
+        fi = {"stagnated": False}
+        if krylov == "pcg":
+            u, its, rn, _ = pcg(Aeps, g, u, M, rtol=rtol, atol=floor, max_it=max_it)
+        else:
+            u, its, rn, _ = fgmres(Aeps, g, u, M, rtol=rtol, atol=floor, restart=restart,
+                                   max_it=max_it, info=fi)
         # an inner solve that stagnated on round-off raises the floor of the later ones
         if fi["stagnated"]:
             floor = max(floor, 2.0 * rn)

@@ -11,6 +11,8 @@ matrices with plain sequential loops, in the order the paper states.
   for each patch in turn u_s ← u_s + A_ss⁻¹ (g − A u)_s.  R^T, the transpose
   with respect to the skeleton inner product (eq. bjac and below), is the
   same sweep with the patches in reverse order.
+* Damped block Jacobi (eq. bjac, the smoother of the theory): all patches
+  against one residual, corrections summed and scaled by ς.
 * Averaging transfer I_{l−1}^l (eq. avgOpt): evaluate Π^CR of the coarse
   function at each fine facet midpoint (inside a coarse cell: that cell's
   value; on a coarse facet: the mean of the two sides); fine boundary facets
@@ -30,6 +32,8 @@ matrices with plain sequential loops, in the order the paper states.
   Π_k^0 (the transpose of the inclusion: the m = 0 normal and tangential
   coefficient of each facet), MG_h on the lowest-order operator of the same
   mesh, inclusion Π_0^k (injection of those coefficients), m_p reverse sweeps.
+  Its additive form (Remark 3.4) sums the symmetric relaxation of g and the
+  lowest-order correction of g.
 """
 
 from __future__ import annotations
@@ -81,6 +85,38 @@ class BlockGS:
         for (v, d), Ar, Ai in zip(reversed(self.patches), reversed(self.rows), reversed(self.inv)):
             u[d] += Ai @ (g[d] - Ar @ u)
         return u
+
+
+class BlockJacobi:
+    """Damped block Jacobi over vertex patches, eq. bjac: every patch solves against the
+    same residual and the corrections are summed, u ← u + ς Σ_s E_s A_ss⁻¹ E_sᵀ (g − A u).
+    For symmetric A the operator is symmetric, so R^T = R (the forward and backward
+    sweeps are the same step)."""
+
+    def __init__(self, A: sp.csr_matrix, patches, damping: float = 0.5):
+        self.A = A.tocsr()
+        self.patches = patches
+        self.damping = damping
+        self.inv = [np.linalg.inv(self.A[d, :][:, d].toarray()) for _, d in patches]
+
+    def forward(self, g, u):
+        r = g - self.A @ u
+        du = np.zeros_like(u)
+        for (v, d), Ai in zip(self.patches, self.inv):
+            du[d] += Ai @ r[d]
+        u += self.damping * du
+        return u
+
+    backward = forward
+
+
+def make_smoother(A: sp.csr_matrix, patches, smoother: str = "gs", damping: float = 0.5):
+    """Block Gauss–Seidel (Section 5) or damped block Jacobi (eq. bjac) over `patches`."""
+    if smoother == "gs":
+        return BlockGS(A, patches)
+    if smoother == "jacobi":
+        return BlockJacobi(A, patches, damping)
+    raise ValueError(smoother)
 
 
 def averaging_prolongation(coarse: Topology, fine: Topology, parent: np.ndarray) -> sp.csr_matrix:
@@ -139,10 +175,11 @@ def harmonic_prolongation(A_fine: sp.csr_matrix, I_avg: sp.csr_matrix, T: np.nda
 
 
 class Level:
-    def __init__(self, hdg: HDG):
+    def __init__(self, hdg: HDG, smoother: str = "gs", damping: float = 0.5):
         self.hdg = hdg
         self.A = hdg.matrix(with_al=True).tocsr()
-        self.gs = BlockGS(self.A, vertex_patches(hdg.topo, hdg.dpf))
+        # the level's smoother (named gs for block GS, the default; damped block Jacobi otherwise)
+        self.gs = make_smoother(self.A, vertex_patches(hdg.topo, hdg.dpf), smoother, damping)
         self.P: Optional[sp.csr_matrix] = None    # prolongation from the level below
 
 
@@ -195,21 +232,35 @@ def inclusion_matrix(n_int: int, k: int) -> sp.csr_matrix:
 
 
 class MGhp:
-    """Algorithm 2: z = MG_hp(g, 0, m_p, m_h, q)."""
+    """Algorithm 2: z = MG_hp(g, 0, m_p, m_h, q).
 
-    def __init__(self, hdg_k: HDG, mgh: MGh, m_p: int = 1, m_h: int = 1, q: int = 1):
+    additive=True gives the additive form of the same space decomposition (Remark 3.4,
+    eq. hpSubspace): the relaxation part (m_p forward then m_p backward sweeps from zero)
+    and the lowest-order correction Π_0^k MG_h(Π_k^0 g) are both computed from g and
+    summed, z = R_sym g + Π_0^k MG_h(Π_k^0 g)."""
+
+    def __init__(self, hdg_k: HDG, mgh: MGh, m_p: int = 1, m_h: int = 1, q: int = 1,
+                 smoother: str = "gs", damping: float = 0.5, additive: bool = False):
         self.hdg = hdg_k
         self.A = hdg_k.matrix(with_al=True).tocsr()
         self.k = hdg_k.k
         self.mgh = mgh
         self.m_p, self.m_h, self.q = m_p, m_h, q
+        self.additive = additive
         if self.k > 0:
-            self.gs = BlockGS(self.A, vertex_patches(hdg_k.topo, hdg_k.dpf))
+            self.gs = make_smoother(self.A, vertex_patches(hdg_k.topo, hdg_k.dpf), smoother, damping)
             self.Pi = inclusion_matrix(hdg_k.topo.n_interior, self.k)
 
     def __call__(self, g, u0=None):
         if self.k == 0:
             return self.mgh(g, self.m_h, self.q, u0)
+        if self.additive:
+            z = np.zeros_like(g)
+            for _ in range(self.m_p):
+                self.gs.forward(g, z)
+            for _ in range(self.m_p):
+                self.gs.backward(g, z)
+            return z + self.Pi @ self.mgh(self.Pi.T @ g, self.m_h, self.q)
         u = np.zeros_like(g) if u0 is None else u0.copy()
         for _ in range(self.m_p):
             self.gs.forward(g, u)
@@ -320,17 +371,21 @@ def _bary_point(X: np.ndarray, x: np.ndarray) -> np.ndarray:
 def build_hpmg(topos: List[Topology], parents: List[np.ndarray], k: int, nu: float, beta: float,
                gamma: float, m_p: int = 1, m_h: int = 1, q: int = 1, growth: int = 2,
                hdg_k: Optional[HDG] = None, conv: Optional[np.ndarray] = None,
-               conv_transpose: bool = False) -> MGhp:
+               conv_transpose: bool = False, smoother: str = "gs", damping: float = 0.5,
+               additive: bool = False) -> MGhp:
     """hp-multigrid on the hierarchy topos[0] (coarsest) .. topos[-1] (finest).
 
     conv: lattice values (n_cells_fine, n_lat(k+1), 2) of the convecting field
-    on the finest mesh (Oseen), or None (generalized Stokes).
+    on the finest mesh (Oseen), or None (generalized Stokes).  smoother: "gs" (block
+    Gauss–Seidel, Section 5) or "jacobi" (damped block Jacobi of eq. bjac with
+    ς = damping) on every level; additive: the additive form of Algorithm 2 (MGhp).
     """
     conv_l = [None] * len(topos) if conv is None else lowest_order_convection(topos, parents, conv)
-    levels = [Level(HDG(t, 0, nu=nu, beta=beta, gamma=gamma, conv=cl, conv_transpose=conv_transpose))
+    levels = [Level(HDG(t, 0, nu=nu, beta=beta, gamma=gamma, conv=cl, conv_transpose=conv_transpose),
+                    smoother, damping)
               for t, cl in zip(topos, conv_l)]
     mgh = MGh(levels, parents, growth=growth, symmetric=conv is None)
     if hdg_k is None:
         hdg_k = HDG(topos[-1], k, nu=nu, beta=beta, gamma=gamma, conv=conv,
                     conv_transpose=conv_transpose)
-    return MGhp(hdg_k, mgh, m_p=m_p, m_h=m_h, q=q)
+    return MGhp(hdg_k, mgh, m_p=m_p, m_h=m_h, q=q, smoother=smoother, damping=damping, additive=additive)

@@ -67,7 +67,8 @@ class _Params(ctypes.Structure):
                 ("gamma", ctypes.c_double), ("m_p", ctypes.c_int), ("m_h", ctypes.c_int),
                 ("cycle", ctypes.c_int), ("vcycle_growth", ctypes.c_int), ("precision", ctypes.c_int),
                 ("fused_coarse_cells", ctypes.c_int), ("nu_elem", ctypes.c_void_p), ("conv", ctypes.c_void_p),
-                ("newton_u", ctypes.c_void_p)]
+                ("newton_u", ctypes.c_void_p), ("smoother", ctypes.c_int), ("jacobi_damping", ctypes.c_double),
+                ("hp_additive", ctypes.c_int)]
 
 
 class HierarchyInfo(ctypes.Structure):
@@ -79,7 +80,7 @@ class HierarchyInfo(ctypes.Structure):
 class SolveOpts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", ctypes.c_double), ("floor_rel", ctypes.c_double),
                 ("uzawa_tol", ctypes.c_double), ("restart", ctypes.c_int), ("max_it", ctypes.c_int),
-                ("max_uzawa", ctypes.c_int)]
+                ("max_uzawa", ctypes.c_int), ("krylov", ctypes.c_int)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -117,13 +118,17 @@ class Params:
     nu_elem: object = None          # optional CUDA float64 tensor [n_cells] of per-cell viscosity
     conv: object = None             # optional CUDA float64 tensor [n_cells, n_lat, 2]: Oseen field w_h
     newton_u: object = None         # optional CUDA float64 tensor [n_dof]: previous iterate (Newton step)
+    smoother: int = 0               # 0 = block Gauss-Seidel, 1 = damped block Jacobi
+    jacobi_damping: float = 0.5
+    hp_additive: int = 0            # 1 = additive form of Algorithm 2
 
     def to_c(self) -> _Params:
         ne = None if self.nu_elem is None else _ptr(self.nu_elem)
         cv = None if self.conv is None else _ptr(self.conv)
         nw = None if self.newton_u is None else _ptr(self.newton_u)
         return _Params(self.k, self.nu, self.beta, self.gamma, self.m_p, self.m_h, self.cycle,
-                       self.vcycle_growth, self.precision, self.fused_coarse_cells, ne, cv, nw)
+                       self.vcycle_growth, self.precision, self.fused_coarse_cells, ne, cv, nw,
+                       self.smoother, self.jacobi_damping, self.hp_additive)
 
 
 _lib = None

@@ -85,7 +85,7 @@ void free_operator(DevOperator &op) {
 void free_level(DevLevel &L) {
     dfree(L.coords); dfree(L.cells); dfree(L.cell_int); dfree(L.facet_adj); dfree(L.cell_d); dfree(L.cell_nu);
     dfree(L.cell_area); dfree(L.conv_flux); dfree(L.conv_lat); dfree(L.patch_nf); dfree(L.patch_facets); dfree(L.patch_nc);
-    dfree(L.patch_cells); dfree(L.patch_slot_src); dfree(L.gs0_table);
+    dfree(L.patch_cells); dfree(L.patch_slot_src); dfree(L.gs0_table); dfree(L.facet_slot);
     free_operator(L.op0);
     dfree(L.tr_slots); dfree(L.tr_nbr); dfree(L.tr_children); dfree(L.tr_child_slot);
     dfree(L.tr_fineB); dfree(L.tr_fineB_src); dfree(L.tr_W); dfree(L.tr_H); dfree(L.tr_Wf);
@@ -184,10 +184,31 @@ struct Prec<float> {
     static const float *H(const DevLevel &L) { return L.tr_Hf.p; }
 };
 
+template <class T>
+void apply_op(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, const T *x, const T *g, T *y,
+              cudaStream_t s);
+
+// one step of the damped block Jacobi smoother (eq. bjac): r = g - A u in the residual work
+// vector of the level (the order-k one for the order-k operator), every patch's correction,
+// then u += damping x (the two corrections of each unknown); forward = backward
+template <class T>
+void jacobi_step(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, const T *g, T *u, cudaStream_t s) {
+    const bool dbl = std::is_same<T, double>::value;
+    T *r = &op == &ctx->opk ? (dbl ? (T *)ctx->kr.p : (T *)ctx->krf.p) : Prec<T>::r(const_cast<DevLevel &>(L));
+    T *D = dbl ? (T *)ctx->jD.p : (T *)ctx->jDf.p;
+    apply_op<T>(ctx, L, op, u, g, r, s);
+    const double damp = ctx->prm.jacobi_damping > 0 ? ctx->prm.jacobi_damping : 0.5;
+    CK(launch_jacobi_update<T>(L, op, Prec<T>::P(op), r, D, damp, u, s));
+}
+
 // one sweep of block GS; FP32 sweeps of an operator with 16-bit copies read those
 template <class T>
 void sweep(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, const T *g, T *u, bool reverse,
            cudaStream_t s) {
+    if (ctx->prm.smoother == 1) {
+        jacobi_step<T>(ctx, L, op, g, u, s);
+        return;
+    }
     for (int i = 0; i < L.n_colours; ++i) {
         int c = reverse ? L.n_colours - 1 - i : i;
         if constexpr (std::is_same<T, float>::value) {
@@ -349,6 +370,16 @@ void mg_hp_impl(hdg_ctx *ctx, const T *r, T *z, cudaStream_t s) {
     const DevOperator &op = ctx->opk;
     T *res = std::is_same<T, double>::value ? (T *)ctx->kr.p : (T *)ctx->krf.p;
     CK(launch_fill<T>(z, T(0), ctx->n_dof, s));
+    if (ctx->prm.hp_additive) {
+        // additive form (Remark 3.4): the symmetric relaxation of r plus the lowest-order
+        // correction of r itself
+        for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, false, s);
+        for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, true, s);
+        CK(launch_hp_restrict<T>(k, LJ.n_int, r, Prec<T>::g(LJ), s));
+        mg_h<T>(ctx, J, ctx->prm.m_h, true, s);
+        CK(launch_hp_prolong_add<T>(k, LJ.n_int, Prec<T>::u(LJ), z, s));
+        return;
+    }
     for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, false, s);
     apply_op<T>(ctx, LJ, op, z, r, res, s);
     CK(launch_hp_restrict<T>(k, LJ.n_int, res, Prec<T>::g(LJ), s));
@@ -523,6 +554,68 @@ FgmresOut fgmres(hdg_ctx *ctx, const double *b, double *x, double rtol, double a
     return {total, beta, stagnated};
 }
 
+// preconditioned conjugate gradients on A^eps x = b (Section 5, the paper's Krylov method for
+// the generalized Stokes problem; symmetric operator and preconditioner): stop when the
+// recursively updated residual has |r| <= max(rtol |r0|, atol).  Work vectors r, z, p, q
+// lie consecutively in pcg_buf, so one dot pass gives r.r and z.r together.
+FgmresOut pcg(hdg_ctx *ctx, const double *b, double *x, double rtol, double atol, int max_it, cudaStream_t s) {
+    const int64_t n = ctx->n_dof;
+    dalloc(ctx, ctx->pcg_buf, (size_t)4 * std::max<int64_t>(n, 1));
+    double *r = ctx->pcg_buf.p, *z = r + n, *p = z + n, *q = p + n;
+    SmallLayout Ly{ctx->restart_alloc};
+    double *pt = ctx->partials.p, *sc = ctx->small.p + Ly.h1();
+    auto dots2 = [&](const double *w, int nv, double *out) {   // out[j] = (r + j n) . w
+        CK(launch_dots(r, nv, n, w, n, pt, s));
+        CK(launch_reduce_partials(pt, nv, sc, 0, s));
+        CK(cudaMemcpyAsync(ctx->h_pinned, sc, nv * sizeof(double), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int j = 0; j < nv; ++j) out[j] = ctx->h_pinned[j];
+    };
+    apply_k(ctx, x, b, r, s);   // r = b - A x
+    double v[2];
+    dots2(r, 1, v);
+    double rn = std::sqrt(std::max(v[0], 0.0));
+    if (!std::isfinite(rn)) {
+        ctx->err = "non-finite residual";
+        throw Fail{HDG_ERR_NONFINITE};
+    }
+    const double tol = std::max(rtol * rn, atol);
+    if (rn <= tol) return {0, rn, false};
+    precond(ctx, r, z, s);
+    CK(cudaMemcpyAsync(p, z, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    dots2(z, 1, v);
+    double rz = v[0];
+    int its = 0;
+    while (its < max_it) {
+        apply_k(ctx, p, nullptr, q, s);
+        CK(launch_dots(p, 1, 0, q, n, pt, s));
+        CK(launch_reduce_partials(pt, 1, sc, 0, s));
+        const double pq = read_scalar(ctx, sc, s);
+        if (!(pq > 0) || !std::isfinite(pq)) {
+            ctx->err = "PCG: the operator or the preconditioner is not positive definite (p.Ap = " +
+                       std::to_string(pq) + ")";
+            throw Fail{HDG_ERR_BREAKDOWN};
+        }
+        const double alpha = rz / pq;
+        CK(launch_axpby(alpha, p, 1.0, x, n, s));
+        CK(launch_axpby(-alpha, q, 1.0, r, n, s));
+        ++its;
+        dots2(r, 1, v);
+        rn = std::sqrt(std::max(v[0], 0.0));
+        if (!std::isfinite(rn)) {
+            ctx->err = "non-finite residual";
+            throw Fail{HDG_ERR_NONFINITE};
+        }
+        if (rn <= tol) break;
+        precond(ctx, r, z, s);
+        dots2(r, 2, v);   // v[1] = z . r
+        const double beta = v[1] / rz;
+        rz = v[1];
+        CK(launch_axpby(1.0, z, beta, p, n, s));
+    }
+    return {its, rn, false};
+}
+
 const double *cell_nu_of(hdg_ctx *ctx, int l) {
     return ctx->prm.nu_elem ? ctx->L[l].cell_nu.p : nullptr;
 }
@@ -566,8 +659,16 @@ hdg_status uzawa_solve(hdg_ctx *ctx, const double *F, double *u, double *p, cons
     if (opts_in) o = *opts_in;
     REQUIRE(o.restart >= 1 && o.restart <= 32, "restart out of range 1..32");
     REQUIRE(o.max_uzawa >= 1 && o.max_uzawa <= 64, "max_uzawa out of range 1..64");
+    if (o.krylov != 0) {
+        ctx->err = "batched solves run flexible GMRES only (krylov = 0)";
+        throw Fail{HDG_ERR_UNSUPPORTED};
+    }
     REQUIRE(o.max_it >= 1 && o.rtol >= 0 && o.atol >= 0 && o.floor_rel >= 0 && o.uzawa_tol >= 0,
             "bad tolerances");
+    REQUIRE(o.krylov == 0 || o.krylov == 1, "krylov must be 0 (FGMRES) or 1 (PCG)");
+    REQUIRE(o.krylov == 0 || (!ctx->has_conv && (ctx->prm.precision == HDG_FP64 ||
+                                                 ctx->prm.precision == HDG_MIXED_FP32)),
+            "PCG needs a symmetric operator and preconditioner: no convection, FP64 or FP32 preconditioner");
     ensure_krylov(ctx, o.restart);
     const int J = ctx->n_levels - 1;
     DevLevel &LJ = ctx->L[J];
@@ -583,7 +684,8 @@ hdg_status uzawa_solve(hdg_ctx *ctx, const double *F, double *u, double *p, cons
     bool done = false;
     for (int it = 0; it < o.max_uzawa; ++it) {
         CK(launch_uzawa_rhs(LJ, k, F, p, g, s));
-        FgmresOut fo = fgmres(ctx, g, u, o.rtol, floor_abs, o.restart, o.max_it, s);
+        FgmresOut fo = o.krylov == 1 ? pcg(ctx, g, u, o.rtol, floor_abs, o.max_it, s)
+                                     : fgmres(ctx, g, u, o.rtol, floor_abs, o.restart, o.max_it, s);
         loc.krylov_its[it] = fo.its;
         loc.krylov_its_total += fo.its;
         loc.uzawa_its = it + 1;
@@ -741,9 +843,18 @@ bool ensure_tuned(hdg_ctx *ctx, int R, cudaStream_t s) {
     return true;
 }
 
+// the batched forms run Algorithm 2 with block GS only
+void require_multi_variant(hdg_ctx *ctx) {
+    if (ctx->prm.smoother != 0 || ctx->prm.hp_additive) {
+        ctx->err = "batched (_multi) calls support the block GS smoother and Algorithm 2 only";
+        throw Fail{HDG_ERR_UNSUPPORTED};
+    }
+}
+
 template <class T>
 void sweep_m(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, int R, const T *g, T *u, bool reverse,
              cudaStream_t s) {
+    require_multi_variant(ctx);
     int rb = 0, nt = 0;
     if (&op == &ctx->opk) tile_of<T>(ctx, R, rb, nt);
     bool tc = false;
@@ -840,6 +951,7 @@ void precond_m_direct(hdg_ctx *ctx, const double *r, double *z, int R, cudaStrea
 
 // z = MG_hp(r) for R columns through a CUDA graph captured once per (precision, R)
 void precond_m(hdg_ctx *ctx, const double *r, double *z, int R, cudaStream_t s) {
+    require_multi_variant(ctx);
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(s, &cs));
     ensure_multi_work(ctx, R);
@@ -1106,6 +1218,7 @@ void hdg_default_solve_opts(hdg_solve_opts *o) {
     o->rtol = 1e-8;
     o->atol = 1e-10;
     o->floor_rel = 1e-10;
+    o->krylov = 0;
     o->uzawa_tol = 1e-8;
     o->restart = 30;
     o->max_it = 1000;
@@ -1225,6 +1338,17 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
             upload(ctx, L.patch_nc, H.patch_nc);
             upload(ctx, L.patch_cells, H.patch_cells);
             upload(ctx, L.patch_slot_src, H.patch_slot_src);
+            {
+                // the two vertex-patch slots of every interior facet (block Jacobi gather)
+                std::vector<int32_t> fs(2 * H.n_int, -1);
+                for (int p = 0; p < H.n_patches; ++p)
+                    for (int js = 0; js < H.patch_nf[p]; ++js) {
+                        const int F = H.patch_facets[(size_t)p * H.pf_max + js];
+                        const int q = fs[2 * F] < 0 ? 0 : 1;
+                        fs[2 * F + q] = p * H.pf_max + js;
+                    }
+                upload(ctx, L.facet_slot, fs);
+            }
             if (H.nc <= GS0_TABLE_MAX_CELLS && 2 * H.pf_max <= 16) {
                 // lowest-order gather table: each lane of the sweep reads its row's whole
                 // gather pattern at once instead of chasing patch -> cell -> facet indices
@@ -1445,7 +1569,13 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
     ctx->n0 = 2 * ctx->L[0].n_int;
     dalloc(ctx, ctx->coarse_inv, std::max<int64_t>(ctx->n0 * ctx->n0, 1));
     CK(launch_coarse_inverse(ctx->L[0], ctx->coarse_inv.p, ctx->n0, ctx->status_flag.p, s));
-    ctx->small_Ls = small_levels(ctx);
+    ctx->small_Ls = prm->smoother == 1 ? -1 : small_levels(ctx);   // the fused kernel sweeps by GS
+    if (prm->smoother == 1) {
+        size_t nd = (size_t)LJ.n_patches * op.np_max;
+        for (int l = 0; l < nl; ++l) nd = std::max(nd, (size_t)ctx->L[l].n_patches * ctx->L[l].op0.np_max);
+        dalloc(ctx, ctx->jD, std::max<size_t>(nd, 1));
+        dalloc(ctx, ctx->jDf, std::max<size_t>(nd, 1));
+    }
     if (ctx->small_Ls >= 1) {
         const size_t cb_d = fill_small<double>(ctx, ctx->small_Ls);
         const size_t cb_f = fill_small<float>(ctx, ctx->small_Ls);
@@ -1483,6 +1613,9 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
         REQUIRE(prm->precision == HDG_FP64 || prm->precision == HDG_MIXED_FP32 ||
                     prm->precision == HDG_MIXED_BF16 || prm->precision == HDG_MIXED_FP16, "unknown precision");
         REQUIRE(prm->fused_coarse_cells >= 0, "fused_coarse_cells must be >= 0");
+        REQUIRE(prm->smoother == 0 || prm->smoother == 1, "smoother must be 0 (block GS) or 1 (block Jacobi)");
+        REQUIRE(std::isfinite(prm->jacobi_damping) && prm->jacobi_damping < 2, "jacobi_damping out of range");
+        REQUIRE(prm->hp_additive == 0 || prm->hp_additive == 1, "hp_additive must be 0 or 1");
         REQUIRE(2 * ctx->L[0].n_int <= MAX_COARSE_DOFS,
                 "coarsest level has " + std::to_string(2 * ctx->L[0].n_int) +
                 " unknowns; the dense coarse solve allows at most " + std::to_string(MAX_COARSE_DOFS) +

@@ -175,6 +175,7 @@ struct DevLevel {
     int n_patches = 0, n_colours = 0, pf_max = 0, pc_max = 0;
     std::vector<int32_t> colour_ptr;
     DBuf<int32_t> patch_nf, patch_facets, patch_nc, patch_cells, patch_slot_src;
+    DBuf<int32_t> facet_slot;  // n_int*2: the two patch slots (p pf_max + position) holding each facet
     // lowest-order sweep gather table (levels with at most GS0_TABLE_MAX_CELLS cells): per
     // patch row t < np_max, GS0_TABLE_INTS ints {row 2F+d, element-row offsets of the two
     // cells c*36 + lf*12 + d, their interior facets (3 each, -1 on the boundary)}; rows
@@ -228,6 +229,9 @@ struct hdg_ctx {
     int restart_alloc = 0;
     hdg::DBuf<double> V, Z, w, partials, small;   // small: Hessenberg, rotations, g, y
     hdg::DBuf<double> uz_partials;
+    hdg::DBuf<double> jD;                    // damped block Jacobi: patch corrections (FP64 sweeps)
+    hdg::DBuf<float> jDf;                    // the same for FP32 sweeps
+    hdg::DBuf<double> pcg_buf;               // PCG vectors r, z, p, q (4 n_dof)
     double *h_pinned = nullptr;              // host pinned scalars
     double *h_multi = nullptr;               // host pinned per-column scalars (multi-RHS)
     // CUDA graph of one preconditioner application (fixed staging buffers)
@@ -317,6 +321,12 @@ cudaError_t launch_apply(const DevLevel &L, const DevOperator &op, const T *A, c
 template <class T>
 cudaError_t launch_gs_colour(const DevLevel &L, const DevOperator &op, const T *A, const T *Pinv,
                              int colour, const T *g, T *u, cudaStream_t s);
+// damped block Jacobi update (eq. bjac) from the residual r = g - A u: every patch's
+// correction into D [n_patches][np_max], then u += damping (sum of each unknown's two
+// patch corrections); needs L.facet_slot
+template <class T>
+cudaError_t launch_jacobi_update(const DevLevel &L, const DevOperator &op, const T *Pinv, const T *r, T *D,
+                                 double damping, T *u, cudaStream_t s);
 // the order-k apply and sweep phase on the 16-bit copies (op.h_fmt), FP32 vectors
 cudaError_t launch_apply_h(const DevLevel &L, const DevOperator &op, const float *x, const float *g, float *y,
                            cudaStream_t s);

@@ -1258,7 +1258,83 @@ cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, doubl
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- damped block Jacobi (eq. bjac)
+// Step one: every patch solves against the same residual r = g - A u (one block per patch,
+// patch row t on thread t): D[p np_max + t] = sum_j (A_P^-1)_tj r_{P,j}.
+template <class T, int DPF>
+__global__ void jacobi_patch_kernel(int n_patches, int pf_max, int np_max, const int *__restrict__ patch_nf,
+                                    const int *__restrict__ patch_facets, const T *__restrict__ Pinv,
+                                    const T *__restrict__ r, T *__restrict__ D) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *rs = reinterpret_cast<T *>(smraw);   // np_max
+    const int p = blockIdx.x;
+    if (p >= n_patches) return;
+    const int np = patch_nf[p] * DPF;
+    for (int t = threadIdx.x; t < np; t += blockDim.x)
+        rs[t] = r[(size_t)patch_facets[(size_t)p * pf_max + t / DPF] * DPF + t % DPF];
+    __syncthreads();
+    const T *Pi = Pinv + (size_t)p * np_max * np_max;
+    for (int t = threadIdx.x; t < np; t += blockDim.x) {
+        T acc = 0;
+        for (int j = 0; j < np; ++j) acc += Pi[(size_t)j * np_max + t] * rs[j];
+        D[(size_t)p * np_max + t] = acc;
+    }
+}
+
+// Step two: each interior facet lies in the patches of its two vertices; its unknowns add
+// the two corrections in a fixed order, scaled by the damping s:
+// u_F += s (D[slot_a] + D[slot_b]), slot = patch p x pf_max + position of F in the patch
+template <class T, int DPF>
+__global__ void jacobi_gather_kernel(int64_t n_int, const int *__restrict__ facet_slot, T s,
+                                     const T *__restrict__ D, T *__restrict__ u) {
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n_int * DPF) return;
+    const int64_t F = idx / DPF;
+    const int d = (int)(idx - F * DPF);
+    const int a = facet_slot[2 * F], b = facet_slot[2 * F + 1];
+    T acc = 0;
+    if (a >= 0) acc += D[(size_t)a * DPF + d];
+    if (b >= 0) acc += D[(size_t)b * DPF + d];
+    u[idx] += s * acc;
+}
+
+template <class T, int DPF>
+cudaError_t jacobi_launch(const DevLevel &L, const DevOperator &op, const T *Pinv, const T *r, T *D, T damping,
+                          T *u, cudaStream_t s) {
+    if (L.n_patches > 0) {
+        int nt = ((op.np_max + 31) / 32) * 32;
+        nt = nt > 256 ? 256 : nt;
+        note_launches(1);
+        jacobi_patch_kernel<T, DPF><<<L.n_patches, nt, sizeof(T) * op.np_max, s>>>(
+            L.n_patches, L.pf_max, op.np_max, L.patch_nf.p, L.patch_facets.p, Pinv, r, D);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const int64_t n = L.n_int * DPF;
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    jacobi_gather_kernel<T, DPF><<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, L.facet_slot.p, damping, D, u);
+    return cudaGetLastError();
+}
+
+template <class T>
+cudaError_t launch_jacobi_update(const DevLevel &L, const DevOperator &op, const T *Pinv, const T *r, T *D,
+                                 double damping, T *u, cudaStream_t s) {
+    switch (op.dpf) {
+    case 2: return jacobi_launch<T, 2>(L, op, Pinv, r, D, (T)damping, u, s);
+    case 4: return jacobi_launch<T, 4>(L, op, Pinv, r, D, (T)damping, u, s);
+    case 6: return jacobi_launch<T, 6>(L, op, Pinv, r, D, (T)damping, u, s);
+    case 8: return jacobi_launch<T, 8>(L, op, Pinv, r, D, (T)damping, u, s);
+    case 10: return jacobi_launch<T, 10>(L, op, Pinv, r, D, (T)damping, u, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 // explicit instantiations
+template cudaError_t launch_jacobi_update<double>(const DevLevel &, const DevOperator &, const double *,
+                                                  const double *, double *, double, double *, cudaStream_t);
+template cudaError_t launch_jacobi_update<float>(const DevLevel &, const DevOperator &, const float *,
+                                                 const float *, float *, double, float *, cudaStream_t);
 template cudaError_t launch_apply<double>(const DevLevel &, const DevOperator &, const double *,
                                           const double *, const double *, double *, cudaStream_t);
 template cudaError_t launch_apply<float>(const DevLevel &, const DevOperator &, const float *, const float *,
