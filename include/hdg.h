@@ -153,6 +153,22 @@ typedef struct {
                              /* form (Remark 3.4): z = R_sym r + Pi_0^k MG_h(Pi_k^0 */
                              /* r), R_sym = m_p forward then m_p backward sweeps    */
                              /* from zero; single-load calls only                   */
+    const double *dirichlet; /* inhomogeneous Dirichlet data (Section 3.1 with      */
+                             /* u = g on the boundary, e.g. a driven lid): device   */
+                             /* [n_boundary_facets][dpf], for every boundary facet  */
+                             /* of the finest level in hdg_boundary_facets order,   */
+                             /* the skeleton values of g in the unknowns' layout:   */
+                             /* normal moments int_F (g.n_F) l_m, then tangential   */
+                             /* coefficients int_F (g.t_F) l_m.  Copied by          */
+                             /* hdg_condense.  The loads of hdg_condense / hdg_load */
+                             /* then carry -A_IB g, the pressure update of hdg_solve */
+                             /* the data's boundary fluxes (which must sum to zero),*/
+                             /* and hdg_recover / hdg_postprocess use g on the      */
+                             /* boundary.  Preconditioners act on homogeneous       */
+                             /* corrections and are unchanged.  NULL = homogeneous. */
+                             /* hdg_solve only: batched solves, hdg_picard,         */
+                             /* hdg_newton and hdg_adjoint return                   */
+                             /* HDG_ERR_UNSUPPORTED with data set.                  */
 } hdg_params;
 
 typedef struct {
@@ -198,6 +214,7 @@ typedef struct {
     int64_t n_dof_level[16];    /* lowest-order unknowns per level (2 per facet)    */
     int n_colours_level[16];    /* vertex colours per level                         */
     int n_lat;                  /* forcing lattice points per cell                  */
+    int64_t n_boundary_facets;  /* finest level; the order of hdg_boundary_facets   */
 } hdg_sizes;
 
 /* Fill the defaults of Section 5: rtol 1e-8, atol 1e-10, floor_rel 1e-10,
@@ -283,6 +300,17 @@ hdg_status hdg_solve(hdg_ctx *ctx, const double *F, double *u, double *p,
  *            determine u_h exactly (RT_k is contained in [P^{k+1}]^2). */
 hdg_status hdg_recover(hdg_ctx *ctx, const double *u, const double *forcing, double *L_out,
                        double *ulat_out, hdg_stream_t stream);
+
+/* Local post-processing of eq. stPost (Section 5.1): per cell, u* in
+ * [P^{k+1}(K)]^2 with (grad u*, grad v)_K = (-nu^{-1} L_h, grad v)_K for all v
+ * in P^{k+1}(K) and (u*, 1)_K = (u_h, 1)_K (the equation read with L = -nu grad u,
+ * so that grad u* approximates grad u; u* converges at order k+2 for k >= 1).
+ * L_h and u_h are recovered from the skeleton solution u (device [n_dof]) and
+ * the forcing (device lattice layout, or NULL for zero forcing) as in
+ * hdg_recover.  ustar_out: device [n_cells][n_lat][2], the values of u* at the
+ * degree-(k+1) lattice of each cell (the forcing layout; they determine u*). */
+hdg_status hdg_postprocess(hdg_ctx *ctx, const double *u, const double *forcing, double *ustar_out,
+                           hdg_stream_t stream);
 
 /* Adjoint gradients of J = 1/2 ||u_h - u_target||^2_{L2(Omega)} with respect
  * to the forcing lattice values and the per-cell viscosity (Section 3.2 scheme,
@@ -392,6 +420,11 @@ hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forc
 hdg_status hdg_newton(hdg_ctx *ctx, const hdg_params *params, const double *forcing, double tol, int max_steps,
                       double *u, double *p, const hdg_solve_opts *opts, int *steps_out, double *dist_out,
                       hdg_stream_t stream);
+
+/* The finest level's boundary facets in facet order (lexicographic in the
+ * sorted global vertex pair), the order of hdg_params.dirichlet: pairs (host,
+ * [n_boundary_facets][2]) receives each facet's sorted global vertex ids. */
+hdg_status hdg_boundary_facets(const hdg_ctx *ctx, int32_t *pairs);
 
 /* Sizes after hdg_setup_mesh_hierarchy (k-dependent fields after hdg_condense). */
 hdg_status hdg_get_sizes(const hdg_ctx *ctx, hdg_sizes *out);

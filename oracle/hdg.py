@@ -262,7 +262,11 @@ class HDG:
     def __init__(self, topo: Topology, k: int, nu: float = 1.0, beta: float = 0.0,
                  gamma: float = 0.0, nu_elem: Optional[np.ndarray] = None,
                  cache: bool = True, conv: Optional[np.ndarray] = None,
-                 conv_transpose: bool = False, newton_uhat: Optional[np.ndarray] = None):
+                 conv_transpose: bool = False, newton_uhat: Optional[np.ndarray] = None,
+                 dirichlet: Optional[np.ndarray] = None):
+        """dirichlet: the skeleton values of inhomogeneous Dirichlet data, (n_boundary_facets,
+        2(k+1)) in facet order (boundary facets only), the unknowns' layout (normal moments,
+        then tangential coefficients); None = homogeneous data."""
         self.topo, self.k = topo, k
         self.dpf = 2 * (k + 1)
         self.ng = 3 * self.dpf
@@ -303,6 +307,22 @@ class HDG:
                 i = topo.interior_index[topo.cell_facets[c, f]]
                 if i >= 0:
                     self.l2g[c, f * self.dpf:(f + 1) * self.dpf] = i * self.dpf + np.arange(self.dpf)
+        # boundary data: local unknowns of boundary facets -> entries of the data vector
+        bnd_facets = np.flatnonzero(topo.interior_index < 0)
+        self.n_boundary = len(bnd_facets)
+        self.xD = None
+        self.b2g = -np.ones((nc, self.ng), dtype=np.int64)
+        if dirichlet is not None:
+            data = np.asarray(dirichlet, dtype=float)
+            assert data.shape == (self.n_boundary, self.dpf), "dirichlet: (n_boundary_facets, dpf)"
+            self.xD = data.reshape(-1)
+            bidx = -np.ones(len(topo.interior_index), dtype=np.int64)
+            bidx[bnd_facets] = np.arange(self.n_boundary)
+            for c in range(nc):
+                for f in range(3):
+                    b = bidx[topo.cell_facets[c, f]]
+                    if b >= 0:
+                        self.b2g[c, f * self.dpf:(f + 1) * self.dpf] = b * self.dpf + np.arange(self.dpf)
 
     # ------------------------------------------------------------ element data
     def element_matrix(self, c: int, with_al: bool = True) -> np.ndarray:
@@ -343,18 +363,37 @@ class HDG:
         return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                              shape=(self.topo.n_cells, self.n_dof))
 
+    def local_dirichlet(self, c: int) -> np.ndarray:
+        """Cell c's local unknowns carrying Dirichlet data (zero on interior facets)."""
+        out = np.zeros(self.ng)
+        if self.xD is not None:
+            b = self.b2g[c]
+            out[b >= 0] = self.xD[b[b >= 0]]
+        return out
+
     def load(self, fvals: np.ndarray) -> np.ndarray:
-        """Condensed load F (n_dof,) from lattice forcing (n_cells, n_lat, 2)."""
+        """Condensed load F (n_dof,) from lattice forcing (n_cells, n_lat, 2), minus the
+        coupling of the interior unknowns to the Dirichlet data through A^ε."""
         F = np.zeros(self.n_dof)
         for c in range(self.topo.n_cells):
             idx = self.l2g[c]
             m = idx >= 0
-            F[idx[m]] += self.element_load(c, fvals[c])[m]
+            Fc = self.element_load(c, fvals[c])
+            if self.xD is not None:
+                Fc = Fc - self.element_matrix(c) @ self.local_dirichlet(c)
+            F[idx[m]] += Fc[m]
         return F
+
+    def boundary_flux(self) -> np.ndarray:
+        """Per cell, the flux of the Dirichlet data through its boundary facets (the part of
+        |K| div u_h that the interior unknowns do not carry)."""
+        if self.xD is None:
+            return np.zeros(self.topo.n_cells)
+        return np.array([self.cells[c].d @ self.local_dirichlet(c) for c in range(self.topo.n_cells)])
 
     def gather(self, x: np.ndarray, c: int) -> np.ndarray:
         idx = self.l2g[c]
-        out = np.zeros(self.ng)
+        out = self.local_dirichlet(c)
         out[idx >= 0] = x[idx[idx >= 0]]
         return out
 
@@ -369,7 +408,8 @@ class HDG:
 
     # ------------------------------------------------------------ exact solve
     def solve_direct(self, F: np.ndarray):
-        """Exact discrete solution of A u − Dᵀp = F, D u = 0, Σ|K|p_K = 0.
+        """Exact discrete solution of A u − Dᵀp = F, D u + b = 0, Σ|K|p_K = 0 (b: the
+        cells' boundary fluxes of the Dirichlet data, zero for homogeneous data).
 
         The condensed saddle point of eq. stOptForm (the B-rows are the cell
         fluxes; the mean-zero pressure is imposed by one Lagrange multiplier).
@@ -380,7 +420,10 @@ class HDG:
         nc = self.topo.n_cells
         w = sp.csr_matrix(self.area[:, None])
         K = sp.bmat([[A, -D.T, None], [D, None, w], [None, w.T, None]], format="csc")
-        rhs = np.concatenate([F, np.zeros(nc + 1)])
+        bf = self.boundary_flux()
+        # F carries -A^ε_IB u_D; without the AL term the load is F + eps^-1 d_I (d_B u_D) / |K|
+        Fn = F + D.T @ (self.eps_inv * bf / self.area)
+        rhs = np.concatenate([Fn, -bf, [0.0]])
         sol = spla.splu(K).solve(rhs)
         return sol[:self.n_dof], sol[self.n_dof:self.n_dof + nc]
 
@@ -422,6 +465,36 @@ class HDG:
         p = pv @ pc
         return L, u, divu, p
 
+    def ustar_cell(self, c: int, coeffs, nq: Optional[int] = None) -> np.ndarray:
+        """Post-processed u* ∈ [P^{k+1}]² on cell c (eq. stPost, read with L = −ν∇u):
+        (∇u*, ∇v)_K = (−ν⁻¹L_h, ∇v)_K for v ∈ P^{k+1} except the constant, whose
+        equation is replaced by (u*, 1)_K = (u_h, 1)_K.  Returns the coefficients over
+        the cell's monomials of degree <= k+1, shape (n_mono, 2)."""
+        k = self.k
+        el = self.cells[c].el
+        xq, wq = triangle_points(el.X, nq or (k + 5))
+        L, uh, _, _ = self.fields_at(c, coeffs, xq)
+        Gm = el.mono_grad(xq, k + 1)
+        Mo = el.mono(xq, k + 1)
+        S = np.einsum("q,qid,qjd->ij", wq, Gm, Gm)
+        S[0, :] = wq @ Mo
+        us = np.zeros((Mo.shape[1], 2))
+        for a in range(2):
+            r = np.einsum("q,qid,qd->i", wq, Gm, -L[:, a, :] / self.nu_elem[c])
+            r[0] = wq @ uh[:, a]
+            us[:, a] = np.linalg.solve(S, r)
+        return us
+
+    def postprocess(self, u, p, fvals) -> np.ndarray:
+        """u* at every cell's degree-(k+1) lattice (the forcing layout): (n_cells, n_lat, 2)."""
+        lam = lattice_barycentric_2d(self.k + 1)
+        out = np.zeros((self.topo.n_cells, lam.shape[0], 2))
+        for c in range(self.topo.n_cells):
+            coeffs = self.recover_cell(c, u, p[c], fvals[c])
+            el = self.cells[c].el
+            out[c] = el.mono(lam @ el.X, self.k + 1) @ self.ustar_cell(c, coeffs)
+        return out
+
     def errors(self, u, p, fvals, sol, nq: Optional[int] = None):
         """L2 errors of u_h, L_h (L = −ν∇u), p_h (both mean-free), ‖div u_h‖, and u*.
 
@@ -450,16 +523,7 @@ class HDG:
             pe_vals.append(sol.p(xa))
             wts.append(wq)
             # post-processing u* in [P^{k+1}]^2
-            Gm = el.mono_grad(xq, k + 1)
-            Mo = el.mono(xq, k + 1)
-            S = np.einsum("q,qid,qjd->ij", wq, Gm, Gm)
-            S[0, :] = wq @ Mo
-            us = np.zeros((Mo.shape[1], 2))
-            for a in range(2):
-                r = np.einsum("q,qid,qd->i", wq, Gm, -L[:, a, :] / self.nu_elem[c])
-                r[0] = wq @ uh[:, a]
-                us[:, a] = np.linalg.solve(S, r)
-            ustar = Mo @ us
+            ustar = el.mono(xq, k + 1) @ self.ustar_cell(c, coeffs, nq)
             eus += wq @ np.sum((ue - ustar) ** 2, axis=1)
         ph = np.concatenate(ph_vals)
         pe = np.concatenate(pe_vals)

@@ -170,9 +170,10 @@ class UzawaResult:
 def uzawa(Aeps, D, area, eps_inv, F, M: Callable, rtol: float = 1e-8, atol: float = 1e-10,
           restart: int = 30, max_it: int = 1000, max_uzawa: int = 200,
           uzawa_tol: float = 1e-8, floor_rel: float = 1e-10, u0=None,
-          krylov: str = "fgmres") -> UzawaResult:
+          krylov: str = "fgmres", bflux=None) -> UzawaResult:
     """Augmented-Lagrangian Uzawa with FGMRES (or, krylov="pcg", PCG) inner solves
-    (eq. stOpEq-ALU)."""
+    (eq. stOpEq-ALU).  bflux: per-cell fluxes of inhomogeneous Dirichlet data, added to
+    D u in the pressure update (None = homogeneous data)."""
     normF = float(np.linalg.norm(F))
     u = np.zeros_like(F) if u0 is None else np.array(u0, copy=True)
     p = np.zeros(D.shape[0])
@@ -191,7 +192,7 @@ def uzawa(Aeps, D, area, eps_inv, F, M: Callable, rtol: float = 1e-8, atol: floa
         if fi["stagnated"]:
             floor = max(floor, 2.0 * rn)
         res.res_floor = floor
-        du = D @ u
+        du = D @ u if bflux is None else D @ u + bflux
         res.div_l2 = float(np.sqrt(np.sum(du ** 2 / area)))
         dp = eps_inv * du / area
         p = p - dp

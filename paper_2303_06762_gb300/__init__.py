@@ -40,7 +40,7 @@ EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_check_hier
            "hdg_apply", "hdg_precond_apply", "hdg_solve", "hdg_recover", "hdg_adjoint", "hdg_get_sizes",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
-           "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_set_wait_limit", "hdg_fp64_fma_probe", "hdg_apply_multi",
+           "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_set_wait_limit", "hdg_fp64_fma_probe", "hdg_postprocess", "hdg_boundary_facets", "hdg_apply_multi",
            "hdg_precond_apply_multi", "hdg_smooth_multi", "hdg_set_batched_tile", "hdg_tune_batched", "hdg_solve_multi", "hdg_solve_batched", "hdg_picard", "hdg_newton",
            "hdg_destroy",
            "hdg_status_string", "hdg_last_error")
@@ -68,7 +68,7 @@ class _Params(ctypes.Structure):
                 ("cycle", ctypes.c_int), ("vcycle_growth", ctypes.c_int), ("precision", ctypes.c_int),
                 ("fused_coarse_cells", ctypes.c_int), ("nu_elem", ctypes.c_void_p), ("conv", ctypes.c_void_p),
                 ("newton_u", ctypes.c_void_p), ("smoother", ctypes.c_int), ("jacobi_damping", ctypes.c_double),
-                ("hp_additive", ctypes.c_int)]
+                ("hp_additive", ctypes.c_int), ("dirichlet", ctypes.c_void_p)]
 
 
 class HierarchyInfo(ctypes.Structure):
@@ -99,7 +99,7 @@ class Sizes(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("n_levels", ctypes.c_int), ("n_cells", ctypes.c_int64),
                 ("n_interior_facets", ctypes.c_int64), ("n_dof", ctypes.c_int64),
                 ("n_dof_level", ctypes.c_int64 * 16), ("n_colours_level", ctypes.c_int * 16),
-                ("n_lat", ctypes.c_int)]
+                ("n_lat", ctypes.c_int), ("n_boundary_facets", ctypes.c_int64)]
 
 
 @dataclass
@@ -121,6 +121,7 @@ class Params:
     smoother: int = 0               # 0 = block Gauss-Seidel, 1 = damped block Jacobi
     jacobi_damping: float = 0.5
     hp_additive: int = 0            # 1 = additive form of Algorithm 2
+    dirichlet: object = None        # optional CUDA float64 tensor [n_boundary_facets, dpf]: boundary data
 
     def to_c(self) -> _Params:
         ne = None if self.nu_elem is None else _ptr(self.nu_elem)
@@ -128,7 +129,8 @@ class Params:
         nw = None if self.newton_u is None else _ptr(self.newton_u)
         return _Params(self.k, self.nu, self.beta, self.gamma, self.m_p, self.m_h, self.cycle,
                        self.vcycle_growth, self.precision, self.fused_coarse_cells, ne, cv, nw,
-                       self.smoother, self.jacobi_damping, self.hp_additive)
+                       self.smoother, self.jacobi_damping, self.hp_additive,
+                       None if self.dirichlet is None else _ptr(self.dirichlet))
 
 
 _lib = None
@@ -178,6 +180,8 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "hdg_restrict": (I, [P, I, P, P, P]),
         "hdg_restrict_noalloc": (I, [P, I, P, P, P]),
         "hdg_set_wait_limit": (I, [P, ctypes.c_int64]),
+        "hdg_postprocess": (I, [P, P, P, P, P]),
+        "hdg_boundary_facets": (I, [P, P]),
         "hdg_fp64_fma_probe": (ctypes.c_int64, [I, ctypes.c_int64, P, P]),
         "hdg_coarse_solve": (I, [P, P, P, P]),
         "hdg_mg_h": (I, [P, P, P, P]),
@@ -489,6 +493,25 @@ def hdg_recover(ctx: Context, u, forcing=None, stream=None):
     ctx.check(load_library().hdg_recover(ctx.handle, _ptr(u), _ptr(forcing), _ptr(L), _ptr(ul),
                                          _stream(stream)))
     return L, ul
+
+
+def hdg_boundary_facets(ctx: Context) -> np.ndarray:
+    """Sorted global vertex pairs of the finest level's boundary facets, the order of the
+    Dirichlet data, shape [n_boundary_facets, 2] (int32)."""
+    n = ctx.sizes().n_boundary_facets
+    out = np.zeros((n, 2), dtype=np.int32)
+    ctx.check(load_library().hdg_boundary_facets(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def hdg_postprocess(ctx: Context, u, forcing=None, stream=None):
+    """u* of eq. stPost at each cell's degree-(k+1) lattice, shape [n_cells, n_lat, 2]."""
+    import torch
+    s = ctx.sizes()
+    k = s.k
+    out = torch.empty((s.n_cells, (k + 2) * (k + 3) // 2, 2), dtype=torch.float64, device=u.device)
+    ctx.check(load_library().hdg_postprocess(ctx.handle, _ptr(u), _ptr(forcing), _ptr(out), _stream(stream)))
+    return out
 
 
 def hdg_adjoint(ctx: Context, forcing, u, u_target, opts: Optional[SolveOpts] = None, stream=None):

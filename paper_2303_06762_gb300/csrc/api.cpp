@@ -85,7 +85,7 @@ void free_operator(DevOperator &op) {
 void free_level(DevLevel &L) {
     dfree(L.coords); dfree(L.cells); dfree(L.cell_int); dfree(L.facet_adj); dfree(L.cell_d); dfree(L.cell_nu);
     dfree(L.cell_area); dfree(L.conv_flux); dfree(L.conv_lat); dfree(L.patch_nf); dfree(L.patch_facets); dfree(L.patch_nc);
-    dfree(L.patch_cells); dfree(L.patch_slot_src); dfree(L.gs0_table); dfree(L.facet_slot);
+    dfree(L.patch_cells); dfree(L.patch_slot_src); dfree(L.gs0_table); dfree(L.facet_slot); dfree(L.cell_bnd);
     free_operator(L.op0);
     dfree(L.tr_slots); dfree(L.tr_nbr); dfree(L.tr_children); dfree(L.tr_child_slot);
     dfree(L.tr_fineB); dfree(L.tr_fineB_src); dfree(L.tr_W); dfree(L.tr_H); dfree(L.tr_Wf);
@@ -633,6 +633,7 @@ void load_impl(hdg_ctx *ctx, const double *forcing, double *rhs_out, cudaStream_
                        ctx->prm.beta, ctx->prm.gamma, forcing, conv_of(ctx), ctx->conv_t, newton_of(ctx), nullptr,
                        nullptr, ctx->opk.Fel.p, ctx->status_flag.p, RecoverArgs(), s));
     CK(launch_assemble_load(LJ, ctx->opk, rhs_out, s));
+    if (ctx->has_dir) CK(launch_dirichlet_load(LJ, ctx->opk, ctx->dir_x.p, rhs_out, s));
 }
 
 void recover_impl(hdg_ctx *ctx, const double *u, const double *forcing, double *L, double *rt, double *ulat,
@@ -641,6 +642,8 @@ void recover_impl(hdg_ctx *ctx, const double *u, const double *forcing, double *
     RecoverArgs rec;
     rec.x = u;
     rec.cell_int = LJ.cell_int.p;
+    rec.cell_bnd = LJ.cell_bnd.p;
+    rec.xD = ctx->has_dir ? ctx->dir_x.p : nullptr;
     rec.L = L;
     rec.rt = rt;
     rec.ulat = ulat;
@@ -661,6 +664,10 @@ hdg_status uzawa_solve(hdg_ctx *ctx, const double *F, double *u, double *p, cons
     REQUIRE(o.max_uzawa >= 1 && o.max_uzawa <= 64, "max_uzawa out of range 1..64");
     if (o.krylov != 0) {
         ctx->err = "batched solves run flexible GMRES only (krylov = 0)";
+        throw Fail{HDG_ERR_UNSUPPORTED};
+    }
+    if (ctx->has_dir) {
+        ctx->err = "batched solves take homogeneous Dirichlet data only";
         throw Fail{HDG_ERR_UNSUPPORTED};
     }
     REQUIRE(o.max_it >= 1 && o.rtol >= 0 && o.atol >= 0 && o.floor_rel >= 0 && o.uzawa_tol >= 0,
@@ -693,7 +700,8 @@ hdg_status uzawa_solve(hdg_ctx *ctx, const double *F, double *u, double *p, cons
         if (fo.its >= o.max_it) conv = HDG_ERR_NOT_CONVERGED;
         if (fo.stagnated) floor_abs = std::max(floor_abs, 2.0 * fo.res);
         loc.res_floor = floor_abs;
-        CK(launch_uzawa_update(LJ, k, u, p, ctx->prm.gamma, ctx->prm.nu, cell_nu_of(ctx, J), ctx->partials.p, s));
+        CK(launch_uzawa_update(LJ, k, u, p, ctx->prm.gamma, ctx->prm.nu, cell_nu_of(ctx, J),
+                               ctx->has_dir ? ctx->dir_flux.p : nullptr, ctx->partials.p, s));
         SmallLayout Ly{o.restart};
         CK(launch_reduce_partials(ctx->partials.p, 4, ctx->small.p + Ly.h1(), 0, s));
         CK(cudaMemcpyAsync(ctx->h_pinned, ctx->small.p + Ly.h1(), 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1324,6 +1332,17 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
                 for (int q = 0; q < 2; ++q) fa[2 * i + q] = (H.facet_cells[2 * F + q] << 2) | H.facet_lf[2 * F + q];
             }
             upload(ctx, L.cell_int, ci);
+            if (l == nl - 1) {
+                // boundary facets in facet order (inhomogeneous Dirichlet data of the finest level)
+                std::vector<int32_t> bidx(H.nf, -1), cb(3 * H.nc, -1);
+                int64_t nb = 0;
+                for (int64_t F = 0; F < H.nf; ++F)
+                    if (H.interior_index[F] < 0) bidx[F] = (int32_t)nb++;
+                for (int64_t c = 0; c < H.nc; ++c)
+                    for (int f = 0; f < 3; ++f) cb[3 * c + f] = bidx[H.cell_facet[3 * c + f]];
+                L.n_bnd = nb;
+                upload(ctx, L.cell_bnd, cb);
+            }
             upload(ctx, L.facet_adj, fa);
             dalloc(ctx, L.cell_d, 3 * H.nc);
             dalloc(ctx, L.cell_area, H.nc);
@@ -1441,6 +1460,8 @@ void hdg_destroy(hdg_ctx *ctx) {
     free_operator(ctx->opk);
     dfree(ctx->refk_dev); dfree(ctx->ref0_dev);
     dfree(ctx->kr); dfree(ctx->ku); dfree(ctx->kt); dfree(ctx->krf); dfree(ctx->kuf); dfree(ctx->kgf);
+    dfree(ctx->post_tabs); dfree(ctx->pcg_buf); dfree(ctx->jD); dfree(ctx->jDf); dfree(ctx->dir_x);
+    dfree(ctx->dir_flux);
     dfree(ctx->coarse_inv); dfree(ctx->status_flag); dfree(ctx->wait_flag); dfree(ctx->conv_k); dfree(ctx->newton_x);
     dfree(ctx->V); dfree(ctx->Z); dfree(ctx->w); dfree(ctx->partials); dfree(ctx->small);
     dfree(ctx->uz_partials);
@@ -1477,6 +1498,21 @@ hdg_status hdg_get_sizes(const hdg_ctx *cctx, hdg_sizes *out) {
         out->n_colours_level[l] = ctx->H[l].n_colours;
     }
     out->n_lat = ctx->condensed ? (ctx->prm.k + 2) * (ctx->prm.k + 3) / 2 : 0;
+    out->n_boundary_facets = H.nf - H.n_int;
+    return HDG_OK;
+}
+
+hdg_status hdg_boundary_facets(const hdg_ctx *ctx, int32_t *pairs) {
+    if (!ctx || !pairs) return HDG_ERR_INVALID_ARG;
+    if (ctx->n_levels < 1) return HDG_ERR_STATE;
+    const HostLevel &H = ctx->H[ctx->n_levels - 1];
+    int64_t b = 0;
+    for (int64_t F = 0; F < H.nf; ++F)
+        if (H.interior_index[F] < 0) {
+            pairs[2 * b] = H.facet_v[2 * F];
+            pairs[2 * b + 1] = H.facet_v[2 * F + 1];
+            ++b;
+        }
     return HDG_OK;
 }
 
@@ -1651,9 +1687,20 @@ hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forci
             CK(cudaMemcpyAsync(ctx->newton_x.p, prm->newton_u, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
         }
         condense_all(ctx, forcing, s);
+        // inhomogeneous Dirichlet data: a copy, the cells' boundary fluxes and the load coupling
+        ctx->has_dir = prm->dirichlet != nullptr;
+        if (ctx->has_dir) {
+            DevLevel &F = ctx->L[nl - 1];
+            const size_t nb = (size_t)F.n_bnd * 2 * (prm->k + 1);
+            dalloc(ctx, ctx->dir_x, std::max<size_t>(nb, 1));
+            CK(cudaMemcpyAsync(ctx->dir_x.p, prm->dirichlet, sizeof(double) * nb, cudaMemcpyDeviceToDevice, s));
+            dalloc(ctx, ctx->dir_flux, std::max<int64_t>(F.nc, 1));
+            CK(launch_boundary_flux(F, 2 * (prm->k + 1), ctx->dir_x.p, ctx->dir_flux.p, s));
+        }
         if (rhs_out) {
             if (forcing) CK(launch_assemble_load(ctx->L[nl - 1], ctx->opk, rhs_out, s));
             else CK(cudaMemsetAsync(rhs_out, 0, sizeof(double) * ctx->n_dof, s));
+            if (ctx->has_dir) CK(launch_dirichlet_load(ctx->L[nl - 1], ctx->opk, ctx->dir_x.p, rhs_out, s));
         }
     });
 }
@@ -1842,6 +1889,36 @@ hdg_status hdg_recover(hdg_ctx *ctx, const double *u, const double *forcing, dou
     });
 }
 
+hdg_status hdg_postprocess(hdg_ctx *ctx, const double *u, const double *forcing, double *ustar_out,
+                           hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(u && ustar_out, "null skeleton vector or output");
+        cudaStream_t s = (cudaStream_t)stream;
+        const int k = ctx->prm.k;
+        DevLevel &LJ = ctx->L[ctx->n_levels - 1];
+        const int64_t nlat = (k + 2) * (k + 3) / 2, npk = (k + 1) * (k + 2) / 2;
+        if (ctx->post_k != k || !ctx->post_tabs.p) {
+            std::vector<double> t(ctx->refk.P1);
+            t.insert(t.end(), ctx->refk.P2.begin(), ctx->refk.P2.end());
+            t.insert(t.end(), ctx->refk.P3.begin(), ctx->refk.P3.end());
+            upload(ctx, ctx->post_tabs, t);
+            ctx->post_k = k;
+        }
+        if (!forcing) {
+            dalloc(ctx, ctx->rec_e, (size_t)LJ.nc * 2 * nlat);
+            CK(cudaMemsetAsync(ctx->rec_e.p, 0, sizeof(double) * ctx->rec_e.n, s));
+            forcing = ctx->rec_e.p;
+        }
+        dalloc(ctx, ctx->rec_L, (size_t)LJ.nc * 4 * npk);
+        dalloc(ctx, ctx->rec_ulat, (size_t)LJ.nc * 2 * nlat);
+        recover_impl(ctx, u, forcing, ctx->rec_L.p, nullptr, ctx->rec_ulat.p, s);
+        CK(launch_poststar(k, LJ, ctx->prm.nu, cell_nu_of(ctx, ctx->n_levels - 1), ctx->post_tabs.p, (int)nlat,
+                           (int)npk, ctx->rec_L.p, ctx->rec_ulat.p, ustar_out, s));
+    });
+}
+
 hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, const double *u_target,
                        double *grad_forcing, double *grad_nu, double *J, const hdg_solve_opts *opts,
                        hdg_solve_info *info, hdg_stream_t stream) {
@@ -1851,6 +1928,10 @@ hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, con
     hdg_status st = guard(ctx, [&] {
         NEED_CONDENSED();
         REQUIRE(forcing && u && u_target, "null input");
+        if (ctx->has_dir) {
+            ctx->err = "hdg_adjoint takes homogeneous Dirichlet data only";
+            throw Fail{HDG_ERR_UNSUPPORTED};
+        }
         if (ctx->has_newton) {
             ctx->err = "hdg_adjoint of a Newton-step operator is not implemented";
             throw Fail{HDG_ERR_UNSUPPORTED};
@@ -2125,6 +2206,10 @@ hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forc
     double dist = 0.0;
     hdg_status st = guard(ctx, [&] {
         REQUIRE(params && forcing && u && p, "null argument");
+        if (params->dirichlet) {
+            ctx->err = "hdg_picard takes homogeneous Dirichlet data only";
+            throw Fail{HDG_ERR_UNSUPPORTED};
+        }
         REQUIRE(max_steps >= 1 && tol >= 0 && std::isfinite(tol), "bad tol or max_steps");
         REQUIRE(params->k >= 0 && params->k <= MAX_K, "k out of range 0..4");
         cudaStream_t s = (cudaStream_t)stream;
@@ -2188,6 +2273,10 @@ hdg_status hdg_newton(hdg_ctx *ctx, const hdg_params *params, const double *forc
     hdg_status st = guard(ctx, [&] {
         NEED_CONDENSED();
         REQUIRE(params && forcing && u && p, "null argument");
+        if (params->dirichlet || ctx->has_dir) {
+            ctx->err = "hdg_newton takes homogeneous Dirichlet data only";
+            throw Fail{HDG_ERR_UNSUPPORTED};
+        }
         REQUIRE(max_steps >= 1 && tol >= 0 && std::isfinite(tol), "bad tol or max_steps");
         REQUIRE(params->k == ctx->prm.k, "params->k differs from the condensed operator's k");
         cudaStream_t s = (cudaStream_t)stream;

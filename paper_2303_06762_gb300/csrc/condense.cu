@@ -625,7 +625,11 @@ condense_kernel(int64_t nc, const double *__restrict__ coords, const int *__rest
             for (int p = tid; p < D::NG; p += nt) {
                 int f = p / (2 * D::NF);
                 int j = rec.cell_int[3 * c + f];
-                xg[p] = j >= 0 ? rec.x[(size_t)j * 2 * D::NF + p % (2 * D::NF)] : 0.0;
+                double v = 0.0;
+                if (j >= 0) v = rec.x[(size_t)j * 2 * D::NF + p % (2 * D::NF)];
+                else if (rec.xD && rec.cell_bnd[3 * c + f] >= 0)
+                    v = rec.xD[(size_t)rec.cell_bnd[3 * c + f] * 2 * D::NF + p % (2 * D::NF)];
+                xg[p] = v;
             }
             __syncthreads();
             for (int j = tid; j < D::NPO; j += nt) {

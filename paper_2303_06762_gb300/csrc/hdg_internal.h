@@ -66,6 +66,9 @@ struct RefTables {
     std::vector<double> R1, R2, R3, R4, R5, R6, R7, R8;
     // point values for the upwind convection (reference.cpp)
     std::vector<double> R9, R10, R11, R12, R13, R14, R15, R16;
+    // post-processing of eq. stPost (u* in [P^{k+1}]^2, Lagrange basis lam_n of the lattice):
+    // P1[(a*2+b)][n][n'] = ∫ d_a lam_n d_b lam_n', P2[j][n][b] = ∫ g_j d_b lam_n, P3[n] = ∫ lam_n
+    std::vector<double> P1, P2, P3;
 };
 constexpr int N_REF_TABLES = 16;
 
@@ -128,6 +131,8 @@ struct RecoverArgs {
     double *rt = nullptr;           // [nc][nrt] RT coefficients in the reference dual basis
     double *po = nullptr;           // [nc][npk-1] mean-free pressure coefficients
     double *ulat = nullptr;         // [nc][nlat][2] velocity at the degree-(k+1) lattice
+    const int *cell_bnd = nullptr;  // with xD: boundary facet of each local facet or -1
+    const double *xD = nullptr;     // inhomogeneous Dirichlet data [n_boundary][dpf], or null
 };
 
 // ---------------------------------------------------------------- device data
@@ -176,6 +181,8 @@ struct DevLevel {
     std::vector<int32_t> colour_ptr;
     DBuf<int32_t> patch_nf, patch_facets, patch_nc, patch_cells, patch_slot_src;
     DBuf<int32_t> facet_slot;  // n_int*2: the two patch slots (p pf_max + position) holding each facet
+    DBuf<int32_t> cell_bnd;    // nc*3: boundary facet number of each local facet or -1 (finest level)
+    int64_t n_bnd = 0;         // boundary facets (finest level)
     // lowest-order sweep gather table (levels with at most GS0_TABLE_MAX_CELLS cells): per
     // patch row t < np_max, GS0_TABLE_INTS ints {row 2F+d, element-row offsets of the two
     // cells c*36 + lf*12 + d, their interior facets (3 each, -1 on the boundary)}; rows
@@ -211,6 +218,9 @@ struct hdg_ctx {
     bool has_conv = false;                   // Oseen: convecting field given
     int conv_t = 0;                          // operators built from the transposed convection
     hdg::DBuf<double> conv_k;                // finest convecting field, lattice layout (copy)
+    bool has_dir = false;                    // inhomogeneous Dirichlet data given (finest level)
+    hdg::DBuf<double> dir_x;                 // its skeleton values [n_boundary][dpf] (copy)
+    hdg::DBuf<double> dir_flux;              // per-cell boundary fluxes of the data
     bool has_newton = false;                 // Newton step: previous skeleton iterate below
     hdg::DBuf<double> newton_x;
     hdg::RefTables refk, ref0;
@@ -232,6 +242,8 @@ struct hdg_ctx {
     hdg::DBuf<double> jD;                    // damped block Jacobi: patch corrections (FP64 sweeps)
     hdg::DBuf<float> jDf;                    // the same for FP32 sweeps
     hdg::DBuf<double> pcg_buf;               // PCG vectors r, z, p, q (4 n_dof)
+    hdg::DBuf<double> post_tabs;             // P1, P2, P3 of the order-k tables (post-processing)
+    int post_k = -1;
     double *h_pinned = nullptr;              // host pinned scalars
     double *h_multi = nullptr;               // host pinned per-column scalars (multi-RHS)
     // CUDA graph of one preconditioner application (fixed staging buffers)
@@ -313,6 +325,10 @@ cudaError_t launch_adjoint_gradient(int k, const DevLevel &L, const double *ref,
 cudaError_t launch_objective(int k, const DevLevel &L, const double *ref, const RefTables &rt, const double *ulat,
                              const double *utgt, double *e_out, double *jcell, cudaStream_t s);
 cudaError_t launch_cell_geometry(DevLevel &L, cudaStream_t s);
+// post.cu: u* of eq. stPost at the degree-(k+1) lattice from the recovered L_h coefficients and
+// u_h lattice values; tabs = P1, P2, P3 packed
+cudaError_t launch_poststar(int k, const DevLevel &L, double nu, const double *nu_cell, const double *tabs,
+                            int nlat, int npk, const double *Lcoef, const double *ulat, double *out, cudaStream_t s);
 
 // kernels: hot path (ops.cu)
 template <class T>
@@ -381,7 +397,13 @@ cudaError_t launch_solve_update(double *small, int m, int restart, const double 
 cudaError_t launch_uzawa_rhs(const DevLevel &L, int k, const double *F, const double *p, double *g,
                              cudaStream_t s);
 cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p, double gamma,
-                                double nu, const double *nu_cell, double *partials, cudaStream_t s);
+                                double nu, const double *nu_cell, const double *bflux, double *partials,
+                                cudaStream_t s);
+// inhomogeneous Dirichlet data xD [n_boundary][dpf] (finest level, L.cell_bnd): F -= A_IB xD, and
+// the per-cell boundary fluxes of the data
+cudaError_t launch_dirichlet_load(const DevLevel &L, const DevOperator &op, const double *xD, double *F,
+                                  cudaStream_t s);
+cudaError_t launch_boundary_flux(const DevLevel &L, int dpf, const double *xD, double *bflux, cudaStream_t s);
 cudaError_t launch_sum(const double *x, int64_t n, double *partials, cudaStream_t s);
 
 // multi-right-hand-side kernels (multi.cu): multi-vectors [rows][R], R a power of two <= 64

@@ -830,7 +830,8 @@ __global__ void __launch_bounds__(KRYLOV_THREADS)
 uzawa_update_kernel(int64_t nc, int dpf, const int *__restrict__ cell_int,
                     const double *__restrict__ cell_d, const double *__restrict__ area,
                     const double *__restrict__ u, double *__restrict__ p, double gamma, double nu,
-                    const double *__restrict__ nu_cell, double *__restrict__ partials) {
+                    const double *__restrict__ nu_cell, const double *__restrict__ bflux,
+                    double *__restrict__ partials) {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
          c += (int64_t)gridDim.x * blockDim.x) {
@@ -839,6 +840,7 @@ uzawa_update_kernel(int64_t nc, int dpf, const int *__restrict__ cell_int,
             int j = cell_int[3 * c + f];
             if (j >= 0) du += cell_d[3 * c + f] * u[(size_t)j * dpf];
         }
+        if (bflux) du += bflux[c];   // flux of inhomogeneous Dirichlet data
         double a = area[c];
         double dp = gamma * (nu_cell ? nu_cell[c] : nu) * du / a;
         double pn = p[c] - dp;
@@ -1251,10 +1253,74 @@ cudaError_t launch_sum(const double *x, int64_t n, double *partials, cudaStream_
 }
 
 cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p, double gamma, double nu,
-                                const double *nu_cell, double *partials, cudaStream_t s) {
+                                const double *nu_cell, const double *bflux, double *partials, cudaStream_t s) {
     note_launches(1);
     uzawa_update_kernel<<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(L.nc, 2 * (k + 1), L.cell_int.p, L.cell_d.p,
-                                                                 L.cell_area.p, u, p, gamma, nu, nu_cell, partials);
+                                                                 L.cell_area.p, u, p, gamma, nu, nu_cell, bflux,
+                                                                 partials);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- inhomogeneous Dirichlet data
+// F_i -= sum over the facet's cells of A_K[row i, boundary columns] u_D (pull style, like the
+// apply: each interior facet row reads its two cells' row blocks at the boundary facets' columns)
+template <int DPF>
+__global__ void dirichlet_load_kernel(int64_t n_int, const int *__restrict__ facet_adj,
+                                      const int *__restrict__ cell_bnd, const double *__restrict__ A,
+                                      const double *__restrict__ xD, double *__restrict__ F) {
+    constexpr int NLOC = 3 * DPF;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n_int * DPF) return;
+    const int64_t i = idx / DPF;
+    const int d = (int)(idx - i * DPF);
+    double acc = 0.0;
+    for (int q = 0; q < 2; ++q) {
+        const int adj = facet_adj[2 * i + q];
+        if (adj < 0) continue;
+        const int c = adj >> 2, lf = adj & 3;
+        const double *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d;
+        for (int f2 = 0; f2 < 3; ++f2) {
+            const int b = cell_bnd[3 * c + f2];
+            if (b < 0) continue;
+            for (int d2 = 0; d2 < DPF; ++d2) acc += Ac[(f2 * DPF + d2) * DPF] * xD[(size_t)b * DPF + d2];
+        }
+    }
+    F[idx] -= acc;
+}
+
+// per cell, the flux of the Dirichlet data through its boundary facets: sum of d_f (normal moment 0)
+__global__ void boundary_flux_kernel(int64_t nc, int dpf, const int *__restrict__ cell_bnd,
+                                     const double *__restrict__ cell_d, const double *__restrict__ xD,
+                                     double *__restrict__ bflux) {
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    double s = 0.0;
+    for (int f = 0; f < 3; ++f) {
+        const int b = cell_bnd[3 * c + f];
+        if (b >= 0) s += cell_d[3 * c + f] * xD[(size_t)b * dpf];
+    }
+    bflux[c] = s;
+}
+
+cudaError_t launch_dirichlet_load(const DevLevel &L, const DevOperator &op, const double *xD, double *F,
+                                  cudaStream_t s) {
+    const int64_t n = L.n_int * op.dpf;
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    switch (op.dpf) {
+#define HDG_DIR(D) \
+    case D: dirichlet_load_kernel<D><<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_bnd.p, op.A.p, xD, F); break;
+    HDG_DIR(2) HDG_DIR(4) HDG_DIR(6) HDG_DIR(8) HDG_DIR(10)
+#undef HDG_DIR
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_boundary_flux(const DevLevel &L, int dpf, const double *xD, double *bflux, cudaStream_t s) {
+    if (L.nc == 0) return cudaSuccess;
+    note_launches(1);
+    boundary_flux_kernel<<<blocks_for(L.nc, 256), 256, 0, s>>>(L.nc, dpf, L.cell_bnd.p, L.cell_d.p, xD, bflux);
     return cudaGetLastError();
 }
 

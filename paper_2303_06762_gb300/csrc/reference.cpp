@@ -406,6 +406,9 @@ void build_reference_tables(int k, RefTables &t) {
     t.R14.assign((size_t)3 * nfq * nlat, 0.0);
     t.R15.assign((size_t)nfq * nf, 0.0);
     t.R16.assign((size_t)nfq, 0.0);
+    t.P1.assign((size_t)4 * nlat * nlat, 0.0);
+    t.P2.assign((size_t)npk * nlat * 2, 0.0);
+    t.P3.assign((size_t)nlat, 0.0);
     {
         int pidx = 0;
         for (int a2 = 0; a2 <= q; ++a2)
@@ -449,6 +452,22 @@ void build_reference_tables(int k, RefTables &t) {
         }
         for (int n1 = 0; n1 < nlat; ++n1)
             for (int n2 = 0; n2 < nlat; ++n2) t.R8[n1 * nlat + n2] += wq * lv[n1] * lv[n2];
+        // gradients of the lattice Lagrange basis for the post-processing tables
+        std::vector<double> ld(nlat * 2, 0.0);
+        for (int nn = 0; nn < nlat; ++nn)
+            for (int c = 0; c < nlat; ++c) {
+                ld[nn * 2 + 0] += Li[c * nlat + nn] * dxp[c];
+                ld[nn * 2 + 1] += Li[c * nlat + nn] * dyp[c];
+            }
+        for (int a = 0; a < 2; ++a)
+            for (int b = 0; b < 2; ++b)
+                for (int n1 = 0; n1 < nlat; ++n1)
+                    for (int n2 = 0; n2 < nlat; ++n2)
+                        t.P1[((size_t)(a * 2 + b) * nlat + n1) * nlat + n2] += wq * ld[n1 * 2 + a] * ld[n2 * 2 + b];
+        for (int j = 0; j < npk; ++j)
+            for (int nn = 0; nn < nlat; ++nn)
+                for (int b = 0; b < 2; ++b) t.P2[((size_t)j * nlat + nn) * 2 + b] += wq * gv[j] * ld[nn * 2 + b];
+        for (int nn = 0; nn < nlat; ++nn) t.P3[nn] += wq * lv[nn];
     }
     for (int f = 0; f < 3; ++f)
         for (int p = 0; p < n; ++p) {

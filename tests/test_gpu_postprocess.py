@@ -1,0 +1,81 @@
+"""GPU post-processing u* (eq. stPost) and convergence orders at scale.
+
+Parity: hdg_postprocess against the oracle's u* (the same skeleton solution fed to both)
+on jittered meshes with per-cell viscosity.  Orders: the library's solution and u* on
+N = 16 .. 128 for the manufactured curl solution; the L2 errors of u_h (from hdg_recover)
+and u* are integrated on the host from the lattice values and must decay at the rates of
+Section 5.1 (k+1 and k+2).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from workloads import curl_bubble_2d, unit_square_hierarchy, forcing_at_lattice
+from workloads.manufactured import lattice_barycentric_2d
+from oracle.hdg import HDG
+from oracle.quadrature import triangle_rule
+from _util import hierarchy, forcing, rel, parity_opts
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_postprocess_matches_oracle(k):
+    import paper_2303_06762_gb300 as hdg
+    ms, ts, ps = hierarchy(2, 3, jitter=0.2, seed=9, shuffle_seed=4)
+    rng = np.random.default_rng(2)
+    nu_e = 0.5 * (1 + 0.2 * rng.uniform(-1, 1, ms[-1].n_cells))
+    fv = forcing(ms[-1], k, curl_bubble_2d(), 0.5, 1.0)
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    F = hdg.hdg_condense(ctx, hdg.Params(k=k, nu=0.5, beta=1.0, gamma=100.0,
+                                         nu_elem=torch.tensor(nu_e, device=DEV)), torch.tensor(fv, device=DEV))
+    oh = HDG(ts[-1], k, nu=0.5, beta=1.0, gamma=100.0, nu_elem=nu_e)
+    ud, pd = oh.solve_direct(oh.load(fv))
+    us = hdg.hdg_postprocess(ctx, torch.tensor(ud, device=DEV), torch.tensor(fv, device=DEV))
+    torch.cuda.synchronize()
+    assert rel(us.cpu().numpy(), oh.postprocess(ud, pd, fv)) < 1e-10
+
+
+def _l2_error(coords, cells, vals, q, u_exact):
+    """|| u - v ||_L2 for v in [P^q]^2 given at every cell's degree-q lattice."""
+    lam = lattice_barycentric_2d(q)                       # (nlat, 3) barycentric
+    xi, w = triangle_rule(q + 4)                           # reference rule, sum w = 1/2
+    def mono(p):                                           # monomials of degree <= q at ref points
+        return np.stack([p[:, 0] ** (d - b) * p[:, 1] ** b for d in range(q + 1) for b in range(d + 1)], axis=1)
+    E = mono(xi) @ np.linalg.inv(mono(lam[:, 1:]))         # lattice values -> values at the rule's points
+    X = coords[cells]                                      # (nc, 3, 2)
+    J = np.stack([X[:, 1] - X[:, 0], X[:, 2] - X[:, 0]], axis=2)
+    det = np.abs(np.linalg.det(J))
+    xq = X[:, None, 0, :] + np.einsum("cij,qj->cqi", J, xi)
+    vq = np.einsum("qn,cna->cqa", E, vals)
+    ue = u_exact(xq.reshape(-1, 2)).reshape(vq.shape)
+    return float(np.sqrt(np.einsum("c,q,cqa->", det, w, (ue - vq) ** 2)))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_convergence_orders_at_scale(k):
+    import paper_2303_06762_gb300 as hdg
+    sol = curl_bubble_2d()
+    eu, es, Ns = [], [], (16, 32, 64, 128)
+    for N in Ns:
+        ms = unit_square_hierarchy(4, int(np.log2(N // 4)) + 1)
+        fine = ms[-1]
+        fv = torch.tensor(forcing_at_lattice(fine.coords, fine.cells, k, sol.forcing(1.0, 1.0)), device=DEV)
+        ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+        F = hdg.hdg_condense(ctx, hdg.Params(k=k, nu=1.0, beta=1.0, gamma=100.0, precision=1), fv)
+        u, p, info = hdg.hdg_solve(ctx, F, opts=parity_opts(hdg, 100.0))
+        assert info["div_l2"] < 1e-8
+        _, ul = hdg.hdg_recover(ctx, u, fv)
+        us = hdg.hdg_postprocess(ctx, u, fv)
+        torch.cuda.synchronize()
+        eu.append(_l2_error(fine.coords, fine.cells, ul.cpu().numpy(), k + 1, sol.u))
+        es.append(_l2_error(fine.coords, fine.cells, us.cpu().numpy(), k + 1, sol.u))
+        ctx.close()
+    ru = np.log2(np.array(eu[:-1]) / np.array(eu[1:]))
+    rs = np.log2(np.array(es[:-1]) / np.array(es[1:]))
+    print(f"k={k}: |u-u_h| {eu} rates {ru}; |u-u*| {es} rates {rs}")
+    assert abs(ru[-1] - (k + 1)) < 0.2
+    assert abs(rs[-1] - (k + 2)) < 0.25
+    assert es[-1] < eu[-1]

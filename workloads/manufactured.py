@@ -277,3 +277,48 @@ def fourier_forcing_2d(j: int, n_modes: int = 8, seed0: int = 20230312):
         return out
 
     return f
+
+
+def boundary_facets_2d(cells: np.ndarray) -> np.ndarray:
+    """(n_boundary, 2) sorted global vertex pairs of the boundary facets in facet order
+    (lexicographic in the sorted pair), the order of the Dirichlet data."""
+    e = np.concatenate([cells[:, [1, 2]], cells[:, [0, 2]], cells[:, [0, 1]]])
+    e.sort(axis=1)
+    uniq, cnt = np.unique(e, axis=0, return_counts=True)
+    return uniq[cnt == 1]
+
+
+def dirichlet_facet_data(coords: np.ndarray, cells: np.ndarray, k: int,
+                         g: Callable[[np.ndarray], np.ndarray], nq: Optional[int] = None) -> np.ndarray:
+    """Skeleton values (n_boundary, 2(k+1)) of boundary data g in the unknowns' layout: on a
+    facet F from its lower to its higher global vertex (unit tangent t, normal
+    n = (t_y, -t_x), parameter s from the lower vertex, l_m = sqrt(2m+1) P_m(2s-1)/sqrt|F|),
+    the normal moments int_F (g.n) l_m ds for m = 0..k, then the tangential coefficients
+    int_F (g.t) l_m ds, by Gauss-Legendre quadrature on each facet."""
+    pairs = boundary_facets_2d(cells)
+    nq = nq or (k + 6)
+    z, w = np.polynomial.legendre.leggauss(nq)
+    s, w = 0.5 * (z + 1), 0.5 * w
+    X0, X1 = coords[pairs[:, 0]], coords[pairs[:, 1]]
+    L = np.linalg.norm(X1 - X0, axis=1)
+    t = (X1 - X0) / L[:, None]
+    n = np.stack([t[:, 1], -t[:, 0]], axis=1)
+    pts = X0[:, None, :] + s[None, :, None] * (X1 - X0)[:, None, :]
+    gv = g(pts.reshape(-1, 2)).reshape(len(pairs), nq, 2)
+    gn = np.einsum("fqd,fd->fq", gv, n)
+    gt = np.einsum("fqd,fd->fq", gv, t)
+    leg = np.stack([np.sqrt(2 * m + 1) * np.polynomial.legendre.legval(2 * s - 1, [0] * m + [1])
+                    for m in range(k + 1)], axis=1)                       # (nq, k+1)
+    # int_F v l_m ds = |F| int_0^1 v(s) sqrt(2m+1) P_m(2s-1) ds / sqrt|F|
+    scale = np.sqrt(L)[:, None]
+    return np.concatenate([scale * (gn * w) @ leg, scale * (gt * w) @ leg], axis=1)
+
+
+def lid_velocity_2d(speed: float = 1.0) -> Callable[[np.ndarray], np.ndarray]:
+    """Driven-lid boundary data of the cavity problem (Section 5.2 workloads): tangential
+    velocity (speed, 0) on the top side y = 1, zero on the other sides."""
+    def g(x):
+        out = np.zeros_like(x)
+        out[np.isclose(x[:, 1], 1.0), 0] = speed
+        return out
+    return g
