@@ -274,6 +274,13 @@ hdg_status hdg_load(hdg_ctx *ctx, const double *forcing, double *rhs_out, hdg_st
  * must not overlap. */
 hdg_status hdg_apply(hdg_ctx *ctx, const double *x, double *y, hdg_stream_t stream);
 
+/* y = (A^eps)^T x on a level (level = -1: the order-k operator, >= 0: the
+ * lowest-order operator of that level): the transposed condensed operator,
+ * which differs from A^eps for the Oseen and Newton operators (the upwind
+ * convection is not symmetric) and equals it for the generalized Stokes
+ * problem.  x, y: device FP64 of the level's size, must not overlap. */
+hdg_status hdg_apply_transpose(hdg_ctx *ctx, int level, const double *x, double *y, hdg_stream_t stream);
+
 /* z = MG_hp(r, 0, m_p, m_h, q) of Algorithm 2 (Algorithm 1 inside), in the
  * precision chosen at hdg_condense.  r, z: device [n_dof] FP64, must not
  * overlap. */

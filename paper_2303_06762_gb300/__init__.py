@@ -40,7 +40,7 @@ EXPORTS = ("hdg_default_solve_opts", "hdg_setup_mesh_hierarchy", "hdg_check_hier
            "hdg_apply", "hdg_precond_apply", "hdg_solve", "hdg_recover", "hdg_adjoint", "hdg_get_sizes",
            "hdg_get_element_matrices", "hdg_level_apply", "hdg_smooth", "hdg_prolong_add",
            "hdg_restrict", "hdg_coarse_solve", "hdg_mg_h", "hdg_kernel_launches",
-           "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_set_wait_limit", "hdg_fp64_fma_probe", "hdg_postprocess", "hdg_boundary_facets", "hdg_apply_multi",
+           "hdg_reference_tables", "hdg_restrict_noalloc", "hdg_set_wait_limit", "hdg_fp64_fma_probe", "hdg_postprocess", "hdg_boundary_facets", "hdg_apply_transpose", "hdg_apply_multi",
            "hdg_precond_apply_multi", "hdg_smooth_multi", "hdg_set_batched_tile", "hdg_tune_batched", "hdg_solve_multi", "hdg_solve_batched", "hdg_picard", "hdg_newton",
            "hdg_destroy",
            "hdg_status_string", "hdg_last_error")
@@ -182,6 +182,7 @@ def load_library(path: Optional[str] = None) -> ctypes.CDLL:
         "hdg_set_wait_limit": (I, [P, ctypes.c_int64]),
         "hdg_postprocess": (I, [P, P, P, P, P]),
         "hdg_boundary_facets": (I, [P, P]),
+        "hdg_apply_transpose": (I, [P, I, P, P, P]),
         "hdg_fp64_fma_probe": (ctypes.c_int64, [I, ctypes.c_int64, P, P]),
         "hdg_coarse_solve": (I, [P, P, P, P]),
         "hdg_mg_h": (I, [P, P, P, P]),
@@ -332,6 +333,14 @@ def hdg_apply(ctx: Context, x, y=None, stream=None):
     import torch
     y = torch.empty_like(x) if y is None else y
     ctx.check(load_library().hdg_apply(ctx.handle, _ptr(x), _ptr(y), _stream(stream)))
+    return y
+
+
+def hdg_apply_transpose(ctx: Context, x, y=None, level: int = -1, stream=None):
+    """y = (A^eps)^T x on a level (-1: order k)."""
+    import torch
+    y = torch.empty_like(x) if y is None else y
+    ctx.check(load_library().hdg_apply_transpose(ctx.handle, level, _ptr(x), _ptr(y), _stream(stream)))
     return y
 
 

@@ -1732,6 +1732,17 @@ hdg_status hdg_apply(hdg_ctx *ctx, const double *x, double *y, hdg_stream_t stre
     });
 }
 
+hdg_status hdg_apply_transpose(hdg_ctx *ctx, int level, const double *x, double *y, hdg_stream_t stream) {
+    if (!ctx) return HDG_ERR_INVALID_ARG;
+    return guard(ctx, [&] {
+        NEED_CONDENSED();
+        REQUIRE(level >= -1 && level < ctx->n_levels, "level out of range");
+        REQUIRE(x && y && x != y, "x, y must be distinct non-null device pointers");
+        const DevLevel &L = ctx->L[level < 0 ? ctx->n_levels - 1 : level];
+        CK(launch_apply_t(L, level < 0 ? ctx->opk : L.op0, x, y, (cudaStream_t)stream));
+    });
+}
+
 hdg_status hdg_precond_apply(hdg_ctx *ctx, const double *r, double *z, hdg_stream_t stream) {
     if (!ctx) return HDG_ERR_INVALID_ARG;
     return guard(ctx, [&] {

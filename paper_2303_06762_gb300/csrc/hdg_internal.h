@@ -399,6 +399,8 @@ cudaError_t launch_uzawa_rhs(const DevLevel &L, int k, const double *F, const do
 cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p, double gamma,
                                 double nu, const double *nu_cell, const double *bflux, double *partials,
                                 cudaStream_t s);
+// y = A^T x on a level's FP64 element matrices (non-symmetric operators: Oseen, Newton)
+cudaError_t launch_apply_t(const DevLevel &L, const DevOperator &op, const double *x, double *y, cudaStream_t s);
 // inhomogeneous Dirichlet data xD [n_boundary][dpf] (finest level, L.cell_bnd): F -= A_IB xD, and
 // the per-cell boundary fluxes of the data
 cudaError_t launch_dirichlet_load(const DevLevel &L, const DevOperator &op, const double *xD, double *F,

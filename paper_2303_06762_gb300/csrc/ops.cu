@@ -1261,6 +1261,49 @@ cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, doubl
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- transposed apply
+// y = A^T x, pull style: the row of unknown (facet i, component d) in A^T is its column in the
+// element matrices of its two cells, A_K[(f2, d2), q] with q = lf dpf + d; with the row-block
+// layout that entry sits at (f2 n_loc + q) dpf + d2
+template <int DPF>
+__global__ void apply_t_kernel(int64_t n_int, const int *__restrict__ facet_adj, const int *__restrict__ cell_int,
+                               const double *__restrict__ A, const double *__restrict__ x, double *__restrict__ y) {
+    constexpr int NLOC = 3 * DPF;
+    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (idx >= n_int * DPF) return;
+    const int64_t i = idx / DPF;
+    const int d = (int)(idx - i * DPF);
+    double acc = 0.0;
+    for (int q2 = 0; q2 < 2; ++q2) {
+        const int adj = facet_adj[2 * i + q2];
+        if (adj < 0) continue;
+        const int c = adj >> 2, lf = adj & 3;
+        const int q = lf * DPF + d;
+        const double *Ac = A + (size_t)c * NLOC * NLOC;
+        for (int f2 = 0; f2 < 3; ++f2) {
+            const int j = cell_int[3 * c + f2];
+            if (j < 0) continue;
+            const double *Ar = Ac + ((size_t)f2 * NLOC + q) * DPF;
+            for (int d2 = 0; d2 < DPF; ++d2) acc += Ar[d2] * x[(size_t)j * DPF + d2];
+        }
+    }
+    y[idx] = acc;
+}
+
+cudaError_t launch_apply_t(const DevLevel &L, const DevOperator &op, const double *x, double *y, cudaStream_t s) {
+    const int64_t n = L.n_int * op.dpf;
+    if (n == 0) return cudaSuccess;
+    note_launches(1);
+    switch (op.dpf) {
+#define HDG_APT(D) \
+    case D: apply_t_kernel<D><<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_int.p, op.A.p, x, y); break;
+    HDG_APT(2) HDG_APT(4) HDG_APT(6) HDG_APT(8) HDG_APT(10)
+#undef HDG_APT
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- inhomogeneous Dirichlet data
 // F_i -= sum over the facet's cells of A_K[row i, boundary columns] u_D (pull style, like the
 // apply: each interior facet row reads its two cells' row blocks at the boundary facets' columns)

@@ -55,6 +55,25 @@ def oseen_case(N0, nl, k, Re=100.0, gamma=100.0, beta=0.0, precision=0, fused=0,
 MESHES = [dict(), dict(shuffle_seed=7), dict(jitter=0.25, seed=3, shuffle_seed=5)]
 
 
+@pytest.mark.parametrize("k", [1, 3])
+def test_transposed_apply(k):
+    """hdg_apply_transpose against the transposed oracle matrices, on the order-k level and
+    the lowest-order levels of the Oseen operator."""
+    hdg = _hdg()
+    ms, ts, ps, conv, fv, ctx, F, nu = oseen_case(2, 3, k, Re=50.0, **MESHES[2])
+    oh = HDG(ts[-1], k, nu=nu, gamma=100.0, conv=conv)
+    x = np.random.default_rng(k).standard_normal(oh.n_dof)
+    A = oh.matrix()
+    y = host(hdg.hdg_apply_transpose(ctx, dev(x)))
+    assert rel(y, A.T @ x) < 1e-13
+    assert rel(y, A @ x) > 1e-6            # the Oseen operator is not symmetric
+    cl = lowest_order_convection(ts, ps, conv)
+    for l in range(len(ts)):
+        o0 = HDG(ts[l], 0, nu=nu, gamma=100.0, conv=cl[l])
+        x0 = np.random.default_rng(l).standard_normal(o0.n_dof)
+        assert rel(host(hdg.hdg_apply_transpose(ctx, dev(x0), level=l)), o0.matrix().T @ x0) < 1e-13
+
+
 @pytest.mark.parametrize("k", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("mesh", [0, 2])
 def test_oseen_element_matrices_and_load(k, mesh):
