@@ -5,7 +5,8 @@ single-GPU size): unit square, 512x512 squares split into 524,288 triangles,
 H(div)-HDG order k = 3 (6,283,264 skeleton unknowns), nu = 1, beta = 1,
 gamma = 1e2 (eps^-1 = gamma nu), manufactured solution u = curl(sin^2(pi x)
 sin^2(pi y)), p = sin(2 pi x) cos(2 pi y); hp-multigrid with lowest-order
-(Crouzeix-Raviart) levels 8x8 ... 512x512 (7 levels), variable V-cycle
+(Crouzeix-Raviart) levels 32x32 ... 512x512 (5 levels; the 32x32 level solved exactly by one
+dense FP64 GEMV with its precomputed inverse), variable V-cycle
 (m_p = m_h = 1, doubling), FGMRES(30) inside the augmented-Lagrangian Uzawa
 loop, stopping rules of Section 5 (inner relative 1e-8 / absolute 1e-10).
 
@@ -48,7 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--N", type=int, default=512)
-    ap.add_argument("--N0", type=int, default=8)
+    ap.add_argument("--N0", type=int, default=32,
+                    help="coarsest CR level (exact dense FP64 solve); 32 keeps that solve one 290 MB GEMV")
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--gamma", type=float, default=1e2)
     ap.add_argument("--beta", type=float, default=1.0)
@@ -155,15 +157,16 @@ def ctx_mesh_fine(args):
     return _FINE["mesh"]
 
 
-def sweep_bytes(mesh, k, word, mat_word=None):
-    """Algorithmic bytes of one order-k block-GS sweep (all colours) on `mesh`.
+def sweep_bytes(mesh, k, word, mat_word=None, packed_inverse=False):
+    """Bytes one order-k block-GS sweep (all colours) on `mesh` moves as the kernel reads them.
 
     Per vertex patch with nf interior facets (np = nf dpf unknowns) and nc cells:
     residual rows read 2 cells x dpf rows x n_loc columns per facet, the gathered
-    cell unknowns nc x n_loc, the patch inverse np^2, the right-hand side np and
-    the update np (read + write).  Vectors take `word` bytes per value, matrix
-    entries `mat_word` (default `word`); 16-bit matrices add one 4-byte scale per
-    row read (2 x dpf per facet and np per patch inverse)."""
+    cell unknowns nc x n_loc, the patch inverse np^2 (np (np+1)/2 when it is stored
+    packed symmetric), the right-hand side np and the update np (read + write).
+    Vectors take `word` bytes per value, matrix entries `mat_word` (default `word`);
+    16-bit matrices add one 4-byte scale per row read (2 x dpf per facet and np per
+    patch inverse)."""
     import numpy as np
     dpf = 2 * (k + 1)
     nloc = 3 * dpf
@@ -178,7 +181,8 @@ def sweep_bytes(mesh, k, word, mat_word=None):
     m = nf > 0
     npp = nf[m] * dpf
     mw = word if mat_word is None else mat_word
-    mat = (nf[m] * 2 * dpf * nloc + npp * npp).sum() * mw
+    inv = npp * (npp + 1) // 2 if packed_inverse else npp * npp
+    mat = (nf[m] * 2 * dpf * nloc + inv).sum() * mw
     vec = (ncell[m] * nloc + 3 * npp).sum() * word
     scales = (nf[m] * 2 * dpf + npp).sum() * 4 if mw != word else 0
     return int(mat + vec + scales)
@@ -259,11 +263,11 @@ def cpu_baseline(args, seconds_budget=20.0):
     from oracle.hdg import HDG
     from oracle.mg import build_hpmg
     from oracle.krylov import uzawa
-    N = 32
+    N, N0 = 32, 8          # the sample keeps three lowest-order levels (8x8 .. 32x32)
     nl = 1
-    while args.N0 * 2 ** (nl - 1) < N:
+    while N0 * 2 ** (nl - 1) < N:
         nl += 1
-    ms = unit_square_hierarchy(min(args.N0, N), nl)
+    ms = unit_square_hierarchy(N0, nl)
     ts = [build_topology(m.coords, m.cells, m.vertex_colour) for m in ms]
     ps = [m.parent for m in ms]
     h = HDG(ts[-1], args.k, nu=args.nu, beta=args.beta, gamma=args.gamma)
@@ -315,11 +319,11 @@ def reference_arm(args):
     from oracle.hdg import HDG
     from oracle.mg import build_hpmg
     from oracle.krylov import uzawa
-    N = 32
+    N, N0 = 32, 8          # the sample keeps three lowest-order levels (8x8 .. 32x32)
     nl = 1
-    while args.N0 * 2 ** (nl - 1) < N:
+    while N0 * 2 ** (nl - 1) < N:
         nl += 1
-    ms = unit_square_hierarchy(min(args.N0, N), nl)
+    ms = unit_square_hierarchy(N0, nl)
     ts = [build_topology(m.coords, m.cells, m.vertex_colour) for m in ms]
     ps = [m.parent for m in ms]
     h = HDG(ts[-1], args.k, nu=args.nu, beta=args.beta, gamma=args.gamma)
@@ -342,7 +346,7 @@ def reference_arm(args):
         cores = os.cpu_count()
     val = h.n_dof * its / dt
     # the config of what this arm times: the 32x32 sample of the workload
-    sample_args = argparse.Namespace(**{**vars(args), "N": N, "N0": min(args.N0, N)})
+    sample_args = argparse.Namespace(**{**vars(args), "N": N, "N0": N0})
     cfg = config(sample_args, h.n_dof, nl)
     cfg["sample_of"] = f"{args.N}x{args.N} workload of the GPU arm ({full_skeleton_dofs(args.N, args.k)} skeleton DOFs)"
     sample = (f"{N}x{N} triangulation, {h.n_dof} skeleton DOFs, {nl} levels: a bounded CPU sample of the "
@@ -510,7 +514,7 @@ def batched_form(args, hdg, torch, dev, stream, world):
     one load solved alone by hdg_solve on the same operator."""
     from workloads import unit_square_hierarchy
     from workloads.manufactured import fourier_forcing_2d, lattice_points_2d
-    N, N0, k, nrhs = 256, 8, 3, 64
+    N, N0, k, nrhs = 256, 32, 3, 64
     nl = 1
     while N0 * 2 ** (nl - 1) < N:
         nl += 1
@@ -603,7 +607,7 @@ def coarsest_form(args, hdg, torch, dev, stream):
     trade colour-phase launches of the small levels for a larger dense FP64 coarse inverse."""
     from workloads import unit_square_hierarchy, curl_bubble_2d, forcing_at_lattice
     out = {}
-    for N0 in (4, 16, 32):
+    for N0 in (4, 8, 16, 32):
         if N0 == args.N0 or args.N % N0:
             continue
         nl = 1
@@ -789,14 +793,15 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
     # algorithmic bytes by the scope table's per-unit model (packed symmetric element matrices
     # and patch inverses read once per sweep), and by the kernel's own full-storage access count
     alg = survey_bytes(_FINE["meshes"], k, s_p=2 if half else 4)["A2_sweep"]
-    alg_kernel = sweep_bytes(ctx_mesh_fine(args), k, 4, 2 if half else 4)
+    alg_kernel = sweep_bytes(ctx_mesh_fine(args), k, 4, 2 if half else 4, packed_inverse=not half)
     achieved = alg / t_sweep / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     # DRAM bytes of one sweep from an ncu capture of the same kernel on the 128x128, k = 3 case
     # (TMA_SWEEP_TRAFFIC_128).  Traffic grows with the number of patches like the algorithmic
     # bytes, so the full-size figure is that ratio times the full-size algorithmic bytes
     # (k = 3 only; other k were not captured).
-    traffic = alg_kernel * (TMA_SWEEP_TRAFFIC_128 / 318199104) if k == 3 and not half and TMA_SWEEP_TRAFFIC_128 else None
+    traffic = alg_kernel * (TMA_SWEEP_TRAFFIC_128 / TMA_SWEEP_KERNEL_BYTES_128) \
+        if k == 3 and not half and TMA_SWEEP_TRAFFIC_128 else None
     kname = "gs_kernel<float, 8, __half> (order-k block GS sweep on binary16 copies" if half else \
         "gs_tma_kernel<8> (order-k block GS sweep, matrices staged by cp.async.bulk"
     rs = read_stream_gbs(torch, dev, stream)
@@ -815,10 +820,11 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the three colour launches of one
-# order-k sweep of gs_tma_kernel<8> from an ncu capture on the 128x128, k = 3 case, whose
-# algorithmic bytes are 318,199,104: 104,263,424 + 104,260,096 + 104,269,056 B read and
-# 2,776,576 + 100,352 + 85,760 B written (315,755,264 B, 0.992x).
-TMA_SWEEP_TRAFFIC_128 = 315755264
+# order-k sweep of gs_tma_kernel<8, 1> (packed symmetric patch inverses) from an ncu capture on the
+# 128x128, k = 3 case (profiles/ncu_gs_tma_packed_128_k3.md), and that sweep's bytes as the kernel
+# reads them (sweep_bytes with the packed inverse).  None until captured for the current kernel.
+TMA_SWEEP_TRAFFIC_128 = None
+TMA_SWEEP_KERNEL_BYTES_128 = None
 
 
 def read_stream_gbs(torch, dev, stream):

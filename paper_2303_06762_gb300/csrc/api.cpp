@@ -662,14 +662,6 @@ hdg_status uzawa_solve(hdg_ctx *ctx, const double *F, double *u, double *p, cons
     if (opts_in) o = *opts_in;
     REQUIRE(o.restart >= 1 && o.restart <= 32, "restart out of range 1..32");
     REQUIRE(o.max_uzawa >= 1 && o.max_uzawa <= 64, "max_uzawa out of range 1..64");
-    if (o.krylov != 0) {
-        ctx->err = "batched solves run flexible GMRES only (krylov = 0)";
-        throw Fail{HDG_ERR_UNSUPPORTED};
-    }
-    if (ctx->has_dir) {
-        ctx->err = "batched solves take homogeneous Dirichlet data only";
-        throw Fail{HDG_ERR_UNSUPPORTED};
-    }
     REQUIRE(o.max_it >= 1 && o.rtol >= 0 && o.atol >= 0 && o.floor_rel >= 0 && o.uzawa_tol >= 0,
             "bad tolerances");
     REQUIRE(o.krylov == 0 || o.krylov == 1, "krylov must be 0 (FGMRES) or 1 (PCG)");
@@ -1146,6 +1138,14 @@ hdg_status uzawa_solve_m(hdg_ctx *ctx, int nrhs, int R, const double *F, double 
     if (opts_in) o = *opts_in;
     REQUIRE(o.restart >= 1 && o.restart <= 32, "restart out of range 1..32");
     REQUIRE(o.max_uzawa >= 1 && o.max_uzawa <= 64, "max_uzawa out of range 1..64");
+    if (o.krylov != 0) {
+        ctx->err = "batched solves run flexible GMRES only (krylov = 0)";
+        throw Fail{HDG_ERR_UNSUPPORTED};
+    }
+    if (ctx->has_dir) {
+        ctx->err = "batched solves take homogeneous Dirichlet data only";
+        throw Fail{HDG_ERR_UNSUPPORTED};
+    }
     REQUIRE(o.max_it >= 1 && o.rtol >= 0 && o.atol >= 0 && o.floor_rel >= 0 && o.uzawa_tol >= 0,
             "bad tolerances");
     ensure_krylov_m(ctx, o.restart, R);
