@@ -514,7 +514,9 @@ def batched_form(args, hdg, torch, dev, stream, world):
     one load solved alone by hdg_solve on the same operator."""
     from workloads import unit_square_hierarchy
     from workloads.manufactured import fourier_forcing_2d, lattice_points_2d
-    N, N0, k, nrhs = 256, 32, 3, 64
+    # coarsest 8x8: with 64 columns the dense coarse solve is a GEMM of n0^2 x 64 FP64 products,
+    # 4.6 GFLOP on a 32x32 coarsest level against 16 MFLOP on 8x8
+    N, N0, k, nrhs = 256, 8, 3, 64
     nl = 1
     while N0 * 2 ** (nl - 1) < N:
         nl += 1
