@@ -346,3 +346,22 @@ def test_uzawa_solves_saddle_point():
     assert np.linalg.norm(r.u - u) < 1e-9 * np.linalg.norm(u)
     e = r.p - p
     assert np.linalg.norm(e) < 1e-7 * np.linalg.norm(p)
+
+
+def test_count_trend_flattens_and_is_robust_in_gamma():
+    """PCG counts of Algorithm 2 (k = 1, m = 1, variable V-cycle) on N = 16, 32, 64: the growth per
+    refinement does not increase and stays small, and gamma = 1e2 and 1e4 agree within 2
+    (Section 5.2.1: robust in h and eps; the device continues the trend to N = 512 in
+    tests/test_gpu_counts.py).  The paper's k = 1 counts on levels 5..7 (19, 20, 20) are context."""
+    def its(nl, gamma):
+        ms, ts, ps = hierarchy(2, nl)
+        h = HDG(ts[-1], 1, beta=0.0, gamma=gamma)
+        M = build_hpmg(ts, ps, 1, 1.0, 0.0, gamma, hdg_k=h)
+        F = h.load(forcing(ms[-1], 1, curl_bubble_2d(), 1.0, 0.0))
+        return _pcg_its(M.A, F, M)
+    lo = [its(nl, 1e2) for nl in (4, 5, 6)]
+    hi = [its(nl, 1e4) for nl in (4, 5, 6)]
+    for c in (lo, hi):
+        steps = [b - a for a, b in zip(c, c[1:])]
+        assert steps[1] <= steps[0] and max(steps) <= 3, c
+    assert all(abs(a - b) <= 2 for a, b in zip(lo, hi)), (lo, hi)
