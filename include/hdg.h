@@ -169,6 +169,13 @@ typedef struct {
                              /* hdg_solve only: batched solves, hdg_picard,         */
                              /* hdg_newton and hdg_adjoint return                   */
                              /* HDG_ERR_UNSUPPORTED with data set.                  */
+    double pseudo_dt_inv;    /* hdg_picard only: pseudo-time continuation (Section  */
+                             /* 5.2.2), 1/dt* >= 0.  Each Oseen step n >= 1 then    */
+                             /* solves the backward-Euler step (u^n - u^{n-1})/dt*  */
+                             /* + (Oseen operator) u^n = f, i.e. beta + 1/dt* and   */
+                             /* the load f + u^{n-1}/dt* (u^{n-1} at the lattice,   */
+                             /* exact since RT_k lies in [P^{k+1}]^2); a fixed      */
+                             /* point is the steady solution.  0 = plain Picard.    */
 } hdg_params;
 
 typedef struct {

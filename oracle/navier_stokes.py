@@ -49,17 +49,23 @@ def l2_distance(h: HDG, a: np.ndarray, b: np.ndarray) -> float:
     return float(np.sqrt(s))
 
 
-def picard(topo, k, fvals, nu, beta=0.0, gamma=0.0, tol=1e-8, max_steps=50):
-    """Returns (u, p, steps, last distance, the HDG object of the last step, lattice velocity)."""
+def picard(topo, k, fvals, nu, beta=0.0, gamma=0.0, tol=1e-8, max_steps=50, pseudo_dt_inv=0.0):
+    """Returns (u, p, steps, last distance, the HDG object of the last step, lattice velocity).
+
+    pseudo_dt_inv = 1/δt* > 0 adds the pseudo-time continuation of Section 5.2.2 to the Oseen
+    steps: the backward-Euler step (u^n − u^{n−1})/δt* + (Oseen operator)u^n = f, i.e. β + 1/δt*
+    and the load f + u^{n−1}/δt* (u^{n−1} ∈ RT_k ⊂ [P^{k+1}]² given exactly by its lattice
+    values); a fixed point of the iteration is the steady solution."""
     h = HDG(topo, k, nu=nu, beta=beta, gamma=gamma)
     u, p = h.solve_direct(h.load(fvals))
     prev = lattice_velocity(h, u, p, fvals)
     dist = np.inf
     n = 0
     for n in range(1, max_steps + 1):
-        h = HDG(topo, k, nu=nu, beta=beta, gamma=gamma, conv=prev)
-        u, p = h.solve_direct(h.load(fvals))
-        cur = lattice_velocity(h, u, p, fvals)
+        h = HDG(topo, k, nu=nu, beta=beta + pseudo_dt_inv, gamma=gamma, conv=prev)
+        fn = fvals + pseudo_dt_inv * prev
+        u, p = h.solve_direct(h.load(fn))
+        cur = lattice_velocity(h, u, p, fn)
         dist = l2_distance(h, cur, prev)
         prev = cur
         if dist < tol:

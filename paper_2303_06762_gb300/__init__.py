@@ -68,7 +68,7 @@ class _Params(ctypes.Structure):
                 ("cycle", ctypes.c_int), ("vcycle_growth", ctypes.c_int), ("precision", ctypes.c_int),
                 ("fused_coarse_cells", ctypes.c_int), ("nu_elem", ctypes.c_void_p), ("conv", ctypes.c_void_p),
                 ("newton_u", ctypes.c_void_p), ("smoother", ctypes.c_int), ("jacobi_damping", ctypes.c_double),
-                ("hp_additive", ctypes.c_int), ("dirichlet", ctypes.c_void_p)]
+                ("hp_additive", ctypes.c_int), ("dirichlet", ctypes.c_void_p), ("pseudo_dt_inv", ctypes.c_double)]
 
 
 class HierarchyInfo(ctypes.Structure):
@@ -122,6 +122,7 @@ class Params:
     jacobi_damping: float = 0.5
     hp_additive: int = 0            # 1 = additive form of Algorithm 2
     dirichlet: object = None        # optional CUDA float64 tensor [n_boundary_facets, dpf]: boundary data
+    pseudo_dt_inv: float = 0.0      # hdg_picard: pseudo-time continuation 1/dt* (0 = off)
 
     def to_c(self) -> _Params:
         ne = None if self.nu_elem is None else _ptr(self.nu_elem)
@@ -130,7 +131,7 @@ class Params:
         return _Params(self.k, self.nu, self.beta, self.gamma, self.m_p, self.m_h, self.cycle,
                        self.vcycle_growth, self.precision, self.fused_coarse_cells, ne, cv, nw,
                        self.smoother, self.jacobi_damping, self.hp_additive,
-                       None if self.dirichlet is None else _ptr(self.dirichlet))
+                       None if self.dirichlet is None else _ptr(self.dirichlet), self.pseudo_dt_inv)
 
 
 _lib = None

@@ -1463,7 +1463,7 @@ void hdg_destroy(hdg_ctx *ctx) {
     dfree(ctx->refk_dev); dfree(ctx->ref0_dev);
     dfree(ctx->kr); dfree(ctx->ku); dfree(ctx->kt); dfree(ctx->krf); dfree(ctx->kuf); dfree(ctx->kgf);
     dfree(ctx->post_tabs); dfree(ctx->pcg_buf); dfree(ctx->jD); dfree(ctx->jDf); dfree(ctx->dir_x);
-    dfree(ctx->dir_flux);
+    dfree(ctx->dir_flux); dfree(ctx->pic_f);
     dfree(ctx->coarse_inv); dfree(ctx->status_flag); dfree(ctx->wait_flag); dfree(ctx->conv_k); dfree(ctx->newton_x);
     dfree(ctx->V); dfree(ctx->Z); dfree(ctx->w); dfree(ctx->partials); dfree(ctx->small);
     dfree(ctx->uz_partials);
@@ -2227,6 +2227,7 @@ hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forc
         }
         REQUIRE(max_steps >= 1 && tol >= 0 && std::isfinite(tol), "bad tol or max_steps");
         REQUIRE(params->k >= 0 && params->k <= MAX_K, "k out of range 0..4");
+        REQUIRE(params->pseudo_dt_inv >= 0 && std::isfinite(params->pseudo_dt_inv), "pseudo_dt_inv must be >= 0");
         cudaStream_t s = (cudaStream_t)stream;
         const int J = ctx->n_levels - 1;
         DevLevel &LJ = ctx->L[J];
@@ -2251,12 +2252,22 @@ hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forc
         check(hdg_solve(ctx, ctx->pic_F.p, u, p, opts, nullptr, stream));
         double *wp = ctx->pic_w0.p, *wc = ctx->pic_w1.p;
         recover_impl(ctx, u, forcing, nullptr, nullptr, wp, s);
-        // Oseen steps with w_h = u_h^(n-1) until ||u^(n) - u^(n-1)|| < tol
+        // Oseen steps with w_h = u_h^(n-1) until ||u^(n) - u^(n-1)|| < tol; with pseudo-time the
+        // step adds (u^n - u^(n-1))/dt*: beta + 1/dt* and the load f + u^(n-1)/dt*
+        const double dti = params->pseudo_dt_inv;
+        prm.beta = params->beta + dti;
+        if (dti > 0) dalloc(ctx, ctx->pic_f, nc * 2 * nlat);
         for (int n = 1; n <= max_steps; ++n) {
             prm.conv = wp;
-            check(hdg_condense(ctx, &prm, forcing, ctx->pic_F.p, stream));
+            const double *fn = forcing;
+            if (dti > 0) {
+                CK(cudaMemcpyAsync(ctx->pic_f.p, forcing, sizeof(double) * nc * 2 * nlat, cudaMemcpyDeviceToDevice, s));
+                CK(launch_axpby(dti, wp, 1.0, ctx->pic_f.p, nc * 2 * nlat, s));
+                fn = ctx->pic_f.p;
+            }
+            check(hdg_condense(ctx, &prm, fn, ctx->pic_F.p, stream));
             check(hdg_solve(ctx, ctx->pic_F.p, u, p, opts, nullptr, stream));
-            recover_impl(ctx, u, forcing, nullptr, nullptr, wc, s);
+            recover_impl(ctx, u, fn, nullptr, nullptr, wc, s);
             CK(launch_objective(k, LJ, ctx->refk_dev.p, ctx->refk, wc, wp, ctx->pic_e.p, ctx->pic_j.p, s));
             dist = std::sqrt(std::max(2.0 * device_sum(ctx, ctx->pic_j.p, nc, s), 0.0));
             steps = n;

@@ -278,6 +278,7 @@ struct hdg_ctx {
     hdg::DBuf<double> pcm_in, pcm_out;
     cudaStream_t batch_stream = nullptr;     // private stream for hdg_solve_batched
     hdg::DBuf<double> pic_F, pic_w0, pic_w1, pic_e, pic_j, pic_x;   // Picard / Newton iteration work
+    hdg::DBuf<double> pic_f;                 // Picard with pseudo-time: the step's lattice load
     // fused MG_h on levels 0..small_Ls (one thread block), -1 when not used
     int small_Ls = -1;
     size_t small_smem_d = 0, small_smem_f = 0;   // per-CTA shared memory of the fused kernel

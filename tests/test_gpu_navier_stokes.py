@@ -36,6 +36,27 @@ def test_picard_matches_oracle(k, Re, precision):
     assert rel(pm, pom) < 1e-7
 
 
+@pytest.mark.parametrize("dti", [0.1, 1.0])
+def test_pseudo_time_picard_matches_oracle(dti):
+    """Picard with pseudo-time continuation (Section 5.2.2): the same steps and iterates as the
+    oracle's, and the same fixed point as the plain iteration."""
+    import paper_2303_06762_gb300 as hdg
+    k, nu = 2, 0.05
+    ms, ts, ps = hierarchy(2, 3)
+    fine = ms[-1]
+    fv = forcing_at_lattice(fine.coords, fine.cells, k, SOL.forcing(nu, 0.0, conv=SOL.u))
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    o = hdg.default_solve_opts()
+    o.rtol, o.atol, o.floor_rel, o.uzawa_tol = 1e-12, 1e-14, 1e-12, 1e-11
+    prm = hdg.Params(k=k, nu=nu, beta=0.0, gamma=10.0, pseudo_dt_inv=dti)
+    u, p, steps, dist = hdg.hdg_picard(ctx, prm, torch.tensor(fv, device=DEV), tol=1e-10, max_steps=200, opts=o)
+    uo, po, n, do, h, w = picard(ts[-1], k, fv, nu, gamma=10.0, tol=1e-10, pseudo_dt_inv=dti, max_steps=200)
+    u0, *_ = picard(ts[-1], k, fv, nu, gamma=10.0, tol=1e-10)
+    print(f"pseudo-time 1/dt*={dti}: {steps} Picard steps (oracle {n})")
+    assert abs(steps - n) <= 1
+    assert rel(u.cpu().numpy(), uo) < 1e-8 and rel(u.cpu().numpy(), u0) < 1e-8
+
+
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_newton_operator_matches_oracle(k):
     """Condensed matrices and load of a Newton step (conv = u_old at the lattice, newton_u = the

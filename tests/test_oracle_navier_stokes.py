@@ -75,3 +75,22 @@ def test_newton_quadratic_and_same_fixed_point(k, nu):
             assert b < 5.0 * a * a / max(dists[0], 1e-300) + 1e-13 or b < 1e-3 * a
     uP, pP, nP, dP, hP, wP = picard(t, k, fv, nu, tol=1e-13, max_steps=200)
     assert np.abs(un - uP).max() < 1e-11 * np.abs(uP).max()
+
+
+def test_pseudo_time_picard_same_fixed_point():
+    """Pseudo-time continuation (Section 5.2.2) changes the path, not the limit: with
+    1/dt* = 0.1 and 1 the Picard iteration converges to the fixed point of the plain one,
+    which is the steady discrete solution (re-solving with it as convecting field and
+    no pseudo-time term reproduces it)."""
+    k, nu = 2, 0.05
+    m = unit_square(8)
+    t = topo_of(m)
+    fv = _ns_forcing(m, k, nu)
+    u0, p0, n0, d0, h0, w0 = picard(t, k, fv, nu, gamma=10.0, tol=1e-11)
+    for dti in (0.1, 1.0):
+        u, p, n, d, h, w = picard(t, k, fv, nu, gamma=10.0, tol=1e-11, pseudo_dt_inv=dti, max_steps=200)
+        assert d < 1e-11
+        assert np.abs(u - u0).max() < 1e-8 * np.abs(u0).max()
+        h2 = HDG(t, k, nu=nu, gamma=10.0, conv=w)
+        u2, p2 = h2.solve_direct(h2.load(fv))
+        assert np.abs(u2 - u).max() < 1e-8 * np.abs(u).max()
