@@ -75,7 +75,6 @@ void free_operator(DevOperator &op) {
     dfree(op.Pinv);
     dfree(op.Pinvf);
     dfree(op.Pinvp);
-    dfree(op.Ap);
     dfree(op.Ah);
     dfree(op.Ah_s);
     dfree(op.Pinvh);
@@ -86,7 +85,7 @@ void free_operator(DevOperator &op) {
 void free_level(DevLevel &L) {
     dfree(L.coords); dfree(L.cells); dfree(L.cell_int); dfree(L.facet_adj); dfree(L.cell_d); dfree(L.cell_nu);
     dfree(L.cell_area); dfree(L.conv_flux); dfree(L.conv_lat); dfree(L.patch_nf); dfree(L.patch_facets); dfree(L.patch_nc);
-    dfree(L.patch_cells); dfree(L.patch_slot_src); dfree(L.gs0_table); dfree(L.facet_slot); dfree(L.cell_bnd); dfree(L.patch_vloc);
+    dfree(L.patch_cells); dfree(L.patch_slot_src); dfree(L.gs0_table); dfree(L.facet_slot); dfree(L.cell_bnd);
     free_operator(L.op0);
     dfree(L.tr_slots); dfree(L.tr_nbr); dfree(L.tr_children); dfree(L.tr_child_slot);
     dfree(L.tr_fineB); dfree(L.tr_fineB_src); dfree(L.tr_W); dfree(L.tr_H); dfree(L.tr_Wf);
@@ -1358,7 +1357,6 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
             upload(ctx, L.patch_nc, H.patch_nc);
             upload(ctx, L.patch_cells, H.patch_cells);
             upload(ctx, L.patch_slot_src, H.patch_slot_src);
-            upload(ctx, L.patch_vloc, H.patch_vloc);
             {
                 // the two vertex-patch slots of every interior facet (block Jacobi gather)
                 std::vector<int32_t> fs(2 * H.n_int, -1);
@@ -1590,11 +1588,9 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
     if (!ctx->has_conv && k >= 1 && prm->precision != HDG_FP64) {
         // symmetric patch inverses: the FP32 sweep reads packed triangles (half the bytes)
         dalloc(ctx, op.Pinvp, (size_t)LJ.n_patches * packed_patch_size(op.np_max));
-        dalloc(ctx, op.Ap, (size_t)LJ.nc * packed_cell_size(op.dpf));
         CK(launch_pack_sym(LJ, op, s));
     } else {
         dfree(op.Pinvp);
-        dfree(op.Ap);
     }
     op.h_fmt = 0;
     if (k >= 1 && (prm->precision == HDG_MIXED_BF16 || prm->precision == HDG_MIXED_FP16)) {

@@ -45,7 +45,6 @@ struct HostLevel {
     std::vector<int32_t> patch_cells;    // n_patches*pc_max
     // for slot j of patch p: the two (star-cell index << 2 | local facet) pairs
     std::vector<int32_t> patch_slot_src; // n_patches*pf_max*2
-    std::vector<int32_t> patch_vloc;     // n_patches*pc_max: local index of the patch vertex in each star cell
 };
 
 // transfer data between level l-1 (coarse) and l (fine), stored on level l
@@ -154,10 +153,6 @@ struct DevOperator {
     DBuf<float> Pinvf;
     DBuf<float> Pinvp;   // symmetric operators, order k: packed upper triangles of (Pinv + Pinv^T)/2,
                          // packed_patch_size(np_max) floats per patch (bulk-copy sweep)
-    DBuf<float> Ap;      // symmetric operators, order k: per cell the packed diagonal facet blocks
-                         // D_0, D_1, D_2 (upper triangles, packed_block_size(dpf) floats each) and the
-                         // off-diagonal blocks O_01, O_02, O_12 (dpf x dpf, rows of the lower facet),
-                         // of (A + A^T)/2 in FP32: packed_cell_size(dpf) floats per cell
     // 16-bit copies for HDG_MIXED_BF16 / HDG_MIXED_FP16 (order-k operator only): the
     // layouts of A and Pinv with every stored row divided by its power-of-two scale
     int *tma_flag = nullptr; // device flag of the bulk-copy sweep's bounded waits (bit 4 on timeout),
@@ -186,7 +181,6 @@ struct DevLevel {
     std::vector<int32_t> colour_ptr;
     DBuf<int32_t> patch_nf, patch_facets, patch_nc, patch_cells, patch_slot_src;
     DBuf<int32_t> facet_slot;  // n_int*2: the two patch slots (p pf_max + position) holding each facet
-    DBuf<int32_t> patch_vloc;  // n_patches*pc_max: local index of the patch vertex in each star cell
     DBuf<int32_t> cell_bnd;    // nc*3: boundary facet number of each local facet or -1 (finest level)
     int64_t n_bnd = 0;         // boundary facets (finest level)
     // lowest-order sweep gather table (levels with at most GS0_TABLE_MAX_CELLS cells): per
@@ -291,9 +285,6 @@ namespace hdg {
 
 // floats of one packed symmetric patch inverse: np(np+1)/2 rounded up to 4 (16 bytes)
 inline int packed_patch_size(int np_max) { return (np_max * (np_max + 1) / 2 + 3) / 4 * 4; }
-// floats of one packed diagonal facet block and of one cell of the packed element matrices
-inline int packed_block_size(int dpf) { return (dpf * (dpf + 1) / 2 + 3) / 4 * 4; }
-inline int packed_cell_size(int dpf) { return 3 * packed_block_size(dpf) + 3 * dpf * dpf; }
 
 // kernel-launch counter (ops.cu): every launcher adds the kernels it enqueues
 void note_launches(long long n);
@@ -358,7 +349,7 @@ cudaError_t launch_apply_h(const DevLevel &L, const DevOperator &op, const float
                            cudaStream_t s);
 cudaError_t launch_gs_colour_h(const DevLevel &L, const DevOperator &op, int colour, const float *g, float *u,
                                cudaStream_t s);
-// fills op.Pinvp (allocated by the caller) from op.Pinv, and op.Ap (when allocated) from op.A
+// fills op.Pinvp (allocated by the caller) from op.Pinv
 cudaError_t launch_pack_sym(const DevLevel &L, DevOperator &op, cudaStream_t s);
 // fills op.Ah, Ah_s, Pinvh, Pinvh_s (allocated by the caller) from op.A and op.Pinv
 cudaError_t launch_round16(const DevLevel &L, DevOperator &op, int fmt, cudaStream_t s);

@@ -313,27 +313,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 // SYM: the patch inverses are symmetric (generalized Stokes) and stored as packed upper
 // triangles, row i holding columns i..np_max-1 at offset i np_max - i(i-1)/2, one patch every
 // psz floats (psz = the packed size rounded up to 4 floats, so every copy is 16-byte sized);
-// otherwise full np_max x np_max transposed inverses, of which the np used rows are copied.
-// PE (with SYM): the element matrices come packed (packed_cell_size floats per cell: diagonal
-// facet blocks as upper triangles, then O_01, O_02, O_12); per star cell the patch needs the
-// rows of its two facets at the patch vertex, i.e. the three off-diagonal blocks and the two
-// diagonal blocks of those facets (5 of the 6 blocks, 264 of 576 floats at k = 3), copied into
-// a star-cell chunk [O_01 O_02 O_12 | D_x | D_y] (x < y the facets containing the vertex).
-template <int DPF, bool SYM, bool PE>
+// otherwise full np_max x np_max transposed inverses, of which the np used rows are copied
+template <int DPF, bool SYM>
 __global__ void __launch_bounds__(64)
 gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
               const int *__restrict__ patch_nf, const int *__restrict__ patch_facets,
               const int *__restrict__ patch_nc, const int *__restrict__ patch_cells,
               const int *__restrict__ slot_src, const int *__restrict__ cell_int,
-              const int *__restrict__ patch_vloc,
               const float *__restrict__ A, const float *__restrict__ Pinv,
               const float *__restrict__ g, float *__restrict__ u, int *flag, unsigned long long wait_ns) {
     constexpr int NLOC = 3 * DPF;
     constexpr int RB = NLOC * DPF;             // floats in one facet row block
-    constexpr int DSZ = (DPF * (DPF + 1) / 2 + 3) / 4 * 4;   // packed diagonal block
-    constexpr int OSZ = DPF * DPF;                           // off-diagonal block
-    constexpr int CSZ = 3 * DSZ + 3 * OSZ;                   // packed cell
-    constexpr int SSZ = 3 * OSZ + 2 * DSZ;                   // star-cell chunk in shared memory
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ int s_ok;
@@ -342,8 +332,8 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
     float *Ps = reinterpret_cast<float *>(smraw);            // np rows of np_max, or psz packed
-    float *As = Ps + (SYM ? (size_t)psz : (size_t)np_max * np_max);   // 2 pf_max row blocks / pc_max chunks
-    float *xs = As + (PE ? (size_t)pc_max * SSZ : (size_t)2 * pf_max * RB);   // pc_max * NLOC
+    float *As = Ps + (SYM ? (size_t)psz : (size_t)np_max * np_max);   // 2 pf_max row blocks
+    float *xs = As + (size_t)2 * pf_max * RB;                // pc_max * NLOC
     float *r = xs + (size_t)pc_max * NLOC;                   // np_max
     const uint32_t bar = smem_u32(&mbar);
     if (tid == 0) {
@@ -355,41 +345,21 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
     if (tid < 32) {
         const uint32_t pbytes = (uint32_t)((SYM ? psz : np * np_max) * sizeof(float));
         const uint32_t abytes = (uint32_t)(RB * sizeof(float));
-        const uint32_t ebytes = PE ? (uint32_t)(ncell * SSZ * sizeof(float)) : 2u * nf * abytes;
         if (tid == 0)
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         ::"r"(bar), "r"(pbytes + ebytes) : "memory");
+                         ::"r"(bar), "r"(pbytes + 2u * nf * abytes) : "memory");
         __syncwarp();
         if (tid == 0) {
             const float *src = Pinv + (SYM ? (size_t)p * psz : (size_t)p * np_max * np_max);
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                          ::"r"(smem_u32(Ps)), "l"(src), "r"(pbytes), "r"(bar) : "memory");
         }
-        if constexpr (PE) {
-            for (int si = tid; si < ncell; si += 32) {
-                const int c = patch_cells[(size_t)p * pc_max + si];
-                const int vl = patch_vloc[(size_t)p * pc_max + si];
-                const int fx = vl == 0 ? 1 : 0, fy = vl == 2 ? 1 : 2;   // the facets containing the vertex
-                const float *cb = A + (size_t)c * CSZ;
-                float *dst = As + (size_t)si * SSZ;
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             ::"r"(smem_u32(dst)), "l"(cb + 3 * DSZ), "r"((uint32_t)(3 * OSZ * sizeof(float))),
-                             "r"(bar) : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             ::"r"(smem_u32(dst + 3 * OSZ)), "l"(cb + fx * DSZ), "r"((uint32_t)(DSZ * sizeof(float))),
-                             "r"(bar) : "memory");
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             ::"r"(smem_u32(dst + 3 * OSZ + DSZ)), "l"(cb + fy * DSZ),
-                             "r"((uint32_t)(DSZ * sizeof(float))), "r"(bar) : "memory");
-            }
-        } else {
-            for (int sl = tid; sl < 2 * nf; sl += 32) {
-                const int src = slot_src[(size_t)p * pf_max * 2 + sl];   // slot (js, q) at js*2 + q
-                const int c = patch_cells[(size_t)p * pc_max + (src >> 2)];
-                const float *blk = A + (size_t)c * NLOC * NLOC + (size_t)(src & 3) * RB;
-                asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                             ::"r"(smem_u32(As + (size_t)sl * RB)), "l"(blk), "r"(abytes), "r"(bar) : "memory");
-            }
+        for (int sl = tid; sl < 2 * nf; sl += 32) {
+            const int src = slot_src[(size_t)p * pf_max * 2 + sl];   // slot (js, q) at js*2 + q
+            const int c = patch_cells[(size_t)p * pc_max + (src >> 2)];
+            const float *blk = A + (size_t)c * NLOC * NLOC + (size_t)(src & 3) * RB;
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(As + (size_t)sl * RB)), "l"(blk), "r"(abytes), "r"(bar) : "memory");
         }
     }
     for (int t = tid; t < ncell * NLOC; t += nt) {
@@ -418,33 +388,10 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
         float acc = g[(size_t)F * DPF + d];
         for (int q = 0; q < 2; ++q) {
             int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
+            const float *Ac = As + (size_t)(js * 2 + q) * RB + d;
             const float *xc = xs + (src >> 2) * NLOC;
-            if constexpr (PE) {
-                const int si = src >> 2, a = src & 3;
-                const int vl = patch_vloc[(size_t)p * pc_max + si];
-                const float *Sc = As + (size_t)si * SSZ;
-                const float *Da = Sc + 3 * OSZ + (a == (vl == 0 ? 1 : 0) ? 0 : DSZ);
-                // row (a, d) of the cell matrix: the diagonal block of facet a, then the two
-                // off-diagonal blocks (stored with the rows of the lower facet)
 #pragma unroll
-                for (int d2 = 0; d2 < DPF; ++d2) {
-                    const int i = d < d2 ? d : d2, j = d < d2 ? d2 : d;
-                    acc -= Da[i * DPF - i * (i - 1) / 2 + (j - i)] * xc[a * DPF + d2];
-                }
-#pragma unroll
-                for (int f2 = 0; f2 < 3; ++f2) {
-                    if (f2 == a) continue;
-                    const int lo = a < f2 ? a : f2, hi = a < f2 ? f2 : a;
-                    const float *O = Sc + (lo == 0 ? hi - 1 : 2) * OSZ;
-#pragma unroll
-                    for (int d2 = 0; d2 < DPF; ++d2)
-                        acc -= (a < f2 ? O[d * DPF + d2] : O[d2 * DPF + d]) * xc[f2 * DPF + d2];
-                }
-            } else {
-                const float *Ac = As + (size_t)(js * 2 + q) * RB + d;
-#pragma unroll
-                for (int col = 0; col < NLOC; ++col) acc -= Ac[col * DPF] * xc[col];
-            }
+            for (int col = 0; col < NLOC; ++col) acc -= Ac[col * DPF] * xc[col];
         }
         r[t] = acc;
     }
@@ -923,28 +870,25 @@ cudaError_t apply_dispatch(const DevLevel &L, int dpf, const T *A, const T *x, c
     return cudaGetLastError();
 }
 
-template <int DPF, bool SYM, bool PE = false>
+template <int DPF, bool SYM>
 size_t tma_sweep_smem(const DevLevel &L, const DevOperator &op) {
     const size_t rb = (size_t)3 * DPF * DPF;     // one facet row block, n_loc x dpf
     const size_t pin = SYM ? (size_t)packed_patch_size(op.np_max) : (size_t)op.np_max * op.np_max;
-    const size_t ela = PE ? (size_t)L.pc_max * (3 * DPF * DPF + 2 * packed_block_size(DPF)) : 2 * (size_t)L.pf_max * rb;
-    return sizeof(float) * (pin + ela + (size_t)L.pc_max * 3 * DPF + op.np_max);
+    return sizeof(float) * (pin + 2 * (size_t)L.pf_max * rb + (size_t)L.pc_max * 3 * DPF + op.np_max);
 }
 
 // the bulk copies need 16-byte aligned sources, destinations and sizes: the patch
 // inverse (np_max² floats, rows of np_max; or the packed triangle, psz floats), the facet
 // row blocks (3 DPF² floats, at cell strides of 9 DPF² floats) and both bases
-template <int DPF, bool SYM, bool PE = false>
+template <int DPF, bool SYM>
 bool tma_sweep_ok(const DevLevel &L, const DevOperator &op, const float *A, const float *Pinv) {
-    const size_t smem = tma_sweep_smem<DPF, SYM, PE>(L, op);
+    const size_t smem = tma_sweep_smem<DPF, SYM>(L, op);
     if ((op.np_max * sizeof(float)) % 16 || ((size_t)op.np_max * op.np_max * sizeof(float)) % 16 ||
-        (packed_patch_size(op.np_max) * sizeof(float)) % 16 || (3 * DPF * DPF * sizeof(float)) % 16 ||
-        (DPF * DPF * sizeof(float)) % 16 || (packed_block_size(DPF) * sizeof(float)) % 16)
+        (packed_patch_size(op.np_max) * sizeof(float)) % 16 || (3 * DPF * DPF * sizeof(float)) % 16)
         return false;
-    if (PE && !L.patch_vloc.p) return false;
     if (reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(Pinv) % 16) return false;
     if (smem > 100 * 1024) return false;
-    if (cudaFuncSetAttribute(gs_tma_kernel<DPF, SYM, PE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+    if (cudaFuncSetAttribute(gs_tma_kernel<DPF, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {
         cudaGetLastError();
         return false;
@@ -984,32 +928,21 @@ cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, cons
         // symmetric operators sweep with the packed inverses when this is the operator's own
         // FP32 copy (half the inverse bytes); otherwise the full transposed inverses
         const bool sym = op.Pinvp.p && Pinv == op.Pinvf.p;
-        const bool pe = sym && op.Ap.p && A == op.Af.p;
-        if (op.tma_flag && nt == 64 && pe && tma_sweep_ok<DPF, true, true>(L, op, op.Ap.p, op.Pinvp.p)) {
-            const size_t tsm = tma_sweep_smem<DPF, true, true>(L, op);
-            note_launches(1);
-            gs_tma_kernel<DPF, true, true><<<p1 - p0, 64, tsm, s>>>(
-                p0, p1, L.pf_max, L.pc_max, op.np_max, packed_patch_size(op.np_max), L.patch_nf.p, L.patch_facets.p,
-                L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, L.patch_vloc.p, op.Ap.p, op.Pinvp.p,
-                g, u, op.tma_flag, op.tma_wait_ns);
-            return cudaGetLastError();
-        }
         if (op.tma_flag && nt == 64 && sym && tma_sweep_ok<DPF, true>(L, op, A, op.Pinvp.p)) {
             const size_t tsm = tma_sweep_smem<DPF, true>(L, op);
             note_launches(1);
-            gs_tma_kernel<DPF, true, false><<<p1 - p0, 64, tsm, s>>>(
+            gs_tma_kernel<DPF, true><<<p1 - p0, 64, tsm, s>>>(
                 p0, p1, L.pf_max, L.pc_max, op.np_max, packed_patch_size(op.np_max), L.patch_nf.p, L.patch_facets.p,
-                L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, nullptr, A, op.Pinvp.p, g, u,
-                op.tma_flag, op.tma_wait_ns);
+                L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, A, op.Pinvp.p, g, u, op.tma_flag,
+                op.tma_wait_ns);
             return cudaGetLastError();
         }
         if (op.tma_flag && nt == 64 && tma_sweep_ok<DPF, false>(L, op, A, Pinv)) {
             const size_t tsm = tma_sweep_smem<DPF, false>(L, op);
             note_launches(1);
-            gs_tma_kernel<DPF, false, false><<<p1 - p0, 64, tsm, s>>>(
+            gs_tma_kernel<DPF, false><<<p1 - p0, 64, tsm, s>>>(
                 p0, p1, L.pf_max, L.pc_max, op.np_max, 0, L.patch_nf.p, L.patch_facets.p, L.patch_nc.p,
-                L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, nullptr, A, Pinv, g, u, op.tma_flag,
-                op.tma_wait_ns);
+                L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, A, Pinv, g, u, op.tma_flag, op.tma_wait_ns);
             return cudaGetLastError();
         }
     }
@@ -1073,46 +1006,11 @@ cudaError_t round16_launch(const DevLevel &L, DevOperator &op, cudaStream_t s) {
 
 } // namespace
 
-// packed FP32 element matrices of a symmetric operator (op.Ap layout): the upper triangles of the
-// diagonal facet blocks and the off-diagonal blocks O_01, O_02, O_12 of (A + A^T)/2, from the FP64
-// row-block layout ((lf n_loc + q) dpf + d holds A[lf dpf + d][q]); one block per cell
-template <int DPF>
-__global__ void pack_elem_kernel(int64_t nc, const double *__restrict__ A, float *__restrict__ out) {
-    constexpr int NLOC = 3 * DPF, DSZ = (DPF * (DPF + 1) / 2 + 3) / 4 * 4, OSZ = DPF * DPF;
-    const int64_t c = blockIdx.x;
-    if (c >= nc) return;
-    const double *Ac = A + (size_t)c * NLOC * NLOC;
-    auto at = [&](int r, int q) { return Ac[((r / DPF) * NLOC + q) * DPF + r % DPF]; };
-    float *o = out + (size_t)c * (3 * DSZ + 3 * OSZ);
-    for (int e = threadIdx.x; e < 3 * OSZ; e += blockDim.x) {
-        const int f = e / OSZ, i = (e / DPF) % DPF, j = e % DPF;
-        if (i <= j)
-            o[f * DSZ + i * DPF - i * (i - 1) / 2 + (j - i)] =
-                (float)(0.5 * (at(f * DPF + i, f * DPF + j) + at(f * DPF + j, f * DPF + i)));
-        const int lo = f == 2 ? 1 : 0, hi = f == 0 ? 1 : 2;   // block f: O_01, O_02, O_12
-        o[3 * DSZ + f * OSZ + i * DPF + j] = (float)(0.5 * (at(lo * DPF + i, hi * DPF + j) + at(hi * DPF + j, lo * DPF + i)));
-    }
-    for (int e = threadIdx.x; e < 3 * DSZ; e += blockDim.x)
-        if (e % DSZ >= DPF * (DPF + 1) / 2) o[e] = 0.0f;
-}
-
 cudaError_t launch_pack_sym(const DevLevel &L, DevOperator &op, cudaStream_t s) {
-    if (L.n_patches > 0) {
-        note_launches(1);
-        pack_sym_kernel<<<L.n_patches, 256, 0, s>>>(L.n_patches, op.np_max, packed_patch_size(op.np_max), op.Pinv.p,
-                                                    op.Pinvp.p);
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-    }
-    if (!op.Ap.p || L.nc == 0) return cudaSuccess;
+    if (L.n_patches == 0) return cudaSuccess;
     note_launches(1);
-    switch (op.dpf) {
-    case 4: pack_elem_kernel<4><<<(unsigned)L.nc, 128, 0, s>>>(L.nc, op.A.p, op.Ap.p); break;
-    case 6: pack_elem_kernel<6><<<(unsigned)L.nc, 128, 0, s>>>(L.nc, op.A.p, op.Ap.p); break;
-    case 8: pack_elem_kernel<8><<<(unsigned)L.nc, 128, 0, s>>>(L.nc, op.A.p, op.Ap.p); break;
-    case 10: pack_elem_kernel<10><<<(unsigned)L.nc, 128, 0, s>>>(L.nc, op.A.p, op.Ap.p); break;
-    default: return cudaErrorInvalidValue;
-    }
+    pack_sym_kernel<<<L.n_patches, 256, 0, s>>>(L.n_patches, op.np_max, packed_patch_size(op.np_max), op.Pinv.p,
+                                                op.Pinvp.p);
     return cudaGetLastError();
 }
 

@@ -152,18 +152,13 @@ std::string build_level_topology(HostLevel &L, const int32_t *colour_in) {
     L.patch_facets.assign((size_t)L.n_patches * L.pf_max, -1);
     L.patch_cells.assign((size_t)L.n_patches * L.pc_max, -1);
     L.patch_slot_src.assign((size_t)L.n_patches * L.pf_max * 2, -1);
-    L.patch_vloc.assign((size_t)L.n_patches * L.pc_max, -1);
     for (int p = 0; p < L.n_patches; ++p) {
         int v = pv[p];
         std::vector<int32_t> cs = vc[v];
         std::sort(cs.begin(), cs.end());
         L.patch_nf[p] = (int)pf[p].size();
         L.patch_nc[p] = (int)cs.size();
-        for (size_t i = 0; i < cs.size(); ++i) {
-            L.patch_cells[(size_t)p * L.pc_max + i] = cs[i];
-            for (int lv = 0; lv < 3; ++lv)
-                if (L.cells[3 * (size_t)cs[i] + lv] == v) L.patch_vloc[(size_t)p * L.pc_max + i] = lv;
-        }
+        for (size_t i = 0; i < cs.size(); ++i) L.patch_cells[(size_t)p * L.pc_max + i] = cs[i];
         for (size_t j = 0; j < pf[p].size(); ++j) {
             int F = L.interior_facets[pf[p][j]];
             L.patch_facets[(size_t)p * L.pf_max + j] = pf[p][j];
