@@ -824,9 +824,10 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the three colour launches of one
 # order-k sweep of gs_tma_kernel<8, 1> (packed symmetric patch inverses) from an ncu capture on the
 # 128x128, k = 3 case (profiles/ncu_gs_tma_packed_128_k3.md), and that sweep's bytes as the kernel
-# reads them (sweep_bytes with the packed inverse).  None until captured for the current kernel.
-TMA_SWEEP_TRAFFIC_128 = None
-TMA_SWEEP_KERNEL_BYTES_128 = None
+# reads them (sweep_bytes with the packed inverse): (80,281,088 + 1,419,008) + (80,281,344 + 1,366,272)
+# + (80,273,152 + 1,462,272) B against 245,180,992 B.
+TMA_SWEEP_TRAFFIC_128 = 245083136
+TMA_SWEEP_KERNEL_BYTES_128 = 245180992
 
 
 def read_stream_gbs(torch, dev, stream):
