@@ -811,7 +811,8 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
             "read_stream_gbs": rs, "frac_of_read_stream": achieved / rs,
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": achieved / peak, "traffic": traffic,
-            "traffic_note": "scaled from an ncu capture at 128x128 (same kernel, cold caches)" if traffic else None,
+            "traffic_note": ("per sweep (3 colour launches), like achieved: the ncu DRAM bytes of one sweep at 128x128 "
+                             "scaled by the kernel bytes to 512x512 (same kernel, cold caches)") if traffic else None,
             "traffic_over_algorithmic": traffic / alg if traffic else None,
             "algorithmic_bytes_per_sweep": alg,
             "bytes_model": "scope table per-unit model: B_P + B_A' + 3 N s_v (packed symmetric)",
