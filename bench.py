@@ -7,7 +7,7 @@ gamma = 1e2 (eps^-1 = gamma nu), manufactured solution u = curl(sin^2(pi x)
 sin^2(pi y)), p = sin(2 pi x) cos(2 pi y); hp-multigrid with lowest-order
 (Crouzeix-Raviart) levels 32x32 ... 512x512 (5 levels; the 32x32 level solved exactly by one
 dense FP64 GEMV with its precomputed inverse), variable V-cycle
-(m_p = m_h = 1, doubling), FGMRES(30) inside the augmented-Lagrangian Uzawa
+(m_p = m_h = 1, doubling), FGMRES(15) inside the augmented-Lagrangian Uzawa
 loop, stopping rules of Section 5 (inner relative 1e-8 / absolute 1e-10).
 
 A step is one full solve (hdg_solve: Uzawa + FGMRES + hp-MG, all steps of the
@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--gamma", type=float, default=1e2)
     ap.add_argument("--beta", type=float, default=1.0)
     ap.add_argument("--nu", type=float, default=1.0)
+    ap.add_argument("--restart", type=int, default=15,
+                    help="FGMRES restart length of the single-load solves (15 measured fastest at 512x512)")
+    ap.add_argument("--restart-batched", type=int, default=10,
+                    help="FGMRES restart length of the 64-load batched solve (10 measured fastest)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra-forms", action="store_true",
@@ -84,15 +88,21 @@ def workload(args):
     return ms, fv
 
 
-def config(args, n_dof, n_levels):
+def solve_opts(hdg, restart):
+    o = hdg.default_solve_opts()
+    o.restart = restart
+    return o
+
+
+def config(args, n_dof, n_levels, l2="inputs larger than L2 (element and patch matrices several GB)"):
     return {"workload": f"2D generalized Stokes, unit square {args.N}x{args.N} (2N^2 triangles), "
                         f"H(div)-HDG k={args.k}, gamma={args.gamma:g}, alpha(beta)={args.beta:g}, "
                         f"nu={args.nu:g}, manufactured curl solution; hp-MG with CR levels "
                         f"{args.N0}x{args.N0}..{args.N}x{args.N} ({n_levels} levels), variable V-cycle "
-                        f"m=1, FGMRES(30) in AL-Uzawa, stop rel 1e-8 / abs 1e-10",
+                        f"m=1, FGMRES({args.restart}) in AL-Uzawa, stop rel 1e-8 / abs 1e-10",
             "N": args.N, "k": args.k, "skeleton_dofs": int(n_dof), "cells": 2 * args.N * args.N,
             "gamma": args.gamma, "beta": args.beta, "nu": args.nu,
-            "l2": "inputs larger than L2 (element and patch matrices several GB)"}
+            "restart": args.restart, "l2": l2}
 
 
 class ClockSampler:
@@ -346,8 +356,8 @@ def reference_arm(args):
         cores = os.cpu_count()
     val = h.n_dof * its / dt
     # the config of what this arm times: the 32x32 sample of the workload
-    sample_args = argparse.Namespace(**{**vars(args), "N": N, "N0": N0})
-    cfg = config(sample_args, h.n_dof, nl)
+    sample_args = argparse.Namespace(**{**vars(args), "N": N, "N0": N0, "restart": 30})
+    cfg = config(sample_args, h.n_dof, nl, l2="CPU run on the host cores (no GPU caches involved)")
     cfg["sample_of"] = f"{args.N}x{args.N} workload of the GPU arm ({full_skeleton_dofs(args.N, args.k)} skeleton DOFs)"
     sample = (f"{N}x{N} triangulation, {h.n_dof} skeleton DOFs, {nl} levels: a bounded CPU sample of the "
               f"{args.N}x{args.N} workload, timed over {args.steps} full solve(s)")
@@ -382,6 +392,7 @@ def gpu_arm(args):
     ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=local)
     forcing = torch.tensor(fv, device=dev)
     stream = torch.cuda.current_stream(dev)
+    opts = solve_opts(hdg, args.restart)
     results = {}
     sizes = None
     # (HDG_MIXED_BF16 is not timed here: at 512x512, k = 3 its FGMRES stalls before the
@@ -395,7 +406,7 @@ def gpu_arm(args):
         p = torch.zeros(sizes.n_cells, dtype=torch.float64, device=dev)
         for _ in range(args.warmup):
             u.zero_(); p.zero_()
-            hdg.hdg_solve(ctx, F, u, p)
+            hdg.hdg_solve(ctx, F, u, p, opts=opts)
         torch.cuda.synchronize()
         if dist:
             tdist.barrier()
@@ -410,7 +421,7 @@ def gpu_arm(args):
         infos = []
         for _ in range(args.steps):
             u.zero_(); p.zero_()
-            _, _, info = hdg.hdg_solve(ctx, F, u, p)
+            _, _, info = hdg.hdg_solve(ctx, F, u, p, opts=opts)
             its += info["krylov_its_total"]
             infos.append(info)
         ev1.record(stream)
@@ -461,7 +472,7 @@ def gpu_arm(args):
         for _ in range(args.steps):
             Fd.copy_(F_host, non_blocking=True)
             u.zero_(); p.zero_()
-            _, _, info = hdg.hdg_solve(ctx, Fd, u, p)
+            _, _, info = hdg.hdg_solve(ctx, Fd, u, p, opts=opts)
             its += info["krylov_its_total"]
             u_host.copy_(u, non_blocking=True)
             p_host.copy_(p, non_blocking=True)
@@ -533,19 +544,21 @@ def batched_form(args, hdg, torch, dev, stream, world):
     del X, Xf
     sizes = ctx.sizes()
     rb, nt, tile_ms = hdg.hdg_tune_batched(ctx, nrhs)  # the tile the autotuner keeps for this width
-    hdg.hdg_solve_multi(ctx, F)                      # warm-up (graph capture, allocation)
-    t, (U, P, infos) = _timed(torch, stream, lambda: hdg.hdg_solve_multi(ctx, F))
+    om = solve_opts(hdg, args.restart_batched)
+    hdg.hdg_solve_multi(ctx, F, opts=om)             # warm-up (graph capture, allocation)
+    t, (U, P, infos) = _timed(torch, stream, lambda: hdg.hdg_solve_multi(ctx, F, opts=om))
     its = sum(i["krylov_its_total"] for i in infos)
     F0 = F[0].contiguous()
-    hdg.hdg_solve(ctx, F0)
-    t1, (_, _, info1) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F0))
+    o1 = solve_opts(hdg, args.restart)
+    hdg.hdg_solve(ctx, F0, opts=o1)
+    t1, (_, _, info1) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F0, opts=o1))
     # the same loads with the order-k batched sweep on tensor cores (binary16 operands)
     hdg.hdg_condense(ctx, hdg.Params(k=k, nu=1.0, beta=1.0, gamma=1e2, precision=hdg.HDG_MIXED_FP16))
-    hdg.hdg_solve_multi(ctx, F)
-    th, (_, _, infos_h) = _timed(torch, stream, lambda: hdg.hdg_solve_multi(ctx, F))
+    hdg.hdg_solve_multi(ctx, F, opts=om)
+    th, (_, _, infos_h) = _timed(torch, stream, lambda: hdg.hdg_solve_multi(ctx, F, opts=om))
     its_h = sum(i["krylov_its_total"] for i in infos_h)
     ctx.close()
-    uneven = uneven_meshes_form(hdg, torch, dev, stream, world)
+    uneven = uneven_meshes_form(hdg, torch, dev, stream, world, args.restart)
     return {"uneven_meshes": uneven,
             "workload": f"2D generalized Stokes {N}x{N} ({2 * N * N} triangles), k={k}, gamma=1e2, beta=1, nu=1, "
                         f"{nrhs} seeded Fourier+gradient loads, CR levels {N0}x{N0}..{N}x{N}, hdg_solve_multi",
@@ -563,7 +576,7 @@ def batched_form(args, hdg, torch, dev, stream, world):
                                          "operands and FP32 accumulation"}}
 
 
-def uneven_meshes_form(hdg, torch, dev, stream, world):
+def uneven_meshes_form(hdg, torch, dev, stream, world, restart=15):
     """Eight meshes N = 32, 64, ..., 256 (coarsest 2, 2, 3, 2, 5, 3, 7, 2), k = 3, one load each (the
     manufactured curl solution), mixed preconditioner: solved one after the other with hdg_solve, and
     concurrently with hdg_solve_batched (one host thread and stream per mesh)."""
@@ -582,16 +595,17 @@ def uneven_meshes_form(hdg, torch, dev, stream, world):
                                                      precision=hdg.HDG_MIXED_FP32), torch.tensor(fv, device=dev)))
         ctxs.append(ctx)
     dofs = [c.sizes().n_dof for c in ctxs]
+    o = solve_opts(hdg, restart)
     for c, F in zip(ctxs, Fs):
-        hdg.hdg_solve(c, F)
-    hdg.hdg_solve_batched(ctxs, Fs)
+        hdg.hdg_solve(c, F, opts=o)
+    hdg.hdg_solve_batched(ctxs, Fs, opts=o)
     t_seq, its_seq = 0.0, []
     for c, F in zip(ctxs, Fs):
-        t, (_, _, info) = _timed(torch, stream, lambda c=c, F=F: hdg.hdg_solve(c, F))
+        t, (_, _, info) = _timed(torch, stream, lambda c=c, F=F: hdg.hdg_solve(c, F, opts=o))
         t_seq += t
         its_seq.append(info["krylov_its_total"])
     t0 = time.perf_counter()
-    _, _, infos, stat = hdg.hdg_solve_batched(ctxs, Fs)
+    _, _, infos, stat = hdg.hdg_solve_batched(ctxs, Fs, opts=o)
     t_par = time.perf_counter() - t0
     its = [i["krylov_its_total"] for i in infos]
     work = sum(d * i for d, i in zip(dofs, its))
@@ -621,8 +635,9 @@ def coarsest_form(args, hdg, torch, dev, stream):
         ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=dev.index or 0)
         prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma, precision=hdg.HDG_MIXED_FP32)
         F = hdg.hdg_condense(ctx, prm, torch.tensor(fv, device=dev))
-        hdg.hdg_solve(ctx, F)
-        t, (_, _, info) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F))
+        o = solve_opts(hdg, args.restart)
+        hdg.hdg_solve(ctx, F, opts=o)
+        t, (_, _, info) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F, opts=o))
         n = ctx.sizes().n_dof
         out[f"{N0}x{N0}"] = {"levels": nl, "time_to_tol_s": t, "fgmres_iters": info["krylov_its_total"],
                              "krylov_its": info["krylov_its"], "dof_iters_per_s": n * info["krylov_its_total"] / t,
@@ -857,7 +872,7 @@ def profile_solve(args):
     prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma, precision=args.precision)
     F = hdg.hdg_condense(ctx, prm, torch.tensor(fv, device="cuda:0"))
     for _ in range(max(args.warmup, 0) + 1):
-        u, p, info = hdg.hdg_solve(ctx, F)
+        u, p, info = hdg.hdg_solve(ctx, F, opts=solve_opts(hdg, args.restart))
     torch.cuda.synchronize()
     print(json.dumps({"profile_solve": True, "N": args.N, "k": args.k, "launches": hdg.hdg_kernel_launches(),
                       "info": info}))
