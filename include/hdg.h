@@ -183,7 +183,7 @@ typedef struct {
     double atol;        /* inner absolute tolerance (Section 5: 1e-10)              */
     double floor_rel;   /* inner solves stop at <= floor_rel*|F| at the latest      */
     double uzawa_tol;   /* stop when the pressure error estimate <= uzawa_tol |p|   */
-    int restart;        /* FGMRES restart length, 1..32                             */
+    int restart;        /* FGMRES restart length, 1..64 (batched solves: 1..32)     */
     int max_it;         /* FGMRES iterations per inner solve                        */
     int max_uzawa;      /* Uzawa steps, 1..64                                       */
     int krylov;         /* inner Krylov method: 0 = flexible GMRES (restart);       */

@@ -660,7 +660,7 @@ hdg_status uzawa_solve(hdg_ctx *ctx, const double *F, double *u, double *p, cons
     hdg_solve_opts o;
     hdg_default_solve_opts(&o);
     if (opts_in) o = *opts_in;
-    REQUIRE(o.restart >= 1 && o.restart <= 32, "restart out of range 1..32");
+    REQUIRE(o.restart >= 1 && o.restart <= MAX_RESTART, "restart out of range 1..64");
     REQUIRE(o.max_uzawa >= 1 && o.max_uzawa <= 64, "max_uzawa out of range 1..64");
     REQUIRE(o.max_it >= 1 && o.rtol >= 0 && o.atol >= 0 && o.floor_rel >= 0 && o.uzawa_tol >= 0,
             "bad tolerances");

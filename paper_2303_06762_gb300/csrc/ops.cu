@@ -51,7 +51,7 @@ namespace {
 
 constexpr int KRYLOV_BLOCKS = 456;    // 3 x 152 SMs
 constexpr int KRYLOV_THREADS = 256;
-constexpr int MAXV = 33;              // restart <= 32: up to 33 basis vectors
+constexpr int MAXV = 65;              // restart <= 64: up to 65 basis vectors
 
 unsigned blocks_for(int64_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
 

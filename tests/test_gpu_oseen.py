@@ -165,6 +165,25 @@ def test_oseen_solve_matches_oracle(k, Re, mesh):
     assert eu < 1e-9 and ep < 1e-9
 
 
+def test_oseen_restart_50_matches_oracle():
+    """The Oseen configuration's FGMRES(50) (restart lengths up to 64 in single-load solves)."""
+    hdg = _hdg()
+    k, gamma = 2, 100.0
+    ms, ts, ps, conv, fv, ctx, F, nu = oseen_case(2, 3, k, Re=100.0, gamma=gamma)
+    M = build_hpmg(ts, ps, k, nu, 0.0, gamma, conv=conv)
+    oh = M.hdg
+    ro = uzawa(M.A, oh.flux_matrix(), oh.area, oh.eps_inv, oh.load(fv), M, restart=50)
+    o = hdg.default_solve_opts()
+    o.restart = 50
+    u, p, info = hdg.hdg_solve(ctx, F, opts=o)
+    assert info["krylov_its"] == ro.krylov_its
+    assert relnorm(host(u), ro.u) < 1e-10 and relnorm(host(p), ro.p) < 1e-10
+    o.restart = 65
+    with pytest.raises(hdg.HdgError) as e:
+        hdg.hdg_solve(ctx, F, opts=o)
+    assert e.value.status == 1
+
+
 def test_oseen_mixed_precision_solve():
     hdg = _hdg()
     k = 2
