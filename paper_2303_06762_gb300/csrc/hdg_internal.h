@@ -92,7 +92,7 @@ struct SmallLayout {
 
 // views of the smallest lowest-order levels for the single-block MG kernel (mg_small.cu)
 constexpr int SMALL_MAX_LEVELS = 6;
-constexpr int64_t GS0_TABLE_MAX_CELLS = 32768;
+constexpr int64_t GS0_TABLE_MAX_CELLS = int64_t(1) << 25;   // every level up to 33.5M cells (int32 offsets c*36)
 constexpr int GS0_TABLE_INTS = 12;
 constexpr int SMALL_MAX_COLOURS = 15;
 constexpr int64_t SMALL_MAX_CELLS = 32768;
