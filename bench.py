@@ -400,7 +400,10 @@ def gpu_arm(args):
     for name, prec in (("fp64", hdg.HDG_FP64), ("mixed_fp32", hdg.HDG_MIXED_FP32),
                        ("mixed_fp16", hdg.HDG_MIXED_FP16)):
         prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=args.gamma, precision=prec)
-        F = hdg.hdg_condense(ctx, prm, forcing)
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter()
+        F = hdg.hdg_condense(ctx, prm, forcing)     # synchronises: condensation, inverses, coarse inverse
+        t_setup = time.perf_counter() - t_setup
         sizes = ctx.sizes()
         u = torch.zeros(sizes.n_dof, dtype=torch.float64, device=dev)
         p = torch.zeros(sizes.n_cells, dtype=torch.float64, device=dev)
@@ -440,7 +443,8 @@ def gpu_arm(args):
                          "krylov_its": infos[-1]["krylov_its"],
                          "dof_iters_per_s": dof_its / (ms_total / 1e3),
                          "ms_per_iter": ms_total / its if its else None,
-                         "gpu_launches": launches, "clocks": clk, "F": F}
+                         "gpu_launches": launches, "clocks": clk, "F": F,
+                         "setup_s": t_setup}
     head = results["mixed_fp32"]
     line = {"metric": METRIC, "value": head["dof_iters_per_s"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
