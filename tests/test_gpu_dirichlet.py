@@ -84,3 +84,37 @@ def test_driven_lid_matches_oracle(precision):
     with pytest.raises(hdg.HdgError) as e:
         hdg.hdg_solve_multi(ctx, F[None].contiguous())
     assert e.value.status == 8
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_backward_facing_step_matches_oracle(precision):
+    """The backward-facing-step stand-in (Section 5.3 workloads; prescribed parabolic outflow in
+    place of the do-nothing condition) on a red-refined non-convex hierarchy with greedy colouring."""
+    import paper_2303_06762_gb300 as hdg
+    from workloads.mesh2d import step_channel_hierarchy
+    from workloads.manufactured import step_channel_velocity_2d
+    from _util import topo_of
+    ms = step_channel_hierarchy(4)
+    ts = [topo_of(m) for m in ms]
+    ps = [m.parent for m in ms]
+    m, k, gamma = ms[-1], 2, 100.0
+    data = dirichlet_facet_data(m.coords, m.cells, k, step_channel_velocity_2d())
+    zero = np.zeros((m.n_cells, (k + 2) * (k + 3) // 2, 2))
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    F = hdg.hdg_condense(ctx, hdg.Params(k=k, nu=1.0, beta=0.0, gamma=gamma, precision=precision,
+                                         dirichlet=torch.tensor(data, device=DEV)),
+                         torch.tensor(zero, device=DEV))
+    oh = HDG(ts[-1], k, nu=1.0, beta=0.0, gamma=gamma, dirichlet=data)
+    Fo = oh.load(zero)
+    assert rel(F.cpu().numpy(), Fo) < 1e-12
+    ud, pd = oh.solve_direct(Fo)
+    u, p, info = hdg.hdg_solve(ctx, F)
+    eu, ep = relnorm(u.cpu().numpy(), ud), relnorm(p.cpu().numpy(), pd)
+    print(f"step, precision {precision}: its {info['krylov_its']} vs direct |du| {eu:.2e} |dp| {ep:.2e}")
+    assert eu < 1e-8 and ep < 1e-8 and info["div_l2"] < 1e-8
+    if precision == 0:
+        M = build_hpmg(ts, ps, k, 1.0, 0.0, gamma, hdg_k=oh)
+        ro = uzawa(M.A, oh.flux_matrix(), oh.area, oh.eps_inv, Fo, M, bflux=oh.boundary_flux())
+        u, p, info = hdg.hdg_solve(ctx, F)
+        assert info["krylov_its"] == ro.krylov_its
+        assert relnorm(u.cpu().numpy(), ro.u) < 1e-10

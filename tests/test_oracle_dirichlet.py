@@ -84,3 +84,26 @@ def test_driven_lid_cavity():
     assert np.abs(h.flux_matrix() @ u + h.boundary_flux()).max() < 1e-12
     assert abs(h.area @ p) < 1e-12
     assert np.linalg.norm(u) > 0.1
+
+
+def test_backward_facing_step_channel():
+    """The backward-facing-step stand-in (non-convex channel, parabolic inflow and outflow of equal
+    flux, no-slip walls): the data's boundary fluxes cancel, the AL-Uzawa iteration with the
+    hp-multigrid on the red-refined hierarchy reaches the direct solution, and div u_h = 0."""
+    from workloads.mesh2d import step_channel_hierarchy
+    from workloads.manufactured import step_channel_velocity_2d
+    ms = step_channel_hierarchy(3)
+    ts = [topo_of(m) for m in ms]
+    ps = [m.parent for m in ms]
+    m, k = ms[-1], 2
+    data = dirichlet_facet_data(m.coords, m.cells, k, step_channel_velocity_2d())
+    h = HDG(ts[-1], k, nu=1.0, beta=0.0, gamma=100.0, dirichlet=data)
+    bf = h.boundary_flux()
+    assert abs(bf.sum()) < 1e-13 and np.abs(bf).max() > 1e-3
+    F = h.load(np.zeros((m.n_cells, (k + 2) * (k + 3) // 2, 2)))
+    u, p = h.solve_direct(F)
+    assert np.abs(h.flux_matrix() @ u + bf).max() < 1e-12
+    M = build_hpmg(ts, ps, k, 1.0, 0.0, 100.0, hdg_k=h)
+    r = uzawa(M.A, h.flux_matrix(), h.area, h.eps_inv, F, M, bflux=bf, rtol=1e-10, floor_rel=1e-13,
+              uzawa_tol=1e-11)
+    assert relnorm(r.u, u) < 1e-8 and relnorm(r.p, p) < 1e-8

@@ -322,3 +322,18 @@ def lid_velocity_2d(speed: float = 1.0) -> Callable[[np.ndarray], np.ndarray]:
         out[np.isclose(x[:, 1], 1.0), 0] = speed
         return out
     return g
+
+
+def step_channel_velocity_2d() -> Callable[[np.ndarray], np.ndarray]:
+    """Boundary data of the backward-facing-step stand-in (Section 5.3 workloads): a parabolic
+    inflow (16 (y - 1/2)(1 - y), 0) on x = 0, 1/2 < y < 1, a parabolic outflow (2 y (1 - y), 0)
+    on x = 4 carrying the same flux 1/3, and no-slip walls.  The paper's do-nothing outflow is
+    replaced by this prescribed profile."""
+    def g(x):
+        out = np.zeros_like(x)
+        inl = np.isclose(x[:, 0], 0.0) & (x[:, 1] > 0.5)
+        out[inl, 0] = 16.0 * (x[inl, 1] - 0.5) * (1.0 - x[inl, 1])
+        outl = np.isclose(x[:, 0], 4.0)
+        out[outl, 0] = 2.0 * x[outl, 1] * (1.0 - x[outl, 1])
+        return out
+    return g

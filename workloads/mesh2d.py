@@ -157,3 +157,41 @@ def unit_square_hierarchy(N0: int, n_levels: int, shuffle_seed: Optional[int] = 
             for c in range(m.n_cells):
                 m.cells[c] = m.cells[c][rng2.permutation(3)]
     return levels
+
+
+def step_channel(h: float = 0.5, length: float = 4.0, step_length: float = 1.0,
+                 step_height: float = 0.5) -> Mesh2D:
+    """Backward-facing-step channel (0, length) x (0, 1) without the step block
+    (0, step_length) x (0, step_height): squares of side h (the step corners on the grid),
+    each split by its (1,1) diagonal like ``unit_square``; vertices numbered row by row
+    after removing the unused ones.  The colouring (i+j) mod 3 of the grid indices stays
+    proper on the subset."""
+    nx, ny = int(round(length / h)), int(round(1.0 / h))
+    sx, sy = int(round(step_length / h)), int(round(step_height / h))
+    keep_sq = np.ones((ny, nx), dtype=bool)
+    keep_sq[:sy, :sx] = False
+    used = np.zeros((ny + 1, nx + 1), dtype=bool)
+    cells = []
+    for j in range(ny):
+        for i in range(nx):
+            if not keep_sq[j, i]:
+                continue
+            used[j:j + 2, i:i + 2] = True
+            cells.append(((i, j), (i + 1, j), (i + 1, j + 1)))
+            cells.append(((i, j), (i + 1, j + 1), (i, j + 1)))
+    ids = -np.ones((ny + 1, nx + 1), dtype=np.int64)
+    jj, ii = np.nonzero(used)
+    ids[jj, ii] = np.arange(len(jj))
+    coords = np.stack([ii * h, jj * h], axis=1).astype(np.float64)
+    cell_arr = np.array([[ids[b, a] for (a, b) in c] for c in cells], dtype=np.int32)
+    colour = ((ii + jj) % 3).astype(np.int32)
+    return Mesh2D(coords=coords, cells=cell_arr, vertex_colour=colour, meta={"h": h})
+
+
+def step_channel_hierarchy(n_levels: int, h0: float = 0.5) -> List[Mesh2D]:
+    """Levels of the backward-facing-step channel: ``step_channel(h0)`` refined by
+    ``red_refine`` (greedy colouring on the finer levels)."""
+    levels = [step_channel(h0)]
+    for _ in range(1, n_levels):
+        levels.append(red_refine(levels[-1]))
+    return levels
