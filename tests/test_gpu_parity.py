@@ -181,7 +181,7 @@ def test_solve_matches_oracle(k, gamma, mesh):
     assert eu < 1e-10
     # at gamma = 1e4 the last inner solves stop on the residual floor, where the pressure
     # update eps^-1 div u magnifies rounding-order differences of u (Remark 3.1)
-    assert ep < (1e-10 if gamma <= 1e2 else 1e-8)
+    assert ep < (1e-10 if gamma <= 1e2 else 5e-9)
     # against the exact discrete solution (sparse direct solve of the condensed saddle point)
     # with the parity stopping rule
     ud, pd = oh.solve_direct(Fo)
@@ -189,7 +189,7 @@ def test_solve_matches_oracle(k, gamma, mesh):
     eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
     print(f"k={k} gamma={gamma:g}: vs direct |du| {eu:.2e} |dp| {ep:.2e}")
     assert eu < 1e-10
-    assert ep < (1e-10 if gamma <= 1e2 else 1e-8)
+    assert ep < (1e-10 if gamma <= 1e2 else 5e-9)
 
 
 @pytest.mark.parametrize("k", [1, 3])
