@@ -85,7 +85,7 @@ void free_operator(DevOperator &op) {
 void free_level(DevLevel &L) {
     dfree(L.coords); dfree(L.cells); dfree(L.cell_int); dfree(L.facet_adj); dfree(L.cell_d); dfree(L.cell_nu);
     dfree(L.cell_area); dfree(L.conv_flux); dfree(L.conv_lat); dfree(L.patch_nf); dfree(L.patch_facets); dfree(L.patch_nc);
-    dfree(L.patch_cells); dfree(L.patch_slot_src); dfree(L.gs0_table); dfree(L.facet_slot); dfree(L.cell_bnd);
+    dfree(L.patch_cells); dfree(L.patch_slot_src); dfree(L.gs0_table); dfree(L.facet_slot); dfree(L.cell_bnd); dfree(L.patch_cint);
     free_operator(L.op0);
     dfree(L.tr_slots); dfree(L.tr_nbr); dfree(L.tr_children); dfree(L.tr_child_slot);
     dfree(L.tr_fineB); dfree(L.tr_fineB_src); dfree(L.tr_W); dfree(L.tr_H); dfree(L.tr_Wf);
@@ -1357,6 +1357,15 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
             upload(ctx, L.patch_nc, H.patch_nc);
             upload(ctx, L.patch_cells, H.patch_cells);
             upload(ctx, L.patch_slot_src, H.patch_slot_src);
+            if (l == nl - 1) {
+                std::vector<int32_t> pci((size_t)H.n_patches * H.pc_max * 3, -1);
+                for (int p = 0; p < H.n_patches; ++p)
+                    for (int si = 0; si < H.patch_nc[p]; ++si) {
+                        const int c = H.patch_cells[(size_t)p * H.pc_max + si];
+                        for (int f = 0; f < 3; ++f) pci[((size_t)p * H.pc_max + si) * 3 + f] = ci[3 * c + f];
+                    }
+                upload(ctx, L.patch_cint, pci);
+            }
             {
                 // the two vertex-patch slots of every interior facet (block Jacobi gather)
                 std::vector<int32_t> fs(2 * H.n_int, -1);

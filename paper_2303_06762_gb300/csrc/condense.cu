@@ -934,29 +934,38 @@ __global__ void coarse_assemble_kernel(int64_t n_int, const int *__restrict__ fa
     }
 }
 
+// Gauss-Jordan step at pivot piv (SPD coarsest matrix, no pivoting): save the pivot column and
+// the pivot row divided by the pivot (and the pivot's reciprocal at rowp[n]), so that the update
+// is one FMA per entry
 __global__ void gj_save_kernel(const double *M, int64_t n, int64_t piv, double *colp, double *rowp,
                                int *flag) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    double d = M[piv * n + piv];
+    if (!(d > 0.0)) d = 1.0;
+    const double dinv = 1.0 / d;
     if (i < n) {
         colp[i] = M[i * n + piv];
-        rowp[i] = M[piv * n + i];
+        rowp[i] = M[piv * n + i] * dinv;
     }
-    if (i == 0 && !(M[piv * n + piv] > 0.0)) atomicOr(flag, 8);
+    if (i == 0) {
+        rowp[n] = dinv;
+        if (!(M[piv * n + piv] > 0.0)) atomicOr(flag, 8);
+    }
 }
 
+// one row per blockIdx.y, columns across x: no integer division per entry
 __global__ void gj_update_kernel(double *M, int64_t n, int64_t piv, const double *colp,
                                  const double *rowp) {
-    int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= n * n) return;
-    int64_t i = idx / n, j = idx % n;
-    double d = rowp[piv];
-    if (!(d > 0.0)) d = 1.0;
+    const int64_t i = blockIdx.y;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    const double dinv = rowp[n], ci = colp[i];
+    double *Mi = M + i * n;
     double v;
-    if (i == piv && j == piv) v = 1.0 / d;
-    else if (i == piv) v = rowp[j] / d;
-    else if (j == piv) v = -colp[i] / d;
-    else v = M[idx] - colp[i] * rowp[j] / d;
-    M[idx] = v;
+    if (i == piv) v = j == piv ? dinv : rowp[j];
+    else if (j == piv) v = -ci * dinv;
+    else v = fma(-ci, rowp[j], Mi[j]);
+    Mi[j] = v;
 }
 
 // ------------------------------------------------------------------ geometry, loads
@@ -1238,13 +1247,14 @@ cudaError_t launch_coarse_inverse(const DevLevel &L0, double *inv, int64_t n, in
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     double *tmp = nullptr;
-    e = cudaMallocAsync(&tmp, sizeof(double) * 2 * n, s);
+    e = cudaMallocAsync(&tmp, sizeof(double) * (2 * n + 1), s);
     if (e != cudaSuccess) return e;
+    const dim3 ugrid(blocks_for(n, 256), (unsigned)n);
     for (int64_t piv = 0; piv < n; ++piv) {
         note_launches(1);
         gj_save_kernel<<<blocks_for(n, 256), 256, 0, s>>>(inv, n, piv, tmp, tmp + n, flag);
         note_launches(1);
-        gj_update_kernel<<<blocks_for(n * n, 256), 256, 0, s>>>(inv, n, piv, tmp, tmp + n);
+        gj_update_kernel<<<ugrid, 256, 0, s>>>(inv, n, piv, tmp, tmp + n);
     }
     e = cudaGetLastError();
     cudaFreeAsync(tmp, s);

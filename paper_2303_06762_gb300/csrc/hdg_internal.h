@@ -181,6 +181,8 @@ struct DevLevel {
     std::vector<int32_t> colour_ptr;
     DBuf<int32_t> patch_nf, patch_facets, patch_nc, patch_cells, patch_slot_src;
     DBuf<int32_t> facet_slot;  // n_int*2: the two patch slots (p pf_max + position) holding each facet
+    DBuf<int32_t> patch_cint;  // finest level: n_patches*pc_max*3 interior facet of each star cell's local
+                               // facets (-1 on the boundary or for padding): the order-k sweep's gather
     DBuf<int32_t> cell_bnd;    // nc*3: boundary facet number of each local facet or -1 (finest level)
     int64_t n_bnd = 0;         // boundary facets (finest level)
     // lowest-order sweep gather table (levels with at most GS0_TABLE_MAX_CELLS cells): per

@@ -319,7 +319,7 @@ __global__ void __launch_bounds__(64)
 gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
               const int *__restrict__ patch_nf, const int *__restrict__ patch_facets,
               const int *__restrict__ patch_nc, const int *__restrict__ patch_cells,
-              const int *__restrict__ slot_src, const int *__restrict__ cell_int,
+              const int *__restrict__ slot_src, const int *__restrict__ patch_cint,
               const float *__restrict__ A, const float *__restrict__ Pinv,
               const float *__restrict__ g, float *__restrict__ u, int *flag, unsigned long long wait_ns) {
     constexpr int NLOC = 3 * DPF;
@@ -363,9 +363,9 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
         }
     }
     for (int t = tid; t < ncell * NLOC; t += nt) {
-        int si = t / NLOC, l = t % NLOC;
-        int c = patch_cells[(size_t)p * pc_max + si];
-        int j = cell_int[3 * c + l / DPF];
+        // the star's unknowns through the patch's own table of interior facets (one index load)
+        const int si = t / NLOC, l = t % NLOC;
+        const int j = patch_cint[((size_t)p * pc_max + si) * 3 + l / DPF];
         xs[t] = j >= 0 ? u[(size_t)j * DPF + l % DPF] : 0.0f;
     }
     // first wait: wait_ns of global time (0 = treated as expired at once, the testing hook of
@@ -886,6 +886,7 @@ bool tma_sweep_ok(const DevLevel &L, const DevOperator &op, const float *A, cons
     if ((op.np_max * sizeof(float)) % 16 || ((size_t)op.np_max * op.np_max * sizeof(float)) % 16 ||
         (packed_patch_size(op.np_max) * sizeof(float)) % 16 || (3 * DPF * DPF * sizeof(float)) % 16)
         return false;
+    if (!L.patch_cint.p) return false;
     if (reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(Pinv) % 16) return false;
     if (smem > 100 * 1024) return false;
     if (cudaFuncSetAttribute(gs_tma_kernel<DPF, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -933,8 +934,8 @@ cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, cons
             note_launches(1);
             gs_tma_kernel<DPF, true><<<p1 - p0, 64, tsm, s>>>(
                 p0, p1, L.pf_max, L.pc_max, op.np_max, packed_patch_size(op.np_max), L.patch_nf.p, L.patch_facets.p,
-                L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, A, op.Pinvp.p, g, u, op.tma_flag,
-                op.tma_wait_ns);
+                L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.patch_cint.p, A, op.Pinvp.p, g, u,
+                op.tma_flag, op.tma_wait_ns);
             return cudaGetLastError();
         }
         if (op.tma_flag && nt == 64 && tma_sweep_ok<DPF, false>(L, op, A, Pinv)) {
@@ -942,7 +943,7 @@ cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, cons
             note_launches(1);
             gs_tma_kernel<DPF, false><<<p1 - p0, 64, tsm, s>>>(
                 p0, p1, L.pf_max, L.pc_max, op.np_max, 0, L.patch_nf.p, L.patch_facets.p, L.patch_nc.p,
-                L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, A, Pinv, g, u, op.tma_flag, op.tma_wait_ns);
+                L.patch_cells.p, L.patch_slot_src.p, L.patch_cint.p, A, Pinv, g, u, op.tma_flag, op.tma_wait_ns);
             return cudaGetLastError();
         }
     }
