@@ -502,6 +502,7 @@ def gpu_arm(args):
         line["forms"]["batched_mixed_fp32"] = batched_form(args, hdg, torch, dev, stream, world)
         line["forms"]["oseen_mixed_fp32"] = oseen_form(args, hdg, torch, dev, stream)
         line["forms"]["coarsest_level_mixed_fp32"] = coarsest_form(args, hdg, torch, dev, stream)
+        line["forms"]["variants_mixed_fp32"] = variants_form(args, ms, hdg, torch, dev, stream)
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
@@ -620,6 +621,32 @@ def uneven_meshes_form(hdg, torch, dev, stream, world, restart=15):
             "dof_iters_per_s_sequential": sum(d * i for d, i in zip(dofs, its_seq)) * world / t_seq,
             "dof_iters_per_s_concurrent": work * world / t_par, "speedup": t_seq / t_par,
             "timing": "concurrent time is host wall clock around hdg_solve_batched, which synchronises"}
+
+
+def variants_form(args, ms, hdg, torch, dev, stream):
+    """The headline workload (mixed form) with the solver variants: PCG inner solves (Section 5),
+    the damped block-Jacobi smoother (eq. bjac), the additive hp-MG (Remark 3.4), and the AL weight
+    gamma = 1e4 (robustness in eps, reading r25 at scale)."""
+    from workloads import curl_bubble_2d, forcing_at_lattice
+    fine = ms[-1]
+    fv = torch.tensor(forcing_at_lattice(fine.coords, fine.cells, args.k, curl_bubble_2d().forcing(args.nu, args.beta)),
+                      device=dev)
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=dev.index or 0)
+    out = {}
+    cases = (("pcg", {}, 1, args.gamma), ("block_jacobi", dict(smoother=1), 0, args.gamma),
+             ("additive_hp_mg", dict(hp_additive=1), 0, args.gamma), ("gamma_1e4", {}, 0, 1e4))
+    for name, extra, krylov, gamma in cases:
+        prm = hdg.Params(k=args.k, nu=args.nu, beta=args.beta, gamma=gamma, precision=hdg.HDG_MIXED_FP32, **extra)
+        F = hdg.hdg_condense(ctx, prm, fv)
+        o = solve_opts(hdg, args.restart)
+        o.krylov = krylov
+        hdg.hdg_solve(ctx, F, opts=o, raise_on_nonconvergence=False)
+        t, (_, _, info) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F, opts=o, raise_on_nonconvergence=False))
+        out[name] = {"time_to_tol_s": t, "krylov_its": info["krylov_its"], "iterations": info["krylov_its_total"],
+                     "uzawa_steps": info["uzawa_its"], "res_floor_rel": info["res_floor"] / info["normF"],
+                     "div_l2": info["div_l2"]}
+    ctx.close()
+    return out
 
 
 def coarsest_form(args, hdg, torch, dev, stream):
