@@ -371,7 +371,9 @@ def hdg_solve(ctx: Context, F, u=None, p=None, opts: Optional[SolveOpts] = None,
                                   ctypes.byref(info), _stream(stream))
     if st != 0 and (st != 5 or raise_on_nonconvergence):
         ctx.check(st)
-    return u, p, info.as_dict()
+    d = info.as_dict()
+    d["converged"] = st == 0
+    return u, p, d
 
 
 def hdg_apply_multi(ctx: Context, x, y=None, stream=None):
