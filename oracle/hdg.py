@@ -232,8 +232,13 @@ def condense_cell(el: Element, nu: float, beta: float, conv=None,
                   conv_transpose: bool = False, newton_uhat=None,
                   newton_boundary=(False, False, False)) -> CondensedCell:
     """Static condensation of one cell by a dense Schur complement."""
-    M, rhs_map, g, loc, p0, lat_inv, info = local_system(el, nu, beta, conv, conv_transpose, newton_uhat,
-                                                         newton_boundary)
+    return schur_condense(el, *local_system(el, nu, beta, conv, conv_transpose, newton_uhat,
+                                            newton_boundary))
+
+
+def schur_condense(el, M, rhs_map, g, loc, p0, lat_inv, info) -> CondensedCell:
+    """Eliminate the local unknowns `loc` of the full local system M (the dense Schur
+    complement onto the facet unknowns `g`; the cell-mean pressure p0 stays global)."""
     Mll = M[np.ix_(loc, loc)]
     Mlg = M[np.ix_(loc, g)]
     Mgl = M[np.ix_(g, loc)]
@@ -426,6 +431,24 @@ class HDG:
         rhs = np.concatenate([Fn, -bf, [0.0]])
         sol = spla.splu(K).solve(rhs)
         return sol[:self.n_dof], sol[self.n_dof:self.n_dof + nc]
+
+    def solve_al_exact(self, F: np.ndarray, tol: float = 1e-13, max_steps: int = 60):
+        """The same discrete solution by the augmented-Lagrangian Uzawa iteration of Section 3.3
+        with exact inner solves (one sparse LU of A^ε): p ← p − ε⁻¹|K|⁻¹ D u, which contracts by
+        about 1/(1+γ) per step (Lemma 3.1); stops when |D u|/|F| < tol.  Homogeneous data only.
+        For meshes where the LU of the saddle-point matrix fills in too much (3D)."""
+        assert self.xD is None
+        lu = spla.splu(self.matrix(with_al=True).tocsc())
+        D = self.flux_matrix()
+        p = np.zeros(self.topo.n_cells)
+        nF = np.linalg.norm(F)
+        for _ in range(max_steps):
+            u = lu.solve(F + D.T @ p)
+            du = D @ u
+            if np.linalg.norm(du) <= tol * nF:
+                break
+            p -= self.eps_inv * du / self.area
+        return u, p - (self.area @ p) / self.area.sum()
 
     # ------------------------------------------------------------ recovery
     def recover_cell(self, c: int, u: np.ndarray, pK: float, fvals_c: np.ndarray):

@@ -148,10 +148,93 @@ def lattice_points_2d(coords: np.ndarray, cells: np.ndarray, q: int) -> np.ndarr
 
 def forcing_at_lattice(coords: np.ndarray, cells: np.ndarray, k: int,
                        f: Callable[[np.ndarray], np.ndarray]) -> np.ndarray:
-    """Forcing samples (n_cells, n_lattice(k+1), 2) at the degree-(k+1) lattice."""
-    X = lattice_points_2d(coords, cells, k + 1)
+    """Forcing samples (n_cells, n_lattice(k+1), d) at the degree-(k+1) lattice (d = 2 for
+    triangles, 3 for tetrahedra)."""
+    d = coords.shape[1]
+    X = (lattice_points_2d if d == 2 else lattice_points_3d)(coords, cells, k + 1)
     nc, npt, _ = X.shape
-    return f(X.reshape(-1, 2)).reshape(nc, npt, 2)
+    return f(X.reshape(-1, d)).reshape(nc, npt, d)
+
+
+def n_lattice_3d(q: int) -> int:
+    return (q + 1) * (q + 2) * (q + 3) // 6
+
+
+def lattice_barycentric_3d(q: int) -> np.ndarray:
+    """(n, 4) barycentric coordinates of the degree-q lattice of a tetrahedron.
+
+    Order: for a3 = 0..q, for a2 = 0..q-a3, for a1 = 0..q-a2-a3:
+    (lambda1, lambda2, lambda3) = (a1, a2, a3)/q, lambda0 = 1 - lambda1 - lambda2 - lambda3.
+    For q = 0 the single point is the centroid.
+    """
+    if q == 0:
+        return np.full((1, 4), 0.25)
+    pts = []
+    for a3 in range(q + 1):
+        for a2 in range(q + 1 - a3):
+            for a1 in range(q + 1 - a2 - a3):
+                l1, l2, l3 = a1 / q, a2 / q, a3 / q
+                pts.append((1 - l1 - l2 - l3, l1, l2, l3))
+    return np.asarray(pts)
+
+
+def lattice_points_3d(coords: np.ndarray, cells: np.ndarray, q: int) -> np.ndarray:
+    """(n_cells, n_lattice, 3) physical lattice points of every tetrahedron."""
+    lam = lattice_barycentric_3d(q)
+    V = coords[cells]                      # (nc, 4, 3)
+    return np.einsum("pv,cvd->cpd", lam, V)
+
+
+def curl_bubble_3d() -> Solution2D:
+    """The 3D manufactured solution: u = grad psi x (1, 1, 1) with
+    psi = sin²(pi x) sin²(pi y) sin²(pi z) (divergence free, zero on the boundary of the
+    unit cube) and p = sin(2 pi x) cos(2 pi y) sin(2 pi z) (mean free)."""
+    s = lambda t: np.sin(PI * t) ** 2
+    s1 = lambda t: PI * np.sin(2 * PI * t)
+    s2 = lambda t: 2 * PI ** 2 * np.cos(2 * PI * t)
+    s3 = lambda t: -4 * PI ** 3 * np.sin(2 * PI * t)
+    D = (s, s1, s2, s3)
+
+    def dpsi(x, a, b, c):
+        """d^(a,b,c) psi at points x (a, b, c <= 3 derivatives per coordinate)."""
+        return D[a](x[:, 0]) * D[b](x[:, 1]) * D[c](x[:, 2])
+
+    def e(i):
+        t = [0, 0, 0]
+        t[i] += 1
+        return t
+
+    def grad_psi_d(x, extra):
+        """(n, 3): component i = d_i psi differentiated further by the multi-index extra."""
+        return np.stack([dpsi(x, *(np.array(e(i)) + np.array(extra))) for i in range(3)], axis=1)
+
+    def from_grad(G):
+        # u = grad psi x (1,1,1) = (psi_y - psi_z, psi_z - psi_x, psi_x - psi_y)
+        return np.stack([G[:, 1] - G[:, 2], G[:, 2] - G[:, 0], G[:, 0] - G[:, 1]], axis=1)
+
+    def u(x):
+        return from_grad(grad_psi_d(x, (0, 0, 0)))
+
+    def grad_u(x):
+        g = np.empty((x.shape[0], 3, 3))
+        for j in range(3):
+            g[:, :, j] = from_grad(grad_psi_d(x, e(j)))
+        return g
+
+    def lap_u(x):
+        return sum(from_grad(grad_psi_d(x, [2 * (i == j) for i in range(3)])) for j in range(3))
+
+    def p(x):
+        return np.sin(2 * PI * x[:, 0]) * np.cos(2 * PI * x[:, 1]) * np.sin(2 * PI * x[:, 2])
+
+    def grad_p(x):
+        X, Y, Z = x[:, 0], x[:, 1], x[:, 2]
+        sx, cx = np.sin(2 * PI * X), np.cos(2 * PI * X)
+        sy, cy = np.sin(2 * PI * Y), np.cos(2 * PI * Y)
+        sz, cz = np.sin(2 * PI * Z), np.cos(2 * PI * Z)
+        return 2 * PI * np.stack([cx * cy * sz, -sx * sy * sz, sx * cy * cz], axis=1)
+
+    return Solution2D(u, grad_u, lap_u, p, grad_p)
 
 
 def gradient_field_2d(a: np.ndarray):
