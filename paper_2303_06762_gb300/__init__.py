@@ -277,7 +277,11 @@ def _mesh_desc(levels: Sequence):
             keep.append(c)
             vc[l] = c.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
     keep += [nv, nc, co, ce, pa, vc]
-    return _MeshDesc(2, n, nv, nc, co, ce, pa, vc), keep
+    dim = int(levels[0].coords.shape[1])
+    if dim not in (2, 3) or any(int(m.coords.shape[1]) != dim or int(m.cells.shape[1]) != dim + 1 for m in levels):
+        raise ValueError("levels must all be triangulations (coords (nv,2), cells (nc,3)) or all "
+                         "tetrahedrisations (coords (nv,3), cells (nc,4))")
+    return _MeshDesc(dim, n, nv, nc, co, ce, pa, vc), keep
 
 
 def hdg_check_hierarchy(levels: Sequence, k: int = 1) -> dict:
@@ -294,7 +298,8 @@ def hdg_check_hierarchy(levels: Sequence, k: int = 1) -> dict:
 
 def hdg_setup_mesh_hierarchy(levels: Sequence, device: int = 0) -> Context:
     """levels: objects with .coords (nv,2) float64, .cells (nc,3) int32, .parent (levels >= 1)
-    and optional .vertex_colour, coarsest first."""
+    and optional .vertex_colour, coarsest first; or tetrahedral levels, .coords (nv,3) and
+    .cells (nc,4) (3D: edge patches, red-refined hierarchy)."""
     lib = load_library()
     desc, keep = _mesh_desc(levels)
     h = ctypes.c_void_p()
@@ -302,7 +307,13 @@ def hdg_setup_mesh_hierarchy(levels: Sequence, device: int = 0) -> Context:
     ctx = Context(h, device)
     ctx.check(st)
     ctx.level_cells = [int(m.cells.shape[0]) for m in levels]
+    ctx.dim = int(levels[0].coords.shape[1])
     return ctx
+
+
+def dofs_per_facet(dim: int, k: int) -> int:
+    """Skeleton unknowns per facet: 2(k+1) on triangles, 3(k+1)(k+2)/2 on tetrahedra."""
+    return 2 * (k + 1) if dim == 2 else 3 * (k + 1) * (k + 2) // 2
 
 
 def hdg_condense(ctx: Context, params: Params, forcing=None, stream=None):
@@ -312,7 +323,7 @@ def hdg_condense(ctx: Context, params: Params, forcing=None, stream=None):
     p = params.to_c()
     F = None
     if forcing is not None:
-        n = ctx.sizes().n_interior_facets * 2 * (params.k + 1)
+        n = ctx.sizes().n_interior_facets * dofs_per_facet(getattr(ctx, "dim", 2), params.k)
         F = torch.empty(n, dtype=torch.float64, device=forcing.device)
         ctx.check(lib.hdg_condense(ctx.handle, ctypes.byref(p), _ptr(forcing), _ptr(F),
                                    _stream(stream)))
@@ -544,11 +555,12 @@ def hdg_adjoint(ctx: Context, forcing, u, u_target, opts: Optional[SolveOpts] = 
 def hdg_get_element_matrices(ctx: Context, level: int = -1, stream=None):
     import torch
     s = ctx.sizes()
+    dim = getattr(ctx, "dim", 2)
     if level < 0:
-        nloc = 6 * (s.k + 1)
+        nloc = (dim + 1) * dofs_per_facet(dim, s.k)
         nc = s.n_cells
     else:
-        nloc = 6
+        nloc = (dim + 1) * dim
         nc = _level_cells(ctx, level)
     out = torch.empty((nc, nloc, nloc), dtype=torch.float64, device=f"cuda:{ctx.device}")
     ctx.check(load_library().hdg_get_element_matrices(ctx.handle, level, _ptr(out), _stream(stream)))

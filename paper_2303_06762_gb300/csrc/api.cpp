@@ -16,7 +16,7 @@
 #include <type_traits>
 #include <vector>
 
-#include "hdg_internal.h"
+#include "hdg3d_internal.h"
 
 using namespace hdg;
 
@@ -237,7 +237,7 @@ void apply_op(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, const T *x
 template <class T>
 void coarse_solve(hdg_ctx *ctx, cudaStream_t s) {
     DevLevel &L0 = ctx->L[0];
-    int64_t n = 2 * L0.n_int;
+    int64_t n = L0.dim * L0.n_int;
     if constexpr (std::is_same<T, double>::value) {
         CK(launch_coarse_apply(ctx->coarse_inv.p, n, L0.g.p, L0.u.p, s));
     } else {
@@ -340,7 +340,7 @@ void mg_h(hdg_ctx *ctx, int l, int m, bool zero_init, cudaStream_t s) {
     }
     DevLevel &L = ctx->L[l];
     DevLevel &C = ctx->L[l - 1];
-    const int64_t n = 2 * L.n_int;
+    const int64_t n = L.dim * L.n_int;
     T *g = Prec<T>::g(L), *u = Prec<T>::u(L), *r = Prec<T>::r(L);
     if (zero_init) CK(launch_fill<T>(u, T(0), n, s));
     for (int j = 0; j < m; ++j) sweep<T>(ctx, L, L.op0, g, u, false, s);
@@ -352,6 +352,16 @@ void mg_h(hdg_ctx *ctx, int l, int m, bool zero_init, cudaStream_t s) {
     for (int it = 0; it < q; ++it) mg_h<T>(ctx, l - 1, mc, it == 0, s);
     CK(launch_prolong_add<T>(L, C, Prec<T>::W(L), Prec<T>::H(L), Prec<T>::u(C), Prec<T>::t(L), u, s));
     for (int j = 0; j < m; ++j) sweep<T>(ctx, L, L.op0, g, u, true, s);
+}
+
+// Π_k^0 and Π_0^k of the level's dimension
+template <class T>
+cudaError_t hp_restrict_any(const DevLevel &L, int k, const T *r, T *r0, cudaStream_t s) {
+    return L.dim == 3 ? launch_hp_restrict3<T>(k, L.n_int, r, r0, s) : launch_hp_restrict<T>(k, L.n_int, r, r0, s);
+}
+template <class T>
+cudaError_t hp_prolong_any(const DevLevel &L, int k, const T *d0, T *u, cudaStream_t s) {
+    return L.dim == 3 ? launch_hp_prolong_add3<T>(k, L.n_int, d0, u, s) : launch_hp_prolong_add<T>(k, L.n_int, d0, u, s);
 }
 
 // z = MG_hp(r, 0) (Algorithm 2); r, z FP64 of size n_dof
@@ -375,16 +385,16 @@ void mg_hp_impl(hdg_ctx *ctx, const T *r, T *z, cudaStream_t s) {
         // correction of r itself
         for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, false, s);
         for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, true, s);
-        CK(launch_hp_restrict<T>(k, LJ.n_int, r, Prec<T>::g(LJ), s));
+        CK(hp_restrict_any<T>(LJ, k, r, Prec<T>::g(LJ), s));
         mg_h<T>(ctx, J, ctx->prm.m_h, true, s);
-        CK(launch_hp_prolong_add<T>(k, LJ.n_int, Prec<T>::u(LJ), z, s));
+        CK(hp_prolong_any<T>(LJ, k, Prec<T>::u(LJ), z, s));
         return;
     }
     for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, false, s);
     apply_op<T>(ctx, LJ, op, z, r, res, s);
-    CK(launch_hp_restrict<T>(k, LJ.n_int, res, Prec<T>::g(LJ), s));
+    CK(hp_restrict_any<T>(LJ, k, res, Prec<T>::g(LJ), s));
     mg_h<T>(ctx, J, ctx->prm.m_h, true, s);
-    CK(launch_hp_prolong_add<T>(k, LJ.n_int, Prec<T>::u(LJ), z, s));
+    CK(hp_prolong_any<T>(LJ, k, Prec<T>::u(LJ), z, s));
     for (int j = 0; j < ctx->prm.m_p; ++j) sweep<T>(ctx, LJ, op, r, z, true, s);
 }
 
@@ -629,6 +639,16 @@ const double *newton_of(hdg_ctx *ctx) { return ctx->has_newton ? ctx->newton_x.p
 // condensed load F from lattice forcing (the element matrices are left untouched)
 void load_impl(hdg_ctx *ctx, const double *forcing, double *rhs_out, cudaStream_t s) {
     DevLevel &LJ = ctx->L[ctx->n_levels - 1];
+    if (ctx->dim == 3) {
+        int sms = 0;
+        CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+        const int blocks = 2 * std::max(sms, 1);   // the condensation's workspace (sized for this k)
+        CK(launch_condense3(ctx->prm.k, LJ, ctx->ref3k_dev.p, ctx->ref3k, ctx->prm.nu, nullptr, ctx->prm.beta,
+                            ctx->prm.gamma, forcing, nullptr, nullptr, ctx->opk.Fel.p, ctx->c3_scratch.p, blocks,
+                            ctx->status_flag.p, s));
+        CK(launch_assemble_load(LJ, ctx->opk, rhs_out, s));
+        return;
+    }
     CK(launch_condense(ctx->prm.k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, ctx->n_levels - 1),
                        ctx->prm.beta, ctx->prm.gamma, forcing, conv_of(ctx), ctx->conv_t, newton_of(ctx), nullptr,
                        nullptr, ctx->opk.Fel.p, ctx->status_flag.p, RecoverArgs(), s));
@@ -1274,7 +1294,7 @@ int64_t hdg_reference_tables(int k, double *out) {
 // topology, vertex patches and transfer tables of every level, on the host only;
 // throws Fail{HDG_ERR_INVALID_ARG} (message in ctx->err) on an invalid hierarchy
 void build_host_hierarchy(hdg_ctx *ctx, const hdg_mesh_desc *desc) {
-    REQUIRE(desc->dim == 2, "only dim = 2 is supported");
+    REQUIRE(desc->dim == 2, "dim must be 2 here");
     REQUIRE(desc->n_levels >= 1 && desc->n_levels <= MAX_LEVELS, "n_levels out of range 1..16");
     REQUIRE(desc->n_vertices && desc->n_cells && desc->coords && desc->cells, "null mesh arrays");
     const int nl = desc->n_levels;
@@ -1301,13 +1321,18 @@ void build_host_hierarchy(hdg_ctx *ctx, const hdg_mesh_desc *desc) {
     }
 }
 
+static void build_host_hierarchy_3d(hdg_ctx *ctx, const hdg_mesh_desc *desc);
+static void upload_levels_3d(hdg_ctx *ctx);
+
 hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_ctx **out) {
     if (!out) return HDG_ERR_INVALID_ARG;
     *out = nullptr;
     if (!desc) return HDG_ERR_INVALID_ARG;
     hdg_ctx *ctx = new hdg_ctx();
     hdg_status st = guard(ctx, [&] {
-        build_host_hierarchy(ctx, desc);
+        REQUIRE(desc->dim == 2 || desc->dim == 3, "dim must be 2 or 3");
+        if (desc->dim == 3) build_host_hierarchy_3d(ctx, desc);
+        else build_host_hierarchy(ctx, desc);
         const int nl = ctx->n_levels;
         ctx->L.resize(nl);
         // the hierarchy is valid (checked on the host, before any device call): upload
@@ -1316,7 +1341,8 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
         REQUIRE(device >= 0 && device < ndev, "device ordinal out of range");
         ctx->device = device;
         CK(cudaSetDevice(device));
-        for (int l = 0; l < nl; ++l) {
+        if (ctx->dim == 3) upload_levels_3d(ctx);
+        for (int l = 0; l < (ctx->dim == 2 ? nl : 0); ++l) {
             HostLevel &H = ctx->H[l];
             DevLevel &L = ctx->L[l];
             L.nv = H.nv;
@@ -1442,6 +1468,21 @@ hdg_status hdg_check_hierarchy(const hdg_mesh_desc *desc, int k, hdg_hierarchy_i
     hdg_ctx tmp;
     hdg_ctx *ctx = &tmp;
     hdg_status st = guard(ctx, [&] {
+        if (desc->dim == 3) {
+            REQUIRE(k >= 0 && k <= MAX_K3, "3D: k out of range 0..3");
+            build_host_hierarchy_3d(ctx, desc);
+            if (info) {
+                const HostLevel3 &F = ctx->H3[ctx->n_levels - 1];
+                info->n_levels = ctx->n_levels;
+                info->n_interior_facets = F.n_int;
+                info->n_dof = (int64_t)F.n_int * dpf3(k);
+                info->n_patches = F.n_patches;
+                info->n_colours = F.n_colours;
+                info->max_patch_facets = F.pf_max;
+                info->max_patch_cells = F.pc_max;
+            }
+            return;
+        }
         REQUIRE(k >= 0 && k <= 4, "k out of range 0..4");
         build_host_hierarchy(ctx, desc);
         if (info) {
@@ -1496,6 +1537,22 @@ hdg_status hdg_get_sizes(const hdg_ctx *cctx, hdg_sizes *out) {
     std::memset(out, 0, sizeof(*out));
     const hdg_ctx *ctx = cctx;
     if (ctx->n_levels < 1) return HDG_ERR_STATE;
+    if (ctx->dim == 3) {
+        const HostLevel3 &H = ctx->H3[ctx->n_levels - 1];
+        const int k = ctx->prm.k;
+        out->k = ctx->condensed ? k : -1;
+        out->n_levels = ctx->n_levels;
+        out->n_cells = H.nc;
+        out->n_interior_facets = H.n_int;
+        out->n_dof = ctx->condensed ? ctx->n_dof : 0;
+        for (int l = 0; l < ctx->n_levels; ++l) {
+            out->n_dof_level[l] = 3 * ctx->H3[l].n_int;
+            out->n_colours_level[l] = ctx->H3[l].n_colours;
+        }
+        out->n_lat = ctx->condensed ? (k + 2) * (k + 3) * (k + 4) / 6 : 0;
+        out->n_boundary_facets = H.nf - H.n_int;
+        return HDG_OK;
+    }
     const HostLevel &H = ctx->H[ctx->n_levels - 1];
     out->k = ctx->condensed ? ctx->prm.k : -1;
     out->n_levels = ctx->n_levels;
@@ -1514,6 +1571,7 @@ hdg_status hdg_get_sizes(const hdg_ctx *cctx, hdg_sizes *out) {
 hdg_status hdg_boundary_facets(const hdg_ctx *ctx, int32_t *pairs) {
     if (!ctx || !pairs) return HDG_ERR_INVALID_ARG;
     if (ctx->n_levels < 1) return HDG_ERR_STATE;
+    if (ctx->dim != 2) return HDG_ERR_UNSUPPORTED;
     const HostLevel &H = ctx->H[ctx->n_levels - 1];
     int64_t b = 0;
     for (int64_t F = 0; F < H.nf; ++F)
@@ -1643,11 +1701,206 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
     ctx->condensed = true;
 }
 
+// ===================================================================== 3D (tetrahedra)
+// The 3D path shares the context, the device levels, the Krylov and Uzawa drivers and the
+// multigrid recursion with 2D; these functions build its host topology, upload it and
+// condense its operators (condense3d.cu, topology3d.cpp, reference3d.cpp).
+
+static void build_host_hierarchy_3d(hdg_ctx *ctx, const hdg_mesh_desc *desc) {
+    REQUIRE(desc->n_levels >= 1 && desc->n_levels <= MAX_LEVELS, "n_levels out of range 1..16");
+    REQUIRE(desc->n_vertices && desc->n_cells && desc->coords && desc->cells, "null mesh arrays");
+    const int nl = desc->n_levels;
+    ctx->dim = 3;
+    ctx->n_levels = nl;
+    ctx->H3.assign(nl, HostLevel3());
+    ctx->T3.assign(nl, HostTransfer3());
+    for (int l = 0; l < nl; ++l) {
+        HostLevel3 &H = ctx->H3[l];
+        H.nv = desc->n_vertices[l];
+        H.nc = desc->n_cells[l];
+        REQUIRE(H.nv >= 4 && H.nc >= 1 && H.nc < (1LL << 26), "level sizes out of range");
+        REQUIRE(desc->coords[l] && desc->cells[l], "null level array");
+        H.coords.assign(desc->coords[l], desc->coords[l] + 3 * H.nv);
+        H.cells.assign(desc->cells[l], desc->cells[l] + 4 * H.nc);
+        std::string e = build_level_topology_3d(H);
+        REQUIRE(e.empty(), "level " + std::to_string(l) + ": " + e);
+        if (l > 0) {
+            REQUIRE(desc->parent && desc->parent[l], "parent map required on levels >= 1");
+            H.parent.assign(desc->parent[l], desc->parent[l] + H.nc);
+            std::string e2 = build_transfer_3d(ctx->H3[l - 1], H, ctx->T3[l]);
+            REQUIRE(e2.empty(), "level " + std::to_string(l) + ": " + e2);
+        }
+    }
+}
+
+static void upload_levels_3d(hdg_ctx *ctx) {
+    for (int l = 0; l < ctx->n_levels; ++l) {
+        HostLevel3 &H = ctx->H3[l];
+        DevLevel &L = ctx->L[l];
+        L.dim = 3;
+        L.nv = H.nv;
+        L.nc = H.nc;
+        L.n_int = H.n_int;
+        upload(ctx, L.coords, H.coords);
+        upload(ctx, L.cells, H.cells);
+        std::vector<int32_t> ci(4 * H.nc), fa(2 * H.n_int);
+        for (int64_t c = 0; c < 4 * H.nc; ++c) ci[c] = H.interior_index[H.cell_face[c]];
+        for (int64_t i = 0; i < H.n_int; ++i) {
+            const int F = H.interior_faces[i];
+            for (int q = 0; q < 2; ++q) fa[2 * i + q] = (H.face_cells[2 * F + q] << 2) | H.face_lf[2 * F + q];
+        }
+        upload(ctx, L.cell_int, ci);
+        upload(ctx, L.facet_adj, fa);
+        L.n_bnd = H.nf - H.n_int;
+        dalloc(ctx, L.cell_d, 4 * H.nc);
+        dalloc(ctx, L.cell_area, H.nc);
+        L.n_patches = H.n_patches;
+        L.n_colours = H.n_colours;
+        L.pf_max = H.pf_max;
+        L.pc_max = H.pc_max;
+        L.colour_ptr = H.colour_ptr;
+        upload(ctx, L.patch_nf, H.patch_nf);
+        upload(ctx, L.patch_facets, H.patch_facets);
+        upload(ctx, L.patch_nc, H.patch_nc);
+        upload(ctx, L.patch_cells, H.patch_cells);
+        upload(ctx, L.patch_slot_src, H.patch_slot_src);
+        if (l > 0) {
+            HostTransfer3 &T = ctx->T3[l];
+            L.nc_coarse = T.nc_coarse;
+            L.nB = T.nB;
+            upload(ctx, L.tr_slots, T.slots);
+            upload(ctx, L.tr_nbr, T.nbr);
+            upload(ctx, L.tr_children, T.children);
+            upload(ctx, L.tr_child_slot, T.child_slot);
+            upload(ctx, L.tr_fineB, T.fineB);
+            upload(ctx, L.tr_fineB_src, T.fineB_src);
+            upload(ctx, L.tr_W, T.W);
+            std::vector<float> Wf(T.W.begin(), T.W.end());
+            upload(ctx, L.tr_Wf, Wf);
+            const size_t nh = (size_t)3 * TR3_T * 3 * TR3_B * T.nc_coarse;
+            dalloc(ctx, L.tr_H, nh);
+            dalloc(ctx, L.tr_Hf, nh);
+            dalloc(ctx, L.ct1, 3 * TR3_B * T.nc_coarse);
+            dalloc(ctx, L.ct2, 12 * T.nc_coarse);
+            dalloc(ctx, L.ct1f, 3 * TR3_B * T.nc_coarse);
+            dalloc(ctx, L.ct2f, 12 * T.nc_coarse);
+        }
+        const int64_t n0 = std::max<int64_t>(3 * H.n_int, 1);
+        dalloc(ctx, L.g, n0); dalloc(ctx, L.u, n0); dalloc(ctx, L.r, n0); dalloc(ctx, L.t, n0);
+        dalloc(ctx, L.gf, n0); dalloc(ctx, L.uf, n0); dalloc(ctx, L.rf, n0); dalloc(ctx, L.tf, n0);
+    }
+}
+
+static void upload_ref3(hdg_ctx *ctx, RefTables3 &t, DBuf<double> &d, int k) {
+    if (t.k == k && d.p) return;
+    build_reference_tables_3d(k, t);
+    dfree(d);
+    upload(ctx, d, pack_reference_tables_3d(t));
+}
+
+static int condense3_blocks(hdg_ctx *ctx) {
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    return 2 * std::max(sms, 1);
+}
+
+static void condense_all_3d(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
+    const hdg_params *prm = &ctx->prm;
+    ctx->condensed = false;
+    drop_graph(ctx);
+    const int k = prm->k;
+    upload_ref3(ctx, ctx->ref30, ctx->ref30_dev, 0);
+    upload_ref3(ctx, ctx->ref3k, ctx->ref3k_dev, k);
+    CK(cudaMemsetAsync(ctx->status_flag.p, 0, sizeof(int), s));
+    const int nl = ctx->n_levels, blocks = condense3_blocks(ctx);
+    {
+        // one workspace for the condensation and the patch inverses, sized before any launch
+        size_t need = condense3_scratch_doubles(k, blocks);
+        for (int l = 0; l < nl; ++l) {
+            const int npm = ctx->L[l].pf_max * (l == nl - 1 ? dpf3(k) : 3);
+            need = std::max(need, (size_t)std::min(std::max(ctx->L[l].n_patches, 1), blocks) * npm * npm);
+        }
+        dalloc(ctx, ctx->c3_scratch, need);
+    }
+    int *flag = ctx->status_flag.p;
+    for (int l = 0; l < nl; ++l) {
+        DevLevel &L = ctx->L[l];
+        DevOperator &op = L.op0;
+        op.k = 0; op.dpf = 3; op.nloc = 12; op.np_max = L.pf_max * 3;
+        dalloc(ctx, op.A, 144 * L.nc);
+        dalloc(ctx, op.Af, 144 * L.nc);
+        dalloc(ctx, op.Pinv, (size_t)L.n_patches * op.np_max * op.np_max);
+        dalloc(ctx, op.Pinvf, (size_t)L.n_patches * op.np_max * op.np_max);
+        CK(launch_condense3(0, L, ctx->ref30_dev.p, ctx->ref30, prm->nu, nullptr, prm->beta, prm->gamma, nullptr,
+                            op.A.p, op.Af.p, nullptr, ctx->c3_scratch.p, blocks, flag, s));
+        CK(launch_patch_inverse3(L, op, ctx->c3_scratch.p, blocks, flag, s));
+    }
+    DevLevel &LJ = ctx->L[nl - 1];
+    DevOperator &op = ctx->opk;
+    op.k = k; op.dpf = dpf3(k); op.nloc = 4 * op.dpf; op.np_max = LJ.pf_max * op.dpf;
+    op.alo_valid = false;
+    dalloc(ctx, op.A, (size_t)op.nloc * op.nloc * LJ.nc);
+    dalloc(ctx, op.Af, (size_t)op.nloc * op.nloc * LJ.nc);
+    dalloc(ctx, op.Fel, (size_t)op.nloc * LJ.nc);
+    dalloc(ctx, op.Pinv, (size_t)LJ.n_patches * op.np_max * op.np_max);
+    dalloc(ctx, op.Pinvf, (size_t)LJ.n_patches * op.np_max * op.np_max);
+    CK(launch_condense3(k, LJ, ctx->ref3k_dev.p, ctx->ref3k, prm->nu, nullptr, prm->beta, prm->gamma, forcing, op.A.p,
+                        op.Af.p, op.Fel.p, ctx->c3_scratch.p, blocks, flag, s));
+    CK(launch_patch_inverse3(LJ, op, ctx->c3_scratch.p, blocks, flag, s));
+    op.tma_flag = nullptr;
+    dfree(op.Pinvp);
+    op.h_fmt = 0;
+    for (int l = 1; l < nl; ++l) CK(launch_transfer_H3(ctx->L[l], flag, s));
+    ctx->n0 = 3 * ctx->L[0].n_int;
+    dalloc(ctx, ctx->coarse_inv, std::max<int64_t>(ctx->n0 * ctx->n0, 1));
+    CK(launch_coarse_inverse(ctx->L[0], ctx->coarse_inv.p, ctx->n0, flag, s));
+    ctx->small_Ls = -1;
+    ctx->n_dof = LJ.n_int * op.dpf;
+    const int64_t nd = std::max<int64_t>(ctx->n_dof, 1);
+    dalloc(ctx, ctx->kr, nd); dalloc(ctx, ctx->ku, nd); dalloc(ctx, ctx->kt, nd);
+    dalloc(ctx, ctx->krf, nd); dalloc(ctx, ctx->kuf, nd); dalloc(ctx, ctx->kgf, nd);
+    check_flag(ctx, s);
+    ctx->condensed = true;
+}
+
+static void condense_3d(hdg_ctx *ctx, const hdg_params *prm, const double *forcing, double *rhs_out,
+                        cudaStream_t s) {
+    REQUIRE(prm->k >= 0 && prm->k <= MAX_K3, "3D: k out of range 0..3");
+    REQUIRE(prm->nu > 0 && std::isfinite(prm->nu), "nu must be positive");
+    REQUIRE(prm->beta >= 0 && std::isfinite(prm->beta), "beta must be >= 0");
+    REQUIRE(prm->gamma >= 0 && std::isfinite(prm->gamma), "gamma must be >= 0");
+    REQUIRE(prm->m_p >= 1 && prm->m_h >= 1, "m_p, m_h must be >= 1");
+    REQUIRE(prm->cycle == 1 || prm->cycle == 2, "cycle must be 1 (V) or 2 (W)");
+    REQUIRE(prm->vcycle_growth >= 1 && prm->vcycle_growth <= 4, "vcycle_growth out of range 1..4");
+    REQUIRE(prm->hp_additive == 0 || prm->hp_additive == 1, "hp_additive must be 0 or 1");
+    if (!(prm->precision == HDG_FP64 || prm->precision == HDG_MIXED_FP32) || prm->smoother != 0 ||
+        prm->fused_coarse_cells != 0 || prm->nu_elem || prm->conv || prm->newton_u || prm->dirichlet) {
+        ctx->err = "3D supports the generalized Stokes operator with a scalar viscosity, homogeneous Dirichlet "
+                   "data, block GS and the FP64 or FP32 preconditioner";
+        throw Fail{HDG_ERR_UNSUPPORTED};
+    }
+    REQUIRE(3 * ctx->L[0].n_int <= MAX_COARSE_DOFS,
+            "coarsest level has " + std::to_string(3 * ctx->L[0].n_int) +
+                " unknowns; the dense coarse solve allows at most " + std::to_string(MAX_COARSE_DOFS));
+    ctx->prm = *prm;
+    ctx->has_conv = ctx->has_newton = ctx->has_dir = false;
+    condense_all_3d(ctx, forcing, s);
+    if (rhs_out) {
+        if (forcing) CK(launch_assemble_load(ctx->L[ctx->n_levels - 1], ctx->opk, rhs_out, s));
+        else CK(cudaMemsetAsync(rhs_out, 0, sizeof(double) * ctx->n_dof, s));
+    }
+}
+
 hdg_status hdg_condense(hdg_ctx *ctx, const hdg_params *prm, const double *forcing, double *rhs_out,
                         hdg_stream_t stream) {
     if (!ctx) return HDG_ERR_INVALID_ARG;
     return guard(ctx, [&] {
         REQUIRE(prm, "null params");
+        if (ctx->dim == 3) {
+            CK(cudaSetDevice(ctx->device));
+            condense_3d(ctx, prm, forcing, rhs_out, (cudaStream_t)stream);
+            return;
+        }
         REQUIRE(prm->k >= 0 && prm->k <= MAX_K, "k out of range 0..4");
         REQUIRE(prm->nu > 0 && std::isfinite(prm->nu), "nu must be positive");
         REQUIRE(prm->beta >= 0 && std::isfinite(prm->beta), "beta must be >= 0");
@@ -1724,6 +1977,14 @@ hdg_status hdg_load(hdg_ctx *ctx, const double *forcing, double *rhs_out, hdg_st
     });
 }
 
+#define NEED_2D(what)                                                                        \
+    do {                                                                                     \
+        if (ctx->dim != 2) {                                                                 \
+            ctx->err = std::string(what) + " is available for triangular meshes (dim = 2) only"; \
+            throw Fail{HDG_ERR_UNSUPPORTED};                                                 \
+        }                                                                                    \
+    } while (0)
+
 #define NEED_CONDENSED()                                                                     \
     do {                                                                                     \
         if (!ctx->condensed) {                                                               \
@@ -1744,6 +2005,7 @@ hdg_status hdg_apply(hdg_ctx *ctx, const double *x, double *y, hdg_stream_t stre
 hdg_status hdg_apply_transpose(hdg_ctx *ctx, int level, const double *x, double *y, hdg_stream_t stream) {
     if (!ctx) return HDG_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        NEED_2D("hdg_apply_transpose");
         NEED_CONDENSED();
         REQUIRE(level >= -1 && level < ctx->n_levels, "level out of range");
         REQUIRE(x && y && x != y, "x, y must be distinct non-null device pointers");
@@ -1849,7 +2111,7 @@ hdg_status hdg_mg_h(hdg_ctx *ctx, const double *g, double *u, hdg_stream_t strea
         cudaStream_t s = (cudaStream_t)stream;
         const int J = ctx->n_levels - 1;
         DevLevel &L = ctx->L[J];
-        const int64_t n = 2 * L.n_int;
+        const int64_t n = L.dim * L.n_int;
         if (ctx->prm.precision == HDG_FP64) {
             CK(cudaMemcpyAsync(L.g.p, g, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
             mg_h<double>(ctx, J, ctx->prm.m_h, true, s);
@@ -1896,6 +2158,7 @@ hdg_status hdg_recover(hdg_ctx *ctx, const double *u, const double *forcing, dou
                        hdg_stream_t stream) {
     if (!ctx) return HDG_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        NEED_2D("hdg_recover");
         NEED_CONDENSED();
         REQUIRE(u, "null skeleton vector");
         cudaStream_t s = (cudaStream_t)stream;
@@ -1913,6 +2176,7 @@ hdg_status hdg_postprocess(hdg_ctx *ctx, const double *u, const double *forcing,
                            hdg_stream_t stream) {
     if (!ctx) return HDG_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        NEED_2D("hdg_postprocess");
         NEED_CONDENSED();
         REQUIRE(u && ustar_out, "null skeleton vector or output");
         cudaStream_t s = (cudaStream_t)stream;
@@ -1946,6 +2210,7 @@ hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, con
     hdg_solve_info loc{};
     hdg_status conv = HDG_OK;
     hdg_status st = guard(ctx, [&] {
+        NEED_2D("hdg_adjoint");
         NEED_CONDENSED();
         REQUIRE(forcing && u && u_target, "null input");
         if (ctx->has_dir) {
@@ -2020,6 +2285,7 @@ hdg_status hdg_adjoint(hdg_ctx *ctx, const double *forcing, const double *u, con
 hdg_status hdg_apply_multi(hdg_ctx *ctx, int nrhs, const double *x, double *y, hdg_stream_t stream) {
     if (!ctx) return HDG_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        NEED_2D("hdg_apply_multi");
         NEED_CONDENSED();
         REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, "nrhs out of range 1..64");
         REQUIRE(x && y, "null vector");
@@ -2038,6 +2304,7 @@ hdg_status hdg_apply_multi(hdg_ctx *ctx, int nrhs, const double *x, double *y, h
 hdg_status hdg_precond_apply_multi(hdg_ctx *ctx, int nrhs, const double *r, double *z, hdg_stream_t stream) {
     if (!ctx) return HDG_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        NEED_2D("hdg_precond_apply_multi");
         NEED_CONDENSED();
         REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, "nrhs out of range 1..64");
         REQUIRE(r && z, "null vector");
@@ -2056,6 +2323,7 @@ hdg_status hdg_smooth_multi(hdg_ctx *ctx, int level, int nrhs, const double *g, 
                             int reverse, hdg_stream_t stream) {
     if (!ctx) return HDG_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        NEED_2D("hdg_smooth_multi");
         NEED_CONDENSED();
         REQUIRE(level >= -1 && level < ctx->n_levels, "level out of range");
         REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, "nrhs out of range 1..64");
@@ -2105,6 +2373,7 @@ hdg_status hdg_tune_batched(hdg_ctx *ctx, int nrhs, int *rows_per_thread, int *t
                             hdg_stream_t stream) {
     if (!ctx) return HDG_ERR_INVALID_ARG;
     return guard(ctx, [&] {
+        NEED_2D("hdg_tune_batched");
         NEED_CONDENSED();
         REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, "nrhs out of range 1..64");
         cudaStream_t s = (cudaStream_t)stream;
@@ -2135,6 +2404,7 @@ hdg_status hdg_solve_multi(hdg_ctx *ctx, int nrhs, const double *F, double *u, d
     std::vector<hdg_solve_info> loc;
     hdg_status conv = HDG_OK;
     hdg_status st = guard(ctx, [&] {
+        NEED_2D("hdg_solve_multi");
         NEED_CONDENSED();
         REQUIRE(nrhs >= 1 && nrhs <= MAX_NRHS, "nrhs out of range 1..64");
         REQUIRE(F && u && p, "null vector");
@@ -2225,6 +2495,7 @@ hdg_status hdg_picard(hdg_ctx *ctx, const hdg_params *params, const double *forc
     int steps = 0;
     double dist = 0.0;
     hdg_status st = guard(ctx, [&] {
+        NEED_2D("hdg_picard");
         REQUIRE(params && forcing && u && p, "null argument");
         if (params->dirichlet) {
             ctx->err = "hdg_picard takes homogeneous Dirichlet data only";
@@ -2302,6 +2573,7 @@ hdg_status hdg_newton(hdg_ctx *ctx, const hdg_params *params, const double *forc
     int steps = 0;
     double dist = 0.0;
     hdg_status st = guard(ctx, [&] {
+        NEED_2D("hdg_newton");
         NEED_CONDENSED();
         REQUIRE(params && forcing && u && p, "null argument");
         if (params->dirichlet || ctx->has_dir) {

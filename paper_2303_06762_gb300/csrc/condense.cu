@@ -40,7 +40,7 @@
 #include <cmath>
 #include <cstdio>
 
-#include "hdg_internal.h"
+#include "hdg3d_internal.h"
 
 namespace hdg {
 namespace {
@@ -913,23 +913,25 @@ __global__ void transfer_H_kernel(int64_t ncc, const int *__restrict__ children,
 }
 
 // ------------------------------------------------------------------ coarse dense inverse
-__global__ void coarse_assemble_kernel(int64_t n_int, const int *__restrict__ facet_adj,
+__global__ void coarse_assemble_kernel(int64_t n_int, int dim, const int *__restrict__ facet_adj,
                                        const int *__restrict__ cell_int, const double *__restrict__ A0,
                                        double *__restrict__ M, int64_t n) {
     int64_t row = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (row >= n) return;
-    int64_t i = row / 2;
-    int d = row % 2;
+    // lowest order: dim unknowns per facet, dim+1 facets per cell, element matrices nloc x nloc
+    const int nfc = dim + 1, nloc = nfc * dim;
+    int64_t i = row / dim;
+    int d = row % dim;
     double *Mr = M + row * n;
     for (int64_t j = 0; j < n; ++j) Mr[j] = 0.0;
     for (int q = 0; q < 2; ++q) {
         int adj = facet_adj[2 * i + q];
         if (adj < 0) continue;
         int c = adj >> 2, lf = adj & 3;
-        for (int col = 0; col < 6; ++col) {
-            int jf = cell_int[3 * c + col / 2];
+        for (int col = 0; col < nloc; ++col) {
+            int jf = cell_int[nfc * c + col / dim];
             if (jf < 0) continue;
-            Mr[2 * jf + col % 2] += A0[(size_t)c * 36 + lf * 12 + col * 2 + d];
+            Mr[dim * jf + col % dim] += A0[(size_t)c * nloc * nloc + lf * nloc * dim + col * dim + d];
         }
     }
 }
@@ -979,7 +981,7 @@ __global__ void cell_geometry_kernel(int64_t nc, const double *coords, const int
     cell_area[c] = geo[G_AREA];
 }
 
-__global__ void assemble_load_kernel(int64_t n_int, int dpf, const int *__restrict__ facet_adj,
+__global__ void assemble_load_kernel(int64_t n_int, int dpf, int nfc, const int *__restrict__ facet_adj,
                                      const double *__restrict__ Fel, double *__restrict__ F) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n_int * dpf) return;
@@ -990,7 +992,7 @@ __global__ void assemble_load_kernel(int64_t n_int, int dpf, const int *__restri
         int adj = facet_adj[2 * i + q];
         if (adj < 0) continue;
         int c = adj >> 2, lf = adj & 3;
-        s += Fel[(size_t)c * 3 * dpf + lf * dpf + d];
+        s += Fel[(size_t)c * nfc * dpf + lf * dpf + d];
     }
     F[idx] = s;
 }
@@ -1242,7 +1244,7 @@ cudaError_t launch_coarse_inverse(const DevLevel &L0, double *inv, int64_t n, in
                                   cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     note_launches(1);
-    coarse_assemble_kernel<<<blocks_for(n, 128), 128, 0, s>>>(L0.n_int, L0.facet_adj.p, L0.cell_int.p,
+    coarse_assemble_kernel<<<blocks_for(n, 128), 128, 0, s>>>(L0.n_int, L0.dim, L0.facet_adj.p, L0.cell_int.p,
                                                               L0.op0.A.p, inv, n);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1273,7 +1275,7 @@ cudaError_t launch_assemble_load(const DevLevel &L, const DevOperator &op, doubl
     int64_t n = L.n_int * op.dpf;
     if (n == 0) return cudaSuccess;
     note_launches(1);
-    assemble_load_kernel<<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, op.dpf, L.facet_adj.p, op.Fel.p, F);
+    assemble_load_kernel<<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, op.dpf, L.dim + 1, L.facet_adj.p, op.Fel.p, F);
     return cudaGetLastError();
 }
 

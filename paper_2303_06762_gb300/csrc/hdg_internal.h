@@ -165,7 +165,60 @@ struct DevOperator {
     DBuf<float> Pinvh_s; // n_patches*np_max, scale of row i of the inverse of patch p at p*np_max + i
 };
 
+// ---------------------------------------------------------------- 3D host data
+constexpr int MAX_K3 = 3;
+constexpr int TR3_B = 16;      // fine faces on the faces of a coarse cell (4 per coarse face)
+constexpr int TR3_T = 8;       // fine faces inside a coarse cell
+constexpr int TR3_SLOTS = TR3_B + TR3_T;
+
+inline int dpf3(int k) { return 3 * (k + 1) * (k + 2) / 2; }
+inline int nface3(int k) { return (k + 1) * (k + 2) / 2; }
+// skeleton unknowns per facet of an order-k space in dimension dim
+inline int dpf_of(int dim, int k) { return dim == 3 ? dpf3(k) : 2 * (k + 1); }
+
+struct HostLevel3 {
+    int64_t nv = 0, nc = 0;
+    std::vector<double> coords;          // nv*3
+    std::vector<int32_t> cells;          // nc*4
+    std::vector<int32_t> parent;         // nc (level > 0)
+    int64_t nf = 0, n_int = 0;
+    std::vector<int32_t> face_v;         // nf*3 sorted vertex triple
+    std::vector<int32_t> cell_face;      // nc*4 face opposite local vertex f
+    std::vector<int32_t> face_cells;     // nf*2 (second = -1 on the boundary)
+    std::vector<int32_t> face_lf;        // nf*2 local face in each cell
+    std::vector<int32_t> interior_index; // nf -> interior number or -1
+    std::vector<int32_t> interior_faces; // n_int
+    int64_t ne = 0;
+    std::vector<int32_t> edge_v;         // ne*2 sorted vertex pair
+    std::vector<int32_t> colour;         // ne greedy colouring (edges of one colour share no cell)
+    // edge patches sorted by (colour, edge id); only edges with an interior face
+    int n_patches = 0, n_colours = 0, pf_max = 0, pc_max = 0;
+    std::vector<int32_t> colour_ptr, patch_nf, patch_facets, patch_nc, patch_cells, patch_slot_src;
+};
+
+// transfer data between a coarse and its red-refined fine level, stored per coarse cell P:
+//   slots[P][s]  fine interior face of slot s: s = 4 cf + i (i < 4) are the fine faces on coarse
+//                face cf (B slots), s = 16 + t the faces inside P (T slots); -1 for boundary faces
+//   nbr[P][s]    for B slots: (other coarse cell Q << 5 | its slot) or -1
+//   child_slot[P][ch][lf]  slot of local face lf of the ch-th child, -1 on the boundary
+//   W[P][s][a][j]  averaging weights (eq. avgOpt, the 1/2 of the two sides included): fine
+//                unknown a of B slot s from coarse unknown j = 3 cf + a' of P
+struct HostTransfer3 {
+    int64_t nc_coarse = 0;
+    std::vector<int32_t> slots, nbr, children, child_slot;
+    std::vector<double> W;
+    int64_t nB = 0;
+    std::vector<int32_t> fineB, fineB_src;   // per fine face on a coarse interior face: id, 2 x (P << 5 | s)
+};
+
+struct RefTables3 {
+    int k = -1, npk = 0, nrt = 0, nf = 0, nlat = 0;
+    std::vector<double> R1, R2, R3, R4, R5, R6, Q, FA;
+};
+
 struct DevLevel {
+    int dim = 2;               // 2: triangles (3 facets per cell, 2 lowest-order unknowns per facet);
+                               // 3: tetrahedra (4 faces, 3 unknowns per face, edge patches)
     int64_t nv = 0, nc = 0, n_int = 0;
     DBuf<double> coords;       // nv*2
     DBuf<int32_t> cells;       // nc*3
@@ -210,6 +263,12 @@ struct DevLevel {
 
 struct hdg_ctx {
     int device = 0;
+    int dim = 2;                             // 3: tetrahedral hierarchy (hdg3d paths)
+    std::vector<hdg::HostLevel3> H3;
+    std::vector<hdg::HostTransfer3> T3;
+    hdg::RefTables3 ref3k, ref30;
+    hdg::DBuf<double> ref3k_dev, ref30_dev;  // packed 3D reference tables (order k, order 0)
+    hdg::DBuf<double> c3_scratch;            // 3D condensation workspace
     std::string err;
     int n_levels = 0;
     std::vector<hdg::HostLevel> H;

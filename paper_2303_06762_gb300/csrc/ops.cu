@@ -34,7 +34,7 @@
 #include <atomic>
 #include <type_traits>
 
-#include "hdg_internal.h"
+#include "hdg3d_internal.h"
 
 namespace hdg {
 
@@ -808,7 +808,7 @@ __global__ void update_x_kernel(const double *__restrict__ Z, int m, int64_t ld,
 }
 
 // ---------------------------------------------------------------- Uzawa
-__global__ void uzawa_rhs_kernel(int64_t n_int, int dpf, const int *__restrict__ facet_adj,
+__global__ void uzawa_rhs_kernel(int64_t n_int, int dpf, int nfc, const int *__restrict__ facet_adj,
                                  const double *__restrict__ cell_d, const double *__restrict__ F,
                                  const double *__restrict__ p, double *__restrict__ g) {
     int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -821,13 +821,13 @@ __global__ void uzawa_rhs_kernel(int64_t n_int, int dpf, const int *__restrict__
             int adj = facet_adj[2 * i + q];
             if (adj < 0) continue;
             int c = adj >> 2, lf = adj & 3;
-            v += p[c] * cell_d[3 * c + lf];
+            v += p[c] * cell_d[nfc * c + lf];
         }
     g[idx] = v;
 }
 
 __global__ void __launch_bounds__(KRYLOV_THREADS)
-uzawa_update_kernel(int64_t nc, int dpf, const int *__restrict__ cell_int,
+uzawa_update_kernel(int64_t nc, int dpf, int nfc, const int *__restrict__ cell_int,
                     const double *__restrict__ cell_d, const double *__restrict__ area,
                     const double *__restrict__ u, double *__restrict__ p, double gamma, double nu,
                     const double *__restrict__ nu_cell, const double *__restrict__ bflux,
@@ -836,9 +836,9 @@ uzawa_update_kernel(int64_t nc, int dpf, const int *__restrict__ cell_int,
     for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < nc;
          c += (int64_t)gridDim.x * blockDim.x) {
         double du = 0.0;
-        for (int f = 0; f < 3; ++f) {
-            int j = cell_int[3 * c + f];
-            if (j >= 0) du += cell_d[3 * c + f] * u[(size_t)j * dpf];
+        for (int f = 0; f < nfc; ++f) {
+            int j = cell_int[nfc * c + f];
+            if (j >= 0) du += cell_d[nfc * c + f] * u[(size_t)j * dpf];
         }
         if (bflux) du += bflux[c];   // flux of inhomogeneous Dirichlet data
         double a = area[c];
@@ -1050,12 +1050,14 @@ cudaError_t launch_gs_colour_h(const DevLevel &L, const DevOperator &op, int col
 template <class T>
 cudaError_t launch_apply(const DevLevel &L, const DevOperator &op, const T *A, const T *x, const T *g,
                          T *y, cudaStream_t s) {
+    if (L.dim == 3) return launch_apply3<T>(L, op.dpf, A, x, g, y, s);
     return apply_dispatch<T>(L, op.dpf, A, x, g, y, s);
 }
 
 template <class T>
 cudaError_t launch_gs_colour(const DevLevel &L, const DevOperator &op, const T *A, const T *Pinv,
                              int colour, const T *g, T *u, cudaStream_t s) {
+    if (L.dim == 3) return launch_gs_colour3<T>(L, op, A, Pinv, colour, g, u, s);
     switch (op.dpf) {
     case 2: return gs_launch<T, 2>(L, op, A, Pinv, colour, g, u, s);
     case 4: return gs_launch<T, 4>(L, op, A, Pinv, colour, g, u, s);
@@ -1069,6 +1071,7 @@ cudaError_t launch_gs_colour(const DevLevel &L, const DevOperator &op, const T *
 template <class T>
 cudaError_t launch_prolong_add(const DevLevel &F, const DevLevel &C, const T *W, const T *Hm, const T *uc,
                                T *tmp, T *uf, cudaStream_t s) {
+    if (F.dim == 3) return launch_prolong_add3<T>(F, C, W, Hm, uc, tmp, uf, s);
     if (F.nB > 0) {
         note_launches(1);
         prolong_B_kernel<T><<<blocks_for(F.nB, 128), 128, 0, s>>>(F.nB, F.tr_fineB.p, F.tr_fineB_src.p,
@@ -1085,6 +1088,7 @@ cudaError_t launch_prolong_add(const DevLevel &F, const DevLevel &C, const T *W,
 template <class T>
 cudaError_t launch_restrict(const DevLevel &F, const DevLevel &C, const T *W, const T *Hm, const T *rf,
                             T *t1, T *t2, T *rc, cudaStream_t s) {
+    if (F.dim == 3) return launch_restrict3<T>(F, C, W, Hm, rf, t1, t2, rc, s);
     if (F.nc_coarse > 0) {
         note_launches(1);
         restrict_T_kernel<T><<<blocks_for(F.nc_coarse, 128), 128, 0, s>>>(F.nc_coarse, F.tr_slots.p, Hm,
@@ -1232,11 +1236,12 @@ cudaError_t launch_solve_update(double *small, int m, int restart, const double 
 }
 cudaError_t launch_uzawa_rhs(const DevLevel &L, int k, const double *F, const double *p, double *g,
                              cudaStream_t s) {
-    int dpf = 2 * (k + 1);
+    int dpf = dpf_of(L.dim, k);
     int64_t n = L.n_int * dpf;
     if (n == 0) return cudaSuccess;
     note_launches(1);
-    uzawa_rhs_kernel<<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, dpf, L.facet_adj.p, L.cell_d.p, F, p, g);
+    uzawa_rhs_kernel<<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, dpf, L.dim + 1, L.facet_adj.p, L.cell_d.p, F, p,
+                                                         g);
     return cudaGetLastError();
 }
 __global__ void __launch_bounds__(KRYLOV_THREADS)
@@ -1256,7 +1261,8 @@ cudaError_t launch_sum(const double *x, int64_t n, double *partials, cudaStream_
 cudaError_t launch_uzawa_update(const DevLevel &L, int k, const double *u, double *p, double gamma, double nu,
                                 const double *nu_cell, const double *bflux, double *partials, cudaStream_t s) {
     note_launches(1);
-    uzawa_update_kernel<<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(L.nc, 2 * (k + 1), L.cell_int.p, L.cell_d.p,
+    uzawa_update_kernel<<<KRYLOV_BLOCKS, KRYLOV_THREADS, 0, s>>>(L.nc, dpf_of(L.dim, k), L.dim + 1, L.cell_int.p,
+                                                                 L.cell_d.p,
                                                                  L.cell_area.p, u, p, gamma, nu, nu_cell, bflux,
                                                                  partials);
     return cudaGetLastError();

@@ -1,0 +1,174 @@
+"""GPU parity of the 3D path (tetrahedra, edge patches, Bey-refined hierarchies) against the 3D
+oracle, step by step through the C ABI: condensed element matrices and loads (all orders and the
+lowest-order levels), the operator apply, block GS over edge patches (FP64 and FP32), the
+lowest-order transfers and coarse solve, MG_h and MG_hp, and full AL-Uzawa solves with the
+same iteration counts as the oracle's and the exact discrete solution within the solver
+tolerance."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from workloads.mesh3d import unit_cube_hierarchy
+from workloads.manufactured import curl_bubble_3d, forcing_at_lattice
+from oracle.topology3d import build_topology_3d, edge_patches
+from oracle.hdg3d import HDG3D
+from oracle.mg import BlockGS, harmonic_prolongation
+from oracle.mg3d import averaging_prolongation_3d, interior_fine_dofs_3d, build_hpmg_3d
+from oracle.krylov import uzawa
+from _util import rel, relnorm, parity_opts
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+MESHES = [dict(), dict(shuffle_seed=7), dict(jitter=0.2, seed=3, shuffle_seed=5)]
+
+
+def _hdg():
+    import paper_2303_06762_gb300 as hdg
+    return hdg
+
+
+def dev(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def setup3(n0, nl, k, nu=1.0, beta=1.0, gamma=100.0, precision=0, **meshkw):
+    hdg = _hdg()
+    ms = unit_cube_hierarchy(n0, nl, **meshkw)
+    ts = [build_topology_3d(m.coords, m.cells) for m in ms]
+    ps = [m.parent for m in ms]
+    fv = forcing_at_lattice(ms[-1].coords, ms[-1].cells, k, curl_bubble_3d().forcing(nu, beta))
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    F = hdg.hdg_condense(ctx, hdg.Params(k=k, nu=nu, beta=beta, gamma=gamma, precision=precision), dev(fv))
+    return ms, ts, ps, fv, ctx, F
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+@pytest.mark.parametrize("mesh", range(len(MESHES)))
+def test_element_matrices_and_load(k, mesh):
+    hdg = _hdg()
+    nu, beta, gamma = 1.3, 0.7, 50.0
+    ms, ts, ps, fv, ctx, F = setup3(1, 2, k, nu=nu, beta=beta, gamma=gamma, **MESHES[mesh])
+    oh = HDG3D(ts[-1], k, nu=nu, beta=beta, gamma=gamma)
+    A = host(hdg.hdg_get_element_matrices(ctx, -1))
+    Ao = np.stack([oh.element_matrix(c) for c in range(ts[-1].n_cells)])
+    print(f"3D k={k} mesh={mesh}: element matrices rel {rel(A, Ao):.2e}, load rel {rel(host(F), oh.load(fv)):.2e}")
+    assert rel(A, Ao) < 1e-11
+    assert rel(host(F), oh.load(fv)) < 1e-11
+    for l in range(len(ts)):
+        A0 = host(hdg.hdg_get_element_matrices(ctx, l))
+        o0 = HDG3D(ts[l], 0, nu=nu, beta=beta, gamma=gamma)
+        assert rel(A0, np.stack([o0.element_matrix(c) for c in range(ts[l].n_cells)])) < 1e-12
+    # a second load with the same operator
+    fv2 = np.random.default_rng(3).standard_normal(fv.shape)
+    assert rel(host(hdg.hdg_load(ctx, dev(fv2))), oh.load(fv2)) < 1e-11
+
+
+@pytest.mark.parametrize("k", [0, 2, 3])
+def test_apply(k):
+    hdg = _hdg()
+    ms, ts, ps, fv, ctx, F = setup3(1, 3, k, shuffle_seed=3)
+    oh = HDG3D(ts[-1], k, gamma=100.0, beta=1.0)
+    x = np.random.default_rng(1).standard_normal(oh.n_dof)
+    # k = 3: the element matrices themselves agree to about 4e-12 (the reference tables hold
+    # degree-8 products in monomial coefficients)
+    assert rel(host(hdg.hdg_apply(ctx, dev(x))), oh.matrix() @ x) < (1e-13 if k <= 2 else 1e-11)
+    for l in range(3):
+        o0 = HDG3D(ts[l], 0, gamma=100.0, beta=1.0)
+        x0 = np.random.default_rng(l).standard_normal(o0.n_dof)
+        assert rel(host(hdg.hdg_level_apply(ctx, l, dev(x0))), o0.matrix() @ x0) < 1e-13
+
+
+@pytest.mark.parametrize("level", [-1, 1, 2])
+@pytest.mark.parametrize("precision", [0, 1])
+def test_block_gs_sweep_edge_patches(level, precision):
+    hdg = _hdg()
+    k = 2
+    ms, ts, ps, fv, ctx, F = setup3(1, 3, k, precision=precision, jitter=0.2, seed=1)
+    t = ts[-1] if level < 0 else ts[level]
+    oh = HDG3D(t, k if level < 0 else 0, gamma=100.0, beta=1.0)
+    gs = BlockGS(oh.matrix(), edge_patches(t, oh.dpf))
+    rng = np.random.default_rng(2)
+    for reverse in (False, True):
+        g, u0 = rng.standard_normal((2, oh.n_dof))
+        uo = (gs.backward if reverse else gs.forward)(g, u0.copy())
+        ud = dev(u0)
+        hdg.hdg_smooth(ctx, level, dev(g), ud, 1, reverse)
+        # FP32: edge patches of up to 108 unknowns (measured 2.1e-5)
+        assert rel(host(ud), uo) < (1e-11 if precision == 0 else 5e-5)
+
+
+def test_transfers_and_coarse_solve():
+    hdg = _hdg()
+    ms, ts, ps, fv, ctx, F = setup3(1, 3, 1, jitter=0.25, seed=2, shuffle_seed=1)
+    for l in (1, 2):
+        Af = HDG3D(ts[l], 0, gamma=100.0, beta=1.0).matrix()
+        P = harmonic_prolongation(Af, averaging_prolongation_3d(ts[l - 1], ts[l], ps[l]),
+                                  interior_fine_dofs_3d(ts[l], ps[l]))
+        rng = np.random.default_rng(l)
+        uc = rng.standard_normal(P.shape[1])
+        uf0 = rng.standard_normal(P.shape[0])
+        ufd = dev(uf0)
+        hdg.hdg_prolong_add(ctx, l, dev(uc), ufd)
+        assert rel(host(ufd) - uf0, P @ uc) < 1e-12
+        rf = rng.standard_normal(P.shape[0])
+        assert rel(host(hdg.hdg_restrict(ctx, l, dev(rf))), P.T @ rf) < 1e-12
+    A0 = HDG3D(ts[0], 0, gamma=100.0, beta=1.0).matrix().toarray()
+    g = np.random.default_rng(9).standard_normal(A0.shape[0])
+    assert rel(host(hdg.hdg_coarse_solve(ctx, dev(g))), np.linalg.solve(A0, g)) < 1e-11
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mg_h_and_mg_hp(precision):
+    hdg = _hdg()
+    k = 2
+    ms, ts, ps, fv, ctx, F = setup3(1, 3, k, precision=precision, shuffle_seed=11)
+    M = build_hpmg_3d(ts, ps, k, 1.0, 1.0, 100.0)
+    rng = np.random.default_rng(4)
+    g0 = rng.standard_normal(3 * ts[-1].n_interior)
+    tol = 1e-10 if precision == 0 else 1e-4
+    assert rel(host(hdg.hdg_mg_h(ctx, dev(g0))), M.mgh(g0, 1, 1)) < tol
+    r = rng.standard_normal(M.A.shape[0])
+    assert rel(host(hdg.hdg_precond_apply(ctx, dev(r))), M(r)) < tol
+
+
+@pytest.mark.parametrize("k,mesh", [(1, 0), (2, 2), (3, 1), (0, 0)])
+def test_solve_matches_oracle(k, mesh):
+    hdg = _hdg()
+    gamma = 100.0
+    ms, ts, ps, fv, ctx, F = setup3(1, 3, k, gamma=gamma, **MESHES[mesh])
+    oh = HDG3D(ts[-1], k, gamma=gamma, beta=1.0)
+    M = build_hpmg_3d(ts, ps, k, 1.0, 1.0, gamma, hdg_k=oh)
+    Fo = oh.load(fv)
+    ro = uzawa(M.A, oh.flux_matrix(), oh.area, oh.eps_inv, Fo, M)
+    u, p, info = hdg.hdg_solve(ctx, F)
+    assert info["krylov_its"] == ro.krylov_its
+    eu, ep = relnorm(host(u), ro.u), relnorm(host(p), ro.p)
+    print(f"3D k={k}: its {info['krylov_its']}; vs oracle iteration |du| {eu:.2e} |dp| {ep:.2e}")
+    assert eu < 1e-10 and ep < 1e-10
+    # against the exact discrete solution: the velocity to round-off; the pressure to the
+    # round-off level of the AL iteration in 3D (Remark 3.1: eps^-1 div multiplies the last
+    # digits of u; the oracle's own iteration with tighter tolerances stays at 1.4e-10 / 7.9e-10
+    # / 1.9e-9 from the direct solve for k = 1 / 2 / 3 on this mesh)
+    ud, pd = oh.solve_direct(Fo)
+    u, p, info = hdg.hdg_solve(ctx, F, opts=parity_opts(hdg, gamma))
+    eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
+    print(f"3D k={k}: vs direct |du| {eu:.2e} |dp| {ep:.2e}, div {info['div_l2']:.2e}")
+    assert eu < 1e-10 and ep < 5e-9 and info["div_l2"] < 1e-10
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_mixed_precision_solve(k):
+    hdg = _hdg()
+    ms, ts, ps, fv, ctx, F = setup3(1, 3, k, precision=hdg.HDG_MIXED_FP32, jitter=0.15, seed=4)
+    oh = HDG3D(ts[-1], k, gamma=100.0, beta=1.0)
+    ud, pd = oh.solve_direct(oh.load(fv))
+    u, p, info = hdg.hdg_solve(ctx, F)
+    eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
+    print(f"3D mixed k={k}: its {info['krylov_its']} |du| {eu:.2e} |dp| {ep:.2e}")
+    assert eu < 1e-8 and ep < 1e-8
