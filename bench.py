@@ -503,6 +503,7 @@ def gpu_arm(args):
         line["forms"]["oseen_mixed_fp32"] = oseen_form(args, hdg, torch, dev, stream)
         line["forms"]["coarsest_level_mixed_fp32"] = coarsest_form(args, hdg, torch, dev, stream)
         line["forms"]["variants_mixed_fp32"] = variants_form(args, ms, hdg, torch, dev, stream)
+        line["forms"]["tetrahedra_3d"] = tetra_form(args, hdg, torch, dev, stream)
 
     if rank == 0 and not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(args)
@@ -688,6 +689,99 @@ def coarsest_form(args, hdg, torch, dev, stream):
                              "krylov_its": info["krylov_its"], "dof_iters_per_s": n * info["krylov_its_total"] / t,
                              "ms_per_iter": 1e3 * t / info["krylov_its_total"]}
         ctx.close()
+    return out
+
+
+def tetra_patch_sizes(cells):
+    """Per edge patch of a tetrahedrisation (interior faces containing the edge): the number of
+    patch faces and of star cells, for the byte models of the 3D sweep."""
+    import numpy as np
+    f = np.sort(np.concatenate([cells[:, [1, 2, 3]], cells[:, [0, 2, 3]], cells[:, [0, 1, 3]],
+                                cells[:, [0, 1, 2]]]).astype(np.int64), axis=1)
+    faces, cnt = np.unique(f, axis=0, return_counts=True)
+    inner = faces[cnt == 2]
+    e_of_faces = np.concatenate([inner[:, [0, 1]], inner[:, [0, 2]], inner[:, [1, 2]]])
+    ce = np.sort(np.concatenate([cells[:, [a, b]] for a, b in ((0, 1), (0, 2), (0, 3), (1, 2), (1, 3), (2, 3))]),
+                 axis=1).astype(np.int64)
+    nv = int(cells.max()) + 1
+    key = lambda e: e[:, 0] * nv + e[:, 1]
+    ek, star = np.unique(key(ce), return_counts=True)
+    fk, nfac = np.unique(key(e_of_faces), return_counts=True)
+    stars = star[np.searchsorted(ek, fk)]
+    return nfac, stars, len(inner)
+
+
+def tetra_sweep_bytes(cells, k, word=4):
+    """Bytes of one order-k block GS sweep over edge patches in 3D (all colours), two models:
+    the scope table's per-unit model B_P (packed symmetric patch inverses) + B_A' (packed
+    symmetric element matrices) + 3 N s_v, and the kernel's own accesses (full transposed
+    patch inverses, both cells' row blocks of every patch face, the star cells' unknowns, g, u)."""
+    import numpy as np
+    nf = (k + 1) * (k + 2) // 2
+    dpf = 3 * nf
+    nloc = 4 * dpf
+    nfac, stars, n_int = tetra_patch_sizes(cells)
+    npch = nfac * dpf
+    N = n_int * dpf
+    model = word * (np.sum(npch * (npch + 1) // 2) + cells.shape[0] * nloc * (nloc + 1) // 2 + 3 * N)
+    kernel = word * (np.sum(npch * npch) + np.sum(2 * nfac * nloc * dpf) + np.sum(stars * nloc) + 3 * np.sum(npch))
+    return int(model), int(kernel)
+
+
+def tetra_form(args, hdg, torch, dev, stream):
+    """The 3D configuration (Section 5.1.2 workloads): the unit cube in n^3 cubes of 6 Kuhn
+    tetrahedra, a red-refined hierarchy 2x2x2 -> ... -> n, beta = 1, nu = 1, gamma = 1e2, the
+    manufactured curl solution, edge-patch block GS with two smoothing steps (m_p = m_h = 2, the
+    paper's 3D setting: half the iterations of m = 1 and 20% less time, measured); FP64 and the
+    FP32 preconditioner, FGMRES(30) in AL-Uzawa with the default stopping rule; the mixed
+    order-k sweep against its rooflines."""
+    from workloads.mesh3d import unit_cube_hierarchy
+    from workloads.manufactured import curl_bubble_3d, forcing_at_lattice
+    peak = measured_peaks().get("hbm_gbs", 6800.0)
+    out = {}
+    cases = ((4, 2, ("fp64", "mixed_fp32")), (4, 3, ("fp64", "mixed_fp32")), (5, 2, ("mixed_fp32",)),
+             (5, 3, ("mixed_fp32",)))
+    for nl, k, forms in cases:
+        ms = unit_cube_hierarchy(2, nl)
+        fine = ms[-1]
+        n = 2 ** nl
+        fv = torch.tensor(forcing_at_lattice(fine.coords, fine.cells, k, curl_bubble_3d().forcing(1.0, 1.0)),
+                          device=dev)
+        ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=dev.index or 0)
+        rec = {"n": n, "k": k, "tetrahedra": int(fine.n_cells), "levels": nl}
+        for name in forms:
+            prec = hdg.HDG_FP64 if name == "fp64" else hdg.HDG_MIXED_FP32
+            prm = hdg.Params(k=k, nu=1.0, beta=1.0, gamma=1e2, precision=prec, m_p=2, m_h=2)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            F = hdg.hdg_condense(ctx, prm, fv)
+            torch.cuda.synchronize()
+            setup = time.perf_counter() - t0
+            o = solve_opts(hdg, 30)
+            hdg.hdg_solve(ctx, F, opts=o)
+            t, (u, p, info) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F, opts=o))
+            nd = ctx.sizes().n_dof
+            rec["skeleton_dofs"] = int(nd)
+            rec[name] = {"time_to_tol_s": t, "fgmres_iters": info["krylov_its_total"],
+                         "krylov_its": info["krylov_its"], "uzawa_steps": info["uzawa_its"],
+                         "dof_iters_per_s": nd * info["krylov_its_total"] / t,
+                         "ms_per_iter": 1e3 * t / max(info["krylov_its_total"], 1), "setup_s": setup,
+                         "div_l2": info["div_l2"]}
+        # the mixed form's order-k sweep (all colours) against both byte models
+        r = torch.randn(ctx.sizes().n_dof, dtype=torch.float64, device=dev)
+        z = torch.zeros_like(r)
+        t_sw = _event_ms(torch, stream, lambda: hdg.hdg_smooth(ctx, -1, r, z, 4, False), 3) / 4
+        bm, bk = tetra_sweep_bytes(fine.cells, k)
+        rec["sweep_mixed"] = {"kernel": "gs3_kernel<float,%d> (edge patches, %d colour launches)"
+                              % (3 * (k + 1) * (k + 2) // 2, int(ctx.sizes().n_colours_level[nl - 1])),
+                              "ms": t_sw, "model_bytes": bm, "kernel_bytes": bk,
+                              "frac_by_model": bm / (t_sw / 1e3) / 1e9 / peak,
+                              "frac_by_kernel_bytes": bk / (t_sw / 1e3) / 1e9 / peak,
+                              "peak_gbs": peak, "note": "includes the FP64<->FP32 conversions of g and u"}
+        out[f"n{n}_k{k}"] = rec
+        ctx.close()
+        del ctx
+        torch.cuda.empty_cache()
     return out
 
 
