@@ -316,6 +316,23 @@ def dofs_per_facet(dim: int, k: int) -> int:
     return 2 * (k + 1) if dim == 2 else 3 * (k + 1) * (k + 2) // 2
 
 
+def union_slices(hierarchies: Sequence, k: int):
+    """For a hierarchy built by workloads.mesh2d.disjoint_union(hierarchies): per mesh, the slice of
+    the skeleton unknowns and the slice of the cells (pressures) on the finest level.  One solve of
+    the union is the solve of all meshes' block-diagonal system with every kernel launch (and the
+    preconditioner's captured graph) covering all meshes."""
+    out, d0, c0 = [], 0, 0
+    for h in hierarchies:
+        cells = np.asarray(h[-1].cells)
+        e = np.sort(np.concatenate([cells[:, [1, 2]], cells[:, [0, 2]], cells[:, [0, 1]]]).astype(np.int64), axis=1)
+        _, cnt = np.unique(e, axis=0, return_counts=True)
+        nd = int((cnt == 2).sum()) * 2 * (k + 1)
+        out.append((slice(d0, d0 + nd), slice(c0, c0 + cells.shape[0])))
+        d0 += nd
+        c0 += cells.shape[0]
+    return out
+
+
 def hdg_condense(ctx: Context, params: Params, forcing=None, stream=None):
     """Condense; returns the condensed load F (cuda float64 tensor) when forcing is given."""
     import torch

@@ -195,3 +195,42 @@ def step_channel_hierarchy(n_levels: int, h0: float = 0.5) -> List[Mesh2D]:
     for _ in range(1, n_levels):
         levels.append(red_refine(levels[-1]))
     return levels
+
+
+def disjoint_union(hierarchies: List[List[Mesh2D]], gap: float = 0.5) -> List[Mesh2D]:
+    """One hierarchy holding several meshes side by side, level by level: mesh i is shifted by
+    i·(1 + gap) in x, its vertex and cell ids follow those of meshes 0..i-1, parent maps and
+    vertex colourings are concatenated.  Every hierarchy needs the same number of levels.
+    Because each mesh's vertex ids precede the next mesh's, the lexicographic facet numbering
+    keeps every mesh's facets (and so its skeleton unknowns) in one contiguous block, in mesh
+    order; cells likewise."""
+    nl = len(hierarchies[0])
+    if any(len(h) != nl for h in hierarchies):
+        raise ValueError("all hierarchies need the same number of levels")
+    out = []
+    for l in range(nl):
+        coords, cells, parent, colour = [], [], [], []
+        voff = coff = pcoff = 0
+        for i, h in enumerate(hierarchies):
+            m = h[l]
+            coords.append(m.coords + np.array([i * (1.0 + gap), 0.0]))
+            cells.append(m.cells.astype(np.int64) + voff)
+            if l > 0:
+                parent.append(m.parent.astype(np.int64) + pcoff)
+                pcoff += h[l - 1].n_cells
+            col = m.vertex_colour if m.vertex_colour is not None else None
+            colour.append(col)
+            voff += m.n_vertices
+            coff += m.n_cells
+        vc = None if any(c is None for c in colour) else np.concatenate(colour).astype(np.int32)
+        out.append(Mesh2D(coords=np.vstack(coords), cells=np.vstack(cells).astype(np.int32),
+                          parent=np.concatenate(parent).astype(np.int32) if l > 0 else None,
+                          vertex_colour=vc, meta={"parts": [h[l].n_cells for h in hierarchies]}))
+    return out
+
+
+def interior_facet_count(cells: np.ndarray) -> int:
+    """Interior facets of a triangulation: (3 n_cells - n_boundary) / 2."""
+    e = np.sort(np.concatenate([cells[:, [1, 2]], cells[:, [0, 2]], cells[:, [0, 1]]]).astype(np.int64), axis=1)
+    _, cnt = np.unique(e, axis=0, return_counts=True)
+    return int((cnt == 2).sum())
