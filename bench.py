@@ -69,6 +69,12 @@ def parse():
     ap.add_argument("--profile-precond-multi", action="store_true",
                     help="condense (--N, --k, --precision), then apply the batched preconditioner twice to 64 "
                          "seeded random columns (the command profiled for the batched smoother)")
+    ap.add_argument("--tetra-large", action="store_true",
+                    help="add the 3D configuration at n = 48, k = 2 (23.6M unknowns, about 170 GB) to the 3D form")
+    ap.add_argument("--profile-sweep3d", type=int, default=0, metavar="N",
+                    help="3D: condense the N x N x N unit cube (Kuhn tetrahedra, levels from 2x2x2) at order --k "
+                         "with the FP32 preconditioner, then run 4 order-k edge-patch sweeps (the command "
+                         "profiled for the 3D sweep)")
     ap.add_argument("--precision", type=int, default=1,
                     help="preconditioner precision of --profile-solve / --profile-precond-multi "
                          "(hdg_precision value)")
@@ -761,12 +767,14 @@ def tetra_form(args, hdg, torch, dev, stream):
     from workloads.manufactured import curl_bubble_3d, forcing_at_lattice
     peak = measured_peaks().get("hbm_gbs", 6800.0)
     out = {}
-    cases = ((4, 2, ("fp64", "mixed_fp32")), (4, 3, ("fp64", "mixed_fp32")), (5, 2, ("mixed_fp32",)),
-             (5, 3, ("mixed_fp32",)))
-    for nl, k, forms in cases:
-        ms = unit_cube_hierarchy(2, nl)
+    cases = [(2, 4, 2, ("fp64", "mixed_fp32")), (2, 4, 3, ("fp64", "mixed_fp32")), (2, 5, 2, ("mixed_fp32",)),
+             (2, 5, 3, ("mixed_fp32",))]
+    if getattr(args, "tetra_large", False):
+        cases.append((3, 5, 2, ("mixed_fp32",)))      # n = 48 (hierarchy 3 -> 6 -> 12 -> 24 -> 48), about 170 GB
+    for n0, nl, k, forms in cases:
+        ms = unit_cube_hierarchy(n0, nl)
         fine = ms[-1]
-        n = 2 ** nl
+        n = n0 * 2 ** (nl - 1)
         fv = torch.tensor(forcing_at_lattice(fine.coords, fine.cells, k, curl_bubble_3d().forcing(1.0, 1.0)),
                           device=dev)
         ctx = hdg.hdg_setup_mesh_hierarchy(ms, device=dev.index or 0)
@@ -1058,8 +1066,30 @@ def profile_precond_multi(args):
     ctx.close()
 
 
+def profile_sweep3d(args):
+    import torch
+    import paper_2303_06762_gb300 as hdg
+    from workloads.mesh3d import unit_cube_hierarchy
+    nl = 1
+    while 2 ** nl < args.profile_sweep3d:
+        nl += 1
+    ms = unit_cube_hierarchy(2, nl)
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    hdg.hdg_condense(ctx, hdg.Params(k=args.k, nu=1.0, beta=1.0, gamma=1e2, precision=hdg.HDG_MIXED_FP32))
+    gen = torch.Generator(device="cuda:0").manual_seed(1)
+    g = torch.randn(ctx.sizes().n_dof, dtype=torch.float64, device="cuda:0", generator=gen)
+    u = torch.zeros_like(g)
+    hdg.hdg_smooth(ctx, -1, g, u, 4, False)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_sweep3d": True, "n": 2 ** nl, "k": args.k, "max_abs": float(u.abs().max())}))
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.profile_sweep3d:
+        profile_sweep3d(args)
+        return
     if args.profile_solve:
         profile_solve(args)
         return

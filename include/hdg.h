@@ -37,6 +37,26 @@
  * Pressure: one double per cell (the cell-constant pressure p^∂ of the
  * condensed saddle point, eq. stOptForm).
  *
+ * Tetrahedra (dim = 3; the generalized Stokes operator; Section 3.4.2 edge
+ * patches): local face f is opposite local vertex f; faces are numbered in
+ * lexicographic order of their sorted global vertex triple a < b < c, with
+ * the frame t1 = (x_b - x_a)/|.|, n_F = (x_b - x_a) x (x_c - x_a)/|.|,
+ * t2 = n_F x t1 and the scalar basis l_m: the L2(F)-orthonormal Gram-Schmidt
+ * basis of lambda_b^i lambda_c^j (i + j <= k, by degree then j) in the
+ * barycentrics of x_b, x_c.  An interior face owns dpf = 3 nf doubles,
+ * nf = (k+1)(k+2)/2: the normal moments int_F (u.n_F) l_m dS, then the t1 and
+ * the t2 coefficients of the tangential unknown.  Element matrices have
+ * n_loc = 4 dpf.  Forcing: [n_cells][n_lat][3] at the points
+ * v0 + (a1/q)(v1-v0) + (a2/q)(v2-v0) + (a3/q)(v3-v0), a3 outer, then a2, a1
+ * inner, n_lat = (q+1)(q+2)(q+3)/6.  The lowest-order levels carry 3 unknowns
+ * per face.  Calls available on tetrahedra: hdg_setup_mesh_hierarchy,
+ * hdg_check_hierarchy, hdg_condense (FP64 or FP32 preconditioner, block GS,
+ * scalar nu, no convection or Dirichlet data, k <= 3), hdg_load, hdg_apply,
+ * hdg_level_apply, hdg_smooth, hdg_prolong_add, hdg_restrict,
+ * hdg_coarse_solve, hdg_mg_h, hdg_precond_apply, hdg_get_element_matrices,
+ * hdg_solve, hdg_recover, hdg_get_sizes; the others return
+ * HDG_ERR_UNSUPPORTED.
+ *
  * Memory: pointers documented "device" must be device memory on the
  * context's device; "host" pointers are host memory.  The caller owns every
  * buffer it passes; the context owns the mesh data, element and patch
@@ -95,7 +115,8 @@ typedef enum {
 } hdg_precision;
 
 typedef struct {
-    int dim;                              /* 2                                      */
+    int dim;                              /* 2 (triangles) or 3 (tetrahedra, a red- */
+                                          /* refined hierarchy; edge patches)       */
     int n_levels;                         /* >= 1, level 0 = coarsest               */
     const int64_t *n_vertices;            /* host [n_levels]                        */
     const int64_t *n_cells;               /* host [n_levels]                        */
@@ -311,7 +332,11 @@ hdg_status hdg_solve(hdg_ctx *ctx, const double *F, double *u, double *p,
  *            orthonormal P^k basis of each cell, components (xx, xy, yx, yy),
  *            npk = (k+1)(k+2)/2 (basis: csrc/reference.cpp);
  *   ulat_out [n_cells][n_lat][2]: u_h at the degree-(k+1) lattice points, which
- *            determine u_h exactly (RT_k is contained in [P^{k+1}]^2). */
+ *            determine u_h exactly (RT_k is contained in [P^{k+1}]^2).
+ * On tetrahedra: L_out [n_cells][9][npk] (components xx, xy, xz, yx, ..., zz over
+ * the orthonormal P^k basis of the reference tetrahedron composed with the cell's
+ * affine map, csrc/reference3d.cpp; npk = (k+1)(k+2)(k+3)/6) and ulat_out
+ * [n_cells][n_lat][3] (n_lat = (k+2)(k+3)(k+4)/6). */
 hdg_status hdg_recover(hdg_ctx *ctx, const double *u, const double *forcing, double *L_out,
                        double *ulat_out, hdg_stream_t stream);
 

@@ -523,13 +523,18 @@ def hdg_newton(ctx: Context, params: Params, forcing, u, p, tol: float = 1e-10, 
 
 
 def hdg_recover(ctx: Context, u, forcing=None, stream=None):
-    """Local fields of a skeleton solution: (L coefficients [nc, 4, npk], u at the lattice [nc, nlat, 2])."""
+    """Local fields of a skeleton solution: (L coefficients [nc, d*d, npk], u at the lattice [nc, nlat, d]);
+    d = 2 on triangles, 3 on tetrahedra."""
     import torch
     s = ctx.sizes()
     k = s.k
-    npk, nlat = (k + 1) * (k + 2) // 2, (k + 2) * (k + 3) // 2
-    L = torch.empty((s.n_cells, 4, npk), dtype=torch.float64, device=u.device)
-    ul = torch.empty((s.n_cells, nlat, 2), dtype=torch.float64, device=u.device)
+    d = getattr(ctx, "dim", 2)
+    if d == 2:
+        npk, nlat = (k + 1) * (k + 2) // 2, (k + 2) * (k + 3) // 2
+    else:
+        npk, nlat = (k + 1) * (k + 2) * (k + 3) // 6, (k + 2) * (k + 3) * (k + 4) // 6
+    L = torch.empty((s.n_cells, d * d, npk), dtype=torch.float64, device=u.device)
+    ul = torch.empty((s.n_cells, nlat, d), dtype=torch.float64, device=u.device)
     ctx.check(load_library().hdg_recover(ctx.handle, _ptr(u), _ptr(forcing), _ptr(L), _ptr(ul),
                                          _stream(stream)))
     return L, ul

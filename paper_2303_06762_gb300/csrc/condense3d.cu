@@ -51,7 +51,7 @@ condense3_kernel(int64_t nc, const double *__restrict__ coords, const int *__res
                  const double *__restrict__ ref, double nu, const double *__restrict__ nu_cell, double beta,
                  double gamma, const double *__restrict__ forcing, double *__restrict__ Aout,
                  float *__restrict__ Af, double *__restrict__ Fel, double *__restrict__ cell_d,
-                 double *__restrict__ cell_area, double *__restrict__ scratch, int *flag) {
+                 double *__restrict__ cell_area, double *__restrict__ scratch, int *flag, Recover3 rec) {
     using D = Dims3<K>;
     constexpr int NPK = D::NPK, NF = D::NF, NRT = D::NRT, NLAT = D::NLAT, NUH = D::NUH, N = D::N,
                   LD = D::LD, DPF = D::DPF, NLOC = D::NLOC;
@@ -63,6 +63,7 @@ condense3_kernel(int64_t nc, const double *__restrict__ coords, const int *__res
     const double *R6 = R5 + NRT * NPK;
     const double *Q = R6 + NRT * 3 * NLAT;
     const double *FA = Q + 6 * NF * NF;
+    const double *R7 = FA + 4;
     double *Bm = scratch + (size_t)blockIdx.x * D::SCR;   // [9 NPK][NUH]
     double *Km = Bm + D::NB;                              // [N][LD]
     double *Rm = Km + (size_t)N * LD;                     // [NLOC][NLOC + NRHS]
@@ -70,6 +71,7 @@ condense3_kernel(int64_t nc, const double *__restrict__ coords, const int *__res
     __shared__ double nK[4][3], t1[4][3], t2[4][3], nJ[4][3], farea[4], fsig[4];
     __shared__ int fperm[4];
     __shared__ double colq[N], rowq[LD];
+    __shared__ double Xs[NUH], xl[NLOC];      // recovery: reference-basis unknowns, the cell's skeleton values
     __shared__ int bad;
     const int tid = threadIdx.x, nt = blockDim.x;
     for (int64_t c = blockIdx.x; c < nc; c += gridDim.x) {
@@ -205,6 +207,39 @@ condense3_kernel(int64_t nc, const double *__restrict__ coords, const int *__res
             Km[idx] = v;
         }
         __syncthreads();
+        if (rec.x) {
+            // recovery: the local right-hand side (f, v) - K_lg x_g in column N, with the skeleton
+            // values rotated to the reference face basis (x_ref = T^T x)
+            for (int l = tid; l < NLOC; l += nt) {
+                const int j = rec.cell_int[4 * c + l / DPF];
+                xl[l] = j >= 0 ? rec.x[(size_t)j * DPF + l % DPF] : 0.0;
+            }
+            __syncthreads();
+            for (int x = tid; x < NUH; x += nt) {
+                double v = 0.0;
+                if (x < 4 * NF) {
+                    const int f = x / NF, m2 = x % NF;
+                    for (int m = 0; m < NF; ++m)
+                        v += fsig[f] * sqrt(farea[f]) * Q[((size_t)fperm[f] * NF + m) * NF + m2] * xl[f * DPF + m];
+                } else if (x >= NRT) {
+                    const int hx = x - NRT, f = hx / (2 * NF);
+                    v = xl[f * DPF + NF + hx % (2 * NF)];
+                }
+                Xs[x] = v;
+            }
+            __syncthreads();
+            for (int i = tid; i < N; i += nt) {
+                double v = 0.0;
+                if (forcing) {
+                    const double *fc = forcing + (size_t)c * D::NRHS;
+                    for (int col = 0; col < D::NRHS; ++col) v += Km[(size_t)i * LD + N + col] * fc[col];
+                }
+                for (int x = 0; x < NUH; ++x)
+                    if (x < 4 * NF || x >= NRT) v -= Km[(size_t)i * LD + x] * Xs[x];
+                Km[(size_t)i * LD + N] = v;
+            }
+            __syncthreads();
+        }
         // eliminate the interior RT unknowns, then the mean-free pressure
         for (int t = 0; t < (NRT - 4 * NF) + (NPK - 1); ++t) {
             const int q = t < NRT - 4 * NF ? 4 * NF + t : NUH + 1 + (t - (NRT - 4 * NF));
@@ -223,6 +258,32 @@ condense3_kernel(int64_t nc, const double *__restrict__ coords, const int *__res
         }
         if (bad) {
             if (tid == 0) atomicOr(flag, 1);
+            __syncthreads();
+            continue;
+        }
+        if (rec.x) {
+            // interior RT coefficients from the eliminated local rows, then the outputs
+            for (int t = tid; t < NRT - 4 * NF; t += nt) {
+                const int q = 4 * NF + t;
+                Xs[q] = Km[(size_t)q * LD + N] / Km[(size_t)q * LD + q];
+            }
+            __syncthreads();
+            if (rec.rt)
+                for (int i = tid; i < NRT; i += nt) rec.rt[(size_t)c * NRT + i] = Xs[i];
+            if (rec.L)   // L = -(nu/|det J|) B x: coefficients of component (c, e) over g_j
+                for (int r = tid; r < 9 * NPK; r += nt) {
+                    double v = 0.0;
+                    for (int x = 0; x < NUH; ++x) v += Bm[(size_t)r * NUH + x] * Xs[x];
+                    rec.L[(size_t)c * 9 * NPK + r] = -(nuc / adet) * v;
+                }
+            if (rec.ulat)   // u_h = J u^ / |det J| at the lattice
+                for (int idx = tid; idx < NLAT * 3; idx += nt) {
+                    const int n = idx / 3, a = idx % 3;
+                    double w[3] = {0.0, 0.0, 0.0};
+                    for (int i = 0; i < NRT; ++i)
+                        for (int b = 0; b < 3; ++b) w[b] += Xs[i] * R7[((size_t)n * NRT + i) * 3 + b];
+                    rec.ulat[(size_t)c * NLAT * 3 + idx] = (J[a][0] * w[0] + J[a][1] * w[1] + J[a][2] * w[2]) / adet;
+                }
             __syncthreads();
             continue;
         }
@@ -429,7 +490,8 @@ size_t condense3_scratch_doubles(int k, int blocks) {
 
 cudaError_t launch_condense3(int k, const DevLevel &L, const double *ref, const RefTables3 &rt, double nu,
                              const double *nu_cell, double beta, double gamma, const double *forcing, double *A,
-                             float *Af, double *Fel, double *scratch, int blocks, int *flag, cudaStream_t s) {
+                             float *Af, double *Fel, double *scratch, int blocks, int *flag, cudaStream_t s,
+                             const Recover3 &rec) {
     (void)rt;
     if (L.nc == 0) return cudaSuccess;
     const unsigned nb = (unsigned)std::min<int64_t>(L.nc, blocks);
@@ -437,7 +499,8 @@ cudaError_t launch_condense3(int k, const DevLevel &L, const double *ref, const 
 #define HDG_C3(KK)                                                                                               \
     case KK:                                                                                                     \
         condense3_kernel<KK><<<nb, 128, 0, s>>>(L.nc, L.coords.p, L.cells.p, ref, nu, nu_cell, beta, gamma,       \
-                                                forcing, A, Af, Fel, L.cell_d.p, L.cell_area.p, scratch, flag); \
+                                                forcing, A, Af, Fel, L.cell_d.p, L.cell_area.p, scratch, flag,  \
+                                                rec);                                                     \
         break;
     switch (k) {
         HDG_C3(0)

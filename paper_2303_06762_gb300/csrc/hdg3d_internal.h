@@ -26,9 +26,19 @@ std::string build_transfer_3d(const HostLevel3 &coarse, const HostLevel3 &fine, 
 // condense3d.cu: element matrices (with the AL term), flux weights, volumes and element loads
 // of one tetrahedral level; scratch: device workspace of condense3_scratch_doubles(k) doubles
 size_t condense3_scratch_doubles(int k, int blocks);
+// recovery mode (x non-null): the cell unknowns of the skeleton solution x [n_int][dpf] instead of
+// the element matrices and loads: RT coefficients in the reference basis rt [nc][nrt], L_h over the
+// orthonormal P^k basis L [nc][9][npk] (components xx, xy, xz, yx, ..., zz), u_h at the lattice
+// ulat [nc][nlat][3] (each output nullable)
+struct Recover3 {
+    const double *x = nullptr;
+    const int *cell_int = nullptr;
+    double *rt = nullptr, *L = nullptr, *ulat = nullptr;
+};
 cudaError_t launch_condense3(int k, const DevLevel &L, const double *ref, const RefTables3 &rt, double nu,
                              const double *nu_cell, double beta, double gamma, const double *forcing, double *A,
-                             float *Af, double *Fel, double *scratch, int blocks, int *flag, cudaStream_t s);
+                             float *Af, double *Fel, double *scratch, int blocks, int *flag, cudaStream_t s,
+                             const Recover3 &rec = Recover3());
 cudaError_t launch_transfer_H3(const DevLevel &fine, int *flag, cudaStream_t s);
 // edge-patch inverses with the patch matrices in a global workspace (blocks slices of np_max^2)
 size_t patch_inverse3_scratch_doubles(const DevLevel &L, const DevOperator &op, int blocks);

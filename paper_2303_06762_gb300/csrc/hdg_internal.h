@@ -213,7 +213,7 @@ struct HostTransfer3 {
 
 struct RefTables3 {
     int k = -1, npk = 0, nrt = 0, nf = 0, nlat = 0;
-    std::vector<double> R1, R2, R3, R4, R5, R6, Q, FA;
+    std::vector<double> R1, R2, R3, R4, R5, R6, Q, FA, R7;   // R7: phi at the lattice (recovery)
 };
 
 struct DevLevel {

@@ -25,6 +25,7 @@
 //                    lexicographic order) against the canonical one; orthogonal, the same
 //                    for every face
 //   FA[f]          = |F^_f|
+//   R7[n][i][a]    = phi_{i,a} at lattice point n
 #include <algorithm>
 #include <cmath>
 #include <stdexcept>
@@ -382,12 +383,17 @@ void build_reference_tables_3d(int k, RefTables3 &T) {
                 T.Q[((size_t)p * nf + m) * nf + m2] = integrate_face(mul(lp[m], lf[3][m2]), 3) / FA[3];
     }
     T.FA.assign(FA, FA + 4);
-    (void)eval;
+    // R7[n][i][a] = phi_{i,a} at lattice point n (recovery of u_h at the forcing lattice)
+    T.R7.assign((size_t)nlat * nrt * 3, 0.0);
+    for (int n = 0; n < nlat; ++n)
+        for (int i = 0; i < nrt; ++i)
+            for (int a = 0; a < 3; ++a)
+                T.R7[((size_t)n * nrt + i) * 3 + a] = eval(phi[i][a], pts[n][0], pts[n][1], pts[n][2]);
 }
 
 std::vector<double> pack_reference_tables_3d(const RefTables3 &T) {
     std::vector<double> out;
-    for (const std::vector<double> *t : {&T.R1, &T.R2, &T.R3, &T.R4, &T.R5, &T.R6, &T.Q, &T.FA})
+    for (const std::vector<double> *t : {&T.R1, &T.R2, &T.R3, &T.R4, &T.R5, &T.R6, &T.Q, &T.FA, &T.R7})
         out.insert(out.end(), t->begin(), t->end());
     return out;
 }

@@ -172,3 +172,69 @@ def test_mixed_precision_solve(k):
     eu, ep = relnorm(host(u), ud), relnorm(host(p), pd)
     print(f"3D mixed k={k}: its {info['krylov_its']} |du| {eu:.2e} |dp| {ep:.2e}")
     assert eu < 1e-8 and ep < 1e-8
+
+
+def test_recovery_matches_oracle():
+    """hdg_recover on tetrahedra: u_h at each cell's degree-(k+1) lattice from the exact skeleton
+    solution against the oracle's element-by-element recovery."""
+    from workloads.manufactured import lattice_barycentric_3d
+    hdg = _hdg()
+    k = 2
+    ms, ts, ps, fv, ctx, F = setup3(1, 2, k, jitter=0.2, seed=8, shuffle_seed=2)
+    oh = HDG3D(ts[-1], k, gamma=100.0, beta=1.0)
+    ud, pd = oh.solve_direct(oh.load(fv))
+    _, ul = hdg.hdg_recover(ctx, dev(ud), dev(fv))
+    ul = host(ul)
+    lam = lattice_barycentric_3d(k + 1)
+    err, scale = 0.0, 0.0
+    for c in range(ts[-1].n_cells):
+        el = oh.cells[c].el
+        xl = lam @ el.X
+        _, uo, _, _ = oh.fields_at(c, oh.recover_cell(c, ud, pd[c], fv[c]), xl)
+        err = max(err, np.abs(ul[c] - uo).max())
+        scale = max(scale, np.abs(uo).max())
+    print(f"3D recovery: max |u_h - oracle| {err:.2e} (scale {scale:.2e})")
+    assert err < 1e-10 * scale
+
+
+def _l2_error_3d(coords, cells, ulat, q, u_exact):
+    """|| u - v ||_L2 for v in [P^q]^3 given at every tetrahedron's degree-q lattice."""
+    from workloads.manufactured import lattice_barycentric_3d
+    from oracle.quadrature import tetrahedron_rule
+    lam = lattice_barycentric_3d(q)[:, 1:]                 # reference coordinates of the lattice
+    xi, w = tetrahedron_rule(q + 3)
+    ex = [(a, b, c) for n in range(q + 1) for c in range(n + 1) for b in range(n - c + 1) for a in [n - b - c]]
+
+    def mono(p):
+        return np.stack([p[:, 0] ** a * p[:, 1] ** b * p[:, 2] ** c for a, b, c in ex], axis=1)
+    E = mono(xi) @ np.linalg.inv(mono(lam))
+    X = coords[cells]
+    J = np.stack([X[:, 1] - X[:, 0], X[:, 2] - X[:, 0], X[:, 3] - X[:, 0]], axis=2)
+    det = np.abs(np.linalg.det(J))
+    xq = X[:, None, 0, :] + np.einsum("cij,qj->cqi", J, xi)
+    vq = np.einsum("qn,cna->cqa", E, ulat)
+    ue = u_exact(xq.reshape(-1, 3)).reshape(vq.shape)
+    return float(np.sqrt(np.einsum("c,q,cqa->", det, w, (ue - vq) ** 2)))
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_convergence_order_at_scale(k):
+    """The library's 3D solution of the manufactured problem on n = 4, 8, 16 (levels from 2x2x2):
+    the L2 error of u_h decays at order k + 1 (Section 5.1)."""
+    hdg = _hdg()
+    sol = curl_bubble_3d()
+    errs = []
+    for nl in (2, 3, 4):
+        ms = unit_cube_hierarchy(2, nl)
+        fine = ms[-1]
+        fv = forcing_at_lattice(fine.coords, fine.cells, k, sol.forcing(1.0, 1.0))
+        ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+        F = hdg.hdg_condense(ctx, hdg.Params(k=k, nu=1.0, beta=1.0, gamma=100.0, precision=1, m_p=2, m_h=2), dev(fv))
+        u, p, info = hdg.hdg_solve(ctx, F, opts=parity_opts(hdg, 100.0))
+        assert info["div_l2"] < 1e-8
+        _, ul = hdg.hdg_recover(ctx, u, dev(fv))
+        errs.append(_l2_error_3d(fine.coords, fine.cells, host(ul), k + 1, sol.u))
+        ctx.close()
+    rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    print(f"3D k={k}: |u - u_h| {errs} rates {rates}")
+    assert abs(rates[-1] - (k + 1)) < 0.2
