@@ -70,7 +70,8 @@ def parse():
                     help="condense (--N, --k, --precision), then apply the batched preconditioner twice to 64 "
                          "seeded random columns (the command profiled for the batched smoother)")
     ap.add_argument("--tetra-large", action="store_true",
-                    help="add the 3D configuration at n = 48, k = 2 (23.6M unknowns, about 170 GB) to the 3D form")
+                    help="add the 3D configuration at n = 48, k = 2 and 3 (23.6M and 39.4M unknowns, up to 229 GB) "
+                         "to the 3D form")
     ap.add_argument("--profile-sweep3d", type=int, default=0, metavar="N",
                     help="3D: condense the N x N x N unit cube (Kuhn tetrahedra, levels from 2x2x2) at order --k "
                          "with the FP32 preconditioner, then run 4 order-k edge-patch sweeps (the command "
@@ -770,7 +771,8 @@ def tetra_form(args, hdg, torch, dev, stream):
     cases = [(2, 4, 2, ("fp64", "mixed_fp32")), (2, 4, 3, ("fp64", "mixed_fp32")), (2, 5, 2, ("mixed_fp32",)),
              (2, 5, 3, ("mixed_fp32",))]
     if getattr(args, "tetra_large", False):
-        cases.append((3, 5, 2, ("mixed_fp32",)))      # n = 48 (hierarchy 3 -> 6 -> 12 -> 24 -> 48), about 170 GB
+        # n = 48 (hierarchy 3 -> 6 -> 12 -> 24 -> 48): about 162 GB (k = 2) and 229 GB (k = 3) on the device
+        cases += [(3, 5, 2, ("mixed_fp32",)), (3, 5, 3, ("mixed_fp32",))]
     for n0, nl, k, forms in cases:
         ms = unit_cube_hierarchy(n0, nl)
         fine = ms[-1]
@@ -787,7 +789,7 @@ def tetra_form(args, hdg, torch, dev, stream):
             F = hdg.hdg_condense(ctx, prm, fv)
             torch.cuda.synchronize()
             setup = time.perf_counter() - t0
-            o = solve_opts(hdg, 30)
+            o = solve_opts(hdg, 30 if n < 48 else 15)   # n = 48: FGMRES(15) keeps the basis at 10 GB
             hdg.hdg_solve(ctx, F, opts=o)
             t, (u, p, info) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F, opts=o))
             nd = ctx.sizes().n_dof

@@ -1842,7 +1842,10 @@ static void condense_all_3d(hdg_ctx *ctx, const double *forcing, cudaStream_t s)
     dalloc(ctx, op.A, (size_t)op.nloc * op.nloc * LJ.nc);
     dalloc(ctx, op.Af, (size_t)op.nloc * op.nloc * LJ.nc);
     dalloc(ctx, op.Fel, (size_t)op.nloc * LJ.nc);
-    dalloc(ctx, op.Pinv, (size_t)LJ.n_patches * op.np_max * op.np_max);
+    // the FP32 preconditioner sweeps with the FP32 inverses only: no FP64 copy is kept (at n = 48, k = 3
+    // the FP64 edge-patch inverses alone would take about 200 GB)
+    if (prm->precision == HDG_FP64) dalloc(ctx, op.Pinv, (size_t)LJ.n_patches * op.np_max * op.np_max);
+    else dfree(op.Pinv);
     dalloc(ctx, op.Pinvf, (size_t)LJ.n_patches * op.np_max * op.np_max);
     CK(launch_condense3(k, LJ, ctx->ref3k_dev.p, ctx->ref3k, prm->nu, nullptr, prm->beta, prm->gamma, forcing, op.A.p,
                         op.Af.p, op.Fel.p, ctx->c3_scratch.p, blocks, flag, s));

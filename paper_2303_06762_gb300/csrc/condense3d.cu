@@ -468,7 +468,7 @@ patch_inverse3_kernel(int n_patches, int pf_max, int pc_max, int dpf, int nloc, 
         for (int idx = tid; idx < np_max * np_max; idx += nt) {
             const int j = idx / np_max, i = idx % np_max;
             const double v = (i < np && j < np) ? M[(size_t)i * np + j] : 0.0;
-            Pinv[(size_t)p * np_max * np_max + idx] = v;
+            if (Pinv) Pinv[(size_t)p * np_max * np_max + idx] = v;
             if (Pinvf) Pinvf[(size_t)p * np_max * np_max + idx] = (float)v;
         }
         if (tid == 0 && !ok) atomicOr(flag, 2);
