@@ -69,6 +69,10 @@ def parse():
     ap.add_argument("--profile-precond-multi", action="store_true",
                     help="condense (--N, --k, --precision), then apply the batched preconditioner twice to 64 "
                          "seeded random columns (the command profiled for the batched smoother)")
+    ap.add_argument("--profile-solve-multi", action="store_true",
+                    help="condense --N (levels from 8x8), --k, --precision, then one warm-up and one batched solve of "
+                         "64 seeded Fourier loads with FGMRES(--restart-batched) (the command profiled for the "
+                         "batched solve's launch list)")
     ap.add_argument("--tetra-large", action="store_true",
                     help="add the 3D configuration at n = 48, k = 2 and 3 (23.6M and 39.4M unknowns, up to 229 GB) "
                          "to the 3D form")
@@ -567,6 +571,7 @@ def batched_form(args, hdg, torch, dev, stream, world):
     t1, (_, _, info1) = _timed(torch, stream, lambda: hdg.hdg_solve(ctx, F0, opts=o1))
     # the same loads with the order-k batched sweep on tensor cores (binary16 operands)
     hdg.hdg_condense(ctx, hdg.Params(k=k, nu=1.0, beta=1.0, gamma=1e2, precision=hdg.HDG_MIXED_FP16))
+    _, nt_tc, ms_tc = hdg.hdg_tune_batched(ctx, nrhs)   # the tensor-core sweep's block size
     hdg.hdg_solve_multi(ctx, F, opts=om)
     th, (_, _, infos_h) = _timed(torch, stream, lambda: hdg.hdg_solve_multi(ctx, F, opts=om))
     its_h = sum(i["krylov_its_total"] for i in infos_h)
@@ -585,6 +590,7 @@ def batched_form(args, hdg, torch, dev, stream, world):
             "tensor_core_fp16": {"time_to_tol_s": th, "fgmres_iters_total": its_h,
                                  "dof_iters_per_s": sizes.n_dof * its_h * world / th,
                                  "speedup_time_to_tol_vs_fp32": t / th,
+                                 "autotuned_threads": nt_tc, "colour_phase_ms": ms_tc,
                                  "note": "HDG_MIXED_FP16: order-k batched sweep as mma.sync m16n8k16 with binary16 "
                                          "operands and FP32 accumulation"}}
 
@@ -1068,6 +1074,32 @@ def profile_precond_multi(args):
     ctx.close()
 
 
+def profile_solve_multi(args):
+    import torch
+    import paper_2303_06762_gb300 as hdg
+    from workloads import unit_square_hierarchy
+    from workloads.manufactured import fourier_forcing_2d, lattice_points_2d
+    nl = 1
+    while 8 * 2 ** (nl - 1) < args.N:
+        nl += 1
+    ms = unit_square_hierarchy(8, nl)
+    fine = ms[-1]
+    ctx = hdg.hdg_setup_mesh_hierarchy(ms)
+    hdg.hdg_condense(ctx, hdg.Params(k=args.k, nu=1.0, beta=1.0, gamma=1e2, precision=args.precision))
+    X = torch.tensor(lattice_points_2d(fine.coords, fine.cells, args.k + 1), device="cuda:0")
+    shp = X.shape
+    F = torch.stack([hdg.hdg_load(ctx, fourier_forcing_2d(j)(X.reshape(-1, 2), xp=torch).reshape(shp).contiguous())
+                     for j in range(64)])
+    o = solve_opts(hdg, args.restart_batched)
+    for _ in range(2):
+        U, P, infos = hdg.hdg_solve_multi(ctx, F, opts=o)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_solve_multi": True, "N": args.N, "k": args.k, "precision": args.precision,
+                      "iterations": sum(i["krylov_its_total"] for i in infos),
+                      "launches": hdg.hdg_kernel_launches()}))
+    ctx.close()
+
+
 def profile_sweep3d(args):
     import torch
     import paper_2303_06762_gb300 as hdg
@@ -1091,6 +1123,9 @@ def main():
     args = parse()
     if args.profile_sweep3d:
         profile_sweep3d(args)
+        return
+    if args.profile_solve_multi:
+        profile_solve_multi(args)
         return
     if args.profile_solve:
         profile_solve(args)

@@ -410,10 +410,14 @@ hdg_status hdg_smooth_multi(hdg_ctx *ctx, int level, int nrhs, const double *g, 
  * preconditioner application for each precision and padded width: it times one
  * colour phase of the finest level for every pair on scratch vectors and keeps
  * the fastest.  All pairs give bitwise-identical results.
+ * The tensor-core sweep (16-bit precisions, k = 3) is tuned the same way over
+ * its block size (128 or 256 threads; bitwise-identical results).
  * hdg_set_batched_tile forces a pair for this context (0, 0 = back to the
- * autotuner).  hdg_tune_batched runs the autotuner now for width nrhs and
- * returns its choice and the time of one colour phase in ms (0, 0, 0 when the
- * sweep of that width runs on tensor cores or k = 0); outputs may be NULL. */
+ * autotuner; the tensor-core sweep takes the forced thread count).
+ * hdg_tune_batched runs the autotuner now for width nrhs and returns its choice
+ * and the time of one colour phase in ms (rows_per_thread = 0 and the block
+ * size when the sweep of that width runs on tensor cores; 0, 0, 0 for k = 0);
+ * outputs may be NULL. */
 hdg_status hdg_set_batched_tile(hdg_ctx *ctx, int rows_per_thread, int threads);
 hdg_status hdg_tune_batched(hdg_ctx *ctx, int nrhs, int *rows_per_thread, int *threads, double *ms,
                             hdg_stream_t stream);

@@ -848,17 +848,56 @@ void tune_gs_m(hdg_ctx *ctx, int R, cudaStream_t s) {
     ctx->tile_ms[pi][li] = best;
 }
 
-// tunes the batched order-k sweep of the current precision for width R unless it is
-// done, forced, or the sweep runs on tensor cores; false if the stream is capturing
+// Autotuner of the tensor-core sweep: times the largest colour phase of the finest level for
+// 128 and 256 threads per block and keeps the faster.  Every tile's MMAs and the column
+// maxima are the same for both block sizes, so the results are bitwise identical.
+void tune_gs_tc(hdg_ctx *ctx, int R, cudaStream_t s) {
+    const int li = log2_width(R);
+    const DevLevel &L = ctx->L[ctx->n_levels - 1];
+    const DevOperator &op = ctx->opk;
+    const size_t n = (size_t)std::max<int64_t>(ctx->n_dof, 1) * R;
+    dalloc(ctx, ctx->tune_buf, n);   // two FP32 vectors of n values
+    float *g = reinterpret_cast<float *>(ctx->tune_buf.p), *u = g + n;
+    CK(cudaMemsetAsync(ctx->tune_buf.p, 0, 2 * n * sizeof(float), s));
+    int colour = 0;
+    for (int c = 1; c < L.n_colours; ++c)
+        if (L.colour_ptr[c + 1] - L.colour_ptr[c] > L.colour_ptr[colour + 1] - L.colour_ptr[colour]) colour = c;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    double best = 1e300;
+    int bnt = 256;
+    for (int nt : {128, 256}) {
+        CK(launch_gs_colour_tc(L, op, R, colour, g, u, s, nt));
+        CK(cudaEventRecord(e0, s));
+        for (int it = 0; it < 3; ++it) CK(launch_gs_colour_tc(L, op, R, colour, g, u, s, nt));
+        CK(cudaEventRecord(e1, s));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / 3 < best) {
+            best = ms / 3;
+            bnt = nt;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tile_tc_nt[li] = bnt;
+    ctx->tile_tc_ms[li] = best;
+}
+
+// tunes the batched order-k sweep (CUDA-core tile, or the tensor-core block size) of the
+// current precision for width R unless it is done or forced; false if the stream is capturing
 bool ensure_tuned(hdg_ctx *ctx, int R, cudaStream_t s) {
     if (ctx->tile_force_rb || ctx->tile_force_nt || ctx->prm.k == 0) return true;
     const bool fp64 = ctx->prm.precision == HDG_FP64;
-    if (!fp64 && gs_tc_supported(ctx->L[ctx->n_levels - 1], ctx->opk, R)) return true;
-    if (ctx->tile_rb[fp64 ? 0 : 1][log2_width(R)]) return true;
+    const bool tc = !fp64 && gs_tc_supported(ctx->L[ctx->n_levels - 1], ctx->opk, R);
+    if (tc ? ctx->tile_tc_nt[log2_width(R)] != 0 : ctx->tile_rb[fp64 ? 0 : 1][log2_width(R)] != 0) return true;
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CK(cudaStreamIsCapturing(s, &cs));
     if (cs != cudaStreamCaptureStatusNone) return false;
-    if (fp64) tune_gs_m<double>(ctx, R, s);
+    if (tc) tune_gs_tc(ctx, R, s);
+    else if (fp64) tune_gs_m<double>(ctx, R, s);
     else tune_gs_m<float>(ctx, R, s);
     return true;
 }
@@ -883,7 +922,8 @@ void sweep_m(hdg_ctx *ctx, const DevLevel &L, const DevOperator &op, int R, cons
         const int c = reverse ? L.n_colours - 1 - i : i;
         if constexpr (std::is_same<T, float>::value) {
             if (tc) {
-                CK(launch_gs_colour_tc(L, op, R, c, g, u, s));
+                const int tnt = ctx->tile_force_nt ? ctx->tile_force_nt : ctx->tile_tc_nt[log2_width(R)];
+                CK(launch_gs_colour_tc(L, op, R, c, g, u, s, tnt));
                 continue;
             }
         }
@@ -1605,6 +1645,8 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
     std::memset(ctx->tile_rb, 0, sizeof ctx->tile_rb);   // a new operator is tuned afresh
     std::memset(ctx->tile_nt, 0, sizeof ctx->tile_nt);
     std::memset(ctx->tile_ms, 0, sizeof ctx->tile_ms);
+    std::memset(ctx->tile_tc_nt, 0, sizeof ctx->tile_tc_nt);
+    std::memset(ctx->tile_tc_ms, 0, sizeof ctx->tile_tc_ms);
     const int k = prm->k;
     upload_ref(ctx, ctx->ref0, ctx->ref0_dev, 0);
     upload_ref(ctx, ctx->refk, ctx->refk_dev, k);
@@ -2398,8 +2440,11 @@ hdg_status hdg_tune_batched(hdg_ctx *ctx, int nrhs, int *rows_per_thread, int *t
         const int R = pad_width(nrhs), li = log2_width(R), pi = ctx->prm.precision == HDG_FP64 ? 0 : 1;
         const int frb = ctx->tile_force_rb, fnt = ctx->tile_force_nt;
         ctx->tile_force_rb = ctx->tile_force_nt = 0;
+        const bool tc = pi == 1 && gs_tc_supported(ctx->L[ctx->n_levels - 1], ctx->opk, R);
         ctx->tile_rb[pi][li] = ctx->tile_nt[pi][li] = 0;
         ctx->tile_ms[pi][li] = 0.0;
+        ctx->tile_tc_nt[li] = 0;
+        ctx->tile_tc_ms[li] = 0.0;
         try {
             ensure_tuned(ctx, R, s);
         } catch (...) {
@@ -2410,9 +2455,10 @@ hdg_status hdg_tune_batched(hdg_ctx *ctx, int nrhs, int *rows_per_thread, int *t
         ctx->tile_force_rb = frb;
         ctx->tile_force_nt = fnt;
         drop_graph(ctx);
-        if (rows_per_thread) *rows_per_thread = ctx->tile_rb[pi][li];
-        if (threads) *threads = ctx->tile_nt[pi][li];
-        if (ms) *ms = ctx->tile_ms[pi][li];
+        // the tensor-core sweep reports 0 rows per thread and its block size
+        if (rows_per_thread) *rows_per_thread = tc ? 0 : ctx->tile_rb[pi][li];
+        if (threads) *threads = tc ? ctx->tile_tc_nt[li] : ctx->tile_nt[pi][li];
+        if (ms) *ms = tc ? ctx->tile_tc_ms[li] : ctx->tile_ms[pi][li];
     });
 }
 

@@ -328,6 +328,8 @@ struct hdg_ctx {
     int tile_force_rb = 0, tile_force_nt = 0;
     int tile_rb[2][7] = {}, tile_nt[2][7] = {};
     double tile_ms[2][7] = {};
+    int tile_tc_nt[7] = {};                  // tensor-core sweep: threads per block per log2 R (autotuned)
+    double tile_tc_ms[7] = {};
     hdg::DBuf<double> tune_buf;
     long long pcm_kernels = 0;
     hdg::DBuf<double> pcm_in, pcm_out;
@@ -485,7 +487,7 @@ cudaError_t launch_apply_m(const DevLevel &L, const DevOperator &op, int R, cons
 // copies (op.h_fmt), dpf = 8 and R in {16, 32, 64}
 bool gs_tc_supported(const DevLevel &L, const DevOperator &op, int R);
 cudaError_t launch_gs_colour_tc(const DevLevel &L, const DevOperator &op, int R, int colour, const float *g,
-                                float *u, cudaStream_t s);
+                                float *u, cudaStream_t s, int nt = 0);   // nt: threads per block, 128 or 256 (0)
 int log2_width(int R);
 template <class T>
 cudaError_t launch_gs_colour_m(const DevLevel &L, const DevOperator &op, int R, const T *A, const T *Pinv,

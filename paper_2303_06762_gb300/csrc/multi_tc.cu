@@ -27,7 +27,6 @@ namespace {
 
 constexpr int TC_DPF = 8;
 constexpr int TC_NLOC = 3 * TC_DPF;
-constexpr int TC_THREADS = 256;
 constexpr int TC_XS = TC_NLOC;   // 16-bit values per Xᵀ row (48-byte rows: conflict-free ldmatrix)
 
 template <class H>
@@ -123,8 +122,10 @@ __host__ __device__ inline TcLayout tc_layout(int pf_max, int pc_max, int np_max
     return o;
 }
 
-template <class H>
-__global__ void __launch_bounds__(TC_THREADS)
+// NT: threads per block (128 or 256, chosen by the autotuner); a multiple of R, so that each
+// thread's column r = tid mod R stays fixed in the column-maximum pass
+template <class H, int NT>
+__global__ void __launch_bounds__(NT)
 gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const int *__restrict__ patch_nf,
              const int *__restrict__ patch_facets, const int *__restrict__ patch_nc,
              const int *__restrict__ patch_cells, const int *__restrict__ slot_src,
@@ -153,28 +154,28 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
     const int p = p0 + blockIdx.x;
     if (p >= p1) return;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = TC_THREADS / 32;
+    constexpr int NW = NT / 32;
     const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
 
-    for (int i = tid; i < ncell * NLOC; i += TC_THREADS) {
+    for (int i = tid; i < ncell * NLOC; i += NT) {
         const int si = i / NLOC, l = i - si * NLOC;
         const int c = patch_cells[(size_t)p * pc_max + si];
         const int j = cell_int[3 * c + l / DPF];
         roff[i] = j >= 0 ? (j * DPF + l % DPF) << lgR : -1;
     }
-    for (int i = tid; i < R; i += TC_THREADS) cmx[i] = rmx[i] = 0u;
-    for (int js = tid; js < nf; js += TC_THREADS) rowF[js] = patch_facets[(size_t)p * pf_max + js];
-    for (int sl = tid; sl < 2 * nf; sl += TC_THREADS) sslot[sl] = slot_src[(size_t)p * pf_max * 2 + sl] >> 2;
+    for (int i = tid; i < R; i += NT) cmx[i] = rmx[i] = 0u;
+    for (int js = tid; js < nf; js += NT) rowF[js] = patch_facets[(size_t)p * pf_max + js];
+    for (int sl = tid; sl < 2 * nf; sl += NT) sslot[sl] = slot_src[(size_t)p * pf_max * 2 + sl] >> 2;
     // facet row blocks of the 2 nf slots (slot js*2 + q), 16-byte vectors
     constexpr int VB = RBK * 2 / 16;
-    for (int i = tid; i < 2 * nf * VB; i += TC_THREADS) {
+    for (int i = tid; i < 2 * nf * VB; i += NT) {
         const int sl = i / VB, v = i - sl * VB;
         const int src = slot_src[(size_t)p * pf_max * 2 + sl];
         const int c = patch_cells[(size_t)p * pc_max + (src >> 2)];
         reinterpret_cast<uint4 *>(AS + (size_t)sl * RBK)[v] =
             reinterpret_cast<const uint4 *>(Ah + (size_t)c * NLOC * NLOC + (size_t)(src & 3) * RBK)[v];
     }
-    for (int i = tid; i < 2 * nf * DPF; i += TC_THREADS) {
+    for (int i = tid; i < 2 * nf * DPF; i += NT) {
         const int sl = i / DPF, d = i - sl * DPF;
         const int src = slot_src[(size_t)p * pf_max * 2 + sl];
         const int c = patch_cells[(size_t)p * pc_max + (src >> 2)];
@@ -182,12 +183,12 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
     }
     // the inverse's rows j < np (np_max values each, stored transposed: [j][n] = (A_ss⁻¹)_nj)
     const int pv = np_max / 8;
-    for (int i = tid; i < np * pv; i += TC_THREADS) {
+    for (int i = tid; i < np * pv; i += NT) {
         const int j = i / pv, v = i - j * pv;
         reinterpret_cast<uint4 *>(PS + (size_t)j * psd)[v] =
             reinterpret_cast<const uint4 *>(Ph + (size_t)p * np_max * np_max + (size_t)j * np_max)[v];
     }
-    for (int i = tid; i < np; i += TC_THREADS) psc[i] = Ph_s[(size_t)p * np_max + i];
+    for (int i = tid; i < np; i += NT) psc[i] = Ph_s[(size_t)p * np_max + i];
     __syncthreads();
 
     // gathered unknowns of the star: column maxima (the thread's column is fixed, since
@@ -196,20 +197,20 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
     const int nx = (ncell * NLOC) << lgR;
     {
         float m = 0.f;
-        for (int t = tid; t < nx; t += TC_THREADS) {
+        for (int t = tid; t < nx; t += NT) {
             const int o = roff[t >> lgR];
             if (o >= 0) m = fmaxf(m, fabsf(u[o + (t & (R - 1))]));
         }
         atomicMax(&cmx[tid & (R - 1)], __float_as_uint(m));
     }
     __syncthreads();
-    for (int r = tid; r < R; r += TC_THREADS) {
+    for (int r = tid; r < R; r += NT) {
         float sc;
         xsc[R + r] = col_scale(cmx[r], sc);
         xsc[r] = sc;
     }
     __syncthreads();
-    for (int t = tid; t < nx; t += TC_THREADS) {
+    for (int t = tid; t < nx; t += NT) {
         const int r = t & (R - 1), sl = t >> lgR, si = sl / NLOC, l = sl - si * NLOC;
         const int o = roff[sl];
         const float v = o >= 0 ? u[o + r] : 0.f;
@@ -258,13 +259,13 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
         }
     }
     __syncthreads();
-    for (int r = tid; r < R; r += TC_THREADS) {
+    for (int r = tid; r < R; r += NT) {
         float sc;
         rsc[R + r] = col_scale(rmx[r], sc);
         rsc[r] = sc;
     }
     __syncthreads();
-    for (int t = tid; t < (np << lgR); t += TC_THREADS) {
+    for (int t = tid; t < (np << lgR); t += NT) {
         const int j = t >> lgR, r = t & (R - 1);
         RS[(size_t)r * psd + j] = Mma<H>::from(RF[t] * rsc[R + r]);
     }
@@ -302,16 +303,16 @@ gs_tc_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const 
     }
 }
 
-template <class H>
+template <class H, int NT>
 cudaError_t gs_tc_launch(const DevLevel &L, const DevOperator &op, int R, int colour, const float *g, float *u,
                          cudaStream_t s) {
     const int p0 = L.colour_ptr[colour], p1 = L.colour_ptr[colour + 1];
     if (p1 <= p0) return cudaSuccess;
     const size_t smem = tc_layout(L.pf_max, L.pc_max, op.np_max, R).total;
-    cudaError_t e = cudaFuncSetAttribute(gs_tc_kernel<H>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(gs_tc_kernel<H, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launches(1);
-    gs_tc_kernel<H><<<p1 - p0, TC_THREADS, smem, s>>>(
+    gs_tc_kernel<H, NT><<<p1 - p0, NT, smem, s>>>(
         p0, p1, L.pf_max, L.pc_max, op.np_max, log2_width(R), L.patch_nf.p, L.patch_facets.p, L.patch_nc.p,
         L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p, reinterpret_cast<const H *>(op.Ah.p), op.Ah_s.p,
         reinterpret_cast<const H *>(op.Pinvh.p), op.Pinvh_s.p, g, u);
@@ -327,10 +328,14 @@ bool gs_tc_supported(const DevLevel &L, const DevOperator &op, int R) {
 }
 
 cudaError_t launch_gs_colour_tc(const DevLevel &L, const DevOperator &op, int R, int colour, const float *g,
-                                float *u, cudaStream_t s) {
+                                float *u, cudaStream_t s, int nt) {
     if (!gs_tc_supported(L, op, R)) return cudaErrorInvalidValue;
-    return op.h_fmt == HDG_MIXED_BF16 ? gs_tc_launch<__nv_bfloat16>(L, op, R, colour, g, u, s)
-                                      : gs_tc_launch<__half>(L, op, R, colour, g, u, s);
+    const bool bf = op.h_fmt == HDG_MIXED_BF16;
+    if (nt == 128) return bf ? gs_tc_launch<__nv_bfloat16, 128>(L, op, R, colour, g, u, s)
+                             : gs_tc_launch<__half, 128>(L, op, R, colour, g, u, s);
+    if (nt != 0 && nt != 256) return cudaErrorInvalidValue;
+    return bf ? gs_tc_launch<__nv_bfloat16, 256>(L, op, R, colour, g, u, s)
+              : gs_tc_launch<__half, 256>(L, op, R, colour, g, u, s);
 }
 
 } // namespace hdg

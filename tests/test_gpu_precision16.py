@@ -231,3 +231,23 @@ def test_batched_tensor_core_columns_are_independent(precision):
     Up = X[perm].contiguous()
     hdg.hdg_smooth_multi(ctx, -1, G[perm].contiguous(), Up, 2, False)
     assert np.array_equal(host(Up), host(U)[perm.cpu().numpy()])
+
+
+@pytest.mark.parametrize("precision", [2, 3])
+def test_tensor_core_block_size_autotuned_and_bitwise_equal(precision):
+    """The tensor-core sweep's block size (128 or 256 threads) is chosen by the autotuner
+    (hdg_tune_batched reports 0 rows per thread and the block size) and does not change the
+    result: both block sizes give bitwise the same preconditioner output."""
+    hdg = _hdg()
+    k, nrhs = 3, 32
+    ctx, F, ts, ps, fvs = _multi_case(k, precision, nrhs)
+    rb, nt, ms = hdg.hdg_tune_batched(ctx, nrhs)
+    assert rb == 0 and nt in (128, 256) and ms > 0
+    gen = torch.Generator(device=DEV).manual_seed(7)
+    X = torch.randn(F.shape, dtype=torch.float64, device=DEV, generator=gen)
+    outs = []
+    for threads in (128, 256):
+        hdg.hdg_set_batched_tile(ctx, 1, threads)
+        outs.append(host(hdg.hdg_precond_apply_multi(ctx, X)))
+    hdg.hdg_set_batched_tile(ctx, 0, 0)
+    assert np.array_equal(outs[0], outs[1])
