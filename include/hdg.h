@@ -51,10 +51,12 @@
  * inner, n_lat = (q+1)(q+2)(q+3)/6.  The lowest-order levels carry 3 unknowns
  * per face.  Calls available on tetrahedra: hdg_setup_mesh_hierarchy,
  * hdg_check_hierarchy, hdg_condense (FP64 or FP32 preconditioner, block GS,
- * scalar nu, no convection or Dirichlet data, k <= 3), hdg_load, hdg_apply,
+ * scalar nu, no convection, k <= 3; Dirichlet data as faces' normal moments
+ * and t1, t2 coefficients), hdg_load, hdg_apply,
  * hdg_level_apply, hdg_smooth, hdg_prolong_add, hdg_restrict,
  * hdg_coarse_solve, hdg_mg_h, hdg_precond_apply, hdg_get_element_matrices,
- * hdg_solve, hdg_recover, hdg_get_sizes; the others return
+ * hdg_solve, hdg_recover, hdg_boundary_facets (sorted vertex triples),
+ * hdg_get_sizes; the others return
  * HDG_ERR_UNSUPPORTED.
  *
  * Memory: pointers documented "device" must be device memory on the
@@ -466,7 +468,8 @@ hdg_status hdg_newton(hdg_ctx *ctx, const hdg_params *params, const double *forc
 
 /* The finest level's boundary facets in facet order (lexicographic in the
  * sorted global vertex pair), the order of hdg_params.dirichlet: pairs (host,
- * [n_boundary_facets][2]) receives each facet's sorted global vertex ids. */
+ * [n_boundary_facets][2]) receives each facet's sorted global vertex ids; on
+ * tetrahedra [n_boundary_facets][3], the sorted vertex triples of the faces. */
 hdg_status hdg_boundary_facets(const hdg_ctx *ctx, int32_t *pairs);
 
 /* Sizes after hdg_setup_mesh_hierarchy (k-dependent fields after hdg_condense). */

@@ -541,10 +541,10 @@ def hdg_recover(ctx: Context, u, forcing=None, stream=None):
 
 
 def hdg_boundary_facets(ctx: Context) -> np.ndarray:
-    """Sorted global vertex pairs of the finest level's boundary facets, the order of the
-    Dirichlet data, shape [n_boundary_facets, 2] (int32)."""
+    """Sorted global vertex pairs (triples on tetrahedra) of the finest level's boundary facets,
+    the order of the Dirichlet data, shape [n_boundary_facets, dim] (int32)."""
     n = ctx.sizes().n_boundary_facets
-    out = np.zeros((n, 2), dtype=np.int32)
+    out = np.zeros((n, getattr(ctx, "dim", 2)), dtype=np.int32)
     ctx.check(load_library().hdg_boundary_facets(ctx.handle, out.ctypes.data_as(ctypes.c_void_p)))
     return out
 

@@ -647,6 +647,7 @@ void load_impl(hdg_ctx *ctx, const double *forcing, double *rhs_out, cudaStream_
                             ctx->prm.gamma, forcing, nullptr, nullptr, ctx->opk.Fel.p, ctx->c3_scratch.p, blocks,
                             ctx->status_flag.p, s));
         CK(launch_assemble_load(LJ, ctx->opk, rhs_out, s));
+        if (ctx->has_dir) CK(launch_dirichlet_load(LJ, ctx->opk, ctx->dir_x.p, rhs_out, s));
         return;
     }
     CK(launch_condense(ctx->prm.k, LJ, ctx->refk_dev.p, ctx->refk, ctx->prm.nu, cell_nu_of(ctx, ctx->n_levels - 1),
@@ -1611,7 +1612,16 @@ hdg_status hdg_get_sizes(const hdg_ctx *cctx, hdg_sizes *out) {
 hdg_status hdg_boundary_facets(const hdg_ctx *ctx, int32_t *pairs) {
     if (!ctx || !pairs) return HDG_ERR_INVALID_ARG;
     if (ctx->n_levels < 1) return HDG_ERR_STATE;
-    if (ctx->dim != 2) return HDG_ERR_UNSUPPORTED;
+    if (ctx->dim == 3) {
+        const HostLevel3 &H = ctx->H3[ctx->n_levels - 1];
+        int64_t b = 0;
+        for (int64_t F = 0; F < H.nf; ++F)
+            if (H.interior_index[F] < 0) {
+                for (int q = 0; q < 3; ++q) pairs[3 * b + q] = H.face_v[3 * F + q];
+                ++b;
+            }
+        return HDG_OK;
+    }
     const HostLevel &H = ctx->H[ctx->n_levels - 1];
     int64_t b = 0;
     for (int64_t F = 0; F < H.nf; ++F)
@@ -1794,6 +1804,15 @@ static void upload_levels_3d(hdg_ctx *ctx) {
         upload(ctx, L.cell_int, ci);
         upload(ctx, L.facet_adj, fa);
         L.n_bnd = H.nf - H.n_int;
+        if (l == ctx->n_levels - 1) {
+            // boundary faces in face order (inhomogeneous Dirichlet data of the finest level)
+            std::vector<int32_t> bidx(H.nf, -1), cb(4 * H.nc, -1);
+            int64_t nb = 0;
+            for (int64_t F = 0; F < H.nf; ++F)
+                if (H.interior_index[F] < 0) bidx[F] = (int32_t)nb++;
+            for (int64_t c = 0; c < 4 * H.nc; ++c) cb[c] = bidx[H.cell_face[c]];
+            upload(ctx, L.cell_bnd, cb);
+        }
         dalloc(ctx, L.cell_d, 4 * H.nc);
         dalloc(ctx, L.cell_area, H.nc);
         L.n_patches = H.n_patches;
@@ -1919,20 +1938,31 @@ static void condense_3d(hdg_ctx *ctx, const hdg_params *prm, const double *forci
     REQUIRE(prm->vcycle_growth >= 1 && prm->vcycle_growth <= 4, "vcycle_growth out of range 1..4");
     REQUIRE(prm->hp_additive == 0 || prm->hp_additive == 1, "hp_additive must be 0 or 1");
     if (!(prm->precision == HDG_FP64 || prm->precision == HDG_MIXED_FP32) || prm->smoother != 0 ||
-        prm->fused_coarse_cells != 0 || prm->nu_elem || prm->conv || prm->newton_u || prm->dirichlet) {
-        ctx->err = "3D supports the generalized Stokes operator with a scalar viscosity, homogeneous Dirichlet "
-                   "data, block GS and the FP64 or FP32 preconditioner";
+        prm->fused_coarse_cells != 0 || prm->nu_elem || prm->conv || prm->newton_u) {
+        ctx->err = "3D supports the generalized Stokes operator with a scalar viscosity, Dirichlet data, block GS "
+                   "and the FP64 or FP32 preconditioner";
         throw Fail{HDG_ERR_UNSUPPORTED};
     }
     REQUIRE(3 * ctx->L[0].n_int <= MAX_COARSE_DOFS,
             "coarsest level has " + std::to_string(3 * ctx->L[0].n_int) +
                 " unknowns; the dense coarse solve allows at most " + std::to_string(MAX_COARSE_DOFS));
     ctx->prm = *prm;
-    ctx->has_conv = ctx->has_newton = ctx->has_dir = false;
+    ctx->has_conv = ctx->has_newton = false;
     condense_all_3d(ctx, forcing, s);
+    // inhomogeneous Dirichlet data: a copy, the cells' boundary fluxes and the load coupling
+    DevLevel &LJ = ctx->L[ctx->n_levels - 1];
+    ctx->has_dir = prm->dirichlet != nullptr;
+    if (ctx->has_dir) {
+        const size_t nb = (size_t)LJ.n_bnd * dpf3(prm->k);
+        dalloc(ctx, ctx->dir_x, std::max<size_t>(nb, 1));
+        CK(cudaMemcpyAsync(ctx->dir_x.p, prm->dirichlet, sizeof(double) * nb, cudaMemcpyDeviceToDevice, s));
+        dalloc(ctx, ctx->dir_flux, std::max<int64_t>(LJ.nc, 1));
+        CK(launch_boundary_flux(LJ, dpf3(prm->k), ctx->dir_x.p, ctx->dir_flux.p, s));
+    }
     if (rhs_out) {
-        if (forcing) CK(launch_assemble_load(ctx->L[ctx->n_levels - 1], ctx->opk, rhs_out, s));
+        if (forcing) CK(launch_assemble_load(LJ, ctx->opk, rhs_out, s));
         else CK(cudaMemsetAsync(rhs_out, 0, sizeof(double) * ctx->n_dof, s));
+        if (ctx->has_dir) CK(launch_dirichlet_load(LJ, ctx->opk, ctx->dir_x.p, rhs_out, s));
     }
 }
 
@@ -2214,6 +2244,10 @@ hdg_status hdg_recover(hdg_ctx *ctx, const double *u, const double *forcing, dou
             Recover3 rec;
             rec.x = u;
             rec.cell_int = LJ.cell_int.p;
+            if (ctx->has_dir) {
+                rec.cell_bnd = LJ.cell_bnd.p;
+                rec.xD = ctx->dir_x.p;
+            }
             rec.L = L_out;
             rec.ulat = ulat_out;
             CK(launch_condense3(ctx->prm.k, LJ, ctx->ref3k_dev.p, ctx->ref3k, ctx->prm.nu, nullptr, ctx->prm.beta,

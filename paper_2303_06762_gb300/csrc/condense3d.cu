@@ -212,7 +212,8 @@ condense3_kernel(int64_t nc, const double *__restrict__ coords, const int *__res
             // values rotated to the reference face basis (x_ref = T^T x)
             for (int l = tid; l < NLOC; l += nt) {
                 const int j = rec.cell_int[4 * c + l / DPF];
-                xl[l] = j >= 0 ? rec.x[(size_t)j * DPF + l % DPF] : 0.0;
+                const int b = rec.xD ? rec.cell_bnd[4 * c + l / DPF] : -1;
+                xl[l] = j >= 0 ? rec.x[(size_t)j * DPF + l % DPF] : b >= 0 ? rec.xD[(size_t)b * DPF + l % DPF] : 0.0;
             }
             __syncthreads();
             for (int x = tid; x < NUH; x += nt) {

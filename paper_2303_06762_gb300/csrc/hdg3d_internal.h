@@ -33,6 +33,8 @@ size_t condense3_scratch_doubles(int k, int blocks);
 struct Recover3 {
     const double *x = nullptr;
     const int *cell_int = nullptr;
+    const int *cell_bnd = nullptr;    // with xD: boundary face number of each local face or -1
+    const double *xD = nullptr;       // Dirichlet data [n_boundary][dpf], or null (homogeneous)
     double *rt = nullptr, *L = nullptr, *ulat = nullptr;
 };
 cudaError_t launch_condense3(int k, const DevLevel &L, const double *ref, const RefTables3 &rt, double nu,

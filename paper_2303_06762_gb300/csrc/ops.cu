@@ -1314,11 +1314,11 @@ cudaError_t launch_apply_t(const DevLevel &L, const DevOperator &op, const doubl
 // ---------------------------------------------------------------- inhomogeneous Dirichlet data
 // F_i -= sum over the facet's cells of A_K[row i, boundary columns] u_D (pull style, like the
 // apply: each interior facet row reads its two cells' row blocks at the boundary facets' columns)
-template <int DPF>
+template <int DPF, int NFC>
 __global__ void dirichlet_load_kernel(int64_t n_int, const int *__restrict__ facet_adj,
                                       const int *__restrict__ cell_bnd, const double *__restrict__ A,
                                       const double *__restrict__ xD, double *__restrict__ F) {
-    constexpr int NLOC = 3 * DPF;
+    constexpr int NLOC = NFC * DPF;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (idx >= n_int * DPF) return;
     const int64_t i = idx / DPF;
@@ -1329,8 +1329,8 @@ __global__ void dirichlet_load_kernel(int64_t n_int, const int *__restrict__ fac
         if (adj < 0) continue;
         const int c = adj >> 2, lf = adj & 3;
         const double *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d;
-        for (int f2 = 0; f2 < 3; ++f2) {
-            const int b = cell_bnd[3 * c + f2];
+        for (int f2 = 0; f2 < NFC; ++f2) {
+            const int b = cell_bnd[NFC * c + f2];
             if (b < 0) continue;
             for (int d2 = 0; d2 < DPF; ++d2) acc += Ac[(f2 * DPF + d2) * DPF] * xD[(size_t)b * DPF + d2];
         }
@@ -1339,15 +1339,15 @@ __global__ void dirichlet_load_kernel(int64_t n_int, const int *__restrict__ fac
 }
 
 // per cell, the flux of the Dirichlet data through its boundary facets: sum of d_f (normal moment 0)
-__global__ void boundary_flux_kernel(int64_t nc, int dpf, const int *__restrict__ cell_bnd,
+__global__ void boundary_flux_kernel(int64_t nc, int dpf, int nfc, const int *__restrict__ cell_bnd,
                                      const double *__restrict__ cell_d, const double *__restrict__ xD,
                                      double *__restrict__ bflux) {
     const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (c >= nc) return;
     double s = 0.0;
-    for (int f = 0; f < 3; ++f) {
-        const int b = cell_bnd[3 * c + f];
-        if (b >= 0) s += cell_d[3 * c + f] * xD[(size_t)b * dpf];
+    for (int f = 0; f < nfc; ++f) {
+        const int b = cell_bnd[nfc * c + f];
+        if (b >= 0) s += cell_d[nfc * c + f] * xD[(size_t)b * dpf];
     }
     bflux[c] = s;
 }
@@ -1357,9 +1357,19 @@ cudaError_t launch_dirichlet_load(const DevLevel &L, const DevOperator &op, cons
     const int64_t n = L.n_int * op.dpf;
     if (n == 0) return cudaSuccess;
     note_launches(1);
+    if (L.dim == 3) {
+        switch (op.dpf) {
+#define HDG_DIR3(D) \
+        case D: dirichlet_load_kernel<D, 4><<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_bnd.p, op.A.p, xD, F); break;
+        HDG_DIR3(3) HDG_DIR3(9) HDG_DIR3(18) HDG_DIR3(30)
+#undef HDG_DIR3
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (op.dpf) {
 #define HDG_DIR(D) \
-    case D: dirichlet_load_kernel<D><<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_bnd.p, op.A.p, xD, F); break;
+    case D: dirichlet_load_kernel<D, 3><<<blocks_for(n, 256), 256, 0, s>>>(L.n_int, L.facet_adj.p, L.cell_bnd.p, op.A.p, xD, F); break;
     HDG_DIR(2) HDG_DIR(4) HDG_DIR(6) HDG_DIR(8) HDG_DIR(10)
 #undef HDG_DIR
     default: return cudaErrorInvalidValue;
@@ -1370,7 +1380,8 @@ cudaError_t launch_dirichlet_load(const DevLevel &L, const DevOperator &op, cons
 cudaError_t launch_boundary_flux(const DevLevel &L, int dpf, const double *xD, double *bflux, cudaStream_t s) {
     if (L.nc == 0) return cudaSuccess;
     note_launches(1);
-    boundary_flux_kernel<<<blocks_for(L.nc, 256), 256, 0, s>>>(L.nc, dpf, L.cell_bnd.p, L.cell_d.p, xD, bflux);
+    boundary_flux_kernel<<<blocks_for(L.nc, 256), 256, 0, s>>>(L.nc, dpf, L.dim + 1, L.cell_bnd.p, L.cell_d.p, xD,
+                                                                bflux);
     return cudaGetLastError();
 }
 
