@@ -55,7 +55,8 @@
  * and t1, t2 coefficients), hdg_load, hdg_apply,
  * hdg_level_apply, hdg_smooth, hdg_prolong_add, hdg_restrict,
  * hdg_coarse_solve, hdg_mg_h, hdg_precond_apply, hdg_get_element_matrices,
- * hdg_solve, hdg_recover, hdg_boundary_facets (sorted vertex triples),
+ * hdg_solve, hdg_recover, hdg_postprocess (u* in [P^{k+1}]^3 at the lattice,
+ * [n_cells][n_lat][3]), hdg_boundary_facets (sorted vertex triples),
  * hdg_get_sizes; the others return
  * HDG_ERR_UNSUPPORTED.
  *

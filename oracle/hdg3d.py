@@ -185,6 +185,35 @@ class HDG3D(HDG):
         pv[:, 0] = 1.0
         return L, u, divu, pv @ pc
 
+    def ustar_cell(self, c: int, coeffs, nq: Optional[int] = None) -> np.ndarray:
+        """Post-processed u* ∈ [P^{k+1}]³ on cell c (eq. stPost, read with L = −ν∇u):
+        (∇u*, ∇v)_K = (−ν⁻¹L_h, ∇v)_K for v ∈ P^{k+1} except the constant, whose equation is
+        replaced by (u*, 1)_K = (u_h, 1)_K.  Coefficients over the cell's monomials of degree
+        <= k+1, shape (n_mono, 3)."""
+        k = self.k
+        el = self.cells[c].el
+        xq, wq = tetrahedron_points(el.X, nq or (k + 4))
+        L, uh, _, _ = self.fields_at(c, coeffs, xq)
+        Gm = el.mono_grad(xq, k + 1)
+        Mo = el.mono(xq, k + 1)
+        S = np.einsum("q,qid,qjd->ij", wq, Gm, Gm)
+        S[0, :] = wq @ Mo
+        us = np.zeros((Mo.shape[1], 3))
+        for a in range(3):
+            r = np.einsum("q,qid,qd->i", wq, Gm, -L[:, a, :] / self.nu_elem[c])
+            r[0] = wq @ uh[:, a]
+            us[:, a] = np.linalg.solve(S, r)
+        return us
+
+    def postprocess(self, u, p, fvals) -> np.ndarray:
+        """u* at every cell's degree-(k+1) lattice (the forcing layout): (n_cells, n_lat, 3)."""
+        lam = lattice_barycentric_3d(self.k + 1)
+        out = np.zeros((self.topo.n_cells, lam.shape[0], 3))
+        for c in range(self.topo.n_cells):
+            el = self.cells[c].el
+            out[c] = el.mono(lam @ el.X, self.k + 1) @ self.ustar_cell(c, self.recover_cell(c, u, p[c], fvals[c]))
+        return out
+
     def errors(self, u, p, fvals, sol, nq: Optional[int] = None):
         """L2 errors of u_h, L_h (L = −ν∇u), p_h (both mean-free) and ‖div u_h‖."""
         nq = nq or (self.k + 4)

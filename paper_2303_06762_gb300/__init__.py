@@ -550,11 +550,11 @@ def hdg_boundary_facets(ctx: Context) -> np.ndarray:
 
 
 def hdg_postprocess(ctx: Context, u, forcing=None, stream=None):
-    """u* of eq. stPost at each cell's degree-(k+1) lattice, shape [n_cells, n_lat, 2]."""
+    """u* of eq. stPost at each cell's degree-(k+1) lattice, shape [n_cells, n_lat, d]."""
     import torch
     s = ctx.sizes()
-    k = s.k
-    out = torch.empty((s.n_cells, (k + 2) * (k + 3) // 2, 2), dtype=torch.float64, device=u.device)
+    d = getattr(ctx, "dim", 2)
+    out = torch.empty((s.n_cells, s.n_lat, d), dtype=torch.float64, device=u.device)
     ctx.check(load_library().hdg_postprocess(ctx.handle, _ptr(u), _ptr(forcing), _ptr(out), _stream(stream)))
     return out
 

@@ -2270,12 +2270,43 @@ hdg_status hdg_postprocess(hdg_ctx *ctx, const double *u, const double *forcing,
                            hdg_stream_t stream) {
     if (!ctx) return HDG_ERR_INVALID_ARG;
     return guard(ctx, [&] {
-        NEED_2D("hdg_postprocess");
         NEED_CONDENSED();
         REQUIRE(u && ustar_out, "null skeleton vector or output");
         cudaStream_t s = (cudaStream_t)stream;
         const int k = ctx->prm.k;
         DevLevel &LJ = ctx->L[ctx->n_levels - 1];
+        if (ctx->dim == 3) {
+            // recovery (L_h over the orthonormal P^k basis, u_h at the lattice), then u* per cell
+            const int64_t nlat = (k + 2) * (k + 3) * (k + 4) / 6, npk = (k + 1) * (k + 2) * (k + 3) / 6;
+            if (ctx->post_k != 100 + k || !ctx->post_tabs.p) {
+                std::vector<double> t(ctx->ref3k.P1);
+                t.insert(t.end(), ctx->ref3k.P2.begin(), ctx->ref3k.P2.end());
+                t.insert(t.end(), ctx->ref3k.P3.begin(), ctx->ref3k.P3.end());
+                dfree(ctx->post_tabs);
+                upload(ctx, ctx->post_tabs, t);
+                ctx->post_k = 100 + k;
+            }
+            dalloc(ctx, ctx->rec_L, (size_t)LJ.nc * 9 * npk);
+            dalloc(ctx, ctx->rec_ulat, (size_t)LJ.nc * 3 * nlat);
+            int sms = 0;
+            CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+            Recover3 rec;
+            rec.x = u;
+            rec.cell_int = LJ.cell_int.p;
+            if (ctx->has_dir) {
+                rec.cell_bnd = LJ.cell_bnd.p;
+                rec.xD = ctx->dir_x.p;
+            }
+            rec.L = ctx->rec_L.p;
+            rec.ulat = ctx->rec_ulat.p;
+            CK(launch_condense3(k, LJ, ctx->ref3k_dev.p, ctx->ref3k, ctx->prm.nu, nullptr, ctx->prm.beta,
+                                ctx->prm.gamma, forcing, nullptr, nullptr, nullptr, ctx->c3_scratch.p,
+                                2 * std::max(sms, 1), ctx->status_flag.p, s, rec));
+            CK(launch_poststar3(k, LJ, ctx->prm.nu, ctx->post_tabs.p, (int)nlat, (int)npk, ctx->rec_L.p,
+                                ctx->rec_ulat.p, ustar_out, s));
+            check_flag(ctx, s);
+            return;
+        }
         const int64_t nlat = (k + 2) * (k + 3) / 2, npk = (k + 1) * (k + 2) / 2;
         if (ctx->post_k != k || !ctx->post_tabs.p) {
             std::vector<double> t(ctx->refk.P1);

@@ -47,6 +47,10 @@ size_t patch_inverse3_scratch_doubles(const DevLevel &L, const DevOperator &op, 
 cudaError_t launch_patch_inverse3(const DevLevel &L, const DevOperator &op, double *scratch, int blocks, int *flag,
                                   cudaStream_t s);
 
+// post.cu: u* of eq. stPost on tetrahedra at the degree-(k+1) lattice; tabs = P1, P2, P3 packed
+cudaError_t launch_poststar3(int k, const DevLevel &L, double nu, const double *tabs, int nlat, int npk,
+                             const double *Lcoef, const double *ulat, double *out, cudaStream_t s);
+
 // ops3d.cu: hot-path kernels with four faces per cell
 template <class T>
 cudaError_t launch_apply3(const DevLevel &L, int dpf, const T *A, const T *x, const T *g, T *y, cudaStream_t s);

@@ -214,6 +214,9 @@ struct HostTransfer3 {
 struct RefTables3 {
     int k = -1, npk = 0, nrt = 0, nf = 0, nlat = 0;
     std::vector<double> R1, R2, R3, R4, R5, R6, Q, FA, R7;   // R7: phi at the lattice (recovery)
+    // post-processing u* (eq. stPost): P1[(a*3+b)][n][n'] = ∫ d_a lam_n d_b lam_n', P2[j][n][b] = ∫ g_j d_b lam_n,
+    // P3[n] = ∫ lam_n (lam_n the Lagrange basis of P^{k+1} on the lattice)
+    std::vector<double> P1, P2, P3;
 };
 
 struct DevLevel {

@@ -1,4 +1,4 @@
-// Local post-processing of eq. stPost on the device: u* in [P^{k+1}(K)]^2 with
+// Local post-processing of eq. stPost on the device (triangles; tetrahedra below): u* in [P^{k+1}(K)]^2 with
 //   (grad u*, grad v)_K = (-nu^{-1} L_h, grad v)_K  for all v in P^{k+1}(K),
 //   (u*, 1)_K = (u_h, 1)_K,
 // read with L = -nu grad u so that grad u* approximates grad u (the post-processed
@@ -12,7 +12,7 @@
 // unique solution of the bordered system.  The SPD matrix is factored by Cholesky.
 #include <cuda_runtime.h>
 
-#include "hdg_internal.h"
+#include "hdg3d_internal.h"
 
 namespace hdg {
 namespace {
@@ -88,6 +88,89 @@ poststar_kernel(int64_t nc, const int *__restrict__ cells, const double *__restr
     }
 }
 
+// The same on tetrahedra: u* in [P^{k+1}(K)]^3, G = |det J| J^{-1} J^{-T} (3x3), w = 6 P3 (the
+// reference volume is 1/6), L_h with the 9 components (c, e) over the orthonormal P^k basis.
+template <int K>
+__global__ void __launch_bounds__(64)
+poststar3_kernel(int64_t nc, const int *__restrict__ cells, const double *__restrict__ coords, double nu,
+                 const double *__restrict__ P1, const double *__restrict__ P2, const double *__restrict__ P3,
+                 const double *__restrict__ L, const double *__restrict__ ulat, double *__restrict__ out) {
+    constexpr int N = (K + 2) * (K + 3) * (K + 4) / 6;
+    constexpr int NPK = (K + 1) * (K + 2) * (K + 3) / 6;
+    const int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (c >= nc) return;
+    double X[4][3];
+    for (int v = 0; v < 4; ++v)
+        for (int d = 0; d < 3; ++d) X[v][d] = coords[3 * (size_t)cells[4 * c + v] + d];
+    double J[3][3];
+    for (int r = 0; r < 3; ++r)
+        for (int a = 0; a < 3; ++a) J[r][a] = X[a + 1][r] - X[0][r];
+    const double det = J[0][0] * (J[1][1] * J[2][2] - J[1][2] * J[2][1]) -
+                       J[0][1] * (J[1][0] * J[2][2] - J[1][2] * J[2][0]) +
+                       J[0][2] * (J[1][0] * J[2][1] - J[1][1] * J[2][0]);
+    const double adet = fabs(det), id = 1.0 / det;
+    double Ji[3][3];
+    Ji[0][0] = (J[1][1] * J[2][2] - J[1][2] * J[2][1]) * id;
+    Ji[0][1] = (J[0][2] * J[2][1] - J[0][1] * J[2][2]) * id;
+    Ji[0][2] = (J[0][1] * J[1][2] - J[0][2] * J[1][1]) * id;
+    Ji[1][0] = (J[1][2] * J[2][0] - J[1][0] * J[2][2]) * id;
+    Ji[1][1] = (J[0][0] * J[2][2] - J[0][2] * J[2][0]) * id;
+    Ji[1][2] = (J[0][2] * J[1][0] - J[0][0] * J[1][2]) * id;
+    Ji[2][0] = (J[1][0] * J[2][1] - J[1][1] * J[2][0]) * id;
+    Ji[2][1] = (J[0][1] * J[2][0] - J[0][0] * J[2][1]) * id;
+    Ji[2][2] = (J[0][0] * J[1][1] - J[0][1] * J[1][0]) * id;
+    double G[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) G[a][b] = adet * (Ji[a][0] * Ji[b][0] + Ji[a][1] * Ji[b][1] + Ji[a][2] * Ji[b][2]);
+    double M[N * (N + 1) / 2];
+    double w[N];
+    for (int i = 0; i < N; ++i) w[i] = 6.0 * P3[i];
+    for (int i = 0; i < N; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = w[i] * w[j];
+            for (int ab = 0; ab < 9; ++ab) s += G[ab / 3][ab % 3] * P1[((size_t)ab * N + i) * N + j];
+            M[i * (i + 1) / 2 + j] = s;
+        }
+    for (int j = 0; j < N; ++j) {
+        double d = M[j * (j + 1) / 2 + j];
+        for (int q = 0; q < j; ++q) d -= M[j * (j + 1) / 2 + q] * M[j * (j + 1) / 2 + q];
+        d = sqrt(fmax(d, 1e-300));
+        M[j * (j + 1) / 2 + j] = d;
+        for (int i = j + 1; i < N; ++i) {
+            double s = M[i * (i + 1) / 2 + j];
+            for (int q = 0; q < j; ++q) s -= M[i * (i + 1) / 2 + q] * M[j * (j + 1) / 2 + q];
+            M[i * (i + 1) / 2 + j] = s / d;
+        }
+    }
+    const double *Lc = L + (size_t)c * 9 * NPK;
+    for (int a = 0; a < 3; ++a) {
+        double mean = 0.0;
+        for (int n = 0; n < N; ++n) mean += w[n] * ulat[((size_t)c * N + n) * 3 + a];
+        double y[N];
+        for (int i = 0; i < N; ++i) {
+            double s = 0.0;
+            for (int j = 0; j < NPK; ++j)
+                for (int b = 0; b < 3; ++b) {
+                    const double coef = Lc[(3 * a + 0) * NPK + j] * Ji[b][0] + Lc[(3 * a + 1) * NPK + j] * Ji[b][1] +
+                                        Lc[(3 * a + 2) * NPK + j] * Ji[b][2];
+                    s += coef * P2[((size_t)j * N + i) * 3 + b];
+                }
+            y[i] = -adet * s / nu + w[i] * mean;
+        }
+        for (int i = 0; i < N; ++i) {
+            double s = y[i];
+            for (int q = 0; q < i; ++q) s -= M[i * (i + 1) / 2 + q] * y[q];
+            y[i] = s / M[i * (i + 1) / 2 + i];
+        }
+        for (int i = N - 1; i >= 0; --i) {
+            double s = y[i];
+            for (int q = i + 1; q < N; ++q) s -= M[q * (q + 1) / 2 + i] * y[q];
+            y[i] = s / M[i * (i + 1) / 2 + i];
+        }
+        for (int n = 0; n < N; ++n) out[((size_t)c * N + n) * 3 + a] = y[n];
+    }
+}
+
 } // namespace
 
 cudaError_t launch_poststar(int k, const DevLevel &L, double nu, const double *nu_cell, const double *tabs,
@@ -104,6 +187,24 @@ cudaError_t launch_poststar(int k, const DevLevel &L, double nu, const double *n
         break;
         HDG_POST(0) HDG_POST(1) HDG_POST(2) HDG_POST(3) HDG_POST(4)
 #undef HDG_POST
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_poststar3(int k, const DevLevel &L, double nu, const double *tabs, int nlat, int npk,
+                             const double *Lcoef, const double *ulat, double *out, cudaStream_t s) {
+    if (L.nc == 0) return cudaSuccess;
+    const double *P1 = tabs, *P2 = P1 + (size_t)9 * nlat * nlat, *P3 = P2 + (size_t)npk * nlat * 3;
+    const unsigned nb = (unsigned)((L.nc + 63) / 64);
+    note_launches(1);
+    switch (k) {
+#define HDG_POST3(K)                                                                                          \
+    case K:                                                                                                   \
+        poststar3_kernel<K><<<nb, 64, 0, s>>>(L.nc, L.cells.p, L.coords.p, nu, P1, P2, P3, Lcoef, ulat, out); \
+        break;
+        HDG_POST3(0) HDG_POST3(1) HDG_POST3(2) HDG_POST3(3)
+#undef HDG_POST3
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

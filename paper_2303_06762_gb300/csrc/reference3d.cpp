@@ -26,6 +26,8 @@
 //                    for every face
 //   FA[f]          = |F^_f|
 //   R7[n][i][a]    = phi_{i,a} at lattice point n
+// Post-processing (eq. stPost, not packed with the above):
+//   P1[(a*3+b)][n][n'] = ∫ d_a lam_n d_b lam_n'   P2[j][n][b] = ∫ g_j d_b lam_n   P3[n] = ∫ lam_n
 #include <algorithm>
 #include <cmath>
 #include <stdexcept>
@@ -383,6 +385,22 @@ void build_reference_tables_3d(int k, RefTables3 &T) {
                 T.Q[((size_t)p * nf + m) * nf + m2] = integrate_face(mul(lp[m], lf[3][m2]), 3) / FA[3];
     }
     T.FA.assign(FA, FA + 4);
+    // post-processing tables of eq. stPost
+    std::vector<std::array<P3, 3>> dlam(nlat);
+    for (int n = 0; n < nlat; ++n)
+        for (int a = 0; a < 3; ++a) dlam[n][a] = deriv(lam[n], a);
+    T.P1.assign((size_t)9 * nlat * nlat, 0.0);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b)
+            for (int n1 = 0; n1 < nlat; ++n1)
+                for (int n2 = 0; n2 < nlat; ++n2)
+                    T.P1[((size_t)(a * 3 + b) * nlat + n1) * nlat + n2] = integrate_tet(mul(dlam[n1][a], dlam[n2][b]));
+    T.P2.assign((size_t)npk * nlat * 3, 0.0);
+    for (int j = 0; j < npk; ++j)
+        for (int n = 0; n < nlat; ++n)
+            for (int b = 0; b < 3; ++b) T.P2[((size_t)j * nlat + n) * 3 + b] = integrate_tet(mul(g[j], dlam[n][b]));
+    T.P3.assign((size_t)nlat, 0.0);
+    for (int n = 0; n < nlat; ++n) T.P3[n] = integrate_tet(lam[n]);
     // R7[n][i][a] = phi_{i,a} at lattice point n (recovery of u_h at the forcing lattice)
     T.R7.assign((size_t)nlat * nrt * 3, 0.0);
     for (int n = 0; n < nlat; ++n)

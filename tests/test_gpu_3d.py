@@ -220,10 +220,11 @@ def _l2_error_3d(coords, cells, ulat, q, u_exact):
 @pytest.mark.parametrize("k", [1, 2])
 def test_convergence_order_at_scale(k):
     """The library's 3D solution of the manufactured problem on n = 4, 8, 16 (levels from 2x2x2):
-    the L2 error of u_h decays at order k + 1 (Section 5.1)."""
+    the L2 error of u_h decays at order k + 1 and that of the post-processed u* (eq. stPost) at
+    order k + 2 (Section 5.1)."""
     hdg = _hdg()
     sol = curl_bubble_3d()
-    errs = []
+    errs, ess = [], []
     for nl in (2, 3, 4):
         ms = unit_cube_hierarchy(2, nl)
         fine = ms[-1]
@@ -234,10 +235,13 @@ def test_convergence_order_at_scale(k):
         assert info["div_l2"] < 1e-8
         _, ul = hdg.hdg_recover(ctx, u, dev(fv))
         errs.append(_l2_error_3d(fine.coords, fine.cells, host(ul), k + 1, sol.u))
+        ess.append(_l2_error_3d(fine.coords, fine.cells, host(hdg.hdg_postprocess(ctx, u, dev(fv))), k + 1, sol.u))
         ctx.close()
     rates = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
-    print(f"3D k={k}: |u - u_h| {errs} rates {rates}")
+    rs = np.log2(np.array(ess[:-1]) / np.array(ess[1:]))
+    print(f"3D k={k}: |u - u_h| {errs} rates {rates}; |u - u*| {ess} rates {rs}")
     assert abs(rates[-1] - (k + 1)) < 0.2
+    assert abs(rs[-1] - (k + 2)) < 0.3 and ess[-1] < errs[-1]
 
 
 def _poly3(x):
@@ -337,3 +341,17 @@ def test_driven_lid_pcg_counts_beside_the_paper():
             ctx.close()
         print(f"3D lid-driven PCG, k={k}: n = 4, 8, 16 {counts}; paper (V-cycle, m=2, beta=0, levels 7..10) {paper[k]}")
         assert all(b - a <= 7 for a, b in zip(counts, counts[1:]))
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_postprocess_matches_oracle(k):
+    """hdg_postprocess on tetrahedra (u* of eq. stPost at the degree-(k+1) lattice) against the
+    oracle's u* from the same skeleton solution, on a jittered, reoriented mesh."""
+    hdg = _hdg()
+    ms, ts, ps, fv, ctx, F = setup3(1, 2, k, nu=0.8, beta=1.0, jitter=0.2, seed=4, shuffle_seed=6)
+    oh = HDG3D(ts[-1], k, nu=0.8, beta=1.0, gamma=100.0)
+    ud, pd = oh.solve_direct(oh.load(fv))
+    us = host(hdg.hdg_postprocess(ctx, dev(ud), dev(fv)))
+    err = rel(us, oh.postprocess(ud, pd, fv))
+    print(f"3D u* k={k}: rel {err:.2e}")
+    assert err < 1e-10

@@ -253,3 +253,19 @@ def test_two_level_robust_in_h_and_gamma():
     vals = list(counts.values())
     assert max(vals) <= 18 and max(vals) - min(vals) <= 4, counts
     assert abs(counts[(4, 1e2)] - counts[(4, 1e4)]) <= 1 and abs(counts[(2, 1e2)] - counts[(2, 1e4)]) <= 1
+
+
+def test_postprocessing_reproduces_quadratic_velocity():
+    """u* of eq. stPost on tetrahedra: with the quadratic divergence-free solution and its boundary
+    data at k = 2 (u_h and L_h exact), u* equals u at every lattice point; with a sign or scale error
+    in the gradient equation or the mean closure it would not."""
+    from workloads.manufactured import lattice_barycentric_3d
+    m = unit_cube_hierarchy(2, 1, jitter=0.2, seed=5, shuffle_seed=3)[-1]
+    t = topo3(m)
+    k = 2
+    h = HDG3D(t, k, nu=NU, beta=BETA, gamma=50.0, dirichlet=dirichlet_data_3d(t, k, _poly))
+    fv = forcing_at_lattice(m.coords, m.cells, k, _poly_forcing)
+    u, p = h.solve_direct(h.load(fv))
+    us = h.postprocess(u, p, fv)
+    xl = np.einsum("pv,cvd->cpd", lattice_barycentric_3d(k + 1), m.coords[m.cells])
+    assert np.abs(us - _poly(xl.reshape(-1, 3)).reshape(xl.shape)).max() < 1e-9
