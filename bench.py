@@ -178,13 +178,19 @@ def ctx_mesh_fine(args):
     return _FINE["mesh"]
 
 
-def sweep_bytes(mesh, k, word, mat_word=None, packed_inverse=False):
+def sweep_bytes(mesh, k, word, mat_word=None, packed_inverse=False, closed_form=False, al_split=False):
     """Bytes one order-k block-GS sweep (all colours) on `mesh` moves as the kernel reads them.
 
     Per vertex patch with nf interior facets (np = nf dpf unknowns) and nc cells:
     residual rows read 2 cells x dpf rows x n_loc columns per facet, the gathered
     cell unknowns nc x n_loc, the patch inverse np^2 (np (np+1)/2 when it is stored
     packed symmetric), the right-hand side np and the update np (read + write).
+    In the closed form u_P = A_PP^-1 (g_P - A_PE u_E) the rows read only the dpf x dpf
+    coupling block with the cell's facet opposite the patch vertex, the gather reads
+    nc x dpf unknowns, and the update is written without being read.  The FP32 kernel's
+    augmented-Lagrangian split (al_split) adds per patch the nc columns of Q (np_max rows each,
+    as copied), one AL-free entry per (facet, cell) slot and the nc outside facets' FP64 flux
+    weights.
     Vectors take `word` bytes per value, matrix entries `mat_word` (default `word`);
     16-bit matrices add one 4-byte scale per row read (2 x dpf per facet and np per
     patch inverse)."""
@@ -203,10 +209,12 @@ def sweep_bytes(mesh, k, word, mat_word=None, packed_inverse=False):
     npp = nf[m] * dpf
     mw = word if mat_word is None else mat_word
     inv = npp * (npp + 1) // 2 if packed_inverse else npp * npp
-    mat = (nf[m] * 2 * dpf * nloc + inv).sum() * mw
-    vec = (ncell[m] * nloc + 3 * npp).sum() * word
+    cols, nx, nvec = (dpf, dpf, 2) if closed_form else (nloc, nloc, 3)
+    mat = (nf[m] * 2 * dpf * cols + inv).sum() * mw
+    vec = (ncell[m] * nx + nvec * npp).sum() * word
     scales = (nf[m] * 2 * dpf + npp).sum() * 4 if mw != word else 0
-    return int(mat + vec + scales)
+    split = ((ncell[m] * npp.max() + 2 * nf[m]).sum() * mw + ncell[m].sum() * 8) if al_split else 0
+    return int(mat + vec + scales + split)
 
 
 def patch_facet_counts(mesh):
@@ -988,7 +996,8 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
     # algorithmic bytes by the scope table's per-unit model (packed symmetric element matrices
     # and patch inverses read once per sweep), and by the kernel's own full-storage access count
     alg = survey_bytes(_FINE["meshes"], k, s_p=2 if half else 4)["A2_sweep"]
-    alg_kernel = sweep_bytes(ctx_mesh_fine(args), k, 4, 2 if half else 4, packed_inverse=not half)
+    alg_kernel = sweep_bytes(ctx_mesh_fine(args), k, 4, 2 if half else 4, packed_inverse=not half,
+                             closed_form=not half, al_split=not half)
     achieved = alg / t_sweep / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     # DRAM bytes of one sweep from an ncu capture of the same kernel on the 128x128, k = 3 case
@@ -1016,12 +1025,12 @@ def roofline(args, ctx, hdg, torch, dev, stream, sizes, precision=None):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of the three colour launches of one
-# order-k sweep of gs_tma_kernel<8, 1> (packed symmetric patch inverses) from an ncu capture on the
-# 128x128, k = 3 case (profiles/ncu_gs_tma_packed_128_k3.md), and that sweep's bytes as the kernel
-# reads them (sweep_bytes with the packed inverse): (80,281,088 + 1,419,008) + (80,281,344 + 1,366,272)
-# + (80,273,152 + 1,462,272) B against 245,180,992 B.
-TMA_SWEEP_TRAFFIC_128 = 245083136
-TMA_SWEEP_KERNEL_BYTES_128 = 245180992
+# order-k sweep of gs_tma_kernel<8, 1> (closed form with the AL split, packed symmetric patch
+# inverses) from an ncu capture on the 128x128, k = 3 case (profiles/ncu_gs_tma_closed_form_128_k3.md),
+# and that sweep's bytes as the kernel reads them (sweep_bytes, packed inverse, closed form, split):
+# (54,397,696 + 115,712) + (54,395,648 + 113,152) + (54,387,200 + 128,768) B against 156,064,048 B.
+TMA_SWEEP_TRAFFIC_128 = 163538176
+TMA_SWEEP_KERNEL_BYTES_128 = 156064048
 
 
 def read_stream_gbs(torch, dev, stream):

@@ -79,6 +79,8 @@ void free_operator(DevOperator &op) {
     dfree(op.Ah_s);
     dfree(op.Pinvh);
     dfree(op.Pinvh_s);
+    dfree(op.swQ);
+    dfree(op.swA00);
     op.h_fmt = 0;
 }
 
@@ -86,6 +88,7 @@ void free_level(DevLevel &L) {
     dfree(L.coords); dfree(L.cells); dfree(L.cell_int); dfree(L.facet_adj); dfree(L.cell_d); dfree(L.cell_nu);
     dfree(L.cell_area); dfree(L.conv_flux); dfree(L.conv_lat); dfree(L.patch_nf); dfree(L.patch_facets); dfree(L.patch_nc);
     dfree(L.patch_cells); dfree(L.patch_slot_src); dfree(L.gs0_table); dfree(L.facet_slot); dfree(L.cell_bnd); dfree(L.patch_cint);
+    dfree(L.patch_cext);
     free_operator(L.op0);
     dfree(L.tr_slots); dfree(L.tr_nbr); dfree(L.tr_children); dfree(L.tr_child_slot);
     dfree(L.tr_fineB); dfree(L.tr_fineB_src); dfree(L.tr_W); dfree(L.tr_H); dfree(L.tr_Wf);
@@ -1432,6 +1435,7 @@ hdg_status hdg_setup_mesh_hierarchy(const hdg_mesh_desc *desc, int device, hdg_c
                         for (int f = 0; f < 3; ++f) pci[((size_t)p * H.pc_max + si) * 3 + f] = ci[3 * c + f];
                     }
                 upload(ctx, L.patch_cint, pci);
+                upload(ctx, L.patch_cext, H.patch_cext);
             }
             {
                 // the two vertex-patch slots of every interior facet (block Jacobi gather)
@@ -1648,6 +1652,20 @@ static void upload_ref(hdg_ctx *ctx, RefTables &t, DBuf<double> &d, int k) {
 // Element matrices, patch inverses, transfer blocks and the coarsest inverse of
 // every level from ctx->prm (and ctx->conv_k / ctx->conv_t for Oseen); the
 // order-k element loads of `forcing` (NULL = zero).
+
+// the FP32 closed-form sweeps' augmented-Lagrangian split (op.swQ, op.swA00) on the 2D level
+// with the outside-facet table, for the FP32 preconditioners; returns whether it was allocated
+static bool alloc_al_split(hdg_ctx *ctx, const DevLevel &L, DevOperator &op) {
+    if (ctx->prm.precision == HDG_FP64 || !L.patch_cext.p || L.n_patches == 0) {
+        dfree(op.swQ);
+        dfree(op.swA00);
+        return false;
+    }
+    dalloc(ctx, op.swQ, (size_t)L.n_patches * L.pc_max * op.np_max);
+    dalloc(ctx, op.swA00, (size_t)L.n_patches * L.pf_max * 2);
+    return true;
+}
+
 static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
     const hdg_params *prm = &ctx->prm;
     ctx->condensed = false;
@@ -1703,6 +1721,8 @@ static void condense_all(hdg_ctx *ctx, const double *forcing, cudaStream_t s) {
                        prm->beta, prm->gamma, forcing, conv_of(ctx), ctx->conv_t, newton_of(ctx), op.A.p, op.Af.p,
                        op.Fel.p, ctx->status_flag.p, RecoverArgs(), s));
     CK(launch_patch_inverse(LJ, op, ctx->has_conv ? 1 : 0, ctx->status_flag.p, s));
+    if (alloc_al_split(ctx, LJ, op))
+        CK(launch_al_split(LJ, op, prm->nu, per_cell ? LJ.cell_nu.p : nullptr, prm->gamma, s));
     op.tma_flag = ctx->wait_flag.p;
     if (!ctx->has_conv && k >= 1 && prm->precision != HDG_FP64) {
         // symmetric patch inverses: the FP32 sweep reads packed triangles (half the bytes)
@@ -1825,6 +1845,7 @@ static void upload_levels_3d(hdg_ctx *ctx) {
         upload(ctx, L.patch_nc, H.patch_nc);
         upload(ctx, L.patch_cells, H.patch_cells);
         upload(ctx, L.patch_slot_src, H.patch_slot_src);
+        upload(ctx, L.patch_cext, H.patch_cext);
         if (l > 0) {
             HostTransfer3 &T = ctx->T3[l];
             L.nc_coarse = T.nc_coarse;

@@ -45,6 +45,9 @@ struct HostLevel {
     std::vector<int32_t> patch_cells;    // n_patches*pc_max
     // for slot j of patch p: the two (star-cell index << 2 | local facet) pairs
     std::vector<int32_t> patch_slot_src; // n_patches*pf_max*2
+    // n_patches*pc_max: the local facet of each star cell opposite the patch vertex (-1 pad),
+    // the one facet of the cell outside the patch
+    std::vector<int32_t> patch_cext;
 };
 
 // transfer data between level l-1 (coarse) and l (fine), stored on level l
@@ -153,6 +156,13 @@ struct DevOperator {
     DBuf<float> Pinvf;
     DBuf<float> Pinvp;   // symmetric operators, order k: packed upper triangles of (Pinv + Pinv^T)/2,
                          // packed_patch_size(np_max) floats per patch (bulk-copy sweep)
+    // the FP32 closed-form sweep's split of the augmented-Lagrangian term G_c d_c d_c^T
+    // (G_c = gamma nu_c / |K|, d_c the cell's flux weights on each facet's first unknown), so that
+    // no O(gamma) value meets the FP32 inverse (2D levels with patch_cext, FP32 preconditioners):
+    DBuf<float> swQ;     // n_patches*pc_max*np_max: column si of patch p, Q = A_PP^-1 D_P G (np_max
+                         // rows at (p pc_max + si) np_max), D_P G the AL columns of the star cells
+    DBuf<float> swA00;   // n_patches*pf_max*2: entry (0, 0) of each slot's coupling block with the
+                         // cell's outside facet, without the AL term
     // 16-bit copies for HDG_MIXED_BF16 / HDG_MIXED_FP16 (order-k operator only): the
     // layouts of A and Pinv with every stored row divided by its power-of-two scale
     int *tma_flag = nullptr; // device flag of the bulk-copy sweep's bounded waits (bit 4 on timeout),
@@ -194,6 +204,9 @@ struct HostLevel3 {
     // edge patches sorted by (colour, edge id); only edges with an interior face
     int n_patches = 0, n_colours = 0, pf_max = 0, pc_max = 0;
     std::vector<int32_t> colour_ptr, patch_nf, patch_facets, patch_nc, patch_cells, patch_slot_src;
+    // n_patches*pc_max*2: the two local faces of each star cell that do not contain the patch
+    // edge (the faces opposite its end points; -1 pad)
+    std::vector<int32_t> patch_cext;
 };
 
 // transfer data between a coarse and its red-refined fine level, stored per coarse cell P:
@@ -239,6 +252,8 @@ struct DevLevel {
     DBuf<int32_t> facet_slot;  // n_int*2: the two patch slots (p pf_max + position) holding each facet
     DBuf<int32_t> patch_cint;  // finest level: n_patches*pc_max*3 interior facet of each star cell's local
                                // facets (-1 on the boundary or for padding): the order-k sweep's gather
+    DBuf<int32_t> patch_cext;  // the star cells' local facets outside the patch (HostLevel::patch_cext,
+                               // HostLevel3::patch_cext): on the finest level in 2D, on every level in 3D
     DBuf<int32_t> cell_bnd;    // nc*3: boundary facet number of each local facet or -1 (finest level)
     int64_t n_bnd = 0;         // boundary facets (finest level)
     // lowest-order sweep gather table (levels with at most GS0_TABLE_MAX_CELLS cells): per
@@ -417,6 +432,10 @@ cudaError_t launch_gs_colour_h(const DevLevel &L, const DevOperator &op, int col
                                cudaStream_t s);
 // fills op.Pinvp (allocated by the caller) from op.Pinv
 cudaError_t launch_pack_sym(const DevLevel &L, DevOperator &op, cudaStream_t s);
+// fills op.swQ and op.swA00 (allocated by the caller: n_patches*pc_max*np_max and
+// n_patches*pf_max*2 floats) from op.A, op.Pinv and the level's flux weights (2D)
+cudaError_t launch_al_split(const DevLevel &L, DevOperator &op, double nu, const double *cell_nu, double gamma,
+                            cudaStream_t s);
 // fills op.Ah, Ah_s, Pinvh, Pinvh_s (allocated by the caller) from op.A and op.Pinv
 cudaError_t launch_round16(const DevLevel &L, DevOperator &op, int fmt, cudaStream_t s);
 template <class T>

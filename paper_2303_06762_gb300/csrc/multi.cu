@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "hdg_internal.h"
 
@@ -171,32 +172,46 @@ struct Pair<double> {
 // block inverse are first staged in shared memory with independent, coalesced
 // pair-wide loads; the residual and the block solve then read only shared memory
 // (one broadcast entry per R columns).  A thread owns RB rows of one column.
-template <class T, int DPF, int RB>
+// EXT: the closed form u_s = A_ss^{-1} (g_s - A_sE u_E) (E = each star cell's facet
+// opposite the patch vertex, patch_cext; equal to the update above because Pinv inverts
+// the assembled A_ss): the rows' coupling blocks with E and the unknowns on E only.  With
+// swQ (FP32) the augmented-Lagrangian term is split off, A_ss^{-1} (g_s - A0_sE u_E) - Q z
+// with z the star cells' outside fluxes, so that no O(gamma) value meets the FP32 inverse.
+template <class T, int DPF, int RB, bool EXT>
 __global__ void __launch_bounds__(MT)
 gs_m_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const int *__restrict__ patch_nf,
             const int *__restrict__ patch_facets, const int *__restrict__ patch_nc,
             const int *__restrict__ patch_cells, const int *__restrict__ slot_src,
-            const int *__restrict__ cell_int, const T *__restrict__ A, const T *__restrict__ Pinv,
-            const T *__restrict__ g, T *__restrict__ u) {
+            const int *__restrict__ cell_int, const int *__restrict__ patch_cext, const float *__restrict__ swQ,
+            const float *__restrict__ swA00, const double *__restrict__ cell_d, const T *__restrict__ A,
+            const T *__restrict__ Pinv, const T *__restrict__ g, T *__restrict__ u) {
     using T2 = typename Pair<T>::type;
     constexpr int NLOC = 3 * DPF;
+    constexpr int NX = EXT ? DPF : NLOC;                        // columns read per row, unknowns per cell
     const int R = 1 << lgR;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *xs = reinterpret_cast<T *>(smraw);                       // pc_max * NLOC * R
-    T *rs = xs + ((size_t)pc_max * NLOC << lgR);                // np_max * R
-    T *As = rs + ((size_t)np_max << lgR);                       // pf_max * 2 * NLOC * DPF
-    T *Ps = As + (size_t)pf_max * 2 * NLOC * DPF;               // np_max * np_max
+    T *xs = reinterpret_cast<T *>(smraw);                       // pc_max * NX * R
+    T *rs = xs + ((size_t)pc_max * NX << lgR);                  // np_max * R
+    T *As = rs + ((size_t)np_max << lgR);                       // pf_max * 2 * NX * DPF
+    T *Ps = As + (size_t)pf_max * 2 * NX * DPF;                 // np_max * np_max
     int *jt = reinterpret_cast<int *>(Ps + (size_t)np_max * np_max);   // pc_max * 3
     int *rowF = jt + pc_max * 3;                                // pf_max
     int *rowA = rowF + pf_max;                                  // pf_max * 2
     int *rowS = rowA + pf_max * 2;                              // pf_max * 2
+    T *zs = reinterpret_cast<T *>(jt + ((pc_max * 3 + pf_max * 5 + 3) & ~3));   // pc_max * R (split form)
     const int p = p0 + blockIdx.x;
     if (p >= p1) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
-    for (int i = tid; i < ncell * 3; i += nt) {
-        const int c = patch_cells[(size_t)p * pc_max + i / 3];
-        jt[i] = cell_int[3 * c + i % 3];
+    const bool split = EXT && swQ;
+    if constexpr (EXT) {
+        for (int i = tid; i < ncell; i += nt)
+            jt[i] = cell_int[3 * patch_cells[(size_t)p * pc_max + i] + patch_cext[(size_t)p * pc_max + i]];
+    } else {
+        for (int i = tid; i < ncell * 3; i += nt) {
+            const int c = patch_cells[(size_t)p * pc_max + i / 3];
+            jt[i] = cell_int[3 * c + i % 3];
+        }
     }
     for (int js = tid; js < nf; js += nt) {
         rowF[js] = patch_facets[(size_t)p * pf_max + js];
@@ -204,7 +219,8 @@ gs_m_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const i
             const int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
             const int si = src >> 2, lf = src & 3;
             const int c = patch_cells[(size_t)p * pc_max + si];
-            rowA[2 * js + q] = c * NLOC * NLOC + lf * NLOC * DPF;
+            rowA[2 * js + q] = c * NLOC * NLOC + lf * NLOC * DPF +
+                               (EXT ? patch_cext[(size_t)p * pc_max + si] * DPF * DPF : 0);
             rowS[2 * js + q] = si;
         }
     }
@@ -216,21 +232,29 @@ gs_m_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const i
         for (int i = tid; i < n2; i += nt) dst[i] = src[i];
     }
     __syncthreads();
-    {   // rows (lf, 0..DPF) of every column of the two cells of each patch facet
+    {   // rows (lf, 0..DPF) of every column read (all, or the outside facet's) of the two
+        // cells of each patch facet
         constexpr int U = DPF / 2;              // pairs per column
-        const int n2 = nf * 2 * NLOC * U;
+        const int n2 = nf * 2 * NX * U;
 #pragma unroll 4
         for (int i = tid; i < n2; i += nt) {
-            const int h = i % U, col = (i / U) % NLOC, jq = i / (U * NLOC);
+            const int h = i % U, col = (i / U) % NX, jq = i / (U * NX);
             const T2 *src = reinterpret_cast<const T2 *>(A + rowA[jq] + col * DPF) + h;
-            reinterpret_cast<T2 *>(As)[i] = *src;
+            T2 v = *src;
+            if (split && h == 0 && col == 0) v.x = (T)swA00[(size_t)p * pf_max * 2 + jq];   // AL-free (0, 0)
+            reinterpret_cast<T2 *>(As)[i] = v;
         }
     }
 #pragma unroll 4
-    for (int t = tid; t < (ncell * NLOC) << lgR; t += nt) {
-        const int r = t & (R - 1), sl = t >> lgR, si = sl / NLOC, l = sl - si * NLOC;
-        const int j = jt[si * 3 + l / DPF];
-        xs[t] = j >= 0 ? u[(((size_t)j * DPF + l % DPF) << lgR) + r] : T(0);
+    for (int t = tid; t < (ncell * NX) << lgR; t += nt) {
+        const int r = t & (R - 1), sl = t >> lgR, si = sl / NX, l = sl - si * NX;
+        const int j = EXT ? jt[si] : jt[si * 3 + l / DPF];
+        const T x = j >= 0 ? u[(((size_t)j * DPF + l % DPF) << lgR) + r] : T(0);
+        xs[t] = x;
+        if (split && l == 0) {
+            const int c = patch_cells[(size_t)p * pc_max + si];
+            zs[(si << lgR) + r] = (T)cell_d[3 * (size_t)c + patch_cext[(size_t)p * pc_max + si]] * x;
+        }
     }
     __syncthreads();
     const int nrb = np / RB;
@@ -242,10 +266,10 @@ gs_m_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const i
         for (int b = 0; b < RB; ++b) acc[b] = g[(((size_t)F * DPF + d0 + b) << lgR) + r];
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            const T *Ac = As + (size_t)(2 * js + q) * NLOC * DPF + d0;
-            const T *xc = xs + ((size_t)rowS[2 * js + q] * NLOC << lgR) + r;
+            const T *Ac = As + (size_t)(2 * js + q) * NX * DPF + d0;
+            const T *xc = xs + ((size_t)rowS[2 * js + q] * NX << lgR) + r;
 #pragma unroll
-            for (int col = 0; col < NLOC; ++col) {
+            for (int col = 0; col < NX; ++col) {
                 const T xv = xc[col << lgR];
                 const T *a = Ac + col * DPF;
 #pragma unroll
@@ -268,10 +292,20 @@ gs_m_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int lgR, const i
 #pragma unroll
             for (int b = 0; b < RB; ++b) acc[b] += pj[b] * xv;
         }
+        if (split)
+            for (int si = 0; si < ncell; ++si) {
+                const T z = zs[(si << lgR) + r];
+                const float *qc = swQ + ((size_t)p * pc_max + si) * np_max + row0;
+#pragma unroll
+                for (int b = 0; b < RB; ++b) acc[b] -= (T)qc[b] * z;
+            }
         const int js = row0 / DPF, d0 = row0 - js * DPF;
         const size_t o = (((size_t)rowF[js] * DPF + d0) << lgR) + r;
 #pragma unroll
-        for (int b = 0; b < RB; ++b) u[o + ((size_t)b << lgR)] += acc[b];
+        for (int b = 0; b < RB; ++b) {
+            if constexpr (EXT) u[o + ((size_t)b << lgR)] = acc[b];
+            else u[o + ((size_t)b << lgR)] += acc[b];
+        }
     }
 }
 
@@ -786,10 +820,17 @@ cudaError_t launch_split_lo(const double *A, const float *hi, float *lo, int64_t
     return cudaGetLastError();
 }
 
+// the closed-form sweep (levels with patch_cext; FP32 with the AL split) reads dpf instead of
+// n_loc columns per row and keeps the star cells' outside fluxes after the index tables
+static bool gs_m_closed(const DevLevel &L, const DevOperator &op, bool fp32) {
+    return L.patch_cext.p && (!fp32 || (op.swQ.p && op.swA00.p));
+}
+
 size_t gs_m_smem(const DevLevel &L, const DevOperator &op, int R, size_t word) {
-    return word * (((size_t)L.pc_max * op.nloc + op.np_max) * R + (size_t)L.pf_max * 2 * op.nloc * op.dpf +
-                   (size_t)op.np_max * op.np_max) +
-           sizeof(int) * ((size_t)L.pc_max * 3 + (size_t)L.pf_max * 5);
+    const size_t nx = gs_m_closed(L, op, word == sizeof(float)) ? (size_t)op.dpf : (size_t)op.nloc;
+    return word * (((size_t)L.pc_max * nx + op.np_max) * R + (size_t)L.pf_max * 2 * nx * op.dpf +
+                   (size_t)op.np_max * op.np_max + (size_t)L.pc_max * R) +
+           sizeof(int) * (((size_t)L.pc_max * 3 + (size_t)L.pf_max * 5 + 3) & ~(size_t)3);
 }
 
 namespace {
@@ -799,13 +840,17 @@ cudaError_t gs_m_launch(const DevLevel &L, const DevOperator &op, int R, const T
     const int p0 = L.colour_ptr[colour], p1 = L.colour_ptr[colour + 1];
     if (p1 <= p0) return cudaSuccess;
     const size_t smem = gs_m_smem(L, op, R, sizeof(T));
-    auto kern = gs_m_kernel<T, DPF, RB>;
+    // closed form on levels with the outside-facet table: FP64 directly, FP32 with the AL split
+    // (the batched sweeps run on the operator's own copies, Af / Pinvf in FP32)
+    const bool fp32 = std::is_same<T, float>::value;
+    auto kern = gs_m_closed(L, op, fp32) ? gs_m_kernel<T, DPF, RB, true> : gs_m_kernel<T, DPF, RB, false>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     note_launches(1);
     kern<<<p1 - p0, nt, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, log2_width(R), L.patch_nf.p,
                                    L.patch_facets.p, L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.cell_int.p,
-                                   A, Pinv, g, u);
+                                   L.patch_cext.p, fp32 ? op.swQ.p : nullptr, fp32 ? op.swA00.p : nullptr,
+                                   L.cell_d.p, A, Pinv, g, u);
     return cudaGetLastError();
 }
 

@@ -100,29 +100,42 @@ apply_kernel(int64_t n_int, const int *__restrict__ facet_adj, const int *__rest
 }
 
 // S = storage type of A and Pinv (T, or a 16-bit type with per-row scales As[c*NLOC + row]
-// and Ps[p*np_max + row] of the element matrices and patch inverses)
-template <class T, int DPF, class S = T>
+// and Ps[p*np_max + row] of the element matrices and patch inverses).
+// EXT: the closed-form update u_P = A_PP^-1 (g_P - A_PE u_E) (E = each star cell's facet
+// opposite the patch vertex, patch_cext), which equals the correction form
+// u_P + A_PP^-1 (g - A u)_P because Pinv inverts the assembled A_PP; it reads the DPF x DPF
+// coupling blocks instead of whole facet row blocks, and the unknowns on E only.  With swQ
+// (the FP32 sweep) the AL term is split off as in gs_tma_kernel: A_PP^-1 (g_P - A0_PE u_E) - Q z.
+template <class T, int DPF, class S = T, bool EXT = false>
 __global__ void gs_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
                           const int *__restrict__ patch_nf, const int *__restrict__ patch_facets,
                           const int *__restrict__ patch_nc, const int *__restrict__ patch_cells,
                           const int *__restrict__ slot_src, const int *__restrict__ cell_int,
+                          const int *__restrict__ patch_cext, const float *__restrict__ swQ,
+                          const float *__restrict__ swA00, const double *__restrict__ cell_d,
                           const S *__restrict__ A, const float *__restrict__ As,
                           const S *__restrict__ Pinv, const float *__restrict__ Ps,
                           const T *__restrict__ g, T *__restrict__ u) {
     constexpr int NLOC = 3 * DPF;
+    constexpr int NX = EXT ? DPF : NLOC;        // gathered unknowns per star cell
     constexpr bool scaled = !std::is_same<S, T>::value;
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *xs = reinterpret_cast<T *>(smraw);     // pc_max * NLOC
-    T *r = xs + pc_max * NLOC;                 // np_max
+    T *xs = reinterpret_cast<T *>(smraw);     // pc_max * NX
+    T *r = xs + pc_max * NX;                   // np_max
+    T *zs = r + np_max;                        // pc_max outside fluxes (split form)
     const int p = p0 + blockIdx.x;
     if (p >= p1) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
-    for (int t = tid; t < ncell * NLOC; t += nt) {
-        int si = t / NLOC, l = t % NLOC;
-        int c = patch_cells[(size_t)p * pc_max + si];
-        int j = cell_int[3 * c + l / DPF];
-        xs[t] = j >= 0 ? u[(size_t)j * DPF + l % DPF] : T(0);
+    const bool split = EXT && swQ;
+    for (int t = tid; t < ncell * NX; t += nt) {
+        const int si = t / NX, l = t % NX;
+        const int c = patch_cells[(size_t)p * pc_max + si];
+        const int f = EXT ? patch_cext[(size_t)p * pc_max + si] : l / DPF;
+        const int j = cell_int[3 * c + f];
+        const T x = j >= 0 ? u[(size_t)j * DPF + l % DPF] : T(0);
+        xs[t] = x;
+        if (split && l == 0) zs[si] = (T)cell_d[3 * (size_t)c + f] * x;
     }
     __syncthreads();
     for (int t = tid; t < np; t += nt) {
@@ -133,16 +146,19 @@ __global__ void gs_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
             int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
             int si = src >> 2, lf = src & 3;
             int c = patch_cells[(size_t)p * pc_max + si];
-            const S *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + d;
-            const T *xc = xs + si * NLOC;
+            const int col0 = EXT ? patch_cext[(size_t)p * pc_max + si] * DPF : 0;
+            const S *Ac = A + (size_t)c * NLOC * NLOC + lf * NLOC * DPF + col0 * DPF + d;
+            const T *xc = xs + si * NX;
             if constexpr (scaled) {
                 T part = 0;
 #pragma unroll
-                for (int col = 0; col < NLOC; ++col) part += ld_entry(Ac + col * DPF) * xc[col];
+                for (int col = 0; col < NX; ++col) part += ld_entry(Ac + col * DPF) * xc[col];
                 acc -= As[(size_t)c * NLOC + lf * DPF + d] * part;
             } else {
+                const T a00 = (split && d == 0) ? (T)swA00[((size_t)p * pf_max + js) * 2 + q] : Ac[0];
+                acc -= a00 * xc[0];
 #pragma unroll
-                for (int col = 0; col < NLOC; ++col) acc -= Ac[col * DPF] * xc[col];
+                for (int col = 1; col < NX; ++col) acc -= Ac[col * DPF] * xc[col];
             }
         }
         r[t] = acc;
@@ -161,10 +177,13 @@ __global__ void gs_kernel(int p0, int p1, int pf_max, int pc_max, int np_max,
             a3 += ld_entry(Pi + (size_t)(j + 3) * np_max + t) * r[j + 3];
         }
         for (; j < np; ++j) a0 += ld_entry(Pi + (size_t)j * np_max + t) * r[j];
+        if (split)
+            for (int si = 0; si < ncell; ++si) a2 -= (T)swQ[((size_t)p * pc_max + si) * np_max + t] * zs[si];
         T du = (a0 + a1) + (a2 + a3);
         if constexpr (scaled) du *= Ps[(size_t)p * np_max + t];
         int F = patch_facets[(size_t)p * pf_max + t / DPF];
-        u[(size_t)F * DPF + t % DPF] += du;
+        if constexpr (EXT) u[(size_t)F * DPF + t % DPF] = du;
+        else u[(size_t)F * DPF + t % DPF] += du;
     }
 }
 
@@ -276,16 +295,17 @@ gs0t_kernel(int p0, int p1, int np_max, const int *__restrict__ tbl, const T *__
 }
 
 // ---------------------------------------------------------------- order-k sweep, TMA-staged
-// One colour phase of the order-k FP32 sweep, as gs_kernel<float, DPF>, with the
-// patch's matrices moved into shared memory by the bulk-copy engine: thread 0
-// posts the byte count on an mbarrier, then lanes of warp 0 issue one
-// cp.async.bulk per block (the patch inverse's np rows, and the facet row block
-// of A_K for each of the 2 nf (facet, cell) slots, each a contiguous stretch of
-// the row-block layout).  While the copies fly, the block gathers the star's
-// unknowns; it then waits on the mbarrier (bounded: after about a second of
-// polling it records the timeout in *flag, waits once more, bounded, for its
-// copies, and skips the update) and runs the residual rows and the inverse
-// product from shared memory in the same order as gs_kernel.
+// One colour phase of the order-k FP32 sweep (the closed-form patch update of
+// gs_kernel<float, DPF, float, true>), with the patch's matrices moved into shared
+// memory by the bulk-copy engine: thread 0 posts the byte count on an mbarrier,
+// then lanes of warp 0 issue one cp.async.bulk per block (the patch inverse, the
+// patch's Q, and for each of the 2 nf (facet, cell) slots the coupling block of
+// A_K between the facet and the cell's facet outside the patch, a contiguous
+// stretch of the row-block layout).  While the copies fly, the block gathers the
+// unknowns on the outside facets; it then waits on the mbarrier (bounded: after the
+// wait limit it records the timeout in *flag, waits again, bounded, for its copies,
+// and skips the update) and runs the residual rows and the inverse product from
+// shared memory.
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -313,17 +333,29 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity,
 // SYM: the patch inverses are symmetric (generalized Stokes) and stored as packed upper
 // triangles, row i holding columns i..np_max-1 at offset i np_max - i(i-1)/2, one patch every
 // psz floats (psz = the packed size rounded up to 4 floats, so every copy is 16-byte sized);
-// otherwise full np_max x np_max transposed inverses, of which the np used rows are copied
+// otherwise full np_max x np_max transposed inverses, of which the np used rows are copied.
+//
+// The patch update is taken in closed form.  With P the patch's facets and E the star's
+// facets outside it (one per star cell, opposite the patch vertex), the block GS step
+//   u_P <- u_P + A_PP^-1 (g - A u)_P = u_P + A_PP^-1 (g_P - A_PP u_P - A_PE u_E)
+// equals A_PP^-1 (g_P - A_PE u_E), since the stored inverse is that of the assembled A_PP;
+// with the AL term split off (al_split_kernel) it is A_PP^-1 (g_P - A0_PE u_E) - Q z.  So the
+// kernel reads, per (facet, cell) slot, only the DPF x DPF coupling block between the slot's
+// facet and the cell's outside facet (a contiguous third of the facet's row block) with its
+// (0, 0) entry replaced by the AL-free one, the unknowns on the outside facets and the patch's
+// Q, and overwrites u_P.
 template <int DPF, bool SYM>
 __global__ void __launch_bounds__(64)
 gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
               const int *__restrict__ patch_nf, const int *__restrict__ patch_facets,
               const int *__restrict__ patch_nc, const int *__restrict__ patch_cells,
               const int *__restrict__ slot_src, const int *__restrict__ patch_cint,
-              const float *__restrict__ A, const float *__restrict__ Pinv,
-              const float *__restrict__ g, float *__restrict__ u, int *flag, unsigned long long wait_ns) {
+              const int *__restrict__ patch_cext, const double *__restrict__ cell_d,
+              const float *__restrict__ A, const float *__restrict__ Pinv, const float *__restrict__ swQ,
+              const float *__restrict__ swA00, const float *__restrict__ g, float *__restrict__ u, int *flag,
+              unsigned long long wait_ns) {
     constexpr int NLOC = 3 * DPF;
-    constexpr int RB = NLOC * DPF;             // floats in one facet row block
+    constexpr int BB = DPF * DPF;              // floats in one facet-pair coupling block
     extern __shared__ __align__(128) unsigned char smraw[];
     __shared__ __align__(8) unsigned long long mbar;
     __shared__ int s_ok;
@@ -332,9 +364,11 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
     float *Ps = reinterpret_cast<float *>(smraw);            // np rows of np_max, or psz packed
-    float *As = Ps + (SYM ? (size_t)psz : (size_t)np_max * np_max);   // 2 pf_max row blocks
-    float *xs = As + (size_t)2 * pf_max * RB;                // pc_max * NLOC
-    float *r = xs + (size_t)pc_max * NLOC;                   // np_max
+    float *As = Ps + (SYM ? (size_t)psz : (size_t)np_max * np_max);   // 2 pf_max coupling blocks
+    float *Qs = As + (size_t)2 * pf_max * BB;                // pc_max columns of np_max
+    float *xs = Qs + (size_t)pc_max * np_max;                // pc_max * DPF: u on the outside facets
+    float *r = xs + (size_t)pc_max * DPF;                    // np_max
+    float *zs = r + np_max;                                  // pc_max outside fluxes
     const uint32_t bar = smem_u32(&mbar);
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
@@ -344,29 +378,38 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
     __syncthreads();
     if (tid < 32) {
         const uint32_t pbytes = (uint32_t)((SYM ? psz : np * np_max) * sizeof(float));
-        const uint32_t abytes = (uint32_t)(RB * sizeof(float));
+        const uint32_t qbytes = (uint32_t)(ncell * np_max * sizeof(float));
+        const uint32_t bbytes = (uint32_t)(BB * sizeof(float));
         if (tid == 0)
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         ::"r"(bar), "r"(pbytes + 2u * nf * abytes) : "memory");
+                         ::"r"(bar), "r"(pbytes + qbytes + 2u * nf * bbytes) : "memory");
         __syncwarp();
         if (tid == 0) {
             const float *src = Pinv + (SYM ? (size_t)p * psz : (size_t)p * np_max * np_max);
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
                          ::"r"(smem_u32(Ps)), "l"(src), "r"(pbytes), "r"(bar) : "memory");
+        } else if (tid == 1) {
+            asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                         ::"r"(smem_u32(Qs)), "l"(swQ + (size_t)p * pc_max * np_max), "r"(qbytes), "r"(bar)
+                         : "memory");
         }
         for (int sl = tid; sl < 2 * nf; sl += 32) {
             const int src = slot_src[(size_t)p * pf_max * 2 + sl];   // slot (js, q) at js*2 + q
-            const int c = patch_cells[(size_t)p * pc_max + (src >> 2)];
-            const float *blk = A + (size_t)c * NLOC * NLOC + (size_t)(src & 3) * RB;
+            const int si = src >> 2;
+            const int c = patch_cells[(size_t)p * pc_max + si];
+            const int e = patch_cext[(size_t)p * pc_max + si];
+            const float *blk = A + (size_t)c * NLOC * NLOC + (size_t)(src & 3) * NLOC * DPF + (size_t)e * BB;
             asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                         ::"r"(smem_u32(As + (size_t)sl * RB)), "l"(blk), "r"(abytes), "r"(bar) : "memory");
+                         ::"r"(smem_u32(As + (size_t)sl * BB)), "l"(blk), "r"(bbytes), "r"(bar) : "memory");
         }
     }
-    for (int t = tid; t < ncell * NLOC; t += nt) {
-        // the star's unknowns through the patch's own table of interior facets (one index load)
-        const int si = t / NLOC, l = t % NLOC;
-        const int j = patch_cint[((size_t)p * pc_max + si) * 3 + l / DPF];
-        xs[t] = j >= 0 ? u[(size_t)j * DPF + l % DPF] : 0.0f;
+    for (int t = tid; t < ncell * DPF; t += nt) {
+        const int si = t / DPF, d = t % DPF;
+        const int e = patch_cext[(size_t)p * pc_max + si];
+        const int j = patch_cint[((size_t)p * pc_max + si) * 3 + e];
+        const float x = j >= 0 ? u[(size_t)j * DPF + d] : 0.0f;
+        xs[t] = x;
+        if (d == 0) zs[si] = (float)cell_d[3 * (size_t)patch_cells[(size_t)p * pc_max + si] + e] * x;
     }
     // first wait: wait_ns of global time (0 = treated as expired at once, the testing hook of
     // the timeout path).  On expiry the patch update is skipped and bit 4 of *flag is set; the
@@ -383,15 +426,18 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
     __syncthreads();
     if (!s_ok) return;
     for (int t = tid; t < np; t += nt) {
-        int js = t / DPF, d = t % DPF;
-        int F = patch_facets[(size_t)p * pf_max + js];
+        const int js = t / DPF, d = t % DPF;
+        const int F = patch_facets[(size_t)p * pf_max + js];
         float acc = g[(size_t)F * DPF + d];
-        for (int q = 0; q < 2; ++q) {
-            int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
-            const float *Ac = As + (size_t)(js * 2 + q) * RB + d;
-            const float *xc = xs + (src >> 2) * NLOC;
 #pragma unroll
-            for (int col = 0; col < NLOC; ++col) acc -= Ac[col * DPF] * xc[col];
+        for (int q = 0; q < 2; ++q) {
+            const int sl = js * 2 + q;
+            const int src = slot_src[(size_t)p * pf_max * 2 + sl];
+            const float *Ac = As + (size_t)sl * BB + d;
+            const float *xc = xs + (src >> 2) * DPF;
+            acc -= (d == 0 ? swA00[(size_t)p * pf_max * 2 + sl] : Ac[0]) * xc[0];
+#pragma unroll
+            for (int col = 1; col < DPF; ++col) acc -= Ac[col * DPF] * xc[col];
         }
         r[t] = acc;
     }
@@ -419,8 +465,53 @@ gs_tma_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, int psz,
             }
             for (; j < np; ++j) a0 += Ps[j * np_max + t] * r[j];
         }
-        int F = patch_facets[(size_t)p * pf_max + t / DPF];
-        u[(size_t)F * DPF + t % DPF] += (a0 + a1) + (a2 + a3);
+        for (int si = 0; si < ncell; ++si) a2 -= Qs[si * np_max + t] * zs[si];
+        const int F = patch_facets[(size_t)p * pf_max + t / DPF];
+        u[(size_t)F * DPF + t % DPF] = (a0 + a1) + (a2 + a3);
+    }
+}
+
+// The augmented-Lagrangian split of the FP32 closed-form sweep.  The AL term of cell c is
+// G_c d_c d_c^T with G_c = gamma nu_c / |K| and d_c the flux weights on the first unknown of
+// each of its facets.  With z_c = d_{c,e} u_{e,0} (the outside flux through the facet e
+// opposite the patch vertex), A_PE u_E = A0_PE u_E + D_P G z, so the closed form splits into
+//   u_P = A_PP^-1 (g_P - A0_PE u_E) - Q z,   Q = A_PP^-1 D_P G,
+// whose terms carry no O(gamma) value: Q stays bounded as gamma grows (it tends to
+// A0^-1 D (D^T A0^-1 D)^+), while A_PP^-1 applied in FP32 to the O(gamma) vector D_P G z would
+// lose a factor gamma of accuracy.  One block per patch writes Q (FP64 products, rounded once)
+// and the (0, 0) entries of the slots' coupling blocks without the AL term.
+__global__ void al_split_kernel(int n_patches, int pf_max, int pc_max, int np_max, int dpf,
+                                const int *__restrict__ patch_nf, const int *__restrict__ patch_nc,
+                                const int *__restrict__ patch_cells, const int *__restrict__ slot_src,
+                                const int *__restrict__ patch_cext, const double *__restrict__ A,
+                                const double *__restrict__ Pinv, const double *__restrict__ cell_d,
+                                const double *__restrict__ cell_area, const double *__restrict__ cell_nu,
+                                double nu, double gamma, float *__restrict__ Q, float *__restrict__ A00) {
+    const int p = blockIdx.x;
+    if (p >= n_patches) return;
+    const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * dpf, nloc = 3 * dpf;
+    const int *ss = slot_src + (size_t)p * pf_max * 2;
+    for (int sl = threadIdx.x; sl < 2 * nf; sl += blockDim.x) {
+        const int si = ss[sl] >> 2, lf = ss[sl] & 3;
+        const int c = patch_cells[(size_t)p * pc_max + si];
+        const double G = gamma * (cell_nu ? cell_nu[c] : nu) / cell_area[c];
+        const int e = patch_cext[(size_t)p * pc_max + si];
+        // row 0 of facet lf, column 0 of facet e: offset lf n_loc dpf + (e dpf) dpf
+        const double a = A[(size_t)c * nloc * nloc + (size_t)lf * nloc * dpf + (size_t)e * dpf * dpf];
+        A00[(size_t)p * pf_max * 2 + sl] = (float)(a - G * cell_d[3 * (size_t)c + lf] * cell_d[3 * (size_t)c + e]);
+    }
+    const double *P = Pinv + (size_t)p * np_max * np_max;   // P[t][j] at j np_max + t
+    for (int i = threadIdx.x; i < ncell * np; i += blockDim.x) {
+        const int si = i / np, t = i - si * np;
+        const int c = patch_cells[(size_t)p * pc_max + si];
+        const double G = gamma * (cell_nu ? cell_nu[c] : nu) / cell_area[c];
+        double acc = 0.0;
+        for (int sl = 0; sl < 2 * nf; ++sl) {
+            if ((ss[sl] >> 2) != si) continue;
+            const int js = sl >> 1, lf = ss[sl] & 3;
+            acc += P[(size_t)js * dpf * np_max + t] * cell_d[3 * (size_t)c + lf];
+        }
+        Q[((size_t)p * pc_max + si) * np_max + t] = (float)(G * acc);
     }
 }
 
@@ -872,21 +963,23 @@ cudaError_t apply_dispatch(const DevLevel &L, int dpf, const T *A, const T *x, c
 
 template <int DPF, bool SYM>
 size_t tma_sweep_smem(const DevLevel &L, const DevOperator &op) {
-    const size_t rb = (size_t)3 * DPF * DPF;     // one facet row block, n_loc x dpf
+    const size_t bb = (size_t)DPF * DPF;         // one facet-pair coupling block
     const size_t pin = SYM ? (size_t)packed_patch_size(op.np_max) : (size_t)op.np_max * op.np_max;
-    return sizeof(float) * (pin + 2 * (size_t)L.pf_max * rb + (size_t)L.pc_max * 3 * DPF + op.np_max);
+    return sizeof(float) * (pin + 2 * (size_t)L.pf_max * bb + (size_t)L.pc_max * op.np_max +
+                            (size_t)L.pc_max * DPF + op.np_max + L.pc_max);
 }
 
 // the bulk copies need 16-byte aligned sources, destinations and sizes: the patch
-// inverse (np_max² floats, rows of np_max; or the packed triangle, psz floats), the facet
-// row blocks (3 DPF² floats, at cell strides of 9 DPF² floats) and both bases
+// inverse (np_max² floats, rows of np_max; or the packed triangle, psz floats), the
+// coupling blocks (DPF² floats, at offsets of multiples of DPF² floats), Q (columns of
+// np_max floats) and both bases
 template <int DPF, bool SYM>
 bool tma_sweep_ok(const DevLevel &L, const DevOperator &op, const float *A, const float *Pinv) {
     const size_t smem = tma_sweep_smem<DPF, SYM>(L, op);
     if ((op.np_max * sizeof(float)) % 16 || ((size_t)op.np_max * op.np_max * sizeof(float)) % 16 ||
-        (packed_patch_size(op.np_max) * sizeof(float)) % 16 || (3 * DPF * DPF * sizeof(float)) % 16)
+        (packed_patch_size(op.np_max) * sizeof(float)) % 16 || (DPF * DPF * sizeof(float)) % 16)
         return false;
-    if (!L.patch_cint.p) return false;
+    if (!L.patch_cint.p || !L.patch_cext.p || !op.swQ.p || !op.swA00.p) return false;
     if (reinterpret_cast<uintptr_t>(A) % 16 || reinterpret_cast<uintptr_t>(Pinv) % 16) return false;
     if (smem > 100 * 1024) return false;
     if (cudaFuncSetAttribute(gs_tma_kernel<DPF, SYM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
@@ -928,31 +1021,45 @@ cudaError_t gs_launch(const DevLevel &L, const DevOperator &op, const T *A, cons
     if constexpr (std::is_same<T, float>::value && DPF >= 4) {
         // symmetric operators sweep with the packed inverses when this is the operator's own
         // FP32 copy (half the inverse bytes); otherwise the full transposed inverses
-        const bool sym = op.Pinvp.p && Pinv == op.Pinvf.p;
+        const bool sym = op.Pinvp.p && Pinv == op.Pinvf.p && A == op.Af.p;
         if (op.tma_flag && nt == 64 && sym && tma_sweep_ok<DPF, true>(L, op, A, op.Pinvp.p)) {
             const size_t tsm = tma_sweep_smem<DPF, true>(L, op);
             note_launches(1);
             gs_tma_kernel<DPF, true><<<p1 - p0, 64, tsm, s>>>(
                 p0, p1, L.pf_max, L.pc_max, op.np_max, packed_patch_size(op.np_max), L.patch_nf.p, L.patch_facets.p,
-                L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.patch_cint.p, A, op.Pinvp.p, g, u,
-                op.tma_flag, op.tma_wait_ns);
+                L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.patch_cint.p, L.patch_cext.p, L.cell_d.p, A,
+                op.Pinvp.p, op.swQ.p, op.swA00.p, g, u, op.tma_flag, op.tma_wait_ns);
             return cudaGetLastError();
         }
-        if (op.tma_flag && nt == 64 && tma_sweep_ok<DPF, false>(L, op, A, Pinv)) {
+        if (op.tma_flag && nt == 64 && A == op.Af.p && Pinv == op.Pinvf.p &&
+            tma_sweep_ok<DPF, false>(L, op, A, Pinv)) {
             const size_t tsm = tma_sweep_smem<DPF, false>(L, op);
             note_launches(1);
             gs_tma_kernel<DPF, false><<<p1 - p0, 64, tsm, s>>>(
                 p0, p1, L.pf_max, L.pc_max, op.np_max, 0, L.patch_nf.p, L.patch_facets.p, L.patch_nc.p,
-                L.patch_cells.p, L.patch_slot_src.p, L.patch_cint.p, A, Pinv, g, u, op.tma_flag, op.tma_wait_ns);
+                L.patch_cells.p, L.patch_slot_src.p, L.patch_cint.p, L.patch_cext.p, L.cell_d.p, A, Pinv, op.swQ.p,
+                op.swA00.p, g, u, op.tma_flag, op.tma_wait_ns);
             return cudaGetLastError();
         }
     }
-    size_t smem = sizeof(T) * ((size_t)L.pc_max * 3 * DPF + op.np_max);
+    // closed form where the level has the outside-facet table: FP64 directly, FP32 with the AL
+    // split of its own matrices (otherwise the correction form)
+    const bool fp32 = std::is_same<T, float>::value;
+    const bool own = (const void *)A == (const void *)op.Af.p && (const void *)Pinv == (const void *)op.Pinvf.p;
     note_launches(1);
-    gs_kernel<T, DPF><<<p1 - p0, nt, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
-                                                L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
-                                                L.patch_slot_src.p, L.cell_int.p, A, nullptr, Pinv, nullptr,
-                                                g, u);
+    if (L.patch_cext.p && (!fp32 || (own && op.swQ.p && op.swA00.p))) {
+        const size_t smem = sizeof(T) * ((size_t)L.pc_max * DPF + op.np_max + L.pc_max);
+        gs_kernel<T, DPF, T, true><<<p1 - p0, nt, smem, s>>>(
+            p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p, L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
+            L.patch_slot_src.p, L.cell_int.p, L.patch_cext.p, fp32 ? op.swQ.p : nullptr,
+            fp32 ? op.swA00.p : nullptr, L.cell_d.p, A, nullptr, Pinv, nullptr, g, u);
+    } else {
+        const size_t smem = sizeof(T) * ((size_t)L.pc_max * 3 * DPF + op.np_max + L.pc_max);
+        gs_kernel<T, DPF><<<p1 - p0, nt, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
+                                                    L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
+                                                    L.patch_slot_src.p, L.cell_int.p, nullptr, nullptr, nullptr,
+                                                    nullptr, A, nullptr, Pinv, nullptr, g, u);
+    }
     return cudaGetLastError();
 }
 
@@ -964,12 +1071,14 @@ cudaError_t gs_launch_h(const DevLevel &L, const DevOperator &op, int colour, co
     int nt = ((op.np_max + 31) / 32) * 32;
     if (nt > 256) nt = 256;
     if (nt < 32) nt = 32;
-    size_t smem = sizeof(float) * ((size_t)L.pc_max * 3 * DPF + op.np_max);
+    // the 16-bit copies keep the correction form: their rounding model (u + P (g - A u) with
+    // the rounded matrices) is the one the 16-bit precisions are defined by
+    const size_t smem = sizeof(float) * ((size_t)L.pc_max * 3 * DPF + op.np_max + L.pc_max);
     note_launches(1);
     gs_kernel<float, DPF, S><<<p1 - p0, nt, smem, s>>>(
         p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p, L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
-        L.patch_slot_src.p, L.cell_int.p, reinterpret_cast<const S *>(op.Ah.p), op.Ah_s.p,
-        reinterpret_cast<const S *>(op.Pinvh.p), op.Pinvh_s.p, g, u);
+        L.patch_slot_src.p, L.cell_int.p, nullptr, nullptr, nullptr, nullptr, reinterpret_cast<const S *>(op.Ah.p),
+        op.Ah_s.p, reinterpret_cast<const S *>(op.Pinvh.p), op.Pinvh_s.p, g, u);
     return cudaGetLastError();
 }
 
@@ -1006,6 +1115,22 @@ cudaError_t round16_launch(const DevLevel &L, DevOperator &op, cudaStream_t s) {
 }
 
 } // namespace
+
+cudaError_t launch_al_split(const DevLevel &L, DevOperator &op, double nu, const double *cell_nu, double gamma,
+                            cudaStream_t s) {
+    if (L.n_patches == 0 || !L.patch_cext.p) return cudaSuccess;
+    const size_t nq = (size_t)L.n_patches * L.pc_max * op.np_max;
+    if (!op.swQ.p || op.swQ.n < nq || !op.swA00.p || op.swA00.n < (size_t)L.n_patches * L.pf_max * 2)
+        return cudaErrorInvalidValue;
+    cudaError_t e = cudaMemsetAsync(op.swQ.p, 0, sizeof(float) * nq, s);
+    if (e != cudaSuccess) return e;
+    note_launches(1);
+    al_split_kernel<<<L.n_patches, 128, 0, s>>>(L.n_patches, L.pf_max, L.pc_max, op.np_max, op.dpf, L.patch_nf.p,
+                                                L.patch_nc.p, L.patch_cells.p, L.patch_slot_src.p, L.patch_cext.p,
+                                                op.A.p, op.Pinv.p, L.cell_d.p, L.cell_area.p, cell_nu, nu, gamma,
+                                                op.swQ.p, op.swA00.p);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_pack_sym(const DevLevel &L, DevOperator &op, cudaStream_t s) {
     if (L.n_patches == 0) return cudaSuccess;

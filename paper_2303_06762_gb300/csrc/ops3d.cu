@@ -10,6 +10,8 @@
 //    averaging of each fine face on a coarse face from its two coarse cells, the discrete
 //    harmonic extension H = -A_TT^-1 A_TB per coarse cell, and the transposes;
 //  * Π_k^0 / Π_0^k (Algorithm 2): the constant normal, t1 and t2 coefficients of each face.
+#include <type_traits>
+
 #include "hdg3d_internal.h"
 
 namespace hdg {
@@ -44,24 +46,36 @@ apply3_kernel(int64_t n_int, const int *__restrict__ facet_adj, const int *__res
     y[idx] = g ? g[idx] - acc : acc;
 }
 
-template <class T, int DPF>
+// One colour phase of the block GS over edge patches.  EXT (the FP64 sweep) takes the
+// closed form: with P the patch's faces and E the two faces of each star cell without the
+// patch edge, the update u_P <- u_P + A_PP^-1 (g - A u)_P equals A_PP^-1 (g_P - A_PE u_E),
+// because Pinv is the inverse of the assembled A_PP; each (face, cell) slot then reads the two
+// DPF x DPF coupling blocks of its face row with the cell's outside faces (contiguous in the
+// row-block layout), half of the face's row block, and the patch overwrites u_P.  The FP32
+// sweep keeps the correction form (whole row blocks): in FP32 the closed form applies the
+// rounded inverse to O(gamma) values of the augmented-Lagrangian coupling, which costs a
+// factor gamma of accuracy (the 2D sweeps split that term off; in 3D it is not split).
+template <class T, int DPF, bool EXT>
 __global__ void gs3_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, const int *__restrict__ patch_nf,
                            const int *__restrict__ patch_facets, const int *__restrict__ patch_nc,
                            const int *__restrict__ patch_cells, const int *__restrict__ slot_src,
-                           const int *__restrict__ cell_int, const T *__restrict__ A, const T *__restrict__ Pinv,
-                           const T *__restrict__ g, T *__restrict__ u) {
+                           const int *__restrict__ cell_int, const int *__restrict__ patch_cext,
+                           const T *__restrict__ A, const T *__restrict__ Pinv, const T *__restrict__ g,
+                           T *__restrict__ u) {
     constexpr int NLOC = 4 * DPF;
+    constexpr int NX = EXT ? 2 * DPF : NLOC;   // gathered unknowns per star cell
     extern __shared__ __align__(16) unsigned char smraw[];
-    T *xs = reinterpret_cast<T *>(smraw);     // pc_max * NLOC
-    T *r = xs + pc_max * NLOC;                 // np_max
+    T *xs = reinterpret_cast<T *>(smraw);     // pc_max * NX
+    T *r = xs + pc_max * NX;                   // np_max
     const int p = p0 + blockIdx.x;
     if (p >= p1) return;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int nf = patch_nf[p], ncell = patch_nc[p], np = nf * DPF;
-    for (int t = tid; t < ncell * NLOC; t += nt) {
-        const int si = t / NLOC, l = t % NLOC;
+    for (int t = tid; t < ncell * NX; t += nt) {
+        const int si = t / NX, l = t % NX;
         const int c = patch_cells[(size_t)p * pc_max + si];
-        const int j = cell_int[4 * c + l / DPF];
+        const int f = EXT ? patch_cext[((size_t)p * pc_max + si) * 2 + l / DPF] : l / DPF;
+        const int j = cell_int[4 * c + f];
         xs[t] = j >= 0 ? u[(size_t)j * DPF + l % DPF] : T(0);
     }
     __syncthreads();
@@ -73,9 +87,17 @@ __global__ void gs3_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, c
             const int src = slot_src[((size_t)p * pf_max + js) * 2 + q];
             const int si = src >> 2, lf = src & 3;
             const int c = patch_cells[(size_t)p * pc_max + si];
-            const T *Ac = A + (size_t)c * NLOC * NLOC + (size_t)lf * NLOC * DPF + d;
-            const T *xc = xs + si * NLOC;
-            for (int col = 0; col < NLOC; ++col) acc -= Ac[col * DPF] * xc[col];
+            const T *Ar = A + (size_t)c * NLOC * NLOC + (size_t)lf * NLOC * DPF + d;
+            const T *xc = xs + si * NX;
+            if constexpr (EXT) {
+                for (int w = 0; w < 2; ++w) {
+                    const T *Ac = Ar + (size_t)patch_cext[((size_t)p * pc_max + si) * 2 + w] * DPF * DPF;
+#pragma unroll 6
+                    for (int col = 0; col < DPF; ++col) acc -= Ac[col * DPF] * xc[w * DPF + col];
+                }
+            } else {
+                for (int col = 0; col < NLOC; ++col) acc -= Ar[col * DPF] * xc[col];
+            }
         }
         r[t] = acc;
     }
@@ -90,7 +112,8 @@ __global__ void gs3_kernel(int p0, int p1, int pf_max, int pc_max, int np_max, c
         }
         if (j < np) a0 += Pi[(size_t)j * np_max + t] * r[j];
         const int F = patch_facets[(size_t)p * pf_max + t / DPF];
-        u[(size_t)F * DPF + t % DPF] += a0 + a1;
+        if constexpr (EXT) u[(size_t)F * DPF + t % DPF] = a0 + a1;
+        else u[(size_t)F * DPF + t % DPF] += a0 + a1;
     }
 }
 
@@ -234,11 +257,20 @@ cudaError_t gs3_launch(const DevLevel &L, const DevOperator &op, const T *A, con
     if (p1 <= p0) return cudaSuccess;
     int nt = ((op.np_max + 31) / 32) * 32;
     nt = std::min(std::max(nt, 32), 256);
-    const size_t smem = sizeof(T) * ((size_t)L.pc_max * 4 * DPF + op.np_max);
     note_launches(1);
-    gs3_kernel<T, DPF><<<p1 - p0, nt, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
-                                                 L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
-                                                 L.patch_slot_src.p, L.cell_int.p, A, Pinv, g, u);
+    if (std::is_same<T, double>::value && L.patch_cext.p) {
+        const size_t smem = sizeof(T) * ((size_t)L.pc_max * 2 * DPF + op.np_max);
+        gs3_kernel<T, DPF, true><<<p1 - p0, nt, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
+                                                           L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
+                                                           L.patch_slot_src.p, L.cell_int.p, L.patch_cext.p, A,
+                                                           Pinv, g, u);
+    } else {
+        const size_t smem = sizeof(T) * ((size_t)L.pc_max * 4 * DPF + op.np_max);
+        gs3_kernel<T, DPF, false><<<p1 - p0, nt, smem, s>>>(p0, p1, L.pf_max, L.pc_max, op.np_max, L.patch_nf.p,
+                                                            L.patch_facets.p, L.patch_nc.p, L.patch_cells.p,
+                                                            L.patch_slot_src.p, L.cell_int.p, nullptr, A, Pinv, g,
+                                                            u);
+    }
     return cudaGetLastError();
 }
 

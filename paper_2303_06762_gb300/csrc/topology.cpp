@@ -152,13 +152,20 @@ std::string build_level_topology(HostLevel &L, const int32_t *colour_in) {
     L.patch_facets.assign((size_t)L.n_patches * L.pf_max, -1);
     L.patch_cells.assign((size_t)L.n_patches * L.pc_max, -1);
     L.patch_slot_src.assign((size_t)L.n_patches * L.pf_max * 2, -1);
+    L.patch_cext.assign((size_t)L.n_patches * L.pc_max, -1);
     for (int p = 0; p < L.n_patches; ++p) {
         int v = pv[p];
         std::vector<int32_t> cs = vc[v];
         std::sort(cs.begin(), cs.end());
         L.patch_nf[p] = (int)pf[p].size();
         L.patch_nc[p] = (int)cs.size();
-        for (size_t i = 0; i < cs.size(); ++i) L.patch_cells[(size_t)p * L.pc_max + i] = cs[i];
+        for (size_t i = 0; i < cs.size(); ++i) {
+            L.patch_cells[(size_t)p * L.pc_max + i] = cs[i];
+            // facet f lies opposite local vertex f: the facet of the cell without v
+            for (int f = 0; f < 3; ++f)
+                if (L.cells[3 * (size_t)cs[i] + f] == v) L.patch_cext[(size_t)p * L.pc_max + i] = f;
+            if (L.patch_cext[(size_t)p * L.pc_max + i] < 0) return "patch star inconsistent";
+        }
         for (size_t j = 0; j < pf[p].size(); ++j) {
             int F = L.interior_facets[pf[p][j]];
             L.patch_facets[(size_t)p * L.pf_max + j] = pf[p][j];

@@ -205,6 +205,7 @@ std::string build_level_topology_3d(HostLevel3 &L) {
     L.patch_nc.assign(L.n_patches, 0);
     L.patch_cells.assign((size_t)L.n_patches * pc, -1);
     L.patch_slot_src.assign((size_t)L.n_patches * pf * 2, -1);
+    L.patch_cext.assign((size_t)L.n_patches * pc * 2, -1);
     for (int p = 0; p < L.n_patches; ++p) {
         const int32_t e = order[p];
         std::vector<int32_t> fac = inc[e], cl = ecells[e];
@@ -212,7 +213,20 @@ std::string build_level_topology_3d(HostLevel3 &L) {
         std::sort(cl.begin(), cl.end());
         L.patch_nf[p] = (int)fac.size();
         L.patch_nc[p] = (int)cl.size();
-        for (size_t s = 0; s < cl.size(); ++s) L.patch_cells[(size_t)p * pc + s] = cl[s];
+        for (size_t s = 0; s < cl.size(); ++s) {
+            L.patch_cells[(size_t)p * pc + s] = cl[s];
+            // face f lies opposite local vertex f: the two faces without the edge are those
+            // opposite its end points
+            int w = 0;
+            for (int f = 0; f < 4; ++f) {
+                const int32_t vf = L.cells[4 * (size_t)cl[s] + f];
+                if (vf == L.edge_v[2 * (size_t)e] || vf == L.edge_v[2 * (size_t)e + 1]) {
+                    if (w == 2) return "edge star inconsistent";
+                    L.patch_cext[((size_t)p * pc + s) * 2 + w++] = f;
+                }
+            }
+            if (w != 2) return "edge star inconsistent";
+        }
         for (size_t j = 0; j < fac.size(); ++j) {
             L.patch_facets[(size_t)p * pf + j] = fac[j];
             const int32_t F = L.interior_faces[fac[j]];
