@@ -491,7 +491,13 @@ hdg_status hdg_level_apply(hdg_ctx *ctx, int level, const double *x, double *y, 
 
 /* n_sweeps block Gauss-Seidel sweeps on u for A u = g over the vertex
  * patches, colours in increasing order (reverse = 0) or decreasing order
- * (reverse = 1, the transpose R^T).  u updated in place. */
+ * (reverse = 1, the transpose R^T).  u updated in place.  The 2D order-k
+ * sweeps (FP64 and FP32) and the FP64 sweeps of every 3D level take each patch
+ * step in the closed form u_P = A_PP^-1 (g_P - A_PE u_E), E the star cells'
+ * facets outside the patch, equal to u_P + A_PP^-1 (g - A u)_P up to rounding;
+ * the 2D FP32 sweeps split the augmented-Lagrangian term off that coupling, so
+ * their rounding does not grow with gamma.  The other sweeps (2D lowest order,
+ * 3D FP32, the 16-bit precisions) keep the correction form. */
 hdg_status hdg_smooth(hdg_ctx *ctx, int level, const double *g, double *u, int n_sweeps,
                       int reverse, hdg_stream_t stream);
 
